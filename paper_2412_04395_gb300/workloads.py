@@ -1,0 +1,194 @@
+"""Seeded synthetic workloads: grids, terrain, initial perturbations and run parameters.
+
+This module is shared by the CUDA path, the oracle, the tests and the benchmark.  It holds
+none of the dycore's arithmetic: only the inputs (flat-column face heights, nodal terrain,
+potential-temperature perturbations, face velocities) and the run parameters of each case.
+The base state, the metrics and the conversion of a perturbation into conserved variables
+are computed by each implementation on its own.
+
+Cases (sizes and initial conditions of the paper's benchmark problems, Sec. 4 and Table D):
+  density_current   2D-slab cold bubble, 256 x 4 x 64 at 100 m, Smagorinsky Cs = 0.17
+  hill_bubble       3D warm bubble over a Gaussian hill, 256 x 256 x 128 at 50 m, stretched dz
+  neutral_abl       neutral ABL LES, 1024 x 1024 x 128 at 10 m, MOST, Coriolis, seeded noise
+  convective_abl    convective ABL, 2048 x 2048 x 160 at 40 m, surface heat flux 0.2 K m/s
+Each builder takes smaller sizes for tests; spacing and physics stay those of the case.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+from typing import Optional
+
+import numpy as np
+
+# configuration enums shared by both implementations' wrappers (pure names, no arithmetic)
+MOM_UPWIND5 = 5
+SCAL_WENO5_JS, SCAL_WENO5_Z = 0, 1
+CLOSURE_NONE, CLOSURE_CONST_NU, CLOSURE_SMAGORINSKY, CLOSURE_LEARNED = 0, 1, 2, 3
+SURFACE_SLIP, SURFACE_MOST = 0, 1
+PREC_FP64, PREC_MIXED32 = 0, 1
+
+
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    dy: float
+    zeta: np.ndarray                       # nz+1 flat-column face heights [m], zeta[0] = 0
+    terrain: Optional[np.ndarray] = None   # (ny, nx) nodal terrain heights [m] at (i dx, j dy)
+    terrain_beta: int = 1
+    dt: float = 0.25
+    n_substeps: int = 6
+    beta_s: float = 0.1
+    beta_d: float = 0.1
+    mom_adv: int = MOM_UPWIND5
+    scal_adv: int = SCAL_WENO5_JS
+    closure: int = CLOSURE_NONE
+    Cs: float = 0.17
+    Pr_t: float = 1.0 / 3.0
+    nu: float = 0.0
+    gravity: float = 9.81
+    f_cor: float = 0.0
+    u_g: float = 0.0
+    v_g: float = 0.0
+    surface: int = SURFACE_SLIP
+    z0: float = 0.1
+    sfc_theta_flux: float = 0.0
+    theta_s: float = 300.0
+    brunt_N: float = 0.0
+    p_s: float = 1.0e5
+    knots: Optional[tuple] = None          # (z[], theta[]) piecewise-linear sounding
+    precision: int = PREC_FP64
+    steps: int = 1
+    # initial perturbation (potential temperature at cells) and face velocities
+    dtheta: Optional[np.ndarray] = None
+    u: Optional[np.ndarray] = None
+    v: Optional[np.ndarray] = None
+    w: Optional[np.ndarray] = None
+    notes: str = ""
+
+    @property
+    def ncell(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+
+def uniform_zeta(nz: int, dz: float) -> np.ndarray:
+    return np.arange(nz + 1, dtype=np.float64) * dz
+
+
+def stretched_zeta(nz: int, dz0: float, ratio: float) -> np.ndarray:
+    """Face heights with dz_k = dz0 * ratio**k (bottom spacing + growth ratio, Sec. 3.4)."""
+    dz = dz0 * ratio ** np.arange(nz, dtype=np.float64)
+    return np.concatenate([[0.0], np.cumsum(dz)])
+
+
+def cell_coords(nx, ny, zeta, dx, dy):
+    """Cell-centre x, y and flat-column height zeta_c as [k][j][i] arrays."""
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dy
+    zc = 0.5 * (zeta[:-1] + zeta[1:])
+    Z, Y, X = np.meshgrid(zc, y, x, indexing="ij")
+    return X, Y, Z
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """Counter-based generator (Steele, Lea & Flood 2014), uint64 arithmetic with wraparound."""
+    z = (x.astype(np.uint64) + np.uint64(0x9E3779B97F4A7C15))
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def seeded_noise(shape, seed: int, amplitude: float) -> np.ndarray:
+    """Uniform noise in [-amplitude, amplitude] from splitmix64(seed xor global cell index)."""
+    idx = np.arange(int(np.prod(shape)), dtype=np.uint64)
+    bits = splitmix64(idx ^ np.uint64(seed))
+    u01 = (bits >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return (amplitude * (2.0 * u01 - 1.0)).reshape(shape)
+
+
+# ---------------------------------------------------------------------------------- cases
+def density_current(nx=256, ny=4, nz=64, steps=100, dx=100.0, dt=0.25) -> Workload:
+    """Straka cold bubble (Sec. 4.1.1): dT = -15 (cos(pi L) + 1)/2 for L < 1, radii 4 km / 2 km,
+    centre z = 3 km; placed at the centre of a periodic domain (whole bubble, not the half
+    domain with a symmetry plane).  Neutral theta0 = 300 K, Smagorinsky Cs = 0.17."""
+    zeta = uniform_zeta(nz, dx)
+    X, Y, Z = cell_coords(nx, ny, zeta, dx, dx)
+    xc = 0.5 * nx * dx
+    L = np.sqrt(((X - xc) / 4000.0) ** 2 + ((Z - 3000.0) / 2000.0) ** 2)
+    dth = np.where(L < 1.0, -15.0 * 0.5 * (np.cos(np.pi * L) + 1.0), 0.0)
+    return Workload("density_current", nx, ny, nz, dx, dx, zeta, dt=dt, n_substeps=6,
+                    closure=CLOSURE_SMAGORINSKY, Cs=0.17, steps=steps, dtheta=dth,
+                    notes="2D-slab cold-bubble density current, FP64, Smagorinsky")
+
+
+def gaussian_hill(nx, ny, dx, dy, h0=400.0, a=1000.0):
+    """Nodal terrain h = h0 exp(-r^2/a^2) centred in the domain; nodes at (i dx, j dy)."""
+    x = np.arange(nx) * dx
+    y = np.arange(ny) * dy
+    Y, X = np.meshgrid(y, x, indexing="ij")
+    xc, yc = 0.5 * nx * dx, 0.5 * ny * dy
+    return h0 * np.exp(-((X - xc) ** 2 + (Y - yc) ** 2) / a ** 2)
+
+
+def hill_bubble(nx=256, ny=256, nz=128, steps=500, dx=50.0, dz0=20.0, ratio=1.015,
+                h0=400.0, terrain=True) -> Workload:
+    """Warm bubble (2 cos^2(pi r/2), Sec. 4.1.2 form) of +2 K, radius 500 m, centred 1 km above
+    the domain centre (computational height), over a Gaussian hill h0 = 400 m, a = 1 km;
+    theta0 = 300 exp(N^2 z/g), N = 0.01 1/s; stretched dz from 20 m; inviscid."""
+    zeta = stretched_zeta(nz, dz0, ratio)
+    X, Y, Z = cell_coords(nx, ny, zeta, dx, dx)
+    xc, yc = 0.5 * nx * dx, 0.5 * ny * dx
+    r = np.sqrt((X - xc) ** 2 + (Y - yc) ** 2 + (Z - 1000.0) ** 2) / 500.0
+    dth = np.where(r < 1.0, 2.0 * np.cos(0.5 * np.pi * r) ** 2, 0.0)
+    ter = gaussian_hill(nx, ny, dx, dx, h0=h0) if terrain else None
+    return Workload("hill_bubble", nx, ny, nz, dx, dx, zeta, terrain=ter, terrain_beta=1,
+                    dt=0.25, n_substeps=6, closure=CLOSURE_NONE, brunt_N=0.01, steps=steps,
+                    dtheta=dth, notes="3D warm bubble over a Gaussian hill, FP64, inviscid")
+
+
+NOISE_SEED = 20241205
+
+
+def _abl_common(nx, ny, nz, dx, knots, noise_top, steps, dt, name, flux, precision):
+    zeta = uniform_zeta(nz, dx)
+    X, Y, Z = cell_coords(nx, ny, zeta, dx, dx)
+    noise = seeded_noise((nz, ny, nx), NOISE_SEED, 0.25)
+    dth = np.where(Z < noise_top, noise, 0.0)
+    u = np.full((nz, ny, nx), 10.0)
+    return Workload(name, nx, ny, nz, dx, dx, zeta, dt=dt, n_substeps=10,
+                    closure=CLOSURE_SMAGORINSKY, Cs=0.17, f_cor=1.0e-4, u_g=10.0, v_g=0.0,
+                    surface=SURFACE_MOST, z0=0.1, sfc_theta_flux=flux, knots=knots,
+                    precision=precision, steps=steps, dtheta=dth, u=u)
+
+
+def neutral_abl(nx=1024, ny=1024, nz=128, steps=100, dx=10.0, precision=PREC_MIXED32) -> Workload:
+    """Neutral ABL LES: theta 300 K to 500 m, +10 K/km to 650 m, +3 K/km above; U = U_g = 10 m/s;
+    MOST z0 = 0.1 m; f = 1e-4 1/s; seeded uniform theta noise of +-0.25 K below 400 m."""
+    top = nz * dx
+    knots = (np.array([0.0, 500.0, 650.0, max(top, 651.0)]),
+             np.array([300.0, 300.0, 301.5, 301.5 + 3.0e-3 * (max(top, 651.0) - 650.0)]))
+    return _abl_common(nx, ny, nz, dx, knots, 400.0, steps, 0.1, "neutral_abl", 0.0, precision)
+
+
+def convective_abl(nx=2048, ny=2048, nz=160, steps=1000, dx=40.0, precision=PREC_MIXED32) -> Workload:
+    """Convective ABL: theta 300 K mixed to 1 km, +5 K over 100 m, then +3 K/km; surface
+    kinematic heat flux 0.2 K m/s; U_g = 10 m/s; noise as the neutral case."""
+    top = nz * dx
+    knots = (np.array([0.0, 1000.0, 1100.0, max(top, 1101.0)]),
+             np.array([300.0, 300.0, 305.0, 305.0 + 3.0e-3 * (max(top, 1101.0) - 1100.0)]))
+    return _abl_common(nx, ny, nz, dx, knots, 400.0, steps, 0.4, "convective_abl", 0.2, precision)
+
+
+CASES = {
+    "density_current": density_current,
+    "hill_bubble": hill_bubble,
+    "neutral_abl": neutral_abl,
+    "convective_abl": convective_abl,
+}
