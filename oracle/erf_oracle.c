@@ -286,6 +286,7 @@ orc *orc_create(const orc_cfg *cfg, const double *zeta, const double *hnode,
     o->ux = dalloc(NC); o->vy = dalloc(NC); o->wz = dalloc(NW); o->mu = dalloc(NC);
 
     /* node heights, App. B + canonical smoothing z = zeta + (1 - zeta/z_t)^beta h (Sec. 3.4) */
+    #pragma omp parallel for
     for (int k = 0; k <= nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -293,11 +294,13 @@ orc *orc_create(const orc_cfg *cfg, const double *zeta, const double *hnode,
                 o->zn[IX(o, i, j, k)] = o->zeta[k] + s * o->hnode[(size_t)j * nx + i];
             }
     /* w-face centre heights: 4 surrounding nodes; cell centre: average of the two w-faces (= 8 nodes) */
+    #pragma omp parallel for
     for (int k = 0; k <= nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i)
                 o->zw[IX(o, i, j, k)] = 0.25 * (o->zn[IX(o, i, j, k)] + o->zn[IX(o, i + 1, j, k)]
                                               + o->zn[IX(o, i, j + 1, k)] + o->zn[IX(o, i + 1, j + 1, k)]);
+    #pragma omp parallel for
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -310,6 +313,7 @@ orc *orc_create(const orc_cfg *cfg, const double *zeta, const double *hnode,
                                 + (o->zn[IX(o, i + 1, j, k + 1)] - o->zn[IX(o, i + 1, j, k)]));
             }
     /* h_xi at x-faces from cell-centre heights (App. B, pressure gradient); h_eta likewise */
+    #pragma omp parallel for
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -317,6 +321,7 @@ orc *orc_create(const orc_cfg *cfg, const double *zeta, const double *hnode,
                 o->heta_y[IX(o, i, j, k)] = (o->zc[IX(o, i, j, k)] - o->zc[IX(o, i, j - 1, k)]) / cfg->dy;
             }
     /* 4th-order h_xi, h_eta at w-faces from 4-node-averaged face heights (App. B, Omega) */
+    #pragma omp parallel for
     for (int k = 0; k <= nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -440,6 +445,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
 
     eos_pass(o, rho, rt);
     /* mass fluxes per unit length (Sec. 3.6: normal momentum at the face) and rho*Omega */
+    #pragma omp parallel for
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -450,6 +456,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                 o->ux[c] = ru[c] / (0.5 * (CV(o, rho, i - 1, j, k) + rho[c]));
                 o->vy[c] = rv[c] / (0.5 * (CV(o, rho, i, j - 1, k) + rho[c]));
             }
+    #pragma omp parallel for
     for (int k = 0; k <= nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -460,6 +467,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
             }
 
     /* --- continuity, Eq. con */
+    #pragma omp parallel for
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -472,6 +480,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
 
     /* --- potential temperature advection, Eq. theta: face flux = normal momentum x WENO5(theta) */
     int zf = (C->scal_adv == 1);
+    #pragma omp parallel for
     for (int k = 0; k <= nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -491,6 +500,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                 o->fz[w] = o->rom[w] * (C->scal_adv <= 1 ? orc_weno5(q, sgn(o->rom[w]), zf)
                                                           : orc_interp(q, sgn(o->rom[w]), C->scal_adv));
             }
+    #pragma omp parallel for
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -505,6 +515,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
      * location (reading R5), primitive velocity interpolated with the order mom_adv. */
     int ord = C->mom_adv;
     /* x-momentum: x-fluxes at cell centres, y-fluxes at xy-edges, z-fluxes at xz-edges */
+    #pragma omp parallel for
     for (int k = 0; k <= nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -524,6 +535,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                 for (int m = 0; m < 6; ++m) q[m] = CV(o, o->ux, i, j, k - 3 + m);
                 o->fz[w] = adv * orc_interp(q, sgn(adv), ord);
             }
+    #pragma omp parallel for
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -534,6 +546,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                 Ru[c] = -div / o->Hx[c];
             }
     /* y-momentum */
+    #pragma omp parallel for
     for (int k = 0; k <= nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -553,6 +566,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                 for (int m = 0; m < 6; ++m) q[m] = CV(o, o->vy, i, j, k - 3 + m);
                 o->fz[w] = adv * orc_interp(q, sgn(adv), ord);
             }
+    #pragma omp parallel for
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -563,6 +577,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                 Rv[c] = -div / o->Hy[c];
             }
     /* z-momentum at interior w-faces k = 1..nz-1: x/y fluxes at edges, z fluxes at cell centres */
+    #pragma omp parallel for
     for (int k = 0; k <= nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -582,6 +597,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                     o->fz[w] = adv * orc_interp(q, sgn(adv), ord);
                 }
             }
+    #pragma omp parallel for
     for (int k = 1; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -594,6 +610,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
             }
 
     /* --- pressure gradient (App. B terrain form) and buoyancy (Sec. 2.1, reading R3) */
+    #pragma omp parallel for
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -615,6 +632,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                 Ru[c] -= px;
                 Rv[c] -= py;
             }
+    #pragma omp parallel for
     for (int k = 1; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -648,6 +666,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
         double *t12 = dalloc(o->ncell), *t13 = dalloc(o->nw), *t23 = dalloc(o->nw);
         double *hx = dalloc(o->ncell), *hy = dalloc(o->ncell), *hz = dalloc(o->nw);
         int visc = (C->closure == 1 || C->closure == 2);
+        #pragma omp parallel for
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i) {
@@ -657,6 +676,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                     S33[c] = (o->wz[IX(o, i, j, k + 1)] - o->wz[IX(o, i, j, k)]) / o->Hc[c];
                     S12[c] = 0.5 * ((o->ux[c] - o->ux[IX(o, i, j - 1, k)]) / dy + (o->vy[c] - o->vy[IX(o, i - 1, j, k)]) / dx);
                 }
+        #pragma omp parallel for
         for (int k = 0; k <= nz; ++k)
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i) {
@@ -669,6 +689,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                                   + (o->wz[w] - o->wz[IX(o, i, j - 1, k)]) / dy);
                 }
         /* eddy viscosity mu = rho (Cs Delta)^2 |S|, |S| = sqrt(2 S_ij S_ij), edges averaged to centres */
+        #pragma omp parallel for
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i) {
@@ -691,6 +712,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                     t22[c] = -2.0 * mu * (S22[c] - dv / 3.0);
                     t33[c] = -2.0 * mu * (S33[c] - dv / 3.0);
                 }
+        #pragma omp parallel for
         for (int k = 0; k <= nz; ++k)
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i) {
@@ -750,6 +772,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                     hz[c] = rho[c] * C->sfc_theta_flux;
                 }
         }
+        #pragma omp parallel for
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i) {
@@ -762,6 +785,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                     Rt[c] += (hx[IX(o, i + 1, j, k)] - hx[c]) / dx + (hy[IX(o, i, j + 1, k)] - hy[c]) / dy
                            + (hz[IX(o, i, j, k + 1)] - hz[IX(o, i, j, k)]) / H;
                 }
+        #pragma omp parallel for
         for (int k = 1; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i) {
@@ -797,6 +821,7 @@ static void substep(orc *o, const double *rho_t, const double *rt_t, double dtau
 
     /* horizontal momenta: Delta U'' = dtau(-gamma R_d pi^t (dTheta~/dxi - h_xi/h_zeta dTheta~/dzeta) + R_U) */
     double *Un = dalloc(o->ncell), *Vn = dalloc(o->ncell);
+    #pragma omp parallel for
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -825,9 +850,12 @@ static void substep(orc *o, const double *rho_t, const double *rt_t, double dtau
     free(Un); free(Vn); free(Tt);
 
     /* per column: vertical implicit solve */
+#pragma omp parallel
+    {
     double *Ts = dalloc(nz), *Rs = dalloc(nz), *thw = dalloc(nz + 1), *A = dalloc(nz + 1);
     double *a = dalloc(nz), *b = dalloc(nz), *cc = dalloc(nz), *d = dalloc(nz), *x = dalloc(nz);
     double *Om = dalloc(nz + 1);
+#pragma omp for
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             /* theta^t at w-faces (walls take the adjacent cell) */
@@ -886,6 +914,7 @@ static void substep(orc *o, const double *rho_t, const double *rt_t, double dtau
             }
         }
     free(Ts); free(Rs); free(thw); free(A); free(a); free(b); free(cc); free(d); free(x); free(Om);
+    }
 }
 
 /* ------------------------------------------------------------------ RK3 step (Sec. 3.1) */
@@ -962,7 +991,7 @@ void orc_set_initial(orc *o, const double *dtheta, const double *u, const double
                 size_t c = IX(o, i, j, k);
                 double th = o->th0[c] + (dtheta ? dtheta[c] : 0.0);
                 o->rt[c] = o->rho0[c] * o->th0[c];
-                o->rho[c] = o->rt[c] / th;
+                o->rho[c] = o->rho0[c] * (o->th0[c] / th);   /* = rho0 theta0 / theta; exact at rest */
             }
     for (int k = 0; k <= o->nz; ++k)
         for (int j = 0; j < o->ny; ++j)

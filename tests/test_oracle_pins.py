@@ -469,3 +469,21 @@ def test_most_surface_drag_decelerates():
     us = 0.4 * 8.0 / np.log(5.0 / 0.1)
     np.testing.assert_allclose(r["R_rhou"][0], -rho[0] * us ** 2 / dz, rtol=1e-13)
     assert np.max(np.abs(r["R_rhou"][1:])) < 1e-13
+
+
+def test_openmp_oracle_is_bitwise_serial():
+    """The OpenMP loops of the oracle write disjoint elements; 1 and 4 threads agree bit for bit."""
+    import subprocess, sys, json
+    code = (
+        "import sys, numpy as np; sys.path.insert(0, %r); sys.path.insert(0, %r)\n"
+        "from conftest import make_oracle\n"
+        "from paper_2412_04395_gb300 import workloads as W\n"
+        "wl = W.hill_bubble(nx=20, ny=18, nz=12, dx=300.0, dz0=100.0, ratio=1.03, h0=300.0)\n"
+        "o = make_oracle(wl); o.step(2); s = o.state()\n"
+        "print(sum(hash(v.tobytes()) for v in s.values()))\n"
+    ) % (os.path.dirname(os.path.dirname(os.path.abspath(__file__))), os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for n in (1, 4):
+        env = dict(os.environ, OMP_NUM_THREADS=str(n), PYTHONHASHSEED="0")
+        outs.append(subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True).stdout.strip())
+    assert outs[0] == outs[1] and outs[0] != ""
