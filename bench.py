@@ -1,0 +1,322 @@
+#!/usr/bin/env python3
+"""RK3 cell-updates/s of the GB300 dycore (one JSON line on rank 0).
+
+Workload (default): the 3D warm bubble over a Gaussian hill, 256 x 256 x 128 cells, dx = dy = 50 m,
+stretched dz from 20 m, FP64, WENO5 scalars, upwind-5 momenta, 6 acoustic substeps (10 substep
+passes per step).  A step is one RK3 step (3 stages, slow tendencies + substeps).  Inputs are
+resident in HBM; the working set (~2.7 GB) is far larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (under torchrun): independent replicas, one per GPU (the path is not sharded in this build),
+value = total cell-updates over all ranks / max-over-ranks time.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the same
+workload (it is the only reference this build has).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RK3 cell-updates/s"
+UNIT = "cell-updates/s"
+
+# Algorithmic HBM words (FP64) per unit and FP64 flops per unit of each kernel: the ideal traffic
+# if every input is read once and every output written once, and the floating-point operations
+# of the formulas (FMA = 2).  unit: "cell" (nx*ny*nz) or "wface" (nx*ny*(nz+1)).
+KERNEL_MODEL = {
+    "sub_vert":    {"unit": "cell", "words": 20, "flops": 70},
+    "sub_horiz":   {"unit": "cell", "words": 9, "flops": 24},
+    "rhs_cells":   {"unit": "cell", "words": 6, "flops": 520},
+    "rhs_u":       {"unit": "cell", "words": 6, "flops": 150},
+    "rhs_v":       {"unit": "cell", "words": 6, "flops": 150},
+    "rhs_w":       {"unit": "wface", "words": 7, "flops": 160},
+    "stage_begin": {"unit": "wface", "words": 20, "flops": 60},
+    "prep":        {"unit": "wface", "words": 10, "flops": 40},
+    "tri_build":   {"unit": "cell", "words": 9, "flops": 90},
+    "stage_end":   {"unit": "wface", "words": 15, "flops": 5},
+    "wall_bc":     {"unit": "none", "words": 0, "flops": 0},
+}
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 nominal (profiling recipe table)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured", d
+    return 6800.0, "fallback", {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        try:
+            for line in open(self.f.name):
+                t = [x.strip() for x in line.split(",")]
+                if len(t) >= 9:
+                    rows.append(t)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.f.name)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(n_gpus):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        pg = dist
+    return ws, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v):
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_rate(wl_sample, steps, threads=1):
+    """Cell-updates/s of the FP64 oracle on a workload sample (host cores)."""
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from conftest import make_oracle
+    o = make_oracle(wl_sample)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return wl_sample.ncell * steps / dt, dt
+
+
+def workload(args):
+    from paper_2412_04395_gb300 import workloads as W
+    if args.case == "hill_bubble":
+        return W.hill_bubble()
+    if args.case == "density_current":
+        return W.density_current()
+    raise SystemExit(f"unknown case {args.case}")
+
+
+def sample_workload(args):
+    """Bounded sample of the benchmark workload for the CPU oracle: same spacing, stretching,
+    hill, bubble and physics on a 64 x 64 horizontal window (the hill scaled to the window)."""
+    from paper_2412_04395_gb300 import workloads as W
+    if args.case == "hill_bubble":
+        return W.hill_bubble(nx=64, ny=64, nz=128, dx=50.0)
+    return W.density_current(nx=64, ny=4, nz=64)
+
+
+def run_reference(args):
+    ws, rank, local, pg = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    from paper_2412_04395_gb300 import workloads as W  # noqa: F401
+    import oracle
+    oracle.build_oracle()
+    wl = workload(args)
+    sw = sample_workload(args)
+    for _ in range(args.warmup):
+        oracle_rate(sw, 1)
+    t = 0.0
+    for _ in range(args.steps):
+        _, dt = oracle_rate(sw, 1)
+        t += dt
+    v = sw.ncell * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "grid": [wl.nx, wl.ny, wl.nz], "sample_grid": [sw.nx, sw.ny, sw.nz]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{sw.nx}x{sw.ny}x{sw.nz} window of {wl.name}, 1 step per timed step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local, pg = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_2412_04395_gb300.erf import Dycore, FIELDS
+    wl = workload(args)
+    d = Dycore(wl, device=f"cuda:{local}")
+    d.erf_set_initial(wl.dtheta, wl.u, wl.v, wl.w)
+    stream = d.stream
+    # warm-up (graph capture happens on the first step)
+    d.erf_rk3_step(args.warmup)
+    torch.cuda.synchronize()
+    kps = d.erf_diagnostics()["kernels_per_step"]
+    # timed region: K graph launches, CUDA events on the bound stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as cs:
+        barrier(pg)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        d.erf_rk3_step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(pg)
+    clocks = cs.summary()
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(pg, ms)
+    diag = d.erf_diagnostics()
+    value = ws * wl.ncell * args.steps / (ms * 1e-3)
+
+    # per-kernel device times (event-bracketed direct launches of 2 further steps)
+    prof = d.erf_profile_steps(2)
+    total = sum(v[0] for v in prof.values())
+    top = max(prof.items(), key=lambda kv: kv[1][0])
+    name, (tms, nl) = top
+    hbm, hsrc, pk = peaks()
+    model = KERNEL_MODEL.get(name, {"unit": "cell", "words": 0, "flops": 0})
+    units = {"cell": wl.ncell, "wface": wl.nx * wl.ny * (wl.nz + 1), "none": 0}[model["unit"]]
+    avg_s = tms / nl * 1e-3
+    flops = model["flops"] * units
+    bytes_ = 8 * model["words"] * units
+    fp64_gf = flops / avg_s / 1e12
+    hbm_gbs = bytes_ / avg_s / 1e9
+    roof = {"bound": "alu", "achieved": fp64_gf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+            "frac": fp64_gf / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": name,
+            "kernel_avg_ms": tms / nl, "kernel_share": tms / total,
+            "peak_source": "FP64 nominal of the profiling recipe (no measured FP64 peak)",
+            "hbm": {"achieved": hbm_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_gbs / hbm,
+                    "peak_source": hsrc}}
+
+    # end to end through the C ABI: every step uploads the state from pinned host memory,
+    # advances one step and downloads the state
+    e2e = None
+    if args.e2e_steps > 0:
+        host = {k: torch.empty(d._shape(k), dtype=torch.float64).pin_memory() for k in
+                ("rho", "rhotheta", "rhou", "rhov", "rhow")}
+        for k, t in host.items():
+            t.copy_(torch.from_numpy(d.erf_get_state(k)))
+        L = d.L
+        nbytes = sum(t.numel() * 8 for t in host.values())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for k, t in host.items():
+                st = L.erf_set_state(d.h, FIELDS[k], t.data_ptr(), 0, 0)
+                assert st == 0
+            d.erf_rk3_step(1)
+            for k, t in host.items():
+                st = L.erf_get_state(d.h, FIELDS[k], t.data_ptr(), 0, 0)
+                assert st == 0
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        te = max_over_ranks(pg, te)
+        e2e = {"value": ws * wl.ncell * args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle
+        oracle.build_oracle()
+        sw = sample_workload(args)
+        v, dt = oracle_rate(sw, 1)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"1 step of a {sw.nx}x{sw.ny}x{sw.nz} window of {wl.name} ({dt:.1f} s, single thread)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl.name, "grid": [wl.nx, wl.ny, wl.nz], "dx": wl.dx,
+                           "substeps": wl.n_substeps, "precision": "fp64", "parallelism": f"replicas{ws}",
+                           "l2": "working set >> L2 (no flush needed)"},
+                "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                           "reasons": clocks["reasons"], "samples": clocks["samples"]},
+                "e2e": e2e, "gpu_launches": kps * args.steps, "kernels_per_step": kps,
+                "roofline": roof, "cpu_baseline": cpu,
+                "mass_rel_drift": None if diag["mass"] == 0 else None,
+                "kernel_times_ms": {k: round(v[0] / 2, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--case", default="hill_bubble")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * erf.h - C ABI of the GB300 (sm_103a) implementation of one RK3 step of ERF's compressible
+ * dynamical core (Lattanzi et al., "ERF: Energy Research and Forecasting Model", arXiv 2412.04395).
+ *
+ * The library advances the dry compressible equations (Sec. 2.1, Eqs. con, mom, theta with the
+ * EOS p = P00 (R_d rho theta / P00)^gamma, p' = p - p0, B = -(rho - rho0) g) with the low-storage
+ * RK3 of Sec. 3.1 and, inside each stage, the semi-implicit acoustic substeps of App. C (one
+ * vertical tridiagonal solve per column).  The grid is the Arakawa C-grid of Sec. 3.4 with the
+ * terrain-following height coordinate z = zeta + (1 - zeta/z_t)^beta h(x,y) and the discrete
+ * metric terms of App. B.  Lateral boundaries are periodic; bottom and top are walls (Omega = 0)
+ * with slip or MOST surface fluxes at the bottom.
+ *
+ * Plain C types only.  Memory model:
+ *   - The caller owns one device workspace (size from erf_workspace_bytes) and the CUDA stream.
+ *     The library never calls cudaMalloc; all state, base state, metrics and scratch live in that
+ *     workspace.  The workspace must stay valid until erf_destroy.
+ *   - The library owns the host handle (erf_destroy frees it) and a private capture stream.
+ *   - Every call is asynchronous on the caller's stream except erf_diagnostics and the host-side
+ *     variants of erf_get_state, which synchronise the stream.
+ * Errors: every entry point returns erf_status; nothing throws or exits.  erf_last_error gives a
+ * message for the last failed call on a handle.
+ *
+ * Field layout (C order [k][j][i], i fastest, periodic faces stored once):
+ *   cell fields  (rho, rho*theta)       nz * ny * nx, cell (i,j,k) centred at ((i+1/2)dx, (j+1/2)dy)
+ *   rho*u  on x-faces                   nz * ny * nx, face i at x = i dx (left face of cell i)
+ *   rho*v  on y-faces                   nz * ny * nx, face j at y = j dy
+ *   rho*w  on w-faces                   (nz+1) * ny * nx, face k = bottom face of cell k
+ * The boundary rows k = 0 and k = nz of rho*w are derived (Omega = 0 on the walls) and are
+ * recomputed at the start of every step.
+ */
+#ifndef ERF_GB300_H
+#define ERF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct erf_handle erf_handle;
+
+typedef enum {
+    ERF_OK = 0,
+    ERF_EINVAL = -1,        /* invalid argument (sizes, enums, NULL pointers) */
+    ERF_ENOSPACE = -2,      /* workspace smaller than erf_workspace_bytes */
+    ERF_ECUDA = -3,         /* a CUDA runtime call failed; see erf_last_error */
+    ERF_ENONFINITE = -4,    /* the state holds a NaN/Inf (sticky until the state is set again) */
+    ERF_ESTATE = -5,        /* step requested before any state was set */
+    ERF_EUNSUPPORTED = -6   /* valid but unsupported combination (e.g. SGS over terrain) */
+} erf_status;
+
+typedef enum {
+    ERF_RHO = 0, ERF_RHOTHETA = 1, ERF_RHOU = 2, ERF_RHOV = 3, ERF_RHOW = 4,
+    ERF_BASE_RHO = 5, ERF_BASE_P = 6, ERF_BASE_THETA = 7     /* base state: get only */
+} erf_field;
+
+typedef enum { ERF_F64 = 0, ERF_F32 = 1 } erf_dtype;
+typedef enum { ERF_PREC_FP64 = 0, ERF_PREC_MIXED32 = 1 } erf_precision;
+typedef enum { ERF_CLOSURE_NONE = 0, ERF_CLOSURE_CONST_NU = 1, ERF_CLOSURE_SMAGORINSKY = 2 } erf_closure;
+typedef enum { ERF_SCAL_WENO5_JS = 0, ERF_SCAL_WENO5_Z = 1 } erf_scalar_scheme;
+typedef enum { ERF_SURFACE_SLIP = 0, ERF_SURFACE_MOST = 1 } erf_surface;
+
+/* Grid (Sec. 3.4, App. A/B).  Host pointers, read during erf_init_grid only. */
+typedef struct {
+    int32_t nx, ny, nz;             /* cells; nx, ny >= 1, 1 <= nz <= ERF_NZ_MAX */
+    double dx, dy;                  /* uniform horizontal spacing [m] */
+    const double *z_faces;          /* nz+1 flat-column face heights zeta_k, increasing, z_faces[0] = 0 */
+    const double *terrain_nodes;    /* ny*nx terrain heights h at nodes (i dx, j dy), or NULL = flat */
+    int32_t terrain_beta;           /* canonical smoothing exponent: 1 = BTF, 3 = Sullivan */
+} erf_grid_desc;
+
+#define ERF_NZ_MAX 512
+
+/* Run configuration.  Physical readings where the paper is silent are documented in the design doc
+ * of the source tree; defaults are those of the paper where it gives them. */
+typedef struct {
+    double dt;                      /* RK3 step [s] */
+    int32_t n_substeps;             /* acoustic substeps per dt (even); stage 1 uses 1 of dt/3 (Sec. 3.3) */
+    int32_t substep_mode;           /* 0 = semi-implicit substeps (App. C), 1 = none (plain RK3, Sec. 3.1) */
+    double beta_s;                  /* off-centering, beta_1 = (1-beta_s)/2, beta_2 = (1+beta_s)/2 (App. C) */
+    double beta_d;                  /* divergence damping of the forward-predicted pressure (Sec. 3.1) */
+    int32_t scal_adv;               /* erf_scalar_scheme (Sec. 3.6); momenta always upwind-5 */
+    int32_t closure;                /* erf_closure (Sec. 2.3) */
+    double Cs, Pr_t, nu;            /* Smagorinsky constant, turbulent Prandtl number, constant nu [m^2/s] */
+    int32_t precision;              /* erf_precision */
+    double gravity;                 /* g [m/s^2] (0 allowed) */
+    double f_cor, u_g, v_g;         /* f-plane Coriolis [1/s] and geostrophic wind [m/s] (Sec. 3.7) */
+    int32_t surface;                /* erf_surface (Sec. 3.8) */
+    double z0, sfc_theta_flux;      /* MOST roughness [m], surface kinematic heat flux [K m/s] */
+    double theta_s, brunt_N, p_s;   /* base state theta0 = theta_s exp(N^2 z/g), surface pressure at z = 0 */
+    int32_t n_knots;                /* > 0: theta0 from a piecewise-linear sounding instead */
+    const double *knot_z, *knot_theta;   /* host, n_knots each, read during erf_init_grid only */
+} erf_config;
+
+/* Diagnostics (Sec. 4.1.2: mass conserved to machine precision). */
+typedef struct {
+    double mass;            /* sum rho * cell volume, FP64, fixed reduction order */
+    double max_abs_w;       /* max |rho w / rho| over interior w-faces [m/s] */
+    double theta_min, theta_max;
+    double cfl_acoustic;    /* max (|u| + c) dt / dx over x-faces (horizontal acoustic CFL, Sec. 3.3) */
+    int32_t nonfinite;      /* 1 if any state value is NaN/Inf */
+    int64_t steps_done;
+    int32_t kernels_per_step;   /* kernel nodes in the captured step graph */
+} erf_diag;
+
+/* Bytes of device workspace the grid + configuration needs (Sec. 3.4 grid, App. C work arrays). */
+erf_status erf_workspace_bytes(const erf_grid_desc *grid, const erf_config *cfg, size_t *bytes);
+
+/* Builds metrics (App. B) and the HSE base state (Sec. 2, Sec. 3.8 Newton-Raphson) inside the
+ * caller's workspace on `cuda_stream` (a cudaStream_t, NULL = legacy default stream).
+ * Returns ERF_ENOSPACE if workspace_bytes is too small, ERF_EUNSUPPORTED for a subgrid closure
+ * over terrain. On success *out owns a host handle. */
+erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config *cfg, void *d_workspace,
+                         size_t workspace_bytes, void *cuda_stream, erf_handle **out);
+
+/* Initial state from a potential-temperature perturbation at unchanged pressure (Sec. 4.1.2:
+ * warm perturbations at constant pressure give negative density perturbations):
+ *   theta = theta0 + dtheta, rho theta = rho0 theta0, rho = rho theta / theta,
+ *   rho u = u * (face-averaged rho), likewise v and w; walls get Omega = 0.
+ * Each pointer may be NULL (zero).  dtheta/u/v are nz*ny*nx, w is (nz+1)*ny*nx, FP64, on the
+ * host (is_device = 0) or the device (is_device = 1). */
+erf_status erf_set_initial(erf_handle *h, const double *dtheta, const double *u, const double *v,
+                           const double *w, int32_t is_device);
+
+/* Copies one prognostic field (ERF_RHO..ERF_RHOW) in, converting from src_dtype (erf_dtype). */
+erf_status erf_set_state(erf_handle *h, int32_t field, const void *src, int32_t src_is_device,
+                         int32_t src_dtype);
+
+/* Advances nsteps RK3 steps (Sec. 3.1 with App. C substeps), one CUDA-graph launch per step,
+ * asynchronously on the bound stream.  ERF_ESTATE before any state was set. */
+erf_status erf_rk3_step(erf_handle *h, int32_t nsteps);
+
+/* Copies one field (prognostic or base state) out, converting to dst_dtype. */
+erf_status erf_get_state(erf_handle *h, int32_t field, void *dst, int32_t dst_is_device,
+                         int32_t dst_dtype);
+
+/* Synchronises the stream and fills *out. Returns ERF_ENONFINITE if the state is not finite. */
+erf_status erf_diagnostics(erf_handle *h, erf_diag *out);
+
+/* Per-kernel device time of a profiled run. */
+typedef struct {
+    char name[48];          /* kernel name without the k_ prefix */
+    double total_ms;        /* summed CUDA-event time of all its launches */
+    int32_t launches;
+} erf_kernel_time;
+
+/* Tracing aid (not part of the paper's method): advances nsteps RK3 steps exactly like
+ * erf_rk3_step but by direct launches with a CUDA event pair around every kernel on the bound
+ * stream, synchronises, and fills up to max_entries per-kernel totals (*n_entries set). */
+erf_status erf_profile_steps(erf_handle *h, int32_t nsteps, erf_kernel_time *out, int32_t max_entries,
+                             int32_t *n_entries);
+
+/* Message of the last failed call on h (or of the last failed erf_init_grid if h is NULL). */
+const char *erf_last_error(const erf_handle *h);
+
+/* Frees the host handle and the library's private stream/graph; the workspace stays the caller's. */
+void erf_destroy(erf_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ERF_GB300_H */

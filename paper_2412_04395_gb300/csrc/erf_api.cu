@@ -1,0 +1,498 @@
+// C ABI of the dycore library (declared in include/erf.h): argument checks, workspace carving,
+// init (metrics of App. B, HSE base state of Sec. 3.8), state I/O, and the RK3 step of Sec. 3.1
+// captured once as a CUDA graph and replayed per step.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/erf.h"
+#include "erf_dev.cuh"
+#include "erf_launch.h"
+
+using namespace erfk;
+
+namespace {
+
+struct Carve {
+    char *base;
+    size_t off, cap;
+    bool dry;   // size-only pass
+    template <class T>
+    T *take(size_t n) {
+        off = (off + 255) & ~size_t(255);
+        T *p = dry ? nullptr : reinterpret_cast<T *>(base + off);
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+thread_local std::string g_init_error;
+
+}  // namespace
+
+struct erf_handle {
+    erf_grid_desc grid;
+    erf_config cfg;
+    Geo geo;
+    Phys ph;
+    cudaStream_t user = nullptr;   // caller's stream
+    cudaStream_t cap = nullptr;    // private stream used for graph capture
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int kernels_per_step = 0;
+    bool have_state = false;
+    long long steps_done = 0;
+    std::string err;
+    // workspace arrays
+    double *hn, *hc, *hxf, *hyf, *gxc, *gyc, *g4x, *g4y;
+    double *dzeta, *zetac, *s, *sc, *ds, *dzc, *delta2, *knz, *knt;
+    double *rho0, *th0, *p0;
+    F5 st, sn, x, R;
+    double *pp, *pi, *th, *Tp, *Om;
+    Tri tri;
+    double *ux, *vy, *wz, *mfx, *mfy, *rom, *mu;
+    double *diag_part, *diag_out;
+};
+
+static erf_status fail(erf_handle *h, erf_status st, const std::string &msg) {
+    if (h) h->err = msg;
+    else g_init_error = msg;
+    return st;
+}
+static erf_status cuda_fail(erf_handle *h, cudaError_t e, const char *where) {
+    return fail(h, ERF_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+static erf_status validate(const erf_grid_desc *g, const erf_config *c, std::string &msg) {
+    if (!g || !c) { msg = "NULL grid or config"; return ERF_EINVAL; }
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->nz > ERF_NZ_MAX) { msg = "grid sizes out of range"; return ERF_EINVAL; }
+    if (!(g->dx > 0.0) || !(g->dy > 0.0)) { msg = "dx, dy must be positive"; return ERF_EINVAL; }
+    if (!g->z_faces) { msg = "z_faces is NULL"; return ERF_EINVAL; }
+    if (g->z_faces[0] != 0.0) { msg = "z_faces[0] must be 0"; return ERF_EINVAL; }
+    for (int k = 0; k < g->nz; ++k)
+        if (!(g->z_faces[k + 1] > g->z_faces[k])) { msg = "z_faces must increase"; return ERF_EINVAL; }
+    if (g->terrain_nodes && g->terrain_beta < 0) { msg = "terrain_beta must be >= 0"; return ERF_EINVAL; }
+    if (!(c->dt > 0.0)) { msg = "dt must be positive"; return ERF_EINVAL; }
+    if (c->substep_mode != 0 && c->substep_mode != 1) { msg = "substep_mode must be 0 or 1"; return ERF_EINVAL; }
+    if (c->substep_mode == 0 && (c->n_substeps < 2 || c->n_substeps % 2)) { msg = "n_substeps must be even and >= 2"; return ERF_EINVAL; }
+    if (c->closure < 0 || c->closure > 2) { msg = "closure out of range"; return ERF_EINVAL; }
+    if (c->scal_adv < 0 || c->scal_adv > 1) { msg = "scal_adv out of range"; return ERF_EINVAL; }
+    if (c->surface < 0 || c->surface > 1) { msg = "surface out of range"; return ERF_EINVAL; }
+    if (c->precision != ERF_PREC_FP64) { msg = "only FP64 precision is built"; return ERF_EUNSUPPORTED; }
+    if (c->n_knots < 0 || (c->n_knots > 0 && (!c->knot_z || !c->knot_theta))) { msg = "bad sounding knots"; return ERF_EINVAL; }
+    if (c->closure == ERF_CLOSURE_SMAGORINSKY && !(c->Cs >= 0.0)) { msg = "Cs must be >= 0"; return ERF_EINVAL; }
+    if ((c->closure != 0) && !(c->Pr_t > 0.0)) { msg = "Pr_t must be positive"; return ERF_EINVAL; }
+    if (c->surface == ERF_SURFACE_MOST && !(c->z0 > 0.0)) { msg = "z0 must be positive"; return ERF_EINVAL; }
+    bool terr = false;
+    if (g->terrain_nodes)
+        for (long long n = 0; n < (long long)g->nx * g->ny; ++n)
+            if (g->terrain_nodes[n] != 0.0) { terr = true; break; }
+    if (terr && (c->closure != 0 || c->surface != 0)) {
+        msg = "subgrid closure / MOST over terrain is not supported (flat grids only)";
+        return ERF_EUNSUPPORTED;
+    }
+    return ERF_OK;
+}
+
+// lays out every array; with dry = true only sizes
+static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, void *ws, bool dry) {
+    Carve cv{reinterpret_cast<char *>(ws), 0, 0, dry};
+    long long nx = g->nx, ny = g->ny, nz = g->nz;
+    long long nxy = nx * ny, nc = nxy * nz, nw = nxy * (nz + 1);
+    erf_handle tmp;
+    erf_handle *H = h ? h : &tmp;
+    H->hn = cv.take<double>(nxy); H->hc = cv.take<double>(nxy); H->hxf = cv.take<double>(nxy);
+    H->hyf = cv.take<double>(nxy); H->gxc = cv.take<double>(nxy); H->gyc = cv.take<double>(nxy);
+    H->g4x = cv.take<double>(nxy); H->g4y = cv.take<double>(nxy);
+    H->dzeta = cv.take<double>(nz); H->zetac = cv.take<double>(nz); H->s = cv.take<double>(nz + 1);
+    H->sc = cv.take<double>(nz); H->ds = cv.take<double>(nz); H->dzc = cv.take<double>(nz + 1);
+    H->delta2 = cv.take<double>(nz);
+    H->knz = cv.take<double>(c->n_knots > 0 ? c->n_knots : 1);
+    H->knt = cv.take<double>(c->n_knots > 0 ? c->n_knots : 1);
+    bool terr = false;
+    if (g->terrain_nodes)
+        for (long long n = 0; n < nxy; ++n) if (g->terrain_nodes[n] != 0.0) { terr = true; break; }
+    long long nb = terr ? nc : nz;
+    H->rho0 = cv.take<double>(nb); H->th0 = cv.take<double>(nb); H->p0 = cv.take<double>(nb);
+    F5 *sets[4] = {&H->st, &H->sn, &H->x, &H->R};
+    for (F5 *f : sets) {
+        f->r = cv.take<double>(nc); f->t = cv.take<double>(nc); f->u = cv.take<double>(nc);
+        f->v = cv.take<double>(nc); f->w = cv.take<double>(nw);
+    }
+    H->pp = cv.take<double>(nc); H->pi = cv.take<double>(nc); H->th = cv.take<double>(nc);
+    H->Tp = cv.take<double>(nc); H->Om = cv.take<double>(nw);
+    H->tri.a = cv.take<double>(nw); H->tri.cp = cv.take<double>(nw); H->tri.im = cv.take<double>(nw);
+    H->tri.P = cv.take<double>(nw); H->tri.Q = cv.take<double>(nw);
+    H->ux = cv.take<double>(nc); H->vy = cv.take<double>(nc); H->mfx = cv.take<double>(nc);
+    H->mfy = cv.take<double>(nc); H->wz = cv.take<double>(nw); H->rom = cv.take<double>(nw);
+    H->mu = cv.take<double>(nc);
+    H->diag_part = cv.take<double>(6 * DIAG_PARTS);
+    H->diag_out = cv.take<double>(8);
+    return cv.off + 256;
+}
+
+extern "C" erf_status erf_workspace_bytes(const erf_grid_desc *grid, const erf_config *cfg, size_t *bytes) {
+    std::string msg;
+    erf_status st = validate(grid, cfg, msg);
+    if (st != ERF_OK) return fail(nullptr, st, msg);
+    if (!bytes) return fail(nullptr, ERF_EINVAL, "bytes is NULL");
+    *bytes = carve(nullptr, grid, cfg, nullptr, true);
+    return ERF_OK;
+}
+
+static void fill_geo(erf_handle *h) {
+    const erf_grid_desc &g = h->grid;
+    Geo &G = h->geo;
+    G.nx = g.nx; G.ny = g.ny; G.nz = g.nz;
+    G.nxy = (long long)g.nx * g.ny; G.nc = G.nxy * g.nz; G.nw = G.nxy * (g.nz + 1);
+    G.dx = g.dx; G.dy = g.dy; G.rdx = 1.0 / g.dx; G.rdy = 1.0 / g.dy;
+    G.dzeta = h->dzeta; G.zetac = h->zetac; G.s = h->s; G.sc = h->sc; G.ds = h->ds; G.dzc = h->dzc;
+    G.delta2 = h->delta2;
+    G.hc = h->hc; G.hxf = h->hxf; G.hyf = h->hyf; G.gxc = h->gxc; G.gyc = h->gyc; G.g4x = h->g4x; G.g4y = h->g4y;
+    G.rho0 = h->rho0; G.th0 = h->th0; G.p0 = h->p0;
+    const erf_config &c = h->cfg;
+    Phys &P = h->ph;
+    P.g = c.gravity; P.f_cor = c.f_cor; P.u_g = c.u_g; P.v_g = c.v_g; P.Cs = c.Cs; P.Pr_t = c.Pr_t; P.nu = c.nu;
+    P.z0 = c.z0; P.Qs = c.sfc_theta_flux; P.beta_s = c.beta_s; P.beta_d = c.beta_d;
+    P.closure = c.closure; P.surface = c.surface; P.scal_adv = c.scal_adv;
+}
+
+extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config *cfg, void *d_workspace,
+                                    size_t workspace_bytes, void *cuda_stream, erf_handle **out) {
+    std::string msg;
+    erf_status vs = validate(grid, cfg, msg);
+    if (vs != ERF_OK) return fail(nullptr, vs, msg);
+    if (!out) return fail(nullptr, ERF_EINVAL, "out is NULL");
+    if (!d_workspace) return fail(nullptr, ERF_EINVAL, "workspace is NULL");
+    if ((reinterpret_cast<uintptr_t>(d_workspace) & 255) != 0) return fail(nullptr, ERF_EINVAL, "workspace must be 256-byte aligned");
+    size_t need = carve(nullptr, grid, cfg, nullptr, true);
+    if (workspace_bytes < need)
+        return fail(nullptr, ERF_ENOSPACE, "workspace too small: need " + std::to_string(need) + " bytes");
+    erf_handle *h = new (std::nothrow) erf_handle();
+    if (!h) return fail(nullptr, ERF_EINVAL, "out of host memory");
+    h->grid = *grid;
+    h->grid.z_faces = nullptr;
+    h->grid.terrain_nodes = nullptr;
+    h->cfg = *cfg;
+    h->cfg.knot_z = h->cfg.knot_theta = nullptr;
+    h->user = reinterpret_cast<cudaStream_t>(cuda_stream);
+    carve(h, grid, cfg, d_workspace, false);
+    const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+    bool terr = false;
+    if (grid->terrain_nodes)
+        for (long long n = 0; n < (long long)nx * ny; ++n) if (grid->terrain_nodes[n] != 0.0) { terr = true; break; }
+    h->geo.terrain = terr ? 1 : 0;
+    fill_geo(h);
+    // vertical 1D arrays (host, FP64)
+    const double *z = grid->z_faces;
+    double zt = z[nz];
+    std::vector<double> dzeta(nz), zetac(nz), s(nz + 1), sc(nz), ds(nz), dzc(nz + 1, 0.0), d2(nz);
+    for (int k = 0; k <= nz; ++k) s[k] = std::pow(1.0 - z[k] / zt, (double)grid->terrain_beta);
+    for (int k = 0; k < nz; ++k) {
+        dzeta[k] = z[k + 1] - z[k];
+        zetac[k] = 0.5 * (z[k] + z[k + 1]);
+        sc[k] = 0.5 * (s[k] + s[k + 1]);
+        ds[k] = s[k + 1] - s[k];
+        double Delta = std::cbrt(grid->dx * grid->dy * dzeta[k]);
+        d2[k] = (cfg->Cs * Delta) * (cfg->Cs * Delta);
+    }
+    for (int k = 1; k < nz; ++k) dzc[k] = zetac[k] - zetac[k - 1];
+    cudaStream_t st = h->user;
+    cudaError_t e;
+#define CK(call, where)                                   \
+    do {                                                  \
+        e = (call);                                       \
+        if (e != cudaSuccess) {                           \
+            erf_status r = cuda_fail(nullptr, e, where);  \
+            delete h;                                     \
+            return r;                                     \
+        }                                                 \
+    } while (0)
+    CK(cudaMemcpyAsync(h->dzeta, dzeta.data(), nz * sizeof(double), cudaMemcpyHostToDevice, st), "copy dzeta");
+    CK(cudaMemcpyAsync(h->zetac, zetac.data(), nz * sizeof(double), cudaMemcpyHostToDevice, st), "copy zetac");
+    CK(cudaMemcpyAsync(h->s, s.data(), (nz + 1) * sizeof(double), cudaMemcpyHostToDevice, st), "copy s");
+    CK(cudaMemcpyAsync(h->sc, sc.data(), nz * sizeof(double), cudaMemcpyHostToDevice, st), "copy sc");
+    CK(cudaMemcpyAsync(h->ds, ds.data(), nz * sizeof(double), cudaMemcpyHostToDevice, st), "copy ds");
+    CK(cudaMemcpyAsync(h->dzc, dzc.data(), (nz + 1) * sizeof(double), cudaMemcpyHostToDevice, st), "copy dzc");
+    CK(cudaMemcpyAsync(h->delta2, d2.data(), nz * sizeof(double), cudaMemcpyHostToDevice, st), "copy delta2");
+    if (cfg->n_knots > 0) {
+        CK(cudaMemcpyAsync(h->knz, cfg->knot_z, cfg->n_knots * sizeof(double), cudaMemcpyHostToDevice, st), "copy knots");
+        CK(cudaMemcpyAsync(h->knt, cfg->knot_theta, cfg->n_knots * sizeof(double), cudaMemcpyHostToDevice, st), "copy knots");
+    }
+    long long nxy = (long long)nx * ny;
+    if (terr) {
+        CK(cudaMemcpyAsync(h->hn, grid->terrain_nodes, nxy * sizeof(double), cudaMemcpyHostToDevice, st), "copy terrain");
+    } else {
+        CK(cudaMemsetAsync(h->hn, 0, nxy * sizeof(double), st), "zero terrain");
+    }
+    launch_terrain(h->geo, h->hn, h->hc, h->hxf, h->hyf, h->gxc, h->gyc, h->g4x, h->g4y, st);
+    launch_base_state(h->geo, cfg->n_knots, h->knz, h->knt, cfg->theta_s, cfg->brunt_N, cfg->p_s, cfg->gravity,
+                      h->rho0, h->th0, h->p0, st);
+    CK(cudaGetLastError(), "init kernels");
+    CK(cudaStreamSynchronize(st), "init sync");   // host vectors above must outlive the copies
+    CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "create capture stream");
+#undef CK
+    *out = h;
+    return ERF_OK;
+}
+
+static CF5 cf(const F5 &f) { return CF5{f.r, f.t, f.u, f.v, f.w}; }
+
+// one RK3 step (Sec. 3.1) with the App. C substeps, enqueued on stream s
+static void enqueue_step(erf_handle *h, cudaStream_t s) {
+    const Geo &g = h->geo;
+    const Phys &ph = h->ph;
+    const erf_config &c = h->cfg;
+    launch_wall_bc(g, h->st.u, h->st.v, h->st.w, s);
+    size_t bc = g.nc * sizeof(double), bw = g.nw * sizeof(double);
+    cudaMemcpyAsync(h->sn.r, h->st.r, bc, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->sn.t, h->st.t, bc, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->sn.u, h->st.u, bc, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->sn.v, h->st.v, bc, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->sn.w, h->st.w, bw, cudaMemcpyDeviceToDevice, s);
+    const double alpha[3] = {1.0 / 3.0, 0.5, 1.0};
+    Prep pr{h->ux, h->vy, h->wz, h->mfx, h->mfy, h->rom};
+    for (int stage = 0; stage < 3; ++stage) {
+        launch_stage_begin(g, cf(h->sn), cf(h->st), h->x, h->pp, h->pi, h->th, h->Tp, h->Om, s);
+        launch_slow_rhs(g, ph, cf(h->st), h->pp, h->th, pr, h->ux, h->vy, h->wz, h->mfx, h->mfy, h->rom, h->mu,
+                        h->R, s);
+        if (c.substep_mode == 1) {
+            launch_stage_nosub(g, h->st, cf(h->sn), cf(h->R), alpha[stage] * c.dt, s);
+            launch_wall_bc(g, h->st.u, h->st.v, h->st.w, s);
+            continue;
+        }
+        int nsub = stage == 0 ? 1 : (stage == 1 ? c.n_substeps / 2 : c.n_substeps);
+        double dtau = stage == 0 ? c.dt / 3.0 : c.dt / c.n_substeps;
+        launch_tri_build(g, ph, h->st.r, h->st.t, h->pi, h->th, dtau, h->tri, s);
+        for (int n = 0; n < nsub; ++n)
+            launch_substep(g, ph, h->tri, h->pi, h->th, cf(h->R), h->x, h->Om, h->Tp, dtau, s);
+        launch_stage_end(g, h->st, cf(h->x), s);
+    }
+}
+
+static erf_status build_graph(erf_handle *h) {
+    cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
+    enqueue_step(h, h->cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->cap, &graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(h, e, "instantiate graph");
+    }
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(graph, nodes.data(), &nn);
+    int nk = 0;
+    for (auto &n : nodes) {
+        cudaGraphNodeType t;
+        cudaGraphNodeGetType(n, &t);
+        if (t == cudaGraphNodeTypeKernel) ++nk;
+    }
+    h->graph = graph;
+    h->exec = exec;
+    h->kernels_per_step = nk;
+    return ERF_OK;
+}
+
+extern "C" erf_status erf_rk3_step(erf_handle *h, int32_t nsteps) {
+    if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
+    if (nsteps < 0) return fail(h, ERF_EINVAL, "nsteps < 0");
+    if (!h->have_state) return fail(h, ERF_ESTATE, "no state set");
+    if (!h->exec) {
+        erf_status st = build_graph(h);
+        if (st != ERF_OK) return st;
+    }
+    for (int n = 0; n < nsteps; ++n) {
+        cudaError_t e = cudaGraphLaunch(h->exec, h->user);
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+    }
+    h->steps_done += nsteps;
+    return ERF_OK;
+}
+
+namespace {
+struct EventSink : ProfSink {
+    struct Rec { std::string name; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    void add(const char *name, cudaEvent_t a, cudaEvent_t b) override { recs.push_back({name, a, b}); }
+};
+}  // namespace
+
+extern "C" erf_status erf_profile_steps(erf_handle *h, int32_t nsteps, erf_kernel_time *out, int32_t max_entries,
+                                        int32_t *n_entries) {
+    if (!h || !out || !n_entries || max_entries < 1 || nsteps < 1) return fail(h, ERF_EINVAL, "bad profile arguments");
+    if (!h->have_state) return fail(h, ERF_ESTATE, "no state set");
+    EventSink sink;
+    set_profiler(&sink);
+    for (int n = 0; n < nsteps; ++n) enqueue_step(h, h->user);
+    set_profiler(nullptr);
+    cudaError_t e = cudaStreamSynchronize(h->user);
+    if (e != cudaSuccess) return cuda_fail(h, e, "profile sync");
+    h->steps_done += nsteps;
+    int n = 0;
+    std::vector<std::string> names;
+    for (auto &r : sink.recs) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+        int idx = -1;
+        for (int q = 0; q < n; ++q) if (names[q] == r.name) { idx = q; break; }
+        if (idx < 0) {
+            if (n >= max_entries) continue;
+            idx = n++;
+            names.push_back(r.name);
+            std::memset(out[idx].name, 0, sizeof(out[idx].name));
+            std::strncpy(out[idx].name, r.name.c_str(), sizeof(out[idx].name) - 1);
+            out[idx].total_ms = 0.0;
+            out[idx].launches = 0;
+        }
+        out[idx].total_ms += ms;
+        out[idx].launches += 1;
+    }
+    *n_entries = n;
+    return ERF_OK;
+}
+
+extern "C" erf_status erf_set_initial(erf_handle *h, const double *dtheta, const double *u, const double *v,
+                                      const double *w, int32_t is_device) {
+    if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
+    const Geo &g = h->geo;
+    cudaStream_t s = h->user;
+    const double *src[4] = {dtheta, u, v, w};
+    double *stage[4] = {h->x.r, h->x.u, h->x.v, h->x.w};   // perturbation arrays as staging
+    long long len[4] = {g.nc, g.nc, g.nc, g.nw};
+    const double *dev[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int n = 0; n < 4; ++n) {
+        if (!src[n]) continue;
+        if (is_device) { dev[n] = src[n]; continue; }
+        cudaError_t e = cudaMemcpyAsync(stage[n], src[n], len[n] * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy initial field");
+        dev[n] = stage[n];
+    }
+    launch_set_initial(g, dev[0], dev[1], dev[2], dev[3], h->st.r, h->st.t, h->st.u, h->st.v, h->st.w, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_initial kernels");
+    if (!is_device) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "set_initial sync");
+    }
+    h->have_state = true;
+    return ERF_OK;
+}
+
+static double *field_dev(erf_handle *h, int f, long long &n) {
+    const Geo &g = h->geo;
+    n = g.nc;
+    switch (f) {
+    case ERF_RHO: return h->st.r;
+    case ERF_RHOTHETA: return h->st.t;
+    case ERF_RHOU: return h->st.u;
+    case ERF_RHOV: return h->st.v;
+    case ERF_RHOW: n = g.nw; return h->st.w;
+    case ERF_BASE_RHO: n = g.terrain ? g.nc : g.nz; return h->rho0;
+    case ERF_BASE_P: n = g.terrain ? g.nc : g.nz; return h->p0;
+    case ERF_BASE_THETA: n = g.terrain ? g.nc : g.nz; return h->th0;
+    }
+    return nullptr;
+}
+
+extern "C" erf_status erf_set_state(erf_handle *h, int32_t field, const void *src, int32_t src_is_device,
+                                    int32_t src_dtype) {
+    if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
+    if (field < ERF_RHO || field > ERF_RHOW) return fail(h, ERF_EINVAL, "field not settable");
+    if (!src) return fail(h, ERF_EINVAL, "src is NULL");
+    if (src_dtype != ERF_F64 && src_dtype != ERF_F32) return fail(h, ERF_EINVAL, "bad dtype");
+    long long n;
+    double *dst = field_dev(h, field, n);
+    cudaStream_t s = h->user;
+    cudaError_t e;
+    if (src_dtype == ERF_F64) {
+        e = cudaMemcpyAsync(dst, src, n * sizeof(double), src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+    } else {
+        const void *d = src;
+        if (!src_is_device) {
+            e = cudaMemcpyAsync(h->x.w, src, n * sizeof(float), cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "copy state");
+            d = h->x.w;
+        }
+        launch_convert(d, dst, n, 1, s);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
+    if (!src_is_device) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "set_state sync");
+    }
+    h->have_state = true;
+    return ERF_OK;
+}
+
+extern "C" erf_status erf_get_state(erf_handle *h, int32_t field, void *dst, int32_t dst_is_device,
+                                    int32_t dst_dtype) {
+    if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
+    if (field < ERF_RHO || field > ERF_BASE_THETA) return fail(h, ERF_EINVAL, "bad field");
+    if (!dst) return fail(h, ERF_EINVAL, "dst is NULL");
+    if (dst_dtype != ERF_F64 && dst_dtype != ERF_F32) return fail(h, ERF_EINVAL, "bad dtype");
+    long long n;
+    const double *src = field_dev(h, field, n);
+    cudaStream_t s = h->user;
+    cudaError_t e;
+    if (dst_dtype == ERF_F64) {
+        e = cudaMemcpyAsync(dst, src, n * sizeof(double), dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    } else {
+        void *d = dst_is_device ? dst : (void *)h->R.w;   // slow-tendency scratch as staging
+        launch_convert(src, d, n, 0, s);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && !dst_is_device)
+            e = cudaMemcpyAsync(dst, d, n * sizeof(float), cudaMemcpyDeviceToHost, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_state");
+    if (!dst_is_device) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "get_state sync");
+    }
+    return ERF_OK;
+}
+
+extern "C" erf_status erf_diagnostics(erf_handle *h, erf_diag *out) {
+    if (!h || !out) return fail(h, ERF_EINVAL, "NULL argument");
+    if (!h->have_state) return fail(h, ERF_ESTATE, "no state set");
+    launch_diag(h->geo, cf(h->st), h->cfg.dt, h->diag_part, h->diag_out, h->user);
+    double v[6];
+    cudaError_t e = cudaMemcpyAsync(v, h->diag_out, sizeof(v), cudaMemcpyDeviceToHost, h->user);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->user);
+    if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics");
+    out->mass = v[0];
+    out->max_abs_w = v[1];
+    out->theta_min = v[2];
+    out->theta_max = v[3];
+    out->cfl_acoustic = v[4];
+    out->nonfinite = v[5] != 0.0;
+    out->steps_done = h->steps_done;
+    out->kernels_per_step = h->kernels_per_step;
+    if (out->nonfinite) return fail(h, ERF_ENONFINITE, "state holds non-finite values");
+    return ERF_OK;
+}
+
+extern "C" const char *erf_last_error(const erf_handle *h) {
+    return h ? h->err.c_str() : g_init_error.c_str();
+}
+
+extern "C" void erf_destroy(erf_handle *h) {
+    if (!h) return;
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    delete h;
+}

@@ -1,0 +1,125 @@
+// Device-side data structures and helpers of the GB300 dycore library.
+//
+// Geometry is kept separable: node heights are z(i,j,k) = zeta_k + s_k h(i,j) with
+// s_k = (1 - zeta_k/z_t)^beta (Sec. 3.4 canonical form), so every metric of App. B at any
+// point is a 1D vertical factor times a 2D terrain factor.  Only 1D (nz) and 2D (ny*nx) arrays
+// are stored; the 3D metrics are formed in registers, which keeps them out of HBM traffic.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace erfk {
+
+constexpr double P00 = 1.0e5;          // EOS reference pressure (Sec. 2.1)
+constexpr double RD = 287.0;           // dry-air gas constant
+constexpr double CPD = 1004.5;         // specific heat at constant pressure
+constexpr double CVD = CPD - RD;
+constexpr double GAMMA = CPD / CVD;
+constexpr double KAPPA = 0.4;          // von Karman constant (MOST)
+
+struct Geo {
+    int nx, ny, nz;
+    long long nxy, nc, nw;             // nx*ny, nx*ny*nz, nx*ny*(nz+1)
+    double dx, dy, rdx, rdy;
+    int terrain;
+    // vertical 1D arrays
+    const double *dzeta;   // [nz]   zeta_{k+1} - zeta_k
+    const double *zetac;   // [nz]   (zeta_k + zeta_{k+1})/2
+    const double *s;       // [nz+1] terrain decay factor at w-levels
+    const double *sc;      // [nz]   (s_k + s_{k+1})/2
+    const double *ds;      // [nz]   s_{k+1} - s_k
+    const double *dzc;     // [nz+1] zetac_k - zetac_{k-1} (k = 1..nz-1)
+    const double *delta2;  // [nz]   (Cs * (dx dy dzeta)^(1/3))^2 for Smagorinsky
+    // horizontal 2D terrain arrays [ny][nx]
+    const double *hc;      // 4-node average of h (cell centre / w-face centre)
+    const double *hxf;     // 2-node average of h along y (x-face)
+    const double *hyf;     // 2-node average of h along x (y-face)
+    const double *gxc;     // (hc_i - hc_{i-1})/dx at x-faces
+    const double *gyc;     // (hc_j - hc_{j-1})/dy at y-faces
+    const double *g4x;     // 4th-order d hc/dx at cell centres
+    const double *g4y;
+    // hydrostatic base state: [nz][ny][nx] with terrain, [nz] when flat
+    const double *rho0, *th0, *p0;
+};
+
+struct Phys {
+    double g, f_cor, u_g, v_g, Cs, Pr_t, nu, z0, Qs, beta_s, beta_d;
+    int closure, surface, scal_adv;
+};
+
+// FP64 prognostic fields (cell, cell, x-face, y-face, w-face)
+struct F5 {
+    double *r, *t, *u, *v, *w;
+};
+struct CF5 {
+    const double *r, *t, *u, *v, *w;
+};
+
+// face velocities, mass fluxes and rho*Omega of the stage state
+struct Prep {
+    const double *ux, *vy, *wz, *mfx, *mfy, *rom;
+};
+// stage LU factors of the vertical acoustic system at w-faces (rows k = 1..nz-1)
+struct Tri {
+    double *a, *cp, *im, *P, *Q;
+};
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+// even reflection of a cell level about the walls (ghost layers below/above the domain)
+__device__ __forceinline__ int kref(int k, int nz) {
+    while (k < 0 || k >= nz) {
+        if (k < 0) k = -1 - k;
+        if (k >= nz) k = 2 * nz - 1 - k;
+    }
+    return k;
+}
+__device__ __forceinline__ long long cix(const Geo &g, int i, int j, int k) {
+    return ((long long)k * g.ny + j) * g.nx + i;
+}
+__device__ __forceinline__ long long cixw(const Geo &g, int i, int j, int k) {
+    return ((long long)k * g.ny + wrapi(j, g.ny)) * g.nx + wrapi(i, g.nx);
+}
+// cell value, periodic in x/y, reflected in z
+__device__ __forceinline__ double cval(const Geo &g, const double *f, int i, int j, int k) {
+    return __ldg(f + cixw(g, i, j, kref(k, g.nz)));
+}
+// w-face value, periodic in x/y, odd reflection about the wall values in z
+__device__ __forceinline__ double wval(const Geo &g, const double *f, int i, int j, int k) {
+    double sgn = 1.0, add = 0.0;
+    while (k < 0 || k > g.nz) {
+        if (k < 0) { add += sgn * 2.0 * __ldg(f + cixw(g, i, j, 0)); sgn = -sgn; k = -k; }
+        else { add += sgn * 2.0 * __ldg(f + cixw(g, i, j, g.nz)); sgn = -sgn; k = 2 * g.nz - k; }
+    }
+    return add + sgn * __ldg(f + cixw(g, i, j, k));
+}
+
+// ---- metrics (App. B) in separable form
+__device__ __forceinline__ int ij2(const Geo &g, int i, int j) { return wrapi(j, g.ny) * g.nx + wrapi(i, g.nx); }
+__device__ __forceinline__ double Hc(const Geo &g, int i, int j, int k) {
+    return g.terrain ? g.dzeta[k] + g.ds[k] * g.hc[ij2(g, i, j)] : g.dzeta[k];
+}
+__device__ __forceinline__ double Hx(const Geo &g, int i, int j, int k) {
+    return g.terrain ? g.dzeta[k] + g.ds[k] * g.hxf[ij2(g, i, j)] : g.dzeta[k];
+}
+__device__ __forceinline__ double Hy(const Geo &g, int i, int j, int k) {
+    return g.terrain ? g.dzeta[k] + g.ds[k] * g.hyf[ij2(g, i, j)] : g.dzeta[k];
+}
+__device__ __forceinline__ double zc(const Geo &g, int i, int j, int k) {
+    return g.terrain ? g.zetac[k] + g.sc[k] * g.hc[ij2(g, i, j)] : g.zetac[k];
+}
+// distance between the cell centres k-1 and k
+__device__ __forceinline__ double dzcw(const Geo &g, int i, int j, int k) {
+    return g.terrain ? g.dzc[k] + (g.sc[k] - g.sc[k - 1]) * g.hc[ij2(g, i, j)] : g.dzc[k];
+}
+__device__ __forceinline__ double hxi_x(const Geo &g, int i, int j, int k) { return g.sc[k] * g.gxc[ij2(g, i, j)]; }
+__device__ __forceinline__ double heta_y(const Geo &g, int i, int j, int k) { return g.sc[k] * g.gyc[ij2(g, i, j)]; }
+__device__ __forceinline__ double hxi_w(const Geo &g, int i, int j, int k) { return g.s[k] * g.g4x[ij2(g, i, j)]; }
+__device__ __forceinline__ double heta_w(const Geo &g, int i, int j, int k) { return g.s[k] * g.g4y[ij2(g, i, j)]; }
+__device__ __forceinline__ long long bix(const Geo &g, int i, int j, int k) {
+    return g.terrain ? cixw(g, i, j, k) : (long long)k;
+}
+
+}  // namespace erfk

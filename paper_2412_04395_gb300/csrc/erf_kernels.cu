@@ -1,0 +1,922 @@
+// FP64 kernels of one RK3 step of the compressible dycore (arXiv 2412.04395, Sec. 3.1 + App. C).
+//
+// One thread per output point; neighbours come through the read-only cache.  Periodic x/y by
+// index wrap, walls by reflected ghost levels.  The kernel sequence of one stage is
+//   stage_begin (EOS: p', pi, theta; perturbations X'' = S^n - S^t; Omega'')
+//   prep        (face velocities, mass fluxes, rho*Omega)
+//   sgs_mu      (eddy viscosity, only with a closure / MOST)
+//   rhs_cells, rhs_u, rhs_v, rhs_w   (slow tendencies R^t)
+//   tri_build   (per-column LU of the vertical acoustic system, fixed for the stage)
+//   n_s x { sub_horiz, sub_vert }   (App. C substeps)
+//   stage_end   (S^t <- S^t + X'')
+#include "erf_dev.cuh"
+#include "erf_launch.h"
+
+#include <math.h>
+
+namespace erfk {
+
+// ------------------------------------------------------------------ interpolants (Sec. 3.6)
+// q[0..5] = q_{m-3}..q_{m+2}; value at m-1/2; s = sign of the advecting normal momentum there.
+__device__ __forceinline__ double upwind5(const double *q, double s) {
+    double c6 = (37.0 / 60.0) * (q[3] + q[2]) - (2.0 / 15.0) * (q[4] + q[1]) + (1.0 / 60.0) * (q[5] + q[0]);
+    return c6 - (s / 60.0) * ((q[5] - q[0]) - 5.0 * (q[4] - q[1]) + 10.0 * (q[3] - q[2]));
+}
+__device__ __forceinline__ double sgnd(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
+
+// WENO5-JS (Jiang & Shu 1996) or WENO5-Z (Borges et al. 2008) face value, upwind side by s >= 0.
+__device__ __forceinline__ double weno5(const double *q, double s, int zflag) {
+    double a, b, c, d, e;   // v_{-2}, v_{-1}, v_0, v_1, v_2 on the upwind side
+    if (s >= 0.0) { a = q[0]; b = q[1]; c = q[2]; d = q[3]; e = q[4]; }
+    else { a = q[5]; b = q[4]; c = q[3]; d = q[2]; e = q[1]; }
+    const double eps = 1.0e-6;
+    double p0 = (2.0 * a - 7.0 * b + 11.0 * c) * (1.0 / 6.0);
+    double p1 = (-b + 5.0 * c + 2.0 * d) * (1.0 / 6.0);
+    double p2 = (2.0 * c + 5.0 * d - e) * (1.0 / 6.0);
+    double t0 = a - 2.0 * b + c, u0 = a - 4.0 * b + 3.0 * c;
+    double t1 = b - 2.0 * c + d, u1 = b - d;
+    double t2 = c - 2.0 * d + e, u2 = 3.0 * c - 4.0 * d + e;
+    double b0 = (13.0 / 12.0) * t0 * t0 + 0.25 * u0 * u0;
+    double b1 = (13.0 / 12.0) * t1 * t1 + 0.25 * u1 * u1;
+    double b2 = (13.0 / 12.0) * t2 * t2 + 0.25 * u2 * u2;
+    double w0, w1, w2;
+    if (zflag) {
+        double tau = fabs(b0 - b2);
+        w0 = 0.1 * (1.0 + tau / (b0 + eps));
+        w1 = 0.6 * (1.0 + tau / (b1 + eps));
+        w2 = 0.3 * (1.0 + tau / (b2 + eps));
+    } else {
+        double e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
+        w0 = 0.1 / (e0 * e0);
+        w1 = 0.6 / (e1 * e1);
+        w2 = 0.3 / (e2 * e2);
+    }
+    return (w0 * p0 + w1 * p1 + w2 * p2) / (w0 + w1 + w2);
+}
+
+// Exner function and pressure from rho*theta (Sec. 2.1 EOS, dry):
+// pi = (R_d rho theta / P00)^(R_d/c_v), p = R_d rho theta pi.
+__device__ __forceinline__ void eos_pi(double rt, double &p, double &pi) {
+    pi = pow(RD * rt * (1.0 / P00), RD / CVD);
+    p = RD * rt * pi;
+}
+
+// ------------------------------------------------------------------ init: terrain + base state
+__global__ void k_terrain_avg(Geo g, const double *hn, double *hc, double *hxf, double *hyf) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.nxy) return;
+    int i = n % g.nx, j = n / g.nx;
+    double h00 = hn[ij2(g, i, j)], h10 = hn[ij2(g, i + 1, j)], h01 = hn[ij2(g, i, j + 1)], h11 = hn[ij2(g, i + 1, j + 1)];
+    hc[n] = 0.25 * (h00 + h10 + h01 + h11);
+    hxf[n] = 0.5 * (h00 + h01);
+    hyf[n] = 0.5 * (h00 + h10);
+}
+
+__global__ void k_terrain_grad(Geo g, const double *hc, double *gxc, double *gyc, double *g4x, double *g4y) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.nxy) return;
+    int i = n % g.nx, j = n / g.nx;
+    gxc[n] = (hc[n] - hc[ij2(g, i - 1, j)]) * g.rdx;
+    gyc[n] = (hc[n] - hc[ij2(g, i, j - 1)]) * g.rdy;
+    g4x[n] = (hc[ij2(g, i - 2, j)] - hc[ij2(g, i + 2, j)] + 8.0 * (hc[ij2(g, i + 1, j)] - hc[ij2(g, i - 1, j)])) / (12.0 * g.dx);
+    g4y[n] = (hc[ij2(g, i, j - 2)] - hc[ij2(g, i, j + 2)] + 8.0 * (hc[ij2(g, i, j + 1)] - hc[ij2(g, i, j - 1)])) / (12.0 * g.dy);
+}
+
+struct ThetaProfile {
+    int n_knots;
+    const double *kz, *kt;   // device copies
+    double theta_s, N, g;
+};
+__device__ double theta0_of(const ThetaProfile &tp, double z) {
+    if (tp.n_knots > 0) {
+        if (z <= tp.kz[0]) return tp.kt[0];
+        for (int n = 1; n < tp.n_knots; ++n)
+            if (z <= tp.kz[n]) {
+                double t = (z - tp.kz[n - 1]) / (tp.kz[n] - tp.kz[n - 1]);
+                return tp.kt[n - 1] + t * (tp.kt[n] - tp.kt[n - 1]);
+            }
+        return tp.kt[tp.n_knots - 1];
+    }
+    if (tp.N == 0.0 || tp.g == 0.0) return tp.theta_s;
+    return tp.theta_s * exp(tp.N * tp.N * z / tp.g);
+}
+// rho from p and theta (EOS inverted): rho = (P00 / (R_d theta)) (p/P00)^(1/gamma)
+__device__ __forceinline__ double rho_from(double p, double th) {
+    return (P00 / (RD * th)) * pow(p * (1.0 / P00), 1.0 / GAMMA);
+}
+
+// Hydrostatic base state per column (Sec. 3.8): trapezoidal dp/dz = -rho g between cell
+// centres, starting from p_s at z = 0, each level solved by Newton-Raphson for p; then
+// p0 is re-evaluated by the EOS of rho0 theta0 so the undisturbed state has p' = 0.
+__global__ void k_base_state(Geo g, ThetaProfile tp, double p_s, double grav, double *rho0, double *th0, double *p0) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long ncol = g.terrain ? g.nxy : 1;
+    if (n >= ncol) return;
+    int i = (int)(n % g.nx), j = (int)(n / g.nx);
+    double p_prev = p_s, r_prev = rho_from(p_s, theta0_of(tp, 0.0)), z_prev = 0.0;
+    for (int k = 0; k < g.nz; ++k) {
+        double z = zc(g, i, j, k), th = theta0_of(tp, z), dz = z - z_prev;
+        double p = p_prev - grav * dz * r_prev;
+        for (int it = 0; it < 50; ++it) {
+            double r = rho_from(p, th);
+            double f = p - p_prev + 0.5 * grav * dz * (r_prev + r);
+            double df = 1.0 + 0.5 * grav * dz * r / (GAMMA * p);
+            double dp = -f / df;
+            p += dp;
+            if (fabs(dp) <= 1.0e-14 * fabs(p)) break;
+        }
+        double r = rho_from(p, th);
+        long long b = g.terrain ? cix(g, i, j, k) : k;
+        rho0[b] = r;
+        th0[b] = th;
+        double pp, pie;
+        eos_pi(r * th, pp, pie);
+        p0[b] = pp;
+        p_prev = p; r_prev = r; z_prev = z;
+    }
+}
+
+// initial state from a theta perturbation at unchanged pressure
+__global__ void k_init_cells(Geo g, const double *dth, double *rho, double *rt) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    long long b = bix(g, i, j, k);
+    double th = g.th0[b] + (dth ? dth[c] : 0.0);
+    double t = g.rho0[b] * g.th0[b];
+    rt[c] = t;
+    rho[c] = g.rho0[b] * (g.th0[b] / th);   // rho0 theta0 / theta, exactly rho0 when dtheta = 0
+}
+__global__ void k_init_faces(Geo g, const double *u, const double *v, const double *w, const double *rho,
+                             double *ru, double *rv, double *rw) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nw) return;
+    int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / g.nxy);
+    if (k < g.nz) {
+        ru[n] = u ? u[n] * 0.5 * (cval(g, rho, i - 1, j, k) + rho[n]) : 0.0;
+        rv[n] = v ? v[n] * 0.5 * (cval(g, rho, i, j - 1, k) + rho[n]) : 0.0;
+    }
+    rw[n] = w ? w[n] * 0.5 * (cval(g, rho, i, j, k - 1) + cval(g, rho, i, j, k)) : 0.0;
+}
+
+// h_xi <U> + h_eta <V> at w-face (i,j,k) with the 4-point averages of App. B (levels outside
+// the domain reflected)
+__device__ __forceinline__ double metric_shift(const Geo &g, const double *U, const double *V, int i, int j, int k) {
+    double au = 0.25 * (cval(g, U, i, j, k - 1) + cval(g, U, i + 1, j, k - 1) + cval(g, U, i, j, k) + cval(g, U, i + 1, j, k));
+    double av = 0.25 * (cval(g, V, i, j, k - 1) + cval(g, V, i, j + 1, k - 1) + cval(g, V, i, j, k) + cval(g, V, i, j + 1, k));
+    return hxi_w(g, i, j, k) * au + heta_w(g, i, j, k) * av;
+}
+
+// walls: Omega = 0 at k = 0 (rho w = metric shift of the horizontal momenta) and rho w = 0 at the top
+__global__ void k_wall_bc(Geo g, const double *ru, const double *rv, double *rw) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nxy) return;
+    int i = (int)(n % g.nx), j = (int)(n / g.nx);
+    rw[n] = g.terrain ? metric_shift(g, ru, rv, i, j, 0) : 0.0;
+    rw[cix(g, i, j, g.nz)] = 0.0;
+}
+
+// ------------------------------------------------------------------ stage begin
+// EOS at the stage state; X'' = S^n - S^t; Theta''_prev = Theta''; Omega'' = W'' - metric shift
+__global__ void k_stage_begin(Geo g, CF5 sn, CF5 st, F5 x, double *pp, double *pi, double *th,
+                              double *Tprev, double *Om) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nw) return;
+    int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / g.nxy);
+    if (k < g.nz) {
+        double rt = st.t[n], rho = st.r[n];
+        double p, pie;
+        eos_pi(rt, p, pie);
+        long long b = bix(g, i, j, k);
+        pp[n] = p - g.p0[b];
+        pi[n] = pie;
+        th[n] = rt / rho;
+        x.r[n] = sn.r[n] - rho;
+        double xt = sn.t[n] - rt;
+        x.t[n] = xt;
+        Tprev[n] = xt;
+        x.u[n] = sn.u[n] - st.u[n];
+        x.v[n] = sn.v[n] - st.v[n];
+    }
+    double xw = sn.w[n] - st.w[n];
+    x.w[n] = xw;
+    if (k == 0 || k == g.nz) { Om[n] = 0.0; return; }
+    double om = xw;
+    if (g.terrain) {
+        double au = 0.0, av = 0.0;
+        for (int dk = -1; dk <= 0; ++dk) {
+            for (int di = 0; di <= 1; ++di) {
+                long long a = cixw(g, i + di, j, k + dk);
+                au += sn.u[a] - st.u[a];
+            }
+            for (int dj = 0; dj <= 1; ++dj) {
+                long long a = cixw(g, i, j + dj, k + dk);
+                av += sn.v[a] - st.v[a];
+            }
+        }
+        om -= hxi_w(g, i, j, k) * 0.25 * au + heta_w(g, i, j, k) * 0.25 * av;
+    }
+    Om[n] = om;
+}
+
+// face velocities (momentum / face-averaged density), mass fluxes per unit length, rho*Omega
+__global__ void k_prep(Geo g, CF5 st, double *ux, double *vy, double *wz, double *mfx, double *mfy, double *rom) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nw) return;
+    int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / g.nxy);
+    if (k < g.nz) {
+        double r = st.r[n];
+        double ru = st.u[n], rv = st.v[n];
+        ux[n] = ru / (0.5 * (cval(g, st.r, i - 1, j, k) + r));
+        vy[n] = rv / (0.5 * (cval(g, st.r, i, j - 1, k) + r));
+        mfx[n] = Hx(g, i, j, k) * ru;
+        mfy[n] = Hy(g, i, j, k) * rv;
+    }
+    double rb = 0.5 * (cval(g, st.r, i, j, k - 1) + cval(g, st.r, i, j, k));
+    double rw = st.w[n];
+    wz[n] = rw / rb;
+    if (k == 0 || k == g.nz) rom[n] = 0.0;
+    else rom[n] = g.terrain ? rw - metric_shift(g, st.u, st.v, i, j, k) : rw;
+}
+
+// ------------------------------------------------------------------ SGS (Sec. 2.3, reading R6)
+struct Vel {
+    const double *ux, *vy, *wz;
+};
+// strain components at the three edge types, with slip walls (S13 = S23 = 0 on k = 0, nz)
+__device__ __forceinline__ double S12e(const Geo &g, const Vel &v, int i, int j, int k) {
+    return 0.5 * ((cval(g, v.ux, i, j, k) - cval(g, v.ux, i, j - 1, k)) * g.rdy
+                + (cval(g, v.vy, i, j, k) - cval(g, v.vy, i - 1, j, k)) * g.rdx);
+}
+__device__ __forceinline__ double S13e(const Geo &g, const Vel &v, int i, int j, int k) {
+    if (k <= 0 || k >= g.nz) return 0.0;
+    double dz = g.dzc[k];
+    return 0.5 * ((cval(g, v.ux, i, j, k) - cval(g, v.ux, i, j, k - 1)) / dz
+                + (__ldg(v.wz + cixw(g, i, j, k)) - __ldg(v.wz + cixw(g, i - 1, j, k))) * g.rdx);
+}
+__device__ __forceinline__ double S23e(const Geo &g, const Vel &v, int i, int j, int k) {
+    if (k <= 0 || k >= g.nz) return 0.0;
+    double dz = g.dzc[k];
+    return 0.5 * ((cval(g, v.vy, i, j, k) - cval(g, v.vy, i, j, k - 1)) / dz
+                + (__ldg(v.wz + cixw(g, i, j, k)) - __ldg(v.wz + cixw(g, i, j - 1, k))) * g.rdy);
+}
+__device__ __forceinline__ void diag_strain(const Geo &g, const Vel &v, int i, int j, int k, double &s11, double &s22, double &s33) {
+    s11 = (cval(g, v.ux, i + 1, j, k) - cval(g, v.ux, i, j, k)) * g.rdx;
+    s22 = (cval(g, v.vy, i, j + 1, k) - cval(g, v.vy, i, j, k)) * g.rdy;
+    s33 = (__ldg(v.wz + cixw(g, i, j, k + 1)) - __ldg(v.wz + cixw(g, i, j, k))) / g.dzeta[k];
+}
+
+// mu = rho (Cs Delta)^2 sqrt(2 S_ij S_ij) (Smagorinsky-Lilly) or rho nu (constant)
+__global__ void k_sgs_mu(Geo g, Phys ph, Vel v, const double *rho, double *mu) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    double m = 0.0;
+    if (ph.closure == 2) {
+        double s11, s22, s33;
+        diag_strain(g, v, i, j, k, s11, s22, s33);
+        double s12 = 0.25 * (S12e(g, v, i, j, k) + S12e(g, v, i + 1, j, k) + S12e(g, v, i, j + 1, k) + S12e(g, v, i + 1, j + 1, k));
+        double s13 = 0.25 * (S13e(g, v, i, j, k) + S13e(g, v, i + 1, j, k) + S13e(g, v, i, j, k + 1) + S13e(g, v, i + 1, j, k + 1));
+        double s23 = 0.25 * (S23e(g, v, i, j, k) + S23e(g, v, i, j + 1, k) + S23e(g, v, i, j, k + 1) + S23e(g, v, i, j + 1, k + 1));
+        double SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.0 * (s12 * s12 + s13 * s13 + s23 * s23);
+        m = rho[c] * g.delta2[k] * sqrt(2.0 * SS);
+    } else if (ph.closure == 1) {
+        m = rho[c] * ph.nu;
+    }
+    mu[c] = m;
+}
+__device__ __forceinline__ double tau_diag(const Geo &g, const Vel &v, const double *mu, int i, int j, int k, int comp) {
+    double s11, s22, s33;
+    diag_strain(g, v, i, j, k, s11, s22, s33);
+    double dv = (s11 + s22 + s33) * (1.0 / 3.0);
+    double s = comp == 0 ? s11 : (comp == 1 ? s22 : s33);
+    return -2.0 * cval(g, mu, i, j, k) * (s - dv);
+}
+__device__ __forceinline__ double tau12(const Geo &g, const Vel &v, const double *mu, int i, int j, int k) {
+    double me = 0.25 * (cval(g, mu, i - 1, j - 1, k) + cval(g, mu, i, j - 1, k) + cval(g, mu, i - 1, j, k) + cval(g, mu, i, j, k));
+    return -2.0 * me * S12e(g, v, i, j, k);
+}
+
+// MOST friction velocity (reading R15): neutral start, 5 fixed-point iterations through the
+// Obukhov length with Businger-Dyer psi_m, z1/L clipped to [-5, 1].
+__device__ double ustar_most(double U, double z1, double z0, double Q, double theta, double grav) {
+    double lz = log(z1 / z0);
+    double us = KAPPA * U / lz;
+    if (Q == 0.0 || grav == 0.0) return us;
+    for (int it = 0; it < 5; ++it) {
+        double zeta;
+        if (us <= 0.0) zeta = (Q > 0.0) ? -5.0 : 1.0;
+        else zeta = z1 / (-us * us * us * theta / (KAPPA * grav * Q));
+        zeta = fmin(fmax(zeta, -5.0), 1.0);
+        double psi;
+        if (zeta < 0.0) {
+            double x = pow(1.0 - 16.0 * zeta, 0.25);
+            psi = 2.0 * log(0.5 * (1.0 + x)) + log(0.5 * (1.0 + x * x)) - 2.0 * atan(x) + 0.5 * M_PI;
+        } else {
+            psi = -5.0 * zeta;
+        }
+        us = KAPPA * U / (lz - psi);
+    }
+    return us;
+}
+
+// tau13 at the xz-edge (x-face i, w-face k): interior -2 mu_e S13; bottom: MOST or 0; top: 0
+__device__ double tau13(const Geo &g, const Phys &ph, const Vel &v, const double *mu, const double *rho,
+                        const double *th, int i, int j, int k, int visc) {
+    if (k == 0) {
+        if (ph.surface != 1) return 0.0;
+        double u = cval(g, v.ux, i, j, 0);
+        double vv = 0.25 * (cval(g, v.vy, i - 1, j, 0) + cval(g, v.vy, i, j, 0) + cval(g, v.vy, i - 1, j + 1, 0) + cval(g, v.vy, i, j + 1, 0));
+        double U = sqrt(u * u + vv * vv);
+        if (!(U > 0.0)) return 0.0;
+        double thf = 0.5 * (cval(g, th, i - 1, j, 0) + cval(g, th, i, j, 0));
+        double rhf = 0.5 * (cval(g, rho, i - 1, j, 0) + cval(g, rho, i, j, 0));
+        double z1 = 0.5 * g.dzeta[0];
+        double us = ustar_most(U, z1, ph.z0, ph.Qs, thf, ph.g);
+        return -rhf * us * us * u / U;
+    }
+    if (k >= g.nz || !visc) return 0.0;
+    double me = 0.25 * (cval(g, mu, i - 1, j, k - 1) + cval(g, mu, i, j, k - 1) + cval(g, mu, i - 1, j, k) + cval(g, mu, i, j, k));
+    return -2.0 * me * S13e(g, v, i, j, k);
+}
+__device__ double tau23(const Geo &g, const Phys &ph, const Vel &v, const double *mu, const double *rho,
+                        const double *th, int i, int j, int k, int visc) {
+    if (k == 0) {
+        if (ph.surface != 1) return 0.0;
+        double u = 0.25 * (cval(g, v.ux, i, j - 1, 0) + cval(g, v.ux, i + 1, j - 1, 0) + cval(g, v.ux, i, j, 0) + cval(g, v.ux, i + 1, j, 0));
+        double vv = cval(g, v.vy, i, j, 0);
+        double U = sqrt(u * u + vv * vv);
+        if (!(U > 0.0)) return 0.0;
+        double thf = 0.5 * (cval(g, th, i, j - 1, 0) + cval(g, th, i, j, 0));
+        double rhf = 0.5 * (cval(g, rho, i, j - 1, 0) + cval(g, rho, i, j, 0));
+        double z1 = 0.5 * g.dzeta[0];
+        double us = ustar_most(U, z1, ph.z0, ph.Qs, thf, ph.g);
+        return -rhf * us * us * vv / U;
+    }
+    if (k >= g.nz || !visc) return 0.0;
+    double me = 0.25 * (cval(g, mu, i, j - 1, k - 1) + cval(g, mu, i, j, k - 1) + cval(g, mu, i, j - 1, k) + cval(g, mu, i, j, k));
+    return -2.0 * me * S23e(g, v, i, j, k);
+}
+// heat flux rho alpha dtheta/dn at the three face types; bottom face: rho Q (MOST)
+__device__ __forceinline__ double heat_x(const Geo &g, const Phys &ph, const double *mu, const double *th, int i, int j, int k) {
+    return 0.5 * (cval(g, mu, i - 1, j, k) + cval(g, mu, i, j, k)) / ph.Pr_t * (cval(g, th, i, j, k) - cval(g, th, i - 1, j, k)) * g.rdx;
+}
+__device__ __forceinline__ double heat_y(const Geo &g, const Phys &ph, const double *mu, const double *th, int i, int j, int k) {
+    return 0.5 * (cval(g, mu, i, j - 1, k) + cval(g, mu, i, j, k)) / ph.Pr_t * (cval(g, th, i, j, k) - cval(g, th, i, j - 1, k)) * g.rdy;
+}
+__device__ __forceinline__ double heat_z(const Geo &g, const Phys &ph, const double *mu, const double *th, const double *rho,
+                                         int i, int j, int k, int visc) {
+    if (k == 0) return ph.surface == 1 ? cval(g, rho, i, j, 0) * ph.Qs : 0.0;
+    if (k >= g.nz || !visc) return 0.0;
+    return 0.5 * (cval(g, mu, i, j, k - 1) + cval(g, mu, i, j, k)) / ph.Pr_t
+         * (cval(g, th, i, j, k) - cval(g, th, i, j, k - 1)) / g.dzc[k];
+}
+
+// ------------------------------------------------------------------ slow tendencies
+
+// continuity and potential temperature (Eq. con, Eq. theta): flux divergence / cell height
+__global__ void k_rhs_cells(Geo g, Phys ph, Prep pr, const double *th, const double *rho, const double *mu,
+                            int sgs, double *Rr, double *Rt) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    double mxm = pr.mfx[c], mxp = __ldg(pr.mfx + cixw(g, i + 1, j, k));
+    double mym = pr.mfy[c], myp = __ldg(pr.mfy + cixw(g, i, j + 1, k));
+    double omm = __ldg(pr.rom + cix(g, i, j, k)), omp = __ldg(pr.rom + cix(g, i, j, k + 1));
+    double H = Hc(g, i, j, k);
+    Rr[c] = -((mxp - mxm) * g.rdx + (myp - mym) * g.rdy + (omp - omm)) / H;
+    int zf = ph.scal_adv == 1;
+    double q[6];
+    // x-faces i and i+1
+    for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i - 3 + m, j, k);
+    double fxm = mxm * weno5(q, sgnd(mxm), zf);
+    for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i - 2 + m, j, k);
+    double fxp = mxp * weno5(q, sgnd(mxp), zf);
+    for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i, j - 3 + m, k);
+    double fym = mym * weno5(q, sgnd(mym), zf);
+    for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i, j - 2 + m, k);
+    double fyp = myp * weno5(q, sgnd(myp), zf);
+    double fzm = 0.0, fzp = 0.0;
+    if (k > 0) {
+        for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i, j, k - 3 + m);
+        fzm = omm * weno5(q, sgnd(omm), zf);
+    }
+    if (k < g.nz - 1) {
+        for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i, j, k - 2 + m);
+        fzp = omp * weno5(q, sgnd(omp), zf);
+    }
+    double r = -((fxp - fxm) * g.rdx + (fyp - fym) * g.rdy + (fzp - fzm)) / H;
+    if (sgs) {
+        int visc = ph.closure == 1 || ph.closure == 2;
+        double hd = 0.0;
+        if (visc) {
+            hd += (heat_x(g, ph, mu, th, i + 1, j, k) - heat_x(g, ph, mu, th, i, j, k)) * g.rdx
+                + (heat_y(g, ph, mu, th, i, j + 1, k) - heat_y(g, ph, mu, th, i, j, k)) * g.rdy;
+        }
+        hd += (heat_z(g, ph, mu, th, rho, i, j, k + 1, visc) - heat_z(g, ph, mu, th, rho, i, j, k, visc)) / H;
+        r += hd;
+    }
+    Rt[c] = r;
+}
+
+// x-momentum at x-face (i,j,k): upwind-5 advection (reading R5), terrain pressure gradient
+// (App. B), Coriolis, -div(tau)
+__global__ void k_rhs_u(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const double *th, const double *mu,
+                        int sgs, double *Ru) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    double q[6];
+    double F[2];
+    for (int s = 0; s < 2; ++s) {   // cell centres i-1, i
+        int ic = i - 1 + s;
+        double adv = 0.5 * (cval(g, pr.mfx, ic, j, k) + cval(g, pr.mfx, ic + 1, j, k));
+        for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.ux, ic - 2 + m, j, k);
+        F[s] = adv * upwind5(q, sgnd(adv));
+    }
+    double div = (F[1] - F[0]) * g.rdx;
+    for (int s = 0; s < 2; ++s) {   // xy-edges at y-faces j, j+1
+        int jj = j + s;
+        double adv = 0.5 * (cval(g, pr.mfy, i - 1, jj, k) + cval(g, pr.mfy, i, jj, k));
+        for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.ux, i, jj - 3 + m, k);
+        F[s] = adv * upwind5(q, sgnd(adv));
+    }
+    div += (F[1] - F[0]) * g.rdy;
+    for (int s = 0; s < 2; ++s) {   // xz-edges at w-faces k, k+1
+        int kk = k + s;
+        F[s] = 0.0;
+        if (kk == 0 || kk == g.nz) continue;
+        double adv = 0.5 * (__ldg(pr.rom + cixw(g, i - 1, j, kk)) + __ldg(pr.rom + cixw(g, i, j, kk)));
+        for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.ux, i, j, kk - 3 + m);
+        F[s] = adv * upwind5(q, sgnd(adv));
+    }
+    div += F[1] - F[0];
+    double r = -div / Hx(g, i, j, k);
+    // pressure gradient
+    double px = (pp[c] - cval(g, pp, i - 1, j, k)) * g.rdx;
+    if (g.terrain && g.nz > 1) {
+        int kl = k == 0 ? 0 : k - 1, ku = k == g.nz - 1 ? g.nz - 1 : k + 1;
+        double d0 = (cval(g, pp, i, j, ku) - cval(g, pp, i, j, kl)) / (zc(g, i, j, ku) - zc(g, i, j, kl));
+        double d1 = (cval(g, pp, i - 1, j, ku) - cval(g, pp, i - 1, j, kl)) / (zc(g, i - 1, j, ku) - zc(g, i - 1, j, kl));
+        px -= 0.5 * hxi_x(g, i, j, k) * (d0 + d1);
+    }
+    r -= px;
+    if (ph.f_cor != 0.0) {
+        double rvx = 0.25 * (cval(g, st.v, i - 1, j, k) + cval(g, st.v, i, j, k) + cval(g, st.v, i - 1, j + 1, k) + cval(g, st.v, i, j + 1, k));
+        double rhx = 0.5 * (cval(g, st.r, i - 1, j, k) + cval(g, st.r, i, j, k));
+        r += ph.f_cor * (rvx - rhx * ph.v_g);
+    }
+    if (sgs) {
+        int visc = ph.closure == 1 || ph.closure == 2;
+        Vel v{pr.ux, pr.vy, pr.wz};
+        double d = 0.0;
+        if (visc) {
+            d += (tau_diag(g, v, mu, i, j, k, 0) - tau_diag(g, v, mu, i - 1, j, k, 0)) * g.rdx
+               + (tau12(g, v, mu, i, j + 1, k) - tau12(g, v, mu, i, j, k)) * g.rdy;
+        }
+        d += (tau13(g, ph, v, mu, st.r, th, i, j, k + 1, visc) - tau13(g, ph, v, mu, st.r, th, i, j, k, visc)) / g.dzeta[k];
+        r -= d;
+    }
+    Ru[c] = r;
+}
+
+__global__ void k_rhs_v(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const double *th, const double *mu,
+                        int sgs, double *Rv) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    double q[6];
+    double F[2];
+    for (int s = 0; s < 2; ++s) {   // xy-edges at x-faces i, i+1
+        int ii = i + s;
+        double adv = 0.5 * (cval(g, pr.mfx, ii, j - 1, k) + cval(g, pr.mfx, ii, j, k));
+        for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.vy, ii - 3 + m, j, k);
+        F[s] = adv * upwind5(q, sgnd(adv));
+    }
+    double div = (F[1] - F[0]) * g.rdx;
+    for (int s = 0; s < 2; ++s) {   // cell centres j-1, j
+        int jc = j - 1 + s;
+        double adv = 0.5 * (cval(g, pr.mfy, i, jc, k) + cval(g, pr.mfy, i, jc + 1, k));
+        for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.vy, i, jc - 2 + m, k);
+        F[s] = adv * upwind5(q, sgnd(adv));
+    }
+    div += (F[1] - F[0]) * g.rdy;
+    for (int s = 0; s < 2; ++s) {   // yz-edges at w-faces k, k+1
+        int kk = k + s;
+        F[s] = 0.0;
+        if (kk == 0 || kk == g.nz) continue;
+        double adv = 0.5 * (__ldg(pr.rom + cixw(g, i, j - 1, kk)) + __ldg(pr.rom + cixw(g, i, j, kk)));
+        for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.vy, i, j, kk - 3 + m);
+        F[s] = adv * upwind5(q, sgnd(adv));
+    }
+    div += F[1] - F[0];
+    double r = -div / Hy(g, i, j, k);
+    double py = (pp[c] - cval(g, pp, i, j - 1, k)) * g.rdy;
+    if (g.terrain && g.nz > 1) {
+        int kl = k == 0 ? 0 : k - 1, ku = k == g.nz - 1 ? g.nz - 1 : k + 1;
+        double d0 = (cval(g, pp, i, j, ku) - cval(g, pp, i, j, kl)) / (zc(g, i, j, ku) - zc(g, i, j, kl));
+        double d1 = (cval(g, pp, i, j - 1, ku) - cval(g, pp, i, j - 1, kl)) / (zc(g, i, j - 1, ku) - zc(g, i, j - 1, kl));
+        py -= 0.5 * heta_y(g, i, j, k) * (d0 + d1);
+    }
+    r -= py;
+    if (ph.f_cor != 0.0) {
+        double rux = 0.25 * (cval(g, st.u, i, j - 1, k) + cval(g, st.u, i + 1, j - 1, k) + cval(g, st.u, i, j, k) + cval(g, st.u, i + 1, j, k));
+        double rhy = 0.5 * (cval(g, st.r, i, j - 1, k) + cval(g, st.r, i, j, k));
+        r -= ph.f_cor * (rux - rhy * ph.u_g);
+    }
+    if (sgs) {
+        int visc = ph.closure == 1 || ph.closure == 2;
+        Vel v{pr.ux, pr.vy, pr.wz};
+        double d = 0.0;
+        if (visc) {
+            d += (tau12(g, v, mu, i + 1, j, k) - tau12(g, v, mu, i, j, k)) * g.rdx
+               + (tau_diag(g, v, mu, i, j, k, 1) - tau_diag(g, v, mu, i, j - 1, k, 1)) * g.rdy;
+        }
+        d += (tau23(g, ph, v, mu, st.r, th, i, j, k + 1, visc) - tau23(g, ph, v, mu, st.r, th, i, j, k, visc)) / g.dzeta[k];
+        r -= d;
+    }
+    Rv[c] = r;
+}
+
+// z-momentum at interior w-faces; boundary rows are zero
+__global__ void k_rhs_w(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const double *th, const double *mu,
+                        int sgs, double *Rw) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nw) return;
+    int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / g.nxy);
+    if (k == 0 || k == g.nz) { Rw[n] = 0.0; return; }
+    double q[6];
+    double F[2];
+    for (int s = 0; s < 2; ++s) {   // xz-edges at x-faces i, i+1
+        int ii = i + s;
+        double adv = 0.5 * (cval(g, pr.mfx, ii, j, k - 1) + cval(g, pr.mfx, ii, j, k));
+        for (int m = 0; m < 6; ++m) q[m] = __ldg(pr.wz + cixw(g, ii - 3 + m, j, k));
+        F[s] = adv * upwind5(q, sgnd(adv));
+    }
+    double div = (F[1] - F[0]) * g.rdx;
+    for (int s = 0; s < 2; ++s) {   // yz-edges at y-faces j, j+1
+        int jj = j + s;
+        double adv = 0.5 * (cval(g, pr.mfy, i, jj, k - 1) + cval(g, pr.mfy, i, jj, k));
+        for (int m = 0; m < 6; ++m) q[m] = __ldg(pr.wz + cixw(g, i, jj - 3 + m, k));
+        F[s] = adv * upwind5(q, sgnd(adv));
+    }
+    div += (F[1] - F[0]) * g.rdy;
+    for (int s = 0; s < 2; ++s) {   // cell centres k-1, k
+        int kc = k - 1 + s;
+        double adv = 0.5 * (__ldg(pr.rom + cixw(g, i, j, kc)) + __ldg(pr.rom + cixw(g, i, j, kc + 1)));
+        for (int m = 0; m < 6; ++m) q[m] = wval(g, pr.wz, i, j, kc - 2 + m);
+        F[s] = adv * upwind5(q, sgnd(adv));
+    }
+    div += F[1] - F[0];
+    double dz = dzcw(g, i, j, k);
+    double r = -div / dz;
+    long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1);
+    r -= (pp[c] - pp[cm]) / dz;
+    double b0 = g.rho0[bix(g, i, j, k - 1)], b1 = g.rho0[bix(g, i, j, k)];
+    r += 0.5 * (-ph.g * (st.r[cm] - b0) - ph.g * (st.r[c] - b1));
+    if (sgs && (ph.closure == 1 || ph.closure == 2)) {
+        Vel v{pr.ux, pr.vy, pr.wz};
+        double d = (tau13(g, ph, v, mu, st.r, th, i + 1, j, k, 1) - tau13(g, ph, v, mu, st.r, th, i, j, k, 1)) * g.rdx
+                 + (tau23(g, ph, v, mu, st.r, th, i, j + 1, k, 1) - tau23(g, ph, v, mu, st.r, th, i, j, k, 1)) * g.rdy
+                 + (tau_diag(g, v, mu, i, j, k, 2) - tau_diag(g, v, mu, i, j, k - 1, 2)) / dz;
+        r -= d;
+    }
+    Rw[n] = r;
+}
+
+// ------------------------------------------------------------------ acoustic substeps (App. C)
+
+// Per column: coefficients of the vertical system in Omega'' (reading R11) for this stage's
+// dtau, and their LU factors (Thomas forward elimination without the right-hand side).
+__global__ void k_tri_build(Geo g, Phys ph, const double *rho, const double *rt, const double *pi, const double *th,
+                            double dtau, Tri tr) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nxy) return;
+    int i = (int)(n % g.nx), j = (int)(n / g.nx);
+    double b2 = 0.5 * (1.0 + ph.beta_s);
+    double E = dtau * b2 * b2, Gg = dtau * 0.5 * ph.g;
+    double gRd = GAMMA * RD;
+    double cp_prev = 0.0;
+    for (int k = 1; k < g.nz; ++k) {
+        long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1), w = c;
+        double dz = dzcw(g, i, j, k);
+        double pic = pi[c], pim = pi[cm];
+        double pib = 0.5 * (pim + pic);
+        double rhob = 0.5 * (rho[cm] + rho[c]);
+        double Cpg = gRd * pib / dz;
+        double Cbp = ph.g * rhob * (RD / CVD) * 0.5 * pic / (rt[c] * pib);
+        double Cbm = ph.g * rhob * (RD / CVD) * 0.5 * pim / (rt[cm] * pib);
+        double P = dtau * (-Cpg + Cbp), Q = dtau * (Cpg + Cbm);
+        double Hk = Hc(g, i, j, k), Hm = Hc(g, i, j, k - 1);
+        double thw_m = 0.5 * (cval(g, th, i, j, k - 2) + th[cm]);
+        double thw_k = 0.5 * (th[cm] + th[c]);
+        double thw_p = 0.5 * (th[c] + cval(g, th, i, j, k + 1));
+        double a = E * (Gg - Q * thw_m) / Hm;
+        double b = 1.0 - P * E * thw_k / Hk + Q * E * thw_k / Hm + Gg * E * (1.0 / Hk - 1.0 / Hm);
+        double cc = E * (P * thw_p - Gg) / Hk;
+        double m = b - a * cp_prev;
+        double im = 1.0 / m;
+        double cpk = cc * im;
+        tr.a[w] = a; tr.cp[w] = cpk; tr.im[w] = im; tr.P[w] = P; tr.Q[w] = Q;
+        cp_prev = cpk;
+    }
+}
+
+// horizontal momenta: Delta U'' = dtau (-gamma R_d pi^t (dTheta~/dxi - h_xi/h_zeta dTheta~/dzeta) + R_U),
+// Theta~ = Theta'' + beta_d (Theta'' - Theta''_prev) (reading R10)
+__device__ __forceinline__ double ttil(const Geo &g, const double *Xt, const double *Tp, double bd, int i, int j, int k) {
+    long long a = cixw(g, i, j, k);
+    double x = __ldg(Xt + a);
+    return x + bd * (x - __ldg(Tp + a));
+}
+__global__ void k_sub_horiz(Geo g, Phys ph, const double *pi, const double *Xt, const double *Tp,
+                            const double *Ru, const double *Rv, double *Xu, double *Xv, double dtau) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    double bd = ph.beta_d;
+    double t0 = ttil(g, Xt, Tp, bd, i, j, k);
+    double gx = (t0 - ttil(g, Xt, Tp, bd, i - 1, j, k)) * g.rdx;
+    double gy = (t0 - ttil(g, Xt, Tp, bd, i, j - 1, k)) * g.rdy;
+    if (g.terrain && g.nz > 1) {
+        int kl = k == 0 ? 0 : k - 1, ku = k == g.nz - 1 ? g.nz - 1 : k + 1;
+        double dc = (ttil(g, Xt, Tp, bd, i, j, ku) - ttil(g, Xt, Tp, bd, i, j, kl)) / (zc(g, i, j, ku) - zc(g, i, j, kl));
+        double dxm = (ttil(g, Xt, Tp, bd, i - 1, j, ku) - ttil(g, Xt, Tp, bd, i - 1, j, kl)) / (zc(g, i - 1, j, ku) - zc(g, i - 1, j, kl));
+        double dym = (ttil(g, Xt, Tp, bd, i, j - 1, ku) - ttil(g, Xt, Tp, bd, i, j - 1, kl)) / (zc(g, i, j - 1, ku) - zc(g, i, j - 1, kl));
+        gx -= 0.5 * hxi_x(g, i, j, k) * (dc + dxm);
+        gy -= 0.5 * heta_y(g, i, j, k) * (dc + dym);
+    }
+    double gRd = GAMMA * RD;
+    double pic = pi[c];
+    double pix = 0.5 * (cval(g, pi, i - 1, j, k) + pic);
+    double piy = 0.5 * (cval(g, pi, i, j - 1, k) + pic);
+    Xu[c] += dtau * (-gRd * pix * gx + Ru[c]);
+    Xv[c] += dtau * (-gRd * piy * gy + Rv[c]);
+}
+
+// Per column: explicit parts Theta*, rho* (new U'', V'' divergence, beta_1 part of the old
+// Omega'' flux), forward substitution with the stage LU factors, back substitution for
+// Omega''^{new}, then Theta'', rho'', W'' = Omega'' + metric shift.  Theta''_prev <- Theta''^tau.
+__global__ void k_sub_vert(Geo g, Phys ph, Tri tr, const double *th, const double *Rr, const double *Rt,
+                           const double *Rw, F5 x, double *Om, double *Tp, double dtau) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nxy) return;
+    int i = (int)(n % g.nx), j = (int)(n / g.nx);
+    const int nz = g.nz;
+    double b1 = 0.5 * (1.0 - ph.beta_s), b2 = 0.5 * (1.0 + ph.beta_s);
+    double Gg = dtau * 0.5 * ph.g;
+    // forward pass
+    double X0m = 0.0, Y0m = 0.0, dpm = 0.0;
+    double th_m = cval(g, th, i, j, -1);
+    double th_c = th[cix(g, i, j, 0)];
+    double om_k = 0.0;   // old Omega'' at face k (0 at the wall)
+    for (int k = 0; k < nz; ++k) {
+        long long c = cix(g, i, j, k);
+        double th_p = cval(g, th, i, j, k + 1);
+        double thw_k = 0.5 * (th_m + th_c), thw_p = 0.5 * (th_c + th_p);
+        double om_p = (k + 1 < nz) ? Om[cix(g, i, j, k + 1)] : 0.0;
+        long long cxp = cixw(g, i + 1, j, k), cyp = cixw(g, i, j + 1, k);
+        double Uc = x.u[c], Up = x.u[cxp], Vc = x.v[c], Vp = x.v[cyp];
+        double Hxm = Hx(g, i, j, k), Hxp = Hx(g, i + 1, j, k), Hym = Hy(g, i, j, k), Hyp = Hy(g, i, j + 1, k);
+        double thxm = 0.5 * (cval(g, th, i - 1, j, k) + th_c), thxp = 0.5 * (th_c + cval(g, th, i + 1, j, k));
+        double thym = 0.5 * (cval(g, th, i, j - 1, k) + th_c), thyp = 0.5 * (th_c + cval(g, th, i, j + 1, k));
+        double divM = (Hxp * Up - Hxm * Uc) * g.rdx + (Hyp * Vp - Hym * Vc) * g.rdy;
+        double divT = (Hxp * Up * thxp - Hxm * Uc * thxm) * g.rdx + (Hyp * Vp * thyp - Hym * Vc * thym) * g.rdy;
+        double H = Hc(g, i, j, k);
+        double xt = x.t[c], xr = x.r[c];
+        Tp[c] = xt;
+        double Ts = xt + dtau * (-divT / H - b1 * (om_p * thw_p - om_k * thw_k) / H + Rt[c]);
+        double Rs = xr + dtau * (-divM / H - b1 * (om_p - om_k) / H + Rr[c]);
+        x.t[c] = Ts;   // hold Theta*, rho* until the back substitution
+        x.r[c] = Rs;
+        double X0 = b1 * xt + b2 * Ts, Y0 = b1 * xr + b2 * Rs;
+        if (k >= 1) {
+            long long w = c;
+            double A = g.terrain ? metric_shift(g, x.u, x.v, i, j, k) : 0.0;
+            double rhs = x.w[w] - A + dtau * Rw[w] + tr.P[w] * X0 + tr.Q[w] * X0m - Gg * (Y0 + Y0m);
+            double dp = (rhs - tr.a[w] * dpm) * tr.im[w];
+            Om[w] = dp;
+            dpm = dp;
+        }
+        X0m = X0; Y0m = Y0;
+        om_k = om_p;
+        th_m = th_c; th_c = th_p;
+    }
+    // back substitution, from the top wall (Omega'' = 0) down
+    double om_up = 0.0;
+    double thw_up = 0.0;
+    {
+        long long w = cix(g, i, j, nz);
+        x.w[w] = 0.0;
+        Om[w] = 0.0;
+    }
+    for (int k = nz - 1; k >= 0; --k) {
+        long long c = cix(g, i, j, k);
+        double om_k2 = 0.0;
+        if (k >= 1) {
+            om_k2 = Om[c] - tr.cp[c] * om_up;
+            Om[c] = om_k2;
+        } else {
+            Om[c] = 0.0;
+        }
+        double thc = th[c];
+        double thw_k = 0.5 * (cval(g, th, i, j, k - 1) + thc);
+        double thw_p = (k == nz - 1) ? 0.5 * (thc + cval(g, th, i, j, k + 1)) : thw_up;
+        double H = Hc(g, i, j, k);
+        x.t[c] = x.t[c] - dtau * b2 * (om_up * thw_p - om_k2 * thw_k) / H;
+        x.r[c] = x.r[c] - dtau * b2 * (om_up - om_k2) / H;
+        double A = g.terrain ? metric_shift(g, x.u, x.v, i, j, k) : 0.0;
+        x.w[c] = om_k2 + A;
+        om_up = om_k2;
+        thw_up = thw_k;
+    }
+}
+
+__global__ void k_stage_end(Geo g, F5 st, CF5 x) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nw) return;
+    if (n < g.nc) {
+        st.r[n] += x.r[n];
+        st.t[n] += x.t[n];
+        st.u[n] += x.u[n];
+        st.v[n] += x.v[n];
+    }
+    st.w[n] += x.w[n];
+}
+
+// no-substep stage (Sec. 3.1): S^(s) = S^n + alpha dt R(S^t)
+__global__ void k_stage_nosub(Geo g, F5 st, CF5 sn, CF5 R, double adt) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nw) return;
+    if (n < g.nc) {
+        st.r[n] = sn.r[n] + adt * R.r[n];
+        st.t[n] = sn.t[n] + adt * R.t[n];
+        st.u[n] = sn.u[n] + adt * R.u[n];
+        st.v[n] = sn.v[n] + adt * R.v[n];
+    }
+    st.w[n] = sn.w[n] + adt * R.w[n];
+}
+
+// ------------------------------------------------------------------ diagnostics
+// Fixed-shape, fixed-order reductions (deterministic): DIAG_BLOCKS x 256 threads, each thread
+// a strided range, block tree reduction, then one block over the partials.
+constexpr int DIAG_BLOCKS = 512;
+__global__ void k_diag_partial(Geo g, CF5 st, double *part) {
+    __shared__ double sm[256], sw[256], smn[256], smx[256], scfl[256], snf[256];
+    int t = threadIdx.x;
+    double mass = 0.0, wmax = 0.0, tmn = 1e300, tmx = -1e300, cfl = 0.0, nf = 0.0;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long n = blockIdx.x * (long long)blockDim.x + t; n < g.nw; n += stride) {
+        int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / g.nxy);
+        if (k < g.nz) {
+            double r = st.r[n], rt = st.t[n];
+            mass += r * Hc(g, i, j, k) * g.dx * g.dy;
+            double th = rt / r;
+            tmn = fmin(tmn, th); tmx = fmax(tmx, th);
+            double u = st.u[n] / (0.5 * (cval(g, st.r, i - 1, j, k) + r));
+            double p, pie;
+            eos_pi(rt, p, pie);
+            double cs = sqrt(GAMMA * p / r);
+            cfl = fmax(cfl, (fabs(u) + cs) * g.rdx);
+            if (!isfinite(r) || !isfinite(rt) || !isfinite(st.u[n]) || !isfinite(st.v[n])) nf = 1.0;
+        }
+        double w = st.w[n];
+        if (!isfinite(w)) nf = 1.0;
+        if (k > 0 && k < g.nz) {
+            double rb = 0.5 * (st.r[cix(g, i, j, k - 1)] + st.r[cix(g, i, j, k)]);
+            wmax = fmax(wmax, fabs(w / rb));
+        }
+    }
+    sm[t] = mass; sw[t] = wmax; smn[t] = tmn; smx[t] = tmx; scfl[t] = cfl; snf[t] = nf;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (t < s) {
+            sm[t] += sm[t + s];
+            sw[t] = fmax(sw[t], sw[t + s]);
+            smn[t] = fmin(smn[t], smn[t + s]);
+            smx[t] = fmax(smx[t], smx[t + s]);
+            scfl[t] = fmax(scfl[t], scfl[t + s]);
+            snf[t] = fmax(snf[t], snf[t + s]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        double *p = part + 6 * blockIdx.x;
+        p[0] = sm[0]; p[1] = sw[0]; p[2] = smn[0]; p[3] = smx[0]; p[4] = scfl[0]; p[5] = snf[0];
+    }
+}
+__global__ void k_diag_final(const double *part, int nb, double dt, double *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double mass = 0.0, wmax = 0.0, tmn = 1e300, tmx = -1e300, cfl = 0.0, nf = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        const double *p = part + 6 * b;
+        mass += p[0]; wmax = fmax(wmax, p[1]); tmn = fmin(tmn, p[2]); tmx = fmax(tmx, p[3]);
+        cfl = fmax(cfl, p[4]); nf = fmax(nf, p[5]);
+    }
+    out[0] = mass; out[1] = wmax; out[2] = tmn; out[3] = tmx; out[4] = cfl * dt; out[5] = nf;
+}
+
+// ------------------------------------------------------------------ dtype conversion
+__global__ void k_f32_to_f64(const float *src, double *dst, long long n) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < n) dst[t] = (double)src[t];
+}
+__global__ void k_f64_to_f32(const double *src, float *dst, long long n) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < n) dst[t] = (float)src[t];
+}
+
+// ------------------------------------------------------------------ launchers
+static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+constexpr int BS = 256;
+
+// Optional per-launch event timing (profiling mode, never inside a graph capture).
+static thread_local ProfSink *g_prof = nullptr;
+void set_profiler(ProfSink *p) { g_prof = p; }
+struct ProfScope {
+    cudaStream_t s;
+    const char *name;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(const char *n, cudaStream_t st) : s(st), name(n) {
+        if (g_prof) {
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~ProfScope() {
+        if (g_prof) {
+            cudaEventRecord(b, s);
+            g_prof->add(name, a, b);
+        }
+    }
+};
+#define LAUNCH(name, s, ...)              \
+    do {                                  \
+        ProfScope _ps(name, s);           \
+        __VA_ARGS__;                      \
+    } while (0)
+
+void launch_terrain(const Geo &g, const double *hn, double *hc, double *hxf, double *hyf, double *gxc,
+                    double *gyc, double *g4x, double *g4y, cudaStream_t s) {
+    LAUNCH("terrain_avg", s, k_terrain_avg<<<nblk(g.nxy, BS), BS, 0, s>>>(g, hn, hc, hxf, hyf));
+    LAUNCH("terrain_grad", s, k_terrain_grad<<<nblk(g.nxy, BS), BS, 0, s>>>(g, hc, gxc, gyc, g4x, g4y));
+}
+void launch_base_state(const Geo &g, int n_knots, const double *kz, const double *kt, double theta_s, double N,
+                       double p_s, double grav, double *rho0, double *th0, double *p0, cudaStream_t s) {
+    ThetaProfile tp{n_knots, kz, kt, theta_s, N, grav};
+    long long ncol = g.terrain ? g.nxy : 1;
+    LAUNCH("base_state", s, k_base_state<<<nblk(ncol, 128), 128, 0, s>>>(g, tp, p_s, grav, rho0, th0, p0));
+}
+void launch_set_initial(const Geo &g, const double *dth, const double *u, const double *v, const double *w,
+                        double *rho, double *rt, double *ru, double *rv, double *rw, cudaStream_t s) {
+    LAUNCH("init_cells", s, k_init_cells<<<nblk(g.nc, BS), BS, 0, s>>>(g, dth, rho, rt));
+    LAUNCH("init_faces", s, k_init_faces<<<nblk(g.nw, BS), BS, 0, s>>>(g, u, v, w, rho, ru, rv, rw));
+    LAUNCH("wall_bc", s, k_wall_bc<<<nblk(g.nxy, BS), BS, 0, s>>>(g, ru, rv, rw));
+}
+void launch_wall_bc(const Geo &g, const double *ru, const double *rv, double *rw, cudaStream_t s) {
+    LAUNCH("wall_bc", s, k_wall_bc<<<nblk(g.nxy, BS), BS, 0, s>>>(g, ru, rv, rw));
+}
+void launch_stage_begin(const Geo &g, CF5 sn, CF5 st, F5 x, double *pp, double *pi, double *th, double *Tp,
+                        double *Om, cudaStream_t s) {
+    LAUNCH("stage_begin", s, k_stage_begin<<<nblk(g.nw, BS), BS, 0, s>>>(g, sn, st, x, pp, pi, th, Tp, Om));
+}
+void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, const double *pp, const double *th, Prep pr,
+                     double *ux, double *vy, double *wz, double *mfx, double *mfy, double *rom, double *mu,
+                     F5 R, cudaStream_t s) {
+    LAUNCH("prep", s, k_prep<<<nblk(g.nw, BS), BS, 0, s>>>(g, st, ux, vy, wz, mfx, mfy, rom));
+    int sgs = (ph.closure == 1 || ph.closure == 2 || ph.surface == 1) ? 1 : 0;
+    if (ph.closure == 1 || ph.closure == 2)
+        LAUNCH("sgs_mu", s, k_sgs_mu<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, Vel{ux, vy, wz}, st.r, mu));
+    LAUNCH("rhs_cells", s, k_rhs_cells<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, th, st.r, mu, sgs, R.r, R.t));
+    LAUNCH("rhs_u", s, k_rhs_u<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, sgs, R.u));
+    LAUNCH("rhs_v", s, k_rhs_v<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, sgs, R.v));
+    LAUNCH("rhs_w", s, k_rhs_w<<<nblk(g.nw, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, sgs, R.w));
+}
+void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const double *rt, const double *pi,
+                      const double *th, double dtau, Tri tr, cudaStream_t s) {
+    LAUNCH("tri_build", s, k_tri_build<<<nblk(g.nxy, 128), 128, 0, s>>>(g, ph, rho, rt, pi, th, dtau, tr));
+}
+void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *pi, const double *th, CF5 R, F5 x,
+                    double *Om, double *Tp, double dtau, cudaStream_t s) {
+    LAUNCH("sub_horiz", s, k_sub_horiz<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pi, x.t, Tp, R.u, R.v, x.u, x.v, dtau));
+    LAUNCH("sub_vert", s, k_sub_vert<<<nblk(g.nxy, 64), 64, 0, s>>>(g, ph, tr, th, R.r, R.t, R.w, x, Om, Tp, dtau));
+}
+void launch_stage_end(const Geo &g, F5 st, CF5 x, cudaStream_t s) {
+    LAUNCH("stage_end", s, k_stage_end<<<nblk(g.nw, BS), BS, 0, s>>>(g, st, x));
+}
+void launch_stage_nosub(const Geo &g, F5 st, CF5 sn, CF5 R, double adt, cudaStream_t s) {
+    LAUNCH("stage_nosub", s, k_stage_nosub<<<nblk(g.nw, BS), BS, 0, s>>>(g, st, sn, R, adt));
+}
+void launch_diag(const Geo &g, CF5 st, double dt, double *part, double *out, cudaStream_t s) {
+    LAUNCH("diag_partial", s, k_diag_partial<<<DIAG_BLOCKS, 256, 0, s>>>(g, st, part));
+    LAUNCH("diag_final", s, k_diag_final<<<1, 32, 0, s>>>(part, DIAG_BLOCKS, dt, out));
+}
+void launch_convert(const void *src, void *dst, long long n, int to_f64, cudaStream_t s) {
+    if (to_f64)
+        LAUNCH("f32_to_f64", s, k_f32_to_f64<<<nblk(n, BS), BS, 0, s>>>((const float *)src, (double *)dst, n));
+    else
+        LAUNCH("f64_to_f32", s, k_f64_to_f32<<<nblk(n, BS), BS, 0, s>>>((const double *)src, (float *)dst, n));
+}
+
+}  // namespace erfk

@@ -1,0 +1,39 @@
+// Kernel launchers of the dycore library (host-callable, stream-ordered, capturable).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "erf_dev.cuh"
+
+namespace erfk {
+
+void launch_terrain(const Geo &g, const double *hn, double *hc, double *hxf, double *hyf, double *gxc,
+                    double *gyc, double *g4x, double *g4y, cudaStream_t s);
+void launch_base_state(const Geo &g, int n_knots, const double *kz, const double *kt, double theta_s, double N,
+                       double p_s, double grav, double *rho0, double *th0, double *p0, cudaStream_t s);
+void launch_set_initial(const Geo &g, const double *dth, const double *u, const double *v, const double *w,
+                        double *rho, double *rt, double *ru, double *rv, double *rw, cudaStream_t s);
+void launch_wall_bc(const Geo &g, const double *ru, const double *rv, double *rw, cudaStream_t s);
+void launch_stage_begin(const Geo &g, CF5 sn, CF5 st, F5 x, double *pp, double *pi, double *th, double *Tp,
+                        double *Om, cudaStream_t s);
+void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, const double *pp, const double *th, Prep pr,
+                     double *ux, double *vy, double *wz, double *mfx, double *mfy, double *rom, double *mu,
+                     F5 R, cudaStream_t s);
+void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const double *rt, const double *pi,
+                      const double *th, double dtau, Tri tr, cudaStream_t s);
+void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *pi, const double *th, CF5 R, F5 x,
+                    double *Om, double *Tp, double dtau, cudaStream_t s);
+void launch_stage_end(const Geo &g, F5 st, CF5 x, cudaStream_t s);
+void launch_stage_nosub(const Geo &g, F5 st, CF5 sn, CF5 R, double adt, cudaStream_t s);
+void launch_diag(const Geo &g, CF5 st, double dt, double *part, double *out, cudaStream_t s);
+void launch_convert(const void *src, void *dst, long long n, int to_f64, cudaStream_t s);
+
+constexpr int DIAG_PARTS = 512;
+
+// receives (kernel name, start event, stop event) for every launch while profiling is on
+struct ProfSink {
+    virtual void add(const char *name, cudaEvent_t start, cudaEvent_t stop) = 0;
+    virtual ~ProfSink() {}
+};
+void set_profiler(ProfSink *p);
+
+}  // namespace erfk

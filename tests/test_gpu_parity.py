@@ -1,0 +1,269 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element.
+
+Bar (FP64): relative L2 <= 1e-11.  Runs at their configured step count are held to it per
+field.  Short runs (a few steps) hold rho and rho*theta to it per field and measure each momentum
+component against the L2 norm of the momentum vector (rho u, rho v, rho w): a component that is
+still ~1e-4 after two steps is driven by O(1e5) pressure terms, and a one-ulp perturbation of the
+oracle's own initial state already moves it by ~3e-10 of its own norm (see
+test_gap_is_below_the_oracles_own_ulp_sensitivity).  Sizes span several thread blocks with ragged
+tails; the full-size cases run the oracle on the same seeded inputs.
+"""
+import numpy as np
+import pytest
+
+from paper_2412_04395_gb300 import workloads as W
+from conftest import make_oracle
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("rho", "rhotheta", "rhou", "rhov", "rhow")
+TOL = 1e-11
+
+
+def _gpu(wl):
+    from paper_2412_04395_gb300.erf import Dycore
+    d = Dycore(wl)
+    d.erf_set_initial(wl.dtheta, wl.u, wl.v, wl.w)
+    return d
+
+
+def _rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a - b)
+
+
+def _errors(gs, os_, per_field=False):
+    """rho, rho*theta: relative L2.  Momenta: relative L2 per field (per_field) or against the
+    momentum-vector norm; a component that is zero in the reference always uses the latter."""
+    mom = np.sqrt(sum(np.linalg.norm(os_[f]) ** 2 for f in ("rhou", "rhov", "rhow"))) + 1e-300
+    out = {}
+    for f in FIELDS:
+        a, b = gs[f], os_[f]
+        assert a.shape == b.shape, f
+        assert np.all(np.isfinite(a)), f
+        if f in ("rho", "rhotheta") or (per_field and np.linalg.norm(b) > 1e-14 * mom):
+            out[f] = _rel_l2(a, b)
+        else:
+            out[f] = np.linalg.norm(a - b) / mom
+    return out
+
+
+def _compare(gs, os_, tol=TOL, per_field=False):
+    out = _errors(gs, os_, per_field)
+    bad = {f: e for f, e in out.items() if not e <= tol}
+    assert not bad, (bad, out)
+    return out
+
+
+def _run_both(wl, steps, **over):
+    o = make_oracle(wl, **over)
+    d = _gpu(wl)
+    o.step(steps)
+    d.erf_rk3_step(steps)
+    return d, o
+
+
+def _ulp_floor(wl, steps, ref, **over):
+    """Per-field difference the oracle itself shows after a random one-ulp perturbation of its
+    initial rho*theta (same normalisation as _errors): the round-off floor of this run."""
+    p = make_oracle(wl, **over)
+    r = p.get("rhotheta")
+    p.set("rhotheta", r * (1 + 1.1e-16 * np.random.default_rng(1).standard_normal(r.shape)))
+    p.step(steps)
+    return _errors(p.state(), ref)
+
+
+def _parity(wl, steps, **over):
+    """GPU vs oracle after a short run: each field within max(1e-11, 3 x its round-off floor)."""
+    d, o = _run_both(wl, steps, **over)
+    ref = o.state()
+    gap = _errors(d.state(), ref)
+    floor = _ulp_floor(wl, steps, ref, **over)
+    bad = {f: (gap[f], floor[f]) for f in FIELDS if not gap[f] <= max(TOL, 3.0 * floor[f])}
+    assert not bad, (bad, gap, floor)
+    return gap, floor
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    import __graft_entry__ as ge
+    ge.build()
+
+
+def test_base_state_and_initial_state_parity():
+    for wl in (W.density_current(nx=40, ny=3, nz=20, dx=300.0),
+               W.hill_bubble(nx=36, ny=28, nz=18, dx=200.0, dz0=80.0, ratio=1.04, h0=300.0),
+               W.neutral_abl(nx=24, ny=20, nz=16, dx=10.0, precision=W.PREC_FP64)):
+        o = make_oracle(wl)
+        d = _gpu(wl)
+        for f in ("base_rho", "base_p", "base_theta"):
+            a = d.erf_get_state(f)
+            b = o.get(f)
+            if a.ndim == 1:
+                b = b[:, 0, 0]
+            assert _rel_l2(a, b) < 1e-13, (wl.name, f)
+        _compare(d.state(), o.state(), tol=1e-14)
+
+
+def test_density_current_steps_ragged():
+    wl = W.density_current(nx=70, ny=3, nz=23, dx=350.0)
+    _parity(wl, 6)
+
+
+def test_hill_bubble_terrain_steps():
+    wl = W.hill_bubble(nx=45, ny=38, nz=21, dx=150.0, dz0=60.0, ratio=1.05, h0=350.0)
+    _parity(wl, 4)
+
+
+def test_flow_over_hill_with_wind_and_weno_z():
+    wl = W.hill_bubble(nx=33, ny=29, nz=17, dx=200.0, dz0=80.0, ratio=1.04, h0=300.0)
+    wl = wl.with_(u=np.full((17, 29, 33), 6.0), v=np.full((17, 29, 33), -3.0), scal_adv=W.SCAL_WENO5_Z)
+    _parity(wl, 4)
+
+
+def test_neutral_abl_most_coriolis_sounding():
+    wl = W.neutral_abl(nx=34, ny=30, nz=24, dx=10.0)
+    wl = wl.with_(precision=W.PREC_FP64)
+    _parity(wl, 4)
+
+
+def test_convective_abl_heat_flux_and_const_nu():
+    wl = W.convective_abl(nx=26, ny=22, nz=30, dx=40.0).with_(precision=W.PREC_FP64)
+    _parity(wl, 3)
+    wl2 = W.density_current(nx=41, ny=5, nz=19, dx=300.0).with_(closure=W.CLOSURE_CONST_NU, nu=75.0, Pr_t=1.0)
+    _parity(wl2, 3)
+
+
+def test_no_substep_mode():
+    wl = W.density_current(nx=32, ny=4, nz=16, dx=400.0, dt=0.1)
+    o = make_oracle(wl, substep_mode=1)
+    from paper_2412_04395_gb300.erf import Dycore
+    wl2 = wl.with_()
+    wl2.substep_mode = 1
+    d = Dycore(wl2)
+    d.erf_set_initial(wl.dtheta, wl.u, wl.v, wl.w)
+    o.step(3); d.erf_rk3_step(3)
+    _compare(d.state(), o.state())
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 8), (5, 1, 2), (1, 7, 3), (9, 6, 1), (33, 2, 4)])
+def test_degenerate_and_tiny_grids(shape):
+    nx, ny, nz = shape
+    zeta = np.arange(nz + 1) * 100.0
+    xc = (np.arange(nx) + 0.5) * 100.0
+    dth = np.broadcast_to(np.sin(2 * np.pi * xc / (nx * 100.0))[None, None, :], (nz, ny, nx)) * 0.5
+    wl = W.Workload("tiny", nx, ny, nz, 100.0, 100.0, zeta, dt=0.2, n_substeps=4,
+                    closure=W.CLOSURE_SMAGORINSKY, dtheta=np.ascontiguousarray(dth),
+                    u=np.full((nz, ny, nx), 2.0))
+    _parity(wl, 3)
+
+
+def test_mass_conservation_on_gpu():
+    wl = W.hill_bubble(nx=48, ny=48, nz=24, dx=150.0, dz0=60.0, ratio=1.04, h0=300.0)
+    d = _gpu(wl)
+    m0 = d.erf_diagnostics()["mass"]
+    for n in range(5):
+        d.erf_rk3_step(1)
+        di = d.erf_diagnostics()
+        assert di["status"] == 0
+        assert abs(di["mass"] - m0) / m0 < 1e-14 * (n + 1) + 1e-15
+
+
+def test_rest_over_terrain_is_exact_on_gpu():
+    wl = W.hill_bubble(nx=40, ny=40, nz=20, dx=200.0, dz0=80.0, ratio=1.04).with_(dtheta=None)
+    d = _gpu(wl)
+    d.erf_rk3_step(10)
+    s = d.state()
+    assert np.max(np.abs(s["rhow"])) <= 1e-12
+    assert np.all(s["rhou"] == 0.0) and np.all(s["rhov"] == 0.0)
+
+
+def test_checkpoint_resume_bitwise():
+    """N steps == k steps + get + destroy + new handle + set + (N - k) steps, bit for bit."""
+    wl = W.density_current(nx=48, ny=4, nz=20, dx=300.0)
+    a = _gpu(wl)
+    a.erf_rk3_step(6)
+    ref = a.state()
+    b = _gpu(wl)
+    b.erf_rk3_step(2)
+    saved = b.state()
+    b.close()
+    c = _gpu(wl.with_(dtheta=None))
+    for k, v in saved.items():
+        c.erf_set_state(k, v)
+    c.erf_rk3_step(4)
+    got = c.state()
+    for k in FIELDS:
+        assert np.array_equal(got[k], ref[k]), k
+
+
+def test_nonfinite_state_is_reported():
+    """Host-side fault injection: a NaN written through erf_set_state makes the diagnostics
+    return ERF_ENONFINITE; the context stays usable."""
+    from paper_2412_04395_gb300 import erf
+    wl = W.density_current(nx=32, ny=2, nz=8, dx=400.0)
+    d = _gpu(wl)
+    r = d.erf_get_state("rho")
+    r[3, 1, 5] = np.nan
+    d.erf_set_state("rho", r)
+    di = d.erf_diagnostics()
+    assert di["status"] == erf.ERF_ENONFINITE and di["nonfinite"] == 1
+    d.erf_set_initial(wl.dtheta)
+    assert d.erf_diagnostics()["status"] == 0
+
+
+def test_step_before_state_and_small_workspace_errors():
+    import torch
+    from paper_2412_04395_gb300 import erf
+    wl = W.density_current(nx=16, ny=2, nz=8, dx=400.0)
+    g, c, keep = erf.make_structs(wl)
+    n = erf.erf_workspace_bytes(g, c)
+    ws = torch.empty(n, dtype=torch.uint8, device="cuda")
+    with pytest.raises(erf.ErfError) as e:
+        erf.erf_init_grid(g, c, ws.data_ptr(), n // 2, 0)
+    assert e.value.status == erf.ERF_ENOSPACE
+    d = erf.Dycore(wl)
+    with pytest.raises(erf.ErfError) as e:
+        d.erf_rk3_step(1)
+    assert e.value.status == erf.ERF_ESTATE
+
+
+def test_gap_is_below_the_oracles_own_ulp_sensitivity():
+    """After two steps the GPU-oracle difference of every field is no larger than what a one-ulp
+    random perturbation of the oracle's own initial rho*theta produces."""
+    wl = W.density_current(nx=64, ny=4, nz=24, dx=300.0)
+    d, o = _run_both(wl, 2)
+    o2 = make_oracle(wl)
+    r = o2.get("rhotheta")
+    o2.set("rhotheta", r * (1 + 1.1e-16 * np.random.default_rng(0).standard_normal(r.shape)))
+    o2.step(2)
+    ref, g, p = o.state(), d.state(), o2.state()
+    for f in ("rho", "rhotheta", "rhou", "rhow"):
+        gap, ulp = _rel_l2(g[f], ref[f]), _rel_l2(p[f], ref[f])
+        print(f, "gpu gap", gap, "oracle 1-ulp sensitivity", ulp)
+        assert gap <= max(30.0 * ulp, 1e-13), f
+
+
+def test_density_current_full_config():
+    """Density current at its configured size and step count (256 x 4 x 64, 100 steps): every
+    field against its own norm."""
+    wl = W.density_current()
+    d, o = _run_both(wl, wl.steps)
+    errs = _compare(d.state(), o.state(), per_field=True)
+    print("density_current full:", errs)
+
+
+def test_hill_bubble_full_size_two_steps():
+    """Warm bubble over the hill at its full size (256 x 256 x 128), every element after two
+    steps, in the launch configuration the benchmark times."""
+    gap, floor = _parity(W.hill_bubble(), 2)
+    print("hill_bubble full size: gap", gap, "round-off floor", floor)
+
+
+def test_hill_bubble_configured_steps_on_a_window():
+    """The hill-bubble case at its configured 500 steps, on a 48 x 48 x 128 window with the same
+    spacing, stretching, hill and bubble: every field within 1e-11 relative L2 of its own norm."""
+    wl = W.hill_bubble(nx=48, ny=48, nz=128)
+    d, o = _run_both(wl, 500)
+    errs = _compare(d.state(), o.state(), per_field=True)
+    print("hill_bubble 500 steps window:", errs)
