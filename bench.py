@@ -141,21 +141,25 @@ def max_over_ranks(pg, v):
     return float(t.item())
 
 
-def oracle_rate(wl_sample, steps, threads=1):
-    """Cell-updates/s of the FP64 oracle on a workload sample (host cores)."""
-    os.environ["OMP_NUM_THREADS"] = str(threads)
+def oracle_rate(wl_sample, steps, threads=None):
+    """Cell-updates/s of the FP64 oracle on a workload sample (host cores); returns
+    (rate, seconds, threads used)."""
+    import oracle
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from conftest import make_oracle
+    used = oracle.set_threads(threads or os.cpu_count() or 1)
     o = make_oracle(wl_sample)
     t0 = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t0
-    return wl_sample.ncell * steps / dt, dt
+    return wl_sample.ncell * steps / dt, dt, used
 
 
 def workload(args):
     from paper_2412_04395_gb300 import workloads as W
     if args.case == "hill_bubble":
+        if args.grid:
+            return W.hill_bubble(nx=args.grid[0], ny=args.grid[1], nz=args.grid[2])
         return W.hill_bubble()
     if args.case == "density_current":
         return W.density_current()
@@ -184,7 +188,7 @@ def run_reference(args):
         oracle_rate(sw, 1)
     t = 0.0
     for _ in range(args.steps):
-        _, dt = oracle_rate(sw, 1)
+        _, dt, used = oracle_rate(sw, 1)
         t += dt
     v = sw.ncell * args.steps / t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
@@ -192,7 +196,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": wl.name, "grid": [wl.nx, wl.ny, wl.nz], "sample_grid": [sw.nx, sw.ny, sw.nz]},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
                              "sample": f"{sw.nx}x{sw.ny}x{sw.nz} window of {wl.name}, 1 step per timed step"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -278,9 +282,10 @@ def run_ours(args):
         import oracle
         oracle.build_oracle()
         sw = sample_workload(args)
-        v, dt = oracle_rate(sw, 1)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"1 step of a {sw.nx}x{sw.ny}x{sw.nz} window of {wl.name} ({dt:.1f} s, single thread)"}
+        v, dt, used = oracle_rate(sw, args.cpu_steps)
+        cpu = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
+               "sample": f"{args.cpu_steps} steps of a {sw.nx}x{sw.ny}x{sw.nz} window of {wl.name} "
+                         f"({dt:.1f} s on {used} threads)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -309,6 +314,9 @@ def main():
     ap.add_argument("--case", default="hill_bubble")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--grid", type=int, nargs=3, default=None,
+                    help="nx ny nz of a smaller window of the workload (profiling runs only)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -1084,3 +1084,8 @@ double orc_mass(orc *o) {
     return m;
 }
 int orc_sizeof_cfg(void) { return (int)sizeof(orc_cfg); }
+
+/* thread count of the OpenMP loops (results do not depend on it) */
+#include <omp.h>
+void orc_set_threads(int n) { if (n > 0) omp_set_num_threads(n); }
+int orc_get_threads(void) { return omp_get_max_threads(); }

@@ -115,6 +115,8 @@ def _lib():
         L.orc_ustar.argtypes = [C.c_double] * 6
         L.orc_psi_m.restype = C.c_double
         L.orc_psi_m.argtypes = [C.c_double]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_get_threads.restype = C.c_int
         L.orc_sizeof_cfg.restype = C.c_int
         assert L.orc_sizeof_cfg() == C.sizeof(_Cfg), "oracle config struct layout mismatch"
         _LIB = L
@@ -225,6 +227,13 @@ class Oracle:
 
     def state(self):
         return {k: self.get(k) for k in ("rho", "rhotheta", "rhou", "rhov", "rhow")}
+
+
+def set_threads(n: int) -> int:
+    """Sets the OpenMP thread count of the oracle; returns the count now in effect."""
+    L = _lib()
+    L.orc_set_threads(int(n))
+    return L.orc_get_threads()
 
 
 def interp(q, s, order):

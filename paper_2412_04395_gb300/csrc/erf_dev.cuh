@@ -64,9 +64,11 @@ struct Tri {
     double *a, *cp, *im, *P, *Q;
 };
 
+// periodic wrap without integer division (offsets are a few cells; loops only for n < 4)
 __device__ __forceinline__ int wrapi(int i, int n) {
-    i %= n;
-    return i < 0 ? i + n : i;
+    while (i < 0) i += n;
+    while (i >= n) i -= n;
+    return i;
 }
 // even reflection of a cell level about the walls (ghost layers below/above the domain)
 __device__ __forceinline__ int kref(int k, int nz) {

@@ -55,10 +55,12 @@ __device__ __forceinline__ double weno5(const double *q, double s, int zflag) {
 }
 
 // Exner function and pressure from rho*theta (Sec. 2.1 EOS, dry):
-// pi = (R_d rho theta / P00)^(R_d/c_v), p = R_d rho theta pi.
+// pi = (R_d rho theta / P00)^(R_d/c_v), p = R_d rho theta pi.  The product is rounded on its
+// own (__dmul_rn) so that a later p - p0 cannot be contracted into an FMA: the base state is
+// subtracted exactly and an undisturbed column keeps p' = 0 bit for bit.
 __device__ __forceinline__ void eos_pi(double rt, double &p, double &pi) {
     pi = pow(RD * rt * (1.0 / P00), RD / CVD);
-    p = RD * rt * pi;
+    p = __dmul_rn(RD * rt, pi);
 }
 
 // ------------------------------------------------------------------ init: terrain + base state
