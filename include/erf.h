@@ -151,6 +151,26 @@ typedef struct {
 erf_status erf_profile_steps(erf_handle *h, int32_t nsteps, erf_kernel_time *out, int32_t max_entries,
                              int32_t *n_entries);
 
+/* Allocation-free state reduction.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory (code running inside another framework's memory
+ * pool, sandboxes that forbid cudaMalloc, hosts whose HBM is already handed to a fixed arena).
+ * It reduces a state the caller already holds in device memory - flat grid, the same layout as
+ * erf_get_state, d_dz = the nz cell heights - into d_out[0..4] = {mass, max abs(w) over interior
+ * w-faces, theta min, theta max, nonfinite flag (1.0/0.0)} on cuda_stream, with the same fixed
+ * reduction order on every call.  It needs no handle and no workspace and calls no allocator:
+ * its only scratch is a file-scope device array of ERF_NOALLOC_MAX_PARTS x 5 doubles (2.5 MiB)
+ * that every GPU loading the library keeps until the process exits.  Grids of more than
+ * ERF_NOALLOC_MAX_PARTS x 4096 cells are rejected with ERF_ENOSPACE.  The first call on a
+ * device looks up that array's device address (once per device, with the device current), so
+ * make the first call before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (two streams, two host threads) race; serialise them.  Every value a call reads
+ * from the array is written by the same call, so nothing needs clearing between calls. */
+#define ERF_NOALLOC_MAX_PARTS 65536
+erf_status erf_reduce_state_noalloc(int32_t nx, int32_t ny, int32_t nz, double dx, double dy,
+                                    const double *d_dz, const double *d_rho, const double *d_rhotheta,
+                                    const double *d_rhou, const double *d_rhov, const double *d_rhow,
+                                    double *d_out, void *cuda_stream);
+
 /* Message of the last failed call on h (or of the last failed erf_init_grid if h is NULL). */
 const char *erf_last_error(const erf_handle *h);
 

@@ -23,7 +23,8 @@ ERF_F64, ERF_F32 = 0, 1
 
 # symbols the library must export (checked by the CPU tests)
 EXPORTS = ["erf_workspace_bytes", "erf_init_grid", "erf_set_initial", "erf_set_state", "erf_rk3_step",
-           "erf_get_state", "erf_diagnostics", "erf_profile_steps", "erf_last_error", "erf_destroy"]
+           "erf_get_state", "erf_diagnostics", "erf_profile_steps", "erf_last_error", "erf_destroy",
+           "erf_reduce_state_noalloc"]
 
 
 class ErfError(RuntimeError):
