@@ -746,7 +746,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
             memset(hz, 0, sizeof(double) * o->nw);
         }
         if (C->surface == 1) {
-            /* MOST surface stress tau_i3 = -rho u*^2 u_i/|U| at the bottom edges, heat flux rho Q */
+            /* MOST surface stress tau_i3 = -rho u*^2 u_i/|U| at the bottom edges; upward heat flux rho Q */
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i) {
                     size_t c = IX(o, i, j, 0);
@@ -769,7 +769,8 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                         double us = orc_ustar(U, z1, C->z0, C->sfc_theta_flux, thf, g);
                         t23[c] = -rhf * us * us * v / U;
                     }
-                    hz[c] = rho[c] * C->sfc_theta_flux;
+                    /* upward kinematic flux Q into the domain: rho alpha dtheta/dz = -rho Q at the surface */
+                    hz[c] = -rho[c] * C->sfc_theta_flux;
                 }
         }
         #pragma omp parallel for

@@ -487,3 +487,15 @@ def test_openmp_oracle_is_bitwise_serial():
         env = dict(os.environ, OMP_NUM_THREADS=str(n), PYTHONHASHSEED="0")
         outs.append(subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True).stdout.strip())
     assert outs[0] == outs[1] and outs[0] != ""
+
+
+def test_most_surface_heat_flux_warms_the_lowest_cell():
+    """Sec. 3.8: a positive (upward) kinematic surface heat flux Q heats the first level at rate
+    rho Q / dz and leaves the levels above untouched."""
+    nx = ny = 4; nz = 4; dz = 10.0; Q = 0.2
+    wl = _uniform_box(nx, ny, nz, 10.0, dz, surface=W.SURFACE_MOST, z0=0.1, sfc_theta_flux=Q)
+    o = make_oracle(wl)
+    rho = o.get("rho"); rt = o.get("rhotheta")
+    r = _rhs_with(o, rho, rt, 0 * rho, 0 * rho, np.zeros((nz + 1, ny, nx)))
+    np.testing.assert_allclose(r["R_rhotheta"][0], rho[0] * Q / dz, rtol=1e-13)
+    assert np.max(np.abs(r["R_rhotheta"][1:])) < 1e-13
