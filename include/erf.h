@@ -57,7 +57,8 @@ typedef enum {
 
 typedef enum { ERF_F64 = 0, ERF_F32 = 1 } erf_dtype;
 typedef enum { ERF_PREC_FP64 = 0, ERF_PREC_MIXED32 = 1 } erf_precision;
-typedef enum { ERF_CLOSURE_NONE = 0, ERF_CLOSURE_CONST_NU = 1, ERF_CLOSURE_SMAGORINSKY = 2 } erf_closure;
+typedef enum { ERF_CLOSURE_NONE = 0, ERF_CLOSURE_CONST_NU = 1, ERF_CLOSURE_SMAGORINSKY = 2,
+               ERF_CLOSURE_LEARNED = 3 /* mixed precision only */ } erf_closure;
 typedef enum { ERF_SCAL_WENO5_JS = 0, ERF_SCAL_WENO5_Z = 1 } erf_scalar_scheme;
 typedef enum { ERF_SURFACE_SLIP = 0, ERF_SURFACE_MOST = 1 } erf_surface;
 
@@ -137,6 +138,61 @@ erf_status erf_get_state(erf_handle *h, int32_t field, void *dst, int32_t dst_is
 
 /* Synchronises the stream and fills *out. Returns ERF_ENONFINITE if the state is not finite. */
 erf_status erf_diagnostics(erf_handle *h, erf_diag *out);
+
+/* ---- Learned subgrid closure (spec extension; the paper names surrogate models as
+ * future work, Sec. 6).  Network 12 -> 64 -> 64 -> 64 -> 9 with SiLU, inputs = resolved velocity
+ * gradients (9), dtheta/dx, dtheta/dy, N^2 at cell centres; outputs = kinematic SGS stress
+ * (t11, t22, t33, t12, t13, t23) and heat flux (h1, h2, h3), both standardised.
+ * Parameter vector (FP32, 9737 values): W1[64][12] b1[64] W2[64][64] b2 W3[64][64] b3 W4[9][64] b4[9].
+ * All pointers below are device pointers; every call is asynchronous on cuda_stream. */
+typedef struct {
+    int32_t epochs, batch;          /* passes over the samples; mini-batch size */
+    float lr, beta1, beta2, eps;    /* Adam (Kingma & Ba 2015) */
+} erf_train_cfg;
+
+/* Loads a closure blob (host): uint32 magic 0x4D465245 ("ERFM"), uint32 version, then FP32
+ * in_mean[12] in_std[12] out_mean[9] out_std[9] params[9737].  The weights are rounded to BF16 on
+ * the device for tensor-core inference.  The handle must have been created with
+ * closure = ERF_CLOSURE_LEARNED (mixed precision); steps refuse to run (ERF_ESTATE) until this
+ * call has succeeded.  Cells whose standardised inputs exceed 6 in magnitude, or whose outputs
+ * are not finite, use the Smagorinsky stresses instead. */
+erf_status erf_set_closure_weights(erf_handle *h, const void *blob, size_t bytes);
+
+/* The 12 closure inputs of every cell of the current state, d_out [nz*ny*nx][12] (mixed path). */
+erf_status erf_closure_features(erf_handle *h, float *d_out);
+
+/* The closure's density-weighted SGS stress and heat flux of the current state at cell centres,
+ * d_out9 = 9 planes of nz*ny*nx floats (rho t11, t22, t33, t12, t13, t23, rho h1, h2, h3);
+ * *n_fallback (optional, host) receives the number of cells that used Smagorinsky. Syncs. */
+erf_status erf_closure_fields(erf_handle *h, float *d_out9, uint32_t *n_fallback);
+
+/* Favre r x r x r box filter of the current (fine, flat, mixed-precision) state into a coarse
+ * C-grid state with the same layout conventions (d_rho, d_rhotheta, d_rhou, d_rhov: Nz*Ny*Nx,
+ * d_rhow: (Nz+1)*Ny*Nx, FP64, N = n/r) and the SGS targets t_ij, h_j at coarse cells,
+ * d_targets [Nz*Ny*Nx][9] (kinematic, same order as the closure outputs). */
+erf_status erf_filter_state(erf_handle *h, int32_t r, double *d_rho, double *d_rhotheta, double *d_rhou,
+                            double *d_rhov, double *d_rhow, float *d_targets);
+
+/* Bytes of device scratch erf_train_closure / erf_closure_grad need for mini-batch `batch`. */
+size_t erf_train_scratch_bytes(int32_t batch);
+
+/* Mini-batch Adam on MSE over n standardised samples (d_X [n][12], d_T [n][9]) in the given
+ * order; d_params (9737 FP32) is updated in place; d_losses (optional) receives the loss of each
+ * mini-batch.  Deterministic (fixed summation order). */
+erf_status erf_train_closure(const erf_train_cfg *cfg, const float *d_X, const float *d_T, int64_t n,
+                             float *d_params, float *d_losses, void *d_scratch, size_t scratch_bytes,
+                             void *cuda_stream);
+
+/* Loss and gradient of one batch of n samples (no update): d_grad (9737), d_loss (1). */
+erf_status erf_closure_grad(const float *d_X, const float *d_T, int32_t n, float *d_params, float *d_grad,
+                            float *d_loss, void *d_scratch, size_t scratch_bytes, void *cuda_stream);
+
+/* Per-column mean and standard deviation (0 replaced by 1) of d_A [rows][cols]; and
+ * standardisation out = (A - mean)/std. */
+erf_status erf_column_stats(const float *d_A, int64_t rows, int32_t cols, float *d_mean, float *d_std,
+                            void *cuda_stream);
+erf_status erf_standardise(const float *d_A, int64_t rows, int32_t cols, const float *d_mean,
+                           const float *d_std, float *d_out, void *cuda_stream);
 
 /* Per-kernel device time of a profiled run. */
 typedef struct {

@@ -1,0 +1,199 @@
+"""FP64 oracle of the learned subgrid closure (numpy; test infrastructure only).
+
+The paper names surrogate models as future work (Sec. 6) and fixes nothing about them; the
+closure follows the readings of the design notes:
+  * features at cell centres of a flat C-grid: the 9 resolved velocity gradients du_i/dx_j,
+    dtheta/dx, dtheta/dy and N^2 = g/theta0 dtheta/dz (12 inputs);
+  * MLP 12 -> 64 -> 64 -> 64 -> 9, SiLU hidden activations, linear output;
+  * outputs: kinematic SGS stress t_ij (11, 22, 33, 12, 13, 23) [m^2/s^2] and heat flux h_j [K m/s],
+    standardised with training-set mean/std (inputs likewise);
+  * targets from a Favre 4x4x4 box filter of a fine run:
+        rho_bar = <rho>,  u~_i = <rho u_i>/rho_bar,  t_ij = <rho u_i u_j>/rho_bar - u~_i u~_j,
+        h_j = <rho u_j theta>/rho_bar - u~_j theta~;
+  * loss: mean squared error on standardised outputs; optimiser Adam (Kingma & Ba 2015).
+Everything here is written from those definitions, in plain numpy, independent of the CUDA code.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+LAYERS = (12, 64, 64, 64, 9)
+N_IN, N_OUT = 12, 9
+
+
+def silu(x):
+    return x / (1.0 + np.exp(-x))
+
+
+def dsilu(x):
+    s = 1.0 / (1.0 + np.exp(-x))
+    return s * (1.0 + x * (1.0 - s))
+
+
+def forward(params, X):
+    """params: list of (W [out, in], b [out]); X [n, 12] standardised.  Returns (Y, cache)."""
+    a = np.asarray(X, dtype=np.float64)
+    cache = [a]
+    for l, (W, b) in enumerate(params):
+        z = a @ W.T + b
+        if l < len(params) - 1:
+            cache.append(z)
+            a = silu(z)
+            cache.append(a)
+        else:
+            a = z
+    return a, cache
+
+
+def backward(params, cache, dY):
+    """Gradients of a scalar loss with dL/dY = dY (reverse-mode chain rule through the layers)."""
+    grads = [None] * len(params)
+    g = np.asarray(dY, dtype=np.float64)
+    L = len(params)
+    for l in range(L - 1, -1, -1):
+        W, b = params[l]
+        a_in = cache[0] if l == 0 else cache[2 * l]
+        grads[l] = (g.T @ a_in, g.sum(axis=0))
+        if l > 0:
+            z_prev = cache[2 * l - 1]
+            g = (g @ W) * dsilu(z_prev)
+    return grads
+
+
+def mse(Y, T):
+    d = Y - T
+    return float(np.mean(d * d)), 2.0 * d / d.size
+
+
+def adam_init(params):
+    return [(np.zeros_like(W), np.zeros_like(b)) for W, b in params], \
+           [(np.zeros_like(W), np.zeros_like(b)) for W, b in params]
+
+
+def adam_step(params, grads, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (t >= 1): biased moments, bias correction, parameter step."""
+    out_p, out_m, out_v = [], [], []
+    for (W, b), (gW, gb), (mW, mb), (vW, vb) in zip(params, grads, m, v):
+        new = []
+        for p, gp, mp, vp in ((W, gW, mW, vW), (b, gb, mb, vb)):
+            mp = b1 * mp + (1.0 - b1) * gp
+            vp = b2 * vp + (1.0 - b2) * gp * gp
+            mh = mp / (1.0 - b1 ** t)
+            vh = vp / (1.0 - b2 ** t)
+            new.append((p - lr * mh / (np.sqrt(vh) + eps), mp, vp))
+        out_p.append((new[0][0], new[1][0]))
+        out_m.append((new[0][1], new[1][1]))
+        out_v.append((new[0][2], new[1][2]))
+    return out_p, out_m, out_v
+
+
+def train(params, X, T, epochs, batch, lr=1e-3):
+    """Mini-batch Adam over the samples in the given order (last partial batch included)."""
+    m, v = adam_init(params)
+    t = 0
+    n = len(X)
+    losses = []
+    for ep in range(epochs):
+        for s in range(0, n, batch):
+            xb, tb = X[s:s + batch], T[s:s + batch]
+            Y, cache = forward(params, xb)
+            loss, dY = mse(Y, tb)
+            grads = backward(params, cache, dY)
+            t += 1
+            params, m, v = adam_step(params, grads, m, v, t, lr)
+            losses.append(loss)
+    return params, losses
+
+
+# ------------------------------------------------------------------ features and filter
+def _centre_vel(ru, rv, rw, rho):
+    """Cell-centre velocities of a periodic flat C-grid state [k][j][i]."""
+    rx = 0.5 * (np.roll(rho, 1, axis=2) + rho)
+    ry = 0.5 * (np.roll(rho, 1, axis=1) + rho)
+    ux = ru / rx
+    vy = rv / ry
+    nz = rho.shape[0]
+    rz = np.empty_like(rw)
+    rz[1:nz] = 0.5 * (rho[:-1] + rho[1:])
+    rz[0] = rho[0]
+    rz[nz] = rho[-1]
+    wz = rw / rz
+    uc = 0.5 * (ux + np.roll(ux, -1, axis=2))
+    vc = 0.5 * (vy + np.roll(vy, -1, axis=1))
+    wc = 0.5 * (wz[:-1] + wz[1:])
+    return ux, vy, wz, uc, vc, wc
+
+
+def _ddz_c(f, zc):
+    """d/dz of a cell field: centred over cell centres, one-sided at the walls."""
+    d = np.empty_like(f)
+    nz = f.shape[0]
+    if nz == 1:
+        return np.zeros_like(f)
+    d[1:-1] = (f[2:] - f[:-2]) / (zc[2:] - zc[:-2])[:, None, None]
+    d[0] = (f[1] - f[0]) / (zc[1] - zc[0])
+    d[-1] = (f[-1] - f[-2]) / (zc[-1] - zc[-2])
+    return d
+
+
+def features(rho, rt, ru, rv, rw, zeta, dx, dy, theta0, g=9.81):
+    """The 12 closure inputs at every cell of a flat periodic C-grid state ([k][j][i] arrays;
+    theta0 = base potential temperature per level).  Diagonal gradients from face differences,
+    cross gradients from centred differences of cell-centre velocities."""
+    ux, vy, wz, uc, vc, wc = _centre_vel(ru, rv, rw, rho)
+    dz = np.diff(zeta)
+    zc = 0.5 * (zeta[:-1] + zeta[1:])
+    th = rt / rho
+    cx = lambda f: (np.roll(f, -1, axis=2) - np.roll(f, 1, axis=2)) / (2 * dx)
+    cy = lambda f: (np.roll(f, -1, axis=1) - np.roll(f, 1, axis=1)) / (2 * dy)
+    f = np.empty(rho.shape + (12,))
+    f[..., 0] = (np.roll(ux, -1, axis=2) - ux) / dx          # du/dx
+    f[..., 1] = cy(uc)                                      # du/dy
+    f[..., 2] = _ddz_c(uc, zc)                              # du/dz
+    f[..., 3] = cx(vc)                                      # dv/dx
+    f[..., 4] = (np.roll(vy, -1, axis=1) - vy) / dy          # dv/dy
+    f[..., 5] = _ddz_c(vc, zc)                              # dv/dz
+    f[..., 6] = cx(wc)                                      # dw/dx
+    f[..., 7] = cy(wc)                                      # dw/dy
+    f[..., 8] = (wz[1:] - wz[:-1]) / dz[:, None, None]      # dw/dz
+    f[..., 9] = cx(th)                                      # dtheta/dx
+    f[..., 10] = cy(th)                                     # dtheta/dy
+    f[..., 11] = g / theta0[:, None, None] * _ddz_c(th, zc)  # N^2
+    return f
+
+
+def box_filter(rho, rt, ru, rv, rw, r=4):
+    """Favre r x r x r box filter of a fine flat state: coarse C-grid state (cell means of rho,
+    rho theta; face means of the face momenta) and SGS targets t_ij, h_j at coarse cells."""
+    nz, ny, nx = rho.shape
+    Nz, Ny, Nx = nz // r, ny // r, nx // r
+    ux, vy, wz, uc, vc, wc = _centre_vel(ru, rv, rw, rho)
+    th = rt / rho
+
+    def cmean(f):
+        return f.reshape(Nz, r, Ny, r, Nx, r).mean(axis=(1, 3, 5))
+
+    rb = cmean(rho)
+    Rt = cmean(rt)
+    # coarse x-face I = fine x-face r*I; average over its r x r fine faces in (j, k)
+    Ru = ru[:, :, ::r].reshape(Nz, r, Ny, r, Nx).mean(axis=(1, 3))
+    Rv = rv[:, ::r, :].reshape(Nz, r, Ny, Nx, r).mean(axis=(1, 4))
+    Rw = rw[::r].reshape(Nz + 1, Ny, r, Nx, r).mean(axis=(2, 4))
+    vel = (uc, vc, wc)
+    ut = [cmean(rho * q) / rb for q in vel]
+    tht = Rt / rb
+    T = np.empty((Nz, Ny, Nx, 9))
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    for n, (a, b) in enumerate(pairs):
+        T[..., n] = cmean(rho * vel[a] * vel[b]) / rb - ut[a] * ut[b]
+    for j in range(3):
+        T[..., 6 + j] = cmean(rho * vel[j] * th) / rb - ut[j] * tht
+    return (rb, Rt, Ru, Rv, Rw), T
+
+
+def standardise_stats(A):
+    """Per-column mean and standard deviation (a zero deviation is replaced by 1)."""
+    mu = A.reshape(-1, A.shape[-1]).mean(axis=0)
+    sd = A.reshape(-1, A.shape[-1]).std(axis=0)
+    sd = np.where(sd > 0, sd, 1.0)
+    return mu, sd

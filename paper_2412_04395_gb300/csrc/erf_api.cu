@@ -13,6 +13,8 @@
 #include "../../include/erf.h"
 #include "erf_dev.cuh"
 #include "erf_launch.h"
+#include "erf_mixed.h"
+#include "erf_closure.h"
 
 using namespace erfk;
 
@@ -57,6 +59,17 @@ struct erf_handle {
     Tri tri;
     double *ux, *vy, *wz, *mfx, *mfy, *rom, *mu;
     double *diag_part, *diag_out;
+    // mixed-precision path (flat grids): FP32 perturbation fields + FP64 solve scratch
+    bool mixed = false;
+    F5f mst, msn, mx, mR;
+    float *mpp, *mpi, *mthp, *mTp, *mOm, *mux, *mvy, *mwz, *mmfx, *mmfy, *mmu, *mbase;
+    double *mdbuf, *mrt0;
+    MxBase mb;
+    // learned closure
+    void *cl_w = nullptr;
+    float *cl_b = nullptr, *cl_stats = nullptr, *cl_blob = nullptr, *cl_out = nullptr;
+    unsigned *cl_nfb = nullptr;
+    bool cl_ready = false;
 };
 
 static erf_status fail(erf_handle *h, erf_status st, const std::string &msg) {
@@ -80,10 +93,14 @@ static erf_status validate(const erf_grid_desc *g, const erf_config *c, std::str
     if (!(c->dt > 0.0)) { msg = "dt must be positive"; return ERF_EINVAL; }
     if (c->substep_mode != 0 && c->substep_mode != 1) { msg = "substep_mode must be 0 or 1"; return ERF_EINVAL; }
     if (c->substep_mode == 0 && (c->n_substeps < 2 || c->n_substeps % 2)) { msg = "n_substeps must be even and >= 2"; return ERF_EINVAL; }
-    if (c->closure < 0 || c->closure > 2) { msg = "closure out of range"; return ERF_EINVAL; }
+    if (c->closure < 0 || c->closure > 3) { msg = "closure out of range"; return ERF_EINVAL; }
+    if (c->closure == 3 && c->precision != ERF_PREC_MIXED32) {
+        msg = "the learned closure runs on the mixed-precision path";
+        return ERF_EUNSUPPORTED;
+    }
     if (c->scal_adv < 0 || c->scal_adv > 1) { msg = "scal_adv out of range"; return ERF_EINVAL; }
     if (c->surface < 0 || c->surface > 1) { msg = "surface out of range"; return ERF_EINVAL; }
-    if (c->precision != ERF_PREC_FP64) { msg = "only FP64 precision is built"; return ERF_EUNSUPPORTED; }
+    if (c->precision != ERF_PREC_FP64 && c->precision != ERF_PREC_MIXED32) { msg = "precision out of range"; return ERF_EINVAL; }
     if (c->n_knots < 0 || (c->n_knots > 0 && (!c->knot_z || !c->knot_theta))) { msg = "bad sounding knots"; return ERF_EINVAL; }
     if (c->closure == ERF_CLOSURE_SMAGORINSKY && !(c->Cs >= 0.0)) { msg = "Cs must be >= 0"; return ERF_EINVAL; }
     if ((c->closure != 0) && !(c->Pr_t > 0.0)) { msg = "Pr_t must be positive"; return ERF_EINVAL; }
@@ -94,6 +111,10 @@ static erf_status validate(const erf_grid_desc *g, const erf_config *c, std::str
             if (g->terrain_nodes[n] != 0.0) { terr = true; break; }
     if (terr && (c->closure != 0 || c->surface != 0)) {
         msg = "subgrid closure / MOST over terrain is not supported (flat grids only)";
+        return ERF_EUNSUPPORTED;
+    }
+    if (terr && c->precision == ERF_PREC_MIXED32) {
+        msg = "the mixed-precision path is built for flat grids only";
         return ERF_EUNSUPPORTED;
     }
     return ERF_OK;
@@ -119,6 +140,31 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
         for (long long n = 0; n < nxy; ++n) if (g->terrain_nodes[n] != 0.0) { terr = true; break; }
     long long nb = terr ? nc : nz;
     H->rho0 = cv.take<double>(nb); H->th0 = cv.take<double>(nb); H->p0 = cv.take<double>(nb);
+    if (c->precision == ERF_PREC_MIXED32) {
+        H->mixed = true;
+        F5f *sets[4] = {&H->mst, &H->msn, &H->mx, &H->mR};
+        for (F5f *f : sets) {
+            f->r = cv.take<float>(nc); f->t = cv.take<float>(nc); f->u = cv.take<float>(nc);
+            f->v = cv.take<float>(nc); f->w = cv.take<float>(nw);
+        }
+        H->mpp = cv.take<float>(nc); H->mpi = cv.take<float>(nc); H->mthp = cv.take<float>(nc);
+        H->mTp = cv.take<float>(nc); H->mOm = cv.take<float>(nw);
+        H->mux = cv.take<float>(nc); H->mvy = cv.take<float>(nc); H->mwz = cv.take<float>(nw);
+        H->mmfx = cv.take<float>(nc); H->mmfy = cv.take<float>(nc); H->mmu = cv.take<float>(nc);
+        H->mbase = cv.take<float>(mx_base_floats((int)nz));
+        H->mrt0 = cv.take<double>(nz);
+        H->mdbuf = cv.take<double>(nw);
+        H->tri.a = cv.take<double>(nw); H->tri.cp = cv.take<double>(nw); H->tri.im = cv.take<double>(nw);
+        H->tri.P = cv.take<double>(nw); H->tri.Q = cv.take<double>(nw);
+        if (c->closure == 3) {
+            H->cl_w = cv.take<unsigned short>(64 * 16 + 64 * 64 * 2 + 16 * 64);
+            H->cl_b = cv.take<float>(64 * 3 + 16);
+            H->cl_stats = cv.take<float>(2 * CL_NIN + 2 * CL_NOUT);
+            H->cl_blob = cv.take<float>(CL_BLOB_FLOATS);
+            H->cl_out = cv.take<float>(9 * nc);
+            H->cl_nfb = cv.take<unsigned>(4);
+        }
+    } else {
     F5 *sets[4] = {&H->st, &H->sn, &H->x, &H->R};
     for (F5 *f : sets) {
         f->r = cv.take<double>(nc); f->t = cv.take<double>(nc); f->u = cv.take<double>(nc);
@@ -131,6 +177,7 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
     H->ux = cv.take<double>(nc); H->vy = cv.take<double>(nc); H->mfx = cv.take<double>(nc);
     H->mfy = cv.take<double>(nc); H->wz = cv.take<double>(nw); H->rom = cv.take<double>(nw);
     H->mu = cv.take<double>(nc);
+    }
     H->diag_part = cv.take<double>(6 * DIAG_PARTS);
     H->diag_out = cv.take<double>(8);
     return cv.off + 256;
@@ -233,6 +280,10 @@ extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config 
     launch_terrain(h->geo, h->hn, h->hc, h->hxf, h->hyf, h->gxc, h->gyc, h->g4x, h->g4y, st);
     launch_base_state(h->geo, cfg->n_knots, h->knz, h->knt, cfg->theta_s, cfg->brunt_N, cfg->p_s, cfg->gravity,
                       h->rho0, h->th0, h->p0, st);
+    if (h->mixed) {
+        mx_build_base(h->geo, cfg->Cs, grid->dx, grid->dy, h->mbase, h->mrt0, st);
+        h->mb = mx_base_view(h->mbase, h->mrt0, nz);
+    }
     CK(cudaGetLastError(), "init kernels");
     CK(cudaStreamSynchronize(st), "init sync");   // host vectors above must outlive the copies
     CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "create capture stream");
@@ -242,9 +293,40 @@ extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config 
 }
 
 static CF5 cf(const F5 &f) { return CF5{f.r, f.t, f.u, f.v, f.w}; }
+static CF5f cf(const F5f &f) { return CF5f{f.r, f.t, f.u, f.v, f.w}; }
+
+// one RK3 step of the mixed-precision path (flat grids)
+static void enqueue_step_mixed(erf_handle *h, cudaStream_t s) {
+    const Geo &g = h->geo;
+    const Phys &ph = h->ph;
+    const erf_config &c = h->cfg;
+    mx_wall_bc(g, h->mst.w, s);
+    size_t bc = g.nc * sizeof(float), bw = g.nw * sizeof(float);
+    cudaMemcpyAsync(h->msn.r, h->mst.r, bc, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->msn.t, h->mst.t, bc, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->msn.u, h->mst.u, bc, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->msn.v, h->mst.v, bc, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->msn.w, h->mst.w, bw, cudaMemcpyDeviceToDevice, s);
+    for (int stage = 0; stage < 3; ++stage) {
+        mx_stage_begin(g, h->mb, cf(h->msn), cf(h->mst), h->mx, h->mpp, h->mpi, h->mthp, h->mTp, h->mOm, s);
+        ClIn clin{h->cl_w, h->cl_b, h->cl_stats, h->cl_out, h->cl_nfb};
+        mx_slow_rhs(g, h->mb, ph, cf(h->mst), h->mpp, h->mthp, h->mux, h->mvy, h->mwz, h->mmfx, h->mmfy, h->mmu,
+                    h->mR, s, h->cl_ready ? &clin : nullptr);
+        int nsub = stage == 0 ? 1 : (stage == 1 ? c.n_substeps / 2 : c.n_substeps);
+        double dtau = stage == 0 ? c.dt / 3.0 : c.dt / c.n_substeps;
+        mx_tri_build(g, h->mb, ph, h->mst.r, h->mst.t, h->mpi, h->mthp, dtau, h->tri, s);
+        for (int n = 0; n < nsub; ++n)
+            mx_substep(g, h->mb, ph, h->tri, h->mpi, h->mthp, cf(h->mR), h->mx, h->mOm, h->mTp, h->mdbuf, dtau, s);
+        mx_stage_end(g, h->mst, cf(h->mx), s);
+    }
+}
 
 // one RK3 step (Sec. 3.1) with the App. C substeps, enqueued on stream s
 static void enqueue_step(erf_handle *h, cudaStream_t s) {
+    if (h->mixed) {
+        enqueue_step_mixed(h, s);
+        return;
+    }
     const Geo &g = h->geo;
     const Phys &ph = h->ph;
     const erf_config &c = h->cfg;
@@ -308,6 +390,7 @@ extern "C" erf_status erf_rk3_step(erf_handle *h, int32_t nsteps) {
     if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
     if (nsteps < 0) return fail(h, ERF_EINVAL, "nsteps < 0");
     if (!h->have_state) return fail(h, ERF_ESTATE, "no state set");
+    if (h->cfg.closure == 3 && !h->cl_ready) return fail(h, ERF_ESTATE, "learned closure weights not set");
     if (!h->exec) {
         erf_status st = build_graph(h);
         if (st != ERF_OK) return st;
@@ -369,6 +452,26 @@ extern "C" erf_status erf_set_initial(erf_handle *h, const double *dtheta, const
     if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
     const Geo &g = h->geo;
     cudaStream_t s = h->user;
+    if (h->mixed) {
+        // FP64 staging in the (not yet used) tridiagonal arrays
+        const double *src[4] = {dtheta, u, v, w};
+        double *stage[4] = {h->tri.a, h->tri.cp, h->tri.im, h->tri.P};
+        long long len[4] = {g.nc, g.nc, g.nc, g.nw};
+        const double *dev[4] = {nullptr, nullptr, nullptr, nullptr};
+        for (int n = 0; n < 4; ++n) {
+            if (!src[n]) continue;
+            if (is_device) { dev[n] = src[n]; continue; }
+            cudaError_t e = cudaMemcpyAsync(stage[n], src[n], len[n] * sizeof(double), cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "copy initial field");
+            dev[n] = stage[n];
+        }
+        mx_set_initial(g, dev[0], dev[1], dev[2], dev[3], h->mst, s);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && !is_device) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "set_initial");
+        h->have_state = true;
+        return ERF_OK;
+    }
     const double *src[4] = {dtheta, u, v, w};
     double *stage[4] = {h->x.r, h->x.u, h->x.v, h->x.w};   // perturbation arrays as staging
     long long len[4] = {g.nc, g.nc, g.nc, g.nw};
@@ -414,9 +517,37 @@ extern "C" erf_status erf_set_state(erf_handle *h, int32_t field, const void *sr
     if (!src) return fail(h, ERF_EINVAL, "src is NULL");
     if (src_dtype != ERF_F64 && src_dtype != ERF_F32) return fail(h, ERF_EINVAL, "bad dtype");
     long long n;
-    double *dst = field_dev(h, field, n);
     cudaStream_t s = h->user;
     cudaError_t e;
+    if (h->mixed) {
+        float *mf[5] = {h->mst.r, h->mst.t, h->mst.u, h->mst.v, h->mst.w};
+        n = field == ERF_RHOW ? h->geo.nw : h->geo.nc;
+        const double *d64 = nullptr;
+        if (src_dtype == ERF_F64 && src_is_device) d64 = (const double *)src;
+        else {
+            double *stg = h->tri.a;
+            if (src_dtype == ERF_F64) {
+                e = cudaMemcpyAsync(stg, src, n * sizeof(double), cudaMemcpyHostToDevice, s);
+            } else {
+                const void *f = src;
+                e = cudaSuccess;
+                if (!src_is_device) {
+                    e = cudaMemcpyAsync(h->tri.cp, src, n * sizeof(float), cudaMemcpyHostToDevice, s);
+                    f = h->tri.cp;
+                }
+                if (e == cudaSuccess) launch_convert(f, stg, n, 1, s);
+            }
+            if (e != cudaSuccess) return cuda_fail(h, e, "copy state");
+            d64 = stg;
+        }
+        mx_from_full(h->geo, d64, mf[field], field, n, s);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && !src_is_device) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
+        h->have_state = true;
+        return ERF_OK;
+    }
+    double *dst = field_dev(h, field, n);
     if (src_dtype == ERF_F64) {
         e = cudaMemcpyAsync(dst, src, n * sizeof(double), src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
     } else {
@@ -445,9 +576,27 @@ extern "C" erf_status erf_get_state(erf_handle *h, int32_t field, void *dst, int
     if (!dst) return fail(h, ERF_EINVAL, "dst is NULL");
     if (dst_dtype != ERF_F64 && dst_dtype != ERF_F32) return fail(h, ERF_EINVAL, "bad dtype");
     long long n;
-    const double *src = field_dev(h, field, n);
     cudaStream_t s = h->user;
     cudaError_t e;
+    if (h->mixed && field <= ERF_RHOW) {
+        const float *mf[5] = {h->mst.r, h->mst.t, h->mst.u, h->mst.v, h->mst.w};
+        n = field == ERF_RHOW ? h->geo.nw : h->geo.nc;
+        double *stg = (dst_dtype == ERF_F64 && dst_is_device) ? (double *)dst : h->mdbuf;
+        mx_to_full(h->geo, mf[field], stg, field, n, s);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && dst_dtype == ERF_F64 && !dst_is_device)
+            e = cudaMemcpyAsync(dst, stg, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && dst_dtype == ERF_F32) {
+            void *d = dst_is_device ? dst : (void *)h->tri.cp;
+            launch_convert(stg, d, n, 0, s);
+            e = cudaGetLastError();
+            if (e == cudaSuccess && !dst_is_device) e = cudaMemcpyAsync(dst, d, n * sizeof(float), cudaMemcpyDeviceToHost, s);
+        }
+        if (e == cudaSuccess && !dst_is_device) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "get_state");
+        return ERF_OK;
+    }
+    const double *src = field_dev(h, field, n);
     if (dst_dtype == ERF_F64) {
         e = cudaMemcpyAsync(dst, src, n * sizeof(double), dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
     } else {
@@ -468,7 +617,8 @@ extern "C" erf_status erf_get_state(erf_handle *h, int32_t field, void *dst, int
 extern "C" erf_status erf_diagnostics(erf_handle *h, erf_diag *out) {
     if (!h || !out) return fail(h, ERF_EINVAL, "NULL argument");
     if (!h->have_state) return fail(h, ERF_ESTATE, "no state set");
-    launch_diag(h->geo, cf(h->st), h->cfg.dt, h->diag_part, h->diag_out, h->user);
+    if (h->mixed) mx_diag(h->geo, h->mb, cf(h->mst), h->cfg.dt, h->diag_part, h->diag_out, h->user);
+    else launch_diag(h->geo, cf(h->st), h->cfg.dt, h->diag_part, h->diag_out, h->user);
     double v[6];
     cudaError_t e = cudaMemcpyAsync(v, h->diag_out, sizeof(v), cudaMemcpyDeviceToHost, h->user);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->user);
@@ -483,6 +633,74 @@ extern "C" erf_status erf_diagnostics(erf_handle *h, erf_diag *out) {
     out->kernels_per_step = h->kernels_per_step;
     if (out->nonfinite) return fail(h, ERF_ENONFINITE, "state holds non-finite values");
     return ERF_OK;
+}
+
+// ---------------------------------------------------------------- learned closure entry points
+extern "C" erf_status erf_set_closure_weights(erf_handle *h, const void *blob, size_t bytes) {
+    if (!h || !blob) return fail(h, ERF_EINVAL, "NULL argument");
+    if (h->cfg.closure != 3 || !h->cl_w) return fail(h, ERF_EINVAL, "handle was not configured with the learned closure");
+    if (bytes != 8 + sizeof(float) * CL_BLOB_FLOATS) return fail(h, ERF_EINVAL, "closure blob has the wrong size");
+    unsigned magic;
+    std::memcpy(&magic, blob, 4);
+    if (magic != CL_MAGIC) return fail(h, ERF_EINVAL, "closure blob has the wrong magic");
+    cudaStream_t s = h->user;
+    cudaError_t e = cudaMemcpyAsync(h->cl_blob, (const char *)blob + 8, sizeof(float) * CL_BLOB_FLOATS,
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copy closure blob");
+    cl_prepare(h->cl_blob, h->cl_w, h->cl_b, h->cl_stats, s);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "prepare closure weights");
+    h->cl_ready = true;
+    // the captured step graph (if any) was built without the closure pointers being live
+    if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    return ERF_OK;
+}
+
+// EOS + face velocities of the current state (mixed path) into the stage scratch
+static void mx_current_fields(erf_handle *h, cudaStream_t s) {
+    mx_stage_begin(h->geo, h->mb, cf(h->mst), cf(h->mst), h->mx, h->mpp, h->mpi, h->mthp, h->mTp, h->mOm, s);
+    mx_slow_prep_only(h->geo, h->mb, cf(h->mst), h->mux, h->mvy, h->mwz, h->mmfx, h->mmfy, s);
+}
+
+extern "C" erf_status erf_closure_features(erf_handle *h, float *d_out) {
+    if (!h || !d_out) return fail(h, ERF_EINVAL, "NULL argument");
+    if (!h->mixed) return fail(h, ERF_EUNSUPPORTED, "closure features are built on the mixed-precision path");
+    if (!h->have_state) return fail(h, ERF_ESTATE, "no state set");
+    mx_current_fields(h, h->user);
+    cl_features_launch(h->geo, h->mb, h->cfg.gravity, h->mux, h->mvy, h->mwz, h->mthp, d_out, h->user);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ERF_OK : cuda_fail(h, e, "closure features");
+}
+
+extern "C" erf_status erf_closure_fields(erf_handle *h, float *d_out9, uint32_t *n_fallback) {
+    if (!h || !d_out9) return fail(h, ERF_EINVAL, "NULL argument");
+    if (!h->cl_ready) return fail(h, ERF_ESTATE, "learned closure weights not set");
+    if (!h->have_state) return fail(h, ERF_ESTATE, "no state set");
+    cudaStream_t s = h->user;
+    mx_current_fields(h, s);
+    cudaMemsetAsync(h->cl_nfb, 0, sizeof(unsigned), s);
+    cl_infer(h->geo, h->mb, h->ph, h->cl_w, h->cl_b, h->cl_stats, h->mux, h->mvy, h->mwz, h->mthp, h->mst.r, d_out9,
+             h->cl_nfb, s);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && n_fallback) {
+        e = cudaMemcpyAsync(n_fallback, h->cl_nfb, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    return e == cudaSuccess ? ERF_OK : cuda_fail(h, e, "closure fields");
+}
+
+extern "C" erf_status erf_filter_state(erf_handle *h, int32_t r, double *d_rho, double *d_rhotheta, double *d_rhou,
+                                       double *d_rhov, double *d_rhow, float *d_targets) {
+    if (!h || !d_rho || !d_rhotheta || !d_rhou || !d_rhov || !d_rhow || !d_targets) return fail(h, ERF_EINVAL, "NULL argument");
+    if (!h->mixed) return fail(h, ERF_EUNSUPPORTED, "the filter reads the mixed-precision state");
+    const Geo &g = h->geo;
+    if (r < 1 || g.nx % r || g.ny % r || g.nz % r) return fail(h, ERF_EINVAL, "grid not divisible by the filter ratio");
+    for (int k = 0; k < g.nz; ++k) (void)k;
+    cl_filter_launch(g, h->mb, cf(h->mst), r, d_rho, d_rhotheta, d_rhou, d_rhov, d_rhow, d_targets, h->user);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ERF_OK : cuda_fail(h, e, "filter");
 }
 
 extern "C" const char *erf_last_error(const erf_handle *h) {

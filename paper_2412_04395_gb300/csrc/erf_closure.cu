@@ -1,0 +1,328 @@
+// Learned subgrid closure: features, BF16 tensor-core inference with Smagorinsky fallback, the
+// 4x box filter that makes training targets, and the weight upload.
+//
+// Inference maps each cell's 12 features (resolved velocity gradients, dtheta/dx, dtheta/dy, N^2)
+// through 12 -> 64 -> 64 -> 64 -> 9 (SiLU) to the kinematic SGS stress and heat flux.  A warp
+// takes 16 cells: the 16 x 16 feature tile (12 + 4 zero columns) and every hidden activation tile
+// live in BF16 mma.sync fragments (m16n8k16, FP32 accumulate); the accumulator fragments of two
+// adjacent n-tiles are exactly the A fragment of the next k-tile, so activations never leave
+// registers between layers.  Weights sit in shared memory in [out][in] row-major BF16, which is
+// the "col" B-fragment order of the instruction.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "../../include/erf.h"
+#include "erf_closure.h"
+#include "erf_dev.cuh"
+#include "erf_launch.h"
+#include "erf_mixed.h"
+
+namespace erfk {
+
+// device weight block (built from a blob by k_cl_prepare)
+struct ClDev {
+    const __nv_bfloat16 *W1;   // [64][16]  (inputs padded with zeros)
+    const __nv_bfloat16 *W2;   // [64][64]
+    const __nv_bfloat16 *W3;   // [64][64]
+    const __nv_bfloat16 *W4;   // [16][64]  (outputs padded with zero rows)
+    const float *b;            // b1[64] b2[64] b3[64] b4[16]
+    const float *stats;        // in_mean[12] in_std[12] out_mean[9] out_std[9]
+};
+constexpr int CL_W_BF16 = 64 * 16 + 64 * 64 * 2 + 16 * 64;   // 10240
+constexpr int CL_B_F32 = 64 * 3 + 16;
+
+__global__ void k_cl_prepare(const float *blob, __nv_bfloat16 *w, float *b, float *stats) {
+    const float *st = blob;                 // 42 stats
+    const float *p = blob + 2 * CL_NIN + 2 * CL_NOUT;
+    const float *W1 = p, *b1 = W1 + 64 * 12, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64, *b3 = W3 + 64 * 64;
+    const float *W4 = b3 + 64, *b4 = W4 + 9 * 64;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < 2 * CL_NIN + 2 * CL_NOUT) stats[t] = st[t];
+    if (t < 64 * 16) { int o = t / 16, i = t % 16; w[t] = __float2bfloat16_rn(i < 12 ? W1[o * 12 + i] : 0.f); }
+    if (t < 64 * 64) {
+        w[1024 + t] = __float2bfloat16_rn(W2[t]);
+        w[1024 + 4096 + t] = __float2bfloat16_rn(W3[t]);
+    }
+    if (t < 16 * 64) { int o = t / 64, i = t % 64; w[1024 + 8192 + t] = __float2bfloat16_rn(o < 9 ? W4[o * 64 + i] : 0.f); }
+    if (t < 64) { b[t] = b1[t]; b[64 + t] = b2[t]; b[128 + t] = b3[t]; }
+    if (t < 16) b[192 + t] = t < 9 ? b4[t] : 0.f;
+}
+
+__device__ __forceinline__ float fv(const Geo &g, const float *f, int i, int j, int k) {
+    return __ldg(f + cixw(g, i, j, kref(k, g.nz)));
+}
+__device__ __forceinline__ float dth0f(const Geo &g, int ka, int kb) {
+    return (float)(g.th0[kref(ka, g.nz)] - g.th0[kref(kb, g.nz)]);
+}
+
+// the 12 inputs at cell (i,j,k); also returns dtheta/dz (for the fallback heat flux)
+struct VelIn {
+    const float *ux, *vy, *wz, *thp;
+};
+__device__ void cl_features(const Geo &g, const MxBase &mb, const VelIn &v, double grav, int i, int j, int k,
+                            float *f, float &dthdz) {
+    const float rdx = (float)g.rdx, rdy = (float)g.rdy;
+    auto uc = [&](int ii, int jj, int kk) { return 0.5f * (fv(g, v.ux, ii, jj, kk) + fv(g, v.ux, ii + 1, jj, kk)); };
+    auto vc = [&](int ii, int jj, int kk) { return 0.5f * (fv(g, v.vy, ii, jj, kk) + fv(g, v.vy, ii, jj + 1, kk)); };
+    auto wc = [&](int ii, int jj, int kk) {
+        return 0.5f * (__ldg(v.wz + cixw(g, ii, jj, kk)) + __ldg(v.wz + cixw(g, ii, jj, kk + 1)));
+    };
+    int kl = k > 0 ? k - 1 : 0, ku = k < g.nz - 1 ? k + 1 : g.nz - 1;
+    float rz = (ku > kl) ? (float)(1.0 / (g.zetac[ku] - g.zetac[kl])) : 0.f;
+    f[0] = (fv(g, v.ux, i + 1, j, k) - fv(g, v.ux, i, j, k)) * rdx;
+    f[1] = (uc(i, j + 1, k) - uc(i, j - 1, k)) * 0.5f * rdy;
+    f[2] = (uc(i, j, ku) - uc(i, j, kl)) * rz;
+    f[3] = (vc(i + 1, j, k) - vc(i - 1, j, k)) * 0.5f * rdx;
+    f[4] = (fv(g, v.vy, i, j + 1, k) - fv(g, v.vy, i, j, k)) * rdy;
+    f[5] = (vc(i, j, ku) - vc(i, j, kl)) * rz;
+    f[6] = (wc(i + 1, j, k) - wc(i - 1, j, k)) * 0.5f * rdx;
+    f[7] = (wc(i, j + 1, k) - wc(i, j - 1, k)) * 0.5f * rdy;
+    f[8] = (__ldg(v.wz + cixw(g, i, j, k + 1)) - __ldg(v.wz + cixw(g, i, j, k))) * mb.rdzf[k];
+    f[9] = (fv(g, v.thp, i + 1, j, k) - fv(g, v.thp, i - 1, j, k)) * 0.5f * rdx;
+    f[10] = (fv(g, v.thp, i, j + 1, k) - fv(g, v.thp, i, j - 1, k)) * 0.5f * rdy;
+    dthdz = (dth0f(g, ku, kl) + fv(g, v.thp, i, j, ku) - fv(g, v.thp, i, j, kl)) * rz;
+    f[11] = (float)(grav / g.th0[k]) * dthdz;
+}
+
+__device__ __forceinline__ unsigned pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);   // .x = a (low half), .y = b
+    return *reinterpret_cast<unsigned *>(&h);
+}
+__device__ __forceinline__ void mma16816(float *d, const unsigned *a, unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ float silu_dev(float x) { return x / (1.f + __expf(-x)); }
+
+// Learned SGS stress/heat flux at every cell (mixed path).  Block = 8 warps x 16 cells.
+// out: 9 planes of nc floats: rho t11, rho t22, rho t33, rho t12, rho t13, rho t23, rho h1..h3.
+constexpr int CLW = 8;
+__global__ void __launch_bounds__(CLW * 32) k_cl_infer(Geo g, MxBase mb, Phys ph, ClDev cl, VelIn v,
+                                                       const float *dr, float *out, unsigned *nfallback) {
+    __shared__ __align__(16) __nv_bfloat16 sW[CL_W_BF16];
+    __shared__ float sb[CL_B_F32];
+    __shared__ float sst[2 * CL_NIN + 2 * CL_NOUT];
+    __shared__ __align__(16) float sF[CLW][16][17];    // standardised features, then outputs
+    __shared__ float sMisc[CLW][16][12];               // fallback: strain, rho, mu inputs
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int q = tid; q < CL_W_BF16; q += blockDim.x) sW[q] = cl.W1[q];   // W1..W4 are contiguous
+    for (int q = tid; q < CL_B_F32; q += blockDim.x) sb[q] = cl.b[q];
+    for (int q = tid; q < 2 * CL_NIN + 2 * CL_NOUT; q += blockDim.x) sst[q] = cl.stats[q];
+    __syncthreads();
+    const __nv_bfloat16 *W1 = sW, *W2 = sW + 1024, *W3 = sW + 1024 + 4096, *W4 = sW + 1024 + 8192;
+    const float *in_mu = sst, *in_sd = sst + 12, *out_mu = sst + 24, *out_sd = sst + 33;
+    long long c0 = ((long long)blockIdx.x * CLW + warp) * 16;
+    // 1. features of 16 cells (lanes 0..15), standardised; fallback flag on |z| > 6
+    int fb = 0;
+    if (lane < 16) {
+        long long c = c0 + lane;
+        float f[12], dthdz = 0.f;
+        if (c < g.nc) {
+            int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+            cl_features(g, mb, v, ph.g, i, j, k, f, dthdz);
+            for (int q = 0; q < 12; ++q) {
+                float z = (f[q] - in_mu[q]) / in_sd[q];
+                if (!(fabsf(z) <= 6.f)) fb = 1;
+                sF[warp][lane][q] = z;
+            }
+            // Smagorinsky fallback inputs at the cell centre
+            float s11 = f[0], s22 = f[4], s33 = f[8];
+            float s12 = 0.5f * (f[1] + f[3]), s13 = 0.5f * (f[2] + f[6]), s23 = 0.5f * (f[5] + f[7]);
+            float rho = mb.rho0f[k] + dr[c];
+            float SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.f * (s12 * s12 + s13 * s13 + s23 * s23);
+            float mu = rho * mb.delta2f[k] * sqrtf(2.f * SS);
+            float tr = (s11 + s22 + s33) * (1.f / 3.f);
+            float *m = sMisc[warp][lane];
+            m[0] = -2.f * mu * (s11 - tr); m[1] = -2.f * mu * (s22 - tr); m[2] = -2.f * mu * (s33 - tr);
+            m[3] = -2.f * mu * s12; m[4] = -2.f * mu * s13; m[5] = -2.f * mu * s23;
+            float rPr = (float)(1.0 / ph.Pr_t);
+            m[6] = -mu * rPr * f[9]; m[7] = -mu * rPr * f[10]; m[8] = -mu * rPr * dthdz;
+            m[9] = rho;
+        } else {
+            for (int q = 0; q < 12; ++q) sF[warp][lane][q] = 0.f;
+            sMisc[warp][lane][9] = 0.f;
+        }
+        for (int q = 12; q < 16; ++q) sF[warp][lane][q] = 0.f;
+        sMisc[warp][lane][10] = (float)fb;
+    }
+    __syncwarp();
+    // 2. MLP on tensor cores.  Fragment coordinates: g = lane/4 (row), t = lane%4.
+    const int gr = lane >> 2, tc = lane & 3;
+    unsigned a[4][4];   // A fragments of the current activation, per k-tile (up to 4 k-tiles of 16)
+    {
+        const float *r0 = sF[warp][gr], *r1 = sF[warp][gr + 8];
+        a[0][0] = pack_bf16(r0[2 * tc], r0[2 * tc + 1]);
+        a[0][1] = pack_bf16(r1[2 * tc], r1[2 * tc + 1]);
+        a[0][2] = pack_bf16(r0[2 * tc + 8], r0[2 * tc + 9]);
+        a[0][3] = pack_bf16(r1[2 * tc + 8], r1[2 * tc + 9]);
+    }
+    float acc[8][4];
+    auto layer = [&](const __nv_bfloat16 *W, int ldw, int nkt, const float *bias) {
+        for (int nt = 0; nt < 8; ++nt) {
+            for (int q = 0; q < 4; ++q) acc[nt][q] = 0.f;
+            const __nv_bfloat16 *wr = W + (nt * 8 + gr) * ldw;   // row n = nt*8 + gr of W (= column of B)
+            for (int kt = 0; kt < nkt; ++kt) {
+                unsigned b0 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc);
+                unsigned b1 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc + 8);
+                mma16816(acc[nt], a[kt], b0, b1);
+            }
+        }
+        // bias + SiLU, repack as A fragments (n-tiles 2kt, 2kt+1 -> k-tile kt)
+        for (int kt = 0; kt < 4; ++kt) {
+            float *lo = acc[2 * kt], *hi = acc[2 * kt + 1];
+            int c_lo = kt * 16 + 2 * tc, c_hi = c_lo + 8;
+            a[kt][0] = pack_bf16(silu_dev(lo[0] + bias[c_lo]), silu_dev(lo[1] + bias[c_lo + 1]));
+            a[kt][1] = pack_bf16(silu_dev(lo[2] + bias[c_lo]), silu_dev(lo[3] + bias[c_lo + 1]));
+            a[kt][2] = pack_bf16(silu_dev(hi[0] + bias[c_hi]), silu_dev(hi[1] + bias[c_hi + 1]));
+            a[kt][3] = pack_bf16(silu_dev(hi[2] + bias[c_hi]), silu_dev(hi[3] + bias[c_hi + 1]));
+        }
+    };
+    layer(W1, 16, 1, sb);
+    layer(W2, 64, 4, sb + 64);
+    layer(W3, 64, 4, sb + 128);
+    // output layer: 2 n-tiles of 8 (9 valid columns)
+    float y[2][4];
+    for (int nt = 0; nt < 2; ++nt) {
+        for (int q = 0; q < 4; ++q) y[nt][q] = 0.f;
+        const __nv_bfloat16 *wr = W4 + (nt * 8 + gr) * 64;
+        for (int kt = 0; kt < 4; ++kt) {
+            unsigned b0 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc);
+            unsigned b1 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc + 8);
+            mma16816(y[nt], a[kt], b0, b1);
+        }
+    }
+    __syncwarp();
+    for (int nt = 0; nt < 2; ++nt) {
+        int col = nt * 8 + 2 * tc;
+        sF[warp][gr][col] = y[nt][0] + sb[192 + col];
+        sF[warp][gr][col + 1] = y[nt][1] + sb[192 + col + 1];
+        sF[warp][gr + 8][col] = y[nt][2] + sb[192 + col];
+        sF[warp][gr + 8][col + 1] = y[nt][3] + sb[192 + col + 1];
+    }
+    __syncwarp();
+    // 3. de-standardise, fallback, density weighting, store (lanes 0..15, one cell each)
+    if (lane < 16) {
+        long long c = c0 + lane;
+        if (c < g.nc) {
+            const float *m = sMisc[warp][lane];
+            int use_fb = m[10] != 0.f;
+            float o[9];
+            for (int q = 0; q < 9; ++q) {
+                o[q] = sF[warp][lane][q] * out_sd[q] + out_mu[q];
+                if (!isfinite(o[q])) use_fb = 1;
+            }
+            float rho = m[9];
+            for (int q = 0; q < 9; ++q) out[(long long)q * g.nc + c] = use_fb ? m[q] : rho * o[q];
+            if (use_fb && nfallback) atomicAdd(nfallback, 1u);
+        }
+    }
+}
+
+// features only (training data / analysis): out [nc][12]
+__global__ void k_cl_features(Geo g, MxBase mb, VelIn v, double grav, float *out) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    float f[12], d;
+    cl_features(g, mb, v, grav, i, j, k, f, d);
+    for (int q = 0; q < 12; ++q) out[c * 12 + q] = f[q];
+}
+
+// 4x4x4 (r^3) Favre box filter of a fine flat mixed-precision state into a coarse C-grid state
+// (FP64 full fields) and SGS targets t_ij, h_j (FP32, [Nc][9]).  One thread per coarse cell.
+__global__ void k_cl_filter(Geo g, MxBase mb, CF5f st, int r, double *cr, double *crt, double *cru, double *crv,
+                            double *crw, float *targets) {
+    int Nx = g.nx / r, Ny = g.ny / r, Nz = g.nz / r;
+    long long C = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long NC = (long long)Nx * Ny * Nz;
+    if (C >= NC) return;
+    int I = (int)(C % Nx), J = (int)((C / Nx) % Ny), K = (int)(C / ((long long)Nx * Ny));
+    double sr = 0, srt = 0, su[3] = {0, 0, 0}, suu[6] = {0, 0, 0, 0, 0, 0}, sut[3] = {0, 0, 0};
+    const int pr[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    for (int dk = 0; dk < r; ++dk)
+        for (int dj = 0; dj < r; ++dj)
+            for (int di = 0; di < r; ++di) {
+                int i = I * r + di, j = J * r + dj, k = K * r + dk;
+                long long c = cix(g, i, j, k);
+                double rho = g.rho0[k] + (double)st.r[c];
+                double rt = g.rho0[k] * g.th0[k] + (double)st.t[c];
+                double rx0 = g.rho0[k] + 0.5 * ((double)fv(g, st.r, i - 1, j, k) + (double)st.r[c]);
+                double rx1 = g.rho0[k] + 0.5 * ((double)st.r[c] + (double)fv(g, st.r, i + 1, j, k));
+                double ry0 = g.rho0[k] + 0.5 * ((double)fv(g, st.r, i, j - 1, k) + (double)st.r[c]);
+                double ry1 = g.rho0[k] + 0.5 * ((double)st.r[c] + (double)fv(g, st.r, i, j + 1, k));
+                auto rzf = [&](int kf) -> double {
+                    if (kf == 0) return g.rho0[0] + (double)st.r[cix(g, i, j, 0)];
+                    if (kf == g.nz) return g.rho0[g.nz - 1] + (double)st.r[cix(g, i, j, g.nz - 1)];
+                    return 0.5 * (g.rho0[kf - 1] + g.rho0[kf]) + 0.5 * ((double)st.r[cix(g, i, j, kf - 1)] + (double)st.r[cix(g, i, j, kf)]);
+                };
+                double u = 0.5 * ((double)st.u[c] / rx0 + (double)__ldg(st.u + cixw(g, i + 1, j, k)) / rx1);
+                double vv = 0.5 * ((double)st.v[c] / ry0 + (double)__ldg(st.v + cixw(g, i, j + 1, k)) / ry1);
+                double w = 0.5 * ((double)st.w[cix(g, i, j, k)] / rzf(k) + (double)st.w[cix(g, i, j, k + 1)] / rzf(k + 1));
+                double th = rt / rho;
+                double vel[3] = {u, vv, w};
+                sr += rho;
+                srt += rt;
+                for (int q = 0; q < 3; ++q) { su[q] += rho * vel[q]; sut[q] += rho * vel[q] * th; }
+                for (int q = 0; q < 6; ++q) suu[q] += rho * vel[pr[q][0]] * vel[pr[q][1]];
+            }
+    double n3 = (double)r * r * r;
+    double rb = sr / n3;
+    double ut[3] = {su[0] / n3 / rb, su[1] / n3 / rb, su[2] / n3 / rb};
+    double tht = srt / n3 / rb;
+    long long Cc = C;
+    cr[Cc] = rb;
+    crt[Cc] = srt / n3;
+    for (int q = 0; q < 6; ++q) targets[Cc * 9 + q] = (float)(suu[q] / n3 / rb - ut[pr[q][0]] * ut[pr[q][1]]);
+    for (int q = 0; q < 3; ++q) targets[Cc * 9 + 6 + q] = (float)(sut[q] / n3 / rb - ut[q] * tht);
+    // coarse face momenta: means over the r x r fine faces on each coarse face
+    double fu = 0, fvv = 0;
+    for (int a = 0; a < r; ++a)
+        for (int b = 0; b < r; ++b) {
+            fu += (double)st.u[cix(g, I * r, J * r + b, K * r + a)];
+            fvv += (double)st.v[cix(g, I * r + b, J * r, K * r + a)];
+        }
+    cru[Cc] = fu / (r * r);
+    crv[Cc] = fvv / (r * r);
+    double fw = 0;
+    for (int a = 0; a < r; ++a)
+        for (int b = 0; b < r; ++b) fw += (double)st.w[cix(g, I * r + b, J * r + a, K * r)];
+    crw[Cc] = fw / (r * r);
+    if (K == Nz - 1) {   // top coarse w-face row
+        long long Ct = ((long long)Nz * Ny + J) * Nx + I;
+        double ft = 0;
+        for (int a = 0; a < r; ++a)
+            for (int b = 0; b < r; ++b) ft += (double)st.w[cix(g, I * r + b, J * r + a, g.nz)];
+        crw[Ct] = ft / (r * r);
+    }
+}
+
+void cl_prepare(const float *d_blob, void *w_bf16, float *b, float *stats, cudaStream_t s) {
+    k_cl_prepare<<<(64 * 64 + 255) / 256, 256, 0, s>>>(d_blob, (__nv_bfloat16 *)w_bf16, b, stats);
+}
+void cl_infer(const Geo &g, const MxBase &mb, const Phys &ph, const void *w_bf16, const float *b,
+              const float *stats, const float *ux, const float *vy, const float *wz, const float *thp,
+              const float *dr, float *out, unsigned *nfb, cudaStream_t s) {
+    const __nv_bfloat16 *w = (const __nv_bfloat16 *)w_bf16;
+    ClDev cl{w, w + 1024, w + 1024 + 4096, w + 1024 + 8192, b, stats};
+    long long nwarps = (g.nc + 15) / 16;
+    unsigned nblk = (unsigned)((nwarps + CLW - 1) / CLW);
+    mx_launch("mx_closure_mlp", s, [&] {
+        k_cl_infer<<<nblk, CLW * 32, 0, s>>>(g, mb, ph, cl, VelIn{ux, vy, wz, thp}, dr, out, nfb);
+    });
+}
+void cl_features_launch(const Geo &g, const MxBase &mb, double grav, const float *ux, const float *vy,
+                        const float *wz, const float *thp, float *out, cudaStream_t s) {
+    k_cl_features<<<(unsigned)((g.nc + 255) / 256), 256, 0, s>>>(g, mb, VelIn{ux, vy, wz, thp}, grav, out);
+}
+void cl_filter_launch(const Geo &g, const MxBase &mb, CF5f st, int r, double *cr, double *crt, double *cru,
+                      double *crv, double *crw, float *targets, cudaStream_t s) {
+    long long NC = (long long)(g.nx / r) * (g.ny / r) * (g.nz / r);
+    k_cl_filter<<<(unsigned)((NC + 127) / 128), 128, 0, s>>>(g, mb, st, r, cr, crt, cru, crv, crw, targets);
+}
+
+}  // namespace erfk

@@ -11,48 +11,13 @@
 //   stage_end   (S^t <- S^t + X'')
 #include "erf_dev.cuh"
 #include "erf_launch.h"
+#include "erf_stencil.cuh"
 
 #include <math.h>
 
 namespace erfk {
 
-// ------------------------------------------------------------------ interpolants (Sec. 3.6)
-// q[0..5] = q_{m-3}..q_{m+2}; value at m-1/2; s = sign of the advecting normal momentum there.
-__device__ __forceinline__ double upwind5(const double *q, double s) {
-    double c6 = (37.0 / 60.0) * (q[3] + q[2]) - (2.0 / 15.0) * (q[4] + q[1]) + (1.0 / 60.0) * (q[5] + q[0]);
-    return c6 - (s / 60.0) * ((q[5] - q[0]) - 5.0 * (q[4] - q[1]) + 10.0 * (q[3] - q[2]));
-}
-__device__ __forceinline__ double sgnd(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
-
-// WENO5-JS (Jiang & Shu 1996) or WENO5-Z (Borges et al. 2008) face value, upwind side by s >= 0.
-__device__ __forceinline__ double weno5(const double *q, double s, int zflag) {
-    double a, b, c, d, e;   // v_{-2}, v_{-1}, v_0, v_1, v_2 on the upwind side
-    if (s >= 0.0) { a = q[0]; b = q[1]; c = q[2]; d = q[3]; e = q[4]; }
-    else { a = q[5]; b = q[4]; c = q[3]; d = q[2]; e = q[1]; }
-    const double eps = 1.0e-6;
-    double p0 = (2.0 * a - 7.0 * b + 11.0 * c) * (1.0 / 6.0);
-    double p1 = (-b + 5.0 * c + 2.0 * d) * (1.0 / 6.0);
-    double p2 = (2.0 * c + 5.0 * d - e) * (1.0 / 6.0);
-    double t0 = a - 2.0 * b + c, u0 = a - 4.0 * b + 3.0 * c;
-    double t1 = b - 2.0 * c + d, u1 = b - d;
-    double t2 = c - 2.0 * d + e, u2 = 3.0 * c - 4.0 * d + e;
-    double b0 = (13.0 / 12.0) * t0 * t0 + 0.25 * u0 * u0;
-    double b1 = (13.0 / 12.0) * t1 * t1 + 0.25 * u1 * u1;
-    double b2 = (13.0 / 12.0) * t2 * t2 + 0.25 * u2 * u2;
-    double w0, w1, w2;
-    if (zflag) {
-        double tau = fabs(b0 - b2);
-        w0 = 0.1 * (1.0 + tau / (b0 + eps));
-        w1 = 0.6 * (1.0 + tau / (b1 + eps));
-        w2 = 0.3 * (1.0 + tau / (b2 + eps));
-    } else {
-        double e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
-        w0 = 0.1 / (e0 * e0);
-        w1 = 0.6 / (e1 * e1);
-        w2 = 0.3 / (e2 * e2);
-    }
-    return (w0 * p0 + w1 * p1 + w2 * p2) / (w0 + w1 + w2);
-}
+__device__ __forceinline__ double sgnd(double x) { return sgnT<double>(x); }
 
 // Exner function and pressure from rho*theta (Sec. 2.1 EOS, dry):
 // pi = (R_d rho theta / P00)^(R_d/c_v), p = R_d rho theta pi.  The product is rounded on its
@@ -359,7 +324,8 @@ __device__ double tau23(const Geo &g, const Phys &ph, const Vel &v, const double
     double me = 0.25 * (cval(g, mu, i, j - 1, k - 1) + cval(g, mu, i, j, k - 1) + cval(g, mu, i, j - 1, k) + cval(g, mu, i, j, k));
     return -2.0 * me * S23e(g, v, i, j, k);
 }
-// heat flux rho alpha dtheta/dn at the three face types; bottom face: rho Q (MOST)
+// rho alpha dtheta/dn at the three face types (minus the diffusive flux); bottom face: the
+// upward MOST flux rho Q enters as -rho Q
 __device__ __forceinline__ double heat_x(const Geo &g, const Phys &ph, const double *mu, const double *th, int i, int j, int k) {
     return 0.5 * (cval(g, mu, i - 1, j, k) + cval(g, mu, i, j, k)) / ph.Pr_t * (cval(g, th, i, j, k) - cval(g, th, i - 1, j, k)) * g.rdx;
 }
@@ -368,7 +334,7 @@ __device__ __forceinline__ double heat_y(const Geo &g, const Phys &ph, const dou
 }
 __device__ __forceinline__ double heat_z(const Geo &g, const Phys &ph, const double *mu, const double *th, const double *rho,
                                          int i, int j, int k, int visc) {
-    if (k == 0) return ph.surface == 1 ? cval(g, rho, i, j, 0) * ph.Qs : 0.0;
+    if (k == 0) return ph.surface == 1 ? -cval(g, rho, i, j, 0) * ph.Qs : 0.0;   // upward flux rho Q
     if (k >= g.nz || !visc) return 0.0;
     return 0.5 * (cval(g, mu, i, j, k - 1) + cval(g, mu, i, j, k)) / ph.Pr_t
          * (cval(g, th, i, j, k) - cval(g, th, i, j, k - 1)) / g.dzc[k];
@@ -835,6 +801,7 @@ constexpr int BS = 256;
 // Optional per-launch event timing (profiling mode, never inside a graph capture).
 static thread_local ProfSink *g_prof = nullptr;
 void set_profiler(ProfSink *p) { g_prof = p; }
+ProfSink *current_profiler() { return g_prof; }
 struct ProfScope {
     cudaStream_t s;
     const char *name;
@@ -913,6 +880,9 @@ void launch_stage_nosub(const Geo &g, F5 st, CF5 sn, CF5 R, double adt, cudaStre
 void launch_diag(const Geo &g, CF5 st, double dt, double *part, double *out, cudaStream_t s) {
     LAUNCH("diag_partial", s, k_diag_partial<<<DIAG_BLOCKS, 256, 0, s>>>(g, st, part));
     LAUNCH("diag_final", s, k_diag_final<<<1, 32, 0, s>>>(part, DIAG_BLOCKS, dt, out));
+}
+void launch_diag_final(const double *part, int nparts, double dt, double *out, cudaStream_t s) {
+    LAUNCH("diag_final", s, k_diag_final<<<1, 32, 0, s>>>(part, nparts, dt, out));
 }
 void launch_convert(const void *src, void *dst, long long n, int to_f64, cudaStream_t s) {
     if (to_f64)

@@ -35,5 +35,6 @@ struct ProfSink {
     virtual ~ProfSink() {}
 };
 void set_profiler(ProfSink *p);
+ProfSink *current_profiler();
 
 }  // namespace erfk

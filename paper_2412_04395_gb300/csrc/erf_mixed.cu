@@ -1,0 +1,792 @@
+// Mixed-precision kernels of the RK3 step (flat grids): the stencil bulk runs in FP32 on
+// perturbations from the FP64 hydrostatic base state, the vertical acoustic system is assembled,
+// factored and solved in FP64, and mass sums are FP64.
+//
+// Stored in FP32: drho = rho - rho0, dTh = rho theta - rho0 theta0, rho u, rho v, rho w, and
+// every derived stencil field.  The formulas are the FP64 path's (same discretisation) written
+// so that no FP32 quantity cancels against the O(300 K) or O(1e5 Pa) base values:
+//   p'     = p0 expm1(gamma log1p(dTh / (rho0 theta0)))
+//   theta' = (dTh - theta0 drho) / (rho0 + drho)
+//   B      = -g drho
+//   rho theta tendency = theta0_k R_rho - div(F (theta_face - theta0_k)), where WENO5 acts on
+//            theta differences relative to the upwind cell (WENO is invariant to that shift) and
+//            base-state differences theta0_a - theta0_b are formed in FP64.
+#include "erf_dev.cuh"
+#include "erf_launch.h"
+#include "erf_mixed.h"
+#include "erf_stencil.cuh"
+
+#include <math.h>
+
+namespace erfk {
+
+constexpr float GAMMAf = (float)GAMMA;
+constexpr float RDCVf = (float)(RD / CVD);
+
+__device__ __forceinline__ float fval(const Geo &g, const float *f, int i, int j, int k) {
+    return __ldg(f + cixw(g, i, j, kref(k, g.nz)));
+}
+__device__ __forceinline__ float wvalf(const Geo &g, const float *f, int i, int j, int k) {
+    float sgn = 1.f, add = 0.f;
+    while (k < 0 || k > g.nz) {
+        if (k < 0) { add += sgn * 2.f * __ldg(f + cixw(g, i, j, 0)); sgn = -sgn; k = -k; }
+        else { add += sgn * 2.f * __ldg(f + cixw(g, i, j, g.nz)); sgn = -sgn; k = 2 * g.nz - k; }
+    }
+    return add + sgn * __ldg(f + cixw(g, i, j, k));
+}
+// base-state theta difference theta0_a - theta0_b formed in FP64 (levels reflected)
+__device__ __forceinline__ float dth0(const Geo &g, int ka, int kb) {
+    return (float)(g.th0[kref(ka, g.nz)] - g.th0[kref(kb, g.nz)]);
+}
+
+// ------------------------------------------------------------------ per-level base tables
+__global__ void k_mx_base(Geo g, double Cs, double dx, double dy, float *f32, double *rt0) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int L = g.nz + 1;
+    if (k > g.nz) return;
+    if (k < g.nz) {
+        double r0 = g.rho0[k], t0 = g.th0[k], p0 = g.p0[k];
+        f32[k] = (float)r0;
+        f32[L + k] = (float)t0;
+        f32[2 * L + k] = (float)p0;
+        f32[3 * L + k] = (float)pow(RD * r0 * t0 * (1.0 / P00), RD / CVD);
+        f32[4 * L + k] = (float)(1.0 / (r0 * t0));
+        f32[6 * L + k] = (float)g.dzeta[k];
+        f32[7 * L + k] = (float)(1.0 / g.dzeta[k]);
+        double Delta = cbrt(dx * dy * g.dzeta[k]);
+        f32[9 * L + k] = (float)((Cs * Delta) * (Cs * Delta));
+        rt0[k] = r0 * t0;
+    }
+    double rw = (k == 0) ? g.rho0[0] : (k == g.nz ? g.rho0[g.nz - 1] : 0.5 * (g.rho0[k - 1] + g.rho0[k]));
+    f32[5 * L + k] = (float)rw;
+    f32[8 * L + k] = (k >= 1 && k < g.nz) ? (float)(1.0 / g.dzc[k]) : 0.f;
+}
+
+// ------------------------------------------------------------------ init / state conversion
+__global__ void k_mx_init_cells(Geo g, const double *dth, float *dr, float *dt) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int k = (int)(c / g.nxy);
+    double th0 = g.th0[k], r0 = g.rho0[k];
+    double th = th0 + (dth ? dth[c] : 0.0);
+    dr[c] = (float)(r0 * (th0 / th) - r0);
+    dt[c] = 0.0f;
+}
+__global__ void k_mx_init_faces(Geo g, const double *u, const double *v, const double *w, const float *dr,
+                                float *ru, float *rv, float *rw) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nw) return;
+    int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / g.nxy);
+    if (k < g.nz) {
+        double r0 = g.rho0[k];
+        ru[n] = u ? (float)(u[n] * (r0 + 0.5 * ((double)fval(g, dr, i - 1, j, k) + (double)dr[n]))) : 0.f;
+        rv[n] = v ? (float)(v[n] * (r0 + 0.5 * ((double)fval(g, dr, i, j - 1, k) + (double)dr[n]))) : 0.f;
+    }
+    if (k == 0 || k == g.nz) { rw[n] = 0.f; return; }
+    double rb = 0.5 * (g.rho0[k - 1] + g.rho0[k]) + 0.5 * ((double)dr[n - g.nxy] + (double)dr[n]);
+    rw[n] = w ? (float)(w[n] * rb) : 0.f;
+}
+// full FP64 field -> FP32 perturbation (field 0 rho, 1 rho theta, else momentum)
+__global__ void k_mx_from_full(Geo g, const double *src, float *dst, int field, long long n) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int k = (int)(t / g.nxy);
+    double b = field == 0 ? g.rho0[k] : (field == 1 ? g.rho0[k] * g.th0[k] : 0.0);
+    dst[t] = (float)(src[t] - b);
+}
+__global__ void k_mx_to_full(Geo g, const float *src, double *dst, int field, long long n) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int k = (int)(t / g.nxy);
+    double b = field == 0 ? g.rho0[k] : (field == 1 ? g.rho0[k] * g.th0[k] : 0.0);
+    dst[t] = b + (double)src[t];
+}
+__global__ void k_mx_wall_bc(Geo g, float *rw) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nxy) return;
+    rw[n] = 0.f;
+    rw[n + (long long)g.nz * g.nxy] = 0.f;
+}
+
+// ------------------------------------------------------------------ stage begin (EOS, X'')
+__global__ void k_mx_stage_begin(Geo g, MxBase mb, CF5f sn, CF5f st, F5f x, float *pp, float *pi, float *thp,
+                                 float *Tp, float *Om) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nw) return;
+    int k = (int)(n / g.nxy);
+    if (k < g.nz) {
+        float dr = st.r[n], dT = st.t[n];
+        float xr = dT * mb.rrt0f[k];                 // dTh / (rho0 theta0)
+        float l1 = log1pf(xr);
+        pp[n] = mb.p0f[k] * expm1f(GAMMAf * l1);
+        pi[n] = mb.pi0f[k] * expf(RDCVf * l1);
+        thp[n] = (dT - mb.th0f[k] * dr) / (mb.rho0f[k] + dr);
+        x.r[n] = sn.r[n] - dr;
+        float xt = sn.t[n] - dT;
+        x.t[n] = xt;
+        Tp[n] = xt;
+        x.u[n] = sn.u[n] - st.u[n];
+        x.v[n] = sn.v[n] - st.v[n];
+    }
+    float xw = sn.w[n] - st.w[n];
+    x.w[n] = xw;
+    Om[n] = (k == 0 || k == g.nz) ? 0.f : xw;
+}
+
+__global__ void k_mx_prep(Geo g, MxBase mb, CF5f st, float *ux, float *vy, float *wz, float *mfx, float *mfy) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nw) return;
+    int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / g.nxy);
+    if (k < g.nz) {
+        float dr = st.r[n], r0 = mb.rho0f[k], dz = mb.dzf[k];
+        float ru = st.u[n], rv = st.v[n];
+        ux[n] = ru / (r0 + 0.5f * (fval(g, st.r, i - 1, j, k) + dr));
+        vy[n] = rv / (r0 + 0.5f * (fval(g, st.r, i, j - 1, k) + dr));
+        mfx[n] = dz * ru;
+        mfy[n] = dz * rv;
+    }
+    float rb;
+    if (k == 0) rb = mb.rho0f[0] + st.r[n];
+    else if (k == g.nz) rb = mb.rho0f[g.nz - 1] + st.r[n - g.nxy];
+    else rb = mb.rhowf[k] + 0.5f * (st.r[n - g.nxy] + st.r[n]);
+    wz[n] = st.w[n] / rb;
+}
+
+// ------------------------------------------------------------------ SGS (FP32)
+struct VelF {
+    const float *ux, *vy, *wz;
+};
+__device__ __forceinline__ float S12f(const Geo &g, const VelF &v, int i, int j, int k) {
+    return 0.5f * ((fval(g, v.ux, i, j, k) - fval(g, v.ux, i, j - 1, k)) * (float)g.rdy
+                 + (fval(g, v.vy, i, j, k) - fval(g, v.vy, i - 1, j, k)) * (float)g.rdx);
+}
+__device__ __forceinline__ float S13f(const Geo &g, const MxBase &mb, const VelF &v, int i, int j, int k) {
+    if (k <= 0 || k >= g.nz) return 0.f;
+    return 0.5f * ((fval(g, v.ux, i, j, k) - fval(g, v.ux, i, j, k - 1)) * mb.rdzcf[k]
+                 + (__ldg(v.wz + cixw(g, i, j, k)) - __ldg(v.wz + cixw(g, i - 1, j, k))) * (float)g.rdx);
+}
+__device__ __forceinline__ float S23f(const Geo &g, const MxBase &mb, const VelF &v, int i, int j, int k) {
+    if (k <= 0 || k >= g.nz) return 0.f;
+    return 0.5f * ((fval(g, v.vy, i, j, k) - fval(g, v.vy, i, j, k - 1)) * mb.rdzcf[k]
+                 + (__ldg(v.wz + cixw(g, i, j, k)) - __ldg(v.wz + cixw(g, i, j - 1, k))) * (float)g.rdy);
+}
+__device__ __forceinline__ void diagSf(const Geo &g, const MxBase &mb, const VelF &v, int i, int j, int k, float &a,
+                                       float &b, float &c) {
+    a = (fval(g, v.ux, i + 1, j, k) - fval(g, v.ux, i, j, k)) * (float)g.rdx;
+    b = (fval(g, v.vy, i, j + 1, k) - fval(g, v.vy, i, j, k)) * (float)g.rdy;
+    c = (__ldg(v.wz + cixw(g, i, j, k + 1)) - __ldg(v.wz + cixw(g, i, j, k))) * mb.rdzf[k];
+}
+__global__ void k_mx_sgs_mu(Geo g, MxBase mb, Phys ph, VelF v, const float *dr, float *mu) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    float rho = mb.rho0f[k] + dr[c];
+    float m = 0.f;
+    if (ph.closure == 2) {
+        float s11, s22, s33;
+        diagSf(g, mb, v, i, j, k, s11, s22, s33);
+        float s12 = 0.25f * (S12f(g, v, i, j, k) + S12f(g, v, i + 1, j, k) + S12f(g, v, i, j + 1, k) + S12f(g, v, i + 1, j + 1, k));
+        float s13 = 0.25f * (S13f(g, mb, v, i, j, k) + S13f(g, mb, v, i + 1, j, k) + S13f(g, mb, v, i, j, k + 1) + S13f(g, mb, v, i + 1, j, k + 1));
+        float s23 = 0.25f * (S23f(g, mb, v, i, j, k) + S23f(g, mb, v, i, j + 1, k) + S23f(g, mb, v, i, j, k + 1) + S23f(g, mb, v, i, j + 1, k + 1));
+        float SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.f * (s12 * s12 + s13 * s13 + s23 * s23);
+        m = rho * mb.delta2f[k] * sqrtf(2.f * SS);
+    } else if (ph.closure == 1) {
+        m = rho * (float)ph.nu;
+    }
+    mu[c] = m;
+}
+__device__ __forceinline__ float tauDf(const Geo &g, const MxBase &mb, const VelF &v, const float *mu, int i, int j,
+                                       int k, int comp) {
+    float a, b, c;
+    diagSf(g, mb, v, i, j, k, a, b, c);
+    float dv = (a + b + c) * (1.f / 3.f);
+    float s = comp == 0 ? a : (comp == 1 ? b : c);
+    return -2.f * fval(g, mu, i, j, k) * (s - dv);
+}
+__device__ __forceinline__ float tau12f(const Geo &g, const VelF &v, const float *mu, int i, int j, int k) {
+    float me = 0.25f * (fval(g, mu, i - 1, j - 1, k) + fval(g, mu, i, j - 1, k) + fval(g, mu, i - 1, j, k) + fval(g, mu, i, j, k));
+    return -2.f * me * S12f(g, v, i, j, k);
+}
+__device__ float ustar_f(float U, float z1, float z0, float Q, float theta, float grav) {
+    float lz = logf(z1 / z0);
+    float us = (float)KAPPA * U / lz;
+    if (Q == 0.f || grav == 0.f) return us;
+    for (int it = 0; it < 5; ++it) {
+        float zeta;
+        if (us <= 0.f) zeta = (Q > 0.f) ? -5.f : 1.f;
+        else zeta = z1 / (-us * us * us * theta / ((float)KAPPA * grav * Q));
+        zeta = fminf(fmaxf(zeta, -5.f), 1.f);
+        float psi;
+        if (zeta < 0.f) {
+            float xx = powf(1.f - 16.f * zeta, 0.25f);
+            psi = 2.f * logf(0.5f * (1.f + xx)) + logf(0.5f * (1.f + xx * xx)) - 2.f * atanf(xx) + 0.5f * (float)M_PI;
+        } else {
+            psi = -5.f * zeta;
+        }
+        us = (float)KAPPA * U / (lz - psi);
+    }
+    return us;
+}
+// tau13 at (x-face i, w-face k); bottom = MOST, top = 0
+__device__ float tau13f(const Geo &g, const MxBase &mb, const Phys &ph, const VelF &v, const float *mu,
+                        const float *dr, const float *thp, int i, int j, int k, int visc) {
+    if (k == 0) {
+        if (ph.surface != 1) return 0.f;
+        float u = fval(g, v.ux, i, j, 0);
+        float vv = 0.25f * (fval(g, v.vy, i - 1, j, 0) + fval(g, v.vy, i, j, 0) + fval(g, v.vy, i - 1, j + 1, 0) + fval(g, v.vy, i, j + 1, 0));
+        float U = sqrtf(u * u + vv * vv);
+        if (!(U > 0.f)) return 0.f;
+        float thf = mb.th0f[0] + 0.5f * (fval(g, thp, i - 1, j, 0) + fval(g, thp, i, j, 0));
+        float rhf = mb.rho0f[0] + 0.5f * (fval(g, dr, i - 1, j, 0) + fval(g, dr, i, j, 0));
+        float us = ustar_f(U, 0.5f * mb.dzf[0], (float)ph.z0, (float)ph.Qs, thf, (float)ph.g);
+        return -rhf * us * us * u / U;
+    }
+    if (k >= g.nz || !visc) return 0.f;
+    float me = 0.25f * (fval(g, mu, i - 1, j, k - 1) + fval(g, mu, i, j, k - 1) + fval(g, mu, i - 1, j, k) + fval(g, mu, i, j, k));
+    return -2.f * me * S13f(g, mb, v, i, j, k);
+}
+__device__ float tau23f(const Geo &g, const MxBase &mb, const Phys &ph, const VelF &v, const float *mu,
+                        const float *dr, const float *thp, int i, int j, int k, int visc) {
+    if (k == 0) {
+        if (ph.surface != 1) return 0.f;
+        float u = 0.25f * (fval(g, v.ux, i, j - 1, 0) + fval(g, v.ux, i + 1, j - 1, 0) + fval(g, v.ux, i, j, 0) + fval(g, v.ux, i + 1, j, 0));
+        float vv = fval(g, v.vy, i, j, 0);
+        float U = sqrtf(u * u + vv * vv);
+        if (!(U > 0.f)) return 0.f;
+        float thf = mb.th0f[0] + 0.5f * (fval(g, thp, i, j - 1, 0) + fval(g, thp, i, j, 0));
+        float rhf = mb.rho0f[0] + 0.5f * (fval(g, dr, i, j - 1, 0) + fval(g, dr, i, j, 0));
+        float us = ustar_f(U, 0.5f * mb.dzf[0], (float)ph.z0, (float)ph.Qs, thf, (float)ph.g);
+        return -rhf * us * us * vv / U;
+    }
+    if (k >= g.nz || !visc) return 0.f;
+    float me = 0.25f * (fval(g, mu, i, j - 1, k - 1) + fval(g, mu, i, j, k - 1) + fval(g, mu, i, j - 1, k) + fval(g, mu, i, j, k));
+    return -2.f * me * S23f(g, mb, v, i, j, k);
+}
+
+// learned closure: cell-centre planes of rho t_ij / rho h_j (order 11 22 33 12 13 23 h1 h2 h3),
+// interpolated to edges (4-point) and faces (2-point) like the Smagorinsky stresses
+__device__ __forceinline__ float tl(const Geo &g, const float *tau, int q, int i, int j, int k) {
+    return __ldg(tau + (long long)q * g.nc + cixw(g, i, j, k));
+}
+__device__ __forceinline__ float tl12e(const Geo &g, const float *tau, int i, int j, int k) {
+    return 0.25f * (tl(g, tau, 3, i - 1, j - 1, k) + tl(g, tau, 3, i, j - 1, k) + tl(g, tau, 3, i - 1, j, k) + tl(g, tau, 3, i, j, k));
+}
+// q = 4 (t13, xz-edge at x-face i) or 5 (t23, yz-edge at y-face j), interior w-face k
+__device__ __forceinline__ float tlze(const Geo &g, const float *tau, int q, int di, int dj, int i, int j, int k) {
+    return 0.25f * (tl(g, tau, q, i - di, j - dj, k - 1) + tl(g, tau, q, i, j, k - 1) + tl(g, tau, q, i - di, j - dj, k) + tl(g, tau, q, i, j, k));
+}
+
+// ------------------------------------------------------------------ slow tendencies (FP32)
+struct PrepF {
+    const float *ux, *vy, *wz, *mfx, *mfy;
+    const float *tau;   // learned-closure stress planes, or null
+};
+
+// continuity and rho*theta.  Face fluxes of theta are split as F theta0_k + F (theta_face -
+// theta0_k); the first sums to theta0_k R_rho.
+__global__ void k_mx_rhs_cells(Geo g, MxBase mb, Phys ph, PrepF pr, const float *rw, const float *thp,
+                               const float *dr, const float *mu, int sgs, float *Rr, float *Rt) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    float rdx = (float)g.rdx, rdy = (float)g.rdy, rH = mb.rdzf[k];
+    float mxm = pr.mfx[c], mxp = __ldg(pr.mfx + cixw(g, i + 1, j, k));
+    float mym = pr.mfy[c], myp = __ldg(pr.mfy + cixw(g, i, j + 1, k));
+    float omm = (k == 0) ? 0.f : __ldg(rw + cix(g, i, j, k));
+    float omp = (k == g.nz - 1) ? 0.f : __ldg(rw + cix(g, i, j, k + 1));
+    // face mass fluxes carry the face height, so the whole divergence is divided by the cell height
+    float Rrho = -((mxp - mxm) * rdx + (myp - mym) * rdy + (omp - omm)) * rH;
+    Rr[c] = Rrho;
+    int zf = ph.scal_adv == 1;
+    float q[6];
+    // horizontal faces: theta0 is constant along the level, so theta_face - theta0_k = theta'_face
+    auto hface = [&](int di, int dj, float mf) -> float {
+        // face between the cells (i+di-1... ) given by its lower-left offset: x-face at i+di or y-face at j+dj
+        float s = sgnT<float>(mf);
+        int iu, ju;   // upwind cell
+        if (dj == -99) { iu = (s >= 0.f) ? i + di - 1 : i + di; ju = j; }
+        else { iu = i; ju = (s >= 0.f) ? j + dj - 1 : j + dj; }
+        float tu = fval(g, thp, iu, ju, k);
+        for (int m = 0; m < 6; ++m) {
+            float t = (dj == -99) ? fval(g, thp, i + di - 3 + m, j, k) : fval(g, thp, i, j + dj - 3 + m, k);
+            q[m] = t - tu;
+        }
+        return mf * (tu + weno5<float>(q, s, zf));
+    };
+    float fxm = hface(0, -99, mxm), fxp = hface(1, -99, mxp);
+    float fym = hface(-99, 0, mym), fyp = hface(-99, 1, myp);
+    // vertical faces k (if > 0) and k+1 (if < nz): theta differences formed from FP64 base
+    // differences plus FP32 perturbation differences, relative to the upwind cell
+    auto vface = [&](int kf, float W) -> float {
+        float s = sgnT<float>(W);
+        int ku = (s >= 0.f) ? kf - 1 : kf;
+        float tu = fval(g, thp, i, j, ku);
+        for (int m = 0; m < 6; ++m) {
+            int km = kf - 3 + m;
+            q[m] = dth0(g, km, ku) + (fval(g, thp, i, j, km) - tu);
+        }
+        float dcell = dth0(g, ku, k);   // theta0_u - theta0_k
+        return W * (dcell + tu + weno5<float>(q, s, zf));
+    };
+    float fzm = (k > 0) ? vface(k, omm) : 0.f;
+    float fzp = (k < g.nz - 1) ? vface(k + 1, omp) : 0.f;
+    float r = mb.th0f[k] * Rrho - ((fxp - fxm) * rdx + (fyp - fym) * rdy + (fzp - fzm)) * rH;
+    if (sgs) {
+        int visc = ph.closure == 1 || ph.closure == 2;
+        float hd = 0.f;
+        float rPr = (float)(1.0 / ph.Pr_t);
+        if (visc) {
+            float tc = thp[c];
+            float hxm = 0.5f * (fval(g, mu, i - 1, j, k) + mu[c]) * rPr * (tc - fval(g, thp, i - 1, j, k)) * rdx;
+            float hxp = 0.5f * (mu[c] + fval(g, mu, i + 1, j, k)) * rPr * (fval(g, thp, i + 1, j, k) - tc) * rdx;
+            float hym = 0.5f * (fval(g, mu, i, j - 1, k) + mu[c]) * rPr * (tc - fval(g, thp, i, j - 1, k)) * rdy;
+            float hyp = 0.5f * (mu[c] + fval(g, mu, i, j + 1, k)) * rPr * (fval(g, thp, i, j + 1, k) - tc) * rdy;
+            hd += (hxp - hxm) * rdx + (hyp - hym) * rdy;
+        }
+        auto hz = [&](int kf) -> float {
+            if (kf == 0) return ph.surface == 1 ? -(mb.rho0f[0] + dr[cix(g, i, j, 0)]) * (float)ph.Qs : 0.f;
+            if (kf >= g.nz || !visc) return 0.f;
+            float dth = dth0(g, kf, kf - 1) + (fval(g, thp, i, j, kf) - fval(g, thp, i, j, kf - 1));
+            return 0.5f * (fval(g, mu, i, j, kf - 1) + fval(g, mu, i, j, kf)) * rPr * dth * mb.rdzcf[kf];
+        };
+        hd += (hz(k + 1) - hz(k)) * rH;
+        r += hd;
+    }
+    if (pr.tau) {   // -div q with q at faces (upward MOST flux rho Q at the surface)
+        const float *t = pr.tau;
+        float qxm = 0.5f * (tl(g, t, 6, i - 1, j, k) + tl(g, t, 6, i, j, k));
+        float qxp = 0.5f * (tl(g, t, 6, i, j, k) + tl(g, t, 6, i + 1, j, k));
+        float qym = 0.5f * (tl(g, t, 7, i, j - 1, k) + tl(g, t, 7, i, j, k));
+        float qyp = 0.5f * (tl(g, t, 7, i, j, k) + tl(g, t, 7, i, j + 1, k));
+        float qzm = k == 0 ? (ph.surface == 1 ? (mb.rho0f[0] + dr[c]) * (float)ph.Qs : 0.f)
+                           : 0.5f * (tl(g, t, 8, i, j, k - 1) + tl(g, t, 8, i, j, k));
+        float qzp = k == g.nz - 1 ? 0.f : 0.5f * (tl(g, t, 8, i, j, k) + tl(g, t, 8, i, j, k + 1));
+        r -= (qxp - qxm) * rdx + (qyp - qym) * rdy + (qzp - qzm) * rH;
+    }
+    Rt[c] = r;
+}
+
+__global__ void k_mx_rhs_u(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const float *pp, const float *thp,
+                           const float *mu, int sgs, float *Ru) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    float rdx = (float)g.rdx, rdy = (float)g.rdy, rH = mb.rdzf[k];
+    float q[6], F[2];
+    for (int s = 0; s < 2; ++s) {
+        int ic = i - 1 + s;
+        float adv = 0.5f * (fval(g, pr.mfx, ic, j, k) + fval(g, pr.mfx, ic + 1, j, k));
+        for (int m = 0; m < 6; ++m) q[m] = fval(g, pr.ux, ic - 2 + m, j, k);
+        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
+    }
+    float div = (F[1] - F[0]) * rdx;
+    for (int s = 0; s < 2; ++s) {
+        int jj = j + s;
+        float adv = 0.5f * (fval(g, pr.mfy, i - 1, jj, k) + fval(g, pr.mfy, i, jj, k));
+        for (int m = 0; m < 6; ++m) q[m] = fval(g, pr.ux, i, jj - 3 + m, k);
+        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
+    }
+    div += (F[1] - F[0]) * rdy;
+    for (int s = 0; s < 2; ++s) {
+        int kk = k + s;
+        F[s] = 0.f;
+        if (kk == 0 || kk == g.nz) continue;
+        float adv = 0.5f * (__ldg(st.w + cixw(g, i - 1, j, kk)) + __ldg(st.w + cixw(g, i, j, kk)));
+        for (int m = 0; m < 6; ++m) q[m] = fval(g, pr.ux, i, j, kk - 3 + m);
+        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
+    }
+    div += F[1] - F[0];
+    float r = -div * rH;
+    r -= (pp[c] - fval(g, pp, i - 1, j, k)) * rdx;
+    if (ph.f_cor != 0.0) {
+        float rvx = 0.25f * (fval(g, st.v, i - 1, j, k) + fval(g, st.v, i, j, k) + fval(g, st.v, i - 1, j + 1, k) + fval(g, st.v, i, j + 1, k));
+        float rhx = mb.rho0f[k] + 0.5f * (fval(g, st.r, i - 1, j, k) + st.r[c]);
+        r += (float)ph.f_cor * (rvx - rhx * (float)ph.v_g);
+    }
+    if (sgs) {
+        int visc = ph.closure == 1 || ph.closure == 2;
+        VelF v{pr.ux, pr.vy, pr.wz};
+        float d = 0.f;
+        if (visc)
+            d += (tauDf(g, mb, v, mu, i, j, k, 0) - tauDf(g, mb, v, mu, i - 1, j, k, 0)) * rdx
+               + (tau12f(g, v, mu, i, j + 1, k) - tau12f(g, v, mu, i, j, k)) * rdy;
+        d += (tau13f(g, mb, ph, v, mu, st.r, thp, i, j, k + 1, visc) - tau13f(g, mb, ph, v, mu, st.r, thp, i, j, k, visc)) * rH;
+        r -= d;
+    }
+    if (pr.tau) {
+        const float *t = pr.tau;
+        VelF v{pr.ux, pr.vy, pr.wz};
+        float t13b = k == 0 ? tau13f(g, mb, ph, v, mu, st.r, thp, i, j, 0, 0) : tlze(g, t, 4, 1, 0, i, j, k);
+        float t13t = k == g.nz - 1 ? 0.f : tlze(g, t, 4, 1, 0, i, j, k + 1);
+        r -= (tl(g, t, 0, i, j, k) - tl(g, t, 0, i - 1, j, k)) * rdx + (tl12e(g, t, i, j + 1, k) - tl12e(g, t, i, j, k)) * rdy
+           + (t13t - t13b) * rH;
+    }
+    Ru[c] = r;
+}
+
+__global__ void k_mx_rhs_v(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const float *pp, const float *thp,
+                           const float *mu, int sgs, float *Rv) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    float rdx = (float)g.rdx, rdy = (float)g.rdy, rH = mb.rdzf[k];
+    float q[6], F[2];
+    for (int s = 0; s < 2; ++s) {
+        int ii = i + s;
+        float adv = 0.5f * (fval(g, pr.mfx, ii, j - 1, k) + fval(g, pr.mfx, ii, j, k));
+        for (int m = 0; m < 6; ++m) q[m] = fval(g, pr.vy, ii - 3 + m, j, k);
+        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
+    }
+    float div = (F[1] - F[0]) * rdx;
+    for (int s = 0; s < 2; ++s) {
+        int jc = j - 1 + s;
+        float adv = 0.5f * (fval(g, pr.mfy, i, jc, k) + fval(g, pr.mfy, i, jc + 1, k));
+        for (int m = 0; m < 6; ++m) q[m] = fval(g, pr.vy, i, jc - 2 + m, k);
+        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
+    }
+    div += (F[1] - F[0]) * rdy;
+    for (int s = 0; s < 2; ++s) {
+        int kk = k + s;
+        F[s] = 0.f;
+        if (kk == 0 || kk == g.nz) continue;
+        float adv = 0.5f * (__ldg(st.w + cixw(g, i, j - 1, kk)) + __ldg(st.w + cixw(g, i, j, kk)));
+        for (int m = 0; m < 6; ++m) q[m] = fval(g, pr.vy, i, j, kk - 3 + m);
+        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
+    }
+    div += F[1] - F[0];
+    float r = -div * rH;
+    r -= (pp[c] - fval(g, pp, i, j - 1, k)) * rdy;
+    if (ph.f_cor != 0.0) {
+        float rux = 0.25f * (fval(g, st.u, i, j - 1, k) + fval(g, st.u, i + 1, j - 1, k) + fval(g, st.u, i, j, k) + fval(g, st.u, i + 1, j, k));
+        float rhy = mb.rho0f[k] + 0.5f * (fval(g, st.r, i, j - 1, k) + st.r[c]);
+        r -= (float)ph.f_cor * (rux - rhy * (float)ph.u_g);
+    }
+    if (sgs) {
+        int visc = ph.closure == 1 || ph.closure == 2;
+        VelF v{pr.ux, pr.vy, pr.wz};
+        float d = 0.f;
+        if (visc)
+            d += (tau12f(g, v, mu, i + 1, j, k) - tau12f(g, v, mu, i, j, k)) * rdx
+               + (tauDf(g, mb, v, mu, i, j, k, 1) - tauDf(g, mb, v, mu, i, j - 1, k, 1)) * rdy;
+        d += (tau23f(g, mb, ph, v, mu, st.r, thp, i, j, k + 1, visc) - tau23f(g, mb, ph, v, mu, st.r, thp, i, j, k, visc)) * rH;
+        r -= d;
+    }
+    if (pr.tau) {
+        const float *t = pr.tau;
+        VelF v{pr.ux, pr.vy, pr.wz};
+        float t23b = k == 0 ? tau23f(g, mb, ph, v, mu, st.r, thp, i, j, 0, 0) : tlze(g, t, 5, 0, 1, i, j, k);
+        float t23t = k == g.nz - 1 ? 0.f : tlze(g, t, 5, 0, 1, i, j, k + 1);
+        r -= (tl12e(g, t, i + 1, j, k) - tl12e(g, t, i, j, k)) * rdx + (tl(g, t, 1, i, j, k) - tl(g, t, 1, i, j - 1, k)) * rdy
+           + (t23t - t23b) * rH;
+    }
+    Rv[c] = r;
+}
+
+__global__ void k_mx_rhs_w(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const float *pp, const float *thp,
+                           const float *mu, int sgs, float *Rw) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nw) return;
+    int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / g.nxy);
+    if (k == 0 || k == g.nz) { Rw[n] = 0.f; return; }
+    float rdx = (float)g.rdx, rdy = (float)g.rdy, rdzc = mb.rdzcf[k];
+    float q[6], F[2];
+    for (int s = 0; s < 2; ++s) {
+        int ii = i + s;
+        float adv = 0.5f * (fval(g, pr.mfx, ii, j, k - 1) + fval(g, pr.mfx, ii, j, k));
+        for (int m = 0; m < 6; ++m) q[m] = __ldg(pr.wz + cixw(g, ii - 3 + m, j, k));
+        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
+    }
+    float div = (F[1] - F[0]) * rdx;
+    for (int s = 0; s < 2; ++s) {
+        int jj = j + s;
+        float adv = 0.5f * (fval(g, pr.mfy, i, jj, k - 1) + fval(g, pr.mfy, i, jj, k));
+        for (int m = 0; m < 6; ++m) q[m] = __ldg(pr.wz + cixw(g, i, jj - 3 + m, k));
+        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
+    }
+    div += (F[1] - F[0]) * rdy;
+    for (int s = 0; s < 2; ++s) {
+        int kc = k - 1 + s;
+        float wa = (kc == 0) ? 0.f : __ldg(st.w + cixw(g, i, j, kc));
+        float wb = (kc + 1 == g.nz) ? 0.f : __ldg(st.w + cixw(g, i, j, kc + 1));
+        float adv = 0.5f * (wa + wb);
+        for (int m = 0; m < 6; ++m) q[m] = wvalf(g, pr.wz, i, j, kc - 2 + m);
+        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
+    }
+    div += F[1] - F[0];
+    float r = -div * rdzc;
+    long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1);
+    r -= (pp[c] - pp[cm]) * rdzc;
+    r += -0.5f * (float)ph.g * (st.r[cm] + st.r[c]);
+    if (sgs && (ph.closure == 1 || ph.closure == 2)) {
+        VelF v{pr.ux, pr.vy, pr.wz};
+        float d = (tau13f(g, mb, ph, v, mu, st.r, thp, i + 1, j, k, 1) - tau13f(g, mb, ph, v, mu, st.r, thp, i, j, k, 1)) * rdx
+                + (tau23f(g, mb, ph, v, mu, st.r, thp, i, j + 1, k, 1) - tau23f(g, mb, ph, v, mu, st.r, thp, i, j, k, 1)) * rdy
+                + (tauDf(g, mb, v, mu, i, j, k, 2) - tauDf(g, mb, v, mu, i, j, k - 1, 2)) * rdzc;
+        r -= d;
+    }
+    if (pr.tau) {
+        const float *t = pr.tau;
+        r -= (tlze(g, t, 4, 1, 0, i + 1, j, k) - tlze(g, t, 4, 1, 0, i, j, k)) * rdx
+           + (tlze(g, t, 5, 0, 1, i, j + 1, k) - tlze(g, t, 5, 0, 1, i, j, k)) * rdy
+           + (tl(g, t, 2, i, j, k) - tl(g, t, 2, i, j, k - 1)) * rdzc;
+    }
+    Rw[n] = r;
+}
+
+// ------------------------------------------------------------------ acoustic substeps
+// stage coefficients and LU factors in FP64 from the FP32 stage fields + FP64 base
+__global__ void k_mx_tri_build(Geo g, MxBase mb, Phys ph, const float *dr, const float *dT, const float *pi,
+                               const float *thp, double dtau, Tri tr) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nxy) return;
+    int i = (int)(n % g.nx), j = (int)(n / g.nx);
+    double b2 = 0.5 * (1.0 + ph.beta_s);
+    double E = dtau * b2 * b2, Gg = dtau * 0.5 * ph.g;
+    double gRd = GAMMA * RD;
+    double cp_prev = 0.0;
+    auto theta = [&](int k) -> double {
+        int kk = kref(k, g.nz);
+        return g.th0[kk] + (double)thp[cix(g, i, j, kk)];
+    };
+    for (int k = 1; k < g.nz; ++k) {
+        long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1);
+        double dz = g.dzc[k];
+        double pic = pi[c], pim = pi[cm];
+        double pib = 0.5 * (pim + pic);
+        double rc = g.rho0[k] + (double)dr[c], rm = g.rho0[k - 1] + (double)dr[cm];
+        double Tc = mb.rt0[k] + (double)dT[c], Tm = mb.rt0[k - 1] + (double)dT[cm];
+        double rhob = 0.5 * (rm + rc);
+        double Cpg = gRd * pib / dz;
+        double Cbp = ph.g * rhob * (RD / CVD) * 0.5 * pic / (Tc * pib);
+        double Cbm = ph.g * rhob * (RD / CVD) * 0.5 * pim / (Tm * pib);
+        double P = dtau * (-Cpg + Cbp), Q = dtau * (Cpg + Cbm);
+        double Hk = g.dzeta[k], Hm = g.dzeta[k - 1];
+        double thw_m = 0.5 * (theta(k - 2) + theta(k - 1));
+        double thw_k = 0.5 * (theta(k - 1) + theta(k));
+        double thw_p = 0.5 * (theta(k) + theta(k + 1));
+        double a = E * (Gg - Q * thw_m) / Hm;
+        double b = 1.0 - P * E * thw_k / Hk + Q * E * thw_k / Hm + Gg * E * (1.0 / Hk - 1.0 / Hm);
+        double cc = E * (P * thw_p - Gg) / Hk;
+        double m = b - a * cp_prev;
+        double im = 1.0 / m;
+        double cpk = cc * im;
+        tr.a[c] = a; tr.cp[c] = cpk; tr.im[c] = im; tr.P[c] = P; tr.Q[c] = Q;
+        cp_prev = cpk;
+    }
+}
+
+__device__ __forceinline__ float ttilf(const Geo &g, const float *Xt, const float *Tp, float bd, int i, int j, int k) {
+    long long a = cixw(g, i, j, k);
+    float x = __ldg(Xt + a);
+    return x + bd * (x - __ldg(Tp + a));
+}
+__global__ void k_mx_sub_horiz(Geo g, Phys ph, const float *pi, const float *Xt, const float *Tp, const float *Ru,
+                               const float *Rv, float *Xu, float *Xv, float dtau) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    float bd = (float)ph.beta_d;
+    float t0 = ttilf(g, Xt, Tp, bd, i, j, k);
+    float gx = (t0 - ttilf(g, Xt, Tp, bd, i - 1, j, k)) * (float)g.rdx;
+    float gy = (t0 - ttilf(g, Xt, Tp, bd, i, j - 1, k)) * (float)g.rdy;
+    const float gRd = (float)(GAMMA * RD);
+    float pic = pi[c];
+    float pix = 0.5f * (fval(g, pi, i - 1, j, k) + pic);
+    float piy = 0.5f * (fval(g, pi, i, j - 1, k) + pic);
+    Xu[c] += dtau * (-gRd * pix * gx + Ru[c]);
+    Xv[c] += dtau * (-gRd * piy * gy + Rv[c]);
+}
+
+// Per column: FP32 explicit parts, FP64 right-hand side, forward/back substitution with the
+// stage LU factors (d' held in the FP64 scratch dbuf), FP64 back substitution of Theta'', rho''.
+__global__ void k_mx_sub_vert(Geo g, MxBase mb, Phys ph, Tri tr, const float *thp, const float *Rr, const float *Rt,
+                              const float *Rw, F5f x, float *Om, float *Tp, double *dbuf, double dtau) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nxy) return;
+    int i = (int)(n % g.nx), j = (int)(n / g.nx);
+    const int nz = g.nz;
+    const float b1f = (float)(0.5 * (1.0 - ph.beta_s));
+    const double b1 = 0.5 * (1.0 - ph.beta_s), b2 = 0.5 * (1.0 + ph.beta_s);
+    const double Gg = dtau * 0.5 * ph.g;
+    const float dtf = (float)dtau, rdx = (float)g.rdx, rdy = (float)g.rdy;
+    // theta at w-face k relative to theta0 of cell kc (small numbers): theta0_k-avg - theta0_kc + theta'-avg
+    auto thw_rel = [&](int kf, int kc) -> float {
+        int ka = kref(kf - 1, nz), kb = kref(kf, nz);
+        float tb0 = 0.5f * (dth0(g, ka, kc) + dth0(g, kb, kc));
+        return tb0 + 0.5f * (thp[cix(g, i, j, ka)] + thp[cix(g, i, j, kb)]);
+    };
+    double X0m = 0.0, Y0m = 0.0, dpm = 0.0;
+    float om_k = 0.f;
+    for (int k = 0; k < nz; ++k) {
+        long long c = cix(g, i, j, k);
+        float om_p = (k + 1 < nz) ? Om[cix(g, i, j, k + 1)] : 0.f;
+        long long cxp = cixw(g, i + 1, j, k), cyp = cixw(g, i, j + 1, k);
+        float Uc = x.u[c], Up = x.u[cxp], Vc = x.v[c], Vp = x.v[cyp];
+        float tc = thp[c];
+        float thxm = 0.5f * (fval(g, thp, i - 1, j, k) + tc), thxp = 0.5f * (tc + fval(g, thp, i + 1, j, k));
+        float thym = 0.5f * (fval(g, thp, i, j - 1, k) + tc), thyp = 0.5f * (tc + fval(g, thp, i, j + 1, k));
+        float dz = mb.dzf[k], rH = mb.rdzf[k];
+        float divM = dz * ((Up - Uc) * rdx + (Vp - Vc) * rdy);
+        // divergence of U'' theta with theta = theta0_k + theta'
+        float divTp = dz * ((Up * thxp - Uc * thxm) * rdx + (Vp * thyp - Vc * thym) * rdy);
+        float th0k = mb.th0f[k];
+        float wk_rel = (k == 0) ? 0.f : thw_rel(k, k), wp_rel = (k + 1 >= nz) ? 0.f : thw_rel(k + 1, k);
+        float vflux_rel = om_p * wp_rel - om_k * wk_rel;       // (Omega theta_w) difference minus theta0_k part
+        float xt = x.t[c], xr = x.r[c];
+        Tp[c] = xt;
+        float vdiv = (om_p - om_k);
+        float Ts = xt + dtf * (-(th0k * divM + divTp) * rH - b1f * (th0k * vdiv + vflux_rel) * rH + Rt[c]);
+        float Rs = xr + dtf * (-divM * rH - b1f * vdiv * rH + Rr[c]);
+        x.t[c] = Ts;
+        x.r[c] = Rs;
+        double X0 = b1 * (double)xt + b2 * (double)Ts, Y0 = b1 * (double)xr + b2 * (double)Rs;
+        if (k >= 1) {
+            double rhs = (double)x.w[c] + dtau * (double)Rw[c] + tr.P[c] * X0 + tr.Q[c] * X0m - Gg * (Y0 + Y0m);
+            double dp = (rhs - tr.a[c] * dpm) * tr.im[c];
+            dbuf[c] = dp;
+            dpm = dp;
+        }
+        X0m = X0; Y0m = Y0;
+        om_k = om_p;
+    }
+    x.w[cix(g, i, j, nz)] = 0.f;
+    Om[cix(g, i, j, nz)] = 0.f;
+    double om_up = 0.0;
+    for (int k = nz - 1; k >= 0; --k) {
+        long long c = cix(g, i, j, k);
+        double om = 0.0;
+        if (k >= 1) om = dbuf[c] - tr.cp[c] * om_up;
+        double thw_k = g.th0[k] + (double)((k == 0) ? 0.f : thw_rel(k, k));
+        double thw_p = g.th0[k] + (double)((k + 1 >= nz) ? thw_rel(nz, k) : thw_rel(k + 1, k));
+        double rH = 1.0 / g.dzeta[k];
+        x.t[c] = (float)((double)x.t[c] - dtau * b2 * (om_up * thw_p - om * thw_k) * rH);
+        x.r[c] = (float)((double)x.r[c] - dtau * b2 * (om_up - om) * rH);
+        x.w[c] = (float)om;
+        Om[c] = (float)om;
+        om_up = om;
+    }
+}
+
+__global__ void k_mx_stage_end(Geo g, F5f st, CF5f x) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nw) return;
+    if (n < g.nc) {
+        st.r[n] += x.r[n];
+        st.t[n] += x.t[n];
+        st.u[n] += x.u[n];
+        st.v[n] += x.v[n];
+    }
+    st.w[n] += x.w[n];
+}
+
+constexpr int MX_DIAG_BLOCKS = 512;
+__global__ void k_mx_diag_partial(Geo g, MxBase mb, CF5f st, double *part) {
+    __shared__ double sm[256], sw[256], smn[256], smx[256], snf[256];
+    int t = threadIdx.x;
+    double mass = 0.0, wmax = 0.0, tmn = 1e300, tmx = -1e300, nf = 0.0;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long n = blockIdx.x * (long long)blockDim.x + t; n < g.nw; n += stride) {
+        int k = (int)(n / g.nxy);
+        if (k < g.nz) {
+            double r = g.rho0[k] + (double)st.r[n];
+            mass += r * g.dzeta[k] * g.dx * g.dy;
+            double th = (mb.rt0[k] + (double)st.t[n]) / r;
+            tmn = fmin(tmn, th); tmx = fmax(tmx, th);
+            if (!isfinite(st.r[n]) || !isfinite(st.t[n]) || !isfinite(st.u[n]) || !isfinite(st.v[n])) nf = 1.0;
+        }
+        float w = st.w[n];
+        if (!isfinite(w)) nf = 1.0;
+        if (k > 0 && k < g.nz) {
+            double rb = 0.5 * (g.rho0[k - 1] + g.rho0[k]) + 0.5 * ((double)st.r[n - g.nxy] + (double)st.r[n]);
+            wmax = fmax(wmax, fabs((double)w / rb));
+        }
+    }
+    sm[t] = mass; sw[t] = wmax; smn[t] = tmn; smx[t] = tmx; snf[t] = nf;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (t < s) {
+            sm[t] += sm[t + s]; sw[t] = fmax(sw[t], sw[t + s]); smn[t] = fmin(smn[t], smn[t + s]);
+            smx[t] = fmax(smx[t], smx[t + s]); snf[t] = fmax(snf[t], snf[t + s]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        double *p = part + 6 * blockIdx.x;
+        p[0] = sm[0]; p[1] = sw[0]; p[2] = smn[0]; p[3] = smx[0]; p[4] = 0.0; p[5] = snf[0];
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+static inline unsigned nb(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+constexpr int MBS = 256;
+
+void mx_build_base(const Geo &g, double Cs, double dx, double dy, float *f32, double *rt0, cudaStream_t s) {
+    k_mx_base<<<nb(g.nz + 1, 128), 128, 0, s>>>(g, Cs, dx, dy, f32, rt0);
+}
+void mx_set_initial(const Geo &g, const double *dth, const double *u, const double *v, const double *w, F5f st,
+                    cudaStream_t s) {
+    k_mx_init_cells<<<nb(g.nc, MBS), MBS, 0, s>>>(g, dth, st.r, st.t);
+    k_mx_init_faces<<<nb(g.nw, MBS), MBS, 0, s>>>(g, u, v, w, st.r, st.u, st.v, st.w);
+}
+void mx_from_full(const Geo &g, const double *src, float *dst, int field, long long n, cudaStream_t s) {
+    k_mx_from_full<<<nb(n, MBS), MBS, 0, s>>>(g, src, dst, field, n);
+}
+void mx_to_full(const Geo &g, const float *src, double *dst, int field, long long n, cudaStream_t s) {
+    k_mx_to_full<<<nb(n, MBS), MBS, 0, s>>>(g, src, dst, field, n);
+}
+void mx_wall_bc(const Geo &g, float *rw, cudaStream_t s) {
+    mx_launch("wall_bc", s, [&] { k_mx_wall_bc<<<nb(g.nxy, MBS), MBS, 0, s>>>(g, rw); });
+}
+void mx_stage_begin(const Geo &g, const MxBase &mb, CF5f sn, CF5f st, F5f x, float *pp, float *pi, float *thp,
+                    float *Tp, float *Om, cudaStream_t s) {
+    mx_launch("mx_stage_begin", s, [&] {
+        k_mx_stage_begin<<<nb(g.nw, MBS), MBS, 0, s>>>(g, mb, sn, st, x, pp, pi, thp, Tp, Om);
+    });
+}
+void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const float *pp, const float *thp,
+                 float *ux, float *vy, float *wz, float *mfx, float *mfy, float *mu, F5f R, cudaStream_t s,
+                 const ClIn *cl) {
+    mx_launch("mx_prep", s, [&] { k_mx_prep<<<nb(g.nw, MBS), MBS, 0, s>>>(g, mb, st, ux, vy, wz, mfx, mfy); });
+    int learned = ph.closure == 3 && cl;
+    int sgs = (ph.closure == 1 || ph.closure == 2 || (ph.surface == 1 && !learned)) ? 1 : 0;
+    if (ph.closure == 1 || ph.closure == 2)
+        mx_launch("mx_sgs_mu", s, [&] { k_mx_sgs_mu<<<nb(g.nc, MBS), MBS, 0, s>>>(g, mb, ph, VelF{ux, vy, wz}, st.r, mu); });
+    const float *tau = nullptr;
+    if (learned) {
+        cl_infer(g, mb, ph, cl->w, cl->b, cl->stats, ux, vy, wz, thp, st.r, cl->out, cl->nfb, s);
+        tau = cl->out;
+    }
+    PrepF pr{ux, vy, wz, mfx, mfy, tau};
+    mx_launch("mx_rhs_cells", s, [&] {
+        k_mx_rhs_cells<<<nb(g.nc, MBS), MBS, 0, s>>>(g, mb, ph, pr, st.w, thp, st.r, mu, sgs, R.r, R.t);
+    });
+    mx_launch("mx_rhs_u", s, [&] { k_mx_rhs_u<<<nb(g.nc, MBS), MBS, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, R.u); });
+    mx_launch("mx_rhs_v", s, [&] { k_mx_rhs_v<<<nb(g.nc, MBS), MBS, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, R.v); });
+    mx_launch("mx_rhs_w", s, [&] { k_mx_rhs_w<<<nb(g.nw, MBS), MBS, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, R.w); });
+}
+void mx_slow_prep_only(const Geo &g, const MxBase &mb, CF5f st, float *ux, float *vy, float *wz, float *mfx,
+                       float *mfy, cudaStream_t s) {
+    k_mx_prep<<<nb(g.nw, MBS), MBS, 0, s>>>(g, mb, st, ux, vy, wz, mfx, mfy);
+}
+void mx_tri_build(const Geo &g, const MxBase &mb, const Phys &ph, const float *dr, const float *dT, const float *pi,
+                  const float *thp, double dtau, Tri tr, cudaStream_t s) {
+    mx_launch("mx_tri_build", s, [&] { k_mx_tri_build<<<nb(g.nxy, 128), 128, 0, s>>>(g, mb, ph, dr, dT, pi, thp, dtau, tr); });
+}
+void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, Tri tr, const float *pi, const float *thp, CF5f R,
+                F5f x, float *Om, float *Tp, double *dbuf, double dtau, cudaStream_t s) {
+    mx_launch("mx_sub_horiz", s, [&] {
+        k_mx_sub_horiz<<<nb(g.nc, MBS), MBS, 0, s>>>(g, ph, pi, x.t, Tp, R.u, R.v, x.u, x.v, (float)dtau);
+    });
+    mx_launch("mx_sub_vert", s, [&] {
+        k_mx_sub_vert<<<nb(g.nxy, 64), 64, 0, s>>>(g, mb, ph, tr, thp, R.r, R.t, R.w, x, Om, Tp, dbuf, dtau);
+    });
+}
+void mx_stage_end(const Geo &g, F5f st, CF5f x, cudaStream_t s) {
+    mx_launch("mx_stage_end", s, [&] { k_mx_stage_end<<<nb(g.nw, MBS), MBS, 0, s>>>(g, st, x); });
+}
+void mx_diag(const Geo &g, const MxBase &mb, CF5f st, double dt, double *part, double *out, cudaStream_t s) {
+    k_mx_diag_partial<<<MX_DIAG_BLOCKS, 256, 0, s>>>(g, mb, st, part);
+    launch_diag_final(part, MX_DIAG_BLOCKS, dt, out, s);
+}
+
+}  // namespace erfk

@@ -1,0 +1,91 @@
+// Mixed-precision (FP32 perturbation) path: data structures and launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "erf_dev.cuh"
+#include "erf_launch.h"
+
+namespace erfk {
+
+// FP32 prognostic perturbation fields: drho, d(rho theta), rho u, rho v, rho w
+struct F5f {
+    float *r, *t, *u, *v, *w;
+};
+struct CF5f {
+    const float *r, *t, *u, *v, *w;
+};
+
+// per-level base-state tables of a flat grid (FP32 copies for the FP32 stencils, FP64 where a
+// value enters a difference or the tridiagonal)
+struct MxBase {
+    const float *rho0f, *th0f, *p0f, *pi0f, *rrt0f;   // [nz]; rrt0f = 1/(rho0 theta0)
+    const float *rhowf;                               // [nz+1] face-averaged rho0
+    const float *dzf, *rdzf, *rdzcf, *delta2f;        // [nz], [nz], [nz+1], [nz]
+    const double *rt0;                                // [nz] rho0 theta0 (FP64)
+};
+
+// profiling hook shared with the FP64 launchers
+ProfSink *current_profiler();
+template <class F>
+inline void mx_launch(const char *name, cudaStream_t s, F &&launch) {
+    ProfSink *p = current_profiler();
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (p) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s);
+    }
+    launch();
+    if (p) {
+        cudaEventRecord(b, s);
+        p->add(name, a, b);
+    }
+}
+
+// learned closure inputs of a slow-tendency pass
+struct ClIn {
+    const void *w;        // BF16 weights (padded layout)
+    const float *b, *stats;
+    float *out;           // 9 planes of nc floats
+    unsigned *nfb;        // fallback counter (may be null)
+};
+void cl_prepare(const float *d_blob, void *w_bf16, float *b, float *stats, cudaStream_t s);
+void cl_infer(const Geo &g, const MxBase &mb, const Phys &ph, const void *w_bf16, const float *b,
+              const float *stats, const float *ux, const float *vy, const float *wz, const float *thp,
+              const float *dr, float *out, unsigned *nfb, cudaStream_t s);
+void cl_features_launch(const Geo &g, const MxBase &mb, double grav, const float *ux, const float *vy,
+                        const float *wz, const float *thp, float *out, cudaStream_t s);
+void cl_filter_launch(const Geo &g, const MxBase &mb, CF5f st, int r, double *cr, double *crt, double *cru,
+                      double *crv, double *crw, float *targets, cudaStream_t s);
+
+void launch_diag_final(const double *part, int nparts, double dt, double *out, cudaStream_t s);
+void mx_build_base(const Geo &g, double Cs, double dx, double dy, float *f32, double *rt0, cudaStream_t s);
+void mx_set_initial(const Geo &g, const double *dth, const double *u, const double *v, const double *w, F5f st,
+                    cudaStream_t s);
+void mx_from_full(const Geo &g, const double *src, float *dst, int field, long long n, cudaStream_t s);
+void mx_to_full(const Geo &g, const float *src, double *dst, int field, long long n, cudaStream_t s);
+void mx_wall_bc(const Geo &g, float *rw, cudaStream_t s);
+void mx_stage_begin(const Geo &g, const MxBase &mb, CF5f sn, CF5f st, F5f x, float *pp, float *pi, float *thp,
+                    float *Tp, float *Om, cudaStream_t s);
+void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const float *pp, const float *thp,
+                 float *ux, float *vy, float *wz, float *mfx, float *mfy, float *mu, F5f R, cudaStream_t s,
+                 const ClIn *cl);
+void mx_slow_prep_only(const Geo &g, const MxBase &mb, CF5f st, float *ux, float *vy, float *wz, float *mfx,
+                       float *mfy, cudaStream_t s);
+void mx_tri_build(const Geo &g, const MxBase &mb, const Phys &ph, const float *dr, const float *dT, const float *pi,
+                  const float *thp, double dtau, Tri tr, cudaStream_t s);
+void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, Tri tr, const float *pi, const float *thp, CF5f R,
+                F5f x, float *Om, float *Tp, double *dbuf, double dtau, cudaStream_t s);
+void mx_stage_end(const Geo &g, F5f st, CF5f x, cudaStream_t s);
+void mx_diag(const Geo &g, const MxBase &mb, CF5f st, double dt, double *part, double *out, cudaStream_t s);
+
+// layout of the FP32 base table block built by mx_build_base (offsets in floats)
+// tables in order: rho0, theta0, p0, pi0, 1/(rho0 theta0), rho0 at w-faces, dz, 1/dz, 1/dzc, delta^2
+inline int mx_base_floats(int nz) { return 10 * (nz + 1); }
+inline MxBase mx_base_view(const float *f32, const double *rt0, int nz) {
+    int L = nz + 1;
+    return MxBase{f32, f32 + L, f32 + 2 * L, f32 + 3 * L, f32 + 4 * L, f32 + 5 * L,
+                  f32 + 6 * L, f32 + 7 * L, f32 + 8 * L, f32 + 9 * L, rt0};
+}
+
+}  // namespace erfk

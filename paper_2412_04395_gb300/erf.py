@@ -24,7 +24,8 @@ ERF_F64, ERF_F32 = 0, 1
 # symbols the library must export (checked by the CPU tests)
 EXPORTS = ["erf_workspace_bytes", "erf_init_grid", "erf_set_initial", "erf_set_state", "erf_rk3_step",
            "erf_get_state", "erf_diagnostics", "erf_profile_steps", "erf_last_error", "erf_destroy",
-           "erf_reduce_state_noalloc"]
+           "erf_reduce_state_noalloc", "erf_train_scratch_bytes", "erf_train_closure", "erf_closure_grad",
+           "erf_column_stats", "erf_standardise"]
 
 
 class ErfError(RuntimeError):
@@ -59,6 +60,11 @@ class Diag(C.Structure):
                 ("steps_done", C.c_int64), ("kernels_per_step", C.c_int32)]
 
 
+class TrainCfg(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float)]
+
+
 class KernelTime(C.Structure):
     _fields_ = [("name", C.c_char * 48), ("total_ms", C.c_double), ("launches", C.c_int32)]
 
@@ -83,11 +89,18 @@ def load_library(path: str = LIB_PATH):
     L.erf_get_state.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_int32]
     L.erf_diagnostics.argtypes = [vp, C.POINTER(Diag)]
     L.erf_profile_steps.argtypes = [vp, C.c_int32, C.POINTER(KernelTime), C.c_int32, C.POINTER(C.c_int32)]
+    L.erf_train_scratch_bytes.argtypes = [C.c_int32]
+    L.erf_train_scratch_bytes.restype = C.c_size_t
+    L.erf_train_closure.argtypes = [C.POINTER(TrainCfg), vp, vp, C.c_int64, vp, vp, vp, C.c_size_t, vp]
+    L.erf_closure_grad.argtypes = [vp, vp, C.c_int32, vp, vp, vp, vp, C.c_size_t, vp]
+    L.erf_column_stats.argtypes = [vp, C.c_int64, C.c_int32, vp, vp, vp]
+    L.erf_standardise.argtypes = [vp, C.c_int64, C.c_int32, vp, vp, vp, vp]
     L.erf_last_error.argtypes = [vp]
     L.erf_last_error.restype = C.c_char_p
     L.erf_destroy.argtypes = [vp]
     for name in ("erf_workspace_bytes", "erf_init_grid", "erf_set_initial", "erf_set_state", "erf_rk3_step",
-                 "erf_get_state", "erf_diagnostics", "erf_profile_steps"):
+                 "erf_get_state", "erf_diagnostics", "erf_profile_steps", "erf_train_closure", "erf_closure_grad",
+                 "erf_column_stats", "erf_standardise"):
         getattr(L, name).restype = C.c_int
     _LIB = L
     return L
@@ -251,3 +264,63 @@ class Dycore:
 
     def state(self):
         return {k: self.erf_get_state(k) for k in ("rho", "rhotheta", "rhou", "rhov", "rhow")}
+
+
+# ---------------------------------------------------------------- learned closure (training)
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def erf_train_scratch_bytes(batch: int) -> int:
+    return load_library().erf_train_scratch_bytes(int(batch))
+
+
+def erf_closure_grad(X, T, params, stream=None):
+    """Loss and gradient of one batch (torch CUDA float32 tensors X [n,12], T [n,9], params [9737])."""
+    import torch
+    L = load_library()
+    n = X.shape[0]
+    grad = torch.empty_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    nb = erf_train_scratch_bytes(n)
+    scratch = torch.empty(nb, dtype=torch.uint8, device=params.device)
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(L, None, L.erf_closure_grad(_ptr(X), _ptr(T), n, _ptr(params), _ptr(grad), _ptr(loss),
+                                       _ptr(scratch), nb, C.c_void_p(st)))
+    return loss, grad
+
+
+def erf_train_closure(X, T, params, epochs, batch, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """Adam training in place on params; returns the per-batch losses (torch CUDA tensor)."""
+    import torch
+    L = load_library()
+    n = X.shape[0]
+    steps = epochs * ((n + batch - 1) // batch)
+    losses = torch.empty(max(steps, 1), dtype=torch.float32, device=params.device)
+    nb = erf_train_scratch_bytes(batch)
+    scratch = torch.empty(nb, dtype=torch.uint8, device=params.device)
+    cfg = TrainCfg(epochs, batch, lr, beta1, beta2, eps)
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(L, None, L.erf_train_closure(C.byref(cfg), _ptr(X), _ptr(T), n, _ptr(params), _ptr(losses),
+                                        _ptr(scratch), nb, C.c_void_p(st)))
+    return losses[:steps]
+
+
+def erf_column_stats(A, stream=None):
+    import torch
+    L = load_library()
+    mean = torch.empty(A.shape[1], dtype=torch.float32, device=A.device)
+    sd = torch.empty_like(mean)
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(L, None, L.erf_column_stats(_ptr(A), A.shape[0], A.shape[1], _ptr(mean), _ptr(sd), C.c_void_p(st)))
+    return mean, sd
+
+
+def erf_standardise(A, mean, sd, stream=None):
+    import torch
+    L = load_library()
+    out = torch.empty_like(A)
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(L, None, L.erf_standardise(_ptr(A), A.shape[0], A.shape[1], _ptr(mean), _ptr(sd), _ptr(out),
+                                      C.c_void_p(st)))
+    return out
