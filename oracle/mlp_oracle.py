@@ -30,12 +30,25 @@ def dsilu(x):
     return s * (1.0 + x * (1.0 - s))
 
 
-def forward(params, X):
-    """params: list of (W [out, in], b [out]); X [n, 12] standardised.  Returns (Y, cache)."""
+def bf16(x):
+    """Round to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(params, X, bf16_inputs=False):
+    """params: list of (W [out, in], b [out]); X [n, 12] standardised.  Returns (Y, cache).
+    bf16_inputs: round every layer's input activations and weights to bfloat16 (as tensor-core
+    inference does; products and sums stay in float64)."""
     a = np.asarray(X, dtype=np.float64)
     cache = [a]
     for l, (W, b) in enumerate(params):
-        z = a @ W.T + b
+        if bf16_inputs:
+            z = bf16(a) @ bf16(W).T + b
+        else:
+            z = a @ W.T + b
         if l < len(params) - 1:
             cache.append(z)
             a = silu(z)
@@ -43,6 +56,30 @@ def forward(params, X):
         else:
             a = z
     return a, cache
+
+
+def pack_blob(params, in_mean, in_std, out_mean, out_std, version=1):
+    """Closure blob: uint32 magic 'ERFM', uint32 version, FP32 stats and parameters."""
+    flat = [np.asarray(in_mean), np.asarray(in_std), np.asarray(out_mean), np.asarray(out_std)]
+    for W, b in params:
+        flat += [np.asarray(W).ravel(), np.asarray(b).ravel()]
+    body = np.concatenate(flat).astype(np.float32)
+    head = np.array([0x4D465245, version], dtype=np.uint32)
+    return head.tobytes() + body.tobytes()
+
+
+def unpack_params(vec):
+    """Parameter list from the flat 9737-vector W1 b1 W2 b2 W3 b3 W4 b4."""
+    out, o = [], 0
+    for a, b in zip(LAYERS[:-1], LAYERS[1:]):
+        W = np.asarray(vec[o:o + a * b], dtype=np.float64).reshape(b, a); o += a * b
+        bb = np.asarray(vec[o:o + b], dtype=np.float64); o += b
+        out.append((W, bb))
+    return out
+
+
+def flatten_params(params):
+    return np.concatenate([np.concatenate([np.ravel(W), np.ravel(b)]) for W, b in params])
 
 
 def backward(params, cache, dY):

@@ -25,7 +25,8 @@ ERF_F64, ERF_F32 = 0, 1
 EXPORTS = ["erf_workspace_bytes", "erf_init_grid", "erf_set_initial", "erf_set_state", "erf_rk3_step",
            "erf_get_state", "erf_diagnostics", "erf_profile_steps", "erf_last_error", "erf_destroy",
            "erf_reduce_state_noalloc", "erf_train_scratch_bytes", "erf_train_closure", "erf_closure_grad",
-           "erf_column_stats", "erf_standardise"]
+           "erf_column_stats", "erf_standardise", "erf_set_closure_weights", "erf_closure_features",
+           "erf_closure_fields", "erf_filter_state"]
 
 
 class ErfError(RuntimeError):
@@ -95,12 +96,17 @@ def load_library(path: str = LIB_PATH):
     L.erf_closure_grad.argtypes = [vp, vp, C.c_int32, vp, vp, vp, vp, C.c_size_t, vp]
     L.erf_column_stats.argtypes = [vp, C.c_int64, C.c_int32, vp, vp, vp]
     L.erf_standardise.argtypes = [vp, C.c_int64, C.c_int32, vp, vp, vp, vp]
+    L.erf_set_closure_weights.argtypes = [vp, C.c_char_p, C.c_size_t]
+    L.erf_closure_features.argtypes = [vp, vp]
+    L.erf_closure_fields.argtypes = [vp, vp, C.POINTER(C.c_uint32)]
+    L.erf_filter_state.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp, vp]
     L.erf_last_error.argtypes = [vp]
     L.erf_last_error.restype = C.c_char_p
     L.erf_destroy.argtypes = [vp]
     for name in ("erf_workspace_bytes", "erf_init_grid", "erf_set_initial", "erf_set_state", "erf_rk3_step",
                  "erf_get_state", "erf_diagnostics", "erf_profile_steps", "erf_train_closure", "erf_closure_grad",
-                 "erf_column_stats", "erf_standardise"):
+                 "erf_column_stats", "erf_standardise", "erf_set_closure_weights", "erf_closure_features",
+                 "erf_closure_fields", "erf_filter_state"):
         getattr(L, name).restype = C.c_int
     _LIB = L
     return L
@@ -264,6 +270,37 @@ class Dycore:
 
     def state(self):
         return {k: self.erf_get_state(k) for k in ("rho", "rhotheta", "rhou", "rhov", "rhow")}
+
+    # -- learned closure
+    def erf_set_closure_weights(self, blob: bytes):
+        _check(self.L, self.h, self.L.erf_set_closure_weights(self.h, blob, len(blob)))
+
+    def erf_closure_features(self):
+        import torch
+        out = torch.empty((self.wl.ncell, 12), dtype=torch.float32, device=self.device)
+        _check(self.L, self.h, self.L.erf_closure_features(self.h, out.data_ptr()))
+        return out
+
+    def erf_closure_fields(self):
+        import torch
+        out = torch.empty((9,) + self.shape_c, dtype=torch.float32, device=self.device)
+        nfb = C.c_uint32()
+        _check(self.L, self.h, self.L.erf_closure_fields(self.h, out.data_ptr(), C.byref(nfb)))
+        return out, nfb.value
+
+    def erf_filter_state(self, r=4):
+        """Coarse FP64 C-grid state (dict of torch tensors) and SGS targets [Nc, 9]."""
+        import torch
+        nz, ny, nx = self.shape_c
+        Nz, Ny, Nx = nz // r, ny // r, nx // r
+        dev = self.device
+        f = {k: torch.empty((Nz, Ny, Nx), dtype=torch.float64, device=dev) for k in ("rho", "rhotheta", "rhou", "rhov")}
+        f["rhow"] = torch.empty((Nz + 1, Ny, Nx), dtype=torch.float64, device=dev)
+        T = torch.empty((Nz * Ny * Nx, 9), dtype=torch.float32, device=dev)
+        _check(self.L, self.h, self.L.erf_filter_state(self.h, r, f["rho"].data_ptr(), f["rhotheta"].data_ptr(),
+                                                       f["rhou"].data_ptr(), f["rhov"].data_ptr(),
+                                                       f["rhow"].data_ptr(), T.data_ptr()))
+        return f, T
 
 
 # ---------------------------------------------------------------- learned closure (training)
