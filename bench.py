@@ -202,6 +202,68 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_steps(d, steps, warmup):
+    """Device time (ms) of `steps` graph-launched steps after `warmup`, CUDA events on the bound stream."""
+    import torch
+    d.erf_rk3_step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(d.stream)
+    d.erf_rk3_step(steps)
+    e1.record(d.stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def closure_blob(wl, d):
+    """The trained closure blob shipped with the package if present, else random weights with
+    statistics from the initial state (throughput only)."""
+    path = os.path.join(ROOT, "paper_2412_04395_gb300", "data", "closure_convective_abl.bin")
+    if os.path.exists(path):
+        return open(path, "rb").read(), "trained"
+    rng = np.random.default_rng(0)
+    feats = d.erf_closure_features().cpu().numpy().astype(np.float64)
+    mu, sd = feats.mean(axis=0), feats.std(axis=0)
+    sd = np.where(sd > 0, sd, 1.0)
+    parts = [mu, sd, np.zeros(9), np.full(9, 0.01)]
+    for a, b in zip((12, 64, 64, 64), (64, 64, 64, 9)):
+        parts += [rng.normal(size=a * b) * np.sqrt(1.0 / a), np.zeros(b)]
+    body = np.concatenate(parts).astype(np.float32)
+    return np.array([0x4D465245, 1], dtype=np.uint32).tobytes() + body.tobytes(), "random"
+
+
+def precision_comparison(args):
+    """Flat convective ABL: FP64 Smagorinsky vs FP32 Smagorinsky vs FP32 + learned closure (BF16
+    tensor-core inference), each timed alone on the same grid."""
+    import torch
+    from paper_2412_04395_gb300 import workloads as W
+    from paper_2412_04395_gb300.erf import Dycore
+    nx, ny, nz = args.cmp_grid
+    base = W.convective_abl(nx=nx, ny=ny, nz=nz, dx=40.0)
+    out = {"workload": f"convective_abl {nx}x{ny}x{nz} at 40 m, ns=10, Smagorinsky/learned, MOST",
+           "steps": args.cmp_steps}
+    for name, wl in (("fp64_smagorinsky", base.with_(precision=W.PREC_FP64)),
+                     ("fp32_smagorinsky", base.with_(precision=W.PREC_MIXED32)),
+                     ("fp32_learned", base.with_(precision=W.PREC_MIXED32, closure=W.CLOSURE_LEARNED))):
+        d = Dycore(wl)
+        d.erf_set_initial(wl.dtheta, wl.u, wl.v, wl.w)
+        if wl.closure == W.CLOSURE_LEARNED:
+            blob, kind = closure_blob(wl, d)
+            d.erf_set_closure_weights(blob)
+            out["learned_weights"] = kind
+        steps = max(2, args.cmp_steps // (4 if wl.precision == W.PREC_FP64 else 1))
+        ms = time_steps(d, steps, 3)
+        prof = d.erf_profile_steps(1)
+        out[name] = {"value": wl.ncell * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                     "kernel_ms_per_step": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]}}
+        d.close()
+        del d
+        torch.cuda.empty_cache()
+    out["fp32_learned_over_fp64"] = out["fp32_learned"]["value"] / out["fp64_smagorinsky"]["value"]
+    out["fp32_over_fp64"] = out["fp32_smagorinsky"]["value"] / out["fp64_smagorinsky"]["value"]
+    return out
+
+
 def run_ours(args):
     import torch
     ws, rank, local, pg = dist_setup(args.gpus)
@@ -277,6 +339,13 @@ def run_ours(args):
         e2e = {"value": ws * wl.ncell * args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
 
+    cmp = None
+    if args.cmp_steps > 0:
+        d.close()
+        del d
+        torch.cuda.empty_cache()
+        cmp = precision_comparison(args)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         import oracle
@@ -297,7 +366,7 @@ def run_ours(args):
                 "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                            "reasons": clocks["reasons"], "samples": clocks["samples"]},
                 "e2e": e2e, "gpu_launches": kps * args.steps, "kernels_per_step": kps,
-                "roofline": roof, "cpu_baseline": cpu,
+                "roofline": roof, "cpu_baseline": cpu, "precision_comparison": cmp,
                 "mass_rel_drift": None if diag["mass"] == 0 else None,
                 "kernel_times_ms": {k: round(v[0] / 2, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
         print(json.dumps(line), flush=True)
@@ -315,6 +384,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--cmp-grid", type=int, nargs=3, default=[512, 512, 160])
+    ap.add_argument("--cmp-steps", type=int, default=8)
     ap.add_argument("--grid", type=int, nargs=3, default=None,
                     help="nx ny nz of a smaller window of the workload (profiling runs only)")
     args = ap.parse_args()

@@ -52,12 +52,12 @@ struct erf_handle {
     std::string err;
     // workspace arrays
     double *hn, *hc, *hxf, *hyf, *gxc, *gyc, *g4x, *g4y;
-    double *dzeta, *zetac, *s, *sc, *ds, *dzc, *delta2, *knz, *knt;
+    double *dzeta, *zetac, *s, *sc, *ds, *dzc, *delta2, *rdzeta, *rdzc, *knz, *knt;
     double *rho0, *th0, *p0;
     F5 st, sn, x, R;
     double *pp, *pi, *th, *Tp, *Om;
     Tri tri;
-    double *ux, *vy, *wz, *mfx, *mfy, *rom, *mu;
+    double *ux, *vy, *wz, *mfx, *mfy, *rom, *mu, *flux;
     double *diag_part, *diag_out;
     // mixed-precision path (flat grids): FP32 perturbation fields + FP64 solve scratch
     bool mixed = false;
@@ -133,6 +133,8 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
     H->dzeta = cv.take<double>(nz); H->zetac = cv.take<double>(nz); H->s = cv.take<double>(nz + 1);
     H->sc = cv.take<double>(nz); H->ds = cv.take<double>(nz); H->dzc = cv.take<double>(nz + 1);
     H->delta2 = cv.take<double>(nz);
+    H->rdzeta = cv.take<double>(nz);
+    H->rdzc = cv.take<double>(nz + 1);
     H->knz = cv.take<double>(c->n_knots > 0 ? c->n_knots : 1);
     H->knt = cv.take<double>(c->n_knots > 0 ? c->n_knots : 1);
     bool terr = false;
@@ -177,6 +179,7 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
     H->ux = cv.take<double>(nc); H->vy = cv.take<double>(nc); H->mfx = cv.take<double>(nc);
     H->mfy = cv.take<double>(nc); H->wz = cv.take<double>(nw); H->rom = cv.take<double>(nw);
     H->mu = cv.take<double>(nc);
+    H->flux = cv.take<double>(2 * nc + nw);
     }
     H->diag_part = cv.take<double>(6 * DIAG_PARTS);
     H->diag_out = cv.take<double>(8);
@@ -200,6 +203,8 @@ static void fill_geo(erf_handle *h) {
     G.dx = g.dx; G.dy = g.dy; G.rdx = 1.0 / g.dx; G.rdy = 1.0 / g.dy;
     G.dzeta = h->dzeta; G.zetac = h->zetac; G.s = h->s; G.sc = h->sc; G.ds = h->ds; G.dzc = h->dzc;
     G.delta2 = h->delta2;
+    G.rdzeta = h->rdzeta;
+    G.rdzc = h->rdzc;
     G.hc = h->hc; G.hxf = h->hxf; G.hyf = h->hyf; G.gxc = h->gxc; G.gyc = h->gyc; G.g4x = h->g4x; G.g4y = h->g4y;
     G.rho0 = h->rho0; G.th0 = h->th0; G.p0 = h->p0;
     const erf_config &c = h->cfg;
@@ -249,6 +254,9 @@ extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config 
         d2[k] = (cfg->Cs * Delta) * (cfg->Cs * Delta);
     }
     for (int k = 1; k < nz; ++k) dzc[k] = zetac[k] - zetac[k - 1];
+    std::vector<double> rdzeta(nz), rdzc(nz + 1, 0.0);
+    for (int k = 0; k < nz; ++k) rdzeta[k] = 1.0 / dzeta[k];
+    for (int k = 1; k < nz; ++k) rdzc[k] = 1.0 / dzc[k];
     cudaStream_t st = h->user;
     cudaError_t e;
 #define CK(call, where)                                   \
@@ -267,6 +275,8 @@ extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config 
     CK(cudaMemcpyAsync(h->ds, ds.data(), nz * sizeof(double), cudaMemcpyHostToDevice, st), "copy ds");
     CK(cudaMemcpyAsync(h->dzc, dzc.data(), (nz + 1) * sizeof(double), cudaMemcpyHostToDevice, st), "copy dzc");
     CK(cudaMemcpyAsync(h->delta2, d2.data(), nz * sizeof(double), cudaMemcpyHostToDevice, st), "copy delta2");
+    CK(cudaMemcpyAsync(h->rdzeta, rdzeta.data(), nz * sizeof(double), cudaMemcpyHostToDevice, st), "copy rdzeta");
+    CK(cudaMemcpyAsync(h->rdzc, rdzc.data(), (nz + 1) * sizeof(double), cudaMemcpyHostToDevice, st), "copy rdzc");
     if (cfg->n_knots > 0) {
         CK(cudaMemcpyAsync(h->knz, cfg->knot_z, cfg->n_knots * sizeof(double), cudaMemcpyHostToDevice, st), "copy knots");
         CK(cudaMemcpyAsync(h->knt, cfg->knot_theta, cfg->n_knots * sizeof(double), cudaMemcpyHostToDevice, st), "copy knots");
@@ -342,7 +352,7 @@ static void enqueue_step(erf_handle *h, cudaStream_t s) {
     for (int stage = 0; stage < 3; ++stage) {
         launch_stage_begin(g, cf(h->sn), cf(h->st), h->x, h->pp, h->pi, h->th, h->Tp, h->Om, s);
         launch_slow_rhs(g, ph, cf(h->st), h->pp, h->th, pr, h->ux, h->vy, h->wz, h->mfx, h->mfy, h->rom, h->mu,
-                        h->R, s);
+                        h->flux, h->R, s);
         if (c.substep_mode == 1) {
             launch_stage_nosub(g, h->st, cf(h->sn), cf(h->R), alpha[stage] * c.dt, s);
             launch_wall_bc(g, h->st.u, h->st.v, h->st.w, s);

@@ -30,6 +30,8 @@ struct Geo {
     const double *ds;      // [nz]   s_{k+1} - s_k
     const double *dzc;     // [nz+1] zetac_k - zetac_{k-1} (k = 1..nz-1)
     const double *delta2;  // [nz]   (Cs * (dx dy dzeta)^(1/3))^2 for Smagorinsky
+    const double *rdzeta;  // [nz]   1 / dzeta
+    const double *rdzc;    // [nz+1] 1 / dzc (k = 1..nz-1)
     // horizontal 2D terrain arrays [ny][nx]
     const double *hc;      // 4-node average of h (cell centre / w-face centre)
     const double *hxf;     // 2-node average of h along y (x-face)
@@ -108,6 +110,13 @@ __device__ __forceinline__ double Hx(const Geo &g, int i, int j, int k) {
 }
 __device__ __forceinline__ double Hy(const Geo &g, int i, int j, int k) {
     return g.terrain ? g.dzeta[k] + g.ds[k] * g.hyf[ij2(g, i, j)] : g.dzeta[k];
+}
+// reciprocal cell height: a table lookup on flat grids, one division over terrain
+__device__ __forceinline__ double rHc(const Geo &g, int i, int j, int k) {
+    return g.terrain ? 1.0 / (g.dzeta[k] + g.ds[k] * g.hc[ij2(g, i, j)]) : g.rdzeta[k];
+}
+__device__ __forceinline__ double rdzcw(const Geo &g, int i, int j, int k) {
+    return g.terrain ? 1.0 / (g.dzc[k] + (g.sc[k] - g.sc[k - 1]) * g.hc[ij2(g, i, j)]) : g.rdzc[k];
 }
 __device__ __forceinline__ double zc(const Geo &g, int i, int j, int k) {
     return g.terrain ? g.zetac[k] + g.sc[k] * g.hc[ij2(g, i, j)] : g.zetac[k];

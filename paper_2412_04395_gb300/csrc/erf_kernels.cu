@@ -342,38 +342,37 @@ __device__ __forceinline__ double heat_z(const Geo &g, const Phys &ph, const dou
 
 // ------------------------------------------------------------------ slow tendencies
 
+// theta fluxes through the left x-face, front y-face and bottom w-face of each cell (each face
+// once): normal mass flux x WENO5(theta); walls carry none
+__global__ void k_flux_theta(Geo g, Phys ph, Prep pr, const double *th, double *fx, double *fy, double *fz) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nw) return;
+    int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / g.nxy);
+    int zf = ph.scal_adv == 1;
+    double q[6];
+    if (k < g.nz) {
+        double mx = pr.mfx[n], my = pr.mfy[n];
+        for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i - 3 + m, j, k);
+        fx[n] = mx * weno5(q, sgnd(mx), zf);
+        for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i, j - 3 + m, k);
+        fy[n] = my * weno5(q, sgnd(my), zf);
+    }
+    if (k == 0 || k == g.nz) { fz[n] = 0.0; return; }
+    double om = pr.rom[n];
+    for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i, j, k - 3 + m);
+    fz[n] = om * weno5(q, sgnd(om), zf);
+}
+
 // continuity and potential temperature (Eq. con, Eq. theta): flux divergence / cell height
-__global__ void k_rhs_cells(Geo g, Phys ph, Prep pr, const double *th, const double *rho, const double *mu,
-                            int sgs, double *Rr, double *Rt) {
+__global__ void k_rhs_cells(Geo g, Phys ph, Prep pr, const double *fx, const double *fy, const double *fz,
+                            const double *th, const double *rho, const double *mu, int sgs, double *Rr, double *Rt) {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= g.nc) return;
     int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
-    double mxm = pr.mfx[c], mxp = __ldg(pr.mfx + cixw(g, i + 1, j, k));
-    double mym = pr.mfy[c], myp = __ldg(pr.mfy + cixw(g, i, j + 1, k));
-    double omm = __ldg(pr.rom + cix(g, i, j, k)), omp = __ldg(pr.rom + cix(g, i, j, k + 1));
-    double H = Hc(g, i, j, k);
-    Rr[c] = -((mxp - mxm) * g.rdx + (myp - mym) * g.rdy + (omp - omm)) / H;
-    int zf = ph.scal_adv == 1;
-    double q[6];
-    // x-faces i and i+1
-    for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i - 3 + m, j, k);
-    double fxm = mxm * weno5(q, sgnd(mxm), zf);
-    for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i - 2 + m, j, k);
-    double fxp = mxp * weno5(q, sgnd(mxp), zf);
-    for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i, j - 3 + m, k);
-    double fym = mym * weno5(q, sgnd(mym), zf);
-    for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i, j - 2 + m, k);
-    double fyp = myp * weno5(q, sgnd(myp), zf);
-    double fzm = 0.0, fzp = 0.0;
-    if (k > 0) {
-        for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i, j, k - 3 + m);
-        fzm = omm * weno5(q, sgnd(omm), zf);
-    }
-    if (k < g.nz - 1) {
-        for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i, j, k - 2 + m);
-        fzp = omp * weno5(q, sgnd(omp), zf);
-    }
-    double r = -((fxp - fxm) * g.rdx + (fyp - fym) * g.rdy + (fzp - fzm)) / H;
+    long long cxp = cixw(g, i + 1, j, k), cyp = cixw(g, i, j + 1, k), ckp = c + g.nxy;
+    double rH = rHc(g, i, j, k);
+    Rr[c] = -((pr.mfx[cxp] - pr.mfx[c]) * g.rdx + (pr.mfy[cyp] - pr.mfy[c]) * g.rdy + (pr.rom[ckp] - pr.rom[c])) * rH;
+    double r = -((fx[cxp] - fx[c]) * g.rdx + (fy[cyp] - fy[c]) * g.rdy + (fz[ckp] - fz[c])) * rH;
     if (sgs) {
         int visc = ph.closure == 1 || ph.closure == 2;
         double hd = 0.0;
@@ -381,7 +380,7 @@ __global__ void k_rhs_cells(Geo g, Phys ph, Prep pr, const double *th, const dou
             hd += (heat_x(g, ph, mu, th, i + 1, j, k) - heat_x(g, ph, mu, th, i, j, k)) * g.rdx
                 + (heat_y(g, ph, mu, th, i, j + 1, k) - heat_y(g, ph, mu, th, i, j, k)) * g.rdy;
         }
-        hd += (heat_z(g, ph, mu, th, rho, i, j, k + 1, visc) - heat_z(g, ph, mu, th, rho, i, j, k, visc)) / H;
+        hd += (heat_z(g, ph, mu, th, rho, i, j, k + 1, visc) - heat_z(g, ph, mu, th, rho, i, j, k, visc)) * rH;
         r += hd;
     }
     Rt[c] = r;
@@ -536,17 +535,17 @@ __global__ void k_rhs_w(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const
         F[s] = adv * upwind5(q, sgnd(adv));
     }
     div += F[1] - F[0];
-    double dz = dzcw(g, i, j, k);
-    double r = -div / dz;
+    double rdz = rdzcw(g, i, j, k);
+    double r = -div * rdz;
     long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1);
-    r -= (pp[c] - pp[cm]) / dz;
+    r -= (pp[c] - pp[cm]) * rdz;
     double b0 = g.rho0[bix(g, i, j, k - 1)], b1 = g.rho0[bix(g, i, j, k)];
     r += 0.5 * (-ph.g * (st.r[cm] - b0) - ph.g * (st.r[c] - b1));
     if (sgs && (ph.closure == 1 || ph.closure == 2)) {
         Vel v{pr.ux, pr.vy, pr.wz};
         double d = (tau13(g, ph, v, mu, st.r, th, i + 1, j, k, 1) - tau13(g, ph, v, mu, st.r, th, i, j, k, 1)) * g.rdx
                  + (tau23(g, ph, v, mu, st.r, th, i, j + 1, k, 1) - tau23(g, ph, v, mu, st.r, th, i, j, k, 1)) * g.rdy
-                 + (tau_diag(g, v, mu, i, j, k, 2) - tau_diag(g, v, mu, i, j, k - 1, 2)) / dz;
+                 + (tau_diag(g, v, mu, i, j, k, 2) - tau_diag(g, v, mu, i, j, k - 1, 2)) * rdz;
         r -= d;
     }
     Rw[n] = r;
@@ -565,28 +564,32 @@ __global__ void k_tri_build(Geo g, Phys ph, const double *rho, const double *rt,
     double E = dtau * b2 * b2, Gg = dtau * 0.5 * ph.g;
     double gRd = GAMMA * RD;
     double cp_prev = 0.0;
+    double rrt_m = 1.0 / rt[cix(g, i, j, 0)], rHm = rHc(g, i, j, 0);
     for (int k = 1; k < g.nz; ++k) {
         long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1), w = c;
-        double dz = dzcw(g, i, j, k);
+        double rdz = rdzcw(g, i, j, k);
         double pic = pi[c], pim = pi[cm];
-        double pib = 0.5 * (pim + pic);
+        double pib = 0.5 * (pim + pic), rpib = 1.0 / pib;
         double rhob = 0.5 * (rho[cm] + rho[c]);
-        double Cpg = gRd * pib / dz;
-        double Cbp = ph.g * rhob * (RD / CVD) * 0.5 * pic / (rt[c] * pib);
-        double Cbm = ph.g * rhob * (RD / CVD) * 0.5 * pim / (rt[cm] * pib);
+        double rrt_c = 1.0 / rt[c], rHk = rHc(g, i, j, k);
+        double Cpg = gRd * pib * rdz;
+        double gb = ph.g * rhob * (RD / CVD) * 0.5 * rpib;
+        double Cbp = gb * pic * rrt_c;
+        double Cbm = gb * pim * rrt_m;
         double P = dtau * (-Cpg + Cbp), Q = dtau * (Cpg + Cbm);
-        double Hk = Hc(g, i, j, k), Hm = Hc(g, i, j, k - 1);
         double thw_m = 0.5 * (cval(g, th, i, j, k - 2) + th[cm]);
         double thw_k = 0.5 * (th[cm] + th[c]);
         double thw_p = 0.5 * (th[c] + cval(g, th, i, j, k + 1));
-        double a = E * (Gg - Q * thw_m) / Hm;
-        double b = 1.0 - P * E * thw_k / Hk + Q * E * thw_k / Hm + Gg * E * (1.0 / Hk - 1.0 / Hm);
-        double cc = E * (P * thw_p - Gg) / Hk;
+        double a = E * (Gg - Q * thw_m) * rHm;
+        double b = 1.0 - P * E * thw_k * rHk + Q * E * thw_k * rHm + Gg * E * (rHk - rHm);
+        double cc = E * (P * thw_p - Gg) * rHk;
         double m = b - a * cp_prev;
         double im = 1.0 / m;
         double cpk = cc * im;
         tr.a[w] = a; tr.cp[w] = cpk; tr.im[w] = im; tr.P[w] = P; tr.Q[w] = Q;
         cp_prev = cpk;
+        rrt_m = rrt_c;
+        rHm = rHk;
     }
 }
 
@@ -650,11 +653,11 @@ __global__ void k_sub_vert(Geo g, Phys ph, Tri tr, const double *th, const doubl
         double thym = 0.5 * (cval(g, th, i, j - 1, k) + th_c), thyp = 0.5 * (th_c + cval(g, th, i, j + 1, k));
         double divM = (Hxp * Up - Hxm * Uc) * g.rdx + (Hyp * Vp - Hym * Vc) * g.rdy;
         double divT = (Hxp * Up * thxp - Hxm * Uc * thxm) * g.rdx + (Hyp * Vp * thyp - Hym * Vc * thym) * g.rdy;
-        double H = Hc(g, i, j, k);
+        double rH = rHc(g, i, j, k);
         double xt = x.t[c], xr = x.r[c];
         Tp[c] = xt;
-        double Ts = xt + dtau * (-divT / H - b1 * (om_p * thw_p - om_k * thw_k) / H + Rt[c]);
-        double Rs = xr + dtau * (-divM / H - b1 * (om_p - om_k) / H + Rr[c]);
+        double Ts = xt + dtau * ((-divT - b1 * (om_p * thw_p - om_k * thw_k)) * rH + Rt[c]);
+        double Rs = xr + dtau * ((-divM - b1 * (om_p - om_k)) * rH + Rr[c]);
         x.t[c] = Ts;   // hold Theta*, rho* until the back substitution
         x.r[c] = Rs;
         double X0 = b1 * xt + b2 * Ts, Y0 = b1 * xr + b2 * Rs;
@@ -690,9 +693,9 @@ __global__ void k_sub_vert(Geo g, Phys ph, Tri tr, const double *th, const doubl
         double thc = th[c];
         double thw_k = 0.5 * (cval(g, th, i, j, k - 1) + thc);
         double thw_p = (k == nz - 1) ? 0.5 * (thc + cval(g, th, i, j, k + 1)) : thw_up;
-        double H = Hc(g, i, j, k);
-        x.t[c] = x.t[c] - dtau * b2 * (om_up * thw_p - om_k2 * thw_k) / H;
-        x.r[c] = x.r[c] - dtau * b2 * (om_up - om_k2) / H;
+        double db = dtau * b2 * rHc(g, i, j, k);
+        x.t[c] = x.t[c] - db * (om_up * thw_p - om_k2 * thw_k);
+        x.r[c] = x.r[c] - db * (om_up - om_k2);
         double A = g.terrain ? metric_shift(g, x.u, x.v, i, j, k) : 0.0;
         x.w[c] = om_k2 + A;
         om_up = om_k2;
@@ -852,12 +855,14 @@ void launch_stage_begin(const Geo &g, CF5 sn, CF5 st, F5 x, double *pp, double *
 }
 void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, const double *pp, const double *th, Prep pr,
                      double *ux, double *vy, double *wz, double *mfx, double *mfy, double *rom, double *mu,
-                     F5 R, cudaStream_t s) {
+                     double *flux, F5 R, cudaStream_t s) {
     LAUNCH("prep", s, k_prep<<<nblk(g.nw, BS), BS, 0, s>>>(g, st, ux, vy, wz, mfx, mfy, rom));
     int sgs = (ph.closure == 1 || ph.closure == 2 || ph.surface == 1) ? 1 : 0;
     if (ph.closure == 1 || ph.closure == 2)
         LAUNCH("sgs_mu", s, k_sgs_mu<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, Vel{ux, vy, wz}, st.r, mu));
-    LAUNCH("rhs_cells", s, k_rhs_cells<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, th, st.r, mu, sgs, R.r, R.t));
+    double *fx = flux, *fy = flux + g.nc, *fz = flux + 2 * g.nc;
+    LAUNCH("flux_theta", s, k_flux_theta<<<nblk(g.nw, BS), BS, 0, s>>>(g, ph, pr, th, fx, fy, fz));
+    LAUNCH("rhs_cells", s, k_rhs_cells<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, fx, fy, fz, th, st.r, mu, sgs, R.r, R.t));
     LAUNCH("rhs_u", s, k_rhs_u<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, sgs, R.u));
     LAUNCH("rhs_v", s, k_rhs_v<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, sgs, R.v));
     LAUNCH("rhs_w", s, k_rhs_w<<<nblk(g.nw, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, sgs, R.w));

@@ -17,7 +17,7 @@ void launch_stage_begin(const Geo &g, CF5 sn, CF5 st, F5 x, double *pp, double *
                         double *Om, cudaStream_t s);
 void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, const double *pp, const double *th, Prep pr,
                      double *ux, double *vy, double *wz, double *mfx, double *mfy, double *rom, double *mu,
-                     F5 R, cudaStream_t s);
+                     double *flux, F5 R, cudaStream_t s);
 void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const double *rt, const double *pi,
                       const double *th, double dtau, Tri tr, cudaStream_t s);
 void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *pi, const double *th, CF5 R, F5 x,
