@@ -57,6 +57,7 @@ struct erf_handle {
     F5 st, sn, x, R;
     double *pp, *pi, *th, *Tp, *Om;
     Tri tri;
+    TriM mtri;
     double *ux, *vy, *wz, *mfx, *mfy, *rom, *mu, *flux;
     double *diag_part, *diag_out;
     // mixed-precision path (flat grids): FP32 perturbation fields + FP64 solve scratch
@@ -156,8 +157,8 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
         H->mbase = cv.take<float>(mx_base_floats((int)nz));
         H->mrt0 = cv.take<double>(nz);
         H->mdbuf = cv.take<double>(nw);
-        H->tri.a = cv.take<double>(nw); H->tri.cp = cv.take<double>(nw); H->tri.im = cv.take<double>(nw);
-        H->tri.P = cv.take<double>(nw); H->tri.Q = cv.take<double>(nw);
+        H->mtri.a = cv.take<double>(nw); H->mtri.cp = cv.take<double>(nw); H->mtri.im = cv.take<double>(nw);
+        H->mtri.P = cv.take<float>(nw); H->mtri.Q = cv.take<float>(nw);
         if (c->closure == 3) {
             H->cl_w = cv.take<unsigned short>(64 * 16 + 64 * 64 * 2 + 16 * 64);
             H->cl_b = cv.take<float>(64 * 3 + 16);
@@ -324,9 +325,9 @@ static void enqueue_step_mixed(erf_handle *h, cudaStream_t s) {
                     h->mR, s, h->cl_ready ? &clin : nullptr);
         int nsub = stage == 0 ? 1 : (stage == 1 ? c.n_substeps / 2 : c.n_substeps);
         double dtau = stage == 0 ? c.dt / 3.0 : c.dt / c.n_substeps;
-        mx_tri_build(g, h->mb, ph, h->mst.r, h->mst.t, h->mpi, h->mthp, dtau, h->tri, s);
+        mx_tri_build(g, h->mb, ph, h->mst.r, h->mst.t, h->mpi, h->mthp, dtau, h->mtri, s);
         for (int n = 0; n < nsub; ++n)
-            mx_substep(g, h->mb, ph, h->tri, h->mpi, h->mthp, cf(h->mR), h->mx, h->mOm, h->mTp, h->mdbuf, dtau, s);
+            mx_substep(g, h->mb, ph, h->mtri, h->mpi, h->mthp, cf(h->mR), h->mx, h->mOm, h->mTp, h->mdbuf, dtau, s);
         mx_stage_end(g, h->mst, cf(h->mx), s);
     }
 }
@@ -463,9 +464,9 @@ extern "C" erf_status erf_set_initial(erf_handle *h, const double *dtheta, const
     const Geo &g = h->geo;
     cudaStream_t s = h->user;
     if (h->mixed) {
-        // FP64 staging in the (not yet used) tridiagonal arrays
+        // FP64 staging in the (not yet used) LU arrays and solve scratch
         const double *src[4] = {dtheta, u, v, w};
-        double *stage[4] = {h->tri.a, h->tri.cp, h->tri.im, h->tri.P};
+        double *stage[4] = {h->mtri.a, h->mtri.cp, h->mtri.im, h->mdbuf};
         long long len[4] = {g.nc, g.nc, g.nc, g.nw};
         const double *dev[4] = {nullptr, nullptr, nullptr, nullptr};
         for (int n = 0; n < 4; ++n) {
@@ -535,15 +536,15 @@ extern "C" erf_status erf_set_state(erf_handle *h, int32_t field, const void *sr
         const double *d64 = nullptr;
         if (src_dtype == ERF_F64 && src_is_device) d64 = (const double *)src;
         else {
-            double *stg = h->tri.a;
+            double *stg = h->mtri.a;
             if (src_dtype == ERF_F64) {
                 e = cudaMemcpyAsync(stg, src, n * sizeof(double), cudaMemcpyHostToDevice, s);
             } else {
                 const void *f = src;
                 e = cudaSuccess;
                 if (!src_is_device) {
-                    e = cudaMemcpyAsync(h->tri.cp, src, n * sizeof(float), cudaMemcpyHostToDevice, s);
-                    f = h->tri.cp;
+                    e = cudaMemcpyAsync(h->mtri.cp, src, n * sizeof(float), cudaMemcpyHostToDevice, s);
+                    f = h->mtri.cp;
                 }
                 if (e == cudaSuccess) launch_convert(f, stg, n, 1, s);
             }
@@ -597,7 +598,7 @@ extern "C" erf_status erf_get_state(erf_handle *h, int32_t field, void *dst, int
         if (e == cudaSuccess && dst_dtype == ERF_F64 && !dst_is_device)
             e = cudaMemcpyAsync(dst, stg, n * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && dst_dtype == ERF_F32) {
-            void *d = dst_is_device ? dst : (void *)h->tri.cp;
+            void *d = dst_is_device ? dst : (void *)h->mtri.cp;
             launch_convert(stg, d, n, 0, s);
             e = cudaGetLastError();
             if (e == cudaSuccess && !dst_is_device) e = cudaMemcpyAsync(dst, d, n * sizeof(float), cudaMemcpyDeviceToHost, s);

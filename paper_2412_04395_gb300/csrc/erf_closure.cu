@@ -3,11 +3,14 @@
 //
 // Inference maps each cell's 12 features (resolved velocity gradients, dtheta/dx, dtheta/dy, N^2)
 // through 12 -> 64 -> 64 -> 64 -> 9 (SiLU) to the kinematic SGS stress and heat flux.  A warp
-// takes 16 cells: the 16 x 16 feature tile (12 + 4 zero columns) and every hidden activation tile
-// live in BF16 mma.sync fragments (m16n8k16, FP32 accumulate); the accumulator fragments of two
-// adjacent n-tiles are exactly the A fragment of the next k-tile, so activations never leave
-// registers between layers.  Weights sit in shared memory in [out][in] row-major BF16, which is
-// the "col" B-fragment order of the instruction.
+// takes 32 cells (one per lane for the features and the store), as two 16-row tiles: the
+// 16 x 16 feature tiles (12 + 4 zero columns) and every hidden activation tile live in BF16
+// mma.sync fragments (m16n8k16, FP32 accumulate); the accumulator fragments of two adjacent
+// n-tiles are exactly the A fragment of the next k-tile, so activations never leave registers
+// between layers, and each B fragment loaded from shared memory feeds both tiles.  Weights sit
+// in shared memory in [out][in] row-major BF16 (the "col" B-fragment order of the instruction),
+// rows padded to 24 / 72 elements so that the eight rows one B load touches fall in distinct
+// banks.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -53,9 +56,7 @@ __global__ void k_cl_prepare(const float *blob, __nv_bfloat16 *w, float *b, floa
 __device__ __forceinline__ float fv(const Geo &g, const float *f, int i, int j, int k) {
     return __ldg(f + cixw(g, i, j, kref(k, g.nz)));
 }
-__device__ __forceinline__ float dth0f(const Geo &g, int ka, int kb) {
-    return (float)(g.th0[kref(ka, g.nz)] - g.th0[kref(kb, g.nz)]);
-}
+__device__ __forceinline__ float dth0f(const MxBase &mb, int ka, int kb) { return mx_dth0(mb, ka, kb); }
 
 // the 12 inputs at cell (i,j,k); also returns dtheta/dz (for the fallback heat flux)
 struct VelIn {
@@ -82,7 +83,7 @@ __device__ void cl_features(const Geo &g, const MxBase &mb, const VelIn &v, doub
     f[8] = (__ldg(v.wz + cixw(g, i, j, k + 1)) - __ldg(v.wz + cixw(g, i, j, k))) * mb.rdzf[k];
     f[9] = (fv(g, v.thp, i + 1, j, k) - fv(g, v.thp, i - 1, j, k)) * 0.5f * rdx;
     f[10] = (fv(g, v.thp, i, j + 1, k) - fv(g, v.thp, i, j - 1, k)) * 0.5f * rdy;
-    dthdz = (dth0f(g, ku, kl) + fv(g, v.thp, i, j, ku) - fv(g, v.thp, i, j, kl)) * rz;
+    dthdz = (dth0f(mb, ku, kl) + fv(g, v.thp, i, j, ku) - fv(g, v.thp, i, j, kl)) * rz;
     f[11] = (float)(grav / g.th0[k]) * dthdz;
 }
 
@@ -97,47 +98,55 @@ __device__ __forceinline__ void mma16816(float *d, const unsigned *a, unsigned b
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
-__device__ __forceinline__ float silu_dev(float x) { return x / (1.f + __expf(-x)); }
+__device__ __forceinline__ float silu_dev(float x) { return __fdividef(x, 1.f + __expf(-x)); }
 
-// Learned SGS stress/heat flux at every cell (mixed path).  Block = 8 warps x 16 cells.
+// Learned SGS stress/heat flux at every cell (mixed path).  Block = 4 warps x 32 cells; each
+// warp runs two m16 tiles through every layer, reusing each B fragment for both.
 // out: 9 planes of nc floats: rho t11, rho t22, rho t33, rho t12, rho t13, rho t23, rho h1..h3.
-constexpr int CLW = 8;
+constexpr int CLW = 4;
+constexpr int LD1 = 24, LDH = 72;   // padded shared-memory row lengths (bank-conflict-free B loads)
+constexpr int SW_W1 = 0, SW_W2 = 64 * LD1, SW_W3 = SW_W2 + 64 * LDH, SW_W4 = SW_W3 + 64 * LDH;
+constexpr int SW_TOTAL = SW_W4 + 16 * LDH;
 __global__ void __launch_bounds__(CLW * 32) k_cl_infer(Geo g, MxBase mb, Phys ph, ClDev cl, VelIn v,
                                                        const float *dr, float *out, unsigned *nfallback) {
-    __shared__ __align__(16) __nv_bfloat16 sW[CL_W_BF16];
+    __shared__ __align__(16) __nv_bfloat16 sW[SW_TOTAL];
     __shared__ float sb[CL_B_F32];
     __shared__ float sst[2 * CL_NIN + 2 * CL_NOUT];
-    __shared__ __align__(16) float sF[CLW][16][17];    // standardised features, then outputs
-    __shared__ float sMisc[CLW][16][12];               // fallback: strain, rho, mu inputs
+    __shared__ __align__(16) float sF[CLW][32][17];   // standardised features, then outputs
+    __shared__ float sMisc[CLW][32][11];              // fallback stresses/fluxes, rho, flag
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int q = tid; q < CL_W_BF16; q += blockDim.x) sW[q] = cl.W1[q];   // W1..W4 are contiguous
+    for (int q = tid; q < 64 * 16; q += blockDim.x) sW[SW_W1 + (q / 16) * LD1 + q % 16] = cl.W1[q];
+    for (int q = tid; q < 64 * 64; q += blockDim.x) {
+        sW[SW_W2 + (q / 64) * LDH + q % 64] = cl.W2[q];
+        sW[SW_W3 + (q / 64) * LDH + q % 64] = cl.W3[q];
+    }
+    for (int q = tid; q < 16 * 64; q += blockDim.x) sW[SW_W4 + (q / 64) * LDH + q % 64] = cl.W4[q];
     for (int q = tid; q < CL_B_F32; q += blockDim.x) sb[q] = cl.b[q];
     for (int q = tid; q < 2 * CL_NIN + 2 * CL_NOUT; q += blockDim.x) sst[q] = cl.stats[q];
     __syncthreads();
-    const __nv_bfloat16 *W1 = sW, *W2 = sW + 1024, *W3 = sW + 1024 + 4096, *W4 = sW + 1024 + 8192;
     const float *in_mu = sst, *in_sd = sst + 12, *out_mu = sst + 24, *out_sd = sst + 33;
-    long long c0 = ((long long)blockIdx.x * CLW + warp) * 16;
-    // 1. features of 16 cells (lanes 0..15), standardised; fallback flag on |z| > 6
-    int fb = 0;
-    if (lane < 16) {
+    const long long c0 = ((long long)blockIdx.x * CLW + warp) * 32;
+    // 1. features of 32 cells (one per lane), standardised; fallback flag on |z| > 6
+    {
         long long c = c0 + lane;
-        float f[12], dthdz = 0.f;
+        float *m = sMisc[warp][lane];
+        int fb = 0;
         if (c < g.nc) {
             int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+            float f[12], dthdz;
             cl_features(g, mb, v, ph.g, i, j, k, f, dthdz);
             for (int q = 0; q < 12; ++q) {
                 float z = (f[q] - in_mu[q]) / in_sd[q];
                 if (!(fabsf(z) <= 6.f)) fb = 1;
                 sF[warp][lane][q] = z;
             }
-            // Smagorinsky fallback inputs at the cell centre
+            // Smagorinsky fallback at the cell centre
             float s11 = f[0], s22 = f[4], s33 = f[8];
             float s12 = 0.5f * (f[1] + f[3]), s13 = 0.5f * (f[2] + f[6]), s23 = 0.5f * (f[5] + f[7]);
             float rho = mb.rho0f[k] + dr[c];
             float SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.f * (s12 * s12 + s13 * s13 + s23 * s23);
             float mu = rho * mb.delta2f[k] * sqrtf(2.f * SS);
             float tr = (s11 + s22 + s33) * (1.f / 3.f);
-            float *m = sMisc[warp][lane];
             m[0] = -2.f * mu * (s11 - tr); m[1] = -2.f * mu * (s22 - tr); m[2] = -2.f * mu * (s33 - tr);
             m[3] = -2.f * mu * s12; m[4] = -2.f * mu * s13; m[5] = -2.f * mu * s23;
             float rPr = (float)(1.0 / ph.Pr_t);
@@ -145,68 +154,74 @@ __global__ void __launch_bounds__(CLW * 32) k_cl_infer(Geo g, MxBase mb, Phys ph
             m[9] = rho;
         } else {
             for (int q = 0; q < 12; ++q) sF[warp][lane][q] = 0.f;
-            sMisc[warp][lane][9] = 0.f;
+            m[9] = 0.f;
         }
         for (int q = 12; q < 16; ++q) sF[warp][lane][q] = 0.f;
-        sMisc[warp][lane][10] = (float)fb;
+        m[10] = (float)fb;
     }
     __syncwarp();
-    // 2. MLP on tensor cores.  Fragment coordinates: g = lane/4 (row), t = lane%4.
+    // 2. MLP on tensor cores.  Fragment coordinates: gr = lane/4 (row), tc = lane%4.
     const int gr = lane >> 2, tc = lane & 3;
-    unsigned a[4][4];   // A fragments of the current activation, per k-tile (up to 4 k-tiles of 16)
-    {
-        const float *r0 = sF[warp][gr], *r1 = sF[warp][gr + 8];
-        a[0][0] = pack_bf16(r0[2 * tc], r0[2 * tc + 1]);
-        a[0][1] = pack_bf16(r1[2 * tc], r1[2 * tc + 1]);
-        a[0][2] = pack_bf16(r0[2 * tc + 8], r0[2 * tc + 9]);
-        a[0][3] = pack_bf16(r1[2 * tc + 8], r1[2 * tc + 9]);
+    unsigned a[2][4][4];   // [m-tile][k-tile][reg]
+    for (int mt = 0; mt < 2; ++mt) {
+        const float *r0 = sF[warp][mt * 16 + gr], *r1 = sF[warp][mt * 16 + gr + 8];
+        a[mt][0][0] = pack_bf16(r0[2 * tc], r0[2 * tc + 1]);
+        a[mt][0][1] = pack_bf16(r1[2 * tc], r1[2 * tc + 1]);
+        a[mt][0][2] = pack_bf16(r0[2 * tc + 8], r0[2 * tc + 9]);
+        a[mt][0][3] = pack_bf16(r1[2 * tc + 8], r1[2 * tc + 9]);
     }
-    float acc[8][4];
-    auto layer = [&](const __nv_bfloat16 *W, int ldw, int nkt, const float *bias) {
+    auto hidden = [&](int woff, int ldw, int nkt, const float *bias) {
+        float acc[2][8][4];
         for (int nt = 0; nt < 8; ++nt) {
-            for (int q = 0; q < 4; ++q) acc[nt][q] = 0.f;
-            const __nv_bfloat16 *wr = W + (nt * 8 + gr) * ldw;   // row n = nt*8 + gr of W (= column of B)
+            for (int mt = 0; mt < 2; ++mt)
+                for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
+            const __nv_bfloat16 *wr = sW + woff + (nt * 8 + gr) * ldw;
             for (int kt = 0; kt < nkt; ++kt) {
                 unsigned b0 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc);
                 unsigned b1 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc + 8);
-                mma16816(acc[nt], a[kt], b0, b1);
+                mma16816(acc[0][nt], a[0][kt], b0, b1);
+                mma16816(acc[1][nt], a[1][kt], b0, b1);
             }
         }
-        // bias + SiLU, repack as A fragments (n-tiles 2kt, 2kt+1 -> k-tile kt)
-        for (int kt = 0; kt < 4; ++kt) {
-            float *lo = acc[2 * kt], *hi = acc[2 * kt + 1];
-            int c_lo = kt * 16 + 2 * tc, c_hi = c_lo + 8;
-            a[kt][0] = pack_bf16(silu_dev(lo[0] + bias[c_lo]), silu_dev(lo[1] + bias[c_lo + 1]));
-            a[kt][1] = pack_bf16(silu_dev(lo[2] + bias[c_lo]), silu_dev(lo[3] + bias[c_lo + 1]));
-            a[kt][2] = pack_bf16(silu_dev(hi[0] + bias[c_hi]), silu_dev(hi[1] + bias[c_hi + 1]));
-            a[kt][3] = pack_bf16(silu_dev(hi[2] + bias[c_hi]), silu_dev(hi[3] + bias[c_hi + 1]));
-        }
+        for (int mt = 0; mt < 2; ++mt)
+            for (int kt = 0; kt < 4; ++kt) {
+                const float *lo = acc[mt][2 * kt], *hi = acc[mt][2 * kt + 1];
+                int c_lo = kt * 16 + 2 * tc, c_hi = c_lo + 8;
+                a[mt][kt][0] = pack_bf16(silu_dev(lo[0] + bias[c_lo]), silu_dev(lo[1] + bias[c_lo + 1]));
+                a[mt][kt][1] = pack_bf16(silu_dev(lo[2] + bias[c_lo]), silu_dev(lo[3] + bias[c_lo + 1]));
+                a[mt][kt][2] = pack_bf16(silu_dev(hi[0] + bias[c_hi]), silu_dev(hi[1] + bias[c_hi + 1]));
+                a[mt][kt][3] = pack_bf16(silu_dev(hi[2] + bias[c_hi]), silu_dev(hi[3] + bias[c_hi + 1]));
+            }
     };
-    layer(W1, 16, 1, sb);
-    layer(W2, 64, 4, sb + 64);
-    layer(W3, 64, 4, sb + 128);
+    hidden(SW_W1, LD1, 1, sb);
+    hidden(SW_W2, LDH, 4, sb + 64);
+    hidden(SW_W3, LDH, 4, sb + 128);
     // output layer: 2 n-tiles of 8 (9 valid columns)
-    float y[2][4];
+    float y[2][2][4];
     for (int nt = 0; nt < 2; ++nt) {
-        for (int q = 0; q < 4; ++q) y[nt][q] = 0.f;
-        const __nv_bfloat16 *wr = W4 + (nt * 8 + gr) * 64;
+        for (int mt = 0; mt < 2; ++mt)
+            for (int q = 0; q < 4; ++q) y[mt][nt][q] = 0.f;
+        const __nv_bfloat16 *wr = sW + SW_W4 + (nt * 8 + gr) * LDH;
         for (int kt = 0; kt < 4; ++kt) {
             unsigned b0 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc);
             unsigned b1 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc + 8);
-            mma16816(y[nt], a[kt], b0, b1);
+            mma16816(y[0][nt], a[0][kt], b0, b1);
+            mma16816(y[1][nt], a[1][kt], b0, b1);
         }
     }
     __syncwarp();
-    for (int nt = 0; nt < 2; ++nt) {
-        int col = nt * 8 + 2 * tc;
-        sF[warp][gr][col] = y[nt][0] + sb[192 + col];
-        sF[warp][gr][col + 1] = y[nt][1] + sb[192 + col + 1];
-        sF[warp][gr + 8][col] = y[nt][2] + sb[192 + col];
-        sF[warp][gr + 8][col + 1] = y[nt][3] + sb[192 + col + 1];
-    }
+    for (int mt = 0; mt < 2; ++mt)
+        for (int nt = 0; nt < 2; ++nt) {
+            int col = nt * 8 + 2 * tc;
+            float *r0 = sF[warp][mt * 16 + gr], *r1 = sF[warp][mt * 16 + gr + 8];
+            r0[col] = y[mt][nt][0] + sb[192 + col];
+            r0[col + 1] = y[mt][nt][1] + sb[192 + col + 1];
+            r1[col] = y[mt][nt][2] + sb[192 + col];
+            r1[col + 1] = y[mt][nt][3] + sb[192 + col + 1];
+        }
     __syncwarp();
-    // 3. de-standardise, fallback, density weighting, store (lanes 0..15, one cell each)
-    if (lane < 16) {
+    // 3. de-standardise, fallback, density weighting, store (one cell per lane, coalesced)
+    {
         long long c = c0 + lane;
         if (c < g.nc) {
             const float *m = sMisc[warp][lane];
@@ -309,7 +324,7 @@ void cl_infer(const Geo &g, const MxBase &mb, const Phys &ph, const void *w_bf16
               const float *dr, float *out, unsigned *nfb, cudaStream_t s) {
     const __nv_bfloat16 *w = (const __nv_bfloat16 *)w_bf16;
     ClDev cl{w, w + 1024, w + 1024 + 4096, w + 1024 + 8192, b, stats};
-    long long nwarps = (g.nc + 15) / 16;
+    long long nwarps = (g.nc + 31) / 32;
     unsigned nblk = (unsigned)((nwarps + CLW - 1) / CLW);
     mx_launch("mx_closure_mlp", s, [&] {
         k_cl_infer<<<nblk, CLW * 32, 0, s>>>(g, mb, ph, cl, VelIn{ux, vy, wz, thp}, dr, out, nfb);

@@ -34,10 +34,8 @@ __device__ __forceinline__ float wvalf(const Geo &g, const float *f, int i, int 
     }
     return add + sgn * __ldg(f + cixw(g, i, j, k));
 }
-// base-state theta difference theta0_a - theta0_b formed in FP64 (levels reflected)
-__device__ __forceinline__ float dth0(const Geo &g, int ka, int kb) {
-    return (float)(g.th0[kref(ka, g.nz)] - g.th0[kref(kb, g.nz)]);
-}
+// base-state theta difference theta0_a - theta0_b (table built in FP64, |ka - kb| <= 3)
+__device__ __forceinline__ float dth0(const MxBase &mb, int ka, int kb) { return mx_dth0(mb, ka, kb); }
 
 // ------------------------------------------------------------------ per-level base tables
 __global__ void k_mx_base(Geo g, double Cs, double dx, double dy, float *f32, double *rt0) {
@@ -57,6 +55,8 @@ __global__ void k_mx_base(Geo g, double Cs, double dx, double dy, float *f32, do
         f32[9 * L + k] = (float)((Cs * Delta) * (Cs * Delta));
         rt0[k] = r0 * t0;
     }
+    if (k < g.nz)
+        for (int o = -3; o <= 3; ++o) f32[10 * L + k * 7 + o + 3] = (float)(g.th0[kref(k + o, g.nz)] - g.th0[k]);
     double rw = (k == 0) ? g.rho0[0] : (k == g.nz ? g.rho0[g.nz - 1] : 0.5 * (g.rho0[k - 1] + g.rho0[k]));
     f32[5 * L + k] = (float)rw;
     f32[8 * L + k] = (k >= 1 && k < g.nz) ? (float)(1.0 / g.dzc[k]) : 0.f;
@@ -323,9 +323,9 @@ __global__ void k_mx_rhs_cells(Geo g, MxBase mb, Phys ph, PrepF pr, const float 
         float tu = fval(g, thp, i, j, ku);
         for (int m = 0; m < 6; ++m) {
             int km = kf - 3 + m;
-            q[m] = dth0(g, km, ku) + (fval(g, thp, i, j, km) - tu);
+            q[m] = dth0(mb, km, ku) + (fval(g, thp, i, j, km) - tu);
         }
-        float dcell = dth0(g, ku, k);   // theta0_u - theta0_k
+        float dcell = dth0(mb, ku, k);   // theta0_u - theta0_k
         return W * (dcell + tu + weno5<float>(q, s, zf));
     };
     float fzm = (k > 0) ? vface(k, omm) : 0.f;
@@ -346,7 +346,7 @@ __global__ void k_mx_rhs_cells(Geo g, MxBase mb, Phys ph, PrepF pr, const float 
         auto hz = [&](int kf) -> float {
             if (kf == 0) return ph.surface == 1 ? -(mb.rho0f[0] + dr[cix(g, i, j, 0)]) * (float)ph.Qs : 0.f;
             if (kf >= g.nz || !visc) return 0.f;
-            float dth = dth0(g, kf, kf - 1) + (fval(g, thp, i, j, kf) - fval(g, thp, i, j, kf - 1));
+            float dth = dth0(mb, kf, kf - 1) + (fval(g, thp, i, j, kf) - fval(g, thp, i, j, kf - 1));
             return 0.5f * (fval(g, mu, i, j, kf - 1) + fval(g, mu, i, j, kf)) * rPr * dth * mb.rdzcf[kf];
         };
         hd += (hz(k + 1) - hz(k)) * rH;
@@ -534,44 +534,46 @@ __global__ void k_mx_rhs_w(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const f
 }
 
 // ------------------------------------------------------------------ acoustic substeps
-// stage coefficients and LU factors in FP64 from the FP32 stage fields + FP64 base
+// Stage coefficients of the vertical system from the FP32 stage fields (their precision), the
+// LU factors (elimination and pivot reciprocals) in FP64.
 __global__ void k_mx_tri_build(Geo g, MxBase mb, Phys ph, const float *dr, const float *dT, const float *pi,
-                               const float *thp, double dtau, Tri tr) {
+                               const float *thp, double dtau, TriM tr) {
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= g.nxy) return;
     int i = (int)(n % g.nx), j = (int)(n / g.nx);
-    double b2 = 0.5 * (1.0 + ph.beta_s);
-    double E = dtau * b2 * b2, Gg = dtau * 0.5 * ph.g;
-    double gRd = GAMMA * RD;
+    const float b2 = (float)(0.5 * (1.0 + ph.beta_s));
+    const float dtf = (float)dtau;
+    const float E = dtf * b2 * b2, Gg = dtf * 0.5f * (float)ph.g;
+    const float gRd = (float)(GAMMA * RD), gRc = (float)(ph.g * (RD / CVD));
     double cp_prev = 0.0;
-    auto theta = [&](int k) -> double {
-        int kk = kref(k, g.nz);
-        return g.th0[kk] + (double)thp[cix(g, i, j, kk)];
+    // theta at the w-faces below/above cell k, relative to theta0_k, plus theta0_k
+    auto thw = [&](int kf) -> float {   // full theta at w-face kf (kf in 0..nz), FP32
+        int ka = kref(kf - 1, g.nz), kb = kref(kf, g.nz);
+        return 0.5f * (mb.th0f[ka] + mb.th0f[kb]) + 0.5f * (thp[cix(g, i, j, ka)] + thp[cix(g, i, j, kb)]);
     };
+    float rrt_m = 1.f / ((float)mb.rt0[0] + dT[cix(g, i, j, 0)]);
+    float thw_m = thw(0), thw_k = thw(1);
     for (int k = 1; k < g.nz; ++k) {
         long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1);
-        double dz = g.dzc[k];
-        double pic = pi[c], pim = pi[cm];
-        double pib = 0.5 * (pim + pic);
-        double rc = g.rho0[k] + (double)dr[c], rm = g.rho0[k - 1] + (double)dr[cm];
-        double Tc = mb.rt0[k] + (double)dT[c], Tm = mb.rt0[k - 1] + (double)dT[cm];
-        double rhob = 0.5 * (rm + rc);
-        double Cpg = gRd * pib / dz;
-        double Cbp = ph.g * rhob * (RD / CVD) * 0.5 * pic / (Tc * pib);
-        double Cbm = ph.g * rhob * (RD / CVD) * 0.5 * pim / (Tm * pib);
-        double P = dtau * (-Cpg + Cbp), Q = dtau * (Cpg + Cbm);
-        double Hk = g.dzeta[k], Hm = g.dzeta[k - 1];
-        double thw_m = 0.5 * (theta(k - 2) + theta(k - 1));
-        double thw_k = 0.5 * (theta(k - 1) + theta(k));
-        double thw_p = 0.5 * (theta(k) + theta(k + 1));
-        double a = E * (Gg - Q * thw_m) / Hm;
-        double b = 1.0 - P * E * thw_k / Hk + Q * E * thw_k / Hm + Gg * E * (1.0 / Hk - 1.0 / Hm);
-        double cc = E * (P * thw_p - Gg) / Hk;
-        double m = b - a * cp_prev;
+        float pic = pi[c], pim = pi[cm];
+        float pib = 0.5f * (pim + pic), rpib = 1.f / pib;
+        float rhob = mb.rhowf[k] + 0.5f * (dr[cm] + dr[c]);
+        float rrt_c = 1.f / ((float)mb.rt0[k] + dT[c]);
+        float Cpg = gRd * pib * mb.rdzcf[k];
+        float gb = gRc * rhob * 0.5f * rpib;
+        float P = dtf * (-Cpg + gb * pic * rrt_c), Q = dtf * (Cpg + gb * pim * rrt_m);
+        float rHk = mb.rdzf[k], rHm = mb.rdzf[k - 1];
+        float thw_p = thw(k + 1);
+        float a = E * (Gg - Q * thw_m) * rHm;
+        float b = 1.f - P * E * thw_k * rHk + Q * E * thw_k * rHm + Gg * E * (rHk - rHm);
+        float cc = E * (P * thw_p - Gg) * rHk;
+        double m = (double)b - (double)a * cp_prev;
         double im = 1.0 / m;
-        double cpk = cc * im;
-        tr.a[c] = a; tr.cp[c] = cpk; tr.im[c] = im; tr.P[c] = P; tr.Q[c] = Q;
+        double cpk = (double)cc * im;
+        tr.a[c] = (double)a; tr.cp[c] = cpk; tr.im[c] = im; tr.P[c] = P; tr.Q[c] = Q;
         cp_prev = cpk;
+        rrt_m = rrt_c;
+        thw_m = thw_k; thw_k = thw_p;
     }
 }
 
@@ -597,29 +599,29 @@ __global__ void k_mx_sub_horiz(Geo g, Phys ph, const float *pi, const float *Xt,
     Xv[c] += dtau * (-gRd * piy * gy + Rv[c]);
 }
 
-// Per column: FP32 explicit parts, FP64 right-hand side, forward/back substitution with the
-// stage LU factors (d' held in the FP64 scratch dbuf), FP64 back substitution of Theta'', rho''.
-__global__ void k_mx_sub_vert(Geo g, MxBase mb, Phys ph, Tri tr, const float *thp, const float *Rr, const float *Rt,
+// Per column: explicit parts, right-hand side and the Theta'', rho'' updates in FP32; the
+// forward elimination and back substitution with the stage LU factors in FP64 (d' held in the
+// FP64 scratch dbuf).
+__global__ void k_mx_sub_vert(Geo g, MxBase mb, Phys ph, TriM tr, const float *thp, const float *Rr, const float *Rt,
                               const float *Rw, F5f x, float *Om, float *Tp, double *dbuf, double dtau) {
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= g.nxy) return;
     int i = (int)(n % g.nx), j = (int)(n / g.nx);
     const int nz = g.nz;
-    const float b1f = (float)(0.5 * (1.0 - ph.beta_s));
-    const double b1 = 0.5 * (1.0 - ph.beta_s), b2 = 0.5 * (1.0 + ph.beta_s);
-    const double Gg = dtau * 0.5 * ph.g;
-    const float dtf = (float)dtau, rdx = (float)g.rdx, rdy = (float)g.rdy;
-    // theta at w-face k relative to theta0 of cell kc (small numbers): theta0_k-avg - theta0_kc + theta'-avg
+    const float b1 = (float)(0.5 * (1.0 - ph.beta_s)), b2 = (float)(0.5 * (1.0 + ph.beta_s));
+    const float dtf = (float)dtau, Gg = (float)(dtau * 0.5 * ph.g);
+    const float rdx = (float)g.rdx, rdy = (float)g.rdy;
+    // theta at w-face kf relative to theta0 of cell kc (small numbers)
     auto thw_rel = [&](int kf, int kc) -> float {
         int ka = kref(kf - 1, nz), kb = kref(kf, nz);
-        float tb0 = 0.5f * (dth0(g, ka, kc) + dth0(g, kb, kc));
-        return tb0 + 0.5f * (thp[cix(g, i, j, ka)] + thp[cix(g, i, j, kb)]);
+        return 0.5f * (dth0(mb, ka, kc) + dth0(mb, kb, kc)) + 0.5f * (thp[cix(g, i, j, ka)] + thp[cix(g, i, j, kb)]);
     };
-    double X0m = 0.0, Y0m = 0.0, dpm = 0.0;
+    float X0m = 0.f, Y0m = 0.f;
+    double dpm = 0.0;
     float om_k = 0.f;
     for (int k = 0; k < nz; ++k) {
         long long c = cix(g, i, j, k);
-        float om_p = (k + 1 < nz) ? Om[cix(g, i, j, k + 1)] : 0.f;
+        float om_p = (k + 1 < nz) ? Om[c + g.nxy] : 0.f;
         long long cxp = cixw(g, i + 1, j, k), cyp = cixw(g, i, j + 1, k);
         float Uc = x.u[c], Up = x.u[cxp], Vc = x.v[c], Vp = x.v[cyp];
         float tc = thp[c];
@@ -627,22 +629,21 @@ __global__ void k_mx_sub_vert(Geo g, MxBase mb, Phys ph, Tri tr, const float *th
         float thym = 0.5f * (fval(g, thp, i, j - 1, k) + tc), thyp = 0.5f * (tc + fval(g, thp, i, j + 1, k));
         float dz = mb.dzf[k], rH = mb.rdzf[k];
         float divM = dz * ((Up - Uc) * rdx + (Vp - Vc) * rdy);
-        // divergence of U'' theta with theta = theta0_k + theta'
         float divTp = dz * ((Up * thxp - Uc * thxm) * rdx + (Vp * thyp - Vc * thym) * rdy);
         float th0k = mb.th0f[k];
         float wk_rel = (k == 0) ? 0.f : thw_rel(k, k), wp_rel = (k + 1 >= nz) ? 0.f : thw_rel(k + 1, k);
-        float vflux_rel = om_p * wp_rel - om_k * wk_rel;       // (Omega theta_w) difference minus theta0_k part
+        float vflux_rel = om_p * wp_rel - om_k * wk_rel;
         float xt = x.t[c], xr = x.r[c];
         Tp[c] = xt;
-        float vdiv = (om_p - om_k);
-        float Ts = xt + dtf * (-(th0k * divM + divTp) * rH - b1f * (th0k * vdiv + vflux_rel) * rH + Rt[c]);
-        float Rs = xr + dtf * (-divM * rH - b1f * vdiv * rH + Rr[c]);
+        float vdiv = om_p - om_k;
+        float Ts = xt + dtf * (-(th0k * divM + divTp) * rH - b1 * (th0k * vdiv + vflux_rel) * rH + Rt[c]);
+        float Rs = xr + dtf * (-divM * rH - b1 * vdiv * rH + Rr[c]);
         x.t[c] = Ts;
         x.r[c] = Rs;
-        double X0 = b1 * (double)xt + b2 * (double)Ts, Y0 = b1 * (double)xr + b2 * (double)Rs;
+        float X0 = b1 * xt + b2 * Ts, Y0 = b1 * xr + b2 * Rs;
         if (k >= 1) {
-            double rhs = (double)x.w[c] + dtau * (double)Rw[c] + tr.P[c] * X0 + tr.Q[c] * X0m - Gg * (Y0 + Y0m);
-            double dp = (rhs - tr.a[c] * dpm) * tr.im[c];
+            float rhs = x.w[c] + dtf * Rw[c] + tr.P[c] * X0 + tr.Q[c] * X0m - Gg * (Y0 + Y0m);
+            double dp = ((double)rhs - tr.a[c] * dpm) * tr.im[c];
             dbuf[c] = dp;
             dpm = dp;
         }
@@ -652,18 +653,22 @@ __global__ void k_mx_sub_vert(Geo g, MxBase mb, Phys ph, Tri tr, const float *th
     x.w[cix(g, i, j, nz)] = 0.f;
     Om[cix(g, i, j, nz)] = 0.f;
     double om_up = 0.0;
+    float omf_up = 0.f;
     for (int k = nz - 1; k >= 0; --k) {
         long long c = cix(g, i, j, k);
         double om = 0.0;
         if (k >= 1) om = dbuf[c] - tr.cp[c] * om_up;
-        double thw_k = g.th0[k] + (double)((k == 0) ? 0.f : thw_rel(k, k));
-        double thw_p = g.th0[k] + (double)((k + 1 >= nz) ? thw_rel(nz, k) : thw_rel(k + 1, k));
-        double rH = 1.0 / g.dzeta[k];
-        x.t[c] = (float)((double)x.t[c] - dtau * b2 * (om_up * thw_p - om * thw_k) * rH);
-        x.r[c] = (float)((double)x.r[c] - dtau * b2 * (om_up - om) * rH);
-        x.w[c] = (float)om;
-        Om[c] = (float)om;
+        float omf = (float)om;
+        float th0k = mb.th0f[k];
+        float wk_rel = (k == 0) ? 0.f : thw_rel(k, k);
+        float wp_rel = (k + 1 >= nz) ? thw_rel(nz, k) : thw_rel(k + 1, k);
+        float db = dtf * b2 * mb.rdzf[k];
+        x.t[c] -= db * (th0k * (omf_up - omf) + (omf_up * wp_rel - omf * wk_rel));
+        x.r[c] -= db * (omf_up - omf);
+        x.w[c] = omf;
+        Om[c] = omf;
         om_up = om;
+        omf_up = omf;
     }
 }
 
@@ -769,10 +774,10 @@ void mx_slow_prep_only(const Geo &g, const MxBase &mb, CF5f st, float *ux, float
     k_mx_prep<<<nb(g.nw, MBS), MBS, 0, s>>>(g, mb, st, ux, vy, wz, mfx, mfy);
 }
 void mx_tri_build(const Geo &g, const MxBase &mb, const Phys &ph, const float *dr, const float *dT, const float *pi,
-                  const float *thp, double dtau, Tri tr, cudaStream_t s) {
+                  const float *thp, double dtau, TriM tr, cudaStream_t s) {
     mx_launch("mx_tri_build", s, [&] { k_mx_tri_build<<<nb(g.nxy, 128), 128, 0, s>>>(g, mb, ph, dr, dT, pi, thp, dtau, tr); });
 }
-void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, Tri tr, const float *pi, const float *thp, CF5f R,
+void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, TriM tr, const float *pi, const float *thp, CF5f R,
                 F5f x, float *Om, float *Tp, double *dbuf, double dtau, cudaStream_t s) {
     mx_launch("mx_sub_horiz", s, [&] {
         k_mx_sub_horiz<<<nb(g.nc, MBS), MBS, 0, s>>>(g, ph, pi, x.t, Tp, R.u, R.v, x.u, x.v, (float)dtau);

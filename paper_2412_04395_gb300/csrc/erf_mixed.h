@@ -22,6 +22,15 @@ struct MxBase {
     const float *rhowf;                               // [nz+1] face-averaged rho0
     const float *dzf, *rdzf, *rdzcf, *delta2f;        // [nz], [nz], [nz+1], [nz]
     const double *rt0;                                // [nz] rho0 theta0 (FP64)
+    const float *dth0t;                               // [nz][7]: theta0(k+o) - theta0(k), o = -3..3, formed in FP64
+};
+// theta0(ka) - theta0(kb) for |ka - kb| <= 3 (ka reflected at the walls)
+__device__ __forceinline__ float mx_dth0(const MxBase &mb, int ka, int kb) { return mb.dth0t[kb * 7 + (ka - kb) + 3]; }
+
+// stage LU factors of the vertical system in FP64 and its right-hand-side coefficients in FP32
+struct TriM {
+    double *a, *cp, *im;
+    float *P, *Q;
 };
 
 // profiling hook shared with the FP64 launchers
@@ -73,19 +82,19 @@ void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const 
 void mx_slow_prep_only(const Geo &g, const MxBase &mb, CF5f st, float *ux, float *vy, float *wz, float *mfx,
                        float *mfy, cudaStream_t s);
 void mx_tri_build(const Geo &g, const MxBase &mb, const Phys &ph, const float *dr, const float *dT, const float *pi,
-                  const float *thp, double dtau, Tri tr, cudaStream_t s);
-void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, Tri tr, const float *pi, const float *thp, CF5f R,
+                  const float *thp, double dtau, TriM tr, cudaStream_t s);
+void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, TriM tr, const float *pi, const float *thp, CF5f R,
                 F5f x, float *Om, float *Tp, double *dbuf, double dtau, cudaStream_t s);
 void mx_stage_end(const Geo &g, F5f st, CF5f x, cudaStream_t s);
 void mx_diag(const Geo &g, const MxBase &mb, CF5f st, double dt, double *part, double *out, cudaStream_t s);
 
 // layout of the FP32 base table block built by mx_build_base (offsets in floats)
 // tables in order: rho0, theta0, p0, pi0, 1/(rho0 theta0), rho0 at w-faces, dz, 1/dz, 1/dzc, delta^2
-inline int mx_base_floats(int nz) { return 10 * (nz + 1); }
+inline int mx_base_floats(int nz) { return 10 * (nz + 1) + 7 * nz; }
 inline MxBase mx_base_view(const float *f32, const double *rt0, int nz) {
     int L = nz + 1;
     return MxBase{f32, f32 + L, f32 + 2 * L, f32 + 3 * L, f32 + 4 * L, f32 + 5 * L,
-                  f32 + 6 * L, f32 + 7 * L, f32 + 8 * L, f32 + 9 * L, rt0};
+                  f32 + 6 * L, f32 + 7 * L, f32 + 8 * L, f32 + 9 * L, rt0, f32 + 10 * L};
 }
 
 }  // namespace erfk
