@@ -54,6 +54,7 @@ struct erf_handle {
     double *hn, *hc, *hxf, *hyf, *gxc, *gyc, *g4x, *g4y;
     double *dzeta, *zetac, *s, *sc, *ds, *dzc, *delta2, *rdzeta, *rdzc, *knz, *knt;
     double *rho0, *th0, *p0;
+    double *rH3 = nullptr, *rHx3 = nullptr, *rHy3 = nullptr, *rdzw3 = nullptr, *rdz2 = nullptr;
     F5 st, sn, x, R;
     double *pp, *pi, *th, *Tp, *Om;
     Tri tri;
@@ -181,6 +182,10 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
     H->mfy = cv.take<double>(nc); H->wz = cv.take<double>(nw); H->rom = cv.take<double>(nw);
     H->mu = cv.take<double>(nc);
     H->flux = cv.take<double>(2 * nc + nw);
+    if (terr) {
+        H->rH3 = cv.take<double>(nc); H->rHx3 = cv.take<double>(nc); H->rHy3 = cv.take<double>(nc);
+        H->rdzw3 = cv.take<double>(nc); H->rdz2 = cv.take<double>(nc);
+    }
     }
     H->diag_part = cv.take<double>(6 * DIAG_PARTS);
     H->diag_out = cv.take<double>(8);
@@ -208,10 +213,12 @@ static void fill_geo(erf_handle *h) {
     G.rdzc = h->rdzc;
     G.hc = h->hc; G.hxf = h->hxf; G.hyf = h->hyf; G.gxc = h->gxc; G.gyc = h->gyc; G.g4x = h->g4x; G.g4y = h->g4y;
     G.rho0 = h->rho0; G.th0 = h->th0; G.p0 = h->p0;
+    G.rH3 = h->rH3; G.rHx3 = h->rHx3; G.rHy3 = h->rHy3; G.rdzw3 = h->rdzw3; G.rdz2 = h->rdz2;
     const erf_config &c = h->cfg;
     Phys &P = h->ph;
     P.g = c.gravity; P.f_cor = c.f_cor; P.u_g = c.u_g; P.v_g = c.v_g; P.Cs = c.Cs; P.Pr_t = c.Pr_t; P.nu = c.nu;
     P.z0 = c.z0; P.Qs = c.sfc_theta_flux; P.beta_s = c.beta_s; P.beta_d = c.beta_d;
+    P.rPr_t = 1.0 / c.Pr_t;
     P.closure = c.closure; P.surface = c.surface; P.scal_adv = c.scal_adv;
 }
 
@@ -289,6 +296,8 @@ extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config 
         CK(cudaMemsetAsync(h->hn, 0, nxy * sizeof(double), st), "zero terrain");
     }
     launch_terrain(h->geo, h->hn, h->hc, h->hxf, h->hyf, h->gxc, h->gyc, h->g4x, h->g4y, st);
+    if (h->geo.terrain && h->rH3)
+        launch_terrain_recip(h->geo, h->rH3, h->rHx3, h->rHy3, h->rdzw3, h->rdz2, st);
     launch_base_state(h->geo, cfg->n_knots, h->knz, h->knt, cfg->theta_s, cfg->brunt_N, cfg->p_s, cfg->gravity,
                       h->rho0, h->th0, h->p0, st);
     if (h->mixed) {

@@ -33,7 +33,6 @@ struct ClDev {
     const float *b;            // b1[64] b2[64] b3[64] b4[16]
     const float *stats;        // in_mean[12] in_std[12] out_mean[9] out_std[9]
 };
-constexpr int CL_W_BF16 = 64 * 16 + 64 * 64 * 2 + 16 * 64;   // 10240
 constexpr int CL_B_F32 = 64 * 3 + 16;
 
 __global__ void k_cl_prepare(const float *blob, __nv_bfloat16 *w, float *b, float *stats) {

@@ -42,10 +42,15 @@ struct Geo {
     const double *g4y;
     // hydrostatic base state: [nz][ny][nx] with terrain, [nz] when flat
     const double *rho0, *th0, *p0;
+    // reciprocal 3D metrics, terrain only ([nz][ny][nx]; null on flat grids): 1/H at cells,
+    // x-faces and y-faces, 1/(z_c(k) - z_c(k-1)) at w-faces (k >= 1), and 1/(z_c(ku) - z_c(kl))
+    // of the centred vertical difference at cells (kl = max(k-1, 0), ku = min(k+1, nz-1)).
+    // An FP64 division costs ~10 FP64-pipe instructions, so each is taken once at init.
+    const double *rH3, *rHx3, *rHy3, *rdzw3, *rdz2;
 };
 
 struct Phys {
-    double g, f_cor, u_g, v_g, Cs, Pr_t, nu, z0, Qs, beta_s, beta_d;
+    double g, f_cor, u_g, v_g, Cs, Pr_t, nu, z0, Qs, beta_s, beta_d, rPr_t;
     int closure, surface, scal_adv;
 };
 
@@ -111,12 +116,22 @@ __device__ __forceinline__ double Hx(const Geo &g, int i, int j, int k) {
 __device__ __forceinline__ double Hy(const Geo &g, int i, int j, int k) {
     return g.terrain ? g.dzeta[k] + g.ds[k] * g.hyf[ij2(g, i, j)] : g.dzeta[k];
 }
-// reciprocal cell height: a table lookup on flat grids, one division over terrain
+// reciprocal heights: 1D tables on flat grids, 3D tables over terrain
 __device__ __forceinline__ double rHc(const Geo &g, int i, int j, int k) {
-    return g.terrain ? 1.0 / (g.dzeta[k] + g.ds[k] * g.hc[ij2(g, i, j)]) : g.rdzeta[k];
+    return g.terrain ? __ldg(g.rH3 + cixw(g, i, j, k)) : g.rdzeta[k];
+}
+__device__ __forceinline__ double rHxf(const Geo &g, int i, int j, int k) {
+    return g.terrain ? __ldg(g.rHx3 + cixw(g, i, j, k)) : g.rdzeta[k];
+}
+__device__ __forceinline__ double rHyf(const Geo &g, int i, int j, int k) {
+    return g.terrain ? __ldg(g.rHy3 + cixw(g, i, j, k)) : g.rdzeta[k];
 }
 __device__ __forceinline__ double rdzcw(const Geo &g, int i, int j, int k) {
-    return g.terrain ? 1.0 / (g.dzc[k] + (g.sc[k] - g.sc[k - 1]) * g.hc[ij2(g, i, j)]) : g.rdzc[k];
+    return g.terrain ? __ldg(g.rdzw3 + cixw(g, i, j, k)) : g.rdzc[k];
+}
+// terrain only: 1 / (z_c(ku) - z_c(kl)) of the centred vertical difference at cell (i,j,k)
+__device__ __forceinline__ double rdz2c(const Geo &g, int i, int j, int k) {
+    return __ldg(g.rdz2 + cixw(g, i, j, k));
 }
 __device__ __forceinline__ double zc(const Geo &g, int i, int j, int k) {
     return g.terrain ? g.zetac[k] + g.sc[k] * g.hc[ij2(g, i, j)] : g.zetac[k];

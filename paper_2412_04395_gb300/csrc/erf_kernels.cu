@@ -24,7 +24,23 @@ __device__ __forceinline__ double sgnd(double x) { return sgnT<double>(x); }
 // own (__dmul_rn) so that a later p - p0 cannot be contracted into an FMA: the base state is
 // subtracted exactly and an undisturbed column keeps p' = 0 bit for bit.
 __device__ __forceinline__ void eos_pi(double rt, double &p, double &pi) {
-    pi = pow(RD * rt * (1.0 / P00), RD / CVD);
+    // pi = x^(R_d/c_v) with x = R_d rho theta / P00 and R_d/c_v = 2/5, so pi = x z with
+    // z = a^(-1/5), a = x^3.  z starts from an FP32 estimate and takes two Newton steps of the
+    // reciprocal n-th root, z <- z + z (1 - a z^n)/n (no division; the relative error e
+    // becomes ~(n+1)/2 e^2 per step: 1e-6 -> 3e-12 -> rounding), so the FP64 cost is 17
+    // multiply/FMA instead of a general pow.
+    static_assert(RD / CVD == 0.4, "the Newton form of the EOS assumes R_d/c_v = 2/5");
+    double x = RD * rt * (1.0 / P00);
+    double a = x * x * x;
+    double z = (double)exp2f(-0.6f * log2f((float)x));
+    #pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        double z2 = z * z;
+        double z5 = z2 * z2 * z;
+        double r = fma(-a, z5, 1.0);
+        z = fma(z * 0.2, r, z);
+    }
+    pi = x * z;
     p = __dmul_rn(RD * rt, pi);
 }
 
@@ -47,6 +63,20 @@ __global__ void k_terrain_grad(Geo g, const double *hc, double *gxc, double *gyc
     gyc[n] = (hc[n] - hc[ij2(g, i, j - 1)]) * g.rdy;
     g4x[n] = (hc[ij2(g, i - 2, j)] - hc[ij2(g, i + 2, j)] + 8.0 * (hc[ij2(g, i + 1, j)] - hc[ij2(g, i - 1, j)])) / (12.0 * g.dx);
     g4y[n] = (hc[ij2(g, i, j - 2)] - hc[ij2(g, i, j + 2)] + 8.0 * (hc[ij2(g, i, j + 1)] - hc[ij2(g, i, j - 1)])) / (12.0 * g.dy);
+}
+
+// reciprocal 3D metrics over terrain (built once; the step kernels multiply by them)
+__global__ void k_terrain_recip(Geo g, double *rH3, double *rHx3, double *rHy3, double *rdzw3, double *rdz2) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    double hc = g.hc[ij2(g, i, j)];
+    rH3[c] = 1.0 / (g.dzeta[k] + g.ds[k] * hc);
+    rHx3[c] = 1.0 / (g.dzeta[k] + g.ds[k] * g.hxf[ij2(g, i, j)]);
+    rHy3[c] = 1.0 / (g.dzeta[k] + g.ds[k] * g.hyf[ij2(g, i, j)]);
+    rdzw3[c] = k >= 1 ? 1.0 / (g.dzc[k] + (g.sc[k] - g.sc[k - 1]) * hc) : 0.0;
+    int kl = k == 0 ? 0 : k - 1, ku = k == g.nz - 1 ? g.nz - 1 : k + 1;
+    rdz2[c] = ku > kl ? 1.0 / ((g.zetac[ku] + g.sc[ku] * hc) - (g.zetac[kl] + g.sc[kl] * hc)) : 0.0;
 }
 
 struct ThetaProfile {
@@ -217,20 +247,20 @@ __device__ __forceinline__ double S12e(const Geo &g, const Vel &v, int i, int j,
 }
 __device__ __forceinline__ double S13e(const Geo &g, const Vel &v, int i, int j, int k) {
     if (k <= 0 || k >= g.nz) return 0.0;
-    double dz = g.dzc[k];
-    return 0.5 * ((cval(g, v.ux, i, j, k) - cval(g, v.ux, i, j, k - 1)) / dz
+    double rdz = g.rdzc[k];
+    return 0.5 * ((cval(g, v.ux, i, j, k) - cval(g, v.ux, i, j, k - 1)) * rdz
                 + (__ldg(v.wz + cixw(g, i, j, k)) - __ldg(v.wz + cixw(g, i - 1, j, k))) * g.rdx);
 }
 __device__ __forceinline__ double S23e(const Geo &g, const Vel &v, int i, int j, int k) {
     if (k <= 0 || k >= g.nz) return 0.0;
-    double dz = g.dzc[k];
-    return 0.5 * ((cval(g, v.vy, i, j, k) - cval(g, v.vy, i, j, k - 1)) / dz
+    double rdz = g.rdzc[k];
+    return 0.5 * ((cval(g, v.vy, i, j, k) - cval(g, v.vy, i, j, k - 1)) * rdz
                 + (__ldg(v.wz + cixw(g, i, j, k)) - __ldg(v.wz + cixw(g, i, j - 1, k))) * g.rdy);
 }
 __device__ __forceinline__ void diag_strain(const Geo &g, const Vel &v, int i, int j, int k, double &s11, double &s22, double &s33) {
     s11 = (cval(g, v.ux, i + 1, j, k) - cval(g, v.ux, i, j, k)) * g.rdx;
     s22 = (cval(g, v.vy, i, j + 1, k) - cval(g, v.vy, i, j, k)) * g.rdy;
-    s33 = (__ldg(v.wz + cixw(g, i, j, k + 1)) - __ldg(v.wz + cixw(g, i, j, k))) / g.dzeta[k];
+    s33 = (__ldg(v.wz + cixw(g, i, j, k + 1)) - __ldg(v.wz + cixw(g, i, j, k))) * g.rdzeta[k];
 }
 
 // mu = rho (Cs Delta)^2 sqrt(2 S_ij S_ij) (Smagorinsky-Lilly) or rho nu (constant)
@@ -327,17 +357,17 @@ __device__ double tau23(const Geo &g, const Phys &ph, const Vel &v, const double
 // rho alpha dtheta/dn at the three face types (minus the diffusive flux); bottom face: the
 // upward MOST flux rho Q enters as -rho Q
 __device__ __forceinline__ double heat_x(const Geo &g, const Phys &ph, const double *mu, const double *th, int i, int j, int k) {
-    return 0.5 * (cval(g, mu, i - 1, j, k) + cval(g, mu, i, j, k)) / ph.Pr_t * (cval(g, th, i, j, k) - cval(g, th, i - 1, j, k)) * g.rdx;
+    return 0.5 * (cval(g, mu, i - 1, j, k) + cval(g, mu, i, j, k)) * ph.rPr_t * (cval(g, th, i, j, k) - cval(g, th, i - 1, j, k)) * g.rdx;
 }
 __device__ __forceinline__ double heat_y(const Geo &g, const Phys &ph, const double *mu, const double *th, int i, int j, int k) {
-    return 0.5 * (cval(g, mu, i, j - 1, k) + cval(g, mu, i, j, k)) / ph.Pr_t * (cval(g, th, i, j, k) - cval(g, th, i, j - 1, k)) * g.rdy;
+    return 0.5 * (cval(g, mu, i, j - 1, k) + cval(g, mu, i, j, k)) * ph.rPr_t * (cval(g, th, i, j, k) - cval(g, th, i, j - 1, k)) * g.rdy;
 }
 __device__ __forceinline__ double heat_z(const Geo &g, const Phys &ph, const double *mu, const double *th, const double *rho,
                                          int i, int j, int k, int visc) {
     if (k == 0) return ph.surface == 1 ? -cval(g, rho, i, j, 0) * ph.Qs : 0.0;   // upward flux rho Q
     if (k >= g.nz || !visc) return 0.0;
-    return 0.5 * (cval(g, mu, i, j, k - 1) + cval(g, mu, i, j, k)) / ph.Pr_t
-         * (cval(g, th, i, j, k) - cval(g, th, i, j, k - 1)) / g.dzc[k];
+    return 0.5 * (cval(g, mu, i, j, k - 1) + cval(g, mu, i, j, k)) * ph.rPr_t
+         * (cval(g, th, i, j, k) - cval(g, th, i, j, k - 1)) * g.rdzc[k];
 }
 
 // ------------------------------------------------------------------ slow tendencies
@@ -418,13 +448,13 @@ __global__ void k_rhs_u(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const
         F[s] = adv * upwind5(q, sgnd(adv));
     }
     div += F[1] - F[0];
-    double r = -div / Hx(g, i, j, k);
+    double r = -div * rHxf(g, i, j, k);
     // pressure gradient
     double px = (pp[c] - cval(g, pp, i - 1, j, k)) * g.rdx;
     if (g.terrain && g.nz > 1) {
         int kl = k == 0 ? 0 : k - 1, ku = k == g.nz - 1 ? g.nz - 1 : k + 1;
-        double d0 = (cval(g, pp, i, j, ku) - cval(g, pp, i, j, kl)) / (zc(g, i, j, ku) - zc(g, i, j, kl));
-        double d1 = (cval(g, pp, i - 1, j, ku) - cval(g, pp, i - 1, j, kl)) / (zc(g, i - 1, j, ku) - zc(g, i - 1, j, kl));
+        double d0 = (cval(g, pp, i, j, ku) - cval(g, pp, i, j, kl)) * rdz2c(g, i, j, k);
+        double d1 = (cval(g, pp, i - 1, j, ku) - cval(g, pp, i - 1, j, kl)) * rdz2c(g, i - 1, j, k);
         px -= 0.5 * hxi_x(g, i, j, k) * (d0 + d1);
     }
     r -= px;
@@ -441,7 +471,7 @@ __global__ void k_rhs_u(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const
             d += (tau_diag(g, v, mu, i, j, k, 0) - tau_diag(g, v, mu, i - 1, j, k, 0)) * g.rdx
                + (tau12(g, v, mu, i, j + 1, k) - tau12(g, v, mu, i, j, k)) * g.rdy;
         }
-        d += (tau13(g, ph, v, mu, st.r, th, i, j, k + 1, visc) - tau13(g, ph, v, mu, st.r, th, i, j, k, visc)) / g.dzeta[k];
+        d += (tau13(g, ph, v, mu, st.r, th, i, j, k + 1, visc) - tau13(g, ph, v, mu, st.r, th, i, j, k, visc)) * g.rdzeta[k];
         r -= d;
     }
     Ru[c] = r;
@@ -477,12 +507,12 @@ __global__ void k_rhs_v(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const
         F[s] = adv * upwind5(q, sgnd(adv));
     }
     div += F[1] - F[0];
-    double r = -div / Hy(g, i, j, k);
+    double r = -div * rHyf(g, i, j, k);
     double py = (pp[c] - cval(g, pp, i, j - 1, k)) * g.rdy;
     if (g.terrain && g.nz > 1) {
         int kl = k == 0 ? 0 : k - 1, ku = k == g.nz - 1 ? g.nz - 1 : k + 1;
-        double d0 = (cval(g, pp, i, j, ku) - cval(g, pp, i, j, kl)) / (zc(g, i, j, ku) - zc(g, i, j, kl));
-        double d1 = (cval(g, pp, i, j - 1, ku) - cval(g, pp, i, j - 1, kl)) / (zc(g, i, j - 1, ku) - zc(g, i, j - 1, kl));
+        double d0 = (cval(g, pp, i, j, ku) - cval(g, pp, i, j, kl)) * rdz2c(g, i, j, k);
+        double d1 = (cval(g, pp, i, j - 1, ku) - cval(g, pp, i, j - 1, kl)) * rdz2c(g, i, j - 1, k);
         py -= 0.5 * heta_y(g, i, j, k) * (d0 + d1);
     }
     r -= py;
@@ -499,7 +529,7 @@ __global__ void k_rhs_v(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const
             d += (tau12(g, v, mu, i + 1, j, k) - tau12(g, v, mu, i, j, k)) * g.rdx
                + (tau_diag(g, v, mu, i, j, k, 1) - tau_diag(g, v, mu, i, j - 1, k, 1)) * g.rdy;
         }
-        d += (tau23(g, ph, v, mu, st.r, th, i, j, k + 1, visc) - tau23(g, ph, v, mu, st.r, th, i, j, k, visc)) / g.dzeta[k];
+        d += (tau23(g, ph, v, mu, st.r, th, i, j, k + 1, visc) - tau23(g, ph, v, mu, st.r, th, i, j, k, visc)) * g.rdzeta[k];
         r -= d;
     }
     Rv[c] = r;
@@ -594,26 +624,21 @@ __global__ void k_tri_build(Geo g, Phys ph, const double *rho, const double *rt,
 }
 
 // horizontal momenta: Delta U'' = dtau (-gamma R_d pi^t (dTheta~/dxi - h_xi/h_zeta dTheta~/dzeta) + R_U),
-// Theta~ = Theta'' + beta_d (Theta'' - Theta''_prev) (reading R10)
-__device__ __forceinline__ double ttil(const Geo &g, const double *Xt, const double *Tp, double bd, int i, int j, int k) {
-    long long a = cixw(g, i, j, k);
-    double x = __ldg(Xt + a);
-    return x + bd * (x - __ldg(Tp + a));
-}
-__global__ void k_sub_horiz(Geo g, Phys ph, const double *pi, const double *Xt, const double *Tp,
-                            const double *Ru, const double *Rv, double *Xu, double *Xv, double dtau) {
+// Theta~ = Theta'' + beta_d (Theta'' - Theta''_prev) (reading R10), which the previous vertical
+// solve (or the stage start, where Theta~ = Theta'') left in Tt.
+__global__ void k_sub_horiz(Geo g, Phys ph, const double *pi, const double *Tt, const double *Ru, const double *Rv,
+                            double *Xu, double *Xv, double dtau) {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= g.nc) return;
     int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
-    double bd = ph.beta_d;
-    double t0 = ttil(g, Xt, Tp, bd, i, j, k);
-    double gx = (t0 - ttil(g, Xt, Tp, bd, i - 1, j, k)) * g.rdx;
-    double gy = (t0 - ttil(g, Xt, Tp, bd, i, j - 1, k)) * g.rdy;
+    double t0 = __ldg(Tt + c);
+    double gx = (t0 - cval(g, Tt, i - 1, j, k)) * g.rdx;
+    double gy = (t0 - cval(g, Tt, i, j - 1, k)) * g.rdy;
     if (g.terrain && g.nz > 1) {
         int kl = k == 0 ? 0 : k - 1, ku = k == g.nz - 1 ? g.nz - 1 : k + 1;
-        double dc = (ttil(g, Xt, Tp, bd, i, j, ku) - ttil(g, Xt, Tp, bd, i, j, kl)) / (zc(g, i, j, ku) - zc(g, i, j, kl));
-        double dxm = (ttil(g, Xt, Tp, bd, i - 1, j, ku) - ttil(g, Xt, Tp, bd, i - 1, j, kl)) / (zc(g, i - 1, j, ku) - zc(g, i - 1, j, kl));
-        double dym = (ttil(g, Xt, Tp, bd, i, j - 1, ku) - ttil(g, Xt, Tp, bd, i, j - 1, kl)) / (zc(g, i, j - 1, ku) - zc(g, i, j - 1, kl));
+        double dc = (cval(g, Tt, i, j, ku) - cval(g, Tt, i, j, kl)) * rdz2c(g, i, j, k);
+        double dxm = (cval(g, Tt, i - 1, j, ku) - cval(g, Tt, i - 1, j, kl)) * rdz2c(g, i - 1, j, k);
+        double dym = (cval(g, Tt, i, j - 1, ku) - cval(g, Tt, i, j - 1, kl)) * rdz2c(g, i, j - 1, k);
         gx -= 0.5 * hxi_x(g, i, j, k) * (dc + dxm);
         gy -= 0.5 * heta_y(g, i, j, k) * (dc + dym);
     }
@@ -627,79 +652,85 @@ __global__ void k_sub_horiz(Geo g, Phys ph, const double *pi, const double *Xt, 
 
 // Per column: explicit parts Theta*, rho* (new U'', V'' divergence, beta_1 part of the old
 // Omega'' flux), forward substitution with the stage LU factors, back substitution for
-// Omega''^{new}, then Theta'', rho'', W'' = Omega'' + metric shift.  Theta''_prev <- Theta''^tau.
-__global__ void k_sub_vert(Geo g, Phys ph, Tri tr, const double *th, const double *Rr, const double *Rt,
-                           const double *Rw, F5 x, double *Om, double *Tp, double dtau) {
+// Omega''^{new}, then Theta'', rho'', W'' = Omega'' + metric shift, and Theta~ of the next
+// substep into Tt.  Over terrain the metric shift of each w-face is parked in W'' between the
+// two passes (it depends only on the new U'', V'').
+__global__ void __launch_bounds__(64) k_sub_vert(Geo g, Phys ph, Tri tr, const double *th, const double *Rr,
+                                                 const double *Rt, const double *Rw, F5 x, double *Om, double *Tt,
+                                                 double dtau) {
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= g.nxy) return;
     int i = (int)(n % g.nx), j = (int)(n / g.nx);
     const int nz = g.nz;
-    double b1 = 0.5 * (1.0 - ph.beta_s), b2 = 0.5 * (1.0 + ph.beta_s);
-    double Gg = dtau * 0.5 * ph.g;
+    const long long nxy = g.nxy;
+    const double b1 = 0.5 * (1.0 - ph.beta_s), b2 = 0.5 * (1.0 + ph.beta_s), bd = ph.beta_d;
+    const double Gg = dtau * 0.5 * ph.g, db2 = dtau * b2;
+    const long long cx1 = cixw(g, i + 1, j, 0) - n, cy1 = cixw(g, i, j + 1, 0) - n;   // neighbour offsets
+    const long long cxm = cixw(g, i - 1, j, 0) - n, cym = cixw(g, i, j - 1, 0) - n;
     // forward pass
     double X0m = 0.0, Y0m = 0.0, dpm = 0.0;
-    double th_m = cval(g, th, i, j, -1);
-    double th_c = th[cix(g, i, j, 0)];
-    double om_k = 0.0;   // old Omega'' at face k (0 at the wall)
+    double th_c = th[n];
+    double om_k = 0.0, omth_k = 0.0;   // old Omega'' and Omega'' theta_w at face k (0 at the wall)
     for (int k = 0; k < nz; ++k) {
-        long long c = cix(g, i, j, k);
+        long long c = n + (long long)k * nxy;
         double th_p = cval(g, th, i, j, k + 1);
-        double thw_k = 0.5 * (th_m + th_c), thw_p = 0.5 * (th_c + th_p);
-        double om_p = (k + 1 < nz) ? Om[cix(g, i, j, k + 1)] : 0.0;
-        long long cxp = cixw(g, i + 1, j, k), cyp = cixw(g, i, j + 1, k);
-        double Uc = x.u[c], Up = x.u[cxp], Vc = x.v[c], Vp = x.v[cyp];
+        double thw_p = 0.5 * (th_c + th_p);
+        double om_p = (k + 1 < nz) ? Om[c + nxy] : 0.0;
+        double omth_p = om_p * thw_p;
+        double Uc = x.u[c], Up = x.u[c + cx1], Vc = x.v[c], Vp = x.v[c + cy1];
         double Hxm = Hx(g, i, j, k), Hxp = Hx(g, i + 1, j, k), Hym = Hy(g, i, j, k), Hyp = Hy(g, i, j + 1, k);
-        double thxm = 0.5 * (cval(g, th, i - 1, j, k) + th_c), thxp = 0.5 * (th_c + cval(g, th, i + 1, j, k));
-        double thym = 0.5 * (cval(g, th, i, j - 1, k) + th_c), thyp = 0.5 * (th_c + cval(g, th, i, j + 1, k));
-        double divM = (Hxp * Up - Hxm * Uc) * g.rdx + (Hyp * Vp - Hym * Vc) * g.rdy;
-        double divT = (Hxp * Up * thxp - Hxm * Uc * thxm) * g.rdx + (Hyp * Vp * thyp - Hym * Vc * thym) * g.rdy;
+        double thxm = 0.5 * (__ldg(th + c + cxm) + th_c), thxp = 0.5 * (th_c + __ldg(th + c + cx1));
+        double thym = 0.5 * (__ldg(th + c + cym) + th_c), thyp = 0.5 * (th_c + __ldg(th + c + cy1));
+        double fxm = Hxm * Uc, fxp = Hxp * Up, fym = Hym * Vc, fyp = Hyp * Vp;
+        double divM = (fxp - fxm) * g.rdx + (fyp - fym) * g.rdy;
+        double divT = (fxp * thxp - fxm * thxm) * g.rdx + (fyp * thyp - fym * thym) * g.rdy;
         double rH = rHc(g, i, j, k);
         double xt = x.t[c], xr = x.r[c];
-        Tp[c] = xt;
-        double Ts = xt + dtau * ((-divT - b1 * (om_p * thw_p - om_k * thw_k)) * rH + Rt[c]);
+        Tt[c] = xt;   // Theta''^tau, until the back substitution
+        double Ts = xt + dtau * ((-divT - b1 * (omth_p - omth_k)) * rH + Rt[c]);
         double Rs = xr + dtau * ((-divM - b1 * (om_p - om_k)) * rH + Rr[c]);
         x.t[c] = Ts;   // hold Theta*, rho* until the back substitution
         x.r[c] = Rs;
         double X0 = b1 * xt + b2 * Ts, Y0 = b1 * xr + b2 * Rs;
         if (k >= 1) {
-            long long w = c;
-            double A = g.terrain ? metric_shift(g, x.u, x.v, i, j, k) : 0.0;
-            double rhs = x.w[w] - A + dtau * Rw[w] + tr.P[w] * X0 + tr.Q[w] * X0m - Gg * (Y0 + Y0m);
-            double dp = (rhs - tr.a[w] * dpm) * tr.im[w];
-            Om[w] = dp;
+            double A = 0.0;
+            if (g.terrain) A = metric_shift(g, x.u, x.v, i, j, k);
+            double rhs = x.w[c] - A + dtau * Rw[c] + tr.P[c] * X0 + tr.Q[c] * X0m - Gg * (Y0 + Y0m);
+            if (g.terrain) x.w[c] = A;
+            double dp = (rhs - tr.a[c] * dpm) * tr.im[c];
+            Om[c] = dp;
             dpm = dp;
         }
         X0m = X0; Y0m = Y0;
-        om_k = om_p;
-        th_m = th_c; th_c = th_p;
+        om_k = om_p; omth_k = omth_p;
+        th_c = th_p;
     }
     // back substitution, from the top wall (Omega'' = 0) down
-    double om_up = 0.0;
-    double thw_up = 0.0;
     {
-        long long w = cix(g, i, j, nz);
+        long long w = n + (long long)nz * nxy;
         x.w[w] = 0.0;
         Om[w] = 0.0;
     }
+    double om_up = 0.0, omth_up = 0.0;
+    th_c = th[n + (long long)(nz - 1) * nxy];
     for (int k = nz - 1; k >= 0; --k) {
-        long long c = cix(g, i, j, k);
-        double om_k2 = 0.0;
-        if (k >= 1) {
-            om_k2 = Om[c] - tr.cp[c] * om_up;
-            Om[c] = om_k2;
-        } else {
-            Om[c] = 0.0;
-        }
-        double thc = th[c];
-        double thw_k = 0.5 * (cval(g, th, i, j, k - 1) + thc);
-        double thw_p = (k == nz - 1) ? 0.5 * (thc + cval(g, th, i, j, k + 1)) : thw_up;
-        double db = dtau * b2 * rHc(g, i, j, k);
-        x.t[c] = x.t[c] - db * (om_up * thw_p - om_k2 * thw_k);
-        x.r[c] = x.r[c] - db * (om_up - om_k2);
-        double A = g.terrain ? metric_shift(g, x.u, x.v, i, j, k) : 0.0;
-        x.w[c] = om_k2 + A;
-        om_up = om_k2;
-        thw_up = thw_k;
+        long long c = n + (long long)k * nxy;
+        double om = 0.0;
+        if (k >= 1) om = Om[c] - tr.cp[c] * om_up;
+        Om[c] = om;
+        double th_m = cval(g, th, i, j, k - 1);
+        double omth = om * (0.5 * (th_m + th_c));
+        double db = db2 * rHc(g, i, j, k);
+        double xt = x.t[c] - db * (omth_up - omth);
+        x.t[c] = xt;
+        x.r[c] = x.r[c] - db * (om_up - om);
+        double told = Tt[c];
+        Tt[c] = xt + bd * (xt - told);
+        double A = 0.0;
+        if (g.terrain) A = k >= 1 ? x.w[c] : metric_shift(g, x.u, x.v, i, j, 0);
+        x.w[c] = om + A;
+        om_up = om; omth_up = omth;
+        th_c = th_m;
     }
 }
 
@@ -834,6 +865,10 @@ void launch_terrain(const Geo &g, const double *hn, double *hc, double *hxf, dou
     LAUNCH("terrain_avg", s, k_terrain_avg<<<nblk(g.nxy, BS), BS, 0, s>>>(g, hn, hc, hxf, hyf));
     LAUNCH("terrain_grad", s, k_terrain_grad<<<nblk(g.nxy, BS), BS, 0, s>>>(g, hc, gxc, gyc, g4x, g4y));
 }
+void launch_terrain_recip(const Geo &g, double *rH3, double *rHx3, double *rHy3, double *rdzw3, double *rdz2,
+                          cudaStream_t s) {
+    LAUNCH("terrain_recip", s, k_terrain_recip<<<nblk(g.nc, BS), BS, 0, s>>>(g, rH3, rHx3, rHy3, rdzw3, rdz2));
+}
 void launch_base_state(const Geo &g, int n_knots, const double *kz, const double *kt, double theta_s, double N,
                        double p_s, double grav, double *rho0, double *th0, double *p0, cudaStream_t s) {
     ThetaProfile tp{n_knots, kz, kt, theta_s, N, grav};
@@ -873,7 +908,7 @@ void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const dou
 }
 void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *pi, const double *th, CF5 R, F5 x,
                     double *Om, double *Tp, double dtau, cudaStream_t s) {
-    LAUNCH("sub_horiz", s, k_sub_horiz<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pi, x.t, Tp, R.u, R.v, x.u, x.v, dtau));
+    LAUNCH("sub_horiz", s, k_sub_horiz<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pi, Tp, R.u, R.v, x.u, x.v, dtau));
     LAUNCH("sub_vert", s, k_sub_vert<<<nblk(g.nxy, 64), 64, 0, s>>>(g, ph, tr, th, R.r, R.t, R.w, x, Om, Tp, dtau));
 }
 void launch_stage_end(const Geo &g, F5 st, CF5 x, cudaStream_t s) {
