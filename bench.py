@@ -157,12 +157,21 @@ def oracle_rate(wl_sample, steps, threads=None):
 
 def workload(args):
     from paper_2412_04395_gb300 import workloads as W
+    prec = W.PREC_MIXED32 if args.precision == "mixed" else W.PREC_FP64
     if args.case == "hill_bubble":
+        if args.precision != "fp64":
+            raise SystemExit("the hill bubble runs over terrain, which the mixed path does not support")
         if args.grid:
             return W.hill_bubble(nx=args.grid[0], ny=args.grid[1], nz=args.grid[2])
         return W.hill_bubble()
     if args.case == "density_current":
-        return W.density_current()
+        return W.density_current().with_(precision=prec)
+    if args.case == "convective_abl":
+        nx, ny, nz = args.grid or (512, 512, 160)
+        wl = W.convective_abl(nx=nx, ny=ny, nz=nz, dx=40.0).with_(precision=prec)
+        if args.closure == "learned":
+            wl = wl.with_(closure=W.CLOSURE_LEARNED)
+        return wl
     raise SystemExit(f"unknown case {args.case}")
 
 
@@ -172,6 +181,8 @@ def sample_workload(args):
     from paper_2412_04395_gb300 import workloads as W
     if args.case == "hill_bubble":
         return W.hill_bubble(nx=64, ny=64, nz=128, dx=50.0)
+    if args.case == "convective_abl":
+        return W.convective_abl(nx=32, ny=32, nz=160, dx=40.0).with_(precision=W.PREC_FP64)
     return W.density_current(nx=64, ny=4, nz=64)
 
 
@@ -272,6 +283,9 @@ def run_ours(args):
     wl = workload(args)
     d = Dycore(wl, device=f"cuda:{local}")
     d.erf_set_initial(wl.dtheta, wl.u, wl.v, wl.w)
+    if args.closure == "learned":
+        blob, _ = closure_blob(wl, d)
+        d.erf_set_closure_weights(blob)
     stream = d.stream
     # warm-up (graph capture happens on the first step)
     d.erf_rk3_step(args.warmup)
@@ -359,9 +373,11 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+                "data": "synthetic",
                 "config": {"workload": wl.name, "grid": [wl.nx, wl.ny, wl.nz], "dx": wl.dx,
-                           "substeps": wl.n_substeps, "precision": "fp64", "parallelism": f"replicas{ws}",
+                           "substeps": wl.n_substeps, "precision": args.precision, "closure": args.closure,
+                           "parallelism": f"replicas{ws}",
                            "l2": "working set >> L2 (no flush needed)"},
                 "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                            "reasons": clocks["reasons"], "samples": clocks["samples"]},
@@ -386,6 +402,9 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--cmp-grid", type=int, nargs=3, default=[512, 512, 160])
     ap.add_argument("--cmp-steps", type=int, default=8)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--closure", default="default", choices=["default", "learned"],
+                    help="learned: the MLP closure (convective_abl with --precision mixed)")
     ap.add_argument("--grid", type=int, nargs=3, default=None,
                     help="nx ny nz of a smaller window of the workload (profiling runs only)")
     args = ap.parse_args()

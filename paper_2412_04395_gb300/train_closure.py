@@ -6,7 +6,9 @@
   4. standardisation statistics and mini-batch Adam on the GPU (erf_column_stats,
      erf_standardise, erf_train_closure);
   5. a closure blob (erf_set_closure_weights format) and an a-priori comparison on held-out
-     snapshots: learned closure vs Smagorinsky vs no model.
+     snapshots: learned closure vs Smagorinsky vs no model;
+  6. an a-posteriori comparison: coarse runs (learned, Smagorinsky, no model) started from the
+     filtered fine state and compared, at several horizons, with the filtered fine run.
 
     python -m paper_2412_04395_gb300.train_closure --out closure.bin [--grid 256 256 128] ...
 """
@@ -54,9 +56,9 @@ def smagorinsky_prediction(F, rho_unused, delta, Cs=0.17, Pr_t=1.0 / 3.0, g=9.81
     return out
 
 
-def collect(fine: W.Workload, r: int, spinup: int, n_snap: int, every: int, log=print):
+def collect(fine: W.Workload, r: int, spinup: int, n_snap: int, every: int, log=print, keep_fine=False):
     """Fine run + filtered snapshots.  Returns (features per snapshot [Nc,12], targets per
-    snapshot [Nc,9], coarse states per snapshot, coarse workload)."""
+    snapshot [Nc,9], coarse states per snapshot, coarse workload[, the fine Dycore])."""
     import torch
     from .erf import Dycore
     d = Dycore(fine.with_(precision=W.PREC_MIXED32))
@@ -77,6 +79,8 @@ def collect(fine: W.Workload, r: int, spinup: int, n_snap: int, every: int, log=
         Ts.append(T)
         states.append(f)
     torch.cuda.synchronize()
+    if keep_fine:
+        return Xs, Ts, states, cw, d
     d.close()
     return Xs, Ts, states, cw
 
@@ -137,20 +141,96 @@ def apriori(blob, Xs, Ts, states, cw, test_idx, stats):
     return {k: (float(np.mean(v)) if k != "fallback_cells" else int(np.sum(v))) for k, v in res.items()}
 
 
+def primitives(st):
+    """theta at cells and u, v, w at their faces of a flat periodic C-grid state (numpy dict)."""
+    rho = st["rho"]
+    th = st["rhotheta"] / rho
+    u = st["rhou"] / (0.5 * (np.roll(rho, 1, axis=2) + rho))
+    v = st["rhov"] / (0.5 * (np.roll(rho, 1, axis=1) + rho))
+    rz = np.concatenate([rho[:1], 0.5 * (rho[:-1] + rho[1:]), rho[-1:]])
+    w = st["rhow"] / rz
+    return th, u, v, w
+
+
+def field_errors(coarse, ref, th_mean0, u_g, v_g):
+    """Relative L2 errors of a coarse state against the filtered fine state (reading of the
+    2% criterion): theta - <theta>_0(z) (planar mean of the filtered field at the start) and the
+    velocity departure from the geostrophic wind, pointwise; the same on the raw fields; and the
+    planar-mean theta profile against its change since the start."""
+    tc, uc, vc, wc = primitives(coarse)
+    tf, uf, vf, wf = primitives(ref)
+    m = th_mean0[:, None, None]
+    dv = np.sqrt(np.sum((uc - uf) ** 2) + np.sum((vc - vf) ** 2) + np.sum((wc - wf) ** 2))
+    pc, pf = tc.mean(axis=(1, 2)), tf.mean(axis=(1, 2))
+    return {
+        "theta_dev": float(np.linalg.norm(tc - tf) / np.linalg.norm(tf - m)),
+        "vel_dev": float(dv / np.sqrt(np.sum((uf - u_g) ** 2) + np.sum((vf - v_g) ** 2) + np.sum(wf ** 2))),
+        "theta_raw": float(np.linalg.norm(tc - tf) / np.linalg.norm(tf)),
+        "vel_raw": float(dv / np.sqrt(np.sum(uf ** 2) + np.sum(vf ** 2) + np.sum(wf ** 2))),
+        "theta_mean_profile": float(np.linalg.norm(pc - pf) / max(np.linalg.norm(pf - th_mean0), 1e-300)),
+    }
+
+
+def aposteriori(fine_d, fine: W.Workload, cw: W.Workload, blob: bytes, r: int, horizons, log=print):
+    """Coarse runs from the filtered fine state at t0 with the learned closure, Smagorinsky and no
+    model (coarse dt = r x fine dt, so one coarse step spans r fine steps), compared with the
+    filtered fine run after each horizon (in fine steps, multiples of r)."""
+    from .erf import Dycore
+    f0, _ = fine_d.erf_filter_state(r)
+    s0 = {k: v.cpu().numpy() for k, v in f0.items()}
+    th_mean0 = (s0["rhotheta"] / s0["rho"]).mean(axis=(1, 2))
+    runs = {}
+    for name, clo in (("learned", W.CLOSURE_LEARNED), ("smagorinsky", W.CLOSURE_SMAGORINSKY),
+                      ("none", W.CLOSURE_NONE)):
+        c = Dycore(cw.with_(closure=clo, dt=fine.dt * r, precision=W.PREC_MIXED32))
+        for k in ("rho", "rhotheta", "rhou", "rhov", "rhow"):
+            c.erf_set_state(k, f0[k].contiguous())
+        if clo == W.CLOSURE_LEARNED:
+            c.erf_set_closure_weights(blob)
+        runs[name] = c
+    out = []
+    done = 0
+    for h in horizons:
+        assert h % r == 0 and h > done
+        fine_d.erf_rk3_step(h - done)
+        for c in runs.values():
+            c.erf_rk3_step((h - done) // r)
+        done = h
+        fh, _ = fine_d.erf_filter_state(r)
+        ref = {k: v.cpu().numpy() for k, v in fh.items()}
+        row = {"seconds": h * fine.dt}
+        for name, c in runs.items():
+            row[name] = field_errors(c.state(), ref, th_mean0, cw.u_g, cw.v_g)
+        out.append(row)
+        log(f"a-posteriori after {h * fine.dt:.0f} s: " + ", ".join(
+            f"{n}: theta_dev {row[n]['theta_dev']:.3f} vel_dev {row[n]['vel_dev']:.3f} "
+            f"theta_raw {row[n]['theta_raw']:.2e} vel_raw {row[n]['vel_raw']:.3f}" for n in runs))
+    for c in runs.values():
+        c.close()
+    return out
+
+
 def run(grid=(256, 256, 128), dx=10.0, dt=0.1, spinup=6000, snapshots=10, every=300, test_every=5,
-        epochs=20, batch=8192, lr=1e-3, seed=7, log=print):
+        epochs=20, batch=8192, lr=1e-3, seed=7, horizons=(), log=print):
     """Every test_every-th snapshot is held out (interleaved, so train and test see the same
-    stage of the boundary layer's development)."""
+    stage of the boundary layer's development).  With horizons (fine steps), the fine run goes
+    on after the last snapshot for the a-posteriori comparison."""
     nx, ny, nz = grid
+    r = 4
     fine = W.convective_abl(nx=nx, ny=ny, nz=nz, dx=dx).with_(dt=dt)
-    Xs, Ts, states, cw = collect(fine, 4, spinup, snapshots, every, log)
+    res = collect(fine, r, spinup, snapshots, every, log, keep_fine=bool(horizons))
+    Xs, Ts, states, cw = res[:4]
     test_idx = [i for i in range(snapshots) if i % test_every == test_every - 1]
     train_idx = [i for i in range(snapshots) if i not in test_idx]
     params, stats, losses = train(Xs, Ts, train_idx, epochs, batch, lr, seed, log)
     blob = blob_from(params, stats)
     ap = apriori(blob, Xs, Ts, states, cw, test_idx, stats)
     log(f"a-priori MSE (standardised, held-out): {ap}")
-    return blob, ap, losses, cw
+    post = None
+    if horizons:
+        post = aposteriori(res[4], fine, cw, blob, r, horizons, log)
+        res[4].close()
+    return blob, ap, losses, cw, post
 
 
 def main():
@@ -167,15 +247,18 @@ def main():
     ap.add_argument("--batch", type=int, default=8192)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--horizons", type=int, nargs="*", default=[],
+                    help="a-posteriori comparison after these numbers of fine steps (multiples of 4)")
     ap.add_argument("--report", default=None)
     args = ap.parse_args()
-    blob, ap, losses, cw = run(tuple(args.grid), args.dx, args.dt, args.spinup, args.snapshots, args.every,
-                               args.test_every, args.epochs, args.batch, args.lr, args.seed)
+    blob, ap, losses, cw, post = run(tuple(args.grid), args.dx, args.dt, args.spinup, args.snapshots, args.every,
+                                     args.test_every, args.epochs, args.batch, args.lr, args.seed,
+                                     tuple(args.horizons))
     open(args.out, "wb").write(blob)
     print(f"wrote {args.out} ({len(blob)} bytes)")
     if args.report:
-        json.dump({"apriori_mse": ap, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
-                   "args": vars(args)}, open(args.report, "w"), indent=1)
+        json.dump({"apriori_mse": ap, "aposteriori": post, "loss_first": float(losses[0]),
+                   "loss_last": float(losses[-1]), "args": vars(args)}, open(args.report, "w"), indent=1)
 
 
 if __name__ == "__main__":
