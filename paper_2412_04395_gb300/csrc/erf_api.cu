@@ -66,6 +66,7 @@ struct erf_handle {
     F5f mst, msn, mx, mR;
     float *mpp, *mpi, *mthp, *mTp, *mOm, *mux, *mvy, *mwz, *mmfx, *mmfy, *mmu, *mbase;
     double *mdbuf, *mrt0;
+    float *mX0 = nullptr, *mY0 = nullptr;   // beta-weighted Theta'', rho'' of the vertical substep
     MxBase mb;
     // learned closure
     void *cl_w = nullptr;
@@ -158,6 +159,7 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
         H->mbase = cv.take<float>(mx_base_floats((int)nz));
         H->mrt0 = cv.take<double>(nz);
         H->mdbuf = cv.take<double>(nw);
+        H->mX0 = cv.take<float>(nc); H->mY0 = cv.take<float>(nc);
         H->mtri.a = cv.take<double>(nw); H->mtri.cp = cv.take<double>(nw); H->mtri.im = cv.take<double>(nw);
         H->mtri.P = cv.take<float>(nw); H->mtri.Q = cv.take<float>(nw);
         if (c->closure == 3) {
@@ -301,7 +303,7 @@ extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config 
     launch_base_state(h->geo, cfg->n_knots, h->knz, h->knt, cfg->theta_s, cfg->brunt_N, cfg->p_s, cfg->gravity,
                       h->rho0, h->th0, h->p0, st);
     if (h->mixed) {
-        mx_build_base(h->geo, cfg->Cs, grid->dx, grid->dy, h->mbase, h->mrt0, st);
+        mx_build_base(h->geo, cfg->Cs, grid->dx, grid->dy, cfg->gravity, h->mbase, h->mrt0, st);
         h->mb = mx_base_view(h->mbase, h->mrt0, nz);
     }
     CK(cudaGetLastError(), "init kernels");
@@ -336,7 +338,8 @@ static void enqueue_step_mixed(erf_handle *h, cudaStream_t s) {
         double dtau = stage == 0 ? c.dt / 3.0 : c.dt / c.n_substeps;
         mx_tri_build(g, h->mb, ph, h->mst.r, h->mst.t, h->mpi, h->mthp, dtau, h->mtri, s);
         for (int n = 0; n < nsub; ++n)
-            mx_substep(g, h->mb, ph, h->mtri, h->mpi, h->mthp, cf(h->mR), h->mx, h->mOm, h->mTp, h->mdbuf, dtau, s);
+            mx_substep(g, h->mb, ph, h->mtri, h->mpi, h->mthp, cf(h->mR), h->mx, h->mOm, h->mTp, h->mdbuf, h->mX0, h->mY0,
+                       dtau, s);
         mx_stage_end(g, h->mst, cf(h->mx), s);
     }
 }

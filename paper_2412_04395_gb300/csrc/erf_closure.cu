@@ -55,35 +55,40 @@ __global__ void k_cl_prepare(const float *blob, __nv_bfloat16 *w, float *b, floa
 __device__ __forceinline__ float fv(const Geo &g, const float *f, int i, int j, int k) {
     return __ldg(f + cixw(g, i, j, kref(k, g.nz)));
 }
-__device__ __forceinline__ float dth0f(const MxBase &mb, int ka, int kb) { return mx_dth0(mb, ka, kb); }
 
-// the 12 inputs at cell (i,j,k); also returns dtheta/dz (for the fallback heat flux)
+// the 12 inputs at cell (i,j,k); also returns dtheta/dz (for the fallback heat flux).  Neighbour
+// loads use offsets from the cell index: periodic wrap in x and y, the reflected (clamped)
+// neighbour level in z.
 struct VelIn {
     const float *ux, *vy, *wz, *thp;
 };
-__device__ void cl_features(const Geo &g, const MxBase &mb, const VelIn &v, double grav, int i, int j, int k,
-                            float *f, float &dthdz) {
+__device__ void cl_features(const Geo &g, const MxBase &mb, const VelIn &v, int i, int j, int k, float *f,
+                            float &dthdz) {
     const float rdx = (float)g.rdx, rdy = (float)g.rdy;
-    auto uc = [&](int ii, int jj, int kk) { return 0.5f * (fv(g, v.ux, ii, jj, kk) + fv(g, v.ux, ii + 1, jj, kk)); };
-    auto vc = [&](int ii, int jj, int kk) { return 0.5f * (fv(g, v.vy, ii, jj, kk) + fv(g, v.vy, ii, jj + 1, kk)); };
-    auto wc = [&](int ii, int jj, int kk) {
-        return 0.5f * (__ldg(v.wz + cixw(g, ii, jj, kk)) + __ldg(v.wz + cixw(g, ii, jj, kk + 1)));
-    };
+    const long long nx = g.nx, nxy = g.nxy;
+    const long long c = ((long long)k * g.ny + j) * nx + i;
+    const long long oxp = i + 1 < g.nx ? 1 : 1 - nx, oxm = i > 0 ? -1 : nx - 1;
+    const long long oyp = j + 1 < g.ny ? nx : nx - nxy, oym = j > 0 ? -nx : nxy - nx;
+    const long long okp = k + 1 < g.nz ? nxy : 0, okm = k > 0 ? -nxy : 0;
+    auto L = [](const float *p, long long o) { return __ldg(p + o); };
+    auto uc = [&](long long o) { return 0.5f * (L(v.ux, c + o) + L(v.ux, c + o + oxp)); };
+    auto vc = [&](long long o) { return 0.5f * (L(v.vy, c + o) + L(v.vy, c + o + oyp)); };
+    auto wc = [&](long long o) { return 0.5f * (L(v.wz, c + o) + L(v.wz, c + o + nxy)); };
+    const float rz = mb.r2dzf[k];
+    f[0] = (L(v.ux, c + oxp) - L(v.ux, c)) * rdx;
+    f[1] = (uc(oyp) - uc(oym)) * 0.5f * rdy;
+    f[2] = (uc(okp) - uc(okm)) * rz;
+    f[3] = (vc(oxp) - vc(oxm)) * 0.5f * rdx;
+    f[4] = (L(v.vy, c + oyp) - L(v.vy, c)) * rdy;
+    f[5] = (vc(okp) - vc(okm)) * rz;
+    f[6] = (wc(oxp) - wc(oxm)) * 0.5f * rdx;
+    f[7] = (wc(oyp) - wc(oym)) * 0.5f * rdy;
+    f[8] = (L(v.wz, c + nxy) - L(v.wz, c)) * mb.rdzf[k];
+    f[9] = (L(v.thp, c + oxp) - L(v.thp, c + oxm)) * 0.5f * rdx;
+    f[10] = (L(v.thp, c + oyp) - L(v.thp, c + oym)) * 0.5f * rdy;
     int kl = k > 0 ? k - 1 : 0, ku = k < g.nz - 1 ? k + 1 : g.nz - 1;
-    float rz = (ku > kl) ? (float)(1.0 / (g.zetac[ku] - g.zetac[kl])) : 0.f;
-    f[0] = (fv(g, v.ux, i + 1, j, k) - fv(g, v.ux, i, j, k)) * rdx;
-    f[1] = (uc(i, j + 1, k) - uc(i, j - 1, k)) * 0.5f * rdy;
-    f[2] = (uc(i, j, ku) - uc(i, j, kl)) * rz;
-    f[3] = (vc(i + 1, j, k) - vc(i - 1, j, k)) * 0.5f * rdx;
-    f[4] = (fv(g, v.vy, i, j + 1, k) - fv(g, v.vy, i, j, k)) * rdy;
-    f[5] = (vc(i, j, ku) - vc(i, j, kl)) * rz;
-    f[6] = (wc(i + 1, j, k) - wc(i - 1, j, k)) * 0.5f * rdx;
-    f[7] = (wc(i, j + 1, k) - wc(i, j - 1, k)) * 0.5f * rdy;
-    f[8] = (__ldg(v.wz + cixw(g, i, j, k + 1)) - __ldg(v.wz + cixw(g, i, j, k))) * mb.rdzf[k];
-    f[9] = (fv(g, v.thp, i + 1, j, k) - fv(g, v.thp, i - 1, j, k)) * 0.5f * rdx;
-    f[10] = (fv(g, v.thp, i, j + 1, k) - fv(g, v.thp, i, j - 1, k)) * 0.5f * rdy;
-    dthdz = (dth0f(mb, ku, kl) + fv(g, v.thp, i, j, ku) - fv(g, v.thp, i, j, kl)) * rz;
-    f[11] = (float)(grav / g.th0[k]) * dthdz;
+    dthdz = (mx_dth0(mb, ku, kl) + L(v.thp, c + okp) - L(v.thp, c + okm)) * rz;
+    f[11] = mb.gth0f[k] * dthdz;
 }
 
 __device__ __forceinline__ unsigned pack_bf16(float a, float b) {
@@ -99,18 +104,20 @@ __device__ __forceinline__ void mma16816(float *d, const unsigned *a, unsigned b
 }
 __device__ __forceinline__ float silu_dev(float x) { return __fdividef(x, 1.f + __expf(-x)); }
 
-// Learned SGS stress/heat flux at every cell (mixed path).  Block = 4 warps x 32 cells; each
-// warp runs two m16 tiles through every layer, reusing each B fragment for both.
+// Learned SGS stress/heat flux at every cell (mixed path).  Persistent blocks of 4 warps load
+// the weights into shared memory once and then take 32-cell tiles in turn; each warp runs its
+// tile as two m16 tiles through every layer, reusing each B fragment for both.  The bias is the
+// accumulator's initial value.
 // out: 9 planes of nc floats: rho t11, rho t22, rho t33, rho t12, rho t13, rho t23, rho h1..h3.
 constexpr int CLW = 4;
 constexpr int LD1 = 24, LDH = 72;   // padded shared-memory row lengths (bank-conflict-free B loads)
 constexpr int SW_W1 = 0, SW_W2 = 64 * LD1, SW_W3 = SW_W2 + 64 * LDH, SW_W4 = SW_W3 + 64 * LDH;
 constexpr int SW_TOTAL = SW_W4 + 16 * LDH;
-__global__ void __launch_bounds__(CLW * 32) k_cl_infer(Geo g, MxBase mb, Phys ph, ClDev cl, VelIn v,
+__global__ void __launch_bounds__(CLW * 32, 4) k_cl_infer(Geo g, MxBase mb, Phys ph, ClDev cl, VelIn v,
                                                        const float *dr, float *out, unsigned *nfallback) {
     __shared__ __align__(16) __nv_bfloat16 sW[SW_TOTAL];
     __shared__ float sb[CL_B_F32];
-    __shared__ float sst[2 * CL_NIN + 2 * CL_NOUT];
+    __shared__ float sst[2 * CL_NIN + 2 * CL_NOUT];   // in_mean, 1/in_std, out_mean, out_std
     __shared__ __align__(16) float sF[CLW][32][17];   // standardised features, then outputs
     __shared__ float sMisc[CLW][32][11];              // fallback stresses/fluxes, rho, flag
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -121,119 +128,129 @@ __global__ void __launch_bounds__(CLW * 32) k_cl_infer(Geo g, MxBase mb, Phys ph
     }
     for (int q = tid; q < 16 * 64; q += blockDim.x) sW[SW_W4 + (q / 64) * LDH + q % 64] = cl.W4[q];
     for (int q = tid; q < CL_B_F32; q += blockDim.x) sb[q] = cl.b[q];
-    for (int q = tid; q < 2 * CL_NIN + 2 * CL_NOUT; q += blockDim.x) sst[q] = cl.stats[q];
+    for (int q = tid; q < 2 * CL_NIN + 2 * CL_NOUT; q += blockDim.x)
+        sst[q] = (q >= CL_NIN && q < 2 * CL_NIN) ? 1.f / cl.stats[q] : cl.stats[q];
     __syncthreads();
-    const float *in_mu = sst, *in_sd = sst + 12, *out_mu = sst + 24, *out_sd = sst + 33;
-    const long long c0 = ((long long)blockIdx.x * CLW + warp) * 32;
-    // 1. features of 32 cells (one per lane), standardised; fallback flag on |z| > 6
-    {
-        long long c = c0 + lane;
-        float *m = sMisc[warp][lane];
-        int fb = 0;
-        if (c < g.nc) {
-            int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
-            float f[12], dthdz;
-            cl_features(g, mb, v, ph.g, i, j, k, f, dthdz);
-            for (int q = 0; q < 12; ++q) {
-                float z = (f[q] - in_mu[q]) / in_sd[q];
-                if (!(fabsf(z) <= 6.f)) fb = 1;
-                sF[warp][lane][q] = z;
+    const float *in_mu = sst, *in_rsd = sst + 12, *out_mu = sst + 24, *out_sd = sst + 33;
+    const float rPr = (float)(1.0 / ph.Pr_t);
+    const int gr = lane >> 2, tc = lane & 3;   // fragment coordinates: row, column pair
+    const long long ntiles = (g.nc + 31) / 32;
+    for (long long tile = (long long)blockIdx.x * CLW + warp; tile < ntiles; tile += (long long)gridDim.x * CLW) {
+        const long long c0 = tile * 32;
+        // 1. features of 32 cells (one per lane), standardised; fallback flag on |z| > 6
+        {
+            long long c = c0 + lane;
+            float *m = sMisc[warp][lane];
+            int fb = 0;
+            if (c < g.nc) {
+                unsigned row = (unsigned)(c / g.nx);
+                int i = (int)(c - (long long)row * g.nx);
+                int j = (int)(row % (unsigned)g.ny), k = (int)(row / (unsigned)g.ny);
+                float f[12], dthdz;
+                cl_features(g, mb, v, i, j, k, f, dthdz);
+                for (int q = 0; q < 12; ++q) {
+                    float z = (f[q] - in_mu[q]) * in_rsd[q];
+                    if (!(fabsf(z) <= 6.f)) fb = 1;
+                    sF[warp][lane][q] = z;
+                }
+                // Smagorinsky fallback at the cell centre
+                float s11 = f[0], s22 = f[4], s33 = f[8];
+                float s12 = 0.5f * (f[1] + f[3]), s13 = 0.5f * (f[2] + f[6]), s23 = 0.5f * (f[5] + f[7]);
+                float rho = mb.rho0f[k] + dr[c];
+                float SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.f * (s12 * s12 + s13 * s13 + s23 * s23);
+                float mu = rho * mb.delta2f[k] * sqrtf(2.f * SS);
+                float tr = (s11 + s22 + s33) * (1.f / 3.f);
+                m[0] = -2.f * mu * (s11 - tr); m[1] = -2.f * mu * (s22 - tr); m[2] = -2.f * mu * (s33 - tr);
+                m[3] = -2.f * mu * s12; m[4] = -2.f * mu * s13; m[5] = -2.f * mu * s23;
+                m[6] = -mu * rPr * f[9]; m[7] = -mu * rPr * f[10]; m[8] = -mu * rPr * dthdz;
+                m[9] = rho;
+            } else {
+                for (int q = 0; q < 12; ++q) sF[warp][lane][q] = 0.f;
+                m[9] = 0.f;
             }
-            // Smagorinsky fallback at the cell centre
-            float s11 = f[0], s22 = f[4], s33 = f[8];
-            float s12 = 0.5f * (f[1] + f[3]), s13 = 0.5f * (f[2] + f[6]), s23 = 0.5f * (f[5] + f[7]);
-            float rho = mb.rho0f[k] + dr[c];
-            float SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.f * (s12 * s12 + s13 * s13 + s23 * s23);
-            float mu = rho * mb.delta2f[k] * sqrtf(2.f * SS);
-            float tr = (s11 + s22 + s33) * (1.f / 3.f);
-            m[0] = -2.f * mu * (s11 - tr); m[1] = -2.f * mu * (s22 - tr); m[2] = -2.f * mu * (s33 - tr);
-            m[3] = -2.f * mu * s12; m[4] = -2.f * mu * s13; m[5] = -2.f * mu * s23;
-            float rPr = (float)(1.0 / ph.Pr_t);
-            m[6] = -mu * rPr * f[9]; m[7] = -mu * rPr * f[10]; m[8] = -mu * rPr * dthdz;
-            m[9] = rho;
-        } else {
-            for (int q = 0; q < 12; ++q) sF[warp][lane][q] = 0.f;
-            m[9] = 0.f;
+            for (int q = 12; q < 16; ++q) sF[warp][lane][q] = 0.f;
+            m[10] = (float)fb;
         }
-        for (int q = 12; q < 16; ++q) sF[warp][lane][q] = 0.f;
-        m[10] = (float)fb;
-    }
-    __syncwarp();
-    // 2. MLP on tensor cores.  Fragment coordinates: gr = lane/4 (row), tc = lane%4.
-    const int gr = lane >> 2, tc = lane & 3;
-    unsigned a[2][4][4];   // [m-tile][k-tile][reg]
-    for (int mt = 0; mt < 2; ++mt) {
-        const float *r0 = sF[warp][mt * 16 + gr], *r1 = sF[warp][mt * 16 + gr + 8];
-        a[mt][0][0] = pack_bf16(r0[2 * tc], r0[2 * tc + 1]);
-        a[mt][0][1] = pack_bf16(r1[2 * tc], r1[2 * tc + 1]);
-        a[mt][0][2] = pack_bf16(r0[2 * tc + 8], r0[2 * tc + 9]);
-        a[mt][0][3] = pack_bf16(r1[2 * tc + 8], r1[2 * tc + 9]);
-    }
-    auto hidden = [&](int woff, int ldw, int nkt, const float *bias) {
-        float acc[2][8][4];
-        for (int nt = 0; nt < 8; ++nt) {
+        __syncwarp();
+        // 2. MLP on tensor cores
+        unsigned a[2][4][4];   // [m-tile][k-tile][reg]
+        for (int mt = 0; mt < 2; ++mt) {
+            const float *r0 = sF[warp][mt * 16 + gr], *r1 = sF[warp][mt * 16 + gr + 8];
+            a[mt][0][0] = pack_bf16(r0[2 * tc], r0[2 * tc + 1]);
+            a[mt][0][1] = pack_bf16(r1[2 * tc], r1[2 * tc + 1]);
+            a[mt][0][2] = pack_bf16(r0[2 * tc + 8], r0[2 * tc + 9]);
+            a[mt][0][3] = pack_bf16(r1[2 * tc + 8], r1[2 * tc + 9]);
+        }
+        auto hidden = [&](int woff, int ldw, int nkt, const float *bias) {
+            float acc[2][8][4];
+            for (int nt = 0; nt < 8; ++nt) {
+                float bl = bias[nt * 8 + 2 * tc], bh = bias[nt * 8 + 2 * tc + 1];
+                for (int mt = 0; mt < 2; ++mt) {
+                    acc[mt][nt][0] = bl; acc[mt][nt][1] = bh; acc[mt][nt][2] = bl; acc[mt][nt][3] = bh;
+                }
+                const __nv_bfloat16 *wr = sW + woff + (nt * 8 + gr) * ldw;
+                for (int kt = 0; kt < nkt; ++kt) {
+                    unsigned b0 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc);
+                    unsigned b1 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc + 8);
+                    mma16816(acc[0][nt], a[0][kt], b0, b1);
+                    mma16816(acc[1][nt], a[1][kt], b0, b1);
+                }
+            }
             for (int mt = 0; mt < 2; ++mt)
-                for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
-            const __nv_bfloat16 *wr = sW + woff + (nt * 8 + gr) * ldw;
-            for (int kt = 0; kt < nkt; ++kt) {
+                for (int kt = 0; kt < 4; ++kt) {
+                    const float *lo = acc[mt][2 * kt], *hi = acc[mt][2 * kt + 1];
+                    a[mt][kt][0] = pack_bf16(silu_dev(lo[0]), silu_dev(lo[1]));
+                    a[mt][kt][1] = pack_bf16(silu_dev(lo[2]), silu_dev(lo[3]));
+                    a[mt][kt][2] = pack_bf16(silu_dev(hi[0]), silu_dev(hi[1]));
+                    a[mt][kt][3] = pack_bf16(silu_dev(hi[2]), silu_dev(hi[3]));
+                }
+        };
+        hidden(SW_W1, LD1, 1, sb);
+        hidden(SW_W2, LDH, 4, sb + 64);
+        hidden(SW_W3, LDH, 4, sb + 128);
+        // output layer: 2 n-tiles of 8 (9 valid columns)
+        float y[2][2][4];
+        for (int nt = 0; nt < 2; ++nt) {
+            float bl = sb[192 + nt * 8 + 2 * tc], bh = sb[192 + nt * 8 + 2 * tc + 1];
+            for (int mt = 0; mt < 2; ++mt) {
+                y[mt][nt][0] = bl; y[mt][nt][1] = bh; y[mt][nt][2] = bl; y[mt][nt][3] = bh;
+            }
+            const __nv_bfloat16 *wr = sW + SW_W4 + (nt * 8 + gr) * LDH;
+            for (int kt = 0; kt < 4; ++kt) {
                 unsigned b0 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc);
                 unsigned b1 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc + 8);
-                mma16816(acc[0][nt], a[0][kt], b0, b1);
-                mma16816(acc[1][nt], a[1][kt], b0, b1);
+                mma16816(y[0][nt], a[0][kt], b0, b1);
+                mma16816(y[1][nt], a[1][kt], b0, b1);
             }
         }
+        __syncwarp();
         for (int mt = 0; mt < 2; ++mt)
-            for (int kt = 0; kt < 4; ++kt) {
-                const float *lo = acc[mt][2 * kt], *hi = acc[mt][2 * kt + 1];
-                int c_lo = kt * 16 + 2 * tc, c_hi = c_lo + 8;
-                a[mt][kt][0] = pack_bf16(silu_dev(lo[0] + bias[c_lo]), silu_dev(lo[1] + bias[c_lo + 1]));
-                a[mt][kt][1] = pack_bf16(silu_dev(lo[2] + bias[c_lo]), silu_dev(lo[3] + bias[c_lo + 1]));
-                a[mt][kt][2] = pack_bf16(silu_dev(hi[0] + bias[c_hi]), silu_dev(hi[1] + bias[c_hi + 1]));
-                a[mt][kt][3] = pack_bf16(silu_dev(hi[2] + bias[c_hi]), silu_dev(hi[3] + bias[c_hi + 1]));
+            for (int nt = 0; nt < 2; ++nt) {
+                int col = nt * 8 + 2 * tc;
+                float *r0 = sF[warp][mt * 16 + gr], *r1 = sF[warp][mt * 16 + gr + 8];
+                r0[col] = y[mt][nt][0];
+                r0[col + 1] = y[mt][nt][1];
+                r1[col] = y[mt][nt][2];
+                r1[col + 1] = y[mt][nt][3];
             }
-    };
-    hidden(SW_W1, LD1, 1, sb);
-    hidden(SW_W2, LDH, 4, sb + 64);
-    hidden(SW_W3, LDH, 4, sb + 128);
-    // output layer: 2 n-tiles of 8 (9 valid columns)
-    float y[2][2][4];
-    for (int nt = 0; nt < 2; ++nt) {
-        for (int mt = 0; mt < 2; ++mt)
-            for (int q = 0; q < 4; ++q) y[mt][nt][q] = 0.f;
-        const __nv_bfloat16 *wr = sW + SW_W4 + (nt * 8 + gr) * LDH;
-        for (int kt = 0; kt < 4; ++kt) {
-            unsigned b0 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc);
-            unsigned b1 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc + 8);
-            mma16816(y[0][nt], a[0][kt], b0, b1);
-            mma16816(y[1][nt], a[1][kt], b0, b1);
-        }
-    }
-    __syncwarp();
-    for (int mt = 0; mt < 2; ++mt)
-        for (int nt = 0; nt < 2; ++nt) {
-            int col = nt * 8 + 2 * tc;
-            float *r0 = sF[warp][mt * 16 + gr], *r1 = sF[warp][mt * 16 + gr + 8];
-            r0[col] = y[mt][nt][0] + sb[192 + col];
-            r0[col + 1] = y[mt][nt][1] + sb[192 + col + 1];
-            r1[col] = y[mt][nt][2] + sb[192 + col];
-            r1[col + 1] = y[mt][nt][3] + sb[192 + col + 1];
-        }
-    __syncwarp();
-    // 3. de-standardise, fallback, density weighting, store (one cell per lane, coalesced)
-    {
-        long long c = c0 + lane;
-        if (c < g.nc) {
-            const float *m = sMisc[warp][lane];
-            int use_fb = m[10] != 0.f;
-            float o[9];
-            for (int q = 0; q < 9; ++q) {
-                o[q] = sF[warp][lane][q] * out_sd[q] + out_mu[q];
-                if (!isfinite(o[q])) use_fb = 1;
+        __syncwarp();
+        // 3. de-standardise, fallback, density weighting, store (one cell per lane, coalesced)
+        {
+            long long c = c0 + lane;
+            if (c < g.nc) {
+                const float *m = sMisc[warp][lane];
+                int use_fb = m[10] != 0.f;
+                float o[9];
+                for (int q = 0; q < 9; ++q) {
+                    o[q] = sF[warp][lane][q] * out_sd[q] + out_mu[q];
+                    if (!isfinite(o[q])) use_fb = 1;
+                }
+                float rho = m[9];
+                for (int q = 0; q < 9; ++q) out[(long long)q * g.nc + c] = use_fb ? m[q] : rho * o[q];
+                if (use_fb && nfallback) atomicAdd(nfallback, 1u);
             }
-            float rho = m[9];
-            for (int q = 0; q < 9; ++q) out[(long long)q * g.nc + c] = use_fb ? m[q] : rho * o[q];
-            if (use_fb && nfallback) atomicAdd(nfallback, 1u);
         }
+        __syncwarp();
     }
 }
 
@@ -243,7 +260,7 @@ __global__ void k_cl_features(Geo g, MxBase mb, VelIn v, double grav, float *out
     if (c >= g.nc) return;
     int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
     float f[12], d;
-    cl_features(g, mb, v, grav, i, j, k, f, d);
+    cl_features(g, mb, v, i, j, k, f, d);
     for (int q = 0; q < 12; ++q) out[c * 12 + q] = f[q];
 }
 
@@ -323,8 +340,18 @@ void cl_infer(const Geo &g, const MxBase &mb, const Phys &ph, const void *w_bf16
               const float *dr, float *out, unsigned *nfb, cudaStream_t s) {
     const __nv_bfloat16 *w = (const __nv_bfloat16 *)w_bf16;
     ClDev cl{w, w + 1024, w + 1024 + 4096, w + 1024 + 8192, b, stats};
-    long long nwarps = (g.nc + 31) / 32;
-    unsigned nblk = (unsigned)((nwarps + CLW - 1) / CLW);
+    // persistent grid: as many resident blocks as fit on the device, each looping over tiles
+    static int dev_blocks = 0;
+    if (dev_blocks == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cl_infer, CLW * 32, 0);
+        dev_blocks = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    long long ntiles = (g.nc + 31) / 32;
+    long long need = (ntiles + CLW - 1) / CLW;
+    unsigned nblk = (unsigned)(need < dev_blocks ? need : dev_blocks);
     mx_launch("mx_closure_mlp", s, [&] {
         k_cl_infer<<<nblk, CLW * 32, 0, s>>>(g, mb, ph, cl, VelIn{ux, vy, wz, thp}, dr, out, nfb);
     });

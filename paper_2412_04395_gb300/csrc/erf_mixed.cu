@@ -38,7 +38,7 @@ __device__ __forceinline__ float wvalf(const Geo &g, const float *f, int i, int 
 __device__ __forceinline__ float dth0(const MxBase &mb, int ka, int kb) { return mx_dth0(mb, ka, kb); }
 
 // ------------------------------------------------------------------ per-level base tables
-__global__ void k_mx_base(Geo g, double Cs, double dx, double dy, float *f32, double *rt0) {
+__global__ void k_mx_base(Geo g, double Cs, double dx, double dy, double grav, float *f32, double *rt0) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     int L = g.nz + 1;
     if (k > g.nz) return;
@@ -55,8 +55,13 @@ __global__ void k_mx_base(Geo g, double Cs, double dx, double dy, float *f32, do
         f32[9 * L + k] = (float)((Cs * Delta) * (Cs * Delta));
         rt0[k] = r0 * t0;
     }
-    if (k < g.nz)
+    if (k < g.nz) {
         for (int o = -3; o <= 3; ++o) f32[10 * L + k * 7 + o + 3] = (float)(g.th0[kref(k + o, g.nz)] - g.th0[k]);
+        float *tail = f32 + 10 * L + 7 * g.nz;
+        tail[k] = (float)(grav / g.th0[k]);
+        int kl = k > 0 ? k - 1 : 0, ku = k < g.nz - 1 ? k + 1 : g.nz - 1;
+        tail[L + k] = ku > kl ? (float)(1.0 / (g.zetac[ku] - g.zetac[kl])) : 0.f;
+    }
     double rw = (k == 0) ? g.rho0[0] : (k == g.nz ? g.rho0[g.nz - 1] : 0.5 * (g.rho0[k - 1] + g.rho0[k]));
     f32[5 * L + k] = (float)rw;
     f32[8 * L + k] = (k >= 1 && k < g.nz) ? (float)(1.0 / g.dzc[k]) : 0.f;
@@ -577,99 +582,137 @@ __global__ void k_mx_tri_build(Geo g, MxBase mb, Phys ph, const float *dr, const
     }
 }
 
-__device__ __forceinline__ float ttilf(const Geo &g, const float *Xt, const float *Tp, float bd, int i, int j, int k) {
-    long long a = cixw(g, i, j, k);
-    float x = __ldg(Xt + a);
-    return x + bd * (x - __ldg(Tp + a));
-}
-__global__ void k_mx_sub_horiz(Geo g, Phys ph, const float *pi, const float *Xt, const float *Tp, const float *Ru,
+// Theta~ (Theta'' forward-weighted by divergence damping) is held in Tt: the stage start sets it
+// to Theta'' and every vertical update leaves Theta~ for the next substep there.
+__global__ void k_mx_sub_horiz(Geo g, Phys ph, const float *pi, const float *Tt, const float *Ru,
                                const float *Rv, float *Xu, float *Xv, float dtau) {
-    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c >= g.nc) return;
-    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
-    float bd = (float)ph.beta_d;
-    float t0 = ttilf(g, Xt, Tp, bd, i, j, k);
-    float gx = (t0 - ttilf(g, Xt, Tp, bd, i - 1, j, k)) * (float)g.rdx;
-    float gy = (t0 - ttilf(g, Xt, Tp, bd, i, j - 1, k)) * (float)g.rdy;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long c = ((long long)k * g.ny + j) * g.nx + i;
+    const long long oxm = i > 0 ? -1 : g.nx - 1;
+    const long long oym = j > 0 ? -(long long)g.nx : (long long)(g.ny - 1) * g.nx;
+    float t0 = __ldg(Tt + c);
+    float gx = (t0 - __ldg(Tt + c + oxm)) * (float)g.rdx;
+    float gy = (t0 - __ldg(Tt + c + oym)) * (float)g.rdy;
     const float gRd = (float)(GAMMA * RD);
     float pic = pi[c];
-    float pix = 0.5f * (fval(g, pi, i - 1, j, k) + pic);
-    float piy = 0.5f * (fval(g, pi, i, j - 1, k) + pic);
+    float pix = 0.5f * (__ldg(pi + c + oxm) + pic);
+    float piy = 0.5f * (__ldg(pi + c + oym) + pic);
     Xu[c] += dtau * (-gRd * pix * gx + Ru[c]);
     Xv[c] += dtau * (-gRd * piy * gy + Rv[c]);
 }
 
-// Per column: explicit parts, right-hand side and the Theta'', rho'' updates in FP32; the
-// forward elimination and back substitution with the stage LU factors in FP64 (d' held in the
-// FP64 scratch dbuf).
-__global__ void k_mx_sub_vert(Geo g, MxBase mb, Phys ph, TriM tr, const float *thp, const float *Rr, const float *Rt,
-                              const float *Rw, F5f x, float *Om, float *Tp, double *dbuf, double dtau) {
-    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (n >= g.nxy) return;
-    int i = (int)(n % g.nx), j = (int)(n / g.nx);
-    const int nz = g.nz;
+// theta at w-face kf relative to theta0 of cell kc (small numbers), from the FP32 table of
+// base-state differences and the perturbation theta' of the two cells around the face
+__device__ __forceinline__ float mx_thw_rel(const MxBase &mb, const float *thp, long long c0, long long nxy, int nz,
+                                            int kf, int kc) {
+    int ka = kref(kf - 1, nz), kb = kref(kf, nz);
+    return 0.5f * (dth0(mb, ka, kc) + dth0(mb, kb, kc)) + 0.5f * (__ldg(thp + c0 + ka * nxy) + __ldg(thp + c0 + kb * nxy));
+}
+
+// Vertical acoustic update, part 1 (one thread per cell): explicit Theta*, rho* from the new
+// U'', V'' divergence and the beta_1 part of the old Omega'' flux (App. C rows 3-4), and the
+// beta-weighted X0 = b1 Theta''^tau + b2 Theta*, Y0 = b1 rho''^tau + b2 rho* that enter the
+// Omega'' rows.  Theta''^tau is kept in Tt for the divergence damping of the next substep.
+__global__ void k_mx_sub_expl(Geo g, MxBase mb, Phys ph, const float *thp, const float *Rr, const float *Rt,
+                              F5f x, const float *Om, float *Tt, float *X0o, float *Y0o, float dtf) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z, nz = g.nz;
+    const long long nxy = g.nxy;
+    const long long c0 = (long long)j * g.nx + i, c = c0 + k * nxy;
+    const long long oxp = i + 1 < g.nx ? 1 : 1 - g.nx, oxm = i > 0 ? -1 : g.nx - 1;
+    const long long oyp = j + 1 < g.ny ? (long long)g.nx : (long long)g.nx - nxy;
+    const long long oym = j > 0 ? -(long long)g.nx : nxy - g.nx;
     const float b1 = (float)(0.5 * (1.0 - ph.beta_s)), b2 = (float)(0.5 * (1.0 + ph.beta_s));
-    const float dtf = (float)dtau, Gg = (float)(dtau * 0.5 * ph.g);
     const float rdx = (float)g.rdx, rdy = (float)g.rdy;
-    // theta at w-face kf relative to theta0 of cell kc (small numbers)
-    auto thw_rel = [&](int kf, int kc) -> float {
-        int ka = kref(kf - 1, nz), kb = kref(kf, nz);
-        return 0.5f * (dth0(mb, ka, kc) + dth0(mb, kb, kc)) + 0.5f * (thp[cix(g, i, j, ka)] + thp[cix(g, i, j, kb)]);
-    };
-    float X0m = 0.f, Y0m = 0.f;
+    float om_k = k >= 1 ? Om[c] : 0.f;
+    float om_p = k + 1 < nz ? Om[c + nxy] : 0.f;
+    float Uc = x.u[c], Up = x.u[c + oxp], Vc = x.v[c], Vp = x.v[c + oyp];
+    float tc = __ldg(thp + c);
+    float thxm = 0.5f * (__ldg(thp + c + oxm) + tc), thxp = 0.5f * (tc + __ldg(thp + c + oxp));
+    float thym = 0.5f * (__ldg(thp + c + oym) + tc), thyp = 0.5f * (tc + __ldg(thp + c + oyp));
+    float dz = mb.dzf[k], rH = mb.rdzf[k];
+    float divM = dz * ((Up - Uc) * rdx + (Vp - Vc) * rdy);
+    float divTp = dz * ((Up * thxp - Uc * thxm) * rdx + (Vp * thyp - Vc * thym) * rdy);
+    float th0k = mb.th0f[k];
+    float wk_rel = k == 0 ? 0.f : mx_thw_rel(mb, thp, c0, nxy, nz, k, k);
+    float wp_rel = k + 1 >= nz ? 0.f : mx_thw_rel(mb, thp, c0, nxy, nz, k + 1, k);
+    float vflux_rel = om_p * wp_rel - om_k * wk_rel;
+    float xt = x.t[c], xr = x.r[c];
+    float vdiv = om_p - om_k;
+    float Ts = xt + dtf * (-(th0k * divM + divTp) * rH - b1 * (th0k * vdiv + vflux_rel) * rH + Rt[c]);
+    float Rs = xr + dtf * (-divM * rH - b1 * vdiv * rH + Rr[c]);
+    Tt[c] = xt;
+    x.t[c] = Ts;
+    x.r[c] = Rs;
+    X0o[c] = b1 * xt + b2 * Ts;
+    Y0o[c] = b1 * xr + b2 * Rs;
+}
+
+// Part 2 (one thread per column): the Omega'' rows' right-hand side, forward elimination with the
+// stage LU factors and back substitution, in FP64 (d' in the FP64 scratch dbuf); W'' = Omega''.
+// Only the two recurrences are serial; every load is independent of them, so the unrolled loop
+// keeps several levels of loads in flight.
+__global__ void __launch_bounds__(128) k_mx_sub_col(int nz, long long nxy, const double *__restrict__ ta,
+                                                    const double *__restrict__ tcp, const double *__restrict__ tim,
+                                                    const float *__restrict__ tP, const float *__restrict__ tQ,
+                                                    const float *__restrict__ X0, const float *__restrict__ Y0,
+                                                    const float *__restrict__ Rw, float *__restrict__ W,
+                                                    float *__restrict__ Om, double *__restrict__ dbuf, float dtf,
+                                                    float Gg) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= nxy) return;
     double dpm = 0.0;
-    float om_k = 0.f;
-    for (int k = 0; k < nz; ++k) {
-        long long c = cix(g, i, j, k);
-        float om_p = (k + 1 < nz) ? Om[c + g.nxy] : 0.f;
-        long long cxp = cixw(g, i + 1, j, k), cyp = cixw(g, i, j + 1, k);
-        float Uc = x.u[c], Up = x.u[cxp], Vc = x.v[c], Vp = x.v[cyp];
-        float tc = thp[c];
-        float thxm = 0.5f * (fval(g, thp, i - 1, j, k) + tc), thxp = 0.5f * (tc + fval(g, thp, i + 1, j, k));
-        float thym = 0.5f * (fval(g, thp, i, j - 1, k) + tc), thyp = 0.5f * (tc + fval(g, thp, i, j + 1, k));
-        float dz = mb.dzf[k], rH = mb.rdzf[k];
-        float divM = dz * ((Up - Uc) * rdx + (Vp - Vc) * rdy);
-        float divTp = dz * ((Up * thxp - Uc * thxm) * rdx + (Vp * thyp - Vc * thym) * rdy);
-        float th0k = mb.th0f[k];
-        float wk_rel = (k == 0) ? 0.f : thw_rel(k, k), wp_rel = (k + 1 >= nz) ? 0.f : thw_rel(k + 1, k);
-        float vflux_rel = om_p * wp_rel - om_k * wk_rel;
-        float xt = x.t[c], xr = x.r[c];
-        Tp[c] = xt;
-        float vdiv = om_p - om_k;
-        float Ts = xt + dtf * (-(th0k * divM + divTp) * rH - b1 * (th0k * vdiv + vflux_rel) * rH + Rt[c]);
-        float Rs = xr + dtf * (-divM * rH - b1 * vdiv * rH + Rr[c]);
-        x.t[c] = Ts;
-        x.r[c] = Rs;
-        float X0 = b1 * xt + b2 * Ts, Y0 = b1 * xr + b2 * Rs;
-        if (k >= 1) {
-            float rhs = x.w[c] + dtf * Rw[c] + tr.P[c] * X0 + tr.Q[c] * X0m - Gg * (Y0 + Y0m);
-            double dp = ((double)rhs - tr.a[c] * dpm) * tr.im[c];
-            dbuf[c] = dp;
-            dpm = dp;
-        }
-        X0m = X0; Y0m = Y0;
-        om_k = om_p;
+    float X0m = X0[n], Y0m = Y0[n];
+#pragma unroll 4
+    for (int k = 1; k < nz; ++k) {
+        long long c = n + k * nxy;
+        float X0c = X0[c], Y0c = Y0[c];
+        float rhs = W[c] + dtf * Rw[c] + tP[c] * X0c + tQ[c] * X0m - Gg * (Y0c + Y0m);
+        double dp = ((double)rhs - ta[c] * dpm) * tim[c];
+        dbuf[c] = dp;
+        dpm = dp;
+        X0m = X0c; Y0m = Y0c;
     }
-    x.w[cix(g, i, j, nz)] = 0.f;
-    Om[cix(g, i, j, nz)] = 0.f;
+    long long top = n + nz * nxy;
+    W[top] = 0.f;
+    Om[top] = 0.f;
     double om_up = 0.0;
-    float omf_up = 0.f;
-    for (int k = nz - 1; k >= 0; --k) {
-        long long c = cix(g, i, j, k);
-        double om = 0.0;
-        if (k >= 1) om = dbuf[c] - tr.cp[c] * om_up;
+#pragma unroll 4
+    for (int k = nz - 1; k >= 1; --k) {
+        long long c = n + k * nxy;
+        double om = dbuf[c] - tcp[c] * om_up;
         float omf = (float)om;
-        float th0k = mb.th0f[k];
-        float wk_rel = (k == 0) ? 0.f : thw_rel(k, k);
-        float wp_rel = (k + 1 >= nz) ? thw_rel(nz, k) : thw_rel(k + 1, k);
-        float db = dtf * b2 * mb.rdzf[k];
-        x.t[c] -= db * (th0k * (omf_up - omf) + (omf_up * wp_rel - omf * wk_rel));
-        x.r[c] -= db * (omf_up - omf);
-        x.w[c] = omf;
+        W[c] = omf;
         Om[c] = omf;
         om_up = om;
-        omf_up = omf;
     }
+    W[n] = 0.f;
+    Om[n] = 0.f;
+}
+
+// Part 3 (one thread per cell): Theta'', rho'' from the new Omega'' (App. C rows 3-4, beta_2
+// part) and Theta~ of the next substep.
+__global__ void k_mx_sub_fin(Geo g, MxBase mb, Phys ph, const float *thp, const float *Om, F5f x, float *Tt,
+                             float dtf) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z, nz = g.nz;
+    const long long nxy = g.nxy;
+    const long long c0 = (long long)j * g.nx + i, c = c0 + k * nxy;
+    const float b2 = (float)(0.5 * (1.0 + ph.beta_s)), bd = (float)ph.beta_d;
+    float omf = Om[c], omf_up = Om[c + nxy];
+    float th0k = mb.th0f[k];
+    float wk_rel = k == 0 ? 0.f : mx_thw_rel(mb, thp, c0, nxy, nz, k, k);
+    float wp_rel = mx_thw_rel(mb, thp, c0, nxy, nz, k + 1 >= nz ? nz : k + 1, k);
+    float db = dtf * b2 * mb.rdzf[k];
+    float xt = x.t[c] - db * (th0k * (omf_up - omf) + (omf_up * wp_rel - omf * wk_rel));
+    x.t[c] = xt;
+    x.r[c] -= db * (omf_up - omf);
+    float told = Tt[c];
+    Tt[c] = xt + bd * (xt - told);
 }
 
 __global__ void k_mx_stage_end(Geo g, F5f st, CF5f x) {
@@ -725,8 +768,8 @@ __global__ void k_mx_diag_partial(Geo g, MxBase mb, CF5f st, double *part) {
 static inline unsigned nb(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 constexpr int MBS = 256;
 
-void mx_build_base(const Geo &g, double Cs, double dx, double dy, float *f32, double *rt0, cudaStream_t s) {
-    k_mx_base<<<nb(g.nz + 1, 128), 128, 0, s>>>(g, Cs, dx, dy, f32, rt0);
+void mx_build_base(const Geo &g, double Cs, double dx, double dy, double grav, float *f32, double *rt0, cudaStream_t s) {
+    k_mx_base<<<nb(g.nz + 1, 128), 128, 0, s>>>(g, Cs, dx, dy, grav, f32, rt0);
 }
 void mx_set_initial(const Geo &g, const double *dth, const double *u, const double *v, const double *w, F5f st,
                     cudaStream_t s) {
@@ -778,13 +821,20 @@ void mx_tri_build(const Geo &g, const MxBase &mb, const Phys &ph, const float *d
     mx_launch("mx_tri_build", s, [&] { k_mx_tri_build<<<nb(g.nxy, 128), 128, 0, s>>>(g, mb, ph, dr, dT, pi, thp, dtau, tr); });
 }
 void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, TriM tr, const float *pi, const float *thp, CF5f R,
-                F5f x, float *Om, float *Tp, double *dbuf, double dtau, cudaStream_t s) {
+                F5f x, float *Om, float *Tt, double *dbuf, float *X0, float *Y0, double dtau, cudaStream_t s) {
+    const dim3 blk(128), grd((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)g.nz);
+    const float dtf = (float)dtau, Gg = (float)(dtau * 0.5 * ph.g);
     mx_launch("mx_sub_horiz", s, [&] {
-        k_mx_sub_horiz<<<nb(g.nc, MBS), MBS, 0, s>>>(g, ph, pi, x.t, Tp, R.u, R.v, x.u, x.v, (float)dtau);
+        k_mx_sub_horiz<<<grd, blk, 0, s>>>(g, ph, pi, Tt, R.u, R.v, x.u, x.v, dtf);
     });
-    mx_launch("mx_sub_vert", s, [&] {
-        k_mx_sub_vert<<<nb(g.nxy, 64), 64, 0, s>>>(g, mb, ph, tr, thp, R.r, R.t, R.w, x, Om, Tp, dbuf, dtau);
+    mx_launch("mx_sub_expl", s, [&] {
+        k_mx_sub_expl<<<grd, blk, 0, s>>>(g, mb, ph, thp, R.r, R.t, x, Om, Tt, X0, Y0, dtf);
     });
+    mx_launch("mx_sub_col", s, [&] {
+        k_mx_sub_col<<<nb(g.nxy, 128), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q, X0, Y0, R.w, x.w, Om,
+                                                    dbuf, dtf, Gg);
+    });
+    mx_launch("mx_sub_fin", s, [&] { k_mx_sub_fin<<<grd, blk, 0, s>>>(g, mb, ph, thp, Om, x, Tt, dtf); });
 }
 void mx_stage_end(const Geo &g, F5f st, CF5f x, cudaStream_t s) {
     mx_launch("mx_stage_end", s, [&] { k_mx_stage_end<<<nb(g.nw, MBS), MBS, 0, s>>>(g, st, x); });

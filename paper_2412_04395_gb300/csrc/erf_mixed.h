@@ -23,6 +23,8 @@ struct MxBase {
     const float *dzf, *rdzf, *rdzcf, *delta2f;        // [nz], [nz], [nz+1], [nz]
     const double *rt0;                                // [nz] rho0 theta0 (FP64)
     const float *dth0t;                               // [nz][7]: theta0(k+o) - theta0(k), o = -3..3, formed in FP64
+    const float *gth0f;                               // [nz] g / theta0
+    const float *r2dzf;                               // [nz] 1/(zc(ku) - zc(kl)), kl = max(k-1,0), ku = min(k+1,nz-1)
 };
 // theta0(ka) - theta0(kb) for |ka - kb| <= 3 (ka reflected at the walls)
 __device__ __forceinline__ float mx_dth0(const MxBase &mb, int ka, int kb) { return mb.dth0t[kb * 7 + (ka - kb) + 3]; }
@@ -68,7 +70,7 @@ void cl_filter_launch(const Geo &g, const MxBase &mb, CF5f st, int r, double *cr
                       double *crv, double *crw, float *targets, cudaStream_t s);
 
 void launch_diag_final(const double *part, int nparts, double dt, double *out, cudaStream_t s);
-void mx_build_base(const Geo &g, double Cs, double dx, double dy, float *f32, double *rt0, cudaStream_t s);
+void mx_build_base(const Geo &g, double Cs, double dx, double dy, double grav, float *f32, double *rt0, cudaStream_t s);
 void mx_set_initial(const Geo &g, const double *dth, const double *u, const double *v, const double *w, F5f st,
                     cudaStream_t s);
 void mx_from_full(const Geo &g, const double *src, float *dst, int field, long long n, cudaStream_t s);
@@ -84,17 +86,19 @@ void mx_slow_prep_only(const Geo &g, const MxBase &mb, CF5f st, float *ux, float
 void mx_tri_build(const Geo &g, const MxBase &mb, const Phys &ph, const float *dr, const float *dT, const float *pi,
                   const float *thp, double dtau, TriM tr, cudaStream_t s);
 void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, TriM tr, const float *pi, const float *thp, CF5f R,
-                F5f x, float *Om, float *Tp, double *dbuf, double dtau, cudaStream_t s);
+                F5f x, float *Om, float *Tt, double *dbuf, float *X0, float *Y0, double dtau, cudaStream_t s);
 void mx_stage_end(const Geo &g, F5f st, CF5f x, cudaStream_t s);
 void mx_diag(const Geo &g, const MxBase &mb, CF5f st, double dt, double *part, double *out, cudaStream_t s);
 
 // layout of the FP32 base table block built by mx_build_base (offsets in floats)
 // tables in order: rho0, theta0, p0, pi0, 1/(rho0 theta0), rho0 at w-faces, dz, 1/dz, 1/dzc, delta^2
-inline int mx_base_floats(int nz) { return 10 * (nz + 1) + 7 * nz; }
+// (nz+1 each), the theta0 differences (7 nz), g/theta0 and the centred 1/dz (nz+1 each)
+inline int mx_base_floats(int nz) { return 12 * (nz + 1) + 7 * nz; }
 inline MxBase mx_base_view(const float *f32, const double *rt0, int nz) {
     int L = nz + 1;
+    const float *tail = f32 + 10 * L + 7 * nz;
     return MxBase{f32, f32 + L, f32 + 2 * L, f32 + 3 * L, f32 + 4 * L, f32 + 5 * L,
-                  f32 + 6 * L, f32 + 7 * L, f32 + 8 * L, f32 + 9 * L, rt0, f32 + 10 * L};
+                  f32 + 6 * L, f32 + 7 * L, f32 + 8 * L, f32 + 9 * L, rt0, f32 + 10 * L, tail, tail + L};
 }
 
 }  // namespace erfk
