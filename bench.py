@@ -37,7 +37,8 @@ UNIT = "cell-updates/s"
 KERNEL_MODEL = {
     "sub_vert":    {"unit": "cell", "words": 20, "flops": 70},
     "sub_horiz":   {"unit": "cell", "words": 9, "flops": 24},
-    "rhs_cells":   {"unit": "cell", "words": 6, "flops": 520},
+    "flux_theta":  {"unit": "wface", "words": 7, "flops": 520},
+    "rhs_cells":   {"unit": "cell", "words": 6, "flops": 20},
     "rhs_u":       {"unit": "cell", "words": 6, "flops": 150},
     "rhs_v":       {"unit": "cell", "words": 6, "flops": 150},
     "rhs_w":       {"unit": "wface", "words": 7, "flops": 160},
@@ -47,7 +48,26 @@ KERNEL_MODEL = {
     "stage_end":   {"unit": "wface", "words": 15, "flops": 5},
     "wall_bc":     {"unit": "none", "words": 0, "flops": 0},
 }
-FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 nominal (profiling recipe table)
+# mixed path: algorithmic bytes per cell per launch (FP32 fields, FP64 LU factors and d');
+# these kernels are bound by HBM or latency, so their roofline is in GB/s
+KERNEL_MODEL_MIXED = {
+    "mx_sub_col":     {"unit": "cell", "bytes": 80},
+    "mx_sub_expl":    {"unit": "cell", "bytes": 52},
+    "mx_sub_fin":     {"unit": "cell", "bytes": 32},
+    "mx_sub_horiz":   {"unit": "cell", "bytes": 32},
+    "mx_closure_mlp": {"unit": "cell", "bytes": 60},
+    "mx_rhs_cells":   {"unit": "cell", "bytes": 56},
+    "mx_rhs_u":       {"unit": "cell", "bytes": 44},
+    "mx_rhs_v":       {"unit": "cell", "bytes": 44},
+    "mx_rhs_w":       {"unit": "wface", "bytes": 40},
+    "mx_tri_build":   {"unit": "cell", "bytes": 60},
+    "mx_stage_begin": {"unit": "wface", "bytes": 60},
+    "mx_prep":        {"unit": "wface", "bytes": 36},
+    "mx_stage_end":   {"unit": "wface", "bytes": 60},
+}
+# FP64 peak from the unit count ncu reports on GB300 (sm__sass_thread_inst_executed_op_dfma_
+# pred_on.sum.peak_sustained = 304 per cycle, 2 per SM) x 2 flop x 2.07 GHz maximum SM clock
+FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
 
 
 def peaks():
@@ -313,19 +333,27 @@ def run_ours(args):
     top = max(prof.items(), key=lambda kv: kv[1][0])
     name, (tms, nl) = top
     hbm, hsrc, pk = peaks()
-    model = KERNEL_MODEL.get(name, {"unit": "cell", "words": 0, "flops": 0})
-    units = {"cell": wl.ncell, "wface": wl.nx * wl.ny * (wl.nz + 1), "none": 0}[model["unit"]]
     avg_s = tms / nl * 1e-3
-    flops = model["flops"] * units
-    bytes_ = 8 * model["words"] * units
-    fp64_gf = flops / avg_s / 1e12
-    hbm_gbs = bytes_ / avg_s / 1e9
-    roof = {"bound": "alu", "achieved": fp64_gf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-            "frac": fp64_gf / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": name,
-            "kernel_avg_ms": tms / nl, "kernel_share": tms / total,
-            "peak_source": "FP64 nominal of the profiling recipe (no measured FP64 peak)",
-            "hbm": {"achieved": hbm_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_gbs / hbm,
-                    "peak_source": hsrc}}
+    if name in KERNEL_MODEL_MIXED:
+        mm = KERNEL_MODEL_MIXED[name]
+        units = {"cell": wl.ncell, "wface": wl.nx * wl.ny * (wl.nz + 1)}[mm["unit"]]
+        gbs = mm["bytes"] * units / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "traffic": None, "kernel": name, "kernel_avg_ms": tms / nl, "kernel_share": tms / total,
+                "peak_source": hsrc}
+    else:
+        model = KERNEL_MODEL.get(name, {"unit": "cell", "words": 0, "flops": 0})
+        units = {"cell": wl.ncell, "wface": wl.nx * wl.ny * (wl.nz + 1), "none": 0}[model["unit"]]
+        flops = model["flops"] * units
+        bytes_ = 8 * model["words"] * units
+        fp64_tf = flops / avg_s / 1e12
+        hbm_gbs = bytes_ / avg_s / 1e9
+        roof = {"bound": "alu", "achieved": fp64_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": fp64_tf / FP64_PEAK_TFLOPS, "traffic": None, "kernel": name,
+                "kernel_avg_ms": tms / nl, "kernel_share": tms / total,
+                "peak_source": "derived: 304 DFMA/cycle (ncu unit count) x 2 flop x 2.07 GHz",
+                "hbm": {"achieved": hbm_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_gbs / hbm,
+                        "peak_source": hsrc}}
 
     # end to end through the C ABI: every step uploads the state from pinned host memory,
     # advances one step and downloads the state

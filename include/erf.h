@@ -64,7 +64,8 @@ typedef enum { ERF_SURFACE_SLIP = 0, ERF_SURFACE_MOST = 1 } erf_surface;
 
 /* Grid (Sec. 3.4, App. A/B).  Host pointers, read during erf_init_grid only. */
 typedef struct {
-    int32_t nx, ny, nz;             /* cells; nx, ny >= 1, 1 <= nz <= ERF_NZ_MAX */
+    int32_t nx, ny, nz;             /* cells; nx >= 1, 1 <= ny <= 65535, 1 <= nz <= ERF_NZ_MAX,
+                                       nx*ny*(nz+1) < 2^31 (else ERF_EINVAL) */
     double dx, dy;                  /* uniform horizontal spacing [m] */
     const double *z_faces;          /* nz+1 flat-column face heights zeta_k, increasing, z_faces[0] = 0 */
     const double *terrain_nodes;    /* ny*nx terrain heights h at nodes (i dx, j dy), or NULL = flat */

@@ -10,7 +10,10 @@ closure follows the readings of the design notes:
   * targets from a Favre 4x4x4 box filter of a fine run:
         rho_bar = <rho>,  u~_i = <rho u_i>/rho_bar,  t_ij = <rho u_i u_j>/rho_bar - u~_i u~_j,
         h_j = <rho u_j theta>/rho_bar - u~_j theta~;
-  * loss: mean squared error on standardised outputs; optimiser Adam (Kingma & Ba 2015).
+  * loss: mean squared error on standardised outputs; optimiser Adam (Kingma & Ba 2015);
+  * at inference, backscatter is limited: where the learned stress transfers energy from the
+    subgrid to the resolved scales at more than half the Smagorinsky dissipation rate
+    (-t_ij S_ij < -0.5 Pi_s), the six stresses are scaled so that -t_ij S_ij = -0.5 Pi_s.
 Everything here is written from those definitions, in plain numpy, independent of the CUDA code.
 """
 from __future__ import annotations
@@ -226,6 +229,44 @@ def box_filter(rho, rt, ru, rv, rw, r=4):
     for j in range(3):
         T[..., 6 + j] = cmean(rho * vel[j] * th) / rb - ut[j] * tht
     return (rb, Rt, Ru, Rv, Rw), T
+
+
+def strain_from_features(F):
+    """Resolved strain-rate components (S11, S22, S33, S12, S13, S23) from the 12 features."""
+    F = np.asarray(F, dtype=np.float64)
+    return np.stack([F[..., 0], F[..., 4], F[..., 8], 0.5 * (F[..., 1] + F[..., 3]),
+                     0.5 * (F[..., 2] + F[..., 6]), 0.5 * (F[..., 5] + F[..., 7])], axis=-1)
+
+
+def smagorinsky_stress(F, delta2):
+    """Kinematic Smagorinsky-Lilly stress -2 nu (S_ij - S_kk delta_ij / 3), nu = delta2 sqrt(2 S:S),
+    delta2 = (Cs Delta)^2 per cell; order 11, 22, 33, 12, 13, 23."""
+    S = strain_from_features(F)
+    SS = S[..., 0] ** 2 + S[..., 1] ** 2 + S[..., 2] ** 2 + 2 * (S[..., 3] ** 2 + S[..., 4] ** 2 + S[..., 5] ** 2)
+    nu = np.asarray(delta2) * np.sqrt(2 * SS)
+    tr = (S[..., 0] + S[..., 1] + S[..., 2]) / 3
+    dev = S.copy()
+    dev[..., :3] -= tr[..., None]
+    return -2 * nu[..., None] * dev
+
+
+def transfer(tau, S):
+    """Resolved-to-subgrid energy transfer -t_ij S_ij of a symmetric stress (6 components)."""
+    return -(tau[..., 0] * S[..., 0] + tau[..., 1] * S[..., 1] + tau[..., 2] * S[..., 2]
+             + 2 * (tau[..., 3] * S[..., 3] + tau[..., 4] * S[..., 4] + tau[..., 5] * S[..., 5]))
+
+
+def clip_backscatter(Y, F, delta2):
+    """Y [n, 9] kinematic learned outputs, F [n, 12] features, delta2 [n]: the six stresses of each
+    cell whose transfer is below -0.5 x the Smagorinsky transfer are scaled onto that bound."""
+    Y = np.array(Y, dtype=np.float64, copy=True)
+    S = strain_from_features(F)
+    pl = transfer(Y[:, :6], S)
+    ps = transfer(smagorinsky_stress(F, delta2), S)
+    lim = -0.5 * ps
+    bad = pl < lim
+    Y[bad, :6] *= (lim[bad] / pl[bad])[:, None]
+    return Y
 
 
 def standardise_stats(A):

@@ -87,6 +87,10 @@ static erf_status cuda_fail(erf_handle *h, cudaError_t e, const char *where) {
 static erf_status validate(const erf_grid_desc *g, const erf_config *c, std::string &msg) {
     if (!g || !c) { msg = "NULL grid or config"; return ERF_EINVAL; }
     if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->nz > ERF_NZ_MAX) { msg = "grid sizes out of range"; return ERF_EINVAL; }
+    if ((long long)g->nx * g->ny * (g->nz + 1) >= (1LL << 31) || g->ny > 65535) {
+        msg = "grid too large: nx*ny*(nz+1) must be below 2^31 and ny at most 65535";
+        return ERF_EINVAL;
+    }
     if (!(g->dx > 0.0) || !(g->dy > 0.0)) { msg = "dx, dy must be positive"; return ERF_EINVAL; }
     if (!g->z_faces) { msg = "z_faces is NULL"; return ERF_EINVAL; }
     if (g->z_faces[0] != 0.0) { msg = "z_faces[0] must be 0"; return ERF_EINVAL; }
@@ -305,6 +309,7 @@ extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config 
     if (h->mixed) {
         mx_build_base(h->geo, cfg->Cs, grid->dx, grid->dy, cfg->gravity, h->mbase, h->mrt0, st);
         h->mb = mx_base_view(h->mbase, h->mrt0, nz);
+        mx_base_scalars(h->mb, h->geo, h->ph);
     }
     CK(cudaGetLastError(), "init kernels");
     CK(cudaStreamSynchronize(st), "init sync");   // host vectors above must outlive the copies

@@ -64,7 +64,7 @@ struct VelIn {
 };
 __device__ void cl_features(const Geo &g, const MxBase &mb, const VelIn &v, int i, int j, int k, float *f,
                             float &dthdz) {
-    const float rdx = (float)g.rdx, rdy = (float)g.rdy;
+    const float rdx = mb.rdx, rdy = mb.rdy;
     const long long nx = g.nx, nxy = g.nxy;
     const long long c = ((long long)k * g.ny + j) * nx + i;
     const long long oxp = i + 1 < g.nx ? 1 : 1 - nx, oxm = i > 0 ? -1 : nx - 1;
@@ -104,7 +104,8 @@ __device__ __forceinline__ void mma16816(float *d, const unsigned *a, unsigned b
 }
 __device__ __forceinline__ float silu_dev(float x) { return __fdividef(x, 1.f + __expf(-x)); }
 
-// Learned SGS stress/heat flux at every cell (mixed path).  Persistent blocks of 4 warps load
+// Learned SGS stress/heat flux at every cell (mixed path), with Smagorinsky as the per-cell
+// fallback and backscatter limited to half the Smagorinsky transfer.  Persistent blocks of 4 warps load
 // the weights into shared memory once and then take 32-cell tiles in turn; each warp runs its
 // tile as two m16 tiles through every layer, reusing each B fragment for both.  The bias is the
 // accumulator's initial value.
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(CLW * 32, 4) k_cl_infer(Geo g, MxBase mb, Phys
     __shared__ float sb[CL_B_F32];
     __shared__ float sst[2 * CL_NIN + 2 * CL_NOUT];   // in_mean, 1/in_std, out_mean, out_std
     __shared__ __align__(16) float sF[CLW][32][17];   // standardised features, then outputs
-    __shared__ float sMisc[CLW][32][11];              // fallback stresses/fluxes, rho, flag
+    __shared__ float sMisc[CLW][32][19];              // fallback stresses/fluxes, rho, flag, S_ij, bound
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int q = tid; q < 64 * 16; q += blockDim.x) sW[SW_W1 + (q / 16) * LD1 + q % 16] = cl.W1[q];
     for (int q = tid; q < 64 * 64; q += blockDim.x) {
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(CLW * 32, 4) k_cl_infer(Geo g, MxBase mb, Phys
         sst[q] = (q >= CL_NIN && q < 2 * CL_NIN) ? 1.f / cl.stats[q] : cl.stats[q];
     __syncthreads();
     const float *in_mu = sst, *in_rsd = sst + 12, *out_mu = sst + 24, *out_sd = sst + 33;
-    const float rPr = (float)(1.0 / ph.Pr_t);
+    const float rPr = mb.rPr;
     const int gr = lane >> 2, tc = lane & 3;   // fragment coordinates: row, column pair
     const long long ntiles = (g.nc + 31) / 32;
     for (long long tile = (long long)blockIdx.x * CLW + warp; tile < ntiles; tile += (long long)gridDim.x * CLW) {
@@ -164,6 +165,11 @@ __global__ void __launch_bounds__(CLW * 32, 4) k_cl_infer(Geo g, MxBase mb, Phys
                 m[3] = -2.f * mu * s12; m[4] = -2.f * mu * s13; m[5] = -2.f * mu * s23;
                 m[6] = -mu * rPr * f[9]; m[7] = -mu * rPr * f[10]; m[8] = -mu * rPr * dthdz;
                 m[9] = rho;
+                m[11] = s11; m[12] = s22; m[13] = s33; m[14] = s12; m[15] = s13; m[16] = s23;
+                // backscatter bound: the learned transfer -t_ij S_ij may not fall below -1/2 of
+                // the Smagorinsky transfer (both density-weighted)
+                float ps = -(m[0] * s11 + m[1] * s22 + m[2] * s33 + 2.f * (m[3] * s12 + m[4] * s13 + m[5] * s23));
+                m[17] = -0.5f * ps;
             } else {
                 for (int q = 0; q < 12; ++q) sF[warp][lane][q] = 0.f;
                 m[9] = 0.f;
@@ -246,7 +252,13 @@ __global__ void __launch_bounds__(CLW * 32, 4) k_cl_infer(Geo g, MxBase mb, Phys
                     if (!isfinite(o[q])) use_fb = 1;
                 }
                 float rho = m[9];
-                for (int q = 0; q < 9; ++q) out[(long long)q * g.nc + c] = use_fb ? m[q] : rho * o[q];
+                for (int q = 0; q < 9; ++q) o[q] *= rho;
+                float pl = -(o[0] * m[11] + o[1] * m[12] + o[2] * m[13] + 2.f * (o[3] * m[14] + o[4] * m[15] + o[5] * m[16]));
+                if (pl < m[17]) {
+                    float a = m[17] / pl;
+                    for (int q = 0; q < 6; ++q) o[q] *= a;
+                }
+                for (int q = 0; q < 9; ++q) out[(long long)q * g.nc + c] = use_fb ? m[q] : o[q];
                 if (use_fb && nfallback) atomicAdd(nfallback, 1u);
             }
         }

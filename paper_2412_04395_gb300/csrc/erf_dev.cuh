@@ -71,25 +71,38 @@ struct Tri {
     double *a, *cp, *im, *P, *Q;
 };
 
-// periodic wrap without integer division (offsets are a few cells; loops only for n < 4)
+// periodic wrap without integer division: one conditional correction covers the stencil
+// offsets used here (|offset| <= 3) once n >= 4; smaller extents loop
 __device__ __forceinline__ int wrapi(int i, int n) {
+    if (n >= 4) {
+        i += i < 0 ? n : 0;
+        i -= i >= n ? n : 0;
+        return i;
+    }
     while (i < 0) i += n;
     while (i >= n) i -= n;
     return i;
 }
-// even reflection of a cell level about the walls (ghost layers below/above the domain)
+// even reflection of a cell level about the walls (ghost layers below/above the domain);
+// one reflection covers k in [-3, nz+2] once nz >= 3
 __device__ __forceinline__ int kref(int k, int nz) {
+    if (nz >= 3) {
+        k = k < 0 ? -1 - k : k;
+        k = k >= nz ? 2 * nz - 1 - k : k;
+        return k;
+    }
     while (k < 0 || k >= nz) {
         if (k < 0) k = -1 - k;
         if (k >= nz) k = 2 * nz - 1 - k;
     }
     return k;
 }
+// linear indices in 32-bit arithmetic (grids are limited to fewer than 2^31 w-face points)
 __device__ __forceinline__ long long cix(const Geo &g, int i, int j, int k) {
-    return ((long long)k * g.ny + j) * g.nx + i;
+    return (long long)((k * g.ny + j) * g.nx + i);
 }
 __device__ __forceinline__ long long cixw(const Geo &g, int i, int j, int k) {
-    return ((long long)k * g.ny + wrapi(j, g.ny)) * g.nx + wrapi(i, g.nx);
+    return (long long)((k * g.ny + wrapi(j, g.ny)) * g.nx + wrapi(i, g.nx));
 }
 // cell value, periodic in x/y, reflected in z
 __device__ __forceinline__ double cval(const Geo &g, const double *f, int i, int j, int k) {

@@ -116,9 +116,10 @@ __global__ void k_mx_wall_bc(Geo g, float *rw) {
 // ------------------------------------------------------------------ stage begin (EOS, X'')
 __global__ void k_mx_stage_begin(Geo g, MxBase mb, CF5f sn, CF5f st, F5f x, float *pp, float *pi, float *thp,
                                  float *Tp, float *Om) {
-    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (n >= g.nw) return;
-    int k = (int)(n / g.nxy);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int k = blockIdx.z;
+    const long long n = ((long long)k * g.ny + blockIdx.y) * g.nx + i;
     if (k < g.nz) {
         float dr = st.r[n], dT = st.t[n];
         float xr = dT * mb.rrt0f[k];                 // dTh / (rho0 theta0)
@@ -139,9 +140,10 @@ __global__ void k_mx_stage_begin(Geo g, MxBase mb, CF5f sn, CF5f st, F5f x, floa
 }
 
 __global__ void k_mx_prep(Geo g, MxBase mb, CF5f st, float *ux, float *vy, float *wz, float *mfx, float *mfy) {
-    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (n >= g.nw) return;
-    int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / g.nxy);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long n = ((long long)k * g.ny + j) * g.nx + i;
     if (k < g.nz) {
         float dr = st.r[n], r0 = mb.rho0f[k], dz = mb.dzf[k];
         float ru = st.u[n], rv = st.v[n];
@@ -161,42 +163,43 @@ __global__ void k_mx_prep(Geo g, MxBase mb, CF5f st, float *ux, float *vy, float
 struct VelF {
     const float *ux, *vy, *wz;
 };
-__device__ __forceinline__ float S12f(const Geo &g, const VelF &v, int i, int j, int k) {
-    return 0.5f * ((fval(g, v.ux, i, j, k) - fval(g, v.ux, i, j - 1, k)) * (float)g.rdy
-                 + (fval(g, v.vy, i, j, k) - fval(g, v.vy, i - 1, j, k)) * (float)g.rdx);
+__device__ __forceinline__ float S12f(const Geo &g, const MxBase &mb, const VelF &v, int i, int j, int k) {
+    return 0.5f * ((fval(g, v.ux, i, j, k) - fval(g, v.ux, i, j - 1, k)) * mb.rdy
+                 + (fval(g, v.vy, i, j, k) - fval(g, v.vy, i - 1, j, k)) * mb.rdx);
 }
 __device__ __forceinline__ float S13f(const Geo &g, const MxBase &mb, const VelF &v, int i, int j, int k) {
     if (k <= 0 || k >= g.nz) return 0.f;
     return 0.5f * ((fval(g, v.ux, i, j, k) - fval(g, v.ux, i, j, k - 1)) * mb.rdzcf[k]
-                 + (__ldg(v.wz + cixw(g, i, j, k)) - __ldg(v.wz + cixw(g, i - 1, j, k))) * (float)g.rdx);
+                 + (__ldg(v.wz + cixw(g, i, j, k)) - __ldg(v.wz + cixw(g, i - 1, j, k))) * mb.rdx);
 }
 __device__ __forceinline__ float S23f(const Geo &g, const MxBase &mb, const VelF &v, int i, int j, int k) {
     if (k <= 0 || k >= g.nz) return 0.f;
     return 0.5f * ((fval(g, v.vy, i, j, k) - fval(g, v.vy, i, j, k - 1)) * mb.rdzcf[k]
-                 + (__ldg(v.wz + cixw(g, i, j, k)) - __ldg(v.wz + cixw(g, i, j - 1, k))) * (float)g.rdy);
+                 + (__ldg(v.wz + cixw(g, i, j, k)) - __ldg(v.wz + cixw(g, i, j - 1, k))) * mb.rdy);
 }
 __device__ __forceinline__ void diagSf(const Geo &g, const MxBase &mb, const VelF &v, int i, int j, int k, float &a,
                                        float &b, float &c) {
-    a = (fval(g, v.ux, i + 1, j, k) - fval(g, v.ux, i, j, k)) * (float)g.rdx;
-    b = (fval(g, v.vy, i, j + 1, k) - fval(g, v.vy, i, j, k)) * (float)g.rdy;
+    a = (fval(g, v.ux, i + 1, j, k) - fval(g, v.ux, i, j, k)) * mb.rdx;
+    b = (fval(g, v.vy, i, j + 1, k) - fval(g, v.vy, i, j, k)) * mb.rdy;
     c = (__ldg(v.wz + cixw(g, i, j, k + 1)) - __ldg(v.wz + cixw(g, i, j, k))) * mb.rdzf[k];
 }
 __global__ void k_mx_sgs_mu(Geo g, MxBase mb, Phys ph, VelF v, const float *dr, float *mu) {
-    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c >= g.nc) return;
-    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long c = ((long long)k * g.ny + j) * g.nx + i;
     float rho = mb.rho0f[k] + dr[c];
     float m = 0.f;
     if (ph.closure == 2) {
         float s11, s22, s33;
         diagSf(g, mb, v, i, j, k, s11, s22, s33);
-        float s12 = 0.25f * (S12f(g, v, i, j, k) + S12f(g, v, i + 1, j, k) + S12f(g, v, i, j + 1, k) + S12f(g, v, i + 1, j + 1, k));
+        float s12 = 0.25f * (S12f(g, mb, v, i, j, k) + S12f(g, mb, v, i + 1, j, k) + S12f(g, mb, v, i, j + 1, k) + S12f(g, mb, v, i + 1, j + 1, k));
         float s13 = 0.25f * (S13f(g, mb, v, i, j, k) + S13f(g, mb, v, i + 1, j, k) + S13f(g, mb, v, i, j, k + 1) + S13f(g, mb, v, i + 1, j, k + 1));
         float s23 = 0.25f * (S23f(g, mb, v, i, j, k) + S23f(g, mb, v, i, j + 1, k) + S23f(g, mb, v, i, j, k + 1) + S23f(g, mb, v, i, j + 1, k + 1));
         float SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.f * (s12 * s12 + s13 * s13 + s23 * s23);
         m = rho * mb.delta2f[k] * sqrtf(2.f * SS);
     } else if (ph.closure == 1) {
-        m = rho * (float)ph.nu;
+        m = rho * mb.nu;
     }
     mu[c] = m;
 }
@@ -208,9 +211,9 @@ __device__ __forceinline__ float tauDf(const Geo &g, const MxBase &mb, const Vel
     float s = comp == 0 ? a : (comp == 1 ? b : c);
     return -2.f * fval(g, mu, i, j, k) * (s - dv);
 }
-__device__ __forceinline__ float tau12f(const Geo &g, const VelF &v, const float *mu, int i, int j, int k) {
+__device__ __forceinline__ float tau12f(const Geo &g, const MxBase &mb, const VelF &v, const float *mu, int i, int j, int k) {
     float me = 0.25f * (fval(g, mu, i - 1, j - 1, k) + fval(g, mu, i, j - 1, k) + fval(g, mu, i - 1, j, k) + fval(g, mu, i, j, k));
-    return -2.f * me * S12f(g, v, i, j, k);
+    return -2.f * me * S12f(g, mb, v, i, j, k);
 }
 __device__ float ustar_f(float U, float z1, float z0, float Q, float theta, float grav) {
     float lz = logf(z1 / z0);
@@ -243,7 +246,7 @@ __device__ float tau13f(const Geo &g, const MxBase &mb, const Phys &ph, const Ve
         if (!(U > 0.f)) return 0.f;
         float thf = mb.th0f[0] + 0.5f * (fval(g, thp, i - 1, j, 0) + fval(g, thp, i, j, 0));
         float rhf = mb.rho0f[0] + 0.5f * (fval(g, dr, i - 1, j, 0) + fval(g, dr, i, j, 0));
-        float us = ustar_f(U, 0.5f * mb.dzf[0], (float)ph.z0, (float)ph.Qs, thf, (float)ph.g);
+        float us = ustar_f(U, 0.5f * mb.dzf[0], mb.z0, mb.Qs, thf, mb.grav);
         return -rhf * us * us * u / U;
     }
     if (k >= g.nz || !visc) return 0.f;
@@ -260,7 +263,7 @@ __device__ float tau23f(const Geo &g, const MxBase &mb, const Phys &ph, const Ve
         if (!(U > 0.f)) return 0.f;
         float thf = mb.th0f[0] + 0.5f * (fval(g, thp, i, j - 1, 0) + fval(g, thp, i, j, 0));
         float rhf = mb.rho0f[0] + 0.5f * (fval(g, dr, i, j - 1, 0) + fval(g, dr, i, j, 0));
-        float us = ustar_f(U, 0.5f * mb.dzf[0], (float)ph.z0, (float)ph.Qs, thf, (float)ph.g);
+        float us = ustar_f(U, 0.5f * mb.dzf[0], mb.z0, mb.Qs, thf, mb.grav);
         return -rhf * us * us * vv / U;
     }
     if (k >= g.nz || !visc) return 0.f;
@@ -291,10 +294,11 @@ struct PrepF {
 // theta0_k); the first sums to theta0_k R_rho.
 __global__ void k_mx_rhs_cells(Geo g, MxBase mb, Phys ph, PrepF pr, const float *rw, const float *thp,
                                const float *dr, const float *mu, int sgs, float *Rr, float *Rt) {
-    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c >= g.nc) return;
-    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
-    float rdx = (float)g.rdx, rdy = (float)g.rdy, rH = mb.rdzf[k];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long c = ((long long)k * g.ny + j) * g.nx + i;
+    float rdx = mb.rdx, rdy = mb.rdy, rH = mb.rdzf[k];
     float mxm = pr.mfx[c], mxp = __ldg(pr.mfx + cixw(g, i + 1, j, k));
     float mym = pr.mfy[c], myp = __ldg(pr.mfy + cixw(g, i, j + 1, k));
     float omm = (k == 0) ? 0.f : __ldg(rw + cix(g, i, j, k));
@@ -339,7 +343,7 @@ __global__ void k_mx_rhs_cells(Geo g, MxBase mb, Phys ph, PrepF pr, const float 
     if (sgs) {
         int visc = ph.closure == 1 || ph.closure == 2;
         float hd = 0.f;
-        float rPr = (float)(1.0 / ph.Pr_t);
+        float rPr = mb.rPr;
         if (visc) {
             float tc = thp[c];
             float hxm = 0.5f * (fval(g, mu, i - 1, j, k) + mu[c]) * rPr * (tc - fval(g, thp, i - 1, j, k)) * rdx;
@@ -349,7 +353,7 @@ __global__ void k_mx_rhs_cells(Geo g, MxBase mb, Phys ph, PrepF pr, const float 
             hd += (hxp - hxm) * rdx + (hyp - hym) * rdy;
         }
         auto hz = [&](int kf) -> float {
-            if (kf == 0) return ph.surface == 1 ? -(mb.rho0f[0] + dr[cix(g, i, j, 0)]) * (float)ph.Qs : 0.f;
+            if (kf == 0) return ph.surface == 1 ? -(mb.rho0f[0] + dr[cix(g, i, j, 0)]) * mb.Qs : 0.f;
             if (kf >= g.nz || !visc) return 0.f;
             float dth = dth0(mb, kf, kf - 1) + (fval(g, thp, i, j, kf) - fval(g, thp, i, j, kf - 1));
             return 0.5f * (fval(g, mu, i, j, kf - 1) + fval(g, mu, i, j, kf)) * rPr * dth * mb.rdzcf[kf];
@@ -363,7 +367,7 @@ __global__ void k_mx_rhs_cells(Geo g, MxBase mb, Phys ph, PrepF pr, const float 
         float qxp = 0.5f * (tl(g, t, 6, i, j, k) + tl(g, t, 6, i + 1, j, k));
         float qym = 0.5f * (tl(g, t, 7, i, j - 1, k) + tl(g, t, 7, i, j, k));
         float qyp = 0.5f * (tl(g, t, 7, i, j, k) + tl(g, t, 7, i, j + 1, k));
-        float qzm = k == 0 ? (ph.surface == 1 ? (mb.rho0f[0] + dr[c]) * (float)ph.Qs : 0.f)
+        float qzm = k == 0 ? (ph.surface == 1 ? (mb.rho0f[0] + dr[c]) * mb.Qs : 0.f)
                            : 0.5f * (tl(g, t, 8, i, j, k - 1) + tl(g, t, 8, i, j, k));
         float qzp = k == g.nz - 1 ? 0.f : 0.5f * (tl(g, t, 8, i, j, k) + tl(g, t, 8, i, j, k + 1));
         r -= (qxp - qxm) * rdx + (qyp - qym) * rdy + (qzp - qzm) * rH;
@@ -373,10 +377,11 @@ __global__ void k_mx_rhs_cells(Geo g, MxBase mb, Phys ph, PrepF pr, const float 
 
 __global__ void k_mx_rhs_u(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const float *pp, const float *thp,
                            const float *mu, int sgs, float *Ru) {
-    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c >= g.nc) return;
-    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
-    float rdx = (float)g.rdx, rdy = (float)g.rdy, rH = mb.rdzf[k];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long c = ((long long)k * g.ny + j) * g.nx + i;
+    float rdx = mb.rdx, rdy = mb.rdy, rH = mb.rdzf[k];
     float q[6], F[2];
     for (int s = 0; s < 2; ++s) {
         int ic = i - 1 + s;
@@ -403,10 +408,10 @@ __global__ void k_mx_rhs_u(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const f
     div += F[1] - F[0];
     float r = -div * rH;
     r -= (pp[c] - fval(g, pp, i - 1, j, k)) * rdx;
-    if (ph.f_cor != 0.0) {
+    if (mb.f_cor != 0.f) {
         float rvx = 0.25f * (fval(g, st.v, i - 1, j, k) + fval(g, st.v, i, j, k) + fval(g, st.v, i - 1, j + 1, k) + fval(g, st.v, i, j + 1, k));
         float rhx = mb.rho0f[k] + 0.5f * (fval(g, st.r, i - 1, j, k) + st.r[c]);
-        r += (float)ph.f_cor * (rvx - rhx * (float)ph.v_g);
+        r += mb.f_cor * (rvx - rhx * mb.v_g);
     }
     if (sgs) {
         int visc = ph.closure == 1 || ph.closure == 2;
@@ -414,7 +419,7 @@ __global__ void k_mx_rhs_u(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const f
         float d = 0.f;
         if (visc)
             d += (tauDf(g, mb, v, mu, i, j, k, 0) - tauDf(g, mb, v, mu, i - 1, j, k, 0)) * rdx
-               + (tau12f(g, v, mu, i, j + 1, k) - tau12f(g, v, mu, i, j, k)) * rdy;
+               + (tau12f(g, mb, v, mu, i, j + 1, k) - tau12f(g, mb, v, mu, i, j, k)) * rdy;
         d += (tau13f(g, mb, ph, v, mu, st.r, thp, i, j, k + 1, visc) - tau13f(g, mb, ph, v, mu, st.r, thp, i, j, k, visc)) * rH;
         r -= d;
     }
@@ -431,10 +436,11 @@ __global__ void k_mx_rhs_u(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const f
 
 __global__ void k_mx_rhs_v(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const float *pp, const float *thp,
                            const float *mu, int sgs, float *Rv) {
-    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c >= g.nc) return;
-    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
-    float rdx = (float)g.rdx, rdy = (float)g.rdy, rH = mb.rdzf[k];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long c = ((long long)k * g.ny + j) * g.nx + i;
+    float rdx = mb.rdx, rdy = mb.rdy, rH = mb.rdzf[k];
     float q[6], F[2];
     for (int s = 0; s < 2; ++s) {
         int ii = i + s;
@@ -461,17 +467,17 @@ __global__ void k_mx_rhs_v(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const f
     div += F[1] - F[0];
     float r = -div * rH;
     r -= (pp[c] - fval(g, pp, i, j - 1, k)) * rdy;
-    if (ph.f_cor != 0.0) {
+    if (mb.f_cor != 0.f) {
         float rux = 0.25f * (fval(g, st.u, i, j - 1, k) + fval(g, st.u, i + 1, j - 1, k) + fval(g, st.u, i, j, k) + fval(g, st.u, i + 1, j, k));
         float rhy = mb.rho0f[k] + 0.5f * (fval(g, st.r, i, j - 1, k) + st.r[c]);
-        r -= (float)ph.f_cor * (rux - rhy * (float)ph.u_g);
+        r -= mb.f_cor * (rux - rhy * mb.u_g);
     }
     if (sgs) {
         int visc = ph.closure == 1 || ph.closure == 2;
         VelF v{pr.ux, pr.vy, pr.wz};
         float d = 0.f;
         if (visc)
-            d += (tau12f(g, v, mu, i + 1, j, k) - tau12f(g, v, mu, i, j, k)) * rdx
+            d += (tau12f(g, mb, v, mu, i + 1, j, k) - tau12f(g, mb, v, mu, i, j, k)) * rdx
                + (tauDf(g, mb, v, mu, i, j, k, 1) - tauDf(g, mb, v, mu, i, j - 1, k, 1)) * rdy;
         d += (tau23f(g, mb, ph, v, mu, st.r, thp, i, j, k + 1, visc) - tau23f(g, mb, ph, v, mu, st.r, thp, i, j, k, visc)) * rH;
         r -= d;
@@ -489,11 +495,12 @@ __global__ void k_mx_rhs_v(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const f
 
 __global__ void k_mx_rhs_w(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const float *pp, const float *thp,
                            const float *mu, int sgs, float *Rw) {
-    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (n >= g.nw) return;
-    int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / g.nxy);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long n = ((long long)k * g.ny + j) * g.nx + i;
     if (k == 0 || k == g.nz) { Rw[n] = 0.f; return; }
-    float rdx = (float)g.rdx, rdy = (float)g.rdy, rdzc = mb.rdzcf[k];
+    float rdx = mb.rdx, rdy = mb.rdy, rdzc = mb.rdzcf[k];
     float q[6], F[2];
     for (int s = 0; s < 2; ++s) {
         int ii = i + s;
@@ -521,7 +528,7 @@ __global__ void k_mx_rhs_w(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const f
     float r = -div * rdzc;
     long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1);
     r -= (pp[c] - pp[cm]) * rdzc;
-    r += -0.5f * (float)ph.g * (st.r[cm] + st.r[c]);
+    r += -0.5f * mb.grav * (st.r[cm] + st.r[c]);
     if (sgs && (ph.closure == 1 || ph.closure == 2)) {
         VelF v{pr.ux, pr.vy, pr.wz};
         float d = (tau13f(g, mb, ph, v, mu, st.r, thp, i + 1, j, k, 1) - tau13f(g, mb, ph, v, mu, st.r, thp, i, j, k, 1)) * rdx
@@ -546,24 +553,24 @@ __global__ void k_mx_tri_build(Geo g, MxBase mb, Phys ph, const float *dr, const
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= g.nxy) return;
     int i = (int)(n % g.nx), j = (int)(n / g.nx);
-    const float b2 = (float)(0.5 * (1.0 + ph.beta_s));
+    const float b2 = mb.b2;
     const float dtf = (float)dtau;
-    const float E = dtf * b2 * b2, Gg = dtf * 0.5f * (float)ph.g;
-    const float gRd = (float)(GAMMA * RD), gRc = (float)(ph.g * (RD / CVD));
+    const float E = dtf * b2 * b2, Gg = dtf * 0.5f * mb.grav;
+    const float gRd = (float)(GAMMA * RD), gRc = mb.grav * (float)(RD / CVD);
     double cp_prev = 0.0;
     // theta at the w-faces below/above cell k, relative to theta0_k, plus theta0_k
     auto thw = [&](int kf) -> float {   // full theta at w-face kf (kf in 0..nz), FP32
         int ka = kref(kf - 1, g.nz), kb = kref(kf, g.nz);
         return 0.5f * (mb.th0f[ka] + mb.th0f[kb]) + 0.5f * (thp[cix(g, i, j, ka)] + thp[cix(g, i, j, kb)]);
     };
-    float rrt_m = 1.f / ((float)mb.rt0[0] + dT[cix(g, i, j, 0)]);
+    float rrt_m = 1.f / (mb.rho0f[0] * mb.th0f[0] + dT[cix(g, i, j, 0)]);
     float thw_m = thw(0), thw_k = thw(1);
     for (int k = 1; k < g.nz; ++k) {
         long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1);
         float pic = pi[c], pim = pi[cm];
         float pib = 0.5f * (pim + pic), rpib = 1.f / pib;
         float rhob = mb.rhowf[k] + 0.5f * (dr[cm] + dr[c]);
-        float rrt_c = 1.f / ((float)mb.rt0[k] + dT[c]);
+        float rrt_c = 1.f / (mb.rho0f[k] * mb.th0f[k] + dT[c]);
         float Cpg = gRd * pib * mb.rdzcf[k];
         float gb = gRc * rhob * 0.5f * rpib;
         float P = dtf * (-Cpg + gb * pic * rrt_c), Q = dtf * (Cpg + gb * pim * rrt_m);
@@ -584,7 +591,7 @@ __global__ void k_mx_tri_build(Geo g, MxBase mb, Phys ph, const float *dr, const
 
 // Theta~ (Theta'' forward-weighted by divergence damping) is held in Tt: the stage start sets it
 // to Theta'' and every vertical update leaves Theta~ for the next substep there.
-__global__ void k_mx_sub_horiz(Geo g, Phys ph, const float *pi, const float *Tt, const float *Ru,
+__global__ void k_mx_sub_horiz(Geo g, MxBase mb, const float *pi, const float *Tt, const float *Ru,
                                const float *Rv, float *Xu, float *Xv, float dtau) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
@@ -593,8 +600,8 @@ __global__ void k_mx_sub_horiz(Geo g, Phys ph, const float *pi, const float *Tt,
     const long long oxm = i > 0 ? -1 : g.nx - 1;
     const long long oym = j > 0 ? -(long long)g.nx : (long long)(g.ny - 1) * g.nx;
     float t0 = __ldg(Tt + c);
-    float gx = (t0 - __ldg(Tt + c + oxm)) * (float)g.rdx;
-    float gy = (t0 - __ldg(Tt + c + oym)) * (float)g.rdy;
+    float gx = (t0 - __ldg(Tt + c + oxm)) * mb.rdx;
+    float gy = (t0 - __ldg(Tt + c + oym)) * mb.rdy;
     const float gRd = (float)(GAMMA * RD);
     float pic = pi[c];
     float pix = 0.5f * (__ldg(pi + c + oxm) + pic);
@@ -625,8 +632,8 @@ __global__ void k_mx_sub_expl(Geo g, MxBase mb, Phys ph, const float *thp, const
     const long long oxp = i + 1 < g.nx ? 1 : 1 - g.nx, oxm = i > 0 ? -1 : g.nx - 1;
     const long long oyp = j + 1 < g.ny ? (long long)g.nx : (long long)g.nx - nxy;
     const long long oym = j > 0 ? -(long long)g.nx : nxy - g.nx;
-    const float b1 = (float)(0.5 * (1.0 - ph.beta_s)), b2 = (float)(0.5 * (1.0 + ph.beta_s));
-    const float rdx = (float)g.rdx, rdy = (float)g.rdy;
+    const float b1 = mb.b1, b2 = mb.b2;
+    const float rdx = mb.rdx, rdy = mb.rdy;
     float om_k = k >= 1 ? Om[c] : 0.f;
     float om_p = k + 1 < nz ? Om[c + nxy] : 0.f;
     float Uc = x.u[c], Up = x.u[c + oxp], Vc = x.v[c], Vp = x.v[c + oyp];
@@ -702,7 +709,7 @@ __global__ void k_mx_sub_fin(Geo g, MxBase mb, Phys ph, const float *thp, const 
     const int j = blockIdx.y, k = blockIdx.z, nz = g.nz;
     const long long nxy = g.nxy;
     const long long c0 = (long long)j * g.nx + i, c = c0 + k * nxy;
-    const float b2 = (float)(0.5 * (1.0 + ph.beta_s)), bd = (float)ph.beta_d;
+    const float b2 = mb.b2, bd = mb.bd;
     float omf = Om[c], omf_up = Om[c + nxy];
     float th0k = mb.th0f[k];
     float wk_rel = k == 0 ? 0.f : mx_thw_rel(mb, thp, c0, nxy, nz, k, k);
@@ -766,6 +773,9 @@ __global__ void k_mx_diag_partial(Geo g, MxBase mb, CF5f st, double *part) {
 
 // ------------------------------------------------------------------ launchers
 static inline unsigned nb(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+// 3D launch over cells (nzl = nz) or w-faces (nzl = nz + 1): x covers i, y = j, z = k
+constexpr int MBX = 128;
+static inline dim3 g3(const Geo &g, int nzl) { return dim3((unsigned)((g.nx + MBX - 1) / MBX), (unsigned)g.ny, (unsigned)nzl); }
 constexpr int MBS = 256;
 
 void mx_build_base(const Geo &g, double Cs, double dx, double dy, double grav, float *f32, double *rt0, cudaStream_t s) {
@@ -788,17 +798,17 @@ void mx_wall_bc(const Geo &g, float *rw, cudaStream_t s) {
 void mx_stage_begin(const Geo &g, const MxBase &mb, CF5f sn, CF5f st, F5f x, float *pp, float *pi, float *thp,
                     float *Tp, float *Om, cudaStream_t s) {
     mx_launch("mx_stage_begin", s, [&] {
-        k_mx_stage_begin<<<nb(g.nw, MBS), MBS, 0, s>>>(g, mb, sn, st, x, pp, pi, thp, Tp, Om);
+        k_mx_stage_begin<<<g3(g, g.nz + 1), MBX, 0, s>>>(g, mb, sn, st, x, pp, pi, thp, Tp, Om);
     });
 }
 void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const float *pp, const float *thp,
                  float *ux, float *vy, float *wz, float *mfx, float *mfy, float *mu, F5f R, cudaStream_t s,
                  const ClIn *cl) {
-    mx_launch("mx_prep", s, [&] { k_mx_prep<<<nb(g.nw, MBS), MBS, 0, s>>>(g, mb, st, ux, vy, wz, mfx, mfy); });
+    mx_launch("mx_prep", s, [&] { k_mx_prep<<<g3(g, g.nz + 1), MBX, 0, s>>>(g, mb, st, ux, vy, wz, mfx, mfy); });
     int learned = ph.closure == 3 && cl;
     int sgs = (ph.closure == 1 || ph.closure == 2 || (ph.surface == 1 && !learned)) ? 1 : 0;
     if (ph.closure == 1 || ph.closure == 2)
-        mx_launch("mx_sgs_mu", s, [&] { k_mx_sgs_mu<<<nb(g.nc, MBS), MBS, 0, s>>>(g, mb, ph, VelF{ux, vy, wz}, st.r, mu); });
+        mx_launch("mx_sgs_mu", s, [&] { k_mx_sgs_mu<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, VelF{ux, vy, wz}, st.r, mu); });
     const float *tau = nullptr;
     if (learned) {
         cl_infer(g, mb, ph, cl->w, cl->b, cl->stats, ux, vy, wz, thp, st.r, cl->out, cl->nfb, s);
@@ -806,15 +816,15 @@ void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const 
     }
     PrepF pr{ux, vy, wz, mfx, mfy, tau};
     mx_launch("mx_rhs_cells", s, [&] {
-        k_mx_rhs_cells<<<nb(g.nc, MBS), MBS, 0, s>>>(g, mb, ph, pr, st.w, thp, st.r, mu, sgs, R.r, R.t);
+        k_mx_rhs_cells<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, pr, st.w, thp, st.r, mu, sgs, R.r, R.t);
     });
-    mx_launch("mx_rhs_u", s, [&] { k_mx_rhs_u<<<nb(g.nc, MBS), MBS, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, R.u); });
-    mx_launch("mx_rhs_v", s, [&] { k_mx_rhs_v<<<nb(g.nc, MBS), MBS, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, R.v); });
-    mx_launch("mx_rhs_w", s, [&] { k_mx_rhs_w<<<nb(g.nw, MBS), MBS, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, R.w); });
+    mx_launch("mx_rhs_u", s, [&] { k_mx_rhs_u<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, R.u); });
+    mx_launch("mx_rhs_v", s, [&] { k_mx_rhs_v<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, R.v); });
+    mx_launch("mx_rhs_w", s, [&] { k_mx_rhs_w<<<g3(g, g.nz + 1), MBX, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, R.w); });
 }
 void mx_slow_prep_only(const Geo &g, const MxBase &mb, CF5f st, float *ux, float *vy, float *wz, float *mfx,
                        float *mfy, cudaStream_t s) {
-    k_mx_prep<<<nb(g.nw, MBS), MBS, 0, s>>>(g, mb, st, ux, vy, wz, mfx, mfy);
+    k_mx_prep<<<g3(g, g.nz + 1), MBX, 0, s>>>(g, mb, st, ux, vy, wz, mfx, mfy);
 }
 void mx_tri_build(const Geo &g, const MxBase &mb, const Phys &ph, const float *dr, const float *dT, const float *pi,
                   const float *thp, double dtau, TriM tr, cudaStream_t s) {
@@ -825,7 +835,7 @@ void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, TriM tr, const f
     const dim3 blk(128), grd((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)g.nz);
     const float dtf = (float)dtau, Gg = (float)(dtau * 0.5 * ph.g);
     mx_launch("mx_sub_horiz", s, [&] {
-        k_mx_sub_horiz<<<grd, blk, 0, s>>>(g, ph, pi, Tt, R.u, R.v, x.u, x.v, dtf);
+        k_mx_sub_horiz<<<grd, blk, 0, s>>>(g, mb, pi, Tt, R.u, R.v, x.u, x.v, dtf);
     });
     mx_launch("mx_sub_expl", s, [&] {
         k_mx_sub_expl<<<grd, blk, 0, s>>>(g, mb, ph, thp, R.r, R.t, x, Om, Tt, X0, Y0, dtf);

@@ -25,7 +25,17 @@ struct MxBase {
     const float *dth0t;                               // [nz][7]: theta0(k+o) - theta0(k), o = -3..3, formed in FP64
     const float *gth0f;                               // [nz] g / theta0
     const float *r2dzf;                               // [nz] 1/(zc(ku) - zc(kl)), kl = max(k-1,0), ku = min(k+1,nz-1)
+    // FP32 copies of the scalar parameters, converted once on the host: a double-to-float
+    // conversion per thread would occupy GB300's FP64 pipe (1/64 of the FP32 rate)
+    float rdx, rdy, grav, f_cor, u_g, v_g, nu, z0, Qs, rPr, b1, b2, bd;
 };
+// fills the scalar members from the grid and the physics parameters (host)
+inline void mx_base_scalars(MxBase &mb, const Geo &g, const Phys &ph) {
+    mb.rdx = (float)g.rdx; mb.rdy = (float)g.rdy; mb.grav = (float)ph.g; mb.f_cor = (float)ph.f_cor;
+    mb.u_g = (float)ph.u_g; mb.v_g = (float)ph.v_g; mb.nu = (float)ph.nu; mb.z0 = (float)ph.z0; mb.Qs = (float)ph.Qs;
+    mb.rPr = (float)(1.0 / ph.Pr_t); mb.b1 = (float)(0.5 * (1.0 - ph.beta_s)); mb.b2 = (float)(0.5 * (1.0 + ph.beta_s));
+    mb.bd = (float)ph.beta_d;
+}
 // theta0(ka) - theta0(kb) for |ka - kb| <= 3 (ka reflected at the walls)
 __device__ __forceinline__ float mx_dth0(const MxBase &mb, int ka, int kb) { return mb.dth0t[kb * 7 + (ka - kb) + 3]; }
 
@@ -98,7 +108,8 @@ inline MxBase mx_base_view(const float *f32, const double *rt0, int nz) {
     int L = nz + 1;
     const float *tail = f32 + 10 * L + 7 * nz;
     return MxBase{f32, f32 + L, f32 + 2 * L, f32 + 3 * L, f32 + 4 * L, f32 + 5 * L,
-                  f32 + 6 * L, f32 + 7 * L, f32 + 8 * L, f32 + 9 * L, rt0, f32 + 10 * L, tail, tail + L};
+                  f32 + 6 * L, f32 + 7 * L, f32 + 8 * L, f32 + 9 * L, rt0, f32 + 10 * L, tail, tail + L,
+                  0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 }
 
 }  // namespace erfk

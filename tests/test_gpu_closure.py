@@ -154,9 +154,12 @@ def test_bf16_inference_matches_oracle():
     Z = (fo.reshape(-1, 12) - mu) / sd
     assert nfb == int(np.sum(np.any(np.abs(Z) > 6.0, axis=1)))
     rho = st["rho"].reshape(-1)
+    dz = np.diff(wl.zeta)
+    d2 = ((wl.Cs * np.cbrt(wl.dx * wl.dy * dz)) ** 2)[:, None, None] * np.ones(fo.shape[:3])
     for bf, tol in ((True, 5e-3), (False, 3e-2)):
         Y, _ = M.forward(p, Z, bf16_inputs=bf)
-        ref = (rho[:, None] * (Y * osd + omu)).T.reshape(tau.shape)
+        Yk = M.clip_backscatter(Y * osd + omu, fo.reshape(-1, 12), d2.reshape(-1))
+        ref = (rho[:, None] * Yk).T.reshape(tau.shape)
         ok = ~np.any(np.abs(Z) > 6.0, axis=1).reshape(tau.shape[1:])
         for q in range(9):
             e = _rel(tau[q][ok], ref[q][ok])

@@ -138,3 +138,37 @@ def test_features_second_order_on_smooth_fields():
         e2 = np.max(np.abs(f[..., 9] + k * np.sin(k * xc)[None, None, :]))       # dtheta/dx
         errs.append(max(e1, e2))
     assert np.log2(errs[0] / errs[1]) > 1.9 and np.log2(errs[1] / errs[2]) > 1.9
+
+
+def test_backscatter_clip_closed_form():
+    """Pure strain S11 = 1, S22 = -1 with (Cs Delta)^2 = 1: Smagorinsky nu = 2, transfer 8, so the
+    bound is -4.  A learned stress c S (transfer -2c) is scaled by 4/(2c) when 2c > 4 and left alone
+    otherwise; forward scatter and the heat fluxes are never touched."""
+    F = np.zeros((4, 12))
+    F[:, 0], F[:, 4] = 1.0, -1.0
+    c = np.array([10.0, 1.0, -10.0, 3.0])
+    Y = np.zeros((4, 9))
+    Y[:, 0], Y[:, 1] = c, -c
+    Y[:, 6:] = [[0.1, 0.2, 0.3]] * 4
+    out = M.clip_backscatter(Y, F, np.ones(4))
+    S = M.strain_from_features(F)
+    assert np.allclose(M.transfer(M.smagorinsky_stress(F, np.ones(4)), S), 8.0)
+    np.testing.assert_allclose(out[0, :2], [2.0, -2.0])
+    np.testing.assert_allclose(out[1:3], Y[1:3])
+    np.testing.assert_allclose(out[3, :2], [4.0 / 6.0 * 3.0, -4.0 / 6.0 * 3.0])
+    np.testing.assert_allclose(out[:, 6:], Y[:, 6:])
+
+
+def test_backscatter_clip_bound_holds_for_random_stresses():
+    rng = np.random.default_rng(5)
+    F = rng.normal(size=(500, 12))
+    d2 = rng.uniform(0.1, 2.0, size=500)
+    Y = rng.normal(size=(500, 9)) * 3
+    out = M.clip_backscatter(Y, F, d2)
+    S = M.strain_from_features(F)
+    lim = -0.5 * M.transfer(M.smagorinsky_stress(F, d2), S)
+    t_in, t_out = M.transfer(Y[:, :6], S), M.transfer(out[:, :6], S)
+    assert np.all(t_out >= lim - 1e-12 * np.abs(lim))
+    keep = t_in >= lim
+    np.testing.assert_array_equal(out[keep], Y[keep])
+    assert np.any(~keep)
