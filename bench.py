@@ -35,19 +35,28 @@ UNIT = "cell-updates/s"
 # if every input is read once and every output written once, and the floating-point operations
 # of the formulas (FMA = 2).  unit: "cell" (nx*ny*nz) or "wface" (nx*ny*(nz+1)).
 KERNEL_MODEL = {
-    "sub_vert":    {"unit": "cell", "words": 20, "flops": 70},
-    "sub_horiz":   {"unit": "cell", "words": 9, "flops": 24},
-    "flux_theta":  {"unit": "wface", "words": 7, "flops": 520},
+    "flux_theta":  {"unit": "wface", "words": 7, "flops": 225},
+    "sub_expl":    {"unit": "cell", "words": 18, "flops": 67},
+    "sub_col":     {"unit": "cell", "words": 11, "flops": 12},
+    "sub_fin":     {"unit": "cell", "words": 10, "flops": 18},
+    "sub_horiz":   {"unit": "cell", "words": 9, "flops": 26},
+    "flux_u":      {"unit": "wface", "words": 7, "flops": 63},
+    "flux_v":      {"unit": "wface", "words": 7, "flops": 63},
+    "flux_w":      {"unit": "wface", "words": 7, "flops": 63},
     "rhs_cells":   {"unit": "cell", "words": 6, "flops": 20},
-    "rhs_u":       {"unit": "cell", "words": 6, "flops": 150},
-    "rhs_v":       {"unit": "cell", "words": 6, "flops": 150},
-    "rhs_w":       {"unit": "wface", "words": 7, "flops": 160},
+    "rhs_u":       {"unit": "cell", "words": 6, "flops": 25},
+    "rhs_v":       {"unit": "cell", "words": 6, "flops": 25},
+    "rhs_w":       {"unit": "wface", "words": 7, "flops": 25},
     "stage_begin": {"unit": "wface", "words": 20, "flops": 60},
     "prep":        {"unit": "wface", "words": 10, "flops": 40},
-    "tri_build":   {"unit": "cell", "words": 9, "flops": 90},
+    "tri_build":   {"unit": "cell", "words": 11, "flops": 90},
     "stage_end":   {"unit": "wface", "words": 15, "flops": 5},
     "wall_bc":     {"unit": "none", "words": 0, "flops": 0},
 }
+# DRAM bytes per unit from an ncu capture of the kernel as it stands (dram__bytes_read.sum +
+# dram__bytes_write.sum of a 128^3 hill-bubble launch / its units; profiles/ has the summary),
+# scaled to the benchmark's units.  A kernel missing here reports traffic null.
+KERNEL_TRAFFIC_PER_UNIT = {"flux_theta": 39.7}
 # mixed path: algorithmic bytes per cell per launch (FP32 fields, FP64 LU factors and d');
 # these kernels are bound by HBM or latency, so their roofline is in GB/s
 KERNEL_MODEL_MIXED = {
@@ -263,35 +272,51 @@ def closure_blob(wl, d):
     return np.array([0x4D465245, 1], dtype=np.uint32).tobytes() + body.tobytes(), "random"
 
 
-def precision_comparison(args):
-    """Flat convective ABL: FP64 Smagorinsky vs FP32 Smagorinsky vs FP32 + learned closure (BF16
-    tensor-core inference), each timed alone on the same grid."""
+def _time_form(wl, steps, out, name):
+    """Cell-updates/s of one form of a workload (CUDA events around graph-launched steps after
+    3 warm-up steps) and its per-kernel device times of one further step."""
     import torch
     from paper_2412_04395_gb300 import workloads as W
     from paper_2412_04395_gb300.erf import Dycore
+    d = Dycore(wl)
+    d.erf_set_initial(wl.dtheta, wl.u, wl.v, wl.w)
+    if wl.closure == W.CLOSURE_LEARNED:
+        blob, kind = closure_blob(wl, d)
+        d.erf_set_closure_weights(blob)
+        out["learned_weights"] = kind
+    ms = time_steps(d, steps, 3)
+    prof = d.erf_profile_steps(1)
+    out[name] = {"value": wl.ncell * steps / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps,
+                 "kernel_ms_per_step": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]}}
+    d.close()
+    del d
+    torch.cuda.empty_cache()
+
+
+def precision_comparison(args):
+    """FP64 Smagorinsky vs FP32 perturbations (Smagorinsky) vs FP32 + learned closure (BF16
+    tensor-core inference), each timed alone on the same GB300: the coarse convective ABL
+    (default 2048 x 2048 x 160 at 40 m, 671 M cells) and the neutral ABL 1024 x 1024 x 128 at
+    10 m (FP64 vs FP32)."""
+    from paper_2412_04395_gb300 import workloads as W
     nx, ny, nz = args.cmp_grid
     base = W.convective_abl(nx=nx, ny=ny, nz=nz, dx=40.0)
-    out = {"workload": f"convective_abl {nx}x{ny}x{nz} at 40 m, ns=10, Smagorinsky/learned, MOST",
-           "steps": args.cmp_steps}
-    for name, wl in (("fp64_smagorinsky", base.with_(precision=W.PREC_FP64)),
-                     ("fp32_smagorinsky", base.with_(precision=W.PREC_MIXED32)),
-                     ("fp32_learned", base.with_(precision=W.PREC_MIXED32, closure=W.CLOSURE_LEARNED))):
-        d = Dycore(wl)
-        d.erf_set_initial(wl.dtheta, wl.u, wl.v, wl.w)
-        if wl.closure == W.CLOSURE_LEARNED:
-            blob, kind = closure_blob(wl, d)
-            d.erf_set_closure_weights(blob)
-            out["learned_weights"] = kind
-        steps = max(2, args.cmp_steps // (4 if wl.precision == W.PREC_FP64 else 1))
-        ms = time_steps(d, steps, 3)
-        prof = d.erf_profile_steps(1)
-        out[name] = {"value": wl.ncell * steps / (ms * 1e-3), "ms_per_step": ms / steps,
-                     "kernel_ms_per_step": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]}}
-        d.close()
-        del d
-        torch.cuda.empty_cache()
+    out = {"workload": f"convective_abl {nx}x{ny}x{nz} at 40 m, ns=10, Smagorinsky/learned, MOST"}
+    fp64_steps = max(1, args.cmp_steps // 4)
+    _time_form(base.with_(precision=W.PREC_FP64), fp64_steps, out, "fp64_smagorinsky")
+    _time_form(base.with_(precision=W.PREC_MIXED32), args.cmp_steps, out, "fp32_smagorinsky")
+    _time_form(base.with_(precision=W.PREC_MIXED32, closure=W.CLOSURE_LEARNED), args.cmp_steps, out, "fp32_learned")
+    del base
     out["fp32_learned_over_fp64"] = out["fp32_learned"]["value"] / out["fp64_smagorinsky"]["value"]
     out["fp32_over_fp64"] = out["fp32_smagorinsky"]["value"] / out["fp64_smagorinsky"]["value"]
+    if args.neutral_grid[0] > 0:
+        mx, my, mz = args.neutral_grid
+        nb = W.neutral_abl(nx=mx, ny=my, nz=mz, dx=10.0)
+        neu = {"workload": f"neutral_abl {mx}x{my}x{mz} at 10 m, ns=10, Smagorinsky, MOST"}
+        _time_form(nb.with_(precision=W.PREC_FP64), fp64_steps, neu, "fp64")
+        _time_form(nb.with_(precision=W.PREC_MIXED32), args.cmp_steps, neu, "fp32")
+        neu["fp32_over_fp64"] = neu["fp32"]["value"] / neu["fp64"]["value"]
+        out["neutral_abl"] = neu
     return out
 
 
@@ -348,8 +373,10 @@ def run_ours(args):
         bytes_ = 8 * model["words"] * units
         fp64_tf = flops / avg_s / 1e12
         hbm_gbs = bytes_ / avg_s / 1e9
+        tpu = KERNEL_TRAFFIC_PER_UNIT.get(name)
         roof = {"bound": "alu", "achieved": fp64_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": fp64_tf / FP64_PEAK_TFLOPS, "traffic": None, "kernel": name,
+                "frac": fp64_tf / FP64_PEAK_TFLOPS, "traffic": None if tpu is None else tpu * units,
+                "kernel": name,
                 "kernel_avg_ms": tms / nl, "kernel_share": tms / total,
                 "peak_source": "derived: 304 DFMA/cycle (ncu unit count) x 2 flop x 2.07 GHz",
                 "hbm": {"achieved": hbm_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_gbs / hbm,
@@ -428,8 +455,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=20)
-    ap.add_argument("--cmp-grid", type=int, nargs=3, default=[512, 512, 160])
-    ap.add_argument("--cmp-steps", type=int, default=8)
+    ap.add_argument("--cmp-grid", type=int, nargs=3, default=[2048, 2048, 160],
+                    help="grid of the precision comparison (convective ABL at 40 m)")
+    ap.add_argument("--neutral-grid", type=int, nargs=3, default=[1024, 1024, 128],
+                    help="grid of the neutral-ABL FP64/FP32 line (0 0 0 skips it)")
+    ap.add_argument("--cmp-steps", type=int, default=8, help="timed steps per FP32 form (FP64: a quarter); 0 skips")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--closure", default="default", choices=["default", "learned"],
                     help="learned: the MLP closure (convective_abl with --precision mixed)")

@@ -187,7 +187,7 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
     H->ux = cv.take<double>(nc); H->vy = cv.take<double>(nc); H->mfx = cv.take<double>(nc);
     H->mfy = cv.take<double>(nc); H->wz = cv.take<double>(nw); H->rom = cv.take<double>(nw);
     H->mu = cv.take<double>(nc);
-    H->flux = cv.take<double>(2 * nc + nw);
+    H->flux = cv.take<double>(3 * nw);   // theta, then each momentum component's fluxes (3 planes of nw)
     if (terr) {
         H->rH3 = cv.take<double>(nc); H->rHx3 = cv.take<double>(nc); H->rHy3 = cv.take<double>(nc);
         H->rdzw3 = cv.take<double>(nc); H->rdz2 = cv.take<double>(nc);
@@ -378,9 +378,12 @@ static void enqueue_step(erf_handle *h, cudaStream_t s) {
         }
         int nsub = stage == 0 ? 1 : (stage == 1 ? c.n_substeps / 2 : c.n_substeps);
         double dtau = stage == 0 ? c.dt / 3.0 : c.dt / c.n_substeps;
-        launch_tri_build(g, ph, h->st.r, h->st.t, h->pi, h->th, dtau, h->tri, s);
+        // the slow-tendency scratch is free once the tendencies exist: the mass-flux arrays take
+        // the stage's H theta at faces, the face velocities the substeps' X0, Y0 and metric shift
+        launch_tri_build(g, ph, h->st.r, h->st.t, h->pi, h->th, dtau, h->tri, h->mfx, h->mfy, s);
         for (int n = 0; n < nsub; ++n)
-            launch_substep(g, ph, h->tri, h->pi, h->th, cf(h->R), h->x, h->Om, h->Tp, dtau, s);
+            launch_substep(g, ph, h->tri, h->pi, h->th, h->mfx, h->mfy, cf(h->R), h->x, h->Om, h->Tp, h->ux, h->vy,
+                           h->wz, dtau, s);
         launch_stage_end(g, h->st, cf(h->x), s);
     }
 }

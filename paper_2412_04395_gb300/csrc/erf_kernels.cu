@@ -416,38 +416,77 @@ __global__ void k_rhs_cells(Geo g, Phys ph, Prep pr, const double *fx, const dou
     Rt[c] = r;
 }
 
+// Advective momentum fluxes (reading R5), each computed once: the u-, v- and w-control volumes
+// share every face with a neighbour, so the divergence kernels read two values per direction
+// instead of evaluating both upwind-5 fluxes themselves.  One thread per (i, j, k), k = 0..nz.
+#define CELL3D_W()                                                  \
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;            \
+    if (i >= g.nx) return;                                          \
+    const int j = blockIdx.y, k = blockIdx.z;                       \
+    const long long n = ((long long)k * g.ny + j) * g.nx + i;
+// u: x-flux at the cell centre (i,j,k), y-flux at the xy-edge (x-face i, y-face j), z-flux at the
+// xz-edge (x-face i, w-face k; zero on the walls)
+__global__ void k_flux_u(Geo g, Prep pr, double *fx, double *fy, double *fz) {
+    CELL3D_W();
+    double q[6];
+    if (k < g.nz) {
+        double adv = 0.5 * (__ldg(pr.mfx + n) + cval(g, pr.mfx, i + 1, j, k));
+        for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.ux, i - 2 + m, j, k);
+        fx[n] = adv * upwind5(q, sgnd(adv));
+        adv = 0.5 * (cval(g, pr.mfy, i - 1, j, k) + __ldg(pr.mfy + n));
+        for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.ux, i, j - 3 + m, k);
+        fy[n] = adv * upwind5(q, sgnd(adv));
+    }
+    if (k == 0 || k == g.nz) { fz[n] = 0.0; return; }
+    double adv = 0.5 * (__ldg(pr.rom + cixw(g, i - 1, j, k)) + __ldg(pr.rom + n));
+    for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.ux, i, j, k - 3 + m);
+    fz[n] = adv * upwind5(q, sgnd(adv));
+}
+// v: x-flux at the xy-edge (x-face i, y-face j), y-flux at the cell centre, z-flux at the yz-edge
+__global__ void k_flux_v(Geo g, Prep pr, double *fx, double *fy, double *fz) {
+    CELL3D_W();
+    double q[6];
+    if (k < g.nz) {
+        double adv = 0.5 * (cval(g, pr.mfx, i, j - 1, k) + __ldg(pr.mfx + n));
+        for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.vy, i - 3 + m, j, k);
+        fx[n] = adv * upwind5(q, sgnd(adv));
+        adv = 0.5 * (__ldg(pr.mfy + n) + cval(g, pr.mfy, i, j + 1, k));
+        for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.vy, i, j - 2 + m, k);
+        fy[n] = adv * upwind5(q, sgnd(adv));
+    }
+    if (k == 0 || k == g.nz) { fz[n] = 0.0; return; }
+    double adv = 0.5 * (__ldg(pr.rom + cixw(g, i, j - 1, k)) + __ldg(pr.rom + n));
+    for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.vy, i, j, k - 3 + m);
+    fz[n] = adv * upwind5(q, sgnd(adv));
+}
+// w: x-flux at the xz-edge (x-face i, w-face k), y-flux at the yz-edge (both [nz+1] planes, zero on
+// the walls), z-flux at the cell centre (i,j,k) ([nz] planes)
+__global__ void k_flux_w(Geo g, Prep pr, double *fx, double *fy, double *fz) {
+    CELL3D_W();
+    double q[6];
+    if (k < g.nz) {
+        double adv = 0.5 * (__ldg(pr.rom + n) + __ldg(pr.rom + n + g.nxy));
+        for (int m = 0; m < 6; ++m) q[m] = wval(g, pr.wz, i, j, k - 2 + m);
+        fz[n] = adv * upwind5(q, sgnd(adv));
+    }
+    if (k == 0 || k == g.nz) { fx[n] = 0.0; fy[n] = 0.0; return; }
+    double adv = 0.5 * (cval(g, pr.mfx, i, j, k - 1) + __ldg(pr.mfx + n));
+    for (int m = 0; m < 6; ++m) q[m] = __ldg(pr.wz + cixw(g, i - 3 + m, j, k));
+    fx[n] = adv * upwind5(q, sgnd(adv));
+    adv = 0.5 * (cval(g, pr.mfy, i, j, k - 1) + __ldg(pr.mfy + n));
+    for (int m = 0; m < 6; ++m) q[m] = __ldg(pr.wz + cixw(g, i, j - 3 + m, k));
+    fy[n] = adv * upwind5(q, sgnd(adv));
+}
+
 // x-momentum at x-face (i,j,k): upwind-5 advection (reading R5), terrain pressure gradient
 // (App. B), Coriolis, -div(tau)
 __global__ void k_rhs_u(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const double *th, const double *mu,
-                        int sgs, double *Ru) {
+                        int sgs, const double *fx, const double *fy, const double *fz, double *Ru) {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= g.nc) return;
     int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
-    double q[6];
-    double F[2];
-    for (int s = 0; s < 2; ++s) {   // cell centres i-1, i
-        int ic = i - 1 + s;
-        double adv = 0.5 * (cval(g, pr.mfx, ic, j, k) + cval(g, pr.mfx, ic + 1, j, k));
-        for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.ux, ic - 2 + m, j, k);
-        F[s] = adv * upwind5(q, sgnd(adv));
-    }
-    double div = (F[1] - F[0]) * g.rdx;
-    for (int s = 0; s < 2; ++s) {   // xy-edges at y-faces j, j+1
-        int jj = j + s;
-        double adv = 0.5 * (cval(g, pr.mfy, i - 1, jj, k) + cval(g, pr.mfy, i, jj, k));
-        for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.ux, i, jj - 3 + m, k);
-        F[s] = adv * upwind5(q, sgnd(adv));
-    }
-    div += (F[1] - F[0]) * g.rdy;
-    for (int s = 0; s < 2; ++s) {   // xz-edges at w-faces k, k+1
-        int kk = k + s;
-        F[s] = 0.0;
-        if (kk == 0 || kk == g.nz) continue;
-        double adv = 0.5 * (__ldg(pr.rom + cixw(g, i - 1, j, kk)) + __ldg(pr.rom + cixw(g, i, j, kk)));
-        for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.ux, i, j, kk - 3 + m);
-        F[s] = adv * upwind5(q, sgnd(adv));
-    }
-    div += F[1] - F[0];
+    double div = (__ldg(fx + c) - __ldg(fx + cixw(g, i - 1, j, k))) * g.rdx
+               + (__ldg(fy + cixw(g, i, j + 1, k)) - __ldg(fy + c)) * g.rdy + (__ldg(fz + c + g.nxy) - __ldg(fz + c));
     double r = -div * rHxf(g, i, j, k);
     // pressure gradient
     double px = (pp[c] - cval(g, pp, i - 1, j, k)) * g.rdx;
@@ -478,35 +517,12 @@ __global__ void k_rhs_u(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const
 }
 
 __global__ void k_rhs_v(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const double *th, const double *mu,
-                        int sgs, double *Rv) {
+                        int sgs, const double *fx, const double *fy, const double *fz, double *Rv) {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= g.nc) return;
     int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
-    double q[6];
-    double F[2];
-    for (int s = 0; s < 2; ++s) {   // xy-edges at x-faces i, i+1
-        int ii = i + s;
-        double adv = 0.5 * (cval(g, pr.mfx, ii, j - 1, k) + cval(g, pr.mfx, ii, j, k));
-        for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.vy, ii - 3 + m, j, k);
-        F[s] = adv * upwind5(q, sgnd(adv));
-    }
-    double div = (F[1] - F[0]) * g.rdx;
-    for (int s = 0; s < 2; ++s) {   // cell centres j-1, j
-        int jc = j - 1 + s;
-        double adv = 0.5 * (cval(g, pr.mfy, i, jc, k) + cval(g, pr.mfy, i, jc + 1, k));
-        for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.vy, i, jc - 2 + m, k);
-        F[s] = adv * upwind5(q, sgnd(adv));
-    }
-    div += (F[1] - F[0]) * g.rdy;
-    for (int s = 0; s < 2; ++s) {   // yz-edges at w-faces k, k+1
-        int kk = k + s;
-        F[s] = 0.0;
-        if (kk == 0 || kk == g.nz) continue;
-        double adv = 0.5 * (__ldg(pr.rom + cixw(g, i, j - 1, kk)) + __ldg(pr.rom + cixw(g, i, j, kk)));
-        for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.vy, i, j, kk - 3 + m);
-        F[s] = adv * upwind5(q, sgnd(adv));
-    }
-    div += F[1] - F[0];
+    double div = (__ldg(fx + cixw(g, i + 1, j, k)) - __ldg(fx + c)) * g.rdx
+               + (__ldg(fy + c) - __ldg(fy + cixw(g, i, j - 1, k))) * g.rdy + (__ldg(fz + c + g.nxy) - __ldg(fz + c));
     double r = -div * rHyf(g, i, j, k);
     double py = (pp[c] - cval(g, pp, i, j - 1, k)) * g.rdy;
     if (g.terrain && g.nz > 1) {
@@ -537,34 +553,13 @@ __global__ void k_rhs_v(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const
 
 // z-momentum at interior w-faces; boundary rows are zero
 __global__ void k_rhs_w(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const double *th, const double *mu,
-                        int sgs, double *Rw) {
+                        int sgs, const double *fx, const double *fy, const double *fz, double *Rw) {
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= g.nw) return;
     int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / g.nxy);
     if (k == 0 || k == g.nz) { Rw[n] = 0.0; return; }
-    double q[6];
-    double F[2];
-    for (int s = 0; s < 2; ++s) {   // xz-edges at x-faces i, i+1
-        int ii = i + s;
-        double adv = 0.5 * (cval(g, pr.mfx, ii, j, k - 1) + cval(g, pr.mfx, ii, j, k));
-        for (int m = 0; m < 6; ++m) q[m] = __ldg(pr.wz + cixw(g, ii - 3 + m, j, k));
-        F[s] = adv * upwind5(q, sgnd(adv));
-    }
-    double div = (F[1] - F[0]) * g.rdx;
-    for (int s = 0; s < 2; ++s) {   // yz-edges at y-faces j, j+1
-        int jj = j + s;
-        double adv = 0.5 * (cval(g, pr.mfy, i, jj, k - 1) + cval(g, pr.mfy, i, jj, k));
-        for (int m = 0; m < 6; ++m) q[m] = __ldg(pr.wz + cixw(g, i, jj - 3 + m, k));
-        F[s] = adv * upwind5(q, sgnd(adv));
-    }
-    div += (F[1] - F[0]) * g.rdy;
-    for (int s = 0; s < 2; ++s) {   // cell centres k-1, k
-        int kc = k - 1 + s;
-        double adv = 0.5 * (__ldg(pr.rom + cixw(g, i, j, kc)) + __ldg(pr.rom + cixw(g, i, j, kc + 1)));
-        for (int m = 0; m < 6; ++m) q[m] = wval(g, pr.wz, i, j, kc - 2 + m);
-        F[s] = adv * upwind5(q, sgnd(adv));
-    }
-    div += F[1] - F[0];
+    double div = (__ldg(fx + cixw(g, i + 1, j, k)) - __ldg(fx + n)) * g.rdx
+               + (__ldg(fy + cixw(g, i, j + 1, k)) - __ldg(fy + n)) * g.rdy + (__ldg(fz + n) - __ldg(fz + n - g.nxy));
     double rdz = rdzcw(g, i, j, k);
     double r = -div * rdz;
     long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1);
@@ -586,7 +581,7 @@ __global__ void k_rhs_w(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const
 // Per column: coefficients of the vertical system in Omega'' (reading R11) for this stage's
 // dtau, and their LU factors (Thomas forward elimination without the right-hand side).
 __global__ void k_tri_build(Geo g, Phys ph, const double *rho, const double *rt, const double *pi, const double *th,
-                            double dtau, Tri tr) {
+                            double dtau, Tri tr, double *TX, double *TY) {
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= g.nxy) return;
     int i = (int)(n % g.nx), j = (int)(n / g.nx);
@@ -595,7 +590,16 @@ __global__ void k_tri_build(Geo g, Phys ph, const double *rho, const double *rt,
     double gRd = GAMMA * RD;
     double cp_prev = 0.0;
     double rrt_m = 1.0 / rt[cix(g, i, j, 0)], rHm = rHc(g, i, j, 0);
+    // H theta^t at the x- and y-faces of the column (stage-fixed factors of the Theta'' flux)
+    auto face_theta = [&](int k) {
+        long long c = cix(g, i, j, k);
+        double thc = th[c];
+        TX[c] = Hx(g, i, j, k) * (0.5 * (cval(g, th, i - 1, j, k) + thc));
+        TY[c] = Hy(g, i, j, k) * (0.5 * (cval(g, th, i, j - 1, k) + thc));
+    };
+    face_theta(0);
     for (int k = 1; k < g.nz; ++k) {
+        face_theta(k);
         long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1), w = c;
         double rdz = rdzcw(g, i, j, k);
         double pic = pi[c], pim = pi[cm];
@@ -650,88 +654,106 @@ __global__ void k_sub_horiz(Geo g, Phys ph, const double *pi, const double *Tt, 
     Xv[c] += dtau * (-gRd * piy * gy + Rv[c]);
 }
 
-// Per column: explicit parts Theta*, rho* (new U'', V'' divergence, beta_1 part of the old
-// Omega'' flux), forward substitution with the stage LU factors, back substitution for
-// Omega''^{new}, then Theta'', rho'', W'' = Omega'' + metric shift, and Theta~ of the next
-// substep into Tt.  Over terrain the metric shift of each w-face is parked in W'' between the
-// two passes (it depends only on the new U'', V'').
-__global__ void __launch_bounds__(64) k_sub_vert(Geo g, Phys ph, Tri tr, const double *th, const double *Rr,
-                                                 const double *Rt, const double *Rw, F5 x, double *Om, double *Tt,
-                                                 double dtau) {
-    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (n >= g.nxy) return;
-    int i = (int)(n % g.nx), j = (int)(n / g.nx);
-    const int nz = g.nz;
+// Vertical acoustic update (App. C rows 3-5) in three kernels.  Part 1, one thread per cell:
+// explicit Theta*, rho* from the new U'', V'' divergence and the beta_1 part of the old Omega''
+// flux; the beta-weighted X0 = b1 Theta''^tau + b2 Theta*, Y0 = b1 rho''^tau + b2 rho* of the
+// Omega'' rows; and, at the cell's bottom w-face, W'' - (metric shift) + dtau R_W.  TX, TY hold
+// H theta^t at x- and y-faces for this stage.  Theta''^tau is kept in Tt.
+__global__ void k_sub_expl(Geo g, Phys ph, const double *th, const double *TX, const double *TY, const double *Rr,
+                           const double *Rt, const double *Rw, F5 x, const double *Om, double *Tt, double *X0,
+                           double *Y0, double *Ash, double dtau) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z, nz = g.nz;
     const long long nxy = g.nxy;
-    const double b1 = 0.5 * (1.0 - ph.beta_s), b2 = 0.5 * (1.0 + ph.beta_s), bd = ph.beta_d;
-    const double Gg = dtau * 0.5 * ph.g, db2 = dtau * b2;
-    const long long cx1 = cixw(g, i + 1, j, 0) - n, cy1 = cixw(g, i, j + 1, 0) - n;   // neighbour offsets
-    const long long cxm = cixw(g, i - 1, j, 0) - n, cym = cixw(g, i, j - 1, 0) - n;
-    // forward pass
-    double X0m = 0.0, Y0m = 0.0, dpm = 0.0;
-    double th_c = th[n];
-    double om_k = 0.0, omth_k = 0.0;   // old Omega'' and Omega'' theta_w at face k (0 at the wall)
-    for (int k = 0; k < nz; ++k) {
-        long long c = n + (long long)k * nxy;
-        double th_p = cval(g, th, i, j, k + 1);
-        double thw_p = 0.5 * (th_c + th_p);
-        double om_p = (k + 1 < nz) ? Om[c + nxy] : 0.0;
-        double omth_p = om_p * thw_p;
-        double Uc = x.u[c], Up = x.u[c + cx1], Vc = x.v[c], Vp = x.v[c + cy1];
-        double Hxm = Hx(g, i, j, k), Hxp = Hx(g, i + 1, j, k), Hym = Hy(g, i, j, k), Hyp = Hy(g, i, j + 1, k);
-        double thxm = 0.5 * (__ldg(th + c + cxm) + th_c), thxp = 0.5 * (th_c + __ldg(th + c + cx1));
-        double thym = 0.5 * (__ldg(th + c + cym) + th_c), thyp = 0.5 * (th_c + __ldg(th + c + cy1));
-        double fxm = Hxm * Uc, fxp = Hxp * Up, fym = Hym * Vc, fyp = Hyp * Vp;
-        double divM = (fxp - fxm) * g.rdx + (fyp - fym) * g.rdy;
-        double divT = (fxp * thxp - fxm * thxm) * g.rdx + (fyp * thyp - fym * thym) * g.rdy;
-        double rH = rHc(g, i, j, k);
-        double xt = x.t[c], xr = x.r[c];
-        Tt[c] = xt;   // Theta''^tau, until the back substitution
-        double Ts = xt + dtau * ((-divT - b1 * (omth_p - omth_k)) * rH + Rt[c]);
-        double Rs = xr + dtau * ((-divM - b1 * (om_p - om_k)) * rH + Rr[c]);
-        x.t[c] = Ts;   // hold Theta*, rho* until the back substitution
-        x.r[c] = Rs;
-        double X0 = b1 * xt + b2 * Ts, Y0 = b1 * xr + b2 * Rs;
-        if (k >= 1) {
-            double A = 0.0;
-            if (g.terrain) A = metric_shift(g, x.u, x.v, i, j, k);
-            double rhs = x.w[c] - A + dtau * Rw[c] + tr.P[c] * X0 + tr.Q[c] * X0m - Gg * (Y0 + Y0m);
-            if (g.terrain) x.w[c] = A;
-            double dp = (rhs - tr.a[c] * dpm) * tr.im[c];
-            Om[c] = dp;
-            dpm = dp;
-        }
-        X0m = X0; Y0m = Y0;
-        om_k = om_p; omth_k = omth_p;
-        th_c = th_p;
-    }
-    // back substitution, from the top wall (Omega'' = 0) down
-    {
-        long long w = n + (long long)nz * nxy;
-        x.w[w] = 0.0;
-        Om[w] = 0.0;
-    }
-    double om_up = 0.0, omth_up = 0.0;
-    th_c = th[n + (long long)(nz - 1) * nxy];
-    for (int k = nz - 1; k >= 0; --k) {
-        long long c = n + (long long)k * nxy;
-        double om = 0.0;
-        if (k >= 1) om = Om[c] - tr.cp[c] * om_up;
-        Om[c] = om;
-        double th_m = cval(g, th, i, j, k - 1);
-        double omth = om * (0.5 * (th_m + th_c));
-        double db = db2 * rHc(g, i, j, k);
-        double xt = x.t[c] - db * (omth_up - omth);
-        x.t[c] = xt;
-        x.r[c] = x.r[c] - db * (om_up - om);
-        double told = Tt[c];
-        Tt[c] = xt + bd * (xt - told);
+    const long long c = ((long long)k * g.ny + j) * g.nx + i;
+    const long long oxp = i + 1 < g.nx ? 1 : 1 - g.nx;
+    const long long oyp = j + 1 < g.ny ? (long long)g.nx : (long long)g.nx - nxy;
+    const double b1 = 0.5 * (1.0 - ph.beta_s), b2 = 0.5 * (1.0 + ph.beta_s);
+    double om_k = k >= 1 ? Om[c] : 0.0;
+    double om_p = k + 1 < nz ? Om[c + nxy] : 0.0;
+    double th_c = th[c];
+    double thw_k = 0.5 * (cval(g, th, i, j, k - 1) + th_c), thw_p = 0.5 * (th_c + cval(g, th, i, j, k + 1));
+    double Uc = x.u[c], Up = x.u[c + oxp], Vc = x.v[c], Vp = x.v[c + oyp];
+    double divM = (Hx(g, i + 1, j, k) * Up - Hx(g, i, j, k) * Uc) * g.rdx
+                + (Hy(g, i, j + 1, k) * Vp - Hy(g, i, j, k) * Vc) * g.rdy;
+    double divT = (__ldg(TX + c + oxp) * Up - __ldg(TX + c) * Uc) * g.rdx
+                + (__ldg(TY + c + oyp) * Vp - __ldg(TY + c) * Vc) * g.rdy;
+    double rH = rHc(g, i, j, k);
+    double xt = x.t[c], xr = x.r[c];
+    double Ts = xt + dtau * ((-divT - b1 * (om_p * thw_p - om_k * thw_k)) * rH + Rt[c]);
+    double Rs = xr + dtau * ((-divM - b1 * (om_p - om_k)) * rH + Rr[c]);
+    Tt[c] = xt;
+    x.t[c] = Ts;
+    x.r[c] = Rs;
+    X0[c] = b1 * xt + b2 * Ts;
+    Y0[c] = b1 * xr + b2 * Rs;
+    if (k >= 1) {
         double A = 0.0;
-        if (g.terrain) A = k >= 1 ? x.w[c] : metric_shift(g, x.u, x.v, i, j, 0);
-        x.w[c] = om + A;
-        om_up = om; omth_up = omth;
-        th_c = th_m;
+        if (g.terrain) {
+            A = metric_shift(g, x.u, x.v, i, j, k);
+            Ash[c] = A;
+        }
+        x.w[c] = x.w[c] - A + dtau * Rw[c];
     }
+}
+
+// Part 2, one thread per column: the Omega'' rows' right-hand side, forward substitution with the
+// stage LU factors (d' held in Om) and back substitution.  Only the recurrences are serial.
+__global__ void __launch_bounds__(128) k_sub_col(int nz, long long nxy, const double *__restrict__ ta,
+                                                 const double *__restrict__ tcp, const double *__restrict__ tim,
+                                                 const double *__restrict__ tP, const double *__restrict__ tQ,
+                                                 const double *__restrict__ X0, const double *__restrict__ Y0,
+                                                 double *__restrict__ W, double *__restrict__ Om, double Gg) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= nxy) return;
+    double dpm = 0.0;
+    double X0m = X0[n], Y0m = Y0[n];
+#pragma unroll 4
+    for (int k = 1; k < nz; ++k) {
+        long long c = n + k * nxy;
+        double X0c = X0[c], Y0c = Y0[c];
+        double rhs = W[c] + tP[c] * X0c + tQ[c] * X0m - Gg * (Y0c + Y0m);
+        double dp = (rhs - ta[c] * dpm) * tim[c];
+        Om[c] = dp;
+        dpm = dp;
+        X0m = X0c; Y0m = Y0c;
+    }
+    long long top = n + nz * nxy;
+    W[top] = 0.0;
+    Om[top] = 0.0;
+    double om_up = 0.0;
+#pragma unroll 4
+    for (int k = nz - 1; k >= 1; --k) {
+        long long c = n + k * nxy;
+        double om = Om[c] - tcp[c] * om_up;
+        Om[c] = om;
+        om_up = om;
+    }
+    Om[n] = 0.0;
+}
+
+// Part 3, one thread per cell: Theta'', rho'' from the new Omega'' (beta_2 part), Theta~ of the
+// next substep, and W'' = Omega'' + metric shift at the cell's bottom w-face.
+__global__ void k_sub_fin(Geo g, Phys ph, const double *th, const double *Om, const double *Ash, F5 x, double *Tt,
+                          double dtau) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long c = ((long long)k * g.ny + j) * g.nx + i;
+    const double b2 = 0.5 * (1.0 + ph.beta_s), bd = ph.beta_d;
+    double om = Om[c], om_up = Om[c + g.nxy];
+    double th_c = th[c];
+    double thw_k = 0.5 * (cval(g, th, i, j, k - 1) + th_c), thw_p = 0.5 * (th_c + cval(g, th, i, j, k + 1));
+    double db = dtau * b2 * rHc(g, i, j, k);
+    double xt = x.t[c] - db * (om_up * thw_p - om * thw_k);
+    x.t[c] = xt;
+    x.r[c] = x.r[c] - db * (om_up - om);
+    double told = Tt[c];
+    Tt[c] = xt + bd * (xt - told);
+    double A = 0.0;
+    if (g.terrain) A = k >= 1 ? Ash[c] : metric_shift(g, x.u, x.v, i, j, 0);
+    x.w[c] = om + A;
 }
 
 __global__ void k_stage_end(Geo g, F5 st, CF5 x) {
@@ -898,18 +920,29 @@ void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, const double *pp, con
     double *fx = flux, *fy = flux + g.nc, *fz = flux + 2 * g.nc;
     LAUNCH("flux_theta", s, k_flux_theta<<<nblk(g.nw, BS), BS, 0, s>>>(g, ph, pr, th, fx, fy, fz));
     LAUNCH("rhs_cells", s, k_rhs_cells<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, fx, fy, fz, th, st.r, mu, sgs, R.r, R.t));
-    LAUNCH("rhs_u", s, k_rhs_u<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, sgs, R.u));
-    LAUNCH("rhs_v", s, k_rhs_v<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, sgs, R.v));
-    LAUNCH("rhs_w", s, k_rhs_w<<<nblk(g.nw, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, sgs, R.w));
+    // momentum: fluxes of each component into the shared buffer, then its divergence
+    const dim3 g3w((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)(g.nz + 1));
+    double *ax = flux, *ay = flux + g.nw, *az = flux + 2 * g.nw;
+    LAUNCH("flux_u", s, k_flux_u<<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
+    LAUNCH("rhs_u", s, k_rhs_u<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, sgs, ax, ay, az, R.u));
+    LAUNCH("flux_v", s, k_flux_v<<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
+    LAUNCH("rhs_v", s, k_rhs_v<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, sgs, ax, ay, az, R.v));
+    LAUNCH("flux_w", s, k_flux_w<<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
+    LAUNCH("rhs_w", s, k_rhs_w<<<nblk(g.nw, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, sgs, ax, ay, az, R.w));
 }
 void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const double *rt, const double *pi,
-                      const double *th, double dtau, Tri tr, cudaStream_t s) {
-    LAUNCH("tri_build", s, k_tri_build<<<nblk(g.nxy, 128), 128, 0, s>>>(g, ph, rho, rt, pi, th, dtau, tr));
+                      const double *th, double dtau, Tri tr, double *TX, double *TY, cudaStream_t s) {
+    LAUNCH("tri_build", s, k_tri_build<<<nblk(g.nxy, 128), 128, 0, s>>>(g, ph, rho, rt, pi, th, dtau, tr, TX, TY));
 }
-void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *pi, const double *th, CF5 R, F5 x,
-                    double *Om, double *Tp, double dtau, cudaStream_t s) {
+void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *pi, const double *th, const double *TX,
+                    const double *TY, CF5 R, F5 x, double *Om, double *Tp, double *X0, double *Y0, double *Ash,
+                    double dtau, cudaStream_t s) {
+    const dim3 g3c((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)g.nz);
     LAUNCH("sub_horiz", s, k_sub_horiz<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pi, Tp, R.u, R.v, x.u, x.v, dtau));
-    LAUNCH("sub_vert", s, k_sub_vert<<<nblk(g.nxy, 64), 64, 0, s>>>(g, ph, tr, th, R.r, R.t, R.w, x, Om, Tp, dtau));
+    LAUNCH("sub_expl", s, k_sub_expl<<<g3c, 128, 0, s>>>(g, ph, th, TX, TY, R.r, R.t, R.w, x, Om, Tp, X0, Y0, Ash, dtau));
+    LAUNCH("sub_col", s, k_sub_col<<<nblk(g.nxy, 128), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q, X0, Y0,
+                                                                    x.w, Om, dtau * 0.5 * ph.g));
+    LAUNCH("sub_fin", s, k_sub_fin<<<g3c, 128, 0, s>>>(g, ph, th, Om, Ash, x, Tp, dtau));
 }
 void launch_stage_end(const Geo &g, F5 st, CF5 x, cudaStream_t s) {
     LAUNCH("stage_end", s, k_stage_end<<<nblk(g.nw, BS), BS, 0, s>>>(g, st, x));

@@ -21,9 +21,10 @@ void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, const double *pp, con
                      double *ux, double *vy, double *wz, double *mfx, double *mfy, double *rom, double *mu,
                      double *flux, F5 R, cudaStream_t s);
 void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const double *rt, const double *pi,
-                      const double *th, double dtau, Tri tr, cudaStream_t s);
-void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *pi, const double *th, CF5 R, F5 x,
-                    double *Om, double *Tp, double dtau, cudaStream_t s);
+                      const double *th, double dtau, Tri tr, double *TX, double *TY, cudaStream_t s);
+void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *pi, const double *th, const double *TX,
+                    const double *TY, CF5 R, F5 x, double *Om, double *Tp, double *X0, double *Y0, double *Ash,
+                    double dtau, cudaStream_t s);
 void launch_stage_end(const Geo &g, F5 st, CF5 x, cudaStream_t s);
 void launch_stage_nosub(const Geo &g, F5 st, CF5 sn, CF5 R, double adt, cudaStream_t s);
 void launch_diag(const Geo &g, CF5 st, double dt, double *part, double *out, cudaStream_t s);
