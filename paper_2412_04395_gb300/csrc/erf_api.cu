@@ -66,7 +66,8 @@ struct erf_handle {
     F5f mst, msn, mx, mR;
     float *mpp, *mpi, *mthp, *mTp, *mOm, *mux, *mvy, *mwz, *mmfx, *mmfy, *mmu, *mbase;
     double *mdbuf, *mrt0;
-    float *mX0 = nullptr, *mY0 = nullptr;   // beta-weighted Theta'', rho'' of the vertical substep
+    float *mflux = nullptr;                 // slow-tendency face fluxes (3 planes of nw)
+    float *mX0 = nullptr, *mY0 = nullptr;   // beta-weighted Theta'', rho'' of the vertical substep (in mflux)
     MxBase mb;
     // learned closure
     void *cl_w = nullptr;
@@ -163,7 +164,9 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
         H->mbase = cv.take<float>(mx_base_floats((int)nz));
         H->mrt0 = cv.take<double>(nz);
         H->mdbuf = cv.take<double>(nw);
-        H->mX0 = cv.take<float>(nc); H->mY0 = cv.take<float>(nc);
+        // the flux planes are free during the substeps, which keep X0 and Y0 there
+        H->mflux = cv.take<float>(3 * nw);
+        H->mX0 = H->mflux; H->mY0 = H->mflux + nw;
         H->mtri.a = cv.take<double>(nw); H->mtri.cp = cv.take<double>(nw); H->mtri.im = cv.take<double>(nw);
         H->mtri.P = cv.take<float>(nw); H->mtri.Q = cv.take<float>(nw);
         if (c->closure == 3) {
@@ -338,7 +341,7 @@ static void enqueue_step_mixed(erf_handle *h, cudaStream_t s) {
         mx_stage_begin(g, h->mb, cf(h->msn), cf(h->mst), h->mx, h->mpp, h->mpi, h->mthp, h->mTp, h->mOm, s);
         ClIn clin{h->cl_w, h->cl_b, h->cl_stats, h->cl_out, h->cl_nfb};
         mx_slow_rhs(g, h->mb, ph, cf(h->mst), h->mpp, h->mthp, h->mux, h->mvy, h->mwz, h->mmfx, h->mmfy, h->mmu,
-                    h->mR, s, h->cl_ready ? &clin : nullptr);
+                    h->mflux, h->mR, s, h->cl_ready ? &clin : nullptr);
         int nsub = stage == 0 ? 1 : (stage == 1 ? c.n_substeps / 2 : c.n_substeps);
         double dtau = stage == 0 ? c.dt / 3.0 : c.dt / c.n_substeps;
         mx_tri_build(g, h->mb, ph, h->mst.r, h->mst.t, h->mpi, h->mthp, dtau, h->mtri, s);

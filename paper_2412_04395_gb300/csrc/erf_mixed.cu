@@ -290,10 +290,101 @@ struct PrepF {
     const float *tau;   // learned-closure stress planes, or null
 };
 
+// ---- advective fluxes, each face once (the divergence kernels read two values per direction)
+#define MX_CELL3D_W()                                               \
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;            \
+    if (i >= g.nx) return;                                          \
+    const int j = blockIdx.y, k = blockIdx.z;                       \
+    const long long n = ((long long)k * g.ny + j) * g.nx + i;
+// theta (WENO5 relative to the upwind cell): x-face i and y-face j of cell (i,j,k) carry
+// mf (theta'_face), theta0 being constant along a level; the w-face k carries
+// W (theta_face - theta0_{k-1}), i.e. relative to the base state of the cell below it.
+__global__ void k_mx_flux_theta(Geo g, MxBase mb, Phys ph, const float *mfx, const float *mfy, const float *rw,
+                                const float *thp, float *fx, float *fy, float *fz) {
+    MX_CELL3D_W();
+    const int zf = ph.scal_adv == 1;
+    float q[6];
+    if (k < g.nz) {
+        float mf = __ldg(mfx + n), sg = sgnT<float>(mf);
+        float tu = fval(g, thp, sg >= 0.f ? i - 1 : i, j, k);
+        for (int m = 0; m < 6; ++m) q[m] = fval(g, thp, i - 3 + m, j, k) - tu;
+        fx[n] = mf * (tu + weno5<float>(q, sg, zf));
+        mf = __ldg(mfy + n); sg = sgnT<float>(mf);
+        tu = fval(g, thp, i, sg >= 0.f ? j - 1 : j, k);
+        for (int m = 0; m < 6; ++m) q[m] = fval(g, thp, i, j - 3 + m, k) - tu;
+        fy[n] = mf * (tu + weno5<float>(q, sg, zf));
+    }
+    if (k == 0 || k == g.nz) { fz[n] = 0.f; return; }
+    float W = __ldg(rw + n), sg = sgnT<float>(W);
+    int ku = sg >= 0.f ? k - 1 : k;
+    float tu = fval(g, thp, i, j, ku);
+    for (int m = 0; m < 6; ++m) {
+        int km = k - 3 + m;
+        q[m] = dth0(mb, km, ku) + (fval(g, thp, i, j, km) - tu);
+    }
+    fz[n] = W * (dth0(mb, ku, k - 1) + tu + weno5<float>(q, sg, zf));
+}
+// momenta (upwind-5, reading R5): the same face and edge placement as the FP64 path
+__global__ void k_mx_flux_u(Geo g, const float *ux, const float *mfx, const float *mfy, const float *rw, float *fx,
+                            float *fy, float *fz) {
+    MX_CELL3D_W();
+    float q[6];
+    if (k < g.nz) {
+        float adv = 0.5f * (__ldg(mfx + n) + fval(g, mfx, i + 1, j, k));
+        for (int m = 0; m < 6; ++m) q[m] = fval(g, ux, i - 2 + m, j, k);
+        fx[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+        adv = 0.5f * (fval(g, mfy, i - 1, j, k) + __ldg(mfy + n));
+        for (int m = 0; m < 6; ++m) q[m] = fval(g, ux, i, j - 3 + m, k);
+        fy[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+    }
+    if (k == 0 || k == g.nz) { fz[n] = 0.f; return; }
+    float adv = 0.5f * (__ldg(rw + cixw(g, i - 1, j, k)) + __ldg(rw + n));
+    for (int m = 0; m < 6; ++m) q[m] = fval(g, ux, i, j, k - 3 + m);
+    fz[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+}
+__global__ void k_mx_flux_v(Geo g, const float *vy, const float *mfx, const float *mfy, const float *rw, float *fx,
+                            float *fy, float *fz) {
+    MX_CELL3D_W();
+    float q[6];
+    if (k < g.nz) {
+        float adv = 0.5f * (fval(g, mfx, i, j - 1, k) + __ldg(mfx + n));
+        for (int m = 0; m < 6; ++m) q[m] = fval(g, vy, i - 3 + m, j, k);
+        fx[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+        adv = 0.5f * (__ldg(mfy + n) + fval(g, mfy, i, j + 1, k));
+        for (int m = 0; m < 6; ++m) q[m] = fval(g, vy, i, j - 2 + m, k);
+        fy[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+    }
+    if (k == 0 || k == g.nz) { fz[n] = 0.f; return; }
+    float adv = 0.5f * (__ldg(rw + cixw(g, i, j - 1, k)) + __ldg(rw + n));
+    for (int m = 0; m < 6; ++m) q[m] = fval(g, vy, i, j, k - 3 + m);
+    fz[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+}
+__global__ void k_mx_flux_w(Geo g, const float *wz, const float *mfx, const float *mfy, const float *rw, float *fx,
+                            float *fy, float *fz) {
+    MX_CELL3D_W();
+    float q[6];
+    if (k < g.nz) {
+        float wa = k == 0 ? 0.f : __ldg(rw + n), wb = k + 1 == g.nz ? 0.f : __ldg(rw + n + g.nxy);
+        float adv = 0.5f * (wa + wb);
+        for (int m = 0; m < 6; ++m) q[m] = wvalf(g, wz, i, j, k - 2 + m);
+        fz[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+    }
+    if (k == 0 || k == g.nz) { fx[n] = 0.f; fy[n] = 0.f; return; }
+    float adv = 0.5f * (fval(g, mfx, i, j, k - 1) + __ldg(mfx + n));
+    for (int m = 0; m < 6; ++m) q[m] = __ldg(wz + cixw(g, i - 3 + m, j, k));
+    fx[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+    adv = 0.5f * (fval(g, mfy, i, j, k - 1) + __ldg(mfy + n));
+    for (int m = 0; m < 6; ++m) q[m] = __ldg(wz + cixw(g, i, j - 3 + m, k));
+    fy[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+}
+
 // continuity and rho*theta.  Face fluxes of theta are split as F theta0_k + F (theta_face -
 // theta0_k); the first sums to theta0_k R_rho.
+struct FluxF {
+    const float *x, *y, *z;
+};
 __global__ void k_mx_rhs_cells(Geo g, MxBase mb, Phys ph, PrepF pr, const float *rw, const float *thp,
-                               const float *dr, const float *mu, int sgs, float *Rr, float *Rt) {
+                               const float *dr, const float *mu, int sgs, FluxF fth, float *Rr, float *Rt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
@@ -306,39 +397,11 @@ __global__ void k_mx_rhs_cells(Geo g, MxBase mb, Phys ph, PrepF pr, const float 
     // face mass fluxes carry the face height, so the whole divergence is divided by the cell height
     float Rrho = -((mxp - mxm) * rdx + (myp - mym) * rdy + (omp - omm)) * rH;
     Rr[c] = Rrho;
-    int zf = ph.scal_adv == 1;
-    float q[6];
-    // horizontal faces: theta0 is constant along the level, so theta_face - theta0_k = theta'_face
-    auto hface = [&](int di, int dj, float mf) -> float {
-        // face between the cells (i+di-1... ) given by its lower-left offset: x-face at i+di or y-face at j+dj
-        float s = sgnT<float>(mf);
-        int iu, ju;   // upwind cell
-        if (dj == -99) { iu = (s >= 0.f) ? i + di - 1 : i + di; ju = j; }
-        else { iu = i; ju = (s >= 0.f) ? j + dj - 1 : j + dj; }
-        float tu = fval(g, thp, iu, ju, k);
-        for (int m = 0; m < 6; ++m) {
-            float t = (dj == -99) ? fval(g, thp, i + di - 3 + m, j, k) : fval(g, thp, i, j + dj - 3 + m, k);
-            q[m] = t - tu;
-        }
-        return mf * (tu + weno5<float>(q, s, zf));
-    };
-    float fxm = hface(0, -99, mxm), fxp = hface(1, -99, mxp);
-    float fym = hface(-99, 0, mym), fyp = hface(-99, 1, myp);
-    // vertical faces k (if > 0) and k+1 (if < nz): theta differences formed from FP64 base
-    // differences plus FP32 perturbation differences, relative to the upwind cell
-    auto vface = [&](int kf, float W) -> float {
-        float s = sgnT<float>(W);
-        int ku = (s >= 0.f) ? kf - 1 : kf;
-        float tu = fval(g, thp, i, j, ku);
-        for (int m = 0; m < 6; ++m) {
-            int km = kf - 3 + m;
-            q[m] = dth0(mb, km, ku) + (fval(g, thp, i, j, km) - tu);
-        }
-        float dcell = dth0(mb, ku, k);   // theta0_u - theta0_k
-        return W * (dcell + tu + weno5<float>(q, s, zf));
-    };
-    float fzm = (k > 0) ? vface(k, omm) : 0.f;
-    float fzp = (k < g.nz - 1) ? vface(k + 1, omp) : 0.f;
+    // theta fluxes (k_mx_flux_theta); the bottom face's is moved to the theta0_k reference
+    float fxm = __ldg(fth.x + c), fxp = __ldg(fth.x + cixw(g, i + 1, j, k));
+    float fym = __ldg(fth.y + c), fyp = __ldg(fth.y + cixw(g, i, j + 1, k));
+    float fzm = k > 0 ? __ldg(fth.z + c) + omm * dth0(mb, k - 1, k) : 0.f;
+    float fzp = k < g.nz - 1 ? __ldg(fth.z + c + g.nxy) : 0.f;
     float r = mb.th0f[k] * Rrho - ((fxp - fxm) * rdx + (fyp - fym) * rdy + (fzp - fzm)) * rH;
     if (sgs) {
         int visc = ph.closure == 1 || ph.closure == 2;
@@ -376,36 +439,14 @@ __global__ void k_mx_rhs_cells(Geo g, MxBase mb, Phys ph, PrepF pr, const float 
 }
 
 __global__ void k_mx_rhs_u(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const float *pp, const float *thp,
-                           const float *mu, int sgs, float *Ru) {
+                           const float *mu, int sgs, FluxF fm, float *Ru) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
     const long long c = ((long long)k * g.ny + j) * g.nx + i;
     float rdx = mb.rdx, rdy = mb.rdy, rH = mb.rdzf[k];
-    float q[6], F[2];
-    for (int s = 0; s < 2; ++s) {
-        int ic = i - 1 + s;
-        float adv = 0.5f * (fval(g, pr.mfx, ic, j, k) + fval(g, pr.mfx, ic + 1, j, k));
-        for (int m = 0; m < 6; ++m) q[m] = fval(g, pr.ux, ic - 2 + m, j, k);
-        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
-    }
-    float div = (F[1] - F[0]) * rdx;
-    for (int s = 0; s < 2; ++s) {
-        int jj = j + s;
-        float adv = 0.5f * (fval(g, pr.mfy, i - 1, jj, k) + fval(g, pr.mfy, i, jj, k));
-        for (int m = 0; m < 6; ++m) q[m] = fval(g, pr.ux, i, jj - 3 + m, k);
-        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
-    }
-    div += (F[1] - F[0]) * rdy;
-    for (int s = 0; s < 2; ++s) {
-        int kk = k + s;
-        F[s] = 0.f;
-        if (kk == 0 || kk == g.nz) continue;
-        float adv = 0.5f * (__ldg(st.w + cixw(g, i - 1, j, kk)) + __ldg(st.w + cixw(g, i, j, kk)));
-        for (int m = 0; m < 6; ++m) q[m] = fval(g, pr.ux, i, j, kk - 3 + m);
-        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
-    }
-    div += F[1] - F[0];
+    float div = (__ldg(fm.x + c) - __ldg(fm.x + cixw(g, i - 1, j, k))) * rdx
+              + (__ldg(fm.y + cixw(g, i, j + 1, k)) - __ldg(fm.y + c)) * rdy + (__ldg(fm.z + c + g.nxy) - __ldg(fm.z + c));
     float r = -div * rH;
     r -= (pp[c] - fval(g, pp, i - 1, j, k)) * rdx;
     if (mb.f_cor != 0.f) {
@@ -435,36 +476,14 @@ __global__ void k_mx_rhs_u(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const f
 }
 
 __global__ void k_mx_rhs_v(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const float *pp, const float *thp,
-                           const float *mu, int sgs, float *Rv) {
+                           const float *mu, int sgs, FluxF fm, float *Rv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
     const long long c = ((long long)k * g.ny + j) * g.nx + i;
     float rdx = mb.rdx, rdy = mb.rdy, rH = mb.rdzf[k];
-    float q[6], F[2];
-    for (int s = 0; s < 2; ++s) {
-        int ii = i + s;
-        float adv = 0.5f * (fval(g, pr.mfx, ii, j - 1, k) + fval(g, pr.mfx, ii, j, k));
-        for (int m = 0; m < 6; ++m) q[m] = fval(g, pr.vy, ii - 3 + m, j, k);
-        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
-    }
-    float div = (F[1] - F[0]) * rdx;
-    for (int s = 0; s < 2; ++s) {
-        int jc = j - 1 + s;
-        float adv = 0.5f * (fval(g, pr.mfy, i, jc, k) + fval(g, pr.mfy, i, jc + 1, k));
-        for (int m = 0; m < 6; ++m) q[m] = fval(g, pr.vy, i, jc - 2 + m, k);
-        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
-    }
-    div += (F[1] - F[0]) * rdy;
-    for (int s = 0; s < 2; ++s) {
-        int kk = k + s;
-        F[s] = 0.f;
-        if (kk == 0 || kk == g.nz) continue;
-        float adv = 0.5f * (__ldg(st.w + cixw(g, i, j - 1, kk)) + __ldg(st.w + cixw(g, i, j, kk)));
-        for (int m = 0; m < 6; ++m) q[m] = fval(g, pr.vy, i, j, kk - 3 + m);
-        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
-    }
-    div += F[1] - F[0];
+    float div = (__ldg(fm.x + cixw(g, i + 1, j, k)) - __ldg(fm.x + c)) * rdx
+              + (__ldg(fm.y + c) - __ldg(fm.y + cixw(g, i, j - 1, k))) * rdy + (__ldg(fm.z + c + g.nxy) - __ldg(fm.z + c));
     float r = -div * rH;
     r -= (pp[c] - fval(g, pp, i, j - 1, k)) * rdy;
     if (mb.f_cor != 0.f) {
@@ -494,37 +513,15 @@ __global__ void k_mx_rhs_v(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const f
 }
 
 __global__ void k_mx_rhs_w(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const float *pp, const float *thp,
-                           const float *mu, int sgs, float *Rw) {
+                           const float *mu, int sgs, FluxF fm, float *Rw) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
     const long long n = ((long long)k * g.ny + j) * g.nx + i;
     if (k == 0 || k == g.nz) { Rw[n] = 0.f; return; }
     float rdx = mb.rdx, rdy = mb.rdy, rdzc = mb.rdzcf[k];
-    float q[6], F[2];
-    for (int s = 0; s < 2; ++s) {
-        int ii = i + s;
-        float adv = 0.5f * (fval(g, pr.mfx, ii, j, k - 1) + fval(g, pr.mfx, ii, j, k));
-        for (int m = 0; m < 6; ++m) q[m] = __ldg(pr.wz + cixw(g, ii - 3 + m, j, k));
-        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
-    }
-    float div = (F[1] - F[0]) * rdx;
-    for (int s = 0; s < 2; ++s) {
-        int jj = j + s;
-        float adv = 0.5f * (fval(g, pr.mfy, i, jj, k - 1) + fval(g, pr.mfy, i, jj, k));
-        for (int m = 0; m < 6; ++m) q[m] = __ldg(pr.wz + cixw(g, i, jj - 3 + m, k));
-        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
-    }
-    div += (F[1] - F[0]) * rdy;
-    for (int s = 0; s < 2; ++s) {
-        int kc = k - 1 + s;
-        float wa = (kc == 0) ? 0.f : __ldg(st.w + cixw(g, i, j, kc));
-        float wb = (kc + 1 == g.nz) ? 0.f : __ldg(st.w + cixw(g, i, j, kc + 1));
-        float adv = 0.5f * (wa + wb);
-        for (int m = 0; m < 6; ++m) q[m] = wvalf(g, pr.wz, i, j, kc - 2 + m);
-        F[s] = adv * upwind5<float>(q, sgnT<float>(adv));
-    }
-    div += F[1] - F[0];
+    float div = (__ldg(fm.x + cixw(g, i + 1, j, k)) - __ldg(fm.x + n)) * rdx
+              + (__ldg(fm.y + cixw(g, i, j + 1, k)) - __ldg(fm.y + n)) * rdy + (__ldg(fm.z + n) - __ldg(fm.z + n - g.nxy));
     float r = -div * rdzc;
     long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1);
     r -= (pp[c] - pp[cm]) * rdzc;
@@ -802,7 +799,7 @@ void mx_stage_begin(const Geo &g, const MxBase &mb, CF5f sn, CF5f st, F5f x, flo
     });
 }
 void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const float *pp, const float *thp,
-                 float *ux, float *vy, float *wz, float *mfx, float *mfy, float *mu, F5f R, cudaStream_t s,
+                 float *ux, float *vy, float *wz, float *mfx, float *mfy, float *mu, float *flux, F5f R, cudaStream_t s,
                  const ClIn *cl) {
     mx_launch("mx_prep", s, [&] { k_mx_prep<<<g3(g, g.nz + 1), MBX, 0, s>>>(g, mb, st, ux, vy, wz, mfx, mfy); });
     int learned = ph.closure == 3 && cl;
@@ -815,12 +812,21 @@ void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const 
         tau = cl->out;
     }
     PrepF pr{ux, vy, wz, mfx, mfy, tau};
+    // each advected quantity's face fluxes go to the shared buffer (3 planes of nw), then the
+    // divergence kernel of that quantity reads them
+    float *ax = flux, *ay = flux + g.nw, *az = flux + 2 * g.nw;
+    FluxF fl{ax, ay, az};
+    const dim3 gw = g3(g, g.nz + 1);
+    mx_launch("mx_flux_theta", s, [&] { k_mx_flux_theta<<<gw, MBX, 0, s>>>(g, mb, ph, mfx, mfy, st.w, thp, ax, ay, az); });
     mx_launch("mx_rhs_cells", s, [&] {
-        k_mx_rhs_cells<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, pr, st.w, thp, st.r, mu, sgs, R.r, R.t);
+        k_mx_rhs_cells<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, pr, st.w, thp, st.r, mu, sgs, fl, R.r, R.t);
     });
-    mx_launch("mx_rhs_u", s, [&] { k_mx_rhs_u<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, R.u); });
-    mx_launch("mx_rhs_v", s, [&] { k_mx_rhs_v<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, R.v); });
-    mx_launch("mx_rhs_w", s, [&] { k_mx_rhs_w<<<g3(g, g.nz + 1), MBX, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, R.w); });
+    mx_launch("mx_flux_u", s, [&] { k_mx_flux_u<<<gw, MBX, 0, s>>>(g, ux, mfx, mfy, st.w, ax, ay, az); });
+    mx_launch("mx_rhs_u", s, [&] { k_mx_rhs_u<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, fl, R.u); });
+    mx_launch("mx_flux_v", s, [&] { k_mx_flux_v<<<gw, MBX, 0, s>>>(g, vy, mfx, mfy, st.w, ax, ay, az); });
+    mx_launch("mx_rhs_v", s, [&] { k_mx_rhs_v<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, fl, R.v); });
+    mx_launch("mx_flux_w", s, [&] { k_mx_flux_w<<<gw, MBX, 0, s>>>(g, wz, mfx, mfy, st.w, ax, ay, az); });
+    mx_launch("mx_rhs_w", s, [&] { k_mx_rhs_w<<<gw, MBX, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, fl, R.w); });
 }
 void mx_slow_prep_only(const Geo &g, const MxBase &mb, CF5f st, float *ux, float *vy, float *wz, float *mfx,
                        float *mfy, cudaStream_t s) {

@@ -89,7 +89,7 @@ void mx_wall_bc(const Geo &g, float *rw, cudaStream_t s);
 void mx_stage_begin(const Geo &g, const MxBase &mb, CF5f sn, CF5f st, F5f x, float *pp, float *pi, float *thp,
                     float *Tp, float *Om, cudaStream_t s);
 void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const float *pp, const float *thp,
-                 float *ux, float *vy, float *wz, float *mfx, float *mfy, float *mu, F5f R, cudaStream_t s,
+                 float *ux, float *vy, float *wz, float *mfx, float *mfy, float *mu, float *flux, F5f R, cudaStream_t s,
                  const ClIn *cl);
 void mx_slow_prep_only(const Geo &g, const MxBase &mb, CF5f st, float *ux, float *vy, float *wz, float *mfx,
                        float *mfy, cudaStream_t s);
