@@ -142,7 +142,9 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend="nccl"):
+    """torchrun environment -> (world size, rank, local rank, process group or None).  The GPU run
+    uses NCCL; the CPU tests of the replica coordination use gloo."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -150,8 +152,9 @@ def dist_setup(n_gpus):
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
         pg = dist
     return ws, rank, local, pg
 
@@ -161,13 +164,21 @@ def barrier(pg):
         pg.barrier()
 
 
-def max_over_ranks(pg, v):
+def max_over_ranks(pg, v, device="cuda"):
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
     if pg is None:
         return v
     import torch
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     pg.all_reduce(t, op=pg.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_value(pg, ws, units_per_rank, seconds, device="cuda"):
+    """Whole-job throughput of N independent replicas: all ranks' units over the slowest rank's
+    time (weak scaling: each rank runs the full workload)."""
+    t = max_over_ranks(pg, seconds, device)
+    return ws * units_per_rank / t, t
 
 
 def oracle_rate(wl_sample, steps, threads=None):
@@ -348,9 +359,9 @@ def run_ours(args):
         barrier(pg)
     clocks = cs.summary()
     ms = ev0.elapsed_time(ev1)
-    ms = max_over_ranks(pg, ms)
     diag = d.erf_diagnostics()
-    value = ws * wl.ncell * args.steps / (ms * 1e-3)
+    value, sec = replica_value(pg, ws, wl.ncell * args.steps, ms * 1e-3)
+    ms = sec * 1e3
 
     # per-kernel device times (event-bracketed direct launches of 2 further steps)
     prof = d.erf_profile_steps(2)
