@@ -372,6 +372,51 @@ __device__ __forceinline__ double heat_z(const Geo &g, const Phys &ph, const dou
 
 // ------------------------------------------------------------------ slow tendencies
 
+// WENO5-JS / WENO5-Z face value in FP64 (same candidates, indicators and weights as weno5<T>),
+// arranged for GB300's FP64 rate: the three candidate values and the six indicator terms are
+// formed from the four first differences of the stencil, and the normalisation uses the
+// Newton-Raphson iteration for the reciprocal, r <- r + r (1 - D r) (quadratic convergence), from
+// an FP32 estimate: two steps take its 6e-8 relative error to the FP64 rounding level.  A sum
+// outside the FP32 range falls back to the division.
+__device__ __forceinline__ double weno5_d(const double *q, double s, int zflag) {
+    double a, b, c, d, e;   // v_{-2}, v_{-1}, v_0, v_1, v_2 on the upwind side
+    if (s >= 0.0) { a = q[0]; b = q[1]; c = q[2]; d = q[3]; e = q[4]; }
+    else { a = q[5]; b = q[4]; c = q[3]; d = q[2]; e = q[1]; }
+    const double d1 = a - b, d2 = b - c, d3 = c - d, d4 = d - e;
+    const double p0 = fma(1.0 / 3.0, d1, fma(-5.0 / 6.0, d2, c));   // (2a - 7b + 11c)/6
+    const double p1 = fma(-1.0 / 6.0, d2, fma(-1.0 / 3.0, d3, c));  // (-b + 5c + 2d)/6
+    const double p2 = fma(-2.0 / 3.0, d3, fma(1.0 / 6.0, d4, c));   // (2c + 5d - e)/6
+    const double t0 = d1 - d2, u0 = fma(-3.0, d2, d1);               // a - 2b + c, a - 4b + 3c
+    const double t1 = d2 - d3, u1 = d2 + d3;                         // b - 2c + d, b - d
+    const double t2 = d3 - d4, u2 = fma(3.0, d3, -d4);               // c - 2d + e, 3c - 4d + e
+    const double b0 = fma(13.0 / 12.0 * t0, t0, 0.25 * u0 * u0);
+    const double b1 = fma(13.0 / 12.0 * t1, t1, 0.25 * u1 * u1);
+    const double b2 = fma(13.0 / 12.0 * t2, t2, 0.25 * u2 * u2);
+    const double eps = 1.0e-6;
+    double w0, w1, w2;
+    if (zflag) {
+        double tau = fabs(b0 - b2);
+        double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+        w0 = 0.1 * (e0 + tau) * e1 * e2;
+        w1 = 0.6 * (e1 + tau) * e0 * e2;
+        w2 = 0.3 * (e2 + tau) * e0 * e1;
+    } else {
+        double e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
+        double f01 = e0 * e1, f02 = e0 * e2, f12 = e1 * e2;
+        w0 = 0.1 * f12 * f12;
+        w1 = 0.6 * f02 * f02;
+        w2 = 0.3 * f01 * f01;
+    }
+    const double N = fma(w0, p0, fma(w1, p1, w2 * p2));
+    const double D = w0 + w1 + w2;
+    const float Df = (float)D;
+    if (!(fabsf(Df) > 1.0e-30f && fabsf(Df) < 1.0e30f)) return N / D;
+    double r = (double)(1.0f / Df);
+    r = fma(r, fma(-D, r, 1.0), r);
+    r = fma(r, fma(-D, r, 1.0), r);
+    return N * r;
+}
+
 // theta fluxes through the left x-face, front y-face and bottom w-face of each cell (each face
 // once): normal mass flux x WENO5(theta); walls carry none
 __global__ void k_flux_theta(Geo g, Phys ph, Prep pr, const double *th, double *fx, double *fy, double *fz) {
@@ -383,14 +428,14 @@ __global__ void k_flux_theta(Geo g, Phys ph, Prep pr, const double *th, double *
     if (k < g.nz) {
         double mx = pr.mfx[n], my = pr.mfy[n];
         for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i - 3 + m, j, k);
-        fx[n] = mx * weno5(q, sgnd(mx), zf);
+        fx[n] = mx * weno5_d(q, sgnd(mx), zf);
         for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i, j - 3 + m, k);
-        fy[n] = my * weno5(q, sgnd(my), zf);
+        fy[n] = my * weno5_d(q, sgnd(my), zf);
     }
     if (k == 0 || k == g.nz) { fz[n] = 0.0; return; }
     double om = pr.rom[n];
     for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i, j, k - 3 + m);
-    fz[n] = om * weno5(q, sgnd(om), zf);
+    fz[n] = om * weno5_d(q, sgnd(om), zf);
 }
 
 // continuity and potential temperature (Eq. con, Eq. theta): flux divergence / cell height
