@@ -59,6 +59,7 @@ typedef struct {
     int32_t surface;          /* 0 slip wall, 1 MOST (constant z0, prescribed kinematic heat flux) */
     double z0, sfc_theta_flux;
     double theta_s, brunt_N, p_s;  /* base state: theta0 = theta_s exp(N^2 z/g) unless knots given */
+    int32_t tracer;           /* 1: advance a passive scalar rho phi after the substeps (Sec. 3.1) */
 } orc_cfg;
 
 typedef struct {
@@ -86,6 +87,9 @@ typedef struct {
     double *Om;                /* Omega'' at w-faces (previous substep) */
     double *Tprev;             /* Theta'' of the previous substep (divergence damping) */
     double *fx, *fy, *fz, *mfx, *mfy, *rom, *ux, *vy, *wz, *mu;  /* slow-RHS scratch */
+    /* passive scalar: rho phi, its S^n copy, and the sums over a stage's substeps of the
+     * perturbation mass fluxes that advance rho'' (x-faces, y-faces, w-faces) */
+    double *rphi, *sn_phi, *msx, *msy, *msz;
 } orc;
 
 enum { F_RHO = 0, F_RT = 1, F_RU = 2, F_RV = 3, F_RW = 4 };
@@ -284,6 +288,7 @@ orc *orc_create(const orc_cfg *cfg, const double *zeta, const double *hnode,
     o->fx = dalloc(NW); o->fy = dalloc(NW); o->fz = dalloc(NW);
     o->mfx = dalloc(NC); o->mfy = dalloc(NC); o->rom = dalloc(NW);
     o->ux = dalloc(NC); o->vy = dalloc(NC); o->wz = dalloc(NW); o->mu = dalloc(NC);
+    o->rphi = dalloc(NC); o->sn_phi = dalloc(NC); o->msx = dalloc(NC); o->msy = dalloc(NC); o->msz = dalloc(NW);
 
     /* node heights, App. B + canonical smoothing z = zeta + (1 - zeta/z_t)^beta h (Sec. 3.4) */
     #pragma omp parallel for
@@ -358,7 +363,8 @@ void orc_destroy(orc *o) {
                        &o->Hx, &o->Hy, &o->hxi_x, &o->heta_y, &o->hxi_w, &o->heta_w, &o->rho0,
                        &o->th0, &o->p0, &o->rho, &o->rt, &o->ru, &o->rv, &o->rw, &o->pp, &o->pi,
                        &o->th, &o->Om, &o->Tprev, &o->fx, &o->fy, &o->fz, &o->mfx, &o->mfy,
-                       &o->rom, &o->ux, &o->vy, &o->wz, &o->mu};
+                       &o->rom, &o->ux, &o->vy, &o->wz, &o->mu, &o->rphi, &o->sn_phi, &o->msx,
+                       &o->msy, &o->msz};
     for (size_t n = 0; n < sizeof(ptrs) / sizeof(ptrs[0]); ++n) free(*ptrs[n]);
     for (int f = 0; f < 5; ++f) { free(o->sn[f]); free(o->R[f]); free(o->X[f]); }
     free(o);
@@ -848,6 +854,11 @@ static void substep(orc *o, const double *rho_t, const double *rt_t, double dtau
     memcpy(o->Tprev, Xt, sizeof(double) * o->ncell);
     memcpy(Xu, Un, sizeof(double) * o->ncell);
     memcpy(Xv, Vn, sizeof(double) * o->ncell);
+    /* the horizontal perturbation mass fluxes that advance rho'' in this substep */
+    for (size_t c = 0; c < o->ncell; ++c) {
+        o->msx[c] += lin * o->Hx[c] * Un[c];
+        o->msy[c] += lin * o->Hy[c] * Vn[c];
+    }
     free(Un); free(Vn); free(Tt);
 
     /* per column: vertical implicit solve */
@@ -904,8 +915,11 @@ static void substep(orc *o, const double *rho_t, const double *rt_t, double dtau
             Om[0] = 0.0; Om[nz] = 0.0;
             for (int k = 1; k < nz; ++k) Om[k] = x[k - 1];
             for (int k = 0; k <= nz; ++k) {
-                Xw[IX(o, i, j, k)] = Om[k] + A[k];
-                o->Om[IX(o, i, j, k)] = Om[k];
+                size_t w = IX(o, i, j, k);
+                /* vertical perturbation mass flux of the rho'' update: beta_1 old + beta_2 new */
+                o->msz[w] += lin * (b1 * o->Om[w] + b2 * Om[k]);
+                Xw[w] = Om[k] + A[k];
+                o->Om[w] = Om[k];
             }
             for (int k = 0; k < nz; ++k) {
                 size_t c = IX(o, i, j, k);
@@ -916,6 +930,51 @@ static void substep(orc *o, const double *rho_t, const double *rt_t, double dtau
         }
     free(Ts); free(Rs); free(thw); free(A); free(a); free(b); free(cc); free(d); free(x); free(Om);
     }
+}
+
+/* ------------------------------------------------------------------ passive scalar (Sec. 3.1) */
+/* Scalars do not take part in the substeps: after them, rho phi advances over the stage as
+ * without substepping, rho phi^(s) = rho phi^n + alpha_s dt R_phi(phi^t), except that the normal
+ * momenta of the advective fluxes are the average over the stage's substeps of those that
+ * advanced rho (stage momentum + perturbation flux of each substep).  With that average,
+ * rho phi / rho stays 1 for phi = 1 (rho^(s) = rho^n - alpha_s dt div <M>).  phi^t is
+ * interpolated like theta (WENO5 or the linear interpolant of scal_adv). */
+static void tracer_stage(orc *o, const double *rho_t, double adt, int nsub) {
+    const orc_cfg *C = &o->c;
+    int nx = o->nx, ny = o->ny, nz = o->nz;
+    double dx = C->dx, dy = C->dy;
+    int zf = (C->scal_adv == 1);
+    double *phi = dalloc(o->ncell), *F[3] = {dalloc(o->ncell), dalloc(o->ncell), dalloc(o->nw)};
+    for (size_t c = 0; c < o->ncell; ++c) phi[c] = o->rphi[c] / rho_t[c];
+    #pragma omp parallel for
+    for (int k = 0; k <= nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                double q[6];
+                size_t w = IX(o, i, j, k);
+                if (k < nz) {
+                    double mx = o->mfx[w] + o->msx[w] / nsub, my = o->mfy[w] + o->msy[w] / nsub;
+                    for (int m = 0; m < 6; ++m) q[m] = CV(o, phi, i - 3 + m, j, k);
+                    F[0][w] = mx * (C->scal_adv <= 1 ? orc_weno5(q, sgn(mx), zf) : orc_interp(q, sgn(mx), C->scal_adv));
+                    for (int m = 0; m < 6; ++m) q[m] = CV(o, phi, i, j - 3 + m, k);
+                    F[1][w] = my * (C->scal_adv <= 1 ? orc_weno5(q, sgn(my), zf) : orc_interp(q, sgn(my), C->scal_adv));
+                }
+                if (k == 0 || k == nz) { F[2][w] = 0.0; continue; }
+                double mz = o->rom[w] + o->msz[w] / nsub;
+                for (int m = 0; m < 6; ++m) q[m] = CV(o, phi, i, j, k - 3 + m);
+                F[2][w] = mz * (C->scal_adv <= 1 ? orc_weno5(q, sgn(mz), zf) : orc_interp(q, sgn(mz), C->scal_adv));
+            }
+    #pragma omp parallel for
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t c = IX(o, i, j, k);
+                double div = (F[0][IX(o, i + 1, j, k)] - F[0][c]) / dx
+                           + (F[1][IX(o, i, j + 1, k)] - F[1][c]) / dy
+                           + (F[2][IX(o, i, j, k + 1)] - F[2][c]);
+                o->rphi[c] = o->sn_phi[c] + adt * (-div / o->Hc[c]);
+            }
+    free(phi); free(F[0]); free(F[1]); free(F[2]);
 }
 
 /* ------------------------------------------------------------------ RK3 step (Sec. 3.1) */
@@ -937,11 +996,18 @@ static void rk3_step(orc *o) {
     int ns = C->n_substeps;
     apply_wall_bc(o, o->rw, o->ru, o->rv);
     for (int f = 0; f < 5; ++f) memcpy(o->sn[f], field_ptr(o, f), sizeof(double) * field_len(o, f));
+    if (C->tracer) memcpy(o->sn_phi, o->rphi, sizeof(double) * o->ncell);
     const double alpha[3] = {1.0 / 3.0, 0.5, 1.0};
     /* S^t is held in o->rho.. (the state arrays), updated in place at the end of each stage */
     for (int s = 0; s < 3; ++s) {
         slow_rhs(o, o->rho, o->rt, o->ru, o->rv, o->rw);
+        if (C->tracer) {
+            memset(o->msx, 0, sizeof(double) * o->ncell);
+            memset(o->msy, 0, sizeof(double) * o->ncell);
+            memset(o->msz, 0, sizeof(double) * o->nw);
+        }
         if (C->substep_mode == 1) {
+            if (C->tracer) tracer_stage(o, o->rho, alpha[s] * dt, 1);
             /* no substepping: S^(s) = S^n + alpha_s dt f(S^t) */
             for (int f = 0; f < 5; ++f) {
                 double *S = field_ptr(o, f);
@@ -971,6 +1037,7 @@ static void rk3_step(orc *o) {
         memcpy(rho_t, o->rho, sizeof(double) * o->ncell);
         memcpy(rt_t, o->rt, sizeof(double) * o->ncell);
         for (int n = 0; n < nsub; ++n) substep(o, rho_t, rt_t, dtau);
+        if (C->tracer) tracer_stage(o, rho_t, alpha[s] * dt, nsub);
         free(rho_t); free(rt_t);
         /* S^(s) = S^t + X'' */
         for (int f = 0; f < 5; ++f) {
@@ -1008,15 +1075,23 @@ void orc_set_initial(orc *o, const double *dtheta, const double *u, const double
     o->have_state = 1;
 }
 
-/* fields 0..4 = rho, rho theta, rho u, rho v, rho w; 5..7 = base rho0, p0, theta0 (get only) */
+/* fields 0..4 = rho, rho theta, rho u, rho v, rho w; 5..7 = base rho0, p0, theta0 (get only);
+ * 8 = rho phi (passive scalar) */
+/* passive-scalar initial state: rho phi = rho phi0 at cells, with the current rho */
+int orc_set_tracer_initial(orc *o, const double *phi) {
+    for (size_t c = 0; c < o->ncell; ++c) o->rphi[c] = o->rho[c] * phi[c];
+    return 0;
+}
 int orc_get_field(orc *o, int f, double *dst) {
     if (f >= 0 && f < 5) { memcpy(dst, field_ptr(o, f), sizeof(double) * field_len(o, f)); return 0; }
     if (f == 5) { memcpy(dst, o->rho0, sizeof(double) * o->ncell); return 0; }
     if (f == 6) { memcpy(dst, o->p0, sizeof(double) * o->ncell); return 0; }
     if (f == 7) { memcpy(dst, o->th0, sizeof(double) * o->ncell); return 0; }
+    if (f == 8) { memcpy(dst, o->rphi, sizeof(double) * o->ncell); return 0; }
     return -1;
 }
 int orc_set_field(orc *o, int f, const double *src) {
+    if (f == 8) { memcpy(o->rphi, src, sizeof(double) * o->ncell); return 0; }
     if (f < 0 || f >= 5) return -1;
     memcpy(field_ptr(o, f), src, sizeof(double) * field_len(o, f));
     o->have_state = 1;

@@ -47,6 +47,7 @@ class _Cfg(C.Structure):
         ("f_cor", C.c_double), ("u_g", C.c_double), ("v_g", C.c_double),
         ("surface", C.c_int32), ("z0", C.c_double), ("sfc_theta_flux", C.c_double),
         ("theta_s", C.c_double), ("brunt_N", C.c_double), ("p_s", C.c_double),
+        ("tracer", C.c_int32),
     ]
 
 
@@ -80,6 +81,7 @@ class OracleConfig:
     theta_s: float = 300.0
     brunt_N: float = 0.0
     p_s: float = 1.0e5
+    tracer: int = 0
 
 
 _LIB = None
@@ -97,6 +99,7 @@ def _lib():
         L.orc_set_initial.argtypes = [C.c_void_p, dp, dp, dp, dp]
         L.orc_get_field.argtypes = [C.c_void_p, C.c_int, dp]
         L.orc_set_field.argtypes = [C.c_void_p, C.c_int, dp]
+        L.orc_set_tracer_initial.argtypes = [C.c_void_p, dp]
         L.orc_get_geom.argtypes = [C.c_void_p, C.c_int, dp]
         L.orc_step.argtypes = [C.c_void_p, C.c_int]
         L.orc_slow_rhs.argtypes = [C.c_void_p] + [dp] * 8
@@ -134,7 +137,7 @@ def _f64(a):
 
 
 FIELDS = {"rho": 0, "rhotheta": 1, "rhou": 2, "rhov": 3, "rhow": 4,
-          "base_rho": 5, "base_p": 6, "base_theta": 7}
+          "base_rho": 5, "base_p": 6, "base_theta": 7, "rhophi": 8}
 GEOM = {"zc": 0, "Hc": 1, "Hx": 2, "Hy": 3, "hxi_x": 4, "heta_y": 5,
         "zw": 6, "hxi_w": 7, "heta_w": 8, "zn": 9}
 
@@ -177,6 +180,12 @@ class Oracle:
     def set_initial(self, dtheta=None, u=None, v=None, w=None):
         a = [_f64(x) for x in (dtheta, u, v, w)]
         _lib().orc_set_initial(self._h, *[_p(x) for x in a])
+
+    def set_tracer_initial(self, phi):
+        """rho phi = rho phi0 with the current rho (configuration with tracer = 1)."""
+        a = _f64(phi)
+        assert a.shape == self.shape_c
+        _lib().orc_set_tracer_initial(self._h, _p(a))
 
     def get(self, name):
         out = np.empty(self._shape(name), dtype=np.float64)

@@ -67,6 +67,8 @@ class Workload:
     u: Optional[np.ndarray] = None
     v: Optional[np.ndarray] = None
     w: Optional[np.ndarray] = None
+    tracer: int = 0                        # 1: passive scalar rho phi (advanced after the substeps)
+    phi: Optional[np.ndarray] = None       # initial phi at cells (tracer = 1)
     notes: str = ""
 
     @property
@@ -184,6 +186,19 @@ def convective_abl(nx=2048, ny=2048, nz=160, steps=1000, dx=40.0, precision=PREC
     knots = (np.array([0.0, 1000.0, 1100.0, max(top, 1101.0)]),
              np.array([300.0, 300.0, 305.0, 305.0 + 3.0e-3 * (max(top, 1101.0) - 1100.0)]))
     return _abl_common(nx, ny, nz, dx, knots, 400.0, steps, 0.4, "convective_abl", 0.2, precision)
+
+
+def with_tracer(wl: Workload, kind: str = "blob", radius_frac: float = 0.2) -> Workload:
+    """The same case with a passive scalar: phi = 1 everywhere ("one") or a Gaussian blob
+    exp(-r^2/R^2), R = radius_frac x the domain width, centred in x and y at a third of the
+    column height ("blob")."""
+    if kind == "one":
+        return wl.with_(tracer=1, phi=np.ones((wl.nz, wl.ny, wl.nx)))
+    X, Y, Z = cell_coords(wl.nx, wl.ny, wl.zeta, wl.dx, wl.dy)
+    R = radius_frac * wl.nx * wl.dx
+    zc = wl.zeta[-1] / 3.0
+    r2 = (X - 0.5 * wl.nx * wl.dx) ** 2 + (Y - 0.5 * wl.ny * wl.dy) ** 2 * (wl.ny > 4) + (Z - zc) ** 2
+    return wl.with_(tracer=1, phi=np.exp(-r2 / R ** 2))
 
 
 CASES = {

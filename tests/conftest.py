@@ -22,7 +22,7 @@ def oracle_config_from(wl, **over):
                        scal_adv=wl.scal_adv, closure=wl.closure, Cs=wl.Cs, Pr_t=wl.Pr_t,
                        nu=wl.nu, gravity=wl.gravity, f_cor=wl.f_cor, u_g=wl.u_g, v_g=wl.v_g,
                        surface=wl.surface, z0=wl.z0, sfc_theta_flux=wl.sfc_theta_flux,
-                       theta_s=wl.theta_s, brunt_N=wl.brunt_N, p_s=wl.p_s)
+                       theta_s=wl.theta_s, brunt_N=wl.brunt_N, p_s=wl.p_s, tracer=wl.tracer)
     for k, v in over.items():
         setattr(cfg, k, v)
     return cfg
@@ -34,6 +34,8 @@ def make_oracle(wl, init=True, **over):
     o = Oracle(oracle_config_from(wl, **over), wl.zeta, wl.terrain, wl.knots)
     if init:
         o.set_initial(wl.dtheta, wl.u, wl.v, wl.w)
+        if wl.tracer and wl.phi is not None:
+            o.set_tracer_initial(wl.phi)
     return o
 
 
