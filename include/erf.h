@@ -52,7 +52,8 @@ typedef enum {
 
 typedef enum {
     ERF_RHO = 0, ERF_RHOTHETA = 1, ERF_RHOU = 2, ERF_RHOV = 3, ERF_RHOW = 4,
-    ERF_BASE_RHO = 5, ERF_BASE_P = 6, ERF_BASE_THETA = 7     /* base state: get only */
+    ERF_BASE_RHO = 5, ERF_BASE_P = 6, ERF_BASE_THETA = 7,    /* base state: get only */
+    ERF_RHOPHI = 8                  /* passive scalar rho phi at cells (config tracer = 1) */
 } erf_field;
 
 typedef enum { ERF_F64 = 0, ERF_F32 = 1 } erf_dtype;
@@ -93,6 +94,9 @@ typedef struct {
     double theta_s, brunt_N, p_s;   /* base state theta0 = theta_s exp(N^2 z/g), surface pressure at z = 0 */
     int32_t n_knots;                /* > 0: theta0 from a piecewise-linear sounding instead */
     const double *knot_z, *knot_theta;   /* host, n_knots each, read during erf_init_grid only */
+    int32_t tracer;                 /* 1 = advance a passive scalar rho phi (FP64 path; Sec. 3.1: after
+                                       the substeps of each stage, with the stage-averaged momenta
+                                       that advanced rho); 0 = none */
 } erf_config;
 
 /* Diagnostics (Sec. 4.1.2: mass conserved to machine precision). */
@@ -125,7 +129,13 @@ erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config *cfg, void 
 erf_status erf_set_initial(erf_handle *h, const double *dtheta, const double *u, const double *v,
                            const double *w, int32_t is_device);
 
-/* Copies one prognostic field (ERF_RHO..ERF_RHOW) in, converting from src_dtype (erf_dtype). */
+/* Passive-scalar initial state: rho phi = rho phi0 at cells with the current rho (Sec. 3.1,
+ * scalar equation).  phi0 is nz*ny*nx FP64 on the host (is_device = 0) or the device.
+ * ERF_EUNSUPPORTED unless the handle was configured with tracer = 1. */
+erf_status erf_set_tracer_initial(erf_handle *h, const double *phi0, int32_t is_device);
+
+/* Copies one prognostic field (ERF_RHO..ERF_RHOW, ERF_RHOPHI) in, converting from src_dtype
+ * (erf_dtype). */
 erf_status erf_set_state(erf_handle *h, int32_t field, const void *src, int32_t src_is_device,
                          int32_t src_dtype);
 

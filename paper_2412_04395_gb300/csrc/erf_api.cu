@@ -55,6 +55,8 @@ struct erf_handle {
     double *dzeta, *zetac, *s, *sc, *ds, *dzc, *delta2, *rdzeta, *rdzc, *knz, *knt;
     double *rho0, *th0, *p0;
     double *rH3 = nullptr, *rHx3 = nullptr, *rHy3 = nullptr, *rdzw3 = nullptr, *rdz2 = nullptr;
+    // passive scalar (FP64 path): rho phi (stage state), its S^n copy, substep flux sums
+    double *tphi = nullptr, *snphi = nullptr, *msx = nullptr, *msy = nullptr, *msz = nullptr;
     F5 st, sn, x, R;
     double *pp, *pi, *th, *Tp, *Om;
     Tri tri;
@@ -119,6 +121,11 @@ static erf_status validate(const erf_grid_desc *g, const erf_config *c, std::str
             if (g->terrain_nodes[n] != 0.0) { terr = true; break; }
     if (terr && (c->closure != 0 || c->surface != 0)) {
         msg = "subgrid closure / MOST over terrain is not supported (flat grids only)";
+        return ERF_EUNSUPPORTED;
+    }
+    if (c->tracer != 0 && c->tracer != 1) { msg = "tracer must be 0 or 1"; return ERF_EINVAL; }
+    if (c->tracer && c->precision != ERF_PREC_FP64) {
+        msg = "the passive scalar is built on the FP64 path";
         return ERF_EUNSUPPORTED;
     }
     if (terr && c->precision == ERF_PREC_MIXED32) {
@@ -194,6 +201,10 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
     if (terr) {
         H->rH3 = cv.take<double>(nc); H->rHx3 = cv.take<double>(nc); H->rHy3 = cv.take<double>(nc);
         H->rdzw3 = cv.take<double>(nc); H->rdz2 = cv.take<double>(nc);
+    }
+    if (c->tracer) {
+        H->tphi = cv.take<double>(nc); H->snphi = cv.take<double>(nc);
+        H->msx = cv.take<double>(nc); H->msy = cv.take<double>(nc); H->msz = cv.take<double>(nw);
     }
     }
     H->diag_part = cv.take<double>(6 * DIAG_PARTS);
@@ -368,13 +379,22 @@ static void enqueue_step(erf_handle *h, cudaStream_t s) {
     cudaMemcpyAsync(h->sn.u, h->st.u, bc, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(h->sn.v, h->st.v, bc, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(h->sn.w, h->st.w, bw, cudaMemcpyDeviceToDevice, s);
+    if (h->tphi) cudaMemcpyAsync(h->snphi, h->tphi, bc, cudaMemcpyDeviceToDevice, s);
     const double alpha[3] = {1.0 / 3.0, 0.5, 1.0};
     Prep pr{h->ux, h->vy, h->wz, h->mfx, h->mfy, h->rom};
     for (int stage = 0; stage < 3; ++stage) {
         launch_stage_begin(g, cf(h->sn), cf(h->st), h->x, h->pp, h->pi, h->th, h->Tp, h->Om, s);
         launch_slow_rhs(g, ph, cf(h->st), h->pp, h->th, pr, h->ux, h->vy, h->wz, h->mfx, h->mfy, h->rom, h->mu,
                         h->flux, h->R, s);
+        if (h->tphi) {
+            cudaMemsetAsync(h->msx, 0, bc, s);
+            cudaMemsetAsync(h->msy, 0, bc, s);
+            cudaMemsetAsync(h->msz, 0, bw, s);
+        }
         if (c.substep_mode == 1) {
+            if (h->tphi)
+                launch_tracer_stage(g, ph, cf(h->st), h->rom, h->snphi, h->msx, h->msy, h->msz, 1,
+                                    alpha[stage] * c.dt, h->pp, h->flux, h->tphi, s);
             launch_stage_nosub(g, h->st, cf(h->sn), cf(h->R), alpha[stage] * c.dt, s);
             launch_wall_bc(g, h->st.u, h->st.v, h->st.w, s);
             continue;
@@ -386,7 +406,11 @@ static void enqueue_step(erf_handle *h, cudaStream_t s) {
         launch_tri_build(g, ph, h->st.r, h->st.t, h->pi, h->th, dtau, h->tri, h->mfx, h->mfy, s);
         for (int n = 0; n < nsub; ++n)
             launch_substep(g, ph, h->tri, h->pi, h->th, h->mfx, h->mfy, cf(h->R), h->x, h->Om, h->Tp, h->ux, h->vy,
-                           h->wz, dtau, s);
+                           h->wz, h->msx, h->msy, h->msz, dtau, s);
+        // the passive scalar after the substeps, from the stage state S^t (Sec. 3.1)
+        if (h->tphi)
+            launch_tracer_stage(g, ph, cf(h->st), h->rom, h->snphi, h->msx, h->msy, h->msz, nsub,
+                                alpha[stage] * c.dt, h->pp, h->flux, h->tphi, s);
         launch_stage_end(g, h->st, cf(h->x), s);
     }
 }
@@ -540,6 +564,7 @@ static double *field_dev(erf_handle *h, int f, long long &n) {
     case ERF_BASE_RHO: n = g.terrain ? g.nc : g.nz; return h->rho0;
     case ERF_BASE_P: n = g.terrain ? g.nc : g.nz; return h->p0;
     case ERF_BASE_THETA: n = g.terrain ? g.nc : g.nz; return h->th0;
+    case ERF_RHOPHI: return h->tphi;
     }
     return nullptr;
 }
@@ -547,7 +572,8 @@ static double *field_dev(erf_handle *h, int f, long long &n) {
 extern "C" erf_status erf_set_state(erf_handle *h, int32_t field, const void *src, int32_t src_is_device,
                                     int32_t src_dtype) {
     if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
-    if (field < ERF_RHO || field > ERF_RHOW) return fail(h, ERF_EINVAL, "field not settable");
+    if ((field < ERF_RHO || field > ERF_RHOW) && !(field == ERF_RHOPHI && h->tphi))
+        return fail(h, ERF_EINVAL, "field not settable");
     if (!src) return fail(h, ERF_EINVAL, "src is NULL");
     if (src_dtype != ERF_F64 && src_dtype != ERF_F32) return fail(h, ERF_EINVAL, "bad dtype");
     long long n;
@@ -603,10 +629,32 @@ extern "C" erf_status erf_set_state(erf_handle *h, int32_t field, const void *sr
     return ERF_OK;
 }
 
+extern "C" erf_status erf_set_tracer_initial(erf_handle *h, const double *phi0, int32_t is_device) {
+    if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
+    if (!h->tphi) return fail(h, ERF_EUNSUPPORTED, "handle configured without the passive scalar");
+    if (!phi0) return fail(h, ERF_EINVAL, "phi0 is NULL");
+    const Geo &g = h->geo;
+    cudaStream_t s = h->user;
+    const double *d = phi0;
+    cudaError_t e = cudaSuccess;
+    if (!is_device) {
+        e = cudaMemcpyAsync(h->snphi, phi0, g.nc * sizeof(double), cudaMemcpyHostToDevice, s);
+        d = h->snphi;
+    }
+    if (e == cudaSuccess) {
+        launch_tracer_init(g, h->st.r, d, h->tphi, s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && !is_device) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_tracer_initial");
+    return ERF_OK;
+}
+
 extern "C" erf_status erf_get_state(erf_handle *h, int32_t field, void *dst, int32_t dst_is_device,
                                     int32_t dst_dtype) {
     if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
-    if (field < ERF_RHO || field > ERF_BASE_THETA) return fail(h, ERF_EINVAL, "bad field");
+    if ((field < ERF_RHO || field > ERF_BASE_THETA) && !(field == ERF_RHOPHI && h->tphi))
+        return fail(h, ERF_EINVAL, "bad field");
     if (!dst) return fail(h, ERF_EINVAL, "dst is NULL");
     if (dst_dtype != ERF_F64 && dst_dtype != ERF_F32) return fail(h, ERF_EINVAL, "bad dtype");
     long long n;

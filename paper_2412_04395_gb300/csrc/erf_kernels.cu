@@ -706,7 +706,7 @@ __global__ void k_sub_horiz(Geo g, Phys ph, const double *pi, const double *Tt, 
 // H theta^t at x- and y-faces for this stage.  Theta''^tau is kept in Tt.
 __global__ void k_sub_expl(Geo g, Phys ph, const double *th, const double *TX, const double *TY, const double *Rr,
                            const double *Rt, const double *Rw, F5 x, const double *Om, double *Tt, double *X0,
-                           double *Y0, double *Ash, double dtau) {
+                           double *Y0, double *Ash, double *msx, double *msy, double *msz, double dtau) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z, nz = g.nz;
@@ -740,6 +740,11 @@ __global__ void k_sub_expl(Geo g, Phys ph, const double *th, const double *TX, c
             Ash[c] = A;
         }
         x.w[c] = x.w[c] - A + dtau * Rw[c];
+    }
+    if (msx) {   // passive scalar: this substep's perturbation mass fluxes that advance rho''
+        msx[c] += Hx(g, i, j, k) * Uc;
+        msy[c] += Hy(g, i, j, k) * Vc;
+        if (k >= 1) msz[c] += b1 * om_k;
     }
 }
 
@@ -781,7 +786,7 @@ __global__ void __launch_bounds__(128) k_sub_col(int nz, long long nxy, const do
 // Part 3, one thread per cell: Theta'', rho'' from the new Omega'' (beta_2 part), Theta~ of the
 // next substep, and W'' = Omega'' + metric shift at the cell's bottom w-face.
 __global__ void k_sub_fin(Geo g, Phys ph, const double *th, const double *Om, const double *Ash, F5 x, double *Tt,
-                          double dtau) {
+                          double *msz, double dtau) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
@@ -799,6 +804,52 @@ __global__ void k_sub_fin(Geo g, Phys ph, const double *th, const double *Om, co
     double A = 0.0;
     if (g.terrain) A = k >= 1 ? Ash[c] : metric_shift(g, x.u, x.v, i, j, 0);
     x.w[c] = om + A;
+    if (msz && k >= 1) msz[c] += b2 * om;
+}
+
+// ------------------------------------------------------------------ passive scalar (Sec. 3.1)
+// After a stage's substeps: rho phi^(s) = rho phi^n + alpha_s dt R_phi(phi^t), the advective
+// fluxes taking the stage-averaged normal momenta that advanced rho (the stage mass flux plus
+// the mean of the substeps' perturbation fluxes, summed in msx, msy, msz), so that phi = 1 stays
+// 1.  phi^t is interpolated like theta (WENO5).
+__global__ void k_tracer_phi(Geo g, const double *rphi, const double *rho, double *phi) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    phi[c] = rphi[c] / rho[c];
+}
+__global__ void k_tracer_flux(Geo g, Phys ph, const double *ru, const double *rv, const double *rom,
+                              const double *phi, const double *msx, const double *msy, const double *msz,
+                              double rns, double *fx, double *fy, double *fz) {
+    CELL3D_W();
+    const int zf = ph.scal_adv == 1;
+    double q[6];
+    if (k < g.nz) {
+        double mx = Hx(g, i, j, k) * ru[n] + msx[n] * rns;
+        for (int m = 0; m < 6; ++m) q[m] = cval(g, phi, i - 3 + m, j, k);
+        fx[n] = mx * weno5_d(q, sgnd(mx), zf);
+        double my = Hy(g, i, j, k) * rv[n] + msy[n] * rns;
+        for (int m = 0; m < 6; ++m) q[m] = cval(g, phi, i, j - 3 + m, k);
+        fy[n] = my * weno5_d(q, sgnd(my), zf);
+    }
+    if (k == 0 || k == g.nz) { fz[n] = 0.0; return; }
+    double mz = rom[n] + msz[n] * rns;
+    for (int m = 0; m < 6; ++m) q[m] = cval(g, phi, i, j, k - 3 + m);
+    fz[n] = mz * weno5_d(q, sgnd(mz), zf);
+}
+__global__ void k_tracer_update(Geo g, const double *snphi, const double *fx, const double *fy, const double *fz,
+                                double adt, double *rphi) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long c = ((long long)k * g.ny + j) * g.nx + i;
+    double div = (fx[cixw(g, i + 1, j, k)] - fx[c]) * g.rdx + (fy[cixw(g, i, j + 1, k)] - fy[c]) * g.rdy
+               + (fz[c + g.nxy] - fz[c]);
+    rphi[c] = snphi[c] + adt * (-div * rHc(g, i, j, k));
+}
+__global__ void k_tracer_init(Geo g, const double *rho, const double *phi0, double *rphi) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    rphi[c] = rho[c] * phi0[c];
 }
 
 __global__ void k_stage_end(Geo g, F5 st, CF5 x) {
@@ -981,13 +1032,28 @@ void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const dou
 }
 void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *pi, const double *th, const double *TX,
                     const double *TY, CF5 R, F5 x, double *Om, double *Tp, double *X0, double *Y0, double *Ash,
-                    double dtau, cudaStream_t s) {
+                    double *msx, double *msy, double *msz, double dtau, cudaStream_t s) {
     const dim3 g3c((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)g.nz);
     LAUNCH("sub_horiz", s, k_sub_horiz<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pi, Tp, R.u, R.v, x.u, x.v, dtau));
-    LAUNCH("sub_expl", s, k_sub_expl<<<g3c, 128, 0, s>>>(g, ph, th, TX, TY, R.r, R.t, R.w, x, Om, Tp, X0, Y0, Ash, dtau));
+    LAUNCH("sub_expl", s, k_sub_expl<<<g3c, 128, 0, s>>>(g, ph, th, TX, TY, R.r, R.t, R.w, x, Om, Tp, X0, Y0, Ash,
+                                                         msx, msy, msz, dtau));
     LAUNCH("sub_col", s, k_sub_col<<<nblk(g.nxy, 128), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q, X0, Y0,
                                                                     x.w, Om, dtau * 0.5 * ph.g));
-    LAUNCH("sub_fin", s, k_sub_fin<<<g3c, 128, 0, s>>>(g, ph, th, Om, Ash, x, Tp, dtau));
+    LAUNCH("sub_fin", s, k_sub_fin<<<g3c, 128, 0, s>>>(g, ph, th, Om, Ash, x, Tp, msz, dtau));
+}
+void launch_tracer_stage(const Geo &g, const Phys &ph, CF5 st, const double *rom, const double *snphi,
+                         const double *msx, const double *msy, const double *msz, int nsub, double adt,
+                         double *phi, double *flux, double *rphi, cudaStream_t s) {
+    const dim3 g3w((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)(g.nz + 1));
+    const dim3 g3c((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)g.nz);
+    double *fx = flux, *fy = flux + g.nw, *fz = flux + 2 * g.nw;
+    LAUNCH("tracer_phi", s, k_tracer_phi<<<nblk(g.nc, BS), BS, 0, s>>>(g, rphi, st.r, phi));
+    LAUNCH("tracer_flux", s, k_tracer_flux<<<g3w, 128, 0, s>>>(g, ph, st.u, st.v, rom, phi, msx, msy, msz,
+                                                                1.0 / nsub, fx, fy, fz));
+    LAUNCH("tracer_update", s, k_tracer_update<<<g3c, 128, 0, s>>>(g, snphi, fx, fy, fz, adt, rphi));
+}
+void launch_tracer_init(const Geo &g, const double *rho, const double *phi0, double *rphi, cudaStream_t s) {
+    LAUNCH("tracer_init", s, k_tracer_init<<<nblk(g.nc, BS), BS, 0, s>>>(g, rho, phi0, rphi));
 }
 void launch_stage_end(const Geo &g, F5 st, CF5 x, cudaStream_t s) {
     LAUNCH("stage_end", s, k_stage_end<<<nblk(g.nw, BS), BS, 0, s>>>(g, st, x));

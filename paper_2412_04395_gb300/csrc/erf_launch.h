@@ -24,7 +24,11 @@ void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const dou
                       const double *th, double dtau, Tri tr, double *TX, double *TY, cudaStream_t s);
 void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *pi, const double *th, const double *TX,
                     const double *TY, CF5 R, F5 x, double *Om, double *Tp, double *X0, double *Y0, double *Ash,
-                    double dtau, cudaStream_t s);
+                    double *msx, double *msy, double *msz, double dtau, cudaStream_t s);
+void launch_tracer_stage(const Geo &g, const Phys &ph, CF5 st, const double *rom, const double *snphi,
+                         const double *msx, const double *msy, const double *msz, int nsub, double adt,
+                         double *phi, double *flux, double *rphi, cudaStream_t s);
+void launch_tracer_init(const Geo &g, const double *rho, const double *phi0, double *rphi, cudaStream_t s);
 void launch_stage_end(const Geo &g, F5 st, CF5 x, cudaStream_t s);
 void launch_stage_nosub(const Geo &g, F5 st, CF5 sn, CF5 R, double adt, cudaStream_t s);
 void launch_diag(const Geo &g, CF5 st, double dt, double *part, double *out, cudaStream_t s);

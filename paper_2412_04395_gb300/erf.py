@@ -18,7 +18,7 @@ ERF_OK, ERF_EINVAL, ERF_ENOSPACE, ERF_ECUDA, ERF_ENONFINITE, ERF_ESTATE, ERF_EUN
 STATUS_NAMES = {0: "ERF_OK", -1: "ERF_EINVAL", -2: "ERF_ENOSPACE", -3: "ERF_ECUDA", -4: "ERF_ENONFINITE",
                 -5: "ERF_ESTATE", -6: "ERF_EUNSUPPORTED"}
 FIELDS = {"rho": 0, "rhotheta": 1, "rhou": 2, "rhov": 3, "rhow": 4,
-          "base_rho": 5, "base_p": 6, "base_theta": 7}
+          "base_rho": 5, "base_p": 6, "base_theta": 7, "rhophi": 8}
 ERF_F64, ERF_F32 = 0, 1
 
 # symbols the library must export (checked by the CPU tests)
@@ -26,7 +26,7 @@ EXPORTS = ["erf_workspace_bytes", "erf_init_grid", "erf_set_initial", "erf_set_s
            "erf_get_state", "erf_diagnostics", "erf_profile_steps", "erf_last_error", "erf_destroy",
            "erf_reduce_state_noalloc", "erf_train_scratch_bytes", "erf_train_closure", "erf_closure_grad",
            "erf_column_stats", "erf_standardise", "erf_set_closure_weights", "erf_closure_features",
-           "erf_closure_fields", "erf_filter_state"]
+           "erf_closure_fields", "erf_filter_state", "erf_set_tracer_initial"]
 
 
 class ErfError(RuntimeError):
@@ -52,7 +52,7 @@ class Config(C.Structure):
                 ("surface", C.c_int32), ("z0", C.c_double), ("sfc_theta_flux", C.c_double),
                 ("theta_s", C.c_double), ("brunt_N", C.c_double), ("p_s", C.c_double),
                 ("n_knots", C.c_int32), ("knot_z", C.POINTER(C.c_double)),
-                ("knot_theta", C.POINTER(C.c_double))]
+                ("knot_theta", C.POINTER(C.c_double)), ("tracer", C.c_int32)]
 
 
 class Diag(C.Structure):
@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH):
     L.erf_workspace_bytes.argtypes = [C.POINTER(GridDesc), C.POINTER(Config), C.POINTER(C.c_size_t)]
     L.erf_init_grid.argtypes = [C.POINTER(GridDesc), C.POINTER(Config), vp, C.c_size_t, vp, C.POINTER(vp)]
     L.erf_set_initial.argtypes = [vp, vp, vp, vp, vp, C.c_int32]
+    L.erf_set_tracer_initial.argtypes = [vp, vp, C.c_int32]
     L.erf_set_state.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_int32]
     L.erf_rk3_step.argtypes = [vp, C.c_int32]
     L.erf_get_state.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_int32]
@@ -106,7 +107,7 @@ def load_library(path: str = LIB_PATH):
     for name in ("erf_workspace_bytes", "erf_init_grid", "erf_set_initial", "erf_set_state", "erf_rk3_step",
                  "erf_get_state", "erf_diagnostics", "erf_profile_steps", "erf_train_closure", "erf_closure_grad",
                  "erf_column_stats", "erf_standardise", "erf_set_closure_weights", "erf_closure_features",
-                 "erf_closure_fields", "erf_filter_state"):
+                 "erf_closure_fields", "erf_filter_state", "erf_set_tracer_initial"):
         getattr(L, name).restype = C.c_int
     _LIB = L
     return L
@@ -149,7 +150,7 @@ def make_structs(wl):
                Pr_t=wl.Pr_t, nu=wl.nu, precision=wl.precision, gravity=wl.gravity, f_cor=wl.f_cor,
                u_g=wl.u_g, v_g=wl.v_g, surface=wl.surface, z0=wl.z0, sfc_theta_flux=wl.sfc_theta_flux,
                theta_s=wl.theta_s, brunt_N=wl.brunt_N, p_s=wl.p_s, n_knots=nk, knot_z=_dp(kz),
-               knot_theta=_dp(kt))
+               knot_theta=_dp(kt), tracer=getattr(wl, "tracer", 0))
     return g, c, keep
 
 
@@ -225,6 +226,11 @@ class Dycore:
     def erf_set_initial_device(self, dtheta=None, u=None, v=None, w=None):
         ptrs = [None if t is None else t.data_ptr() for t in (dtheta, u, v, w)]
         _check(self.L, self.h, self.L.erf_set_initial(self.h, *ptrs, 1))
+
+    def erf_set_tracer_initial(self, phi):
+        a = _f64(phi)
+        assert a.shape == self.shape_c
+        _check(self.L, self.h, self.L.erf_set_tracer_initial(self.h, a.ctypes.data, 0))
 
     def erf_set_state(self, name, arr):
         import torch
