@@ -238,6 +238,17 @@ erf_status erf_reduce_state_noalloc(int32_t nx, int32_t ny, int32_t nz, double d
                                     const double *d_rhou, const double *d_rhov, const double *d_rhow,
                                     double *d_out, void *cuda_stream);
 
+/* Runtime options (no counterpart in the paper).
+ *   ERF_OPT_TMA_STENCILS: 1 (default) stages the 3D stencils of the mixed-precision flux kernels
+ *   in shared memory with TMA tile loads where the grid allows it (nx % 4 == 0, nx >= 64,
+ *   ny >= 16, nz >= 16); 0 uses plain loads.  Both give bit-identical results.  A TMA wait that
+ *   gives up makes the next erf_diagnostics return ERF_ECUDA.
+ * erf_set_option drops the captured step graph; erf_get_option reports whether the option is in
+ * effect (for ERF_OPT_TMA_STENCILS: 1 if the TMA kernels run). */
+typedef enum { ERF_OPT_TMA_STENCILS = 1 } erf_option;
+erf_status erf_set_option(erf_handle *h, int32_t option, int64_t value);
+erf_status erf_get_option(erf_handle *h, int32_t option, int64_t *value);
+
 /* Message of the last failed call on h (or of the last failed erf_init_grid if h is NULL). */
 const char *erf_last_error(const erf_handle *h);
 

@@ -69,6 +69,9 @@ struct erf_handle {
     float *mpp, *mpi, *mthp, *mTp, *mOm, *mux, *mvy, *mwz, *mmfx, *mmfy, *mmu, *mbase;
     double *mdbuf, *mrt0;
     float *mflux = nullptr;                 // slow-tendency face fluxes (3 planes of nw)
+    MxTma tma{};                            // TMA tile maps of the stencil fields
+    bool tma_enabled = true;
+    unsigned *kerr = nullptr;               // set by a kernel whose bounded wait gave up
     float *mX0 = nullptr, *mY0 = nullptr;   // beta-weighted Theta'', rho'' of the vertical substep (in mflux)
     MxBase mb;
     // learned closure
@@ -77,6 +80,13 @@ struct erf_handle {
     unsigned *cl_nfb = nullptr;
     bool cl_ready = false;
 };
+
+// TMA tile maps of the mixed path's stencil fields (theta' and the face velocities)
+static bool mx_encode_tiles(erf_handle *h) {
+    const Geo &g = h->geo;
+    return mx_encode_cell_tile_map(&h->tma.thp, h->mthp, g, g.nz) && mx_encode_cell_tile_map(&h->tma.ux, h->mux, g, g.nz) &&
+           mx_encode_cell_tile_map(&h->tma.vy, h->mvy, g, g.nz) && mx_encode_cell_tile_map(&h->tma.wz, h->mwz, g, g.nz + 1);
+}
 
 static erf_status fail(erf_handle *h, erf_status st, const std::string &msg) {
     if (h) h->err = msg;
@@ -207,6 +217,7 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
         H->msx = cv.take<double>(nc); H->msy = cv.take<double>(nc); H->msz = cv.take<double>(nw);
     }
     }
+    H->kerr = cv.take<unsigned>(4);
     H->diag_part = cv.take<double>(6 * DIAG_PARTS);
     H->diag_out = cv.take<double>(8);
     return cv.off + 256;
@@ -315,6 +326,7 @@ extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config 
     } else {
         CK(cudaMemsetAsync(h->hn, 0, nxy * sizeof(double), st), "zero terrain");
     }
+    CK(cudaMemsetAsync(h->kerr, 0, 4 * sizeof(unsigned), st), "zero error word");
     launch_terrain(h->geo, h->hn, h->hc, h->hxf, h->hyf, h->gxc, h->gyc, h->g4x, h->g4y, st);
     if (h->geo.terrain && h->rH3)
         launch_terrain_recip(h->geo, h->rH3, h->rHx3, h->rHy3, h->rdzw3, h->rdz2, st);
@@ -324,6 +336,8 @@ extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config 
         mx_build_base(h->geo, cfg->Cs, grid->dx, grid->dy, cfg->gravity, h->mbase, h->mrt0, st);
         h->mb = mx_base_view(h->mbase, h->mrt0, nz);
         mx_base_scalars(h->mb, h->geo, h->ph);
+        h->tma.err = h->kerr;
+        h->tma.use = mx_encode_tiles(h) ? 1 : 0;
     }
     CK(cudaGetLastError(), "init kernels");
     CK(cudaStreamSynchronize(st), "init sync");   // host vectors above must outlive the copies
@@ -352,7 +366,7 @@ static void enqueue_step_mixed(erf_handle *h, cudaStream_t s) {
         mx_stage_begin(g, h->mb, cf(h->msn), cf(h->mst), h->mx, h->mpp, h->mpi, h->mthp, h->mTp, h->mOm, s);
         ClIn clin{h->cl_w, h->cl_b, h->cl_stats, h->cl_out, h->cl_nfb};
         mx_slow_rhs(g, h->mb, ph, cf(h->mst), h->mpp, h->mthp, h->mux, h->mvy, h->mwz, h->mmfx, h->mmfy, h->mmu,
-                    h->mflux, h->mR, s, h->cl_ready ? &clin : nullptr);
+                    h->mflux, h->mR, s, h->cl_ready ? &clin : nullptr, &h->tma);
         int nsub = stage == 0 ? 1 : (stage == 1 ? c.n_substeps / 2 : c.n_substeps);
         double dtau = stage == 0 ? c.dt / 3.0 : c.dt / c.n_substeps;
         mx_tri_build(g, h->mb, ph, h->mst.r, h->mst.t, h->mpi, h->mthp, dtau, h->mtri, s);
@@ -702,9 +716,12 @@ extern "C" erf_status erf_diagnostics(erf_handle *h, erf_diag *out) {
     if (h->mixed) mx_diag(h->geo, h->mb, cf(h->mst), h->cfg.dt, h->diag_part, h->diag_out, h->user);
     else launch_diag(h->geo, cf(h->st), h->cfg.dt, h->diag_part, h->diag_out, h->user);
     double v[6];
+    unsigned kerr = 0;
     cudaError_t e = cudaMemcpyAsync(v, h->diag_out, sizeof(v), cudaMemcpyDeviceToHost, h->user);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&kerr, h->kerr, sizeof(kerr), cudaMemcpyDeviceToHost, h->user);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->user);
     if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics");
+    if (kerr) return fail(h, ERF_ECUDA, "a kernel's bounded wait for its TMA tile gave up; results are invalid");
     out->mass = v[0];
     out->max_abs_w = v[1];
     out->theta_min = v[2];
@@ -714,6 +731,24 @@ extern "C" erf_status erf_diagnostics(erf_handle *h, erf_diag *out) {
     out->steps_done = h->steps_done;
     out->kernels_per_step = h->kernels_per_step;
     if (out->nonfinite) return fail(h, ERF_ENONFINITE, "state holds non-finite values");
+    return ERF_OK;
+}
+
+extern "C" erf_status erf_set_option(erf_handle *h, int32_t option, int64_t value) {
+    if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
+    if (option != ERF_OPT_TMA_STENCILS) return fail(h, ERF_EINVAL, "unknown option");
+    h->tma_enabled = value != 0;
+    if (h->mixed)
+        h->tma.use = (h->tma_enabled && mx_encode_tiles(h)) ? 1 : 0;
+    // the captured step graph holds the previous choice
+    if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    return ERF_OK;
+}
+extern "C" erf_status erf_get_option(erf_handle *h, int32_t option, int64_t *value) {
+    if (!h || !value) return fail(h, ERF_EINVAL, "NULL argument");
+    if (option != ERF_OPT_TMA_STENCILS) return fail(h, ERF_EINVAL, "unknown option");
+    *value = (h->mixed && h->tma.use) ? 1 : 0;
     return ERF_OK;
 }
 

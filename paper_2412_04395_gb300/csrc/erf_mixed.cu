@@ -15,6 +15,7 @@
 #include "erf_launch.h"
 #include "erf_mixed.h"
 #include "erf_stencil.cuh"
+#include "erf_tma.cuh"
 
 #include <math.h>
 
@@ -324,6 +325,196 @@ __global__ void k_mx_flux_theta(Geo g, MxBase mb, Phys ph, const float *mfx, con
     }
     fz[n] = W * (dth0(mb, ku, k - 1) + tu + weno5<float>(q, sg, zf));
 }
+// The same theta fluxes with the stencil staged in shared memory.  A block of 32 x 4 columns and 4
+// levels loads one (32+8) x (4+6) x (4+6) tile of theta' by TMA, starting 4 cells left of the
+// block (16-byte aligned x), 3 cells before it in y and 3 levels below it.  Halo cells outside the
+// periodic domain in x or y (read as zeros by the TMA unit) are then filled by plain loads from the
+// wrapped positions; levels outside [0, nz) are never read, since the wall reflection maps
+// them to levels inside the tile.  Every stencil read is then a shared-memory load at a fixed
+// offset.  Requires nx % 4 == 0 (16-byte row stride), nx >= 64, ny >= 16, nz >= 16.
+constexpr int FT_TX = 32, FT_TY = 4, FT_TZ = 4;
+constexpr int FT_BX = FT_TX + 8, FT_BY = FT_TY + 6, FT_BZ = FT_TZ + 6;
+using FtTile = float[FT_BZ][FT_BY][FT_BX];
+
+// Loads the tile of a block (box origin x0 - 4, y0 - 3, z0 - 3) by TMA and patches the periodic
+// halo; nlev = levels of the field (nz for cell fields, nz + 1 for w-faces).  Returns false (on
+// every thread of the block) if the bounded wait gave up; the error word is then set.
+__device__ __forceinline__ bool ft_load_tile(FtTile &tile, uint64_t *bar, const CUtensorMap *map, const Geo &g,
+                                             const float *src, int nlev, int bx0, int by0, int bz0, unsigned *err) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(bar, (unsigned)sizeof(FtTile));
+        tma_load_3d(&tile[0][0][0], map, bx0, by0, bz0, bar);
+    }
+    bool ok = mbar_wait_bounded(bar, 0, TMA_MAX_POLLS);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+            atomicOr(err, 1u);
+            mbar_wait_bounded(bar, 0, TMA_MAX_POLLS);   // let the copy in flight land before exiting
+        }
+        return false;
+    }
+    if (bx0 < 0 || bx0 + FT_BX > g.nx || by0 < 0 || by0 + FT_BY > g.ny) {
+        for (int q = tid; q < FT_BX * FT_BY * FT_BZ; q += nth) {
+            int lx = q % FT_BX, ly = (q / FT_BX) % FT_BY, lz = q / (FT_BX * FT_BY);
+            int gx = bx0 + lx, gy = by0 + ly, gz = bz0 + lz;
+            if (gz < 0 || gz >= nlev) continue;
+            if (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny) continue;
+            gx += gx < 0 ? g.nx : (gx >= g.nx ? -g.nx : 0);
+            gy += gy < 0 ? g.ny : (gy >= g.ny ? -g.ny : 0);
+            tile[lz][ly][lx] = __ldg(src + ((long long)gz * g.ny + gy) * g.nx + gx);
+        }
+    }
+    __syncthreads();
+    return true;
+}
+__global__ void __launch_bounds__(FT_TX * FT_TY) k_mx_flux_theta_tma(const __grid_constant__ CUtensorMap tmap, Geo g,
+                                                                      MxBase mb, Phys ph, const float *mfx,
+                                                                      const float *mfy, const float *rw,
+                                                                      const float *thp, float *fx, float *fy,
+                                                                      float *fz, unsigned *err) {
+    __shared__ __align__(128) FtTile tile;
+    __shared__ __align__(8) uint64_t bar;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = blockIdx.x * FT_TX, y0 = blockIdx.y * FT_TY, z0 = blockIdx.z * FT_TZ;
+    const int bz0 = z0 - 3;
+    if (!ft_load_tile(tile, &bar, &tmap, g, thp, g.nz, x0 - 4, y0 - 3, bz0, err)) return;
+    const int i = x0 + tx, j = y0 + ty;
+    if (i >= g.nx || j >= g.ny) return;
+    const int zf = ph.scal_adv == 1;
+    const int lx = tx + 4, ly = ty + 3;
+    auto T = [&](int k, int dy, int dx) { return tile[kref(k, g.nz) - bz0][ly + dy][lx + dx]; };
+    float q[6];
+    for (int kk = 0; kk < FT_TZ; ++kk) {
+        const int k = z0 + kk;
+        if (k >= g.nz) break;
+        const long long n = ((long long)k * g.ny + j) * g.nx + i;
+        float mf = __ldg(mfx + n), sg = sgnT<float>(mf);
+        float tu = T(k, 0, sg >= 0.f ? -1 : 0);
+        for (int m = 0; m < 6; ++m) q[m] = T(k, 0, m - 3) - tu;
+        fx[n] = mf * (tu + weno5<float>(q, sg, zf));
+        mf = __ldg(mfy + n); sg = sgnT<float>(mf);
+        tu = T(k, sg >= 0.f ? -1 : 0, 0);
+        for (int m = 0; m < 6; ++m) q[m] = T(k, m - 3, 0) - tu;
+        fy[n] = mf * (tu + weno5<float>(q, sg, zf));
+        if (k == 0) continue;   // wall: the bottom face carries no flux (never read)
+        float W = __ldg(rw + n);
+        sg = sgnT<float>(W);
+        int ku = sg >= 0.f ? k - 1 : k;
+        tu = T(ku, 0, 0);
+        for (int m = 0; m < 6; ++m) {
+            int km = k - 3 + m;
+            q[m] = dth0(mb, km, ku) + (T(km, 0, 0) - tu);
+        }
+        fz[n] = W * (dth0(mb, ku, k - 1) + tu + weno5<float>(q, sg, zf));
+    }
+}
+
+// Momentum fluxes with the advected velocity staged in shared memory (same tiles; comp 0: u at
+// x-faces, 1: v at y-faces, both [nz] levels; 2: w at w-faces, [nz+1] levels, odd reflection about
+// the walls).  Blocks cover levels 0..nz so that the wall fluxes (zero) are written as well.
+template <int COMP>
+__global__ void __launch_bounds__(FT_TX * FT_TY) k_mx_flux_mom_tma(const __grid_constant__ CUtensorMap tmap, Geo g,
+                                                                    const float *vel, const float *mfx,
+                                                                    const float *mfy, const float *rw, float *fx,
+                                                                    float *fy, float *fz, unsigned *err) {
+    __shared__ __align__(128) FtTile tile;
+    __shared__ __align__(8) uint64_t bar;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = blockIdx.x * FT_TX, y0 = blockIdx.y * FT_TY, z0 = blockIdx.z * FT_TZ;
+    const int bz0 = z0 - 3;
+    const int nlev = COMP == 2 ? g.nz + 1 : g.nz;
+    if (!ft_load_tile(tile, &bar, &tmap, g, vel, nlev, x0 - 4, y0 - 3, bz0, err)) return;
+    const int i = x0 + tx, j = y0 + ty;
+    if (i >= g.nx || j >= g.ny) return;
+    const int lx = tx + 4, ly = ty + 3, nz = g.nz;
+    const long long nxy = g.nxy;
+    const long long oxm = i > 0 ? -1 : g.nx - 1, oxp = i + 1 < g.nx ? 1 : 1 - g.nx;
+    const long long oym = j > 0 ? -(long long)g.nx : nxy - g.nx, oyp = j + 1 < g.ny ? (long long)g.nx : (long long)g.nx - nxy;
+    // cell-type field (u, v): wall-reflected level; w: odd reflection about the wall values
+    auto C = [&](int k, int dy, int dx) { return tile[kref(k, nz) - bz0][ly + dy][lx + dx]; };
+    auto Wv = [&](int k) {
+        if (k < 0) return 2.f * tile[0 - bz0][ly][lx] - tile[-k - bz0][ly][lx];
+        if (k > nz) return 2.f * tile[nz - bz0][ly][lx] - tile[2 * nz - k - bz0][ly][lx];
+        return tile[k - bz0][ly][lx];
+    };
+    float q[6];
+    for (int kk = 0; kk < FT_TZ; ++kk) {
+        const int k = z0 + kk;
+        if (k > nz) break;
+        const long long n = ((long long)k * g.ny + j) * g.nx + i;
+        if (COMP == 0) {
+            if (k < nz) {
+                float adv = 0.5f * (__ldg(mfx + n) + __ldg(mfx + n + oxp));
+                for (int m = 0; m < 6; ++m) q[m] = C(k, 0, m - 2);
+                fx[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+                adv = 0.5f * (__ldg(mfy + n + oxm) + __ldg(mfy + n));
+                for (int m = 0; m < 6; ++m) q[m] = C(k, m - 3, 0);
+                fy[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+            }
+            if (k == 0 || k == nz) { fz[n] = 0.f; continue; }
+            float adv = 0.5f * (__ldg(rw + n + oxm) + __ldg(rw + n));
+            for (int m = 0; m < 6; ++m) q[m] = C(k - 3 + m, 0, 0);
+            fz[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+        } else if (COMP == 1) {
+            if (k < nz) {
+                float adv = 0.5f * (__ldg(mfx + n + oym) + __ldg(mfx + n));
+                for (int m = 0; m < 6; ++m) q[m] = C(k, 0, m - 3);
+                fx[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+                adv = 0.5f * (__ldg(mfy + n) + __ldg(mfy + n + oyp));
+                for (int m = 0; m < 6; ++m) q[m] = C(k, m - 2, 0);
+                fy[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+            }
+            if (k == 0 || k == nz) { fz[n] = 0.f; continue; }
+            float adv = 0.5f * (__ldg(rw + n + oym) + __ldg(rw + n));
+            for (int m = 0; m < 6; ++m) q[m] = C(k - 3 + m, 0, 0);
+            fz[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+        } else {
+            if (k < nz) {
+                float wa = k == 0 ? 0.f : __ldg(rw + n), wb = k + 1 == nz ? 0.f : __ldg(rw + n + nxy);
+                float adv = 0.5f * (wa + wb);
+                for (int m = 0; m < 6; ++m) q[m] = Wv(k - 2 + m);
+                fz[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+            }
+            if (k == 0 || k == nz) { fx[n] = 0.f; fy[n] = 0.f; continue; }
+            float adv = 0.5f * (__ldg(mfx + n - nxy) + __ldg(mfx + n));
+            for (int m = 0; m < 6; ++m) q[m] = tile[k - bz0][ly][lx + m - 3];
+            fx[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+            adv = 0.5f * (__ldg(mfy + n - nxy) + __ldg(mfy + n));
+            for (int m = 0; m < 6; ++m) q[m] = tile[k - bz0][ly + m - 3][lx];
+            fy[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+        }
+    }
+}
+
+// host: a 3D tiled tensor map over an FP32 field [nlev][ny][nx] with the tile box above, or false
+// when the driver entry point or the shape does not allow it
+bool mx_encode_cell_tile_map(CUtensorMap *map, const float *base, const Geo &g, int nlev) {
+    if (g.nx % 4 != 0 || g.nx < 64 || g.ny < 16 || g.nz < 16) return false;
+    using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<EncodeFn>(fn);
+    }
+    cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)nlev};
+    cuuint64_t strides[2] = {(cuuint64_t)g.nx * sizeof(float), (cuuint64_t)g.nx * g.ny * sizeof(float)};
+    cuuint32_t box[3] = {FT_BX, FT_BY, FT_BZ};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // momenta (upwind-5, reading R5): the same face and edge placement as the FP64 path
 __global__ void k_mx_flux_u(Geo g, const float *ux, const float *mfx, const float *mfy, const float *rw, float *fx,
                             float *fy, float *fz) {
@@ -800,7 +991,7 @@ void mx_stage_begin(const Geo &g, const MxBase &mb, CF5f sn, CF5f st, F5f x, flo
 }
 void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const float *pp, const float *thp,
                  float *ux, float *vy, float *wz, float *mfx, float *mfy, float *mu, float *flux, F5f R, cudaStream_t s,
-                 const ClIn *cl) {
+                 const ClIn *cl, const MxTma *tma) {
     mx_launch("mx_prep", s, [&] { k_mx_prep<<<g3(g, g.nz + 1), MBX, 0, s>>>(g, mb, st, ux, vy, wz, mfx, mfy); });
     int learned = ph.closure == 3 && cl;
     int sgs = (ph.closure == 1 || ph.closure == 2 || (ph.surface == 1 && !learned)) ? 1 : 0;
@@ -817,15 +1008,51 @@ void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const 
     float *ax = flux, *ay = flux + g.nw, *az = flux + 2 * g.nw;
     FluxF fl{ax, ay, az};
     const dim3 gw = g3(g, g.nz + 1);
-    mx_launch("mx_flux_theta", s, [&] { k_mx_flux_theta<<<gw, MBX, 0, s>>>(g, mb, ph, mfx, mfy, st.w, thp, ax, ay, az); });
+    if (tma && tma->use) {
+        const dim3 gt((unsigned)((g.nx + FT_TX - 1) / FT_TX), (unsigned)((g.ny + FT_TY - 1) / FT_TY),
+                      (unsigned)((g.nz + FT_TZ - 1) / FT_TZ));
+        mx_launch("mx_flux_theta", s, [&] {
+            k_mx_flux_theta_tma<<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->thp, g, mb, ph, mfx, mfy, st.w, thp, ax, ay, az,
+                                                                   tma->err);
+        });
+    } else {
+        mx_launch("mx_flux_theta", s, [&] { k_mx_flux_theta<<<gw, MBX, 0, s>>>(g, mb, ph, mfx, mfy, st.w, thp, ax, ay, az); });
+    }
     mx_launch("mx_rhs_cells", s, [&] {
         k_mx_rhs_cells<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, pr, st.w, thp, st.r, mu, sgs, fl, R.r, R.t);
     });
-    mx_launch("mx_flux_u", s, [&] { k_mx_flux_u<<<gw, MBX, 0, s>>>(g, ux, mfx, mfy, st.w, ax, ay, az); });
+    if (tma && tma->use) {
+        const dim3 gt((unsigned)((g.nx + FT_TX - 1) / FT_TX), (unsigned)((g.ny + FT_TY - 1) / FT_TY),
+                      (unsigned)((g.nz + 1 + FT_TZ - 1) / FT_TZ));
+        mx_launch("mx_flux_u", s, [&] {
+            k_mx_flux_mom_tma<0><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->ux, g, ux, mfx, mfy, st.w, ax, ay, az,
+                                                                      tma->err);
+        });
+    } else {
+        mx_launch("mx_flux_u", s, [&] { k_mx_flux_u<<<gw, MBX, 0, s>>>(g, ux, mfx, mfy, st.w, ax, ay, az); });
+    }
     mx_launch("mx_rhs_u", s, [&] { k_mx_rhs_u<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, fl, R.u); });
-    mx_launch("mx_flux_v", s, [&] { k_mx_flux_v<<<gw, MBX, 0, s>>>(g, vy, mfx, mfy, st.w, ax, ay, az); });
+    if (tma && tma->use) {
+        const dim3 gt((unsigned)((g.nx + FT_TX - 1) / FT_TX), (unsigned)((g.ny + FT_TY - 1) / FT_TY),
+                      (unsigned)((g.nz + 1 + FT_TZ - 1) / FT_TZ));
+        mx_launch("mx_flux_v", s, [&] {
+            k_mx_flux_mom_tma<1><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->vy, g, vy, mfx, mfy, st.w, ax, ay, az,
+                                                                      tma->err);
+        });
+    } else {
+        mx_launch("mx_flux_v", s, [&] { k_mx_flux_v<<<gw, MBX, 0, s>>>(g, vy, mfx, mfy, st.w, ax, ay, az); });
+    }
     mx_launch("mx_rhs_v", s, [&] { k_mx_rhs_v<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, fl, R.v); });
-    mx_launch("mx_flux_w", s, [&] { k_mx_flux_w<<<gw, MBX, 0, s>>>(g, wz, mfx, mfy, st.w, ax, ay, az); });
+    if (tma && tma->use) {
+        const dim3 gt((unsigned)((g.nx + FT_TX - 1) / FT_TX), (unsigned)((g.ny + FT_TY - 1) / FT_TY),
+                      (unsigned)((g.nz + 1 + FT_TZ - 1) / FT_TZ));
+        mx_launch("mx_flux_w", s, [&] {
+            k_mx_flux_mom_tma<2><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->wz, g, wz, mfx, mfy, st.w, ax, ay, az,
+                                                                      tma->err);
+        });
+    } else {
+        mx_launch("mx_flux_w", s, [&] { k_mx_flux_w<<<gw, MBX, 0, s>>>(g, wz, mfx, mfy, st.w, ax, ay, az); });
+    }
     mx_launch("mx_rhs_w", s, [&] { k_mx_rhs_w<<<gw, MBX, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, fl, R.w); });
 }
 void mx_slow_prep_only(const Geo &g, const MxBase &mb, CF5f st, float *ux, float *vy, float *wz, float *mfx,

@@ -1,5 +1,6 @@
 // Mixed-precision (FP32 perturbation) path: data structures and launchers.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "erf_dev.cuh"
@@ -88,9 +89,17 @@ void mx_to_full(const Geo &g, const float *src, double *dst, int field, long lon
 void mx_wall_bc(const Geo &g, float *rw, cudaStream_t s);
 void mx_stage_begin(const Geo &g, const MxBase &mb, CF5f sn, CF5f st, F5f x, float *pp, float *pi, float *thp,
                     float *Tp, float *Om, cudaStream_t s);
+// TMA tile maps of the stencil fields (use = 0: the plain-load kernels) and the device word a
+// kernel sets when a bounded wait gives up
+struct MxTma {
+    CUtensorMap thp, ux, vy, wz;
+    int use;
+    unsigned *err;
+};
+bool mx_encode_cell_tile_map(CUtensorMap *map, const float *base, const Geo &g, int nlev);
 void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const float *pp, const float *thp,
                  float *ux, float *vy, float *wz, float *mfx, float *mfy, float *mu, float *flux, F5f R, cudaStream_t s,
-                 const ClIn *cl);
+                 const ClIn *cl, const MxTma *tma);
 void mx_slow_prep_only(const Geo &g, const MxBase &mb, CF5f st, float *ux, float *vy, float *wz, float *mfx,
                        float *mfy, cudaStream_t s);
 void mx_tri_build(const Geo &g, const MxBase &mb, const Phys &ph, const float *dr, const float *dT, const float *pi,

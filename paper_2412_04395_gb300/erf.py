@@ -20,13 +20,15 @@ STATUS_NAMES = {0: "ERF_OK", -1: "ERF_EINVAL", -2: "ERF_ENOSPACE", -3: "ERF_ECUD
 FIELDS = {"rho": 0, "rhotheta": 1, "rhou": 2, "rhov": 3, "rhow": 4,
           "base_rho": 5, "base_p": 6, "base_theta": 7, "rhophi": 8}
 ERF_F64, ERF_F32 = 0, 1
+ERF_OPT_TMA_STENCILS = 1
 
 # symbols the library must export (checked by the CPU tests)
 EXPORTS = ["erf_workspace_bytes", "erf_init_grid", "erf_set_initial", "erf_set_state", "erf_rk3_step",
            "erf_get_state", "erf_diagnostics", "erf_profile_steps", "erf_last_error", "erf_destroy",
            "erf_reduce_state_noalloc", "erf_train_scratch_bytes", "erf_train_closure", "erf_closure_grad",
            "erf_column_stats", "erf_standardise", "erf_set_closure_weights", "erf_closure_features",
-           "erf_closure_fields", "erf_filter_state", "erf_set_tracer_initial"]
+           "erf_closure_fields", "erf_filter_state", "erf_set_tracer_initial", "erf_set_option",
+           "erf_get_option"]
 
 
 class ErfError(RuntimeError):
@@ -86,6 +88,8 @@ def load_library(path: str = LIB_PATH):
     L.erf_init_grid.argtypes = [C.POINTER(GridDesc), C.POINTER(Config), vp, C.c_size_t, vp, C.POINTER(vp)]
     L.erf_set_initial.argtypes = [vp, vp, vp, vp, vp, C.c_int32]
     L.erf_set_tracer_initial.argtypes = [vp, vp, C.c_int32]
+    L.erf_set_option.argtypes = [vp, C.c_int32, C.c_int64]
+    L.erf_get_option.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64)]
     L.erf_set_state.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_int32]
     L.erf_rk3_step.argtypes = [vp, C.c_int32]
     L.erf_get_state.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_int32]
@@ -107,7 +111,8 @@ def load_library(path: str = LIB_PATH):
     for name in ("erf_workspace_bytes", "erf_init_grid", "erf_set_initial", "erf_set_state", "erf_rk3_step",
                  "erf_get_state", "erf_diagnostics", "erf_profile_steps", "erf_train_closure", "erf_closure_grad",
                  "erf_column_stats", "erf_standardise", "erf_set_closure_weights", "erf_closure_features",
-                 "erf_closure_fields", "erf_filter_state", "erf_set_tracer_initial"):
+                 "erf_closure_fields", "erf_filter_state", "erf_set_tracer_initial", "erf_set_option",
+                 "erf_get_option"):
         getattr(L, name).restype = C.c_int
     _LIB = L
     return L
@@ -226,6 +231,14 @@ class Dycore:
     def erf_set_initial_device(self, dtheta=None, u=None, v=None, w=None):
         ptrs = [None if t is None else t.data_ptr() for t in (dtheta, u, v, w)]
         _check(self.L, self.h, self.L.erf_set_initial(self.h, *ptrs, 1))
+
+    def erf_set_option(self, option, value):
+        _check(self.L, self.h, self.L.erf_set_option(self.h, int(option), int(value)))
+
+    def erf_get_option(self, option):
+        v = C.c_int64()
+        _check(self.L, self.h, self.L.erf_get_option(self.h, int(option), C.byref(v)))
+        return v.value
 
     def erf_set_tracer_initial(self, phi):
         a = _f64(phi)
