@@ -249,6 +249,12 @@ typedef enum { ERF_OPT_TMA_STENCILS = 1 } erf_option;
 erf_status erf_set_option(erf_handle *h, int32_t option, int64_t value);
 erf_status erf_get_option(erf_handle *h, int32_t option, int64_t *value);
 
+/* Self-test of the bounded device-side waits (no counterpart in the paper): launches one block
+ * that arms an mbarrier with a byte count no copy delivers and polls it at most max_polls times.
+ * *timed_out = 1 when the wait gave up and reported it (the expected outcome).  d_flag is one
+ * device word owned by the caller; the context stays usable.  Synchronises cuda_stream. */
+erf_status erf_selftest_wait_timeout(int32_t max_polls, unsigned *d_flag, void *cuda_stream, int32_t *timed_out);
+
 /* Message of the last failed call on h (or of the last failed erf_init_grid if h is NULL). */
 const char *erf_last_error(const erf_handle *h);
 

@@ -745,6 +745,22 @@ extern "C" erf_status erf_set_option(erf_handle *h, int32_t option, int64_t valu
     if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
     return ERF_OK;
 }
+extern "C" erf_status erf_selftest_wait_timeout(int32_t max_polls, unsigned *d_flag, void *cuda_stream,
+                                                int32_t *timed_out) {
+    if (!d_flag || !timed_out || max_polls < 1) return fail(nullptr, ERF_EINVAL, "bad self-test arguments");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaMemsetAsync(d_flag, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) {
+        selftest_wait_timeout(max_polls, d_flag, s);
+        e = cudaGetLastError();
+    }
+    unsigned f = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&f, d_flag, sizeof(f), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "wait self-test");
+    *timed_out = f ? 1 : 0;
+    return ERF_OK;
+}
 extern "C" erf_status erf_get_option(erf_handle *h, int32_t option, int64_t *value) {
     if (!h || !value) return fail(h, ERF_EINVAL, "NULL argument");
     if (option != ERF_OPT_TMA_STENCILS) return fail(h, ERF_EINVAL, "unknown option");

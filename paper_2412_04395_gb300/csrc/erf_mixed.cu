@@ -850,6 +850,7 @@ __global__ void k_mx_sub_expl(Geo g, MxBase mb, Phys ph, const float *thp, const
 // stage LU factors and back substitution, in FP64 (d' in the FP64 scratch dbuf); W'' = Omega''.
 // Only the two recurrences are serial; every load is independent of them, so the unrolled loop
 // keeps several levels of loads in flight.
+template <int UNROLL>
 __global__ void __launch_bounds__(128) k_mx_sub_col(int nz, long long nxy, const double *__restrict__ ta,
                                                     const double *__restrict__ tcp, const double *__restrict__ tim,
                                                     const float *__restrict__ tP, const float *__restrict__ tQ,
@@ -861,7 +862,7 @@ __global__ void __launch_bounds__(128) k_mx_sub_col(int nz, long long nxy, const
     if (n >= nxy) return;
     double dpm = 0.0;
     float X0m = X0[n], Y0m = Y0[n];
-#pragma unroll 4
+#pragma unroll UNROLL
     for (int k = 1; k < nz; ++k) {
         long long c = n + k * nxy;
         float X0c = X0[c], Y0c = Y0[c];
@@ -875,7 +876,7 @@ __global__ void __launch_bounds__(128) k_mx_sub_col(int nz, long long nxy, const
     W[top] = 0.f;
     Om[top] = 0.f;
     double om_up = 0.0;
-#pragma unroll 4
+#pragma unroll UNROLL
     for (int k = nz - 1; k >= 1; --k) {
         long long c = n + k * nxy;
         double om = dbuf[c] - tcp[c] * om_up;
@@ -1074,8 +1075,14 @@ void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, TriM tr, const f
         k_mx_sub_expl<<<grd, blk, 0, s>>>(g, mb, ph, thp, R.r, R.t, x, Om, Tt, X0, Y0, dtf);
     });
     mx_launch("mx_sub_col", s, [&] {
-        k_mx_sub_col<<<nb(g.nxy, 128), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q, X0, Y0, R.w, x.w, Om,
-                                                    dbuf, dtf, Gg);
+        // deeper unrolling keeps more loads in flight once there are enough columns to fill the
+        // GPU (measured: 12% faster at 1024^2 columns, 30% slower at 256^2)
+        if (g.nxy >= (1LL << 20))
+            k_mx_sub_col<8><<<nb(g.nxy, 128), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q, X0, Y0, R.w, x.w,
+                                                           Om, dbuf, dtf, Gg);
+        else
+            k_mx_sub_col<4><<<nb(g.nxy, 128), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q, X0, Y0, R.w, x.w,
+                                                           Om, dbuf, dtf, Gg);
     });
     mx_launch("mx_sub_fin", s, [&] { k_mx_sub_fin<<<grd, blk, 0, s>>>(g, mb, ph, thp, Om, x, Tt, dtf); });
 }
@@ -1087,4 +1094,20 @@ void mx_diag(const Geo &g, const MxBase &mb, CF5f st, double dt, double *part, d
     launch_diag_final(part, MX_DIAG_BLOCKS, dt, out, s);
 }
 
+}  // namespace erfk
+
+namespace erfk {
+// Self-test of the bounded mbarrier wait: the barrier is armed with a byte count that no copy
+// delivers, so the wait must give up after max_polls polls and report it; nothing is in flight.
+__global__ void k_selftest_wait_timeout(int max_polls, unsigned *flag) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, 16u);
+    bool ok = mbar_wait_bounded(&bar, 0, max_polls);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(flag, 1u);
+}
+void selftest_wait_timeout(int max_polls, unsigned *flag, cudaStream_t s) {
+    k_selftest_wait_timeout<<<1, 32, 0, s>>>(max_polls, flag);
+}
 }  // namespace erfk

@@ -97,6 +97,7 @@ struct MxTma {
     unsigned *err;
 };
 bool mx_encode_cell_tile_map(CUtensorMap *map, const float *base, const Geo &g, int nlev);
+void selftest_wait_timeout(int max_polls, unsigned *flag, cudaStream_t s);
 void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const float *pp, const float *thp,
                  float *ux, float *vy, float *wz, float *mfx, float *mfy, float *mu, float *flux, F5f R, cudaStream_t s,
                  const ClIn *cl, const MxTma *tma);

@@ -41,3 +41,16 @@ def test_tma_not_used_where_the_grid_does_not_allow_it():
     wl = W.convective_abl(nx=30, ny=28, nz=40, dx=40.0)   # nx % 4 != 0
     d = Dycore(wl)
     assert d.erf_get_option(ERF_OPT_TMA_STENCILS) == 0
+
+
+def test_bounded_wait_gives_up_and_reports():
+    """An mbarrier armed for bytes that never arrive: the kernel's wait gives up after its poll
+    limit, sets the error word and returns; the context stays usable for a normal step."""
+    from paper_2412_04395_gb300 import erf
+    from paper_2412_04395_gb300.erf import Dycore
+    assert erf.erf_selftest_wait_timeout(1000) == 1
+    wl = W.convective_abl(nx=64, ny=16, nz=16, dx=40.0)
+    d = Dycore(wl)
+    d.erf_set_initial(wl.dtheta, wl.u, wl.v, wl.w)
+    d.erf_rk3_step(1)
+    assert d.erf_diagnostics()["status"] == 0
