@@ -130,6 +130,24 @@ def density_current(nx=256, ny=4, nz=64, steps=100, dx=100.0, dt=0.25) -> Worklo
                     notes="2D-slab cold-bubble density current, FP64, Smagorinsky")
 
 
+def straka_density_current(nx=512, ny=4, nz=64, dx=100.0, dt=1.0, steps=900) -> Workload:
+    """The literature form of the density current (Sec. 4.1.1): the -15 K cos^2 decrement is on
+    temperature, so theta' = dT / pi0(z) with the Exner function of the neutral hydrostatic base
+    state, pi0 = 1 - g z / (c_p theta0); constant nu = alpha_theta = 75 m^2/s, no turbulence model;
+    dt 1 s at 100 m.  The periodic domain of 51.2 km with the bubble at its centre is the paper's
+    half domain with the symmetry plane, mirrored (the fronts stay clear of the periodic images
+    for 900 s)."""
+    zeta = uniform_zeta(nz, dx)
+    X, Y, Z = cell_coords(nx, ny, zeta, dx, dx)
+    xc = 0.5 * nx * dx
+    L = np.sqrt(((X - xc) / 4000.0) ** 2 + ((Z - 3000.0) / 2000.0) ** 2)
+    dT = np.where(L < 1.0, -15.0 * 0.5 * (np.cos(np.pi * L) + 1.0), 0.0)
+    pi0 = 1.0 - 9.81 * Z / (1004.5 * 300.0)
+    return Workload("straka_density_current", nx, ny, nz, dx, dx, zeta, dt=dt, n_substeps=6,
+                    closure=CLOSURE_CONST_NU, nu=75.0, Pr_t=1.0, steps=steps, dtheta=dT / pi0,
+                    notes="Straka (1993) density current, constant nu = alpha = 75 m^2/s, FP64")
+
+
 def gaussian_hill(nx, ny, dx, dy, h0=400.0, a=1000.0):
     """Nodal terrain h = h0 exp(-r^2/a^2) centred in the domain; nodes at (i dx, j dy)."""
     x = np.arange(nx) * dx
