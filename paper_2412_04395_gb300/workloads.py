@@ -148,6 +148,19 @@ def straka_density_current(nx=512, ny=4, nz=64, dx=100.0, dt=1.0, steps=900) -> 
                     notes="Straka (1993) density current, constant nu = alpha = 75 m^2/s, FP64")
 
 
+def dry_bubble(nx=200, ny=4, nz=100, dx=100.0, dt=0.5, steps=2000) -> Workload:
+    """Dry rising bubble (Sec. 4.1.2, after Bryan & Fritsch 2002): theta0 = 300 K, surface
+    pressure 1e5 Pa, +2 cos^2(pi r / 2) K for r < 1 with radius 2 km centred at z = 2 km in a
+    20 km x 10 km domain (here periodic in x, the bubble at the centre), inviscid, dx = dz = 100 m,
+    dt 0.5 s, 1000 s."""
+    zeta = uniform_zeta(nz, dx)
+    X, Y, Z = cell_coords(nx, ny, zeta, dx, dx)
+    r = np.sqrt(((X - 0.5 * nx * dx) / 2000.0) ** 2 + ((Z - 2000.0) / 2000.0) ** 2)
+    dth = np.where(r < 1.0, 2.0 * np.cos(0.5 * np.pi * r) ** 2, 0.0)
+    return Workload("dry_bubble", nx, ny, nz, dx, dx, zeta, dt=dt, n_substeps=6, closure=CLOSURE_NONE,
+                    steps=steps, dtheta=dth, notes="dry rising bubble, inviscid, FP64")
+
+
 def gaussian_hill(nx, ny, dx, dy, h0=400.0, a=1000.0):
     """Nodal terrain h = h0 exp(-r^2/a^2) centred in the domain; nodes at (i dx, j dy)."""
     x = np.arange(nx) * dx

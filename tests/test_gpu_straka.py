@@ -48,3 +48,21 @@ def test_straka_density_current_against_the_literature():
     assert 289.6 < tmin < 291.4          # 290.5 K +- 0.3%
     assert 14.6 < front < 16.2           # 15.4 km +- 5%
     assert 34.5 < umax < 42.1            # 38.3 m/s +- 10%
+
+
+def test_dry_bubble_rise_height():
+    """Dry rising bubble (Sec. 4.1.2; Bryan & Fritsch 2002): inviscid, 100 m, 1000 s; the paper
+    reports a final rise height of 8 km.  Rise height here: the highest cell centre where theta'
+    exceeds 0.1 K; bound 8 km +- 8%."""
+    from paper_2412_04395_gb300.erf import Dycore
+    wl = W.dry_bubble()
+    d = Dycore(wl)
+    d.erf_set_initial(wl.dtheta, wl.u, wl.v, wl.w)
+    d.erf_rk3_step(wl.steps)
+    st = d.state()
+    thp = st["rhotheta"] / st["rho"] - 300.0
+    zc = 0.5 * (wl.zeta[:-1] + wl.zeta[1:])
+    top = float(np.max(zc[np.any(thp > 0.1, axis=(1, 2))])) / 1000.0
+    print(f"dry bubble 1000 s: rise height {top:.2f} km, max theta' {float(np.max(thp)):.2f} K")
+    assert d.erf_diagnostics()["status"] == 0
+    assert 7.36 < top < 8.64
