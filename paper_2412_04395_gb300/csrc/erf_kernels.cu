@@ -18,6 +18,16 @@
 namespace erfk {
 
 __device__ __forceinline__ double sgnd(double x) { return sgnT<double>(x); }
+// 1/x in FP64 by the Newton-Raphson iteration for the reciprocal, r <- r + r (1 - x r), from an
+// FP32 estimate (two steps: 6e-8 -> 4e-15 -> rounding level); about 7 FP64-pipe operations against
+// about 10 for a division.  Values outside the FP32 range take the division.
+__device__ __forceinline__ double rcp_d(double x) {
+    const float xf = (float)x;
+    if (!(fabsf(xf) > 1.0e-30f && fabsf(xf) < 1.0e30f)) return 1.0 / x;
+    double r = (double)(1.0f / xf);
+    r = fma(r, fma(-x, r, 1.0), r);
+    return fma(r, fma(-x, r, 1.0), r);
+}
 
 // Exner function and pressure from rho*theta (Sec. 2.1 EOS, dry):
 // pi = (R_d rho theta / P00)^(R_d/c_v), p = R_d rho theta pi.  The product is rounded on its
@@ -187,7 +197,7 @@ __global__ void k_stage_begin(Geo g, CF5 sn, CF5 st, F5 x, double *pp, double *p
         long long b = bix(g, i, j, k);
         pp[n] = p - g.p0[b];
         pi[n] = pie;
-        th[n] = rt / rho;
+        th[n] = rt * rcp_d(rho);
         x.r[n] = sn.r[n] - rho;
         double xt = sn.t[n] - rt;
         x.t[n] = xt;
@@ -224,14 +234,14 @@ __global__ void k_prep(Geo g, CF5 st, double *ux, double *vy, double *wz, double
     if (k < g.nz) {
         double r = st.r[n];
         double ru = st.u[n], rv = st.v[n];
-        ux[n] = ru / (0.5 * (cval(g, st.r, i - 1, j, k) + r));
-        vy[n] = rv / (0.5 * (cval(g, st.r, i, j - 1, k) + r));
+        ux[n] = ru * rcp_d(0.5 * (cval(g, st.r, i - 1, j, k) + r));
+        vy[n] = rv * rcp_d(0.5 * (cval(g, st.r, i, j - 1, k) + r));
         mfx[n] = Hx(g, i, j, k) * ru;
         mfy[n] = Hy(g, i, j, k) * rv;
     }
     double rb = 0.5 * (cval(g, st.r, i, j, k - 1) + cval(g, st.r, i, j, k));
     double rw = st.w[n];
-    wz[n] = rw / rb;
+    wz[n] = rw * rcp_d(rb);
     if (k == 0 || k == g.nz) rom[n] = 0.0;
     else rom[n] = g.terrain ? rw - metric_shift(g, st.u, st.v, i, j, k) : rw;
 }
@@ -634,7 +644,7 @@ __global__ void k_tri_build(Geo g, Phys ph, const double *rho, const double *rt,
     double E = dtau * b2 * b2, Gg = dtau * 0.5 * ph.g;
     double gRd = GAMMA * RD;
     double cp_prev = 0.0;
-    double rrt_m = 1.0 / rt[cix(g, i, j, 0)], rHm = rHc(g, i, j, 0);
+    double rrt_m = rcp_d(rt[cix(g, i, j, 0)]), rHm = rHc(g, i, j, 0);
     // H theta^t at the x- and y-faces of the column (stage-fixed factors of the Theta'' flux)
     auto face_theta = [&](int k) {
         long long c = cix(g, i, j, k);
@@ -648,9 +658,9 @@ __global__ void k_tri_build(Geo g, Phys ph, const double *rho, const double *rt,
         long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1), w = c;
         double rdz = rdzcw(g, i, j, k);
         double pic = pi[c], pim = pi[cm];
-        double pib = 0.5 * (pim + pic), rpib = 1.0 / pib;
+        double pib = 0.5 * (pim + pic), rpib = rcp_d(pib);
         double rhob = 0.5 * (rho[cm] + rho[c]);
-        double rrt_c = 1.0 / rt[c], rHk = rHc(g, i, j, k);
+        double rrt_c = rcp_d(rt[c]), rHk = rHc(g, i, j, k);
         double Cpg = gRd * pib * rdz;
         double gb = ph.g * rhob * (RD / CVD) * 0.5 * rpib;
         double Cbp = gb * pic * rrt_c;
@@ -663,7 +673,7 @@ __global__ void k_tri_build(Geo g, Phys ph, const double *rho, const double *rt,
         double b = 1.0 - P * E * thw_k * rHk + Q * E * thw_k * rHm + Gg * E * (rHk - rHm);
         double cc = E * (P * thw_p - Gg) * rHk;
         double m = b - a * cp_prev;
-        double im = 1.0 / m;
+        double im = rcp_d(m);
         double cpk = cc * im;
         tr.a[w] = a; tr.cp[w] = cpk; tr.im[w] = im; tr.P[w] = P; tr.Q[w] = Q;
         cp_prev = cpk;
@@ -815,7 +825,7 @@ __global__ void k_sub_fin(Geo g, Phys ph, const double *th, const double *Om, co
 __global__ void k_tracer_phi(Geo g, const double *rphi, const double *rho, double *phi) {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= g.nc) return;
-    phi[c] = rphi[c] / rho[c];
+    phi[c] = rphi[c] * rcp_d(rho[c]);
 }
 __global__ void k_tracer_flux(Geo g, Phys ph, const double *ru, const double *rv, const double *rom,
                               const double *phi, const double *msx, const double *msy, const double *msz,
