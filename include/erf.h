@@ -75,8 +75,8 @@ typedef struct {
 
 #define ERF_NZ_MAX 512
 
-/* Run configuration.  Physical readings where the paper is silent are documented in the design doc
- * of the source tree; defaults are those of the paper where it gives them. */
+/* Run configuration.  Where the paper is silent, the library takes the readings stated with each
+ * field and entry point below; defaults are those of the paper where it gives them. */
 typedef struct {
     double dt;                      /* RK3 step [s] */
     int32_t n_substeps;             /* acoustic substeps per dt (even); stage 1 uses 1 of dt/3 (Sec. 3.3) */
