@@ -150,7 +150,7 @@ erf_status erf_get_state(erf_handle *h, int32_t field, void *dst, int32_t dst_is
 /* Synchronises the stream and fills *out. Returns ERF_ENONFINITE if the state is not finite. */
 erf_status erf_diagnostics(erf_handle *h, erf_diag *out);
 
-/* ---- Learned subgrid closure (spec extension; the paper names surrogate models as
+/* ---- Learned subgrid closure (an extension of the method; the paper names surrogate models as
  * future work, Sec. 6).  Network 12 -> 64 -> 64 -> 64 -> 9 with SiLU, inputs = resolved velocity
  * gradients (9), dtheta/dx, dtheta/dy, N^2 at cell centres; outputs = kinematic SGS stress
  * (t11, t22, t33, t12, t13, t23) and heat flux (h1, h2, h3), both standardised.
