@@ -8,10 +8,10 @@ resident in HBM; the working set (~2.7 GB) is far larger than L2, so no flush is
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 (under torchrun): independent replicas, one per GPU (the path is not sharded in this build),
+N > 1 (under torchrun): independent replicas, one per GPU (the dycore runs one domain per GPU),
 value = total cell-updates over all ranks / max-over-ranks time.
 --impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the same
-workload (it is the only reference this build has).
+workload (the method's reference implementation here is that oracle).
 """
 from __future__ import annotations
 

@@ -1,4 +1,4 @@
-"""The N > 1 path of bench.py runs independent replicas (the dycore is not sharded in this build).
+"""The N > 1 path of bench.py runs independent replicas (one whole domain per GPU, no sharding).
 Two gloo ranks on the CPU exercise its coordination: the torchrun environment, the barrier, the
 max-over-ranks time and the whole-job throughput (all ranks' cell-updates / slowest rank's time)."""
 import os
