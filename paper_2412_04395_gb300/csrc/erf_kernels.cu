@@ -273,8 +273,10 @@ __device__ __forceinline__ void diag_strain(const Geo &g, const Vel &v, int i, i
     s33 = (__ldg(v.wz + cixw(g, i, j, k + 1)) - __ldg(v.wz + cixw(g, i, j, k))) * g.rdzeta[k];
 }
 
-// mu = rho (Cs Delta)^2 sqrt(2 S_ij S_ij) (Smagorinsky-Lilly) or rho nu (constant)
-__global__ void k_sgs_mu(Geo g, Phys ph, Vel v, const double *rho, double *mu) {
+// mu = rho (Cs Delta)^2 sqrt(2 S_ij S_ij) (Smagorinsky-Lilly) or rho nu (constant); the
+// off-diagonal strains come from the edge arrays of k_sgs_edges (4-point averages to the centre)
+__global__ void k_sgs_mu(Geo g, Phys ph, Vel v, const double *rho, const double *e12, const double *e13,
+                         const double *e23, double *mu) {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= g.nc) return;
     int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
@@ -282,9 +284,11 @@ __global__ void k_sgs_mu(Geo g, Phys ph, Vel v, const double *rho, double *mu) {
     if (ph.closure == 2) {
         double s11, s22, s33;
         diag_strain(g, v, i, j, k, s11, s22, s33);
-        double s12 = 0.25 * (S12e(g, v, i, j, k) + S12e(g, v, i + 1, j, k) + S12e(g, v, i, j + 1, k) + S12e(g, v, i + 1, j + 1, k));
-        double s13 = 0.25 * (S13e(g, v, i, j, k) + S13e(g, v, i + 1, j, k) + S13e(g, v, i, j, k + 1) + S13e(g, v, i + 1, j, k + 1));
-        double s23 = 0.25 * (S23e(g, v, i, j, k) + S23e(g, v, i, j + 1, k) + S23e(g, v, i, j, k + 1) + S23e(g, v, i, j + 1, k + 1));
+        double s12 = 0.25 * (cval(g, e12, i, j, k) + cval(g, e12, i + 1, j, k) + cval(g, e12, i, j + 1, k) + cval(g, e12, i + 1, j + 1, k));
+        double s13 = 0.25 * (__ldg(e13 + cixw(g, i, j, k)) + __ldg(e13 + cixw(g, i + 1, j, k)) + __ldg(e13 + cixw(g, i, j, k + 1))
+                           + __ldg(e13 + cixw(g, i + 1, j, k + 1)));
+        double s23 = 0.25 * (__ldg(e23 + cixw(g, i, j, k)) + __ldg(e23 + cixw(g, i, j + 1, k)) + __ldg(e23 + cixw(g, i, j, k + 1))
+                           + __ldg(e23 + cixw(g, i, j + 1, k + 1)));
         double SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.0 * (s12 * s12 + s13 * s13 + s23 * s23);
         m = rho[c] * g.delta2[k] * sqrt(2.0 * SS);
     } else if (ph.closure == 1) {
@@ -378,6 +382,70 @@ __device__ __forceinline__ double heat_z(const Geo &g, const Phys &ph, const dou
     if (k >= g.nz || !visc) return 0.0;
     return 0.5 * (cval(g, mu, i, j, k - 1) + cval(g, mu, i, j, k)) * ph.rPr_t
          * (cval(g, th, i, j, k) - cval(g, th, i, j, k - 1)) * g.rdzc[k];
+}
+
+// The subgrid stress divergence, each strain and stress evaluated once: edge strains (k_sgs_edges),
+// the eddy viscosity (k_sgs_mu), the edge stresses in place with MOST at the bottom (k_sgs_tau),
+// then one kernel differences them into R_U, R_V, R_W and adds the heat-flux divergence to
+// R_Theta.  Edge arrays: xy-edges [nz] levels, xz- and yz-edges [nz+1] w-levels.
+#define SGS_CELL3D_W()                                              \
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;            \
+    if (i >= g.nx) return;                                          \
+    const int j = blockIdx.y, k = blockIdx.z;                       \
+    const long long n = ((long long)k * g.ny + j) * g.nx + i;
+__global__ void k_sgs_edges(Geo g, Vel v, double *e12, double *e13, double *e23) {
+    SGS_CELL3D_W();
+    if (k < g.nz) e12[n] = S12e(g, v, i, j, k);
+    e13[n] = S13e(g, v, i, j, k);
+    e23[n] = S23e(g, v, i, j, k);
+}
+__global__ void k_sgs_tau(Geo g, Phys ph, Vel v, const double *mu, const double *rho, const double *th, int visc,
+                          double *t12, double *t13, double *t23) {
+    SGS_CELL3D_W();
+    if (k < g.nz) {
+        double me = 0.25 * (cval(g, mu, i - 1, j - 1, k) + cval(g, mu, i, j - 1, k) + cval(g, mu, i - 1, j, k) + cval(g, mu, i, j, k));
+        t12[n] = visc ? -2.0 * me * t12[n] : 0.0;
+    }
+    if (k == 0) {
+        t13[n] = tau13(g, ph, v, mu, rho, th, i, j, 0, visc);
+        t23[n] = tau23(g, ph, v, mu, rho, th, i, j, 0, visc);
+    } else if (k >= g.nz || !visc) {
+        t13[n] = 0.0;
+        t23[n] = 0.0;
+    } else {
+        double mx = 0.25 * (cval(g, mu, i - 1, j, k - 1) + cval(g, mu, i, j, k - 1) + cval(g, mu, i - 1, j, k) + cval(g, mu, i, j, k));
+        double my = 0.25 * (cval(g, mu, i, j - 1, k - 1) + cval(g, mu, i, j, k - 1) + cval(g, mu, i, j - 1, k) + cval(g, mu, i, j, k));
+        t13[n] = -2.0 * mx * t13[n];
+        t23[n] = -2.0 * my * t23[n];
+    }
+}
+__global__ void k_sgs_div(Geo g, Phys ph, Vel v, const double *mu, const double *rho, const double *th, int visc,
+                          const double *t12, const double *t13, const double *t23, F5 R) {
+    SGS_CELL3D_W();
+    const long long nxy = g.nxy;
+    if (k < g.nz) {
+        double du = 0.0, dv = 0.0, hd = 0.0;
+        if (visc) {
+            du = (tau_diag(g, v, mu, i, j, k, 0) - tau_diag(g, v, mu, i - 1, j, k, 0)) * g.rdx
+               + (__ldg(t12 + cixw(g, i, j + 1, k)) - __ldg(t12 + n)) * g.rdy;
+            dv = (__ldg(t12 + cixw(g, i + 1, j, k)) - __ldg(t12 + n)) * g.rdx
+               + (tau_diag(g, v, mu, i, j, k, 1) - tau_diag(g, v, mu, i, j - 1, k, 1)) * g.rdy;
+            hd = (heat_x(g, ph, mu, th, i + 1, j, k) - heat_x(g, ph, mu, th, i, j, k)) * g.rdx
+               + (heat_y(g, ph, mu, th, i, j + 1, k) - heat_y(g, ph, mu, th, i, j, k)) * g.rdy;
+        }
+        du += (__ldg(t13 + n + nxy) - __ldg(t13 + n)) * g.rdzeta[k];
+        dv += (__ldg(t23 + n + nxy) - __ldg(t23 + n)) * g.rdzeta[k];
+        hd += (heat_z(g, ph, mu, th, rho, i, j, k + 1, visc) - heat_z(g, ph, mu, th, rho, i, j, k, visc)) * rHc(g, i, j, k);
+        R.u[n] -= du;
+        R.v[n] -= dv;
+        R.t[n] += hd;
+    }
+    if (visc && k >= 1 && k < g.nz) {
+        double dw = (__ldg(t13 + cixw(g, i + 1, j, k)) - __ldg(t13 + n)) * g.rdx
+                  + (__ldg(t23 + cixw(g, i, j + 1, k)) - __ldg(t23 + n)) * g.rdy
+                  + (tau_diag(g, v, mu, i, j, k, 2) - tau_diag(g, v, mu, i, j, k - 1, 2)) * rdzcw(g, i, j, k);
+        R.w[n] -= dw;
+    }
 }
 
 // ------------------------------------------------------------------ slow tendencies
@@ -1020,21 +1088,32 @@ void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, const double *pp, con
                      double *ux, double *vy, double *wz, double *mfx, double *mfy, double *rom, double *mu,
                      double *flux, F5 R, cudaStream_t s) {
     LAUNCH("prep", s, k_prep<<<nblk(g.nw, BS), BS, 0, s>>>(g, st, ux, vy, wz, mfx, mfy, rom));
-    int sgs = (ph.closure == 1 || ph.closure == 2 || ph.surface == 1) ? 1 : 0;
-    if (ph.closure == 1 || ph.closure == 2)
-        LAUNCH("sgs_mu", s, k_sgs_mu<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, Vel{ux, vy, wz}, st.r, mu));
+    const int visc = (ph.closure == 1 || ph.closure == 2) ? 1 : 0;
+    const int sgs = (visc || ph.surface == 1) ? 1 : 0;
+    // advection, pressure gradient, buoyancy and Coriolis (the subgrid terms follow below)
     double *fx = flux, *fy = flux + g.nc, *fz = flux + 2 * g.nc;
     LAUNCH("flux_theta", s, k_flux_theta<<<nblk(g.nw, BS), BS, 0, s>>>(g, ph, pr, th, fx, fy, fz));
-    LAUNCH("rhs_cells", s, k_rhs_cells<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, fx, fy, fz, th, st.r, mu, sgs, R.r, R.t));
+    LAUNCH("rhs_cells", s, k_rhs_cells<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, fx, fy, fz, th, st.r, mu, 0, R.r, R.t));
     // momentum: fluxes of each component into the shared buffer, then its divergence
     const dim3 g3w((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)(g.nz + 1));
     double *ax = flux, *ay = flux + g.nw, *az = flux + 2 * g.nw;
     LAUNCH("flux_u", s, k_flux_u<<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
-    LAUNCH("rhs_u", s, k_rhs_u<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, sgs, ax, ay, az, R.u));
+    LAUNCH("rhs_u", s, k_rhs_u<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, 0, ax, ay, az, R.u));
     LAUNCH("flux_v", s, k_flux_v<<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
-    LAUNCH("rhs_v", s, k_rhs_v<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, sgs, ax, ay, az, R.v));
+    LAUNCH("rhs_v", s, k_rhs_v<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, 0, ax, ay, az, R.v));
     LAUNCH("flux_w", s, k_flux_w<<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
-    LAUNCH("rhs_w", s, k_rhs_w<<<nblk(g.nw, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, sgs, ax, ay, az, R.w));
+    LAUNCH("rhs_w", s, k_rhs_w<<<nblk(g.nw, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, 0, ax, ay, az, R.w));
+    if (sgs) {
+        // subgrid stresses and heat fluxes, each edge and face once (the flux buffer is free again)
+        Vel v{ux, vy, wz};
+        double *e12 = flux, *e13 = flux + g.nw, *e23 = flux + 2 * g.nw;
+        if (visc) {
+            LAUNCH("sgs_edges", s, k_sgs_edges<<<g3w, 128, 0, s>>>(g, v, e12, e13, e23));
+            LAUNCH("sgs_mu", s, k_sgs_mu<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, v, st.r, e12, e13, e23, mu));
+        }
+        LAUNCH("sgs_tau", s, k_sgs_tau<<<g3w, 128, 0, s>>>(g, ph, v, mu, st.r, th, visc, e12, e13, e23));
+        LAUNCH("sgs_div", s, k_sgs_div<<<g3w, 128, 0, s>>>(g, ph, v, mu, st.r, th, visc, e12, e13, e23, R));
+    }
 }
 void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const double *rt, const double *pi,
                       const double *th, double dtau, Tri tr, double *TX, double *TY, cudaStream_t s) {
