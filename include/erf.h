@@ -94,9 +94,10 @@ typedef struct {
     double theta_s, brunt_N, p_s;   /* base state theta0 = theta_s exp(N^2 z/g), surface pressure at z = 0 */
     int32_t n_knots;                /* > 0: theta0 from a piecewise-linear sounding instead */
     const double *knot_z, *knot_theta;   /* host, n_knots each, read during erf_init_grid only */
-    int32_t tracer;                 /* 1 = advance a passive scalar rho phi (FP64 path; Sec. 3.1: after
-                                       the substeps of each stage, with the stage-averaged momenta
-                                       that advanced rho); 0 = none */
+    int32_t tracer;                 /* 1 = advance a passive scalar rho phi (Sec. 3.1: after the
+                                       substeps of each stage, with the stage-averaged momenta that
+                                       advanced rho; FP64, or whole FP32 values on the mixed path);
+                                       0 = none */
 } erf_config;
 
 /* Diagnostics (Sec. 4.1.2: mass conserved to machine precision). */

@@ -73,6 +73,9 @@ struct erf_handle {
     bool tma_enabled = true;
     unsigned *kerr = nullptr;               // set by a kernel whose bounded wait gave up
     float *mX0 = nullptr, *mY0 = nullptr;   // beta-weighted Theta'', rho'' of the vertical substep (in mflux)
+    // passive scalar (mixed path, FP32): rho phi, its S^n copy, substep momentum sums
+    float *mtphi = nullptr, *msnphi = nullptr;
+    TrSum mms{nullptr, nullptr, nullptr};
     MxBase mb;
     // learned closure
     void *cl_w = nullptr;
@@ -134,10 +137,6 @@ static erf_status validate(const erf_grid_desc *g, const erf_config *c, std::str
         return ERF_EUNSUPPORTED;
     }
     if (c->tracer != 0 && c->tracer != 1) { msg = "tracer must be 0 or 1"; return ERF_EINVAL; }
-    if (c->tracer && c->precision != ERF_PREC_FP64) {
-        msg = "the passive scalar is built on the FP64 path";
-        return ERF_EUNSUPPORTED;
-    }
     if (terr && c->precision == ERF_PREC_MIXED32) {
         msg = "the mixed-precision path is built for flat grids only";
         return ERF_EUNSUPPORTED;
@@ -186,6 +185,10 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
         H->mX0 = H->mflux; H->mY0 = H->mflux + nw;
         H->mtri.a = cv.take<double>(nw); H->mtri.cp = cv.take<double>(nw); H->mtri.im = cv.take<double>(nw);
         H->mtri.P = cv.take<float>(nw); H->mtri.Q = cv.take<float>(nw);
+        if (c->tracer) {
+            H->mtphi = cv.take<float>(nc); H->msnphi = cv.take<float>(nc);
+            H->mms.x = cv.take<float>(nc); H->mms.y = cv.take<float>(nc); H->mms.z = cv.take<float>(nw);
+        }
         if (c->closure == 3) {
             H->cl_w = cv.take<unsigned short>(64 * 16 + 64 * 64 * 2 + 16 * 64);
             H->cl_b = cv.take<float>(64 * 3 + 16);
@@ -362,6 +365,8 @@ static void enqueue_step_mixed(erf_handle *h, cudaStream_t s) {
     cudaMemcpyAsync(h->msn.u, h->mst.u, bc, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(h->msn.v, h->mst.v, bc, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(h->msn.w, h->mst.w, bw, cudaMemcpyDeviceToDevice, s);
+    if (h->mtphi) cudaMemcpyAsync(h->msnphi, h->mtphi, bc, cudaMemcpyDeviceToDevice, s);
+    const double alpha[3] = {1.0 / 3.0, 0.5, 1.0};
     for (int stage = 0; stage < 3; ++stage) {
         mx_stage_begin(g, h->mb, cf(h->msn), cf(h->mst), h->mx, h->mpp, h->mpi, h->mthp, h->mTp, h->mOm, s);
         ClIn clin{h->cl_w, h->cl_b, h->cl_stats, h->cl_out, h->cl_nfb};
@@ -370,9 +375,19 @@ static void enqueue_step_mixed(erf_handle *h, cudaStream_t s) {
         int nsub = stage == 0 ? 1 : (stage == 1 ? c.n_substeps / 2 : c.n_substeps);
         double dtau = stage == 0 ? c.dt / 3.0 : c.dt / c.n_substeps;
         mx_tri_build(g, h->mb, ph, h->mst.r, h->mst.t, h->mpi, h->mthp, dtau, h->mtri, s);
+        if (h->mtphi) {
+            cudaMemsetAsync(h->mms.x, 0, bc, s);
+            cudaMemsetAsync(h->mms.y, 0, bc, s);
+            cudaMemsetAsync(h->mms.z, 0, bw, s);
+        }
         for (int n = 0; n < nsub; ++n)
             mx_substep(g, h->mb, ph, h->mtri, h->mpi, h->mthp, cf(h->mR), h->mx, h->mOm, h->mTp, h->mdbuf, h->mX0, h->mY0,
-                       dtau, s);
+                       h->mms, dtau, s);
+        // the passive scalar after the substeps, from the stage state S^t (the pressure and flux
+        // scratch are free until the next stage begins)
+        if (h->mtphi)
+            mx_tracer_stage(g, h->mb, ph, h->mst.r, h->mmfx, h->mmfy, h->mst.w, h->msnphi, h->mms, nsub,
+                            alpha[stage] * c.dt, h->mpp, h->mflux, h->mtphi, s);
         mx_stage_end(g, h->mst, cf(h->mx), s);
     }
 }
@@ -566,6 +581,8 @@ extern "C" erf_status erf_set_initial(erf_handle *h, const double *dtheta, const
     return ERF_OK;
 }
 
+static bool has_tracer(const erf_handle *h) { return h->tphi || h->mtphi; }
+
 static double *field_dev(erf_handle *h, int f, long long &n) {
     const Geo &g = h->geo;
     n = g.nc;
@@ -586,13 +603,34 @@ static double *field_dev(erf_handle *h, int f, long long &n) {
 extern "C" erf_status erf_set_state(erf_handle *h, int32_t field, const void *src, int32_t src_is_device,
                                     int32_t src_dtype) {
     if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
-    if ((field < ERF_RHO || field > ERF_RHOW) && !(field == ERF_RHOPHI && h->tphi))
+    if ((field < ERF_RHO || field > ERF_RHOW) && !(field == ERF_RHOPHI && has_tracer(h)))
         return fail(h, ERF_EINVAL, "field not settable");
     if (!src) return fail(h, ERF_EINVAL, "src is NULL");
     if (src_dtype != ERF_F64 && src_dtype != ERF_F32) return fail(h, ERF_EINVAL, "bad dtype");
     long long n;
     cudaStream_t s = h->user;
     cudaError_t e;
+    if (h->mixed && field == ERF_RHOPHI) {   // rho phi is held whole in FP32
+        n = h->geo.nc;
+        if (src_dtype == ERF_F32) {
+            e = cudaMemcpyAsync(h->mtphi, src, n * sizeof(float),
+                                src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+        } else {
+            const void *d = src;
+            e = cudaSuccess;
+            if (!src_is_device) {
+                e = cudaMemcpyAsync(h->mdbuf, src, n * sizeof(double), cudaMemcpyHostToDevice, s);
+                d = h->mdbuf;
+            }
+            if (e == cudaSuccess) {
+                launch_convert(d, h->mtphi, n, 0, s);
+                e = cudaGetLastError();
+            }
+        }
+        if (e == cudaSuccess && !src_is_device) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
+        return ERF_OK;
+    }
     if (h->mixed) {
         float *mf[5] = {h->mst.r, h->mst.t, h->mst.u, h->mst.v, h->mst.w};
         n = field == ERF_RHOW ? h->geo.nw : h->geo.nc;
@@ -645,18 +683,20 @@ extern "C" erf_status erf_set_state(erf_handle *h, int32_t field, const void *sr
 
 extern "C" erf_status erf_set_tracer_initial(erf_handle *h, const double *phi0, int32_t is_device) {
     if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
-    if (!h->tphi) return fail(h, ERF_EUNSUPPORTED, "handle configured without the passive scalar");
+    if (!has_tracer(h)) return fail(h, ERF_EUNSUPPORTED, "handle configured without the passive scalar");
     if (!phi0) return fail(h, ERF_EINVAL, "phi0 is NULL");
     const Geo &g = h->geo;
     cudaStream_t s = h->user;
     const double *d = phi0;
     cudaError_t e = cudaSuccess;
     if (!is_device) {
-        e = cudaMemcpyAsync(h->snphi, phi0, g.nc * sizeof(double), cudaMemcpyHostToDevice, s);
-        d = h->snphi;
+        double *stg = h->mixed ? h->mdbuf : h->snphi;   // FP64 staging of nc values
+        e = cudaMemcpyAsync(stg, phi0, g.nc * sizeof(double), cudaMemcpyHostToDevice, s);
+        d = stg;
     }
     if (e == cudaSuccess) {
-        launch_tracer_init(g, h->st.r, d, h->tphi, s);
+        if (h->mixed) mx_tracer_init(g, h->rho0, h->mst.r, d, h->mtphi, s);
+        else launch_tracer_init(g, h->st.r, d, h->tphi, s);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && !is_device) e = cudaStreamSynchronize(s);
@@ -667,13 +707,29 @@ extern "C" erf_status erf_set_tracer_initial(erf_handle *h, const double *phi0, 
 extern "C" erf_status erf_get_state(erf_handle *h, int32_t field, void *dst, int32_t dst_is_device,
                                     int32_t dst_dtype) {
     if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
-    if ((field < ERF_RHO || field > ERF_BASE_THETA) && !(field == ERF_RHOPHI && h->tphi))
+    if ((field < ERF_RHO || field > ERF_BASE_THETA) && !(field == ERF_RHOPHI && has_tracer(h)))
         return fail(h, ERF_EINVAL, "bad field");
     if (!dst) return fail(h, ERF_EINVAL, "dst is NULL");
     if (dst_dtype != ERF_F64 && dst_dtype != ERF_F32) return fail(h, ERF_EINVAL, "bad dtype");
     long long n;
     cudaStream_t s = h->user;
     cudaError_t e;
+    if (h->mixed && field == ERF_RHOPHI) {
+        n = h->geo.nc;
+        if (dst_dtype == ERF_F32) {
+            e = cudaMemcpyAsync(dst, h->mtphi, n * sizeof(float),
+                                dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+        } else {
+            double *stg = dst_is_device ? (double *)dst : h->mdbuf;
+            launch_convert(h->mtphi, stg, n, 1, s);
+            e = cudaGetLastError();
+            if (e == cudaSuccess && !dst_is_device)
+                e = cudaMemcpyAsync(dst, stg, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+        }
+        if (e == cudaSuccess && !dst_is_device) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "get_state");
+        return ERF_OK;
+    }
     if (h->mixed && field <= ERF_RHOW) {
         const float *mf[5] = {h->mst.r, h->mst.t, h->mst.u, h->mst.v, h->mst.w};
         n = field == ERF_RHOW ? h->geo.nw : h->geo.nc;

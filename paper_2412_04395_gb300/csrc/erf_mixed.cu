@@ -184,7 +184,8 @@ __device__ __forceinline__ void diagSf(const Geo &g, const MxBase &mb, const Vel
     b = (fval(g, v.vy, i, j + 1, k) - fval(g, v.vy, i, j, k)) * mb.rdy;
     c = (__ldg(v.wz + cixw(g, i, j, k + 1)) - __ldg(v.wz + cixw(g, i, j, k))) * mb.rdzf[k];
 }
-__global__ void k_mx_sgs_mu(Geo g, MxBase mb, Phys ph, VelF v, const float *dr, float *mu) {
+__global__ void k_mx_sgs_mu(Geo g, MxBase mb, Phys ph, VelF v, const float *dr, const float *e12, const float *e13,
+                            const float *e23, float *mu) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
@@ -194,9 +195,11 @@ __global__ void k_mx_sgs_mu(Geo g, MxBase mb, Phys ph, VelF v, const float *dr, 
     if (ph.closure == 2) {
         float s11, s22, s33;
         diagSf(g, mb, v, i, j, k, s11, s22, s33);
-        float s12 = 0.25f * (S12f(g, mb, v, i, j, k) + S12f(g, mb, v, i + 1, j, k) + S12f(g, mb, v, i, j + 1, k) + S12f(g, mb, v, i + 1, j + 1, k));
-        float s13 = 0.25f * (S13f(g, mb, v, i, j, k) + S13f(g, mb, v, i + 1, j, k) + S13f(g, mb, v, i, j, k + 1) + S13f(g, mb, v, i + 1, j, k + 1));
-        float s23 = 0.25f * (S23f(g, mb, v, i, j, k) + S23f(g, mb, v, i, j + 1, k) + S23f(g, mb, v, i, j, k + 1) + S23f(g, mb, v, i, j + 1, k + 1));
+        float s12 = 0.25f * (fval(g, e12, i, j, k) + fval(g, e12, i + 1, j, k) + fval(g, e12, i, j + 1, k) + fval(g, e12, i + 1, j + 1, k));
+        float s13 = 0.25f * (__ldg(e13 + cixw(g, i, j, k)) + __ldg(e13 + cixw(g, i + 1, j, k)) + __ldg(e13 + cixw(g, i, j, k + 1))
+                           + __ldg(e13 + cixw(g, i + 1, j, k + 1)));
+        float s23 = 0.25f * (__ldg(e23 + cixw(g, i, j, k)) + __ldg(e23 + cixw(g, i, j + 1, k)) + __ldg(e23 + cixw(g, i, j, k + 1))
+                           + __ldg(e23 + cixw(g, i, j + 1, k + 1)));
         float SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.f * (s12 * s12 + s13 * s13 + s23 * s23);
         m = rho * mb.delta2f[k] * sqrtf(2.f * SS);
     } else if (ph.closure == 1) {
@@ -272,6 +275,85 @@ __device__ float tau23f(const Geo &g, const MxBase &mb, const Phys &ph, const Ve
     return -2.f * me * S23f(g, mb, v, i, j, k);
 }
 
+// Subgrid stress divergence with each edge strain and stress evaluated once (as in the FP64
+// path): edge strains, eddy viscosity, edge stresses in place (MOST at the bottom), then one kernel
+// differences them into R_U, R_V, R_W and adds the heat-flux divergence to R_Theta.
+__global__ void k_mx_sgs_edges(Geo g, MxBase mb, VelF v, float *e12, float *e13, float *e23) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long n = ((long long)k * g.ny + j) * g.nx + i;
+    if (k < g.nz) e12[n] = S12f(g, mb, v, i, j, k);
+    e13[n] = S13f(g, mb, v, i, j, k);
+    e23[n] = S23f(g, mb, v, i, j, k);
+}
+__global__ void k_mx_sgs_tau(Geo g, MxBase mb, Phys ph, VelF v, const float *mu, const float *dr, const float *thp,
+                             int visc, float *t12, float *t13, float *t23) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long n = ((long long)k * g.ny + j) * g.nx + i;
+    if (k < g.nz) {
+        float me = 0.25f * (fval(g, mu, i - 1, j - 1, k) + fval(g, mu, i, j - 1, k) + fval(g, mu, i - 1, j, k) + fval(g, mu, i, j, k));
+        t12[n] = visc ? -2.f * me * t12[n] : 0.f;
+    }
+    if (k == 0) {
+        t13[n] = tau13f(g, mb, ph, v, mu, dr, thp, i, j, 0, visc);
+        t23[n] = tau23f(g, mb, ph, v, mu, dr, thp, i, j, 0, visc);
+    } else if (k >= g.nz || !visc) {
+        t13[n] = 0.f;
+        t23[n] = 0.f;
+    } else {
+        float mx = 0.25f * (fval(g, mu, i - 1, j, k - 1) + fval(g, mu, i, j, k - 1) + fval(g, mu, i - 1, j, k) + fval(g, mu, i, j, k));
+        float my = 0.25f * (fval(g, mu, i, j - 1, k - 1) + fval(g, mu, i, j, k - 1) + fval(g, mu, i, j - 1, k) + fval(g, mu, i, j, k));
+        t13[n] = -2.f * mx * t13[n];
+        t23[n] = -2.f * my * t23[n];
+    }
+}
+__global__ void k_mx_sgs_div(Geo g, MxBase mb, Phys ph, VelF v, const float *mu, const float *dr, const float *thp,
+                             int visc, const float *t12, const float *t13, const float *t23, F5f R) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long n = ((long long)k * g.ny + j) * g.nx + i;
+    const long long nxy = g.nxy;
+    const float rdx = mb.rdx, rdy = mb.rdy;
+    if (k < g.nz) {
+        const float rH = mb.rdzf[k], rPr = mb.rPr;
+        float du = 0.f, dv = 0.f, hd = 0.f;
+        if (visc) {
+            du = (tauDf(g, mb, v, mu, i, j, k, 0) - tauDf(g, mb, v, mu, i - 1, j, k, 0)) * rdx
+               + (__ldg(t12 + cixw(g, i, j + 1, k)) - __ldg(t12 + n)) * rdy;
+            dv = (__ldg(t12 + cixw(g, i + 1, j, k)) - __ldg(t12 + n)) * rdx
+               + (tauDf(g, mb, v, mu, i, j, k, 1) - tauDf(g, mb, v, mu, i, j - 1, k, 1)) * rdy;
+            float tc = thp[n], mc = mu[n];
+            float hxm = 0.5f * (fval(g, mu, i - 1, j, k) + mc) * rPr * (tc - fval(g, thp, i - 1, j, k)) * rdx;
+            float hxp = 0.5f * (mc + fval(g, mu, i + 1, j, k)) * rPr * (fval(g, thp, i + 1, j, k) - tc) * rdx;
+            float hym = 0.5f * (fval(g, mu, i, j - 1, k) + mc) * rPr * (tc - fval(g, thp, i, j - 1, k)) * rdy;
+            float hyp = 0.5f * (mc + fval(g, mu, i, j + 1, k)) * rPr * (fval(g, thp, i, j + 1, k) - tc) * rdy;
+            hd = (hxp - hxm) * rdx + (hyp - hym) * rdy;
+        }
+        du += (__ldg(t13 + n + nxy) - __ldg(t13 + n)) * rH;
+        dv += (__ldg(t23 + n + nxy) - __ldg(t23 + n)) * rH;
+        auto hz = [&](int kf) -> float {
+            if (kf == 0) return ph.surface == 1 ? -(mb.rho0f[0] + dr[cix(g, i, j, 0)]) * mb.Qs : 0.f;
+            if (kf >= g.nz || !visc) return 0.f;
+            float dth = dth0(mb, kf, kf - 1) + (fval(g, thp, i, j, kf) - fval(g, thp, i, j, kf - 1));
+            return 0.5f * (fval(g, mu, i, j, kf - 1) + fval(g, mu, i, j, kf)) * rPr * dth * mb.rdzcf[kf];
+        };
+        hd += (hz(k + 1) - hz(k)) * rH;
+        R.u[n] -= du;
+        R.v[n] -= dv;
+        R.t[n] += hd;
+    }
+    if (visc && k >= 1 && k < g.nz) {
+        float dw = (__ldg(t13 + cixw(g, i + 1, j, k)) - __ldg(t13 + n)) * rdx
+                 + (__ldg(t23 + cixw(g, i, j + 1, k)) - __ldg(t23 + n)) * rdy
+                 + (tauDf(g, mb, v, mu, i, j, k, 2) - tauDf(g, mb, v, mu, i, j, k - 1, 2)) * mb.rdzcf[k];
+        R.w[n] -= dw;
+    }
+}
+
 // learned closure: cell-centre planes of rho t_ij / rho h_j (order 11 22 33 12 13 23 h1 h2 h3),
 // interpolated to edges (4-point) and faces (2-point) like the Smagorinsky stresses
 __device__ __forceinline__ float tl(const Geo &g, const float *tau, int q, int i, int j, int k) {
@@ -285,11 +367,61 @@ __device__ __forceinline__ float tlze(const Geo &g, const float *tau, int q, int
     return 0.25f * (tl(g, tau, q, i - di, j - dj, k - 1) + tl(g, tau, q, i, j, k - 1) + tl(g, tau, q, i - di, j - dj, k) + tl(g, tau, q, i, j, k));
 }
 
+// Learned-closure stress divergence, each edge value once: the cell-centre planes of the network
+// are averaged to xy-, xz- and yz-edges (MOST stress at the bottom, zero at the top), then one
+// kernel differences them (and the heat flux at faces) into R_U, R_V, R_W and R_Theta.
+__global__ void k_mx_cl_edges(Geo g, MxBase mb, Phys ph, VelF v, const float *mu, const float *dr, const float *thp,
+                              const float *tau, float *t12, float *t13, float *t23) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long n = ((long long)k * g.ny + j) * g.nx + i;
+    if (k < g.nz) t12[n] = tl12e(g, tau, i, j, k);
+    if (k == 0) {
+        t13[n] = tau13f(g, mb, ph, v, mu, dr, thp, i, j, 0, 0);
+        t23[n] = tau23f(g, mb, ph, v, mu, dr, thp, i, j, 0, 0);
+    } else if (k >= g.nz) {
+        t13[n] = 0.f;
+        t23[n] = 0.f;
+    } else {
+        t13[n] = tlze(g, tau, 4, 1, 0, i, j, k);
+        t23[n] = tlze(g, tau, 5, 0, 1, i, j, k);
+    }
+}
+__global__ void k_mx_cl_div(Geo g, MxBase mb, Phys ph, const float *dr, const float *tau, const float *t12,
+                            const float *t13, const float *t23, F5f R) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long n = ((long long)k * g.ny + j) * g.nx + i;
+    const long long nxy = g.nxy;
+    const float rdx = mb.rdx, rdy = mb.rdy;
+    if (k < g.nz) {
+        const float rH = mb.rdzf[k];
+        float du = (tl(g, tau, 0, i, j, k) - tl(g, tau, 0, i - 1, j, k)) * rdx
+                 + (__ldg(t12 + cixw(g, i, j + 1, k)) - __ldg(t12 + n)) * rdy + (__ldg(t13 + n + nxy) - __ldg(t13 + n)) * rH;
+        float dv = (__ldg(t12 + cixw(g, i + 1, j, k)) - __ldg(t12 + n)) * rdx
+                 + (tl(g, tau, 1, i, j, k) - tl(g, tau, 1, i, j - 1, k)) * rdy + (__ldg(t23 + n + nxy) - __ldg(t23 + n)) * rH;
+        float qxm = 0.5f * (tl(g, tau, 6, i - 1, j, k) + tl(g, tau, 6, i, j, k));
+        float qxp = 0.5f * (tl(g, tau, 6, i, j, k) + tl(g, tau, 6, i + 1, j, k));
+        float qym = 0.5f * (tl(g, tau, 7, i, j - 1, k) + tl(g, tau, 7, i, j, k));
+        float qyp = 0.5f * (tl(g, tau, 7, i, j, k) + tl(g, tau, 7, i, j + 1, k));
+        float qzm = k == 0 ? (ph.surface == 1 ? (mb.rho0f[0] + dr[n]) * mb.Qs : 0.f)
+                           : 0.5f * (tl(g, tau, 8, i, j, k - 1) + tl(g, tau, 8, i, j, k));
+        float qzp = k == g.nz - 1 ? 0.f : 0.5f * (tl(g, tau, 8, i, j, k) + tl(g, tau, 8, i, j, k + 1));
+        R.u[n] -= du;
+        R.v[n] -= dv;
+        R.t[n] -= (qxp - qxm) * rdx + (qyp - qym) * rdy + (qzp - qzm) * rH;
+    }
+    if (k >= 1 && k < g.nz) {
+        float dw = (__ldg(t13 + cixw(g, i + 1, j, k)) - __ldg(t13 + n)) * rdx
+                 + (__ldg(t23 + cixw(g, i, j + 1, k)) - __ldg(t23 + n)) * rdy
+                 + (tl(g, tau, 2, i, j, k) - tl(g, tau, 2, i, j, k - 1)) * mb.rdzcf[k];
+        R.w[n] -= dw;
+    }
+}
+
 // ------------------------------------------------------------------ slow tendencies (FP32)
-struct PrepF {
-    const float *ux, *vy, *wz, *mfx, *mfy;
-    const float *tau;   // learned-closure stress planes, or null
-};
 
 // ---- advective fluxes, each face once (the divergence kernels read two values per direction)
 #define MX_CELL3D_W()                                               \
@@ -574,15 +706,15 @@ __global__ void k_mx_flux_w(Geo g, const float *wz, const float *mfx, const floa
 struct FluxF {
     const float *x, *y, *z;
 };
-__global__ void k_mx_rhs_cells(Geo g, MxBase mb, Phys ph, PrepF pr, const float *rw, const float *thp,
-                               const float *dr, const float *mu, int sgs, FluxF fth, float *Rr, float *Rt) {
+__global__ void k_mx_rhs_cells(Geo g, MxBase mb, const float *mfx, const float *mfy, const float *rw, FluxF fth,
+                               float *Rr, float *Rt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
     const long long c = ((long long)k * g.ny + j) * g.nx + i;
     float rdx = mb.rdx, rdy = mb.rdy, rH = mb.rdzf[k];
-    float mxm = pr.mfx[c], mxp = __ldg(pr.mfx + cixw(g, i + 1, j, k));
-    float mym = pr.mfy[c], myp = __ldg(pr.mfy + cixw(g, i, j + 1, k));
+    float mxm = mfx[c], mxp = __ldg(mfx + cixw(g, i + 1, j, k));
+    float mym = mfy[c], myp = __ldg(mfy + cixw(g, i, j + 1, k));
     float omm = (k == 0) ? 0.f : __ldg(rw + cix(g, i, j, k));
     float omp = (k == g.nz - 1) ? 0.f : __ldg(rw + cix(g, i, j, k + 1));
     // face mass fluxes carry the face height, so the whole divergence is divided by the cell height
@@ -594,43 +726,10 @@ __global__ void k_mx_rhs_cells(Geo g, MxBase mb, Phys ph, PrepF pr, const float 
     float fzm = k > 0 ? __ldg(fth.z + c) + omm * dth0(mb, k - 1, k) : 0.f;
     float fzp = k < g.nz - 1 ? __ldg(fth.z + c + g.nxy) : 0.f;
     float r = mb.th0f[k] * Rrho - ((fxp - fxm) * rdx + (fyp - fym) * rdy + (fzp - fzm)) * rH;
-    if (sgs) {
-        int visc = ph.closure == 1 || ph.closure == 2;
-        float hd = 0.f;
-        float rPr = mb.rPr;
-        if (visc) {
-            float tc = thp[c];
-            float hxm = 0.5f * (fval(g, mu, i - 1, j, k) + mu[c]) * rPr * (tc - fval(g, thp, i - 1, j, k)) * rdx;
-            float hxp = 0.5f * (mu[c] + fval(g, mu, i + 1, j, k)) * rPr * (fval(g, thp, i + 1, j, k) - tc) * rdx;
-            float hym = 0.5f * (fval(g, mu, i, j - 1, k) + mu[c]) * rPr * (tc - fval(g, thp, i, j - 1, k)) * rdy;
-            float hyp = 0.5f * (mu[c] + fval(g, mu, i, j + 1, k)) * rPr * (fval(g, thp, i, j + 1, k) - tc) * rdy;
-            hd += (hxp - hxm) * rdx + (hyp - hym) * rdy;
-        }
-        auto hz = [&](int kf) -> float {
-            if (kf == 0) return ph.surface == 1 ? -(mb.rho0f[0] + dr[cix(g, i, j, 0)]) * mb.Qs : 0.f;
-            if (kf >= g.nz || !visc) return 0.f;
-            float dth = dth0(mb, kf, kf - 1) + (fval(g, thp, i, j, kf) - fval(g, thp, i, j, kf - 1));
-            return 0.5f * (fval(g, mu, i, j, kf - 1) + fval(g, mu, i, j, kf)) * rPr * dth * mb.rdzcf[kf];
-        };
-        hd += (hz(k + 1) - hz(k)) * rH;
-        r += hd;
-    }
-    if (pr.tau) {   // -div q with q at faces (upward MOST flux rho Q at the surface)
-        const float *t = pr.tau;
-        float qxm = 0.5f * (tl(g, t, 6, i - 1, j, k) + tl(g, t, 6, i, j, k));
-        float qxp = 0.5f * (tl(g, t, 6, i, j, k) + tl(g, t, 6, i + 1, j, k));
-        float qym = 0.5f * (tl(g, t, 7, i, j - 1, k) + tl(g, t, 7, i, j, k));
-        float qyp = 0.5f * (tl(g, t, 7, i, j, k) + tl(g, t, 7, i, j + 1, k));
-        float qzm = k == 0 ? (ph.surface == 1 ? (mb.rho0f[0] + dr[c]) * mb.Qs : 0.f)
-                           : 0.5f * (tl(g, t, 8, i, j, k - 1) + tl(g, t, 8, i, j, k));
-        float qzp = k == g.nz - 1 ? 0.f : 0.5f * (tl(g, t, 8, i, j, k) + tl(g, t, 8, i, j, k + 1));
-        r -= (qxp - qxm) * rdx + (qyp - qym) * rdy + (qzp - qzm) * rH;
-    }
     Rt[c] = r;
 }
 
-__global__ void k_mx_rhs_u(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const float *pp, const float *thp,
-                           const float *mu, int sgs, FluxF fm, float *Ru) {
+__global__ void k_mx_rhs_u(Geo g, MxBase mb, CF5f st, const float *pp, FluxF fm, float *Ru) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
@@ -645,29 +744,10 @@ __global__ void k_mx_rhs_u(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const f
         float rhx = mb.rho0f[k] + 0.5f * (fval(g, st.r, i - 1, j, k) + st.r[c]);
         r += mb.f_cor * (rvx - rhx * mb.v_g);
     }
-    if (sgs) {
-        int visc = ph.closure == 1 || ph.closure == 2;
-        VelF v{pr.ux, pr.vy, pr.wz};
-        float d = 0.f;
-        if (visc)
-            d += (tauDf(g, mb, v, mu, i, j, k, 0) - tauDf(g, mb, v, mu, i - 1, j, k, 0)) * rdx
-               + (tau12f(g, mb, v, mu, i, j + 1, k) - tau12f(g, mb, v, mu, i, j, k)) * rdy;
-        d += (tau13f(g, mb, ph, v, mu, st.r, thp, i, j, k + 1, visc) - tau13f(g, mb, ph, v, mu, st.r, thp, i, j, k, visc)) * rH;
-        r -= d;
-    }
-    if (pr.tau) {
-        const float *t = pr.tau;
-        VelF v{pr.ux, pr.vy, pr.wz};
-        float t13b = k == 0 ? tau13f(g, mb, ph, v, mu, st.r, thp, i, j, 0, 0) : tlze(g, t, 4, 1, 0, i, j, k);
-        float t13t = k == g.nz - 1 ? 0.f : tlze(g, t, 4, 1, 0, i, j, k + 1);
-        r -= (tl(g, t, 0, i, j, k) - tl(g, t, 0, i - 1, j, k)) * rdx + (tl12e(g, t, i, j + 1, k) - tl12e(g, t, i, j, k)) * rdy
-           + (t13t - t13b) * rH;
-    }
     Ru[c] = r;
 }
 
-__global__ void k_mx_rhs_v(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const float *pp, const float *thp,
-                           const float *mu, int sgs, FluxF fm, float *Rv) {
+__global__ void k_mx_rhs_v(Geo g, MxBase mb, CF5f st, const float *pp, FluxF fm, float *Rv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
@@ -682,29 +762,10 @@ __global__ void k_mx_rhs_v(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const f
         float rhy = mb.rho0f[k] + 0.5f * (fval(g, st.r, i, j - 1, k) + st.r[c]);
         r -= mb.f_cor * (rux - rhy * mb.u_g);
     }
-    if (sgs) {
-        int visc = ph.closure == 1 || ph.closure == 2;
-        VelF v{pr.ux, pr.vy, pr.wz};
-        float d = 0.f;
-        if (visc)
-            d += (tau12f(g, mb, v, mu, i + 1, j, k) - tau12f(g, mb, v, mu, i, j, k)) * rdx
-               + (tauDf(g, mb, v, mu, i, j, k, 1) - tauDf(g, mb, v, mu, i, j - 1, k, 1)) * rdy;
-        d += (tau23f(g, mb, ph, v, mu, st.r, thp, i, j, k + 1, visc) - tau23f(g, mb, ph, v, mu, st.r, thp, i, j, k, visc)) * rH;
-        r -= d;
-    }
-    if (pr.tau) {
-        const float *t = pr.tau;
-        VelF v{pr.ux, pr.vy, pr.wz};
-        float t23b = k == 0 ? tau23f(g, mb, ph, v, mu, st.r, thp, i, j, 0, 0) : tlze(g, t, 5, 0, 1, i, j, k);
-        float t23t = k == g.nz - 1 ? 0.f : tlze(g, t, 5, 0, 1, i, j, k + 1);
-        r -= (tl12e(g, t, i + 1, j, k) - tl12e(g, t, i, j, k)) * rdx + (tl(g, t, 1, i, j, k) - tl(g, t, 1, i, j - 1, k)) * rdy
-           + (t23t - t23b) * rH;
-    }
     Rv[c] = r;
 }
 
-__global__ void k_mx_rhs_w(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const float *pp, const float *thp,
-                           const float *mu, int sgs, FluxF fm, float *Rw) {
+__global__ void k_mx_rhs_w(Geo g, MxBase mb, CF5f st, const float *pp, FluxF fm, float *Rw) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
@@ -717,19 +778,6 @@ __global__ void k_mx_rhs_w(Geo g, MxBase mb, Phys ph, PrepF pr, CF5f st, const f
     long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1);
     r -= (pp[c] - pp[cm]) * rdzc;
     r += -0.5f * mb.grav * (st.r[cm] + st.r[c]);
-    if (sgs && (ph.closure == 1 || ph.closure == 2)) {
-        VelF v{pr.ux, pr.vy, pr.wz};
-        float d = (tau13f(g, mb, ph, v, mu, st.r, thp, i + 1, j, k, 1) - tau13f(g, mb, ph, v, mu, st.r, thp, i, j, k, 1)) * rdx
-                + (tau23f(g, mb, ph, v, mu, st.r, thp, i, j + 1, k, 1) - tau23f(g, mb, ph, v, mu, st.r, thp, i, j, k, 1)) * rdy
-                + (tauDf(g, mb, v, mu, i, j, k, 2) - tauDf(g, mb, v, mu, i, j, k - 1, 2)) * rdzc;
-        r -= d;
-    }
-    if (pr.tau) {
-        const float *t = pr.tau;
-        r -= (tlze(g, t, 4, 1, 0, i + 1, j, k) - tlze(g, t, 4, 1, 0, i, j, k)) * rdx
-           + (tlze(g, t, 5, 0, 1, i, j + 1, k) - tlze(g, t, 5, 0, 1, i, j, k)) * rdy
-           + (tl(g, t, 2, i, j, k) - tl(g, t, 2, i, j, k - 1)) * rdzc;
-    }
     Rw[n] = r;
 }
 
@@ -811,7 +859,7 @@ __device__ __forceinline__ float mx_thw_rel(const MxBase &mb, const float *thp, 
 // beta-weighted X0 = b1 Theta''^tau + b2 Theta*, Y0 = b1 rho''^tau + b2 rho* that enter the
 // Omega'' rows.  Theta''^tau is kept in Tt for the divergence damping of the next substep.
 __global__ void k_mx_sub_expl(Geo g, MxBase mb, Phys ph, const float *thp, const float *Rr, const float *Rt,
-                              F5f x, const float *Om, float *Tt, float *X0o, float *Y0o, float dtf) {
+                              F5f x, const float *Om, float *Tt, float *X0o, float *Y0o, float dtf, TrSum ms) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z, nz = g.nz;
@@ -844,6 +892,11 @@ __global__ void k_mx_sub_expl(Geo g, MxBase mb, Phys ph, const float *thp, const
     x.r[c] = Rs;
     X0o[c] = b1 * xt + b2 * Ts;
     Y0o[c] = b1 * xr + b2 * Rs;
+    if (ms.x) {   // passive scalar: this substep's perturbation momenta that advance rho''
+        ms.x[c] += Uc;
+        ms.y[c] += Vc;
+        if (k >= 1) ms.z[c] += b1 * om_k;
+    }
 }
 
 // Part 2 (one thread per column): the Omega'' rows' right-hand side, forward elimination with the
@@ -892,7 +945,7 @@ __global__ void __launch_bounds__(128) k_mx_sub_col(int nz, long long nxy, const
 // Part 3 (one thread per cell): Theta'', rho'' from the new Omega'' (App. C rows 3-4, beta_2
 // part) and Theta~ of the next substep.
 __global__ void k_mx_sub_fin(Geo g, MxBase mb, Phys ph, const float *thp, const float *Om, F5f x, float *Tt,
-                             float dtf) {
+                             float dtf, float *msz) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z, nz = g.nz;
@@ -909,6 +962,7 @@ __global__ void k_mx_sub_fin(Geo g, MxBase mb, Phys ph, const float *thp, const 
     x.r[c] -= db * (omf_up - omf);
     float told = Tt[c];
     Tt[c] = xt + bd * (xt - told);
+    if (msz && k >= 1) msz[c] += b2 * omf;
 }
 
 // The same finish, four consecutive cells along x per thread with 16-byte loads and stores
@@ -918,7 +972,7 @@ __device__ __forceinline__ float4 ldw4(const float *p) { return *reinterpret_cas
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 __device__ __forceinline__ float &el(float4 &v, int e) { return (&v.x)[e]; }
 __global__ void k_mx_sub_fin4(Geo g, MxBase mb, Phys ph, const float *thp, const float *Om, F5f x, float *Tt,
-                              float dtf) {
+                              float dtf, float *msz) {
     const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z, nz = g.nz;
@@ -954,6 +1008,65 @@ __global__ void k_mx_sub_fin4(Geo g, MxBase mb, Phys ph, const float *thp, const
     st4(x.t + c, xt);
     st4(x.r + c, xr);
     st4(Tt + c, tt);
+    if (msz && k >= 1) {
+        float4 m = ldw4(msz + c);
+        #pragma unroll
+        for (int e = 0; e < 4; ++e) el(m, e) += b2 * el(om, e);
+        st4(msz + c, m);
+    }
+}
+
+// ------------------------------------------------------------------ passive scalar (Sec. 3.1), FP32
+// rho phi is carried whole in FP32 (it has no base state).  After a stage's substeps:
+// rho phi^(s) = rho phi^n + alpha_s dt R_phi(phi^t), the face fluxes taking the stage mass flux
+// plus the mean of the substeps' perturbation fluxes (the momenta that advanced rho), so that
+// phi = 1 stays 1 up to FP32 rounding.  phi^t is interpolated by WENO5 like theta, relative to the
+// upwind cell's value.
+__global__ void k_mx_tracer_phi(Geo g, MxBase mb, const float *rphi, const float *dr, float *phi) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long c = ((long long)k * g.ny + j) * g.nx + i;
+    phi[c] = rphi[c] / (mb.rho0f[k] + dr[c]);
+}
+__global__ void k_mx_tracer_flux(Geo g, MxBase mb, Phys ph, const float *mfx, const float *mfy, const float *rw,
+                                 const float *phi, TrSum ms, float rns, float *fx, float *fy, float *fz) {
+    MX_CELL3D_W();
+    const int zf = ph.scal_adv == 1;
+    float q[6];
+    if (k < g.nz) {
+        const float dz = mb.dzf[k];
+        float mf = __ldg(mfx + n) + dz * (ms.x[n] * rns), sg = sgnT<float>(mf);
+        float tu = fval(g, phi, sg >= 0.f ? i - 1 : i, j, k);
+        for (int m = 0; m < 6; ++m) q[m] = fval(g, phi, i - 3 + m, j, k) - tu;
+        fx[n] = mf * (tu + weno5<float>(q, sg, zf));
+        mf = __ldg(mfy + n) + dz * (ms.y[n] * rns); sg = sgnT<float>(mf);
+        tu = fval(g, phi, i, sg >= 0.f ? j - 1 : j, k);
+        for (int m = 0; m < 6; ++m) q[m] = fval(g, phi, i, j - 3 + m, k) - tu;
+        fy[n] = mf * (tu + weno5<float>(q, sg, zf));
+    }
+    if (k == 0 || k == g.nz) { fz[n] = 0.f; return; }
+    float W = __ldg(rw + n) + ms.z[n] * rns, sg = sgnT<float>(W);
+    float tu = fval(g, phi, i, j, sg >= 0.f ? k - 1 : k);
+    for (int m = 0; m < 6; ++m) q[m] = fval(g, phi, i, j, k - 3 + m) - tu;
+    fz[n] = W * (tu + weno5<float>(q, sg, zf));
+}
+__global__ void k_mx_tracer_update(Geo g, MxBase mb, const float *snphi, const float *fx, const float *fy,
+                                   const float *fz, float adt, float *rphi) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long c = ((long long)k * g.ny + j) * g.nx + i;
+    float div = (__ldg(fx + cixw(g, i + 1, j, k)) - __ldg(fx + c)) * mb.rdx
+              + (__ldg(fy + cixw(g, i, j + 1, k)) - __ldg(fy + c)) * mb.rdy + (__ldg(fz + c + g.nxy) - __ldg(fz + c));
+    rphi[c] = snphi[c] - adt * div * mb.rdzf[k];
+}
+// rho phi = (rho0 + rho') phi0, formed in FP64 from the FP64 base density
+__global__ void k_mx_tracer_init(Geo g, const double *rho0, const float *dr, const double *phi0, float *rphi) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int k = (int)(c / g.nxy);
+    rphi[c] = (float)((rho0[k] + (double)dr[c]) * phi0[c]);
 }
 
 __global__ void k_mx_stage_end(Geo g, F5f st, CF5f x) {
@@ -1040,15 +1153,13 @@ void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const 
                  const ClIn *cl, const MxTma *tma) {
     mx_launch("mx_prep", s, [&] { k_mx_prep<<<g3(g, g.nz + 1), MBX, 0, s>>>(g, mb, st, ux, vy, wz, mfx, mfy); });
     int learned = ph.closure == 3 && cl;
-    int sgs = (ph.closure == 1 || ph.closure == 2 || (ph.surface == 1 && !learned)) ? 1 : 0;
-    if (ph.closure == 1 || ph.closure == 2)
-        mx_launch("mx_sgs_mu", s, [&] { k_mx_sgs_mu<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, VelF{ux, vy, wz}, st.r, mu); });
+    const int visc = (ph.closure == 1 || ph.closure == 2) ? 1 : 0;
+    const int sgs = (visc || (ph.surface == 1 && !learned)) ? 1 : 0;
     const float *tau = nullptr;
     if (learned) {
         cl_infer(g, mb, ph, cl->w, cl->b, cl->stats, ux, vy, wz, thp, st.r, cl->out, cl->nfb, s);
         tau = cl->out;
     }
-    PrepF pr{ux, vy, wz, mfx, mfy, tau};
     // each advected quantity's face fluxes go to the shared buffer (3 planes of nw), then the
     // divergence kernel of that quantity reads them
     float *ax = flux, *ay = flux + g.nw, *az = flux + 2 * g.nw;
@@ -1065,7 +1176,7 @@ void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const 
         mx_launch("mx_flux_theta", s, [&] { k_mx_flux_theta<<<gw, MBX, 0, s>>>(g, mb, ph, mfx, mfy, st.w, thp, ax, ay, az); });
     }
     mx_launch("mx_rhs_cells", s, [&] {
-        k_mx_rhs_cells<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, pr, st.w, thp, st.r, mu, sgs, fl, R.r, R.t);
+        k_mx_rhs_cells<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, mfx, mfy, st.w, fl, R.r, R.t);
     });
     if (tma && tma->use) {
         const dim3 gt((unsigned)((g.nx + FT_TX - 1) / FT_TX), (unsigned)((g.ny + FT_TY - 1) / FT_TY),
@@ -1077,7 +1188,7 @@ void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const 
     } else {
         mx_launch("mx_flux_u", s, [&] { k_mx_flux_u<<<gw, MBX, 0, s>>>(g, ux, mfx, mfy, st.w, ax, ay, az); });
     }
-    mx_launch("mx_rhs_u", s, [&] { k_mx_rhs_u<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, fl, R.u); });
+    mx_launch("mx_rhs_u", s, [&] { k_mx_rhs_u<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, st, pp, fl, R.u); });
     if (tma && tma->use) {
         const dim3 gt((unsigned)((g.nx + FT_TX - 1) / FT_TX), (unsigned)((g.ny + FT_TY - 1) / FT_TY),
                       (unsigned)((g.nz + 1 + FT_TZ - 1) / FT_TZ));
@@ -1088,7 +1199,7 @@ void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const 
     } else {
         mx_launch("mx_flux_v", s, [&] { k_mx_flux_v<<<gw, MBX, 0, s>>>(g, vy, mfx, mfy, st.w, ax, ay, az); });
     }
-    mx_launch("mx_rhs_v", s, [&] { k_mx_rhs_v<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, fl, R.v); });
+    mx_launch("mx_rhs_v", s, [&] { k_mx_rhs_v<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, st, pp, fl, R.v); });
     if (tma && tma->use) {
         const dim3 gt((unsigned)((g.nx + FT_TX - 1) / FT_TX), (unsigned)((g.ny + FT_TY - 1) / FT_TY),
                       (unsigned)((g.nz + 1 + FT_TZ - 1) / FT_TZ));
@@ -1099,7 +1210,22 @@ void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const 
     } else {
         mx_launch("mx_flux_w", s, [&] { k_mx_flux_w<<<gw, MBX, 0, s>>>(g, wz, mfx, mfy, st.w, ax, ay, az); });
     }
-    mx_launch("mx_rhs_w", s, [&] { k_mx_rhs_w<<<gw, MBX, 0, s>>>(g, mb, ph, pr, st, pp, thp, mu, sgs, fl, R.w); });
+    mx_launch("mx_rhs_w", s, [&] { k_mx_rhs_w<<<gw, MBX, 0, s>>>(g, mb, st, pp, fl, R.w); });
+    if (tau) {
+        VelF v{ux, vy, wz};
+        mx_launch("mx_cl_edges", s, [&] { k_mx_cl_edges<<<gw, MBX, 0, s>>>(g, mb, ph, v, mu, st.r, thp, tau, ax, ay, az); });
+        mx_launch("mx_cl_div", s, [&] { k_mx_cl_div<<<gw, MBX, 0, s>>>(g, mb, ph, st.r, tau, ax, ay, az, R); });
+    }
+    if (sgs) {
+        // subgrid stresses and heat fluxes, each edge and face once (the flux planes are free again)
+        VelF v{ux, vy, wz};
+        if (visc) {
+            mx_launch("mx_sgs_edges", s, [&] { k_mx_sgs_edges<<<gw, MBX, 0, s>>>(g, mb, v, ax, ay, az); });
+            mx_launch("mx_sgs_mu", s, [&] { k_mx_sgs_mu<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, v, st.r, ax, ay, az, mu); });
+        }
+        mx_launch("mx_sgs_tau", s, [&] { k_mx_sgs_tau<<<gw, MBX, 0, s>>>(g, mb, ph, v, mu, st.r, thp, visc, ax, ay, az); });
+        mx_launch("mx_sgs_div", s, [&] { k_mx_sgs_div<<<gw, MBX, 0, s>>>(g, mb, ph, v, mu, st.r, thp, visc, ax, ay, az, R); });
+    }
 }
 void mx_slow_prep_only(const Geo &g, const MxBase &mb, CF5f st, float *ux, float *vy, float *wz, float *mfx,
                        float *mfy, cudaStream_t s) {
@@ -1110,14 +1236,15 @@ void mx_tri_build(const Geo &g, const MxBase &mb, const Phys &ph, const float *d
     mx_launch("mx_tri_build", s, [&] { k_mx_tri_build<<<nb(g.nxy, 128), 128, 0, s>>>(g, mb, ph, dr, dT, pi, thp, dtau, tr); });
 }
 void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, TriM tr, const float *pi, const float *thp, CF5f R,
-                F5f x, float *Om, float *Tt, double *dbuf, float *X0, float *Y0, double dtau, cudaStream_t s) {
+                F5f x, float *Om, float *Tt, double *dbuf, float *X0, float *Y0, TrSum ms, double dtau,
+                cudaStream_t s) {
     const dim3 blk(128), grd((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)g.nz);
     const float dtf = (float)dtau, Gg = (float)(dtau * 0.5 * ph.g);
     mx_launch("mx_sub_horiz", s, [&] {
         k_mx_sub_horiz<<<grd, blk, 0, s>>>(g, mb, pi, Tt, R.u, R.v, x.u, x.v, dtf);
     });
     mx_launch("mx_sub_expl", s, [&] {
-        k_mx_sub_expl<<<grd, blk, 0, s>>>(g, mb, ph, thp, R.r, R.t, x, Om, Tt, X0, Y0, dtf);
+        k_mx_sub_expl<<<grd, blk, 0, s>>>(g, mb, ph, thp, R.r, R.t, x, Om, Tt, X0, Y0, dtf, ms);
     });
     mx_launch("mx_sub_col", s, [&] {
         // deeper unrolling keeps more loads in flight once there are enough columns to fill the
@@ -1131,13 +1258,30 @@ void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, TriM tr, const f
     });
     if (g.nx % 4 == 0) {
         const dim3 grd4((unsigned)((g.nx / 4 + 127) / 128), (unsigned)g.ny, (unsigned)g.nz);
-        mx_launch("mx_sub_fin", s, [&] { k_mx_sub_fin4<<<grd4, blk, 0, s>>>(g, mb, ph, thp, Om, x, Tt, dtf); });
+        mx_launch("mx_sub_fin", s, [&] { k_mx_sub_fin4<<<grd4, blk, 0, s>>>(g, mb, ph, thp, Om, x, Tt, dtf, ms.z); });
     } else {
-        mx_launch("mx_sub_fin", s, [&] { k_mx_sub_fin<<<grd, blk, 0, s>>>(g, mb, ph, thp, Om, x, Tt, dtf); });
+        mx_launch("mx_sub_fin", s, [&] { k_mx_sub_fin<<<grd, blk, 0, s>>>(g, mb, ph, thp, Om, x, Tt, dtf, ms.z); });
     }
 }
 void mx_stage_end(const Geo &g, F5f st, CF5f x, cudaStream_t s) {
     mx_launch("mx_stage_end", s, [&] { k_mx_stage_end<<<nb(g.nw, MBS), MBS, 0, s>>>(g, st, x); });
+}
+void mx_tracer_stage(const Geo &g, const MxBase &mb, const Phys &ph, const float *dr, const float *mfx,
+                     const float *mfy, const float *rw, const float *snphi, TrSum ms, int nsub, double adt,
+                     float *phi, float *flux, float *rphi, cudaStream_t s) {
+    float *fx = flux, *fy = flux + g.nw, *fz = flux + 2 * g.nw;
+    const float rns = (float)(1.0 / nsub), adtf = (float)adt;
+    mx_launch("mx_tracer_phi", s, [&] { k_mx_tracer_phi<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, rphi, dr, phi); });
+    mx_launch("mx_tracer_flux", s, [&] {
+        k_mx_tracer_flux<<<g3(g, g.nz + 1), MBX, 0, s>>>(g, mb, ph, mfx, mfy, rw, phi, ms, rns, fx, fy, fz);
+    });
+    mx_launch("mx_tracer_update", s, [&] {
+        k_mx_tracer_update<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, snphi, fx, fy, fz, adtf, rphi);
+    });
+}
+void mx_tracer_init(const Geo &g, const double *rho0, const float *dr, const double *phi0, float *rphi,
+                    cudaStream_t s) {
+    k_mx_tracer_init<<<nb(g.nc, MBS), MBS, 0, s>>>(g, rho0, dr, phi0, rphi);
 }
 void mx_diag(const Geo &g, const MxBase &mb, CF5f st, double dt, double *part, double *out, cudaStream_t s) {
     k_mx_diag_partial<<<MX_DIAG_BLOCKS, 256, 0, s>>>(g, mb, st, part);

@@ -105,9 +105,21 @@ void mx_slow_prep_only(const Geo &g, const MxBase &mb, CF5f st, float *ux, float
                        float *mfy, cudaStream_t s);
 void mx_tri_build(const Geo &g, const MxBase &mb, const Phys &ph, const float *dr, const float *dT, const float *pi,
                   const float *thp, double dtau, TriM tr, cudaStream_t s);
+// passive-scalar sums of the substeps' perturbation momenta U'', V'' and vertical flux
+// b1 Omega''^tau + b2 Omega''^(tau+dtau) (all null without the scalar)
+struct TrSum {
+    float *x, *y, *z;
+};
 void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, TriM tr, const float *pi, const float *thp, CF5f R,
-                F5f x, float *Om, float *Tt, double *dbuf, float *X0, float *Y0, double dtau, cudaStream_t s);
+                F5f x, float *Om, float *Tt, double *dbuf, float *X0, float *Y0, TrSum ms, double dtau,
+                cudaStream_t s);
 void mx_stage_end(const Geo &g, F5f st, CF5f x, cudaStream_t s);
+// rho phi^(s) from S^n's rho phi and the stage's averaged mass fluxes (phi and flux are scratch)
+void mx_tracer_stage(const Geo &g, const MxBase &mb, const Phys &ph, const float *dr, const float *mfx,
+                     const float *mfy, const float *rw, const float *snphi, TrSum ms, int nsub, double adt,
+                     float *phi, float *flux, float *rphi, cudaStream_t s);
+void mx_tracer_init(const Geo &g, const double *rho0, const float *dr, const double *phi0, float *rphi,
+                    cudaStream_t s);
 void mx_diag(const Geo &g, const MxBase &mb, CF5f st, double dt, double *part, double *out, cudaStream_t s);
 
 // layout of the FP32 base table block built by mx_build_base (offsets in floats)
