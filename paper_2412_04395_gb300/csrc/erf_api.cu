@@ -176,7 +176,9 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
         H->mpp = cv.take<float>(nc); H->mpi = cv.take<float>(nc); H->mthp = cv.take<float>(nc);
         H->mTp = cv.take<float>(nc); H->mOm = cv.take<float>(nw);
         H->mux = cv.take<float>(nc); H->mvy = cv.take<float>(nc); H->mwz = cv.take<float>(nw);
-        H->mmfx = cv.take<float>(nc); H->mmfy = cv.take<float>(nc); H->mmu = cv.take<float>(nc);
+        H->mmfx = cv.take<float>(nc); H->mmfy = cv.take<float>(nc);
+        // eddy viscosity, then (eddy-viscosity closures) the three diagonal stresses
+        H->mmu = cv.take<float>((c->closure == 1 || c->closure == 2) ? 4 * nc : nc);
         H->mbase = cv.take<float>(mx_base_floats((int)nz));
         H->mrt0 = cv.take<double>(nz);
         H->mdbuf = cv.take<double>(nw);

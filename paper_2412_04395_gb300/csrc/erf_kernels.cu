@@ -275,15 +275,16 @@ __device__ __forceinline__ void diag_strain(const Geo &g, const Vel &v, int i, i
 
 // mu = rho (Cs Delta)^2 sqrt(2 S_ij S_ij) (Smagorinsky-Lilly) or rho nu (constant); the
 // off-diagonal strains come from the edge arrays of k_sgs_edges (4-point averages to the centre)
+// eddy viscosity at cells and the deviatoric diagonal stresses -2 mu (S_ii - div/3) (t11, t22, t33)
 __global__ void k_sgs_mu(Geo g, Phys ph, Vel v, const double *rho, const double *e12, const double *e13,
-                         const double *e23, double *mu) {
+                         const double *e23, double *mu, double *t11, double *t22, double *t33) {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= g.nc) return;
     int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
     double m = 0.0;
+    double s11, s22, s33;
+    diag_strain(g, v, i, j, k, s11, s22, s33);
     if (ph.closure == 2) {
-        double s11, s22, s33;
-        diag_strain(g, v, i, j, k, s11, s22, s33);
         double s12 = 0.25 * (cval(g, e12, i, j, k) + cval(g, e12, i + 1, j, k) + cval(g, e12, i, j + 1, k) + cval(g, e12, i + 1, j + 1, k));
         double s13 = 0.25 * (__ldg(e13 + cixw(g, i, j, k)) + __ldg(e13 + cixw(g, i + 1, j, k)) + __ldg(e13 + cixw(g, i, j, k + 1))
                            + __ldg(e13 + cixw(g, i + 1, j, k + 1)));
@@ -295,17 +296,10 @@ __global__ void k_sgs_mu(Geo g, Phys ph, Vel v, const double *rho, const double 
         m = rho[c] * ph.nu;
     }
     mu[c] = m;
-}
-__device__ __forceinline__ double tau_diag(const Geo &g, const Vel &v, const double *mu, int i, int j, int k, int comp) {
-    double s11, s22, s33;
-    diag_strain(g, v, i, j, k, s11, s22, s33);
-    double dv = (s11 + s22 + s33) * (1.0 / 3.0);
-    double s = comp == 0 ? s11 : (comp == 1 ? s22 : s33);
-    return -2.0 * cval(g, mu, i, j, k) * (s - dv);
-}
-__device__ __forceinline__ double tau12(const Geo &g, const Vel &v, const double *mu, int i, int j, int k) {
-    double me = 0.25 * (cval(g, mu, i - 1, j - 1, k) + cval(g, mu, i, j - 1, k) + cval(g, mu, i - 1, j, k) + cval(g, mu, i, j, k));
-    return -2.0 * me * S12e(g, v, i, j, k);
+    const double dv = (s11 + s22 + s33) * (1.0 / 3.0);
+    t11[c] = -2.0 * m * (s11 - dv);
+    t22[c] = -2.0 * m * (s22 - dv);
+    t33[c] = -2.0 * m * (s33 - dv);
 }
 
 // MOST friction velocity (reading R15): neutral start, 5 fixed-point iterations through the
@@ -331,42 +325,31 @@ __device__ double ustar_most(double U, double z1, double z0, double Q, double th
     return us;
 }
 
-// tau13 at the xz-edge (x-face i, w-face k): interior -2 mu_e S13; bottom: MOST or 0; top: 0
-__device__ double tau13(const Geo &g, const Phys &ph, const Vel &v, const double *mu, const double *rho,
-                        const double *th, int i, int j, int k, int visc) {
-    if (k == 0) {
-        if (ph.surface != 1) return 0.0;
-        double u = cval(g, v.ux, i, j, 0);
-        double vv = 0.25 * (cval(g, v.vy, i - 1, j, 0) + cval(g, v.vy, i, j, 0) + cval(g, v.vy, i - 1, j + 1, 0) + cval(g, v.vy, i, j + 1, 0));
-        double U = sqrt(u * u + vv * vv);
-        if (!(U > 0.0)) return 0.0;
-        double thf = 0.5 * (cval(g, th, i - 1, j, 0) + cval(g, th, i, j, 0));
-        double rhf = 0.5 * (cval(g, rho, i - 1, j, 0) + cval(g, rho, i, j, 0));
-        double z1 = 0.5 * g.dzeta[0];
-        double us = ustar_most(U, z1, ph.z0, ph.Qs, thf, ph.g);
-        return -rhf * us * us * u / U;
-    }
-    if (k >= g.nz || !visc) return 0.0;
-    double me = 0.25 * (cval(g, mu, i - 1, j, k - 1) + cval(g, mu, i, j, k - 1) + cval(g, mu, i - 1, j, k) + cval(g, mu, i, j, k));
-    return -2.0 * me * S13e(g, v, i, j, k);
+// MOST surface stresses (Sec. 3.8, reading R15) at the ground: tau13 at the x-face (i, j), tau23 at
+// the y-face (i, j), -rho u*^2 u_i / |U| with the first-level wind; 0 for a slip wall
+__device__ double most13(const Geo &g, const Phys &ph, const Vel &v, const double *rho, const double *th, int i, int j) {
+    if (ph.surface != 1) return 0.0;
+    double u = cval(g, v.ux, i, j, 0);
+    double vv = 0.25 * (cval(g, v.vy, i - 1, j, 0) + cval(g, v.vy, i, j, 0) + cval(g, v.vy, i - 1, j + 1, 0) + cval(g, v.vy, i, j + 1, 0));
+    double U = sqrt(u * u + vv * vv);
+    if (!(U > 0.0)) return 0.0;
+    double thf = 0.5 * (cval(g, th, i - 1, j, 0) + cval(g, th, i, j, 0));
+    double rhf = 0.5 * (cval(g, rho, i - 1, j, 0) + cval(g, rho, i, j, 0));
+    double z1 = 0.5 * g.dzeta[0];
+    double us = ustar_most(U, z1, ph.z0, ph.Qs, thf, ph.g);
+    return -rhf * us * us * u / U;
 }
-__device__ double tau23(const Geo &g, const Phys &ph, const Vel &v, const double *mu, const double *rho,
-                        const double *th, int i, int j, int k, int visc) {
-    if (k == 0) {
-        if (ph.surface != 1) return 0.0;
-        double u = 0.25 * (cval(g, v.ux, i, j - 1, 0) + cval(g, v.ux, i + 1, j - 1, 0) + cval(g, v.ux, i, j, 0) + cval(g, v.ux, i + 1, j, 0));
-        double vv = cval(g, v.vy, i, j, 0);
-        double U = sqrt(u * u + vv * vv);
-        if (!(U > 0.0)) return 0.0;
-        double thf = 0.5 * (cval(g, th, i, j - 1, 0) + cval(g, th, i, j, 0));
-        double rhf = 0.5 * (cval(g, rho, i, j - 1, 0) + cval(g, rho, i, j, 0));
-        double z1 = 0.5 * g.dzeta[0];
-        double us = ustar_most(U, z1, ph.z0, ph.Qs, thf, ph.g);
-        return -rhf * us * us * vv / U;
-    }
-    if (k >= g.nz || !visc) return 0.0;
-    double me = 0.25 * (cval(g, mu, i, j - 1, k - 1) + cval(g, mu, i, j, k - 1) + cval(g, mu, i, j - 1, k) + cval(g, mu, i, j, k));
-    return -2.0 * me * S23e(g, v, i, j, k);
+__device__ double most23(const Geo &g, const Phys &ph, const Vel &v, const double *rho, const double *th, int i, int j) {
+    if (ph.surface != 1) return 0.0;
+    double u = 0.25 * (cval(g, v.ux, i, j - 1, 0) + cval(g, v.ux, i + 1, j - 1, 0) + cval(g, v.ux, i, j, 0) + cval(g, v.ux, i + 1, j, 0));
+    double vv = cval(g, v.vy, i, j, 0);
+    double U = sqrt(u * u + vv * vv);
+    if (!(U > 0.0)) return 0.0;
+    double thf = 0.5 * (cval(g, th, i, j - 1, 0) + cval(g, th, i, j, 0));
+    double rhf = 0.5 * (cval(g, rho, i, j - 1, 0) + cval(g, rho, i, j, 0));
+    double z1 = 0.5 * g.dzeta[0];
+    double us = ustar_most(U, z1, ph.z0, ph.Qs, thf, ph.g);
+    return -rhf * us * us * vv / U;
 }
 // rho alpha dtheta/dn at the three face types (minus the diffusive flux); bottom face: the
 // upward MOST flux rho Q enters as -rho Q
@@ -407,8 +390,8 @@ __global__ void k_sgs_tau(Geo g, Phys ph, Vel v, const double *mu, const double 
         t12[n] = visc ? -2.0 * me * t12[n] : 0.0;
     }
     if (k == 0) {
-        t13[n] = tau13(g, ph, v, mu, rho, th, i, j, 0, visc);
-        t23[n] = tau23(g, ph, v, mu, rho, th, i, j, 0, visc);
+        t13[n] = most13(g, ph, v, rho, th, i, j);
+        t23[n] = most23(g, ph, v, rho, th, i, j);
     } else if (k >= g.nz || !visc) {
         t13[n] = 0.0;
         t23[n] = 0.0;
@@ -419,17 +402,18 @@ __global__ void k_sgs_tau(Geo g, Phys ph, Vel v, const double *mu, const double 
         t23[n] = -2.0 * my * t23[n];
     }
 }
-__global__ void k_sgs_div(Geo g, Phys ph, Vel v, const double *mu, const double *rho, const double *th, int visc,
-                          const double *t12, const double *t13, const double *t23, F5 R) {
+__global__ void k_sgs_div(Geo g, Phys ph, const double *mu, const double *t11, const double *t22, const double *t33,
+                          const double *rho, const double *th, int visc, const double *t12, const double *t13,
+                          const double *t23, F5 R) {
     SGS_CELL3D_W();
     const long long nxy = g.nxy;
     if (k < g.nz) {
         double du = 0.0, dv = 0.0, hd = 0.0;
         if (visc) {
-            du = (tau_diag(g, v, mu, i, j, k, 0) - tau_diag(g, v, mu, i - 1, j, k, 0)) * g.rdx
+            du = (__ldg(t11 + n) - __ldg(t11 + cixw(g, i - 1, j, k))) * g.rdx
                + (__ldg(t12 + cixw(g, i, j + 1, k)) - __ldg(t12 + n)) * g.rdy;
             dv = (__ldg(t12 + cixw(g, i + 1, j, k)) - __ldg(t12 + n)) * g.rdx
-               + (tau_diag(g, v, mu, i, j, k, 1) - tau_diag(g, v, mu, i, j - 1, k, 1)) * g.rdy;
+               + (__ldg(t22 + n) - __ldg(t22 + cixw(g, i, j - 1, k))) * g.rdy;
             hd = (heat_x(g, ph, mu, th, i + 1, j, k) - heat_x(g, ph, mu, th, i, j, k)) * g.rdx
                + (heat_y(g, ph, mu, th, i, j + 1, k) - heat_y(g, ph, mu, th, i, j, k)) * g.rdy;
         }
@@ -443,7 +427,7 @@ __global__ void k_sgs_div(Geo g, Phys ph, Vel v, const double *mu, const double 
     if (visc && k >= 1 && k < g.nz) {
         double dw = (__ldg(t13 + cixw(g, i + 1, j, k)) - __ldg(t13 + n)) * g.rdx
                   + (__ldg(t23 + cixw(g, i, j + 1, k)) - __ldg(t23 + n)) * g.rdy
-                  + (tau_diag(g, v, mu, i, j, k, 2) - tau_diag(g, v, mu, i, j, k - 1, 2)) * rdzcw(g, i, j, k);
+                  + (__ldg(t33 + n) - __ldg(t33 + n - nxy)) * rdzcw(g, i, j, k);
         R.w[n] -= dw;
     }
 }
@@ -517,8 +501,8 @@ __global__ void k_flux_theta(Geo g, Phys ph, Prep pr, const double *th, double *
 }
 
 // continuity and potential temperature (Eq. con, Eq. theta): flux divergence / cell height
-__global__ void k_rhs_cells(Geo g, Phys ph, Prep pr, const double *fx, const double *fy, const double *fz,
-                            const double *th, const double *rho, const double *mu, int sgs, double *Rr, double *Rt) {
+__global__ void k_rhs_cells(Geo g, Prep pr, const double *fx, const double *fy, const double *fz, double *Rr,
+                            double *Rt) {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= g.nc) return;
     int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
@@ -526,16 +510,6 @@ __global__ void k_rhs_cells(Geo g, Phys ph, Prep pr, const double *fx, const dou
     double rH = rHc(g, i, j, k);
     Rr[c] = -((pr.mfx[cxp] - pr.mfx[c]) * g.rdx + (pr.mfy[cyp] - pr.mfy[c]) * g.rdy + (pr.rom[ckp] - pr.rom[c])) * rH;
     double r = -((fx[cxp] - fx[c]) * g.rdx + (fy[cyp] - fy[c]) * g.rdy + (fz[ckp] - fz[c])) * rH;
-    if (sgs) {
-        int visc = ph.closure == 1 || ph.closure == 2;
-        double hd = 0.0;
-        if (visc) {
-            hd += (heat_x(g, ph, mu, th, i + 1, j, k) - heat_x(g, ph, mu, th, i, j, k)) * g.rdx
-                + (heat_y(g, ph, mu, th, i, j + 1, k) - heat_y(g, ph, mu, th, i, j, k)) * g.rdy;
-        }
-        hd += (heat_z(g, ph, mu, th, rho, i, j, k + 1, visc) - heat_z(g, ph, mu, th, rho, i, j, k, visc)) * rH;
-        r += hd;
-    }
     Rt[c] = r;
 }
 
@@ -603,8 +577,8 @@ __global__ void k_flux_w(Geo g, Prep pr, double *fx, double *fy, double *fz) {
 
 // x-momentum at x-face (i,j,k): upwind-5 advection (reading R5), terrain pressure gradient
 // (App. B), Coriolis, -div(tau)
-__global__ void k_rhs_u(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const double *th, const double *mu,
-                        int sgs, const double *fx, const double *fy, const double *fz, double *Ru) {
+__global__ void k_rhs_u(Geo g, Phys ph, CF5 st, const double *pp, const double *fx, const double *fy,
+                        const double *fz, double *Ru) {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= g.nc) return;
     int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
@@ -625,22 +599,11 @@ __global__ void k_rhs_u(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const
         double rhx = 0.5 * (cval(g, st.r, i - 1, j, k) + cval(g, st.r, i, j, k));
         r += ph.f_cor * (rvx - rhx * ph.v_g);
     }
-    if (sgs) {
-        int visc = ph.closure == 1 || ph.closure == 2;
-        Vel v{pr.ux, pr.vy, pr.wz};
-        double d = 0.0;
-        if (visc) {
-            d += (tau_diag(g, v, mu, i, j, k, 0) - tau_diag(g, v, mu, i - 1, j, k, 0)) * g.rdx
-               + (tau12(g, v, mu, i, j + 1, k) - tau12(g, v, mu, i, j, k)) * g.rdy;
-        }
-        d += (tau13(g, ph, v, mu, st.r, th, i, j, k + 1, visc) - tau13(g, ph, v, mu, st.r, th, i, j, k, visc)) * g.rdzeta[k];
-        r -= d;
-    }
     Ru[c] = r;
 }
 
-__global__ void k_rhs_v(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const double *th, const double *mu,
-                        int sgs, const double *fx, const double *fy, const double *fz, double *Rv) {
+__global__ void k_rhs_v(Geo g, Phys ph, CF5 st, const double *pp, const double *fx, const double *fy,
+                        const double *fz, double *Rv) {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= g.nc) return;
     int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
@@ -660,23 +623,12 @@ __global__ void k_rhs_v(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const
         double rhy = 0.5 * (cval(g, st.r, i, j - 1, k) + cval(g, st.r, i, j, k));
         r -= ph.f_cor * (rux - rhy * ph.u_g);
     }
-    if (sgs) {
-        int visc = ph.closure == 1 || ph.closure == 2;
-        Vel v{pr.ux, pr.vy, pr.wz};
-        double d = 0.0;
-        if (visc) {
-            d += (tau12(g, v, mu, i + 1, j, k) - tau12(g, v, mu, i, j, k)) * g.rdx
-               + (tau_diag(g, v, mu, i, j, k, 1) - tau_diag(g, v, mu, i, j - 1, k, 1)) * g.rdy;
-        }
-        d += (tau23(g, ph, v, mu, st.r, th, i, j, k + 1, visc) - tau23(g, ph, v, mu, st.r, th, i, j, k, visc)) * g.rdzeta[k];
-        r -= d;
-    }
     Rv[c] = r;
 }
 
 // z-momentum at interior w-faces; boundary rows are zero
-__global__ void k_rhs_w(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const double *th, const double *mu,
-                        int sgs, const double *fx, const double *fy, const double *fz, double *Rw) {
+__global__ void k_rhs_w(Geo g, Phys ph, CF5 st, const double *pp, const double *fx, const double *fy,
+                        const double *fz, double *Rw) {
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= g.nw) return;
     int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / g.nxy);
@@ -689,13 +641,6 @@ __global__ void k_rhs_w(Geo g, Phys ph, Prep pr, CF5 st, const double *pp, const
     r -= (pp[c] - pp[cm]) * rdz;
     double b0 = g.rho0[bix(g, i, j, k - 1)], b1 = g.rho0[bix(g, i, j, k)];
     r += 0.5 * (-ph.g * (st.r[cm] - b0) - ph.g * (st.r[c] - b1));
-    if (sgs && (ph.closure == 1 || ph.closure == 2)) {
-        Vel v{pr.ux, pr.vy, pr.wz};
-        double d = (tau13(g, ph, v, mu, st.r, th, i + 1, j, k, 1) - tau13(g, ph, v, mu, st.r, th, i, j, k, 1)) * g.rdx
-                 + (tau23(g, ph, v, mu, st.r, th, i, j + 1, k, 1) - tau23(g, ph, v, mu, st.r, th, i, j, k, 1)) * g.rdy
-                 + (tau_diag(g, v, mu, i, j, k, 2) - tau_diag(g, v, mu, i, j, k - 1, 2)) * rdz;
-        r -= d;
-    }
     Rw[n] = r;
 }
 
@@ -1084,7 +1029,7 @@ void launch_stage_begin(const Geo &g, CF5 sn, CF5 st, F5 x, double *pp, double *
                         double *Om, cudaStream_t s) {
     LAUNCH("stage_begin", s, k_stage_begin<<<nblk(g.nw, BS), BS, 0, s>>>(g, sn, st, x, pp, pi, th, Tp, Om));
 }
-void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, const double *pp, const double *th, Prep pr,
+void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, double *pp, const double *th, Prep pr,
                      double *ux, double *vy, double *wz, double *mfx, double *mfy, double *rom, double *mu,
                      double *flux, F5 R, cudaStream_t s) {
     LAUNCH("prep", s, k_prep<<<nblk(g.nw, BS), BS, 0, s>>>(g, st, ux, vy, wz, mfx, mfy, rom));
@@ -1093,26 +1038,29 @@ void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, const double *pp, con
     // advection, pressure gradient, buoyancy and Coriolis (the subgrid terms follow below)
     double *fx = flux, *fy = flux + g.nc, *fz = flux + 2 * g.nc;
     LAUNCH("flux_theta", s, k_flux_theta<<<nblk(g.nw, BS), BS, 0, s>>>(g, ph, pr, th, fx, fy, fz));
-    LAUNCH("rhs_cells", s, k_rhs_cells<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, fx, fy, fz, th, st.r, mu, 0, R.r, R.t));
+    LAUNCH("rhs_cells", s, k_rhs_cells<<<nblk(g.nc, BS), BS, 0, s>>>(g, pr, fx, fy, fz, R.r, R.t));
     // momentum: fluxes of each component into the shared buffer, then its divergence
     const dim3 g3w((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)(g.nz + 1));
     double *ax = flux, *ay = flux + g.nw, *az = flux + 2 * g.nw;
     LAUNCH("flux_u", s, k_flux_u<<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
-    LAUNCH("rhs_u", s, k_rhs_u<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, 0, ax, ay, az, R.u));
+    LAUNCH("rhs_u", s, k_rhs_u<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, st, pp, ax, ay, az, R.u));
     LAUNCH("flux_v", s, k_flux_v<<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
-    LAUNCH("rhs_v", s, k_rhs_v<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, 0, ax, ay, az, R.v));
+    LAUNCH("rhs_v", s, k_rhs_v<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, st, pp, ax, ay, az, R.v));
     LAUNCH("flux_w", s, k_flux_w<<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
-    LAUNCH("rhs_w", s, k_rhs_w<<<nblk(g.nw, BS), BS, 0, s>>>(g, ph, pr, st, pp, th, mu, 0, ax, ay, az, R.w));
+    LAUNCH("rhs_w", s, k_rhs_w<<<nblk(g.nw, BS), BS, 0, s>>>(g, ph, st, pp, ax, ay, az, R.w));
     if (sgs) {
         // subgrid stresses and heat fluxes, each edge and face once (the flux buffer is free again)
         Vel v{ux, vy, wz};
         double *e12 = flux, *e13 = flux + g.nw, *e23 = flux + 2 * g.nw;
+        // the pressure and the mass fluxes are no longer needed in this stage's slow pass: they
+        // take the diagonal stresses
+        double *t11 = pp, *t22 = mfx, *t33 = mfy;
         if (visc) {
             LAUNCH("sgs_edges", s, k_sgs_edges<<<g3w, 128, 0, s>>>(g, v, e12, e13, e23));
-            LAUNCH("sgs_mu", s, k_sgs_mu<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, v, st.r, e12, e13, e23, mu));
+            LAUNCH("sgs_mu", s, k_sgs_mu<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, v, st.r, e12, e13, e23, mu, t11, t22, t33));
         }
         LAUNCH("sgs_tau", s, k_sgs_tau<<<g3w, 128, 0, s>>>(g, ph, v, mu, st.r, th, visc, e12, e13, e23));
-        LAUNCH("sgs_div", s, k_sgs_div<<<g3w, 128, 0, s>>>(g, ph, v, mu, st.r, th, visc, e12, e13, e23, R));
+        LAUNCH("sgs_div", s, k_sgs_div<<<g3w, 128, 0, s>>>(g, ph, mu, t11, t22, t33, st.r, th, visc, e12, e13, e23, R));
     }
 }
 void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const double *rt, const double *pi,

@@ -17,7 +17,7 @@ void launch_set_initial(const Geo &g, const double *dth, const double *u, const 
 void launch_wall_bc(const Geo &g, const double *ru, const double *rv, double *rw, cudaStream_t s);
 void launch_stage_begin(const Geo &g, CF5 sn, CF5 st, F5 x, double *pp, double *pi, double *th, double *Tp,
                         double *Om, cudaStream_t s);
-void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, const double *pp, const double *th, Prep pr,
+void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, double *pp, const double *th, Prep pr,
                      double *ux, double *vy, double *wz, double *mfx, double *mfy, double *rom, double *mu,
                      double *flux, F5 R, cudaStream_t s);
 void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const double *rt, const double *pi,

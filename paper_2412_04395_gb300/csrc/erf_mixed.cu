@@ -164,60 +164,48 @@ __global__ void k_mx_prep(Geo g, MxBase mb, CF5f st, float *ux, float *vy, float
 struct VelF {
     const float *ux, *vy, *wz;
 };
-__device__ __forceinline__ float S12f(const Geo &g, const MxBase &mb, const VelF &v, int i, int j, int k) {
-    return 0.5f * ((fval(g, v.ux, i, j, k) - fval(g, v.ux, i, j - 1, k)) * mb.rdy
-                 + (fval(g, v.vy, i, j, k) - fval(g, v.vy, i - 1, j, k)) * mb.rdx);
+// periodic neighbour offsets of cell (i, j) in x and y (one wrap per direction)
+struct NbrOff {
+    long long xm, xp, ym, yp;
+};
+__device__ __forceinline__ NbrOff nbr_off(const Geo &g, int i, int j) {
+    NbrOff o;
+    o.xp = i + 1 < g.nx ? 1 : 1 - g.nx;
+    o.xm = i > 0 ? -1 : g.nx - 1;
+    o.yp = j + 1 < g.ny ? (long long)g.nx : (long long)g.nx - g.nxy;
+    o.ym = j > 0 ? -(long long)g.nx : g.nxy - g.nx;
+    return o;
 }
-__device__ __forceinline__ float S13f(const Geo &g, const MxBase &mb, const VelF &v, int i, int j, int k) {
-    if (k <= 0 || k >= g.nz) return 0.f;
-    return 0.5f * ((fval(g, v.ux, i, j, k) - fval(g, v.ux, i, j, k - 1)) * mb.rdzcf[k]
-                 + (__ldg(v.wz + cixw(g, i, j, k)) - __ldg(v.wz + cixw(g, i - 1, j, k))) * mb.rdx);
-}
-__device__ __forceinline__ float S23f(const Geo &g, const MxBase &mb, const VelF &v, int i, int j, int k) {
-    if (k <= 0 || k >= g.nz) return 0.f;
-    return 0.5f * ((fval(g, v.vy, i, j, k) - fval(g, v.vy, i, j, k - 1)) * mb.rdzcf[k]
-                 + (__ldg(v.wz + cixw(g, i, j, k)) - __ldg(v.wz + cixw(g, i, j - 1, k))) * mb.rdy);
-}
-__device__ __forceinline__ void diagSf(const Geo &g, const MxBase &mb, const VelF &v, int i, int j, int k, float &a,
-                                       float &b, float &c) {
-    a = (fval(g, v.ux, i + 1, j, k) - fval(g, v.ux, i, j, k)) * mb.rdx;
-    b = (fval(g, v.vy, i, j + 1, k) - fval(g, v.vy, i, j, k)) * mb.rdy;
-    c = (__ldg(v.wz + cixw(g, i, j, k + 1)) - __ldg(v.wz + cixw(g, i, j, k))) * mb.rdzf[k];
-}
+// eddy viscosity mu = rho (Cs Delta)^2 |S| (or rho nu) at cells, and, when tD is given, the
+// deviatoric diagonal stresses -2 mu (S_ii - div/3) in the planes tD, tD + nc, tD + 2 nc
 __global__ void k_mx_sgs_mu(Geo g, MxBase mb, Phys ph, VelF v, const float *dr, const float *e12, const float *e13,
-                            const float *e23, float *mu) {
+                            const float *e23, float *mu, float *tD) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
-    const long long c = ((long long)k * g.ny + j) * g.nx + i;
-    float rho = mb.rho0f[k] + dr[c];
+    const long long c = ((long long)k * g.ny + j) * g.nx + i, nxy = g.nxy;
+    const NbrOff o = nbr_off(g, i, j);
+    const float rho = mb.rho0f[k] + dr[c];
+    const float s11 = (__ldg(v.ux + c + o.xp) - __ldg(v.ux + c)) * mb.rdx;
+    const float s22 = (__ldg(v.vy + c + o.yp) - __ldg(v.vy + c)) * mb.rdy;
+    const float s33 = (__ldg(v.wz + c + nxy) - __ldg(v.wz + c)) * mb.rdzf[k];
     float m = 0.f;
     if (ph.closure == 2) {
-        float s11, s22, s33;
-        diagSf(g, mb, v, i, j, k, s11, s22, s33);
-        float s12 = 0.25f * (fval(g, e12, i, j, k) + fval(g, e12, i + 1, j, k) + fval(g, e12, i, j + 1, k) + fval(g, e12, i + 1, j + 1, k));
-        float s13 = 0.25f * (__ldg(e13 + cixw(g, i, j, k)) + __ldg(e13 + cixw(g, i + 1, j, k)) + __ldg(e13 + cixw(g, i, j, k + 1))
-                           + __ldg(e13 + cixw(g, i + 1, j, k + 1)));
-        float s23 = 0.25f * (__ldg(e23 + cixw(g, i, j, k)) + __ldg(e23 + cixw(g, i, j + 1, k)) + __ldg(e23 + cixw(g, i, j, k + 1))
-                           + __ldg(e23 + cixw(g, i, j + 1, k + 1)));
+        float s12 = 0.25f * (__ldg(e12 + c) + __ldg(e12 + c + o.xp) + __ldg(e12 + c + o.yp) + __ldg(e12 + c + o.xp + o.yp));
+        float s13 = 0.25f * (__ldg(e13 + c) + __ldg(e13 + c + o.xp) + __ldg(e13 + c + nxy) + __ldg(e13 + c + o.xp + nxy));
+        float s23 = 0.25f * (__ldg(e23 + c) + __ldg(e23 + c + o.yp) + __ldg(e23 + c + nxy) + __ldg(e23 + c + o.yp + nxy));
         float SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.f * (s12 * s12 + s13 * s13 + s23 * s23);
         m = rho * mb.delta2f[k] * sqrtf(2.f * SS);
     } else if (ph.closure == 1) {
         m = rho * mb.nu;
     }
     mu[c] = m;
-}
-__device__ __forceinline__ float tauDf(const Geo &g, const MxBase &mb, const VelF &v, const float *mu, int i, int j,
-                                       int k, int comp) {
-    float a, b, c;
-    diagSf(g, mb, v, i, j, k, a, b, c);
-    float dv = (a + b + c) * (1.f / 3.f);
-    float s = comp == 0 ? a : (comp == 1 ? b : c);
-    return -2.f * fval(g, mu, i, j, k) * (s - dv);
-}
-__device__ __forceinline__ float tau12f(const Geo &g, const MxBase &mb, const VelF &v, const float *mu, int i, int j, int k) {
-    float me = 0.25f * (fval(g, mu, i - 1, j - 1, k) + fval(g, mu, i, j - 1, k) + fval(g, mu, i - 1, j, k) + fval(g, mu, i, j, k));
-    return -2.f * me * S12f(g, mb, v, i, j, k);
+    if (tD) {
+        const float dv = (s11 + s22 + s33) * (1.f / 3.f);
+        tD[c] = -2.f * m * (s11 - dv);
+        tD[c + g.nc] = -2.f * m * (s22 - dv);
+        tD[c + 2 * g.nc] = -2.f * m * (s33 - dv);
+    }
 }
 __device__ float ustar_f(float U, float z1, float z0, float Q, float theta, float grav) {
     float lz = logf(z1 / z0);
@@ -239,153 +227,152 @@ __device__ float ustar_f(float U, float z1, float z0, float Q, float theta, floa
     }
     return us;
 }
-// tau13 at (x-face i, w-face k); bottom = MOST, top = 0
-__device__ float tau13f(const Geo &g, const MxBase &mb, const Phys &ph, const VelF &v, const float *mu,
-                        const float *dr, const float *thp, int i, int j, int k, int visc) {
-    if (k == 0) {
-        if (ph.surface != 1) return 0.f;
-        float u = fval(g, v.ux, i, j, 0);
-        float vv = 0.25f * (fval(g, v.vy, i - 1, j, 0) + fval(g, v.vy, i, j, 0) + fval(g, v.vy, i - 1, j + 1, 0) + fval(g, v.vy, i, j + 1, 0));
-        float U = sqrtf(u * u + vv * vv);
-        if (!(U > 0.f)) return 0.f;
-        float thf = mb.th0f[0] + 0.5f * (fval(g, thp, i - 1, j, 0) + fval(g, thp, i, j, 0));
-        float rhf = mb.rho0f[0] + 0.5f * (fval(g, dr, i - 1, j, 0) + fval(g, dr, i, j, 0));
-        float us = ustar_f(U, 0.5f * mb.dzf[0], mb.z0, mb.Qs, thf, mb.grav);
-        return -rhf * us * us * u / U;
-    }
-    if (k >= g.nz || !visc) return 0.f;
-    float me = 0.25f * (fval(g, mu, i - 1, j, k - 1) + fval(g, mu, i, j, k - 1) + fval(g, mu, i - 1, j, k) + fval(g, mu, i, j, k));
-    return -2.f * me * S13f(g, mb, v, i, j, k);
+// MOST surface stresses tau13 at the x-face (i, j) and tau23 at the y-face (i, j) of the ground
+// (Sec. 3.8): -rho u*^2 u_i / |U| with the first-level wind
+__device__ float most13f(const Geo &g, const MxBase &mb, const Phys &ph, const VelF &v, const float *dr,
+                         const float *thp, int i, int j) {
+    if (ph.surface != 1) return 0.f;
+    float u = fval(g, v.ux, i, j, 0);
+    float vv = 0.25f * (fval(g, v.vy, i - 1, j, 0) + fval(g, v.vy, i, j, 0) + fval(g, v.vy, i - 1, j + 1, 0) + fval(g, v.vy, i, j + 1, 0));
+    float U = sqrtf(u * u + vv * vv);
+    if (!(U > 0.f)) return 0.f;
+    float thf = mb.th0f[0] + 0.5f * (fval(g, thp, i - 1, j, 0) + fval(g, thp, i, j, 0));
+    float rhf = mb.rho0f[0] + 0.5f * (fval(g, dr, i - 1, j, 0) + fval(g, dr, i, j, 0));
+    float us = ustar_f(U, 0.5f * mb.dzf[0], mb.z0, mb.Qs, thf, mb.grav);
+    return -rhf * us * us * u / U;
 }
-__device__ float tau23f(const Geo &g, const MxBase &mb, const Phys &ph, const VelF &v, const float *mu,
-                        const float *dr, const float *thp, int i, int j, int k, int visc) {
-    if (k == 0) {
-        if (ph.surface != 1) return 0.f;
-        float u = 0.25f * (fval(g, v.ux, i, j - 1, 0) + fval(g, v.ux, i + 1, j - 1, 0) + fval(g, v.ux, i, j, 0) + fval(g, v.ux, i + 1, j, 0));
-        float vv = fval(g, v.vy, i, j, 0);
-        float U = sqrtf(u * u + vv * vv);
-        if (!(U > 0.f)) return 0.f;
-        float thf = mb.th0f[0] + 0.5f * (fval(g, thp, i, j - 1, 0) + fval(g, thp, i, j, 0));
-        float rhf = mb.rho0f[0] + 0.5f * (fval(g, dr, i, j - 1, 0) + fval(g, dr, i, j, 0));
-        float us = ustar_f(U, 0.5f * mb.dzf[0], mb.z0, mb.Qs, thf, mb.grav);
-        return -rhf * us * us * vv / U;
-    }
-    if (k >= g.nz || !visc) return 0.f;
-    float me = 0.25f * (fval(g, mu, i, j - 1, k - 1) + fval(g, mu, i, j, k - 1) + fval(g, mu, i, j - 1, k) + fval(g, mu, i, j, k));
-    return -2.f * me * S23f(g, mb, v, i, j, k);
+__device__ float most23f(const Geo &g, const MxBase &mb, const Phys &ph, const VelF &v, const float *dr,
+                         const float *thp, int i, int j) {
+    if (ph.surface != 1) return 0.f;
+    float u = 0.25f * (fval(g, v.ux, i, j - 1, 0) + fval(g, v.ux, i + 1, j - 1, 0) + fval(g, v.ux, i, j, 0) + fval(g, v.ux, i + 1, j, 0));
+    float vv = fval(g, v.vy, i, j, 0);
+    float U = sqrtf(u * u + vv * vv);
+    if (!(U > 0.f)) return 0.f;
+    float thf = mb.th0f[0] + 0.5f * (fval(g, thp, i, j - 1, 0) + fval(g, thp, i, j, 0));
+    float rhf = mb.rho0f[0] + 0.5f * (fval(g, dr, i, j - 1, 0) + fval(g, dr, i, j, 0));
+    float us = ustar_f(U, 0.5f * mb.dzf[0], mb.z0, mb.Qs, thf, mb.grav);
+    return -rhf * us * us * vv / U;
 }
 
 // Subgrid stress divergence with each edge strain and stress evaluated once (as in the FP64
-// path): edge strains, eddy viscosity, edge stresses in place (MOST at the bottom), then one kernel
-// differences them into R_U, R_V, R_W and adds the heat-flux divergence to R_Theta.
+// path): edge strains; eddy viscosity and diagonal stresses at cells; edge stresses in place (MOST
+// at the bottom); then one kernel differences them into R_U, R_V, R_W and adds the heat-flux
+// divergence to R_Theta.  Every neighbour is a precomputed periodic offset.
+// Strains at xy-edges (i-1/2, j-1/2, k) and at xz-/yz-edges on w-face k (zero on both walls).
 __global__ void k_mx_sgs_edges(Geo g, MxBase mb, VelF v, float *e12, float *e13, float *e23) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
-    const long long n = ((long long)k * g.ny + j) * g.nx + i;
-    if (k < g.nz) e12[n] = S12f(g, mb, v, i, j, k);
-    e13[n] = S13f(g, mb, v, i, j, k);
-    e23[n] = S23f(g, mb, v, i, j, k);
+    const long long n = ((long long)k * g.ny + j) * g.nx + i, nxy = g.nxy;
+    const NbrOff o = nbr_off(g, i, j);
+    if (k < g.nz)
+        e12[n] = 0.5f * ((__ldg(v.ux + n) - __ldg(v.ux + n + o.ym)) * mb.rdy + (__ldg(v.vy + n) - __ldg(v.vy + n + o.xm)) * mb.rdx);
+    if (k == 0 || k >= g.nz) {
+        e13[n] = 0.f;
+        e23[n] = 0.f;
+        return;
+    }
+    const float rdzc = mb.rdzcf[k], wc = __ldg(v.wz + n);
+    e13[n] = 0.5f * ((__ldg(v.ux + n) - __ldg(v.ux + n - nxy)) * rdzc + (wc - __ldg(v.wz + n + o.xm)) * mb.rdx);
+    e23[n] = 0.5f * ((__ldg(v.vy + n) - __ldg(v.vy + n - nxy)) * rdzc + (wc - __ldg(v.wz + n + o.ym)) * mb.rdy);
 }
 __global__ void k_mx_sgs_tau(Geo g, MxBase mb, Phys ph, VelF v, const float *mu, const float *dr, const float *thp,
                              int visc, float *t12, float *t13, float *t23) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
-    const long long n = ((long long)k * g.ny + j) * g.nx + i;
+    const long long n = ((long long)k * g.ny + j) * g.nx + i, nxy = g.nxy;
+    const NbrOff o = nbr_off(g, i, j);
     if (k < g.nz) {
-        float me = 0.25f * (fval(g, mu, i - 1, j - 1, k) + fval(g, mu, i, j - 1, k) + fval(g, mu, i - 1, j, k) + fval(g, mu, i, j, k));
+        float me = 0.25f * (__ldg(mu + n + o.xm + o.ym) + __ldg(mu + n + o.ym) + __ldg(mu + n + o.xm) + __ldg(mu + n));
         t12[n] = visc ? -2.f * me * t12[n] : 0.f;
     }
     if (k == 0) {
-        t13[n] = tau13f(g, mb, ph, v, mu, dr, thp, i, j, 0, visc);
-        t23[n] = tau23f(g, mb, ph, v, mu, dr, thp, i, j, 0, visc);
+        t13[n] = most13f(g, mb, ph, v, dr, thp, i, j);
+        t23[n] = most23f(g, mb, ph, v, dr, thp, i, j);
     } else if (k >= g.nz || !visc) {
         t13[n] = 0.f;
         t23[n] = 0.f;
     } else {
-        float mx = 0.25f * (fval(g, mu, i - 1, j, k - 1) + fval(g, mu, i, j, k - 1) + fval(g, mu, i - 1, j, k) + fval(g, mu, i, j, k));
-        float my = 0.25f * (fval(g, mu, i, j - 1, k - 1) + fval(g, mu, i, j, k - 1) + fval(g, mu, i, j - 1, k) + fval(g, mu, i, j, k));
+        const long long b = n - nxy;
+        float mx = 0.25f * (__ldg(mu + b + o.xm) + __ldg(mu + b) + __ldg(mu + n + o.xm) + __ldg(mu + n));
+        float my = 0.25f * (__ldg(mu + b + o.ym) + __ldg(mu + b) + __ldg(mu + n + o.ym) + __ldg(mu + n));
         t13[n] = -2.f * mx * t13[n];
         t23[n] = -2.f * my * t23[n];
     }
 }
-__global__ void k_mx_sgs_div(Geo g, MxBase mb, Phys ph, VelF v, const float *mu, const float *dr, const float *thp,
-                             int visc, const float *t12, const float *t13, const float *t23, F5f R) {
+__global__ void k_mx_sgs_div(Geo g, MxBase mb, Phys ph, const float *mu, const float *tD, const float *dr,
+                             const float *thp, int visc, const float *t12, const float *t13, const float *t23, F5f R) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
     const long long n = ((long long)k * g.ny + j) * g.nx + i;
-    const long long nxy = g.nxy;
+    const long long nxy = g.nxy, nc = g.nc;
+    const NbrOff o = nbr_off(g, i, j);
     const float rdx = mb.rdx, rdy = mb.rdy;
     if (k < g.nz) {
         const float rH = mb.rdzf[k], rPr = mb.rPr;
         float du = 0.f, dv = 0.f, hd = 0.f;
         if (visc) {
-            du = (tauDf(g, mb, v, mu, i, j, k, 0) - tauDf(g, mb, v, mu, i - 1, j, k, 0)) * rdx
-               + (__ldg(t12 + cixw(g, i, j + 1, k)) - __ldg(t12 + n)) * rdy;
-            dv = (__ldg(t12 + cixw(g, i + 1, j, k)) - __ldg(t12 + n)) * rdx
-               + (tauDf(g, mb, v, mu, i, j, k, 1) - tauDf(g, mb, v, mu, i, j - 1, k, 1)) * rdy;
-            float tc = thp[n], mc = mu[n];
-            float hxm = 0.5f * (fval(g, mu, i - 1, j, k) + mc) * rPr * (tc - fval(g, thp, i - 1, j, k)) * rdx;
-            float hxp = 0.5f * (mc + fval(g, mu, i + 1, j, k)) * rPr * (fval(g, thp, i + 1, j, k) - tc) * rdx;
-            float hym = 0.5f * (fval(g, mu, i, j - 1, k) + mc) * rPr * (tc - fval(g, thp, i, j - 1, k)) * rdy;
-            float hyp = 0.5f * (mc + fval(g, mu, i, j + 1, k)) * rPr * (fval(g, thp, i, j + 1, k) - tc) * rdy;
+            du = (__ldg(tD + n) - __ldg(tD + n + o.xm)) * rdx + (__ldg(t12 + n + o.yp) - __ldg(t12 + n)) * rdy;
+            dv = (__ldg(t12 + n + o.xp) - __ldg(t12 + n)) * rdx + (__ldg(tD + nc + n) - __ldg(tD + nc + n + o.ym)) * rdy;
+            const float tc = __ldg(thp + n), mc = __ldg(mu + n);
+            float hxm = 0.5f * (__ldg(mu + n + o.xm) + mc) * rPr * (tc - __ldg(thp + n + o.xm)) * rdx;
+            float hxp = 0.5f * (mc + __ldg(mu + n + o.xp)) * rPr * (__ldg(thp + n + o.xp) - tc) * rdx;
+            float hym = 0.5f * (__ldg(mu + n + o.ym) + mc) * rPr * (tc - __ldg(thp + n + o.ym)) * rdy;
+            float hyp = 0.5f * (mc + __ldg(mu + n + o.yp)) * rPr * (__ldg(thp + n + o.yp) - tc) * rdy;
             hd = (hxp - hxm) * rdx + (hyp - hym) * rdy;
         }
         du += (__ldg(t13 + n + nxy) - __ldg(t13 + n)) * rH;
         dv += (__ldg(t23 + n + nxy) - __ldg(t23 + n)) * rH;
-        auto hz = [&](int kf) -> float {
-            if (kf == 0) return ph.surface == 1 ? -(mb.rho0f[0] + dr[cix(g, i, j, 0)]) * mb.Qs : 0.f;
+        // vertical heat flux at the cell's bottom (kf = k) and top (kf = k + 1) faces: the MOST
+        // flux at the ground, none at the lid
+        auto hz = [&](int kf, long long cf) -> float {
+            if (kf == 0) return ph.surface == 1 ? -(mb.rho0f[0] + __ldg(dr + cf)) * mb.Qs : 0.f;
             if (kf >= g.nz || !visc) return 0.f;
-            float dth = dth0(mb, kf, kf - 1) + (fval(g, thp, i, j, kf) - fval(g, thp, i, j, kf - 1));
-            return 0.5f * (fval(g, mu, i, j, kf - 1) + fval(g, mu, i, j, kf)) * rPr * dth * mb.rdzcf[kf];
+            float dth = dth0(mb, kf, kf - 1) + (__ldg(thp + cf) - __ldg(thp + cf - nxy));
+            return 0.5f * (__ldg(mu + cf - nxy) + __ldg(mu + cf)) * rPr * dth * mb.rdzcf[kf];
         };
-        hd += (hz(k + 1) - hz(k)) * rH;
+        hd += (hz(k + 1, n + nxy) - hz(k, n)) * rH;
         R.u[n] -= du;
         R.v[n] -= dv;
         R.t[n] += hd;
     }
     if (visc && k >= 1 && k < g.nz) {
-        float dw = (__ldg(t13 + cixw(g, i + 1, j, k)) - __ldg(t13 + n)) * rdx
-                 + (__ldg(t23 + cixw(g, i, j + 1, k)) - __ldg(t23 + n)) * rdy
-                 + (tauDf(g, mb, v, mu, i, j, k, 2) - tauDf(g, mb, v, mu, i, j, k - 1, 2)) * mb.rdzcf[k];
+        float dw = (__ldg(t13 + n + o.xp) - __ldg(t13 + n)) * rdx + (__ldg(t23 + n + o.yp) - __ldg(t23 + n)) * rdy
+                 + (__ldg(tD + 2 * nc + n) - __ldg(tD + 2 * nc + n - nxy)) * mb.rdzcf[k];
         R.w[n] -= dw;
     }
 }
 
-// learned closure: cell-centre planes of rho t_ij / rho h_j (order 11 22 33 12 13 23 h1 h2 h3),
-// interpolated to edges (4-point) and faces (2-point) like the Smagorinsky stresses
-__device__ __forceinline__ float tl(const Geo &g, const float *tau, int q, int i, int j, int k) {
-    return __ldg(tau + (long long)q * g.nc + cixw(g, i, j, k));
-}
-__device__ __forceinline__ float tl12e(const Geo &g, const float *tau, int i, int j, int k) {
-    return 0.25f * (tl(g, tau, 3, i - 1, j - 1, k) + tl(g, tau, 3, i, j - 1, k) + tl(g, tau, 3, i - 1, j, k) + tl(g, tau, 3, i, j, k));
-}
-// q = 4 (t13, xz-edge at x-face i) or 5 (t23, yz-edge at y-face j), interior w-face k
-__device__ __forceinline__ float tlze(const Geo &g, const float *tau, int q, int di, int dj, int i, int j, int k) {
-    return 0.25f * (tl(g, tau, q, i - di, j - dj, k - 1) + tl(g, tau, q, i, j, k - 1) + tl(g, tau, q, i - di, j - dj, k) + tl(g, tau, q, i, j, k));
-}
-
-// Learned-closure stress divergence, each edge value once: the cell-centre planes of the network
-// are averaged to xy-, xz- and yz-edges (MOST stress at the bottom, zero at the top), then one
-// kernel differences them (and the heat flux at faces) into R_U, R_V, R_W and R_Theta.
-__global__ void k_mx_cl_edges(Geo g, MxBase mb, Phys ph, VelF v, const float *mu, const float *dr, const float *thp,
+// Learned-closure stress divergence, each edge value once.  The network's cell-centre planes of
+// rho t_ij / rho h_j (order 11 22 33 12 13 23 h1 h2 h3, nc floats each) are averaged to xy-, xz-
+// and yz-edges by 4-point means (the MOST stress at the ground, zero at the lid), as the
+// Smagorinsky stresses are; one kernel then differences them, with the heat flux averaged to
+// faces, into R_U, R_V, R_W and R_Theta.
+__global__ void k_mx_cl_edges(Geo g, MxBase mb, Phys ph, VelF v, const float *dr, const float *thp,
                               const float *tau, float *t12, float *t13, float *t23) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
-    const long long n = ((long long)k * g.ny + j) * g.nx + i;
-    if (k < g.nz) t12[n] = tl12e(g, tau, i, j, k);
+    const long long n = ((long long)k * g.ny + j) * g.nx + i, nxy = g.nxy, nc = g.nc;
+    const NbrOff o = nbr_off(g, i, j);
+    if (k < g.nz) {
+        const float *q = tau + 3 * nc;
+        t12[n] = 0.25f * (__ldg(q + n + o.xm + o.ym) + __ldg(q + n + o.ym) + __ldg(q + n + o.xm) + __ldg(q + n));
+    }
     if (k == 0) {
-        t13[n] = tau13f(g, mb, ph, v, mu, dr, thp, i, j, 0, 0);
-        t23[n] = tau23f(g, mb, ph, v, mu, dr, thp, i, j, 0, 0);
+        t13[n] = most13f(g, mb, ph, v, dr, thp, i, j);
+        t23[n] = most23f(g, mb, ph, v, dr, thp, i, j);
     } else if (k >= g.nz) {
         t13[n] = 0.f;
         t23[n] = 0.f;
     } else {
-        t13[n] = tlze(g, tau, 4, 1, 0, i, j, k);
-        t23[n] = tlze(g, tau, 5, 0, 1, i, j, k);
+        const long long b = n - nxy;
+        const float *q = tau + 4 * nc;
+        t13[n] = 0.25f * (__ldg(q + b + o.xm) + __ldg(q + b) + __ldg(q + n + o.xm) + __ldg(q + n));
+        q = tau + 5 * nc;
+        t23[n] = 0.25f * (__ldg(q + b + o.ym) + __ldg(q + b) + __ldg(q + n + o.ym) + __ldg(q + n));
     }
 }
 __global__ void k_mx_cl_div(Geo g, MxBase mb, Phys ph, const float *dr, const float *tau, const float *t12,
@@ -394,29 +381,31 @@ __global__ void k_mx_cl_div(Geo g, MxBase mb, Phys ph, const float *dr, const fl
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
     const long long n = ((long long)k * g.ny + j) * g.nx + i;
-    const long long nxy = g.nxy;
+    const long long nxy = g.nxy, nc = g.nc;
+    const NbrOff o = nbr_off(g, i, j);
     const float rdx = mb.rdx, rdy = mb.rdy;
     if (k < g.nz) {
         const float rH = mb.rdzf[k];
-        float du = (tl(g, tau, 0, i, j, k) - tl(g, tau, 0, i - 1, j, k)) * rdx
-                 + (__ldg(t12 + cixw(g, i, j + 1, k)) - __ldg(t12 + n)) * rdy + (__ldg(t13 + n + nxy) - __ldg(t13 + n)) * rH;
-        float dv = (__ldg(t12 + cixw(g, i + 1, j, k)) - __ldg(t12 + n)) * rdx
-                 + (tl(g, tau, 1, i, j, k) - tl(g, tau, 1, i, j - 1, k)) * rdy + (__ldg(t23 + n + nxy) - __ldg(t23 + n)) * rH;
-        float qxm = 0.5f * (tl(g, tau, 6, i - 1, j, k) + tl(g, tau, 6, i, j, k));
-        float qxp = 0.5f * (tl(g, tau, 6, i, j, k) + tl(g, tau, 6, i + 1, j, k));
-        float qym = 0.5f * (tl(g, tau, 7, i, j - 1, k) + tl(g, tau, 7, i, j, k));
-        float qyp = 0.5f * (tl(g, tau, 7, i, j, k) + tl(g, tau, 7, i, j + 1, k));
-        float qzm = k == 0 ? (ph.surface == 1 ? (mb.rho0f[0] + dr[n]) * mb.Qs : 0.f)
-                           : 0.5f * (tl(g, tau, 8, i, j, k - 1) + tl(g, tau, 8, i, j, k));
-        float qzp = k == g.nz - 1 ? 0.f : 0.5f * (tl(g, tau, 8, i, j, k) + tl(g, tau, 8, i, j, k + 1));
+        const float *t11 = tau, *t22 = tau + nc, *h1 = tau + 6 * nc, *h2 = tau + 7 * nc, *h3 = tau + 8 * nc;
+        float du = (__ldg(t11 + n) - __ldg(t11 + n + o.xm)) * rdx
+                 + (__ldg(t12 + n + o.yp) - __ldg(t12 + n)) * rdy + (__ldg(t13 + n + nxy) - __ldg(t13 + n)) * rH;
+        float dv = (__ldg(t12 + n + o.xp) - __ldg(t12 + n)) * rdx
+                 + (__ldg(t22 + n) - __ldg(t22 + n + o.ym)) * rdy + (__ldg(t23 + n + nxy) - __ldg(t23 + n)) * rH;
+        const float hx = __ldg(h1 + n), hy = __ldg(h2 + n), hz = __ldg(h3 + n);
+        float qxm = 0.5f * (__ldg(h1 + n + o.xm) + hx);
+        float qxp = 0.5f * (hx + __ldg(h1 + n + o.xp));
+        float qym = 0.5f * (__ldg(h2 + n + o.ym) + hy);
+        float qyp = 0.5f * (hy + __ldg(h2 + n + o.yp));
+        float qzm = k == 0 ? (ph.surface == 1 ? (mb.rho0f[0] + dr[n]) * mb.Qs : 0.f) : 0.5f * (__ldg(h3 + n - nxy) + hz);
+        float qzp = k == g.nz - 1 ? 0.f : 0.5f * (hz + __ldg(h3 + n + nxy));
         R.u[n] -= du;
         R.v[n] -= dv;
         R.t[n] -= (qxp - qxm) * rdx + (qyp - qym) * rdy + (qzp - qzm) * rH;
     }
     if (k >= 1 && k < g.nz) {
-        float dw = (__ldg(t13 + cixw(g, i + 1, j, k)) - __ldg(t13 + n)) * rdx
-                 + (__ldg(t23 + cixw(g, i, j + 1, k)) - __ldg(t23 + n)) * rdy
-                 + (tl(g, tau, 2, i, j, k) - tl(g, tau, 2, i, j, k - 1)) * mb.rdzcf[k];
+        const float *t33 = tau + 2 * nc;
+        float dw = (__ldg(t13 + n + o.xp) - __ldg(t13 + n)) * rdx + (__ldg(t23 + n + o.yp) - __ldg(t23 + n)) * rdy
+                 + (__ldg(t33 + n) - __ldg(t33 + n - nxy)) * mb.rdzcf[k];
         R.w[n] -= dw;
     }
 }
@@ -1213,7 +1202,7 @@ void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const 
     mx_launch("mx_rhs_w", s, [&] { k_mx_rhs_w<<<gw, MBX, 0, s>>>(g, mb, st, pp, fl, R.w); });
     if (tau) {
         VelF v{ux, vy, wz};
-        mx_launch("mx_cl_edges", s, [&] { k_mx_cl_edges<<<gw, MBX, 0, s>>>(g, mb, ph, v, mu, st.r, thp, tau, ax, ay, az); });
+        mx_launch("mx_cl_edges", s, [&] { k_mx_cl_edges<<<gw, MBX, 0, s>>>(g, mb, ph, v, st.r, thp, tau, ax, ay, az); });
         mx_launch("mx_cl_div", s, [&] { k_mx_cl_div<<<gw, MBX, 0, s>>>(g, mb, ph, st.r, tau, ax, ay, az, R); });
     }
     if (sgs) {
@@ -1221,10 +1210,14 @@ void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const 
         VelF v{ux, vy, wz};
         if (visc) {
             mx_launch("mx_sgs_edges", s, [&] { k_mx_sgs_edges<<<gw, MBX, 0, s>>>(g, mb, v, ax, ay, az); });
-            mx_launch("mx_sgs_mu", s, [&] { k_mx_sgs_mu<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, v, st.r, ax, ay, az, mu); });
+            mx_launch("mx_sgs_mu", s, [&] {
+                k_mx_sgs_mu<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, ph, v, st.r, ax, ay, az, mu, mu + g.nc);
+            });
         }
         mx_launch("mx_sgs_tau", s, [&] { k_mx_sgs_tau<<<gw, MBX, 0, s>>>(g, mb, ph, v, mu, st.r, thp, visc, ax, ay, az); });
-        mx_launch("mx_sgs_div", s, [&] { k_mx_sgs_div<<<gw, MBX, 0, s>>>(g, mb, ph, v, mu, st.r, thp, visc, ax, ay, az, R); });
+        mx_launch("mx_sgs_div", s, [&] {
+            k_mx_sgs_div<<<gw, MBX, 0, s>>>(g, mb, ph, mu, mu + g.nc, st.r, thp, visc, ax, ay, az, R);
+        });
     }
 }
 void mx_slow_prep_only(const Geo &g, const MxBase &mb, CF5f st, float *ux, float *vy, float *wz, float *mfx,
