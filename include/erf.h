@@ -256,6 +256,15 @@ erf_status erf_get_option(erf_handle *h, int32_t option, int64_t *value);
  * device word owned by the caller; the context stays usable.  Synchronises cuda_stream. */
 erf_status erf_selftest_wait_timeout(int32_t max_polls, unsigned *d_flag, void *cuda_stream, int32_t *timed_out);
 
+/* Self-test of the tensor-core (tcgen05) path used by the learned closure: one CTA runs MMAs of
+ * the network's operand shapes (M = 128; K = 64 with N = 64 and N = 16; K = 16 with N = 64) on
+ * exact small-integer BF16 data through the same shared-memory layouts and descriptors, reads
+ * the TMEM accumulators back and compares every output with integer loops.  d_words is two
+ * int32 device words owned by the caller (scratch).  *mismatches = outputs that differ (0 when
+ * the path is correct); *timed_out = 1 if the bounded wait on the MMAs gave up.  Synchronises
+ * cuda_stream. */
+erf_status erf_selftest_tensor_cores(int32_t *d_words, void *cuda_stream, int32_t *mismatches, int32_t *timed_out);
+
 /* Message of the last failed call on h (or of the last failed erf_init_grid if h is NULL). */
 const char *erf_last_error(const erf_handle *h);
 

@@ -819,6 +819,23 @@ extern "C" erf_status erf_selftest_wait_timeout(int32_t max_polls, unsigned *d_f
     *timed_out = f ? 1 : 0;
     return ERF_OK;
 }
+extern "C" erf_status erf_selftest_tensor_cores(int32_t *d_words, void *cuda_stream, int32_t *mismatches,
+                                                 int32_t *timed_out) {
+    if (!d_words || !mismatches || !timed_out) return fail(nullptr, ERF_EINVAL, "bad self-test arguments");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaMemsetAsync(d_words, 0, 2 * sizeof(int32_t), s);
+    if (e == cudaSuccess) {
+        selftest_tensor_cores(d_words, reinterpret_cast<unsigned *>(d_words + 1), s);
+        e = cudaGetLastError();
+    }
+    int32_t w[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w, d_words, sizeof(w), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "tensor-core self-test");
+    *mismatches = w[0];
+    *timed_out = w[1] ? 1 : 0;
+    return ERF_OK;
+}
 extern "C" erf_status erf_get_option(erf_handle *h, int32_t option, int64_t *value) {
     if (!h || !value) return fail(h, ERF_EINVAL, "NULL argument");
     if (option != ERF_OPT_TMA_STENCILS) return fail(h, ERF_EINVAL, "unknown option");
@@ -873,7 +890,7 @@ extern "C" erf_status erf_closure_fields(erf_handle *h, float *d_out9, uint32_t 
     mx_current_fields(h, s);
     cudaMemsetAsync(h->cl_nfb, 0, sizeof(unsigned), s);
     cl_infer(h->geo, h->mb, h->ph, h->cl_w, h->cl_b, h->cl_stats, h->mux, h->mvy, h->mwz, h->mthp, h->mst.r, d_out9,
-             h->cl_nfb, s);
+             h->cl_nfb, h->kerr, s);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && n_fallback) {
         e = cudaMemcpyAsync(n_fallback, h->cl_nfb, sizeof(unsigned), cudaMemcpyDeviceToHost, s);

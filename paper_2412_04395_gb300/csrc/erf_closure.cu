@@ -2,15 +2,14 @@
 // 4x box filter that makes training targets, and the weight upload.
 //
 // Inference maps each cell's 12 features (resolved velocity gradients, dtheta/dx, dtheta/dy, N^2)
-// through 12 -> 64 -> 64 -> 64 -> 9 (SiLU) to the kinematic SGS stress and heat flux.  A warp
-// takes 32 cells (one per lane for the features and the store), as two 16-row tiles: the
-// 16 x 16 feature tiles (12 + 4 zero columns) and every hidden activation tile live in BF16
-// mma.sync fragments (m16n8k16, FP32 accumulate); the accumulator fragments of two adjacent
-// n-tiles are exactly the A fragment of the next k-tile, so activations never leave registers
-// between layers, and each B fragment loaded from shared memory feeds both tiles.  Weights sit
-// in shared memory in [out][in] row-major BF16 (the "col" B-fragment order of the instruction),
-// rows padded to 24 / 72 elements so that the eight rows one B load touches fall in distinct
-// banks.
+// through 12 -> 64 -> 64 -> 64 -> 9 (SiLU) to the kinematic SGS stress and heat flux on the
+// fifth-generation tensor cores (tcgen05).  A CTA of 128 threads takes 128-cell tiles, one cell
+// per thread: the thread writes its cell's standardised features (BF16) as row t of the
+// activation operand in shared memory; one elected thread issues each layer as M = 128 x N = 64
+// (output layer N = 16) MMAs with K = 16 steps into a TMEM accumulator; every thread then reads
+// its own row back (TMEM lane t), adds the bias, applies SiLU and writes the BF16 activations
+// as the next layer's operand.  The weights stay in shared memory for the CTA's lifetime, and
+// each layer's completion is an mbarrier that the MMAs' commit arrives on (bounded waits).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -21,6 +20,7 @@
 #include "erf_dev.cuh"
 #include "erf_launch.h"
 #include "erf_mixed.h"
+#include "erf_tc.cuh"
 
 namespace erfk {
 
@@ -33,7 +33,6 @@ struct ClDev {
     const float *b;            // b1[64] b2[64] b3[64] b4[16]
     const float *stats;        // in_mean[12] in_std[12] out_mean[9] out_std[9]
 };
-constexpr int CL_B_F32 = 64 * 3 + 16;
 
 __global__ void k_cl_prepare(const float *blob, __nv_bfloat16 *w, float *b, float *stats) {
     const float *st = blob;                 // 42 stats
@@ -95,74 +94,106 @@ __device__ __forceinline__ unsigned pack_bf16(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);   // .x = a (low half), .y = b
     return *reinterpret_cast<unsigned *>(&h);
 }
-__device__ __forceinline__ void mma16816(float *d, const unsigned *a, unsigned b0, unsigned b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-// SiLU x sigma(x) = h (1 + tanh h), h = x/2: one MUFU operation (tanh.approx.f32, relative error
-// about 2^-11) instead of an exponential and a reciprocal.  The activation is rounded to BF16
-// (2^-9) right after, and the inference error against a BF16-emulating FP64 network stays at
-// 2e-5 .. 2e-4 relative L2 (measured; the test bound is 5e-3).
-__device__ __forceinline__ float silu_dev(float x) {
-    float h = 0.5f * x, t;
+// SiLU of x = acc + b as h (1 + tanh h), h = x/2 = fma(acc, 1/2, b/2) (hb = b/2): one MUFU
+// operation (tanh.approx.f32, relative error about 2^-11) instead of an exponential and a
+// reciprocal.  The activation is rounded to BF16 (2^-9) right after, and the inference error
+// against a BF16-emulating FP64 network stays at 2e-5 .. 2e-4 relative L2 (measured; the test
+// bound is 5e-3).
+__device__ __forceinline__ float silu_half(float acc, float hb) {
+    float h = fmaf(acc, 0.5f, hb), t;
     asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
     return fmaf(h, t, h);
 }
 
 // Learned SGS stress/heat flux at every cell (mixed path), with Smagorinsky as the per-cell
-// fallback and backscatter limited to half the Smagorinsky transfer.  Persistent blocks of 4 warps load
-// the weights into shared memory once and then take 32-cell tiles in turn; each warp runs its
-// tile as two m16 tiles through every layer, reusing each B fragment for both.  The bias is the
-// accumulator's initial value.
+// fallback and backscatter limited to half the Smagorinsky transfer.  Persistent CTAs of 128
+// threads load the weights once into the canonical K-major operand layout, allocate 64 TMEM
+// columns and loop over 128-cell tiles.  Every wait on the MMA barrier is bounded: a CTA whose
+// wait gives up sets bit 2 of *err, waits once more (bounded) for its MMAs, frees its TMEM and
+// stops.
 // out: 9 planes of nc floats: rho t11, rho t22, rho t33, rho t12, rho t13, rho t23, rho h1..h3.
-constexpr int CLW = 4;
-constexpr int LD1 = 24, LDH = 72;   // padded shared-memory row lengths (bank-conflict-free B loads)
-constexpr int SW_W1 = 0, SW_W2 = 64 * LD1, SW_W3 = SW_W2 + 64 * LDH, SW_W4 = SW_W3 + 64 * LDH;
-constexpr int SW_TOTAL = SW_W4 + 16 * LDH;
-__global__ void __launch_bounds__(CLW * 32, 4) k_cl_infer(Geo g, MxBase mb, Phys ph, ClDev cl, VelIn v,
-                                                       const float *dr, float *out, unsigned *nfallback) {
-    __shared__ __align__(16) __nv_bfloat16 sW[SW_TOTAL];
-    __shared__ float sb[CL_B_F32];
-    __shared__ float sst[2 * CL_NIN + 2 * CL_NOUT];   // in_mean, 1/in_std, out_mean, out_std
-    __shared__ __align__(16) float sF[CLW][32][17];   // standardised features, then outputs
-    __shared__ float sMisc[CLW][32][19];              // fallback stresses/fluxes, rho, flag, S_ij, bound
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int q = tid; q < 64 * 16; q += blockDim.x) sW[SW_W1 + (q / 16) * LD1 + q % 16] = cl.W1[q];
-    for (int q = tid; q < 64 * 64; q += blockDim.x) {
-        sW[SW_W2 + (q / 64) * LDH + q % 64] = cl.W2[q];
-        sW[SW_W3 + (q / 64) * LDH + q % 64] = cl.W3[q];
+constexpr int CLT = 128;            // threads per CTA = cells per tile = MMA rows
+constexpr uint32_t CL_TCOLS = 64;   // TMEM columns per CTA (FP32 accumulators)
+constexpr int CL_CTAS_PER_SM = 4;
+__global__ void __launch_bounds__(CLT, CL_CTAS_PER_SM) k_cl_infer(Geo g, MxBase mb, Phys ph, ClDev cl, VelIn v,
+                                                                  const float *dr, float *out, unsigned *nfallback,
+                                                                  unsigned *err) {
+    __shared__ __align__(1024) unsigned char sA[128 * 64 * 2];   // activations [128 cells][64], K-major
+    __shared__ __align__(1024) unsigned char sW1[64 * 16 * 2];   // [64 out][16 in] (12 used)
+    __shared__ __align__(1024) unsigned char sW2[64 * 64 * 2];
+    __shared__ __align__(1024) unsigned char sW3[64 * 64 * 2];
+    __shared__ __align__(1024) unsigned char sW4[16 * 64 * 2];   // [16 out (9 used)][64 in]
+    __shared__ float shb[3 * 64];                               // half biases of the hidden layers
+    __shared__ float sb4[16];
+    __shared__ float sst[2 * CL_NIN + 2 * CL_NOUT];             // in_mean, 1/in_std, out_mean, out_std
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_taddr;
+    const int t = threadIdx.x, warp = t >> 5;
+    auto put = [&](unsigned char *dst, const __nv_bfloat16 *src, int rows, int K) {
+        for (int q = t; q < rows * K; q += CLT) *reinterpret_cast<__nv_bfloat16 *>(dst + tc_off(q / K, q % K, K)) = src[q];
+    };
+    put(sW1, cl.W1, 64, 16);
+    put(sW2, cl.W2, 64, 64);
+    put(sW3, cl.W3, 64, 64);
+    put(sW4, cl.W4, 16, 64);
+    for (int q = t; q < 192; q += CLT) shb[q] = 0.5f * cl.b[q];
+    if (t < 16) sb4[t] = cl.b[192 + t];
+    if (t < 2 * CL_NIN + 2 * CL_NOUT) sst[t] = (t >= CL_NIN && t < 2 * CL_NIN) ? 1.f / cl.stats[t] : cl.stats[t];
+    if (t == 0) mbar_init(&bar, 1);
+    if (warp == 0) {
+        tc_alloc(&s_taddr, CL_TCOLS);
+        tc_relinquish();
     }
-    for (int q = tid; q < 16 * 64; q += blockDim.x) sW[SW_W4 + (q / 64) * LDH + q % 64] = cl.W4[q];
-    for (int q = tid; q < CL_B_F32; q += blockDim.x) sb[q] = cl.b[q];
-    for (int q = tid; q < 2 * CL_NIN + 2 * CL_NOUT; q += blockDim.x)
-        sst[q] = (q >= CL_NIN && q < 2 * CL_NIN) ? 1.f / cl.stats[q] : cl.stats[q];
+    fence_async_smem();
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
+    const uint32_t tm = s_taddr, tlane = tm + ((uint32_t)(32 * warp) << 16);   // this warp's 32 TMEM lanes
+    const uint64_t dA = tc_smem_desc(smem_u32(sA), 128, 1024);
+    const uint64_t dW1 = tc_smem_desc(smem_u32(sW1), 128, 256), dW2 = tc_smem_desc(smem_u32(sW2), 128, 1024);
+    const uint64_t dW3 = tc_smem_desc(smem_u32(sW3), 128, 1024), dW4 = tc_smem_desc(smem_u32(sW4), 128, 1024);
+    constexpr uint32_t I64 = tc_idesc_bf16(128, 64), I16 = tc_idesc_bf16(128, 16);
     const float *in_mu = sst, *in_rsd = sst + 12, *out_mu = sst + 24, *out_sd = sst + 33;
     const float rPr = mb.rPr;
-    const int gr = lane >> 2, tc = lane & 3;   // fragment coordinates: row, column pair
-    const long long ntiles = (g.nc + 31) / 32;
-    for (long long tile = (long long)blockIdx.x * CLW + warp; tile < ntiles; tile += (long long)gridDim.x * CLW) {
-        const long long c0 = tile * 32;
-        // 1. features of 32 cells (one per lane), standardised; fallback flag on |z| > 6
+    unsigned char *row = sA + (t >> 3) * 1024 + (t & 7) * 16;   // row t, core-matrix column 0
+    unsigned phase = 0, pend = 0;
+    int timeout = 0;
+    // all threads: this layer's operand is written and the previous TMEM reads are done
+    auto sync_layer = [&]() -> int {
+        fence_async_smem();
+        tc_fence_before();
+        int ab = __syncthreads_or(timeout);
+        tc_fence_after();
+        return ab;
+    };
+    auto wait_mma = [&]() {
+        pend = phase;
+        if (!mbar_wait_bounded(&bar, phase, TMA_MAX_POLLS)) timeout = 1;
+        phase ^= 1u;
+        tc_fence_after();
+    };
+    const long long ntiles = (g.nc + CLT - 1) / CLT;
+    int aborted = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long c = tile * CLT + t;
+        const bool valid = c < g.nc;
+        // 1. features (standardised, BF16) into row t; fallback stresses and S_ij in registers
+        float m[18];
+        int fb = 0;
         {
-            long long c = c0 + lane;
-            float *m = sMisc[warp][lane];
-            int fb = 0;
-            if (c < g.nc) {
-                unsigned row = (unsigned)(c / g.nx);
-                int i = (int)(c - (long long)row * g.nx);
-                int j = (int)(row % (unsigned)g.ny), k = (int)(row / (unsigned)g.ny);
+            float z[12];
+            for (int q = 0; q < 12; ++q) z[q] = 0.f;
+            m[9] = 0.f;
+            if (valid) {
+                unsigned rw = (unsigned)(c / g.nx);
+                int i = (int)(c - (long long)rw * g.nx);
+                int j = (int)(rw % (unsigned)g.ny), k = (int)(rw / (unsigned)g.ny);
                 float f[12], dthdz;
                 cl_features(g, mb, v, i, j, k, f, dthdz);
                 for (int q = 0; q < 12; ++q) {
-                    float z = (f[q] - in_mu[q]) * in_rsd[q];
-                    if (!(fabsf(z) <= 6.f)) fb = 1;
-                    sF[warp][lane][q] = z;
+                    z[q] = (f[q] - in_mu[q]) * in_rsd[q];
+                    if (!(fabsf(z[q]) <= 6.f)) fb = 1;
                 }
-                // Smagorinsky fallback at the cell centre
                 float s11 = f[0], s22 = f[4], s33 = f[8];
                 float s12 = 0.5f * (f[1] + f[3]), s13 = 0.5f * (f[2] + f[6]), s23 = 0.5f * (f[5] + f[7]);
                 float rho = mb.rho0f[k] + dr[c];
@@ -178,100 +209,160 @@ __global__ void __launch_bounds__(CLW * 32, 4) k_cl_infer(Geo g, MxBase mb, Phys
                 // the Smagorinsky transfer (both density-weighted)
                 float ps = -(m[0] * s11 + m[1] * s22 + m[2] * s33 + 2.f * (m[3] * s12 + m[4] * s13 + m[5] * s23));
                 m[17] = -0.5f * ps;
-            } else {
-                for (int q = 0; q < 12; ++q) sF[warp][lane][q] = 0.f;
-                m[9] = 0.f;
             }
-            for (int q = 12; q < 16; ++q) sF[warp][lane][q] = 0.f;
-            m[10] = (float)fb;
+            *reinterpret_cast<uint4 *>(row) =
+                make_uint4(pack_bf16(z[0], z[1]), pack_bf16(z[2], z[3]), pack_bf16(z[4], z[5]), pack_bf16(z[6], z[7]));
+            *reinterpret_cast<uint4 *>(row + 128) = make_uint4(pack_bf16(z[8], z[9]), pack_bf16(z[10], z[11]), 0u, 0u);
         }
-        __syncwarp();
-        // 2. MLP on tensor cores
-        unsigned a[2][4][4];   // [m-tile][k-tile][reg]
-        for (int mt = 0; mt < 2; ++mt) {
-            const float *r0 = sF[warp][mt * 16 + gr], *r1 = sF[warp][mt * 16 + gr + 8];
-            a[mt][0][0] = pack_bf16(r0[2 * tc], r0[2 * tc + 1]);
-            a[mt][0][1] = pack_bf16(r1[2 * tc], r1[2 * tc + 1]);
-            a[mt][0][2] = pack_bf16(r0[2 * tc + 8], r0[2 * tc + 9]);
-            a[mt][0][3] = pack_bf16(r1[2 * tc + 8], r1[2 * tc + 9]);
-        }
-        auto hidden = [&](int woff, int ldw, int nkt, const float *bias) {
-            float acc[2][8][4];
-            for (int nt = 0; nt < 8; ++nt) {
-                float bl = bias[nt * 8 + 2 * tc], bh = bias[nt * 8 + 2 * tc + 1];
-                for (int mt = 0; mt < 2; ++mt) {
-                    acc[mt][nt][0] = bl; acc[mt][nt][1] = bh; acc[mt][nt][2] = bl; acc[mt][nt][3] = bh;
+        // 2. three hidden layers: MMA into TMEM, then bias + SiLU back into the operand
+        for (int layer = 0; layer < 3 && !aborted; ++layer) {
+            if (sync_layer()) { aborted = 1; break; }
+            if (t == 0) {
+                if (layer == 0) {
+                    tc_mma_bf16(tm, dA, dW1, I64, 0u);
+                } else {
+                    const uint64_t dW = layer == 1 ? dW2 : dW3;
+                    for (int s = 0; s < 4; ++s) tc_mma_bf16(tm, dA + 16u * s, dW + 16u * s, I64, s > 0 ? 1u : 0u);
                 }
-                const __nv_bfloat16 *wr = sW + woff + (nt * 8 + gr) * ldw;
-                for (int kt = 0; kt < nkt; ++kt) {
-                    unsigned b0 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc);
-                    unsigned b1 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc + 8);
-                    mma16816(acc[0][nt], a[0][kt], b0, b1);
-                    mma16816(acc[1][nt], a[1][kt], b0, b1);
-                }
+                tc_commit(&bar);
             }
-            for (int mt = 0; mt < 2; ++mt)
-                for (int kt = 0; kt < 4; ++kt) {
-                    const float *lo = acc[mt][2 * kt], *hi = acc[mt][2 * kt + 1];
-                    a[mt][kt][0] = pack_bf16(silu_dev(lo[0]), silu_dev(lo[1]));
-                    a[mt][kt][1] = pack_bf16(silu_dev(lo[2]), silu_dev(lo[3]));
-                    a[mt][kt][2] = pack_bf16(silu_dev(hi[0]), silu_dev(hi[1]));
-                    a[mt][kt][3] = pack_bf16(silu_dev(hi[2]), silu_dev(hi[3]));
-                }
-        };
-        hidden(SW_W1, LD1, 1, sb);
-        hidden(SW_W2, LDH, 4, sb + 64);
-        hidden(SW_W3, LDH, 4, sb + 128);
-        // output layer: 2 n-tiles of 8 (9 valid columns)
-        float y[2][2][4];
-        for (int nt = 0; nt < 2; ++nt) {
-            float bl = sb[192 + nt * 8 + 2 * tc], bh = sb[192 + nt * 8 + 2 * tc + 1];
-            for (int mt = 0; mt < 2; ++mt) {
-                y[mt][nt][0] = bl; y[mt][nt][1] = bh; y[mt][nt][2] = bl; y[mt][nt][3] = bh;
-            }
-            const __nv_bfloat16 *wr = sW + SW_W4 + (nt * 8 + gr) * LDH;
-            for (int kt = 0; kt < 4; ++kt) {
-                unsigned b0 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc);
-                unsigned b1 = *reinterpret_cast<const unsigned *>(wr + kt * 16 + 2 * tc + 8);
-                mma16816(y[0][nt], a[0][kt], b0, b1);
-                mma16816(y[1][nt], a[1][kt], b0, b1);
+            wait_mma();
+            const float *hb = shb + 64 * layer;
+            for (int h = 0; h < 2; ++h) {
+                uint32_t r[32];
+                tc_ld32(tlane + 32u * h, r);
+                uint32_t pk[16];
+                for (int q = 0; q < 16; ++q)
+                    pk[q] = pack_bf16(silu_half(__uint_as_float(r[2 * q]), hb[32 * h + 2 * q]),
+                                      silu_half(__uint_as_float(r[2 * q + 1]), hb[32 * h + 2 * q + 1]));
+                for (int u = 0; u < 4; ++u)
+                    *reinterpret_cast<uint4 *>(row + (4 * h + u) * 128) =
+                        make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
             }
         }
-        __syncwarp();
-        for (int mt = 0; mt < 2; ++mt)
-            for (int nt = 0; nt < 2; ++nt) {
-                int col = nt * 8 + 2 * tc;
-                float *r0 = sF[warp][mt * 16 + gr], *r1 = sF[warp][mt * 16 + gr + 8];
-                r0[col] = y[mt][nt][0];
-                r0[col + 1] = y[mt][nt][1];
-                r1[col] = y[mt][nt][2];
-                r1[col + 1] = y[mt][nt][3];
-            }
-        __syncwarp();
-        // 3. de-standardise, fallback, density weighting, store (one cell per lane, coalesced)
-        {
-            long long c = c0 + lane;
-            if (c < g.nc) {
-                const float *m = sMisc[warp][lane];
-                int use_fb = m[10] != 0.f;
-                float o[9];
-                for (int q = 0; q < 9; ++q) {
-                    o[q] = sF[warp][lane][q] * out_sd[q] + out_mu[q];
-                    if (!isfinite(o[q])) use_fb = 1;
-                }
-                float rho = m[9];
-                for (int q = 0; q < 9; ++q) o[q] *= rho;
-                float pl = -(o[0] * m[11] + o[1] * m[12] + o[2] * m[13] + 2.f * (o[3] * m[14] + o[4] * m[15] + o[5] * m[16]));
-                if (pl < m[17]) {
-                    float a = m[17] / pl;
-                    for (int q = 0; q < 6; ++q) o[q] *= a;
-                }
-                for (int q = 0; q < 9; ++q) out[(long long)q * g.nc + c] = use_fb ? m[q] : o[q];
-                if (use_fb && nfallback) atomicAdd(nfallback, 1u);
-            }
+        if (aborted || sync_layer()) { aborted = 1; break; }
+        // 3. output layer (N = 16, 9 used), de-standardise, fallback, density weighting, store
+        if (t == 0) {
+            for (int s = 0; s < 4; ++s) tc_mma_bf16(tm, dA + 16u * s, dW4 + 16u * s, I16, s > 0 ? 1u : 0u);
+            tc_commit(&bar);
         }
-        __syncwarp();
+        wait_mma();
+        uint32_t r[16];
+        tc_ld16(tlane, r);
+        if (valid) {
+            int use_fb = fb;
+            float o[9];
+            for (int q = 0; q < 9; ++q) {
+                o[q] = (__uint_as_float(r[q]) + sb4[q]) * out_sd[q] + out_mu[q];
+                if (!isfinite(o[q])) use_fb = 1;
+            }
+            float rho = m[9];
+            for (int q = 0; q < 9; ++q) o[q] *= rho;
+            float pl = -(o[0] * m[11] + o[1] * m[12] + o[2] * m[13] + 2.f * (o[3] * m[14] + o[4] * m[15] + o[5] * m[16]));
+            if (pl < m[17]) {
+                float a = m[17] / pl;
+                for (int q = 0; q < 6; ++q) o[q] *= a;
+            }
+            for (int q = 0; q < 9; ++q) out[(long long)q * g.nc + c] = use_fb ? m[q] : o[q];
+            if (use_fb && nfallback) atomicAdd(nfallback, 1u);
+        }
     }
+    // the last output layer's wait, then release: on a timeout report it and give the MMAs one
+    // more bounded wait before the TMEM is freed
+    tc_fence_before();
+    if (__syncthreads_or(timeout) || aborted) {
+        if (t == 0 && err) atomicOr(err, 2u);
+        mbar_wait_bounded(&bar, pend, TMA_MAX_POLLS);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tc_dealloc(tm, CL_TCOLS);
+}
+
+// Self-test of the tensor-core path on exact integer data: the operand shapes of the network
+// (K = 64 with N = 64 and with N = 16; K = 16 with N = 64) through the same descriptors and
+// layouts, compared with the products formed by plain integer loops.  mism counts mismatching
+// outputs; bit 0 of *flag reports a wait that gave up.
+constexpr int TCS_SMEM = 64 * 1024;   // generous: three operands need 26 KB
+__global__ void __launch_bounds__(128, 1) k_tc_selftest(int *mism, unsigned *flag) {
+    extern __shared__ __align__(1024) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_taddr;
+    const int t = threadIdx.x, warp = t >> 5;
+    unsigned char *sA = dsm, *sB = dsm + 16384, *sB1 = dsm + 24576;   // A [128][64], B [64][64], B1 [64][16]
+    auto av = [](int m, int k) { return ((m * 7 + k * 3) % 9) - 4; };
+    auto bv = [](int n, int k) { return ((n * 5 + k * 11) % 7) - 3; };
+    for (int q = t; q < 128 * 64; q += 128)
+        *reinterpret_cast<__nv_bfloat16 *>(sA + tc_off(q / 64, q % 64, 64)) = __float2bfloat16_rn((float)av(q / 64, q % 64));
+    for (int q = t; q < 64 * 64; q += 128)
+        *reinterpret_cast<__nv_bfloat16 *>(sB + tc_off(q / 64, q % 64, 64)) = __float2bfloat16_rn((float)bv(q / 64, q % 64));
+    for (int q = t; q < 64 * 16; q += 128)
+        *reinterpret_cast<__nv_bfloat16 *>(sB1 + tc_off(q / 16, q % 16, 16)) = __float2bfloat16_rn((float)bv(q / 16, q % 16));
+    if (t == 0) mbar_init(&bar, 1);
+    if (warp == 0) {
+        tc_alloc(&s_taddr, 256);
+        tc_relinquish();
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tm = s_taddr;
+    if (t == 0) {
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB), b1 = smem_u32(sB1);
+        for (int s = 0; s < 4; ++s)   // K = 64, N = 64 -> columns 0..63
+            tc_mma_bf16(tm, tc_smem_desc(a0 + 256 * s, 128, 1024), tc_smem_desc(b0 + 256 * s, 128, 1024),
+                        tc_idesc_bf16(128, 64), s > 0 ? 1u : 0u);
+        for (int s = 0; s < 4; ++s)   // K = 64, N = 16 (rows 0..15 of B) -> columns 64..79
+            tc_mma_bf16(tm + 64, tc_smem_desc(a0 + 256 * s, 128, 1024), tc_smem_desc(b0 + 256 * s, 128, 1024),
+                        tc_idesc_bf16(128, 16), s > 0 ? 1u : 0u);
+        // K = 16 (columns 0..15 of A, in its K = 64 layout), N = 64 from B1 -> columns 128..191
+        tc_mma_bf16(tm + 128, tc_smem_desc(a0, 128, 1024), tc_smem_desc(b1, 128, 256), tc_idesc_bf16(128, 64), 0u);
+        tc_commit(&bar);
+    }
+    int to = mbar_wait_bounded(&bar, 0, TMA_MAX_POLLS) ? 0 : 1;
+    tc_fence_after();
+    if (__syncthreads_or(to)) {
+        if (t == 0) atomicOr(flag, 1u);
+        mbar_wait_bounded(&bar, 0, TMA_MAX_POLLS);
+    } else {
+        const uint32_t lane = tm + ((uint32_t)(32 * warp) << 16);
+        const int mr = t;   // TMEM lane = row of D
+        int bad = 0;
+        uint32_t r[32];
+        for (int h = 0; h < 2; ++h) {
+            tc_ld32(lane + 32u * h, r);
+            for (int q = 0; q < 32; ++q) {
+                int n = 32 * h + q, e = 0;
+                for (int k = 0; k < 64; ++k) e += av(mr, k) * bv(n, k);
+                bad += __uint_as_float(r[q]) != (float)e;
+            }
+        }
+        tc_ld16(lane + 64u, r);
+        for (int n = 0; n < 16; ++n) {
+            int e = 0;
+            for (int k = 0; k < 64; ++k) e += av(mr, k) * bv(n, k);
+            bad += __uint_as_float(r[n]) != (float)e;
+        }
+        for (int h = 0; h < 2; ++h) {
+            tc_ld32(lane + 128u + 32u * h, r);
+            for (int q = 0; q < 32; ++q) {
+                int n = 32 * h + q, e = 0;
+                for (int k = 0; k < 16; ++k) e += av(mr, k) * bv(n, k);
+                bad += __uint_as_float(r[q]) != (float)e;
+            }
+        }
+        if (bad) atomicAdd(mism, bad);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tc_dealloc(tm, 256);
+}
+void selftest_tensor_cores(int *mism, unsigned *flag, cudaStream_t s) {
+    cudaFuncSetAttribute(k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, TCS_SMEM);
+    k_tc_selftest<<<1, 128, TCS_SMEM, s>>>(mism, flag);
 }
 
 // features only (training data / analysis): out [nc][12]
@@ -357,23 +448,25 @@ void cl_prepare(const float *d_blob, void *w_bf16, float *b, float *stats, cudaS
 }
 void cl_infer(const Geo &g, const MxBase &mb, const Phys &ph, const void *w_bf16, const float *b,
               const float *stats, const float *ux, const float *vy, const float *wz, const float *thp,
-              const float *dr, float *out, unsigned *nfb, cudaStream_t s) {
+              const float *dr, float *out, unsigned *nfb, unsigned *err, cudaStream_t s) {
     const __nv_bfloat16 *w = (const __nv_bfloat16 *)w_bf16;
     ClDev cl{w, w + 1024, w + 1024 + 4096, w + 1024 + 8192, b, stats};
-    // persistent grid: as many resident blocks as fit on the device, each looping over tiles
+    // persistent grid: CL_CTAS_PER_SM CTAs per SM, the residency the launch bounds guarantee for
+    // registers (at most 128 per thread) and that the 38 KB of shared memory allows.  (The
+    // runtime's occupancy query reports one block per SM for kernels that allocate TMEM.)  Their
+    // TMEM, 64 columns each, fits the SM's 512.
+    static_assert(CL_CTAS_PER_SM * CL_TCOLS <= 512, "TMEM of the resident CTAs exceeds an SM's 512 columns");
     static int dev_blocks = 0;
     if (dev_blocks == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
+        int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cl_infer, CLW * 32, 0);
-        dev_blocks = sms * (per_sm > 0 ? per_sm : 1);
+        dev_blocks = sms * CL_CTAS_PER_SM;
     }
-    long long ntiles = (g.nc + 31) / 32;
-    long long need = (ntiles + CLW - 1) / CLW;
-    unsigned nblk = (unsigned)(need < dev_blocks ? need : dev_blocks);
+    long long ntiles = (g.nc + CLT - 1) / CLT;
+    unsigned nblk = (unsigned)(ntiles < dev_blocks ? ntiles : dev_blocks);
     mx_launch("mx_closure_mlp", s, [&] {
-        k_cl_infer<<<nblk, CLW * 32, 0, s>>>(g, mb, ph, cl, VelIn{ux, vy, wz, thp}, dr, out, nfb);
+        k_cl_infer<<<nblk, CLT, 0, s>>>(g, mb, ph, cl, VelIn{ux, vy, wz, thp}, dr, out, nfb, err);
     });
 }
 void cl_features_launch(const Geo &g, const MxBase &mb, double grav, const float *ux, const float *vy,

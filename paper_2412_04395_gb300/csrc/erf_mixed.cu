@@ -1146,7 +1146,7 @@ void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const 
     const int sgs = (visc || (ph.surface == 1 && !learned)) ? 1 : 0;
     const float *tau = nullptr;
     if (learned) {
-        cl_infer(g, mb, ph, cl->w, cl->b, cl->stats, ux, vy, wz, thp, st.r, cl->out, cl->nfb, s);
+        cl_infer(g, mb, ph, cl->w, cl->b, cl->stats, ux, vy, wz, thp, st.r, cl->out, cl->nfb, tma ? tma->err : nullptr, s);
         tau = cl->out;
     }
     // each advected quantity's face fluxes go to the shared buffer (3 planes of nw), then the

@@ -74,7 +74,8 @@ struct ClIn {
 void cl_prepare(const float *d_blob, void *w_bf16, float *b, float *stats, cudaStream_t s);
 void cl_infer(const Geo &g, const MxBase &mb, const Phys &ph, const void *w_bf16, const float *b,
               const float *stats, const float *ux, const float *vy, const float *wz, const float *thp,
-              const float *dr, float *out, unsigned *nfb, cudaStream_t s);
+              const float *dr, float *out, unsigned *nfb, unsigned *err, cudaStream_t s);
+void selftest_tensor_cores(int *mism, unsigned *flag, cudaStream_t s);
 void cl_features_launch(const Geo &g, const MxBase &mb, double grav, const float *ux, const float *vy,
                         const float *wz, const float *thp, float *out, cudaStream_t s);
 void cl_filter_launch(const Geo &g, const MxBase &mb, CF5f st, int r, double *cr, double *crt, double *cru,

@@ -28,7 +28,7 @@ EXPORTS = ["erf_workspace_bytes", "erf_init_grid", "erf_set_initial", "erf_set_s
            "erf_reduce_state_noalloc", "erf_train_scratch_bytes", "erf_train_closure", "erf_closure_grad",
            "erf_column_stats", "erf_standardise", "erf_set_closure_weights", "erf_closure_features",
            "erf_closure_fields", "erf_filter_state", "erf_set_tracer_initial", "erf_set_option",
-           "erf_get_option", "erf_selftest_wait_timeout"]
+           "erf_get_option", "erf_selftest_wait_timeout", "erf_selftest_tensor_cores"]
 
 
 class ErfError(RuntimeError):
@@ -90,6 +90,7 @@ def load_library(path: str = LIB_PATH):
     L.erf_set_tracer_initial.argtypes = [vp, vp, C.c_int32]
     L.erf_set_option.argtypes = [vp, C.c_int32, C.c_int64]
     L.erf_selftest_wait_timeout.argtypes = [C.c_int32, vp, vp, C.POINTER(C.c_int32)]
+    L.erf_selftest_tensor_cores.argtypes = [vp, vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.erf_get_option.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64)]
     L.erf_set_state.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_int32]
     L.erf_rk3_step.argtypes = [vp, C.c_int32]
@@ -113,7 +114,7 @@ def load_library(path: str = LIB_PATH):
                  "erf_get_state", "erf_diagnostics", "erf_profile_steps", "erf_train_closure", "erf_closure_grad",
                  "erf_column_stats", "erf_standardise", "erf_set_closure_weights", "erf_closure_features",
                  "erf_closure_fields", "erf_filter_state", "erf_set_tracer_initial", "erf_set_option",
-                 "erf_get_option", "erf_selftest_wait_timeout"):
+                 "erf_get_option", "erf_selftest_wait_timeout", "erf_selftest_tensor_cores"):
         getattr(L, name).restype = C.c_int
     _LIB = L
     return L
@@ -332,6 +333,19 @@ def erf_selftest_wait_timeout(max_polls=1000):
     _check(L, None, L.erf_selftest_wait_timeout(int(max_polls), C.c_void_p(flag.data_ptr()),
                                                 C.c_void_p(torch.cuda.current_stream().cuda_stream), C.byref(out)))
     return out.value
+
+
+def erf_selftest_tensor_cores():
+    """(mismatching outputs, timed out) of the tcgen05 self-test: MMAs of the closure network's
+    operand shapes on exact integer data, checked against integer loops on the device."""
+    import torch
+    L = load_library()
+    words = torch.zeros(2, dtype=torch.int32, device="cuda")
+    bad, to = C.c_int32(), C.c_int32()
+    _check(L, None, L.erf_selftest_tensor_cores(C.c_void_p(words.data_ptr()),
+                                                C.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                                C.byref(bad), C.byref(to)))
+    return bad.value, to.value
 
 
 # ---------------------------------------------------------------- learned closure (training)

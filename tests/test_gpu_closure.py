@@ -140,6 +140,15 @@ def _blob_for(fo, seed=31):
     return p, mu, sd, out_mu, out_sd, M.pack_blob(p, mu, sd, out_mu, out_sd)
 
 
+def test_tensor_core_selftest_is_exact():
+    """The tcgen05 MMAs of the network's operand shapes (shared-memory layouts, descriptors, TMEM
+    lane mapping) reproduce exact integer products."""
+    from paper_2412_04395_gb300 import erf
+    bad, timed_out = erf.erf_selftest_tensor_cores()
+    assert timed_out == 0
+    assert bad == 0
+
+
 def test_bf16_inference_matches_oracle():
     from paper_2412_04395_gb300.erf import Dycore
     wl = _turbulent_like()
