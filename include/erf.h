@@ -244,9 +244,13 @@ erf_status erf_reduce_state_noalloc(int32_t nx, int32_t ny, int32_t nz, double d
  *   in shared memory with TMA tile loads where the grid allows it (nx % 4 == 0, nx >= 64,
  *   ny >= 16, nz >= 16); 0 uses plain loads.  Both give bit-identical results.  A TMA wait that
  *   gives up makes the next erf_diagnostics return ERF_ECUDA.
+ *   ERF_OPT_COLUMN_FUSION: how the mixed-precision substep runs the explicit vertical part
+ *   (App. C rows 3-4): 1 inside the column sweep of the vertical solve, one thread per column;
+ *   0 as a per-cell kernel before the sweep; -1 (default) fused when nx * ny >= 2^20.  Both give
+ *   bit-identical results.
  * erf_set_option drops the captured step graph; erf_get_option reports whether the option is in
- * effect (for ERF_OPT_TMA_STENCILS: 1 if the TMA kernels run). */
-typedef enum { ERF_OPT_TMA_STENCILS = 1 } erf_option;
+ * effect (1 if the TMA kernels run, 1 if the fused column sweep runs). */
+typedef enum { ERF_OPT_TMA_STENCILS = 1, ERF_OPT_COLUMN_FUSION = 2 } erf_option;
 erf_status erf_set_option(erf_handle *h, int32_t option, int64_t value);
 erf_status erf_get_option(erf_handle *h, int32_t option, int64_t *value);
 

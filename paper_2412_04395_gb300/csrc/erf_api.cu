@@ -66,11 +66,12 @@ struct erf_handle {
     // mixed-precision path (flat grids): FP32 perturbation fields + FP64 solve scratch
     bool mixed = false;
     F5f mst, msn, mx, mR;
-    float *mpp, *mpi, *mthp, *mTp, *mOm, *mux, *mvy, *mwz, *mmfx, *mmfy, *mmu, *mbase;
+    float *mpp, *mpi, *mthp, *mTp, *mux, *mvy, *mwz, *mmfx, *mmfy, *mmu, *mbase;
     double *mdbuf, *mrt0;
     float *mflux = nullptr;                 // slow-tendency face fluxes (3 planes of nw)
     MxTma tma{};                            // TMA tile maps of the stencil fields
     bool tma_enabled = true;
+    int column_fusion = -1;                 // ERF_OPT_COLUMN_FUSION: -1 by column count, 0 off, 1 on
     unsigned *kerr = nullptr;               // set by a kernel whose bounded wait gave up
     float *mX0 = nullptr, *mY0 = nullptr;   // beta-weighted Theta'', rho'' of the vertical substep (in mflux)
     // passive scalar (mixed path, FP32): rho phi, its S^n copy, substep momentum sums
@@ -174,7 +175,7 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
             f->v = cv.take<float>(nc); f->w = cv.take<float>(nw);
         }
         H->mpp = cv.take<float>(nc); H->mpi = cv.take<float>(nc); H->mthp = cv.take<float>(nc);
-        H->mTp = cv.take<float>(nc); H->mOm = cv.take<float>(nw);
+        H->mTp = cv.take<float>(nc);
         H->mux = cv.take<float>(nc); H->mvy = cv.take<float>(nc); H->mwz = cv.take<float>(nw);
         H->mmfx = cv.take<float>(nc); H->mmfy = cv.take<float>(nc);
         // eddy viscosity, then (eddy-viscosity closures) the three diagonal stresses
@@ -356,6 +357,14 @@ static CF5 cf(const F5 &f) { return CF5{f.r, f.t, f.u, f.v, f.w}; }
 static CF5f cf(const F5f &f) { return CF5f{f.r, f.t, f.u, f.v, f.w}; }
 
 // one RK3 step of the mixed-precision path (flat grids)
+// the explicit vertical part runs inside the column sweep once there are enough columns to fill
+// the GPU with one thread each (measured at 1024^2 and 2048^2 columns; below that the per-cell
+// kernel keeps more threads in flight)
+static int fuse_columns(const erf_handle *h) {
+    if (h->column_fusion >= 0) return h->column_fusion;
+    return h->geo.nxy >= (1LL << 20) ? 1 : 0;
+}
+
 static void enqueue_step_mixed(erf_handle *h, cudaStream_t s) {
     const Geo &g = h->geo;
     const Phys &ph = h->ph;
@@ -370,7 +379,7 @@ static void enqueue_step_mixed(erf_handle *h, cudaStream_t s) {
     if (h->mtphi) cudaMemcpyAsync(h->msnphi, h->mtphi, bc, cudaMemcpyDeviceToDevice, s);
     const double alpha[3] = {1.0 / 3.0, 0.5, 1.0};
     for (int stage = 0; stage < 3; ++stage) {
-        mx_stage_begin(g, h->mb, cf(h->msn), cf(h->mst), h->mx, h->mpp, h->mpi, h->mthp, h->mTp, h->mOm, s);
+        mx_stage_begin(g, h->mb, cf(h->msn), cf(h->mst), h->mx, h->mpp, h->mpi, h->mthp, h->mTp, s);
         ClIn clin{h->cl_w, h->cl_b, h->cl_stats, h->cl_out, h->cl_nfb};
         mx_slow_rhs(g, h->mb, ph, cf(h->mst), h->mpp, h->mthp, h->mux, h->mvy, h->mwz, h->mmfx, h->mmfy, h->mmu,
                     h->mflux, h->mR, s, h->cl_ready ? &clin : nullptr, &h->tma);
@@ -383,8 +392,8 @@ static void enqueue_step_mixed(erf_handle *h, cudaStream_t s) {
             cudaMemsetAsync(h->mms.z, 0, bw, s);
         }
         for (int n = 0; n < nsub; ++n)
-            mx_substep(g, h->mb, ph, h->mtri, h->mpi, h->mthp, cf(h->mR), h->mx, h->mOm, h->mTp, h->mdbuf, h->mX0, h->mY0,
-                       h->mms, dtau, s);
+            mx_substep(g, h->mb, ph, h->mtri, h->mpi, h->mthp, cf(h->mR), h->mx, h->mTp, h->mdbuf, h->mX0, h->mY0,
+                       h->mms, fuse_columns(h), dtau, s);
         // the passive scalar after the substeps, from the stage state S^t (the pressure and flux
         // scratch are free until the next stage begins)
         if (h->mtphi)
@@ -794,10 +803,16 @@ extern "C" erf_status erf_diagnostics(erf_handle *h, erf_diag *out) {
 
 extern "C" erf_status erf_set_option(erf_handle *h, int32_t option, int64_t value) {
     if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
-    if (option != ERF_OPT_TMA_STENCILS) return fail(h, ERF_EINVAL, "unknown option");
-    h->tma_enabled = value != 0;
-    if (h->mixed)
-        h->tma.use = (h->tma_enabled && mx_encode_tiles(h)) ? 1 : 0;
+    if (option == ERF_OPT_TMA_STENCILS) {
+        h->tma_enabled = value != 0;
+        if (h->mixed)
+            h->tma.use = (h->tma_enabled && mx_encode_tiles(h)) ? 1 : 0;
+    } else if (option == ERF_OPT_COLUMN_FUSION) {
+        if (value < -1 || value > 1) return fail(h, ERF_EINVAL, "column fusion must be -1, 0 or 1");
+        h->column_fusion = (int)value;
+    } else {
+        return fail(h, ERF_EINVAL, "unknown option");
+    }
     // the captured step graph holds the previous choice
     if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
     if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
@@ -838,8 +853,9 @@ extern "C" erf_status erf_selftest_tensor_cores(int32_t *d_words, void *cuda_str
 }
 extern "C" erf_status erf_get_option(erf_handle *h, int32_t option, int64_t *value) {
     if (!h || !value) return fail(h, ERF_EINVAL, "NULL argument");
-    if (option != ERF_OPT_TMA_STENCILS) return fail(h, ERF_EINVAL, "unknown option");
-    *value = (h->mixed && h->tma.use) ? 1 : 0;
+    if (option == ERF_OPT_TMA_STENCILS) *value = (h->mixed && h->tma.use) ? 1 : 0;
+    else if (option == ERF_OPT_COLUMN_FUSION) *value = (h->mixed && fuse_columns(h)) ? 1 : 0;
+    else return fail(h, ERF_EINVAL, "unknown option");
     return ERF_OK;
 }
 
@@ -868,7 +884,7 @@ extern "C" erf_status erf_set_closure_weights(erf_handle *h, const void *blob, s
 
 // EOS + face velocities of the current state (mixed path) into the stage scratch
 static void mx_current_fields(erf_handle *h, cudaStream_t s) {
-    mx_stage_begin(h->geo, h->mb, cf(h->mst), cf(h->mst), h->mx, h->mpp, h->mpi, h->mthp, h->mTp, h->mOm, s);
+    mx_stage_begin(h->geo, h->mb, cf(h->mst), cf(h->mst), h->mx, h->mpp, h->mpi, h->mthp, h->mTp, s);
     mx_slow_prep_only(h->geo, h->mb, cf(h->mst), h->mux, h->mvy, h->mwz, h->mmfx, h->mmfy, s);
 }
 

@@ -18,16 +18,6 @@
 namespace erfk {
 
 __device__ __forceinline__ double sgnd(double x) { return sgnT<double>(x); }
-// 1/x in FP64 by the Newton-Raphson iteration for the reciprocal, r <- r + r (1 - x r), from an
-// FP32 estimate (two steps: 6e-8 -> 4e-15 -> rounding level); about 7 FP64-pipe operations against
-// about 10 for a division.  Values outside the FP32 range take the division.
-__device__ __forceinline__ double rcp_d(double x) {
-    const float xf = (float)x;
-    if (!(fabsf(xf) > 1.0e-30f && fabsf(xf) < 1.0e30f)) return 1.0 / x;
-    double r = (double)(1.0f / xf);
-    r = fma(r, fma(-x, r, 1.0), r);
-    return fma(r, fma(-x, r, 1.0), r);
-}
 
 // Exner function and pressure from rho*theta (Sec. 2.1 EOS, dry):
 // pi = (R_d rho theta / P00)^(R_d/c_v), p = R_d rho theta pi.  The product is rounded on its

@@ -116,7 +116,7 @@ __global__ void k_mx_wall_bc(Geo g, float *rw) {
 
 // ------------------------------------------------------------------ stage begin (EOS, X'')
 __global__ void k_mx_stage_begin(Geo g, MxBase mb, CF5f sn, CF5f st, F5f x, float *pp, float *pi, float *thp,
-                                 float *Tp, float *Om) {
+                                 float *Tp) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int k = blockIdx.z;
@@ -135,9 +135,7 @@ __global__ void k_mx_stage_begin(Geo g, MxBase mb, CF5f sn, CF5f st, F5f x, floa
         x.u[n] = sn.u[n] - st.u[n];
         x.v[n] = sn.v[n] - st.v[n];
     }
-    float xw = sn.w[n] - st.w[n];
-    x.w[n] = xw;
-    Om[n] = (k == 0 || k == g.nz) ? 0.f : xw;
+    x.w[n] = sn.w[n] - st.w[n];   // on flat grids W'' is Omega'' (the walls are set by the solve)
 }
 
 __global__ void k_mx_prep(Geo g, MxBase mb, CF5f st, float *ux, float *vy, float *wz, float *mfx, float *mfy) {
@@ -837,8 +835,8 @@ __global__ void k_mx_sub_horiz(Geo g, MxBase mb, const float *pi, const float *T
 
 // theta at w-face kf relative to theta0 of cell kc (small numbers), from the FP32 table of
 // base-state differences and the perturbation theta' of the two cells around the face
-__device__ __forceinline__ float mx_thw_rel(const MxBase &mb, const float *thp, long long c0, long long nxy, int nz,
-                                            int kf, int kc) {
+template <class I>
+__device__ __forceinline__ float mx_thw_rel(const MxBase &mb, const float *thp, I c0, I nxy, int nz, int kf, int kc) {
     int ka = kref(kf - 1, nz), kb = kref(kf, nz);
     return 0.5f * (dth0(mb, ka, kc) + dth0(mb, kb, kc)) + 0.5f * (__ldg(thp + c0 + ka * nxy) + __ldg(thp + c0 + kb * nxy));
 }
@@ -848,7 +846,7 @@ __device__ __forceinline__ float mx_thw_rel(const MxBase &mb, const float *thp, 
 // beta-weighted X0 = b1 Theta''^tau + b2 Theta*, Y0 = b1 rho''^tau + b2 rho* that enter the
 // Omega'' rows.  Theta''^tau is kept in Tt for the divergence damping of the next substep.
 __global__ void k_mx_sub_expl(Geo g, MxBase mb, Phys ph, const float *thp, const float *Rr, const float *Rt,
-                              F5f x, const float *Om, float *Tt, float *X0o, float *Y0o, float dtf, TrSum ms) {
+                              F5f x, float *Tt, float *X0o, float *Y0o, float dtf, TrSum ms) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z, nz = g.nz;
@@ -859,6 +857,7 @@ __global__ void k_mx_sub_expl(Geo g, MxBase mb, Phys ph, const float *thp, const
     const long long oym = j > 0 ? -(long long)g.nx : nxy - g.nx;
     const float b1 = mb.b1, b2 = mb.b2;
     const float rdx = mb.rdx, rdy = mb.rdy;
+    const float *Om = x.w;   // Omega'' = W'' on flat grids
     float om_k = k >= 1 ? Om[c] : 0.f;
     float om_p = k + 1 < nz ? Om[c + nxy] : 0.f;
     float Uc = x.u[c], Up = x.u[c + oxp], Vc = x.v[c], Vp = x.v[c + oyp];
@@ -888,6 +887,23 @@ __global__ void k_mx_sub_expl(Geo g, MxBase mb, Phys ph, const float *thp, const
     }
 }
 
+// back substitution of a column with the stage factors c' (d' in dbuf), in FP64; W'' = Omega''
+// (zero on both walls) is stored in FP32
+template <int UNROLL>
+__device__ __forceinline__ void mx_back_substitute(int nz, long long nxy, long long n, const double *__restrict__ tcp,
+                                                   float *__restrict__ W, const double *__restrict__ dbuf) {
+    W[n + nz * nxy] = 0.f;
+    double om_up = 0.0;
+#pragma unroll UNROLL
+    for (int k = nz - 1; k >= 1; --k) {
+        long long c = n + k * nxy;
+        double om = dbuf[c] - tcp[c] * om_up;
+        W[c] = (float)om;
+        om_up = om;
+    }
+    W[n] = 0.f;
+}
+
 // Part 2 (one thread per column): the Omega'' rows' right-hand side, forward elimination with the
 // stage LU factors and back substitution, in FP64 (d' in the FP64 scratch dbuf); W'' = Omega''.
 // Only the two recurrences are serial; every load is independent of them, so the unrolled loop
@@ -898,8 +914,7 @@ __global__ void __launch_bounds__(128) k_mx_sub_col(int nz, long long nxy, const
                                                     const float *__restrict__ tP, const float *__restrict__ tQ,
                                                     const float *__restrict__ X0, const float *__restrict__ Y0,
                                                     const float *__restrict__ Rw, float *__restrict__ W,
-                                                    float *__restrict__ Om, double *__restrict__ dbuf, float dtf,
-                                                    float Gg) {
+                                                    double *__restrict__ dbuf, float dtf, float Gg) {
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= nxy) return;
     double dpm = 0.0;
@@ -914,33 +929,103 @@ __global__ void __launch_bounds__(128) k_mx_sub_col(int nz, long long nxy, const
         dpm = dp;
         X0m = X0c; Y0m = Y0c;
     }
-    long long top = n + nz * nxy;
-    W[top] = 0.f;
-    Om[top] = 0.f;
+    mx_back_substitute<UNROLL>(nz, nxy, n, tcp, W, dbuf);
+}
+
+// Parts 1 and 2 fused (one thread per column, for grids with enough columns to fill the GPU):
+// going up the column, each cell's explicit Theta*, rho*, X0, Y0 (the arithmetic of
+// k_mx_sub_expl, in the same order) feed the row of the face below it at once, so X0 and Y0
+// never leave registers and W'' is read once; then the back substitution.  The horizontal
+// neighbours are the adjacent columns of the same level (coalesced across the warp).
+template <int UNROLL>
+__global__ void __launch_bounds__(128, 8) k_mx_sub_vert(Geo g, MxBase mb, const float *__restrict__ thp,
+                                                        const float *__restrict__ Rr, const float *__restrict__ Rt,
+                                                        const float *__restrict__ Rw, F5f x, float *__restrict__ Tt,
+                                                        const double *__restrict__ ta, const double *__restrict__ tcp,
+                                                        const double *__restrict__ tim, const float *__restrict__ tP,
+                                                        const float *__restrict__ tQ, double *__restrict__ dbuf,
+                                                        float dtf, float Gg, TrSum ms) {
+    // 32-bit indices throughout (grids hold fewer than 2^31 w-points), which keeps the kernel
+    // inside the 64 registers that 8 resident blocks per SM allow
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nxy = (int)g.nxy;
+    if (n >= nxy) return;
+    const int nz = g.nz;
+    const int i = n % g.nx, j = n / g.nx;
+    const int oxp = i + 1 < g.nx ? 1 : 1 - g.nx, oxm = i > 0 ? -1 : g.nx - 1;
+    const int oyp = j + 1 < g.ny ? g.nx : g.nx - nxy;
+    const int oym = j > 0 ? -g.nx : nxy - g.nx;
+    const float b1 = mb.b1, b2 = mb.b2, rdx = mb.rdx, rdy = mb.rdy;
+    float *W = x.w;
+    // explicit part of cell k (om_k, om_p: W'' at its lower and upper faces); the arithmetic of
+    // k_mx_sub_expl in the same order
+    auto cell = [&](int k, float om_k, float om_p, float &X0, float &Y0) {
+        const int c = n + k * nxy;
+        float Uc = x.u[c], Up = x.u[c + oxp], Vc = x.v[c], Vp = x.v[c + oyp];
+        float tc = __ldg(thp + c);
+        float thxm = 0.5f * (__ldg(thp + c + oxm) + tc), thxp = 0.5f * (tc + __ldg(thp + c + oxp));
+        float thym = 0.5f * (__ldg(thp + c + oym) + tc), thyp = 0.5f * (tc + __ldg(thp + c + oyp));
+        float dz = mb.dzf[k], rH = mb.rdzf[k];
+        float divM = dz * ((Up - Uc) * rdx + (Vp - Vc) * rdy);
+        float divTp = dz * ((Up * thxp - Uc * thxm) * rdx + (Vp * thyp - Vc * thym) * rdy);
+        float th0k = mb.th0f[k];
+        float wk_rel = k == 0 ? 0.f : mx_thw_rel(mb, thp, n, nxy, nz, k, k);
+        float wp_rel = k + 1 >= nz ? 0.f : mx_thw_rel(mb, thp, n, nxy, nz, k + 1, k);
+        float vflux_rel = om_p * wp_rel - om_k * wk_rel;
+        float xt = x.t[c], xr = x.r[c];
+        float vdiv = om_p - om_k;
+        float Ts = xt + dtf * (-(th0k * divM + divTp) * rH - b1 * (th0k * vdiv + vflux_rel) * rH + Rt[c]);
+        float Rs = xr + dtf * (-divM * rH - b1 * vdiv * rH + Rr[c]);
+        Tt[c] = xt;
+        x.t[c] = Ts;
+        x.r[c] = Rs;
+        X0 = b1 * xt + b2 * Ts;
+        Y0 = b1 * xr + b2 * Rs;
+        if (ms.x) {
+            ms.x[c] += Uc;
+            ms.y[c] += Vc;
+            if (k >= 1) ms.z[c] += b1 * om_k;
+        }
+    };
+    float om_k = nz > 1 ? W[n + nxy] : 0.f;   // W'' at the top face of cell 0
+    float X0m, Y0m;
+    cell(0, 0.f, om_k, X0m, Y0m);
+    double dpm = 0.0;
+#pragma unroll UNROLL
+    for (int k = 1; k < nz; ++k) {
+        const int c = n + k * nxy;
+        const float om_p = k + 1 < nz ? W[c + nxy] : 0.f;
+        float X0c, Y0c;
+        cell(k, om_k, om_p, X0c, Y0c);
+        float rhs = om_k + dtf * Rw[c] + tP[c] * X0c + tQ[c] * X0m - Gg * (Y0c + Y0m);
+        double dp = ((double)rhs - ta[c] * dpm) * tim[c];
+        dbuf[c] = dp;
+        dpm = dp;
+        X0m = X0c; Y0m = Y0c;
+        om_k = om_p;
+    }
+    W[n + nz * nxy] = 0.f;
     double om_up = 0.0;
 #pragma unroll UNROLL
     for (int k = nz - 1; k >= 1; --k) {
-        long long c = n + k * nxy;
+        const int c = n + k * nxy;
         double om = dbuf[c] - tcp[c] * om_up;
-        float omf = (float)om;
-        W[c] = omf;
-        Om[c] = omf;
+        W[c] = (float)om;
         om_up = om;
     }
     W[n] = 0.f;
-    Om[n] = 0.f;
 }
 
 // Part 3 (one thread per cell): Theta'', rho'' from the new Omega'' (App. C rows 3-4, beta_2
 // part) and Theta~ of the next substep.
-__global__ void k_mx_sub_fin(Geo g, MxBase mb, Phys ph, const float *thp, const float *Om, F5f x, float *Tt,
-                             float dtf, float *msz) {
+__global__ void k_mx_sub_fin(Geo g, MxBase mb, Phys ph, const float *thp, F5f x, float *Tt, float dtf, float *msz) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z, nz = g.nz;
     const long long nxy = g.nxy;
     const long long c0 = (long long)j * g.nx + i, c = c0 + k * nxy;
     const float b2 = mb.b2, bd = mb.bd;
+    const float *Om = x.w;   // Omega'' = W'' on flat grids
     float omf = Om[c], omf_up = Om[c + nxy];
     float th0k = mb.th0f[k];
     float wk_rel = k == 0 ? 0.f : mx_thw_rel(mb, thp, c0, nxy, nz, k, k);
@@ -960,14 +1045,14 @@ __device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret
 __device__ __forceinline__ float4 ldw4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 __device__ __forceinline__ float &el(float4 &v, int e) { return (&v.x)[e]; }
-__global__ void k_mx_sub_fin4(Geo g, MxBase mb, Phys ph, const float *thp, const float *Om, F5f x, float *Tt,
-                              float dtf, float *msz) {
+__global__ void k_mx_sub_fin4(Geo g, MxBase mb, Phys ph, const float *thp, F5f x, float *Tt, float dtf, float *msz) {
     const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z, nz = g.nz;
     const long long nxy = g.nxy;
     const long long c0 = (long long)j * g.nx + i, c = c0 + k * nxy;
     const float b2 = mb.b2, bd = mb.bd;
+    const float *Om = x.w;   // Omega'' = W'' on flat grids
     float4 om = ld4(Om + c), omu = ld4(Om + c + nxy);
     const float th0k = mb.th0f[k];
     // theta' at the reflected levels below, at and above k (the w-faces k and k+1)
@@ -1132,9 +1217,9 @@ void mx_wall_bc(const Geo &g, float *rw, cudaStream_t s) {
     mx_launch("wall_bc", s, [&] { k_mx_wall_bc<<<nb(g.nxy, MBS), MBS, 0, s>>>(g, rw); });
 }
 void mx_stage_begin(const Geo &g, const MxBase &mb, CF5f sn, CF5f st, F5f x, float *pp, float *pi, float *thp,
-                    float *Tp, float *Om, cudaStream_t s) {
+                    float *Tp, cudaStream_t s) {
     mx_launch("mx_stage_begin", s, [&] {
-        k_mx_stage_begin<<<g3(g, g.nz + 1), MBX, 0, s>>>(g, mb, sn, st, x, pp, pi, thp, Tp, Om);
+        k_mx_stage_begin<<<g3(g, g.nz + 1), MBX, 0, s>>>(g, mb, sn, st, x, pp, pi, thp, Tp);
     });
 }
 void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const float *pp, const float *thp,
@@ -1229,31 +1314,39 @@ void mx_tri_build(const Geo &g, const MxBase &mb, const Phys &ph, const float *d
     mx_launch("mx_tri_build", s, [&] { k_mx_tri_build<<<nb(g.nxy, 128), 128, 0, s>>>(g, mb, ph, dr, dT, pi, thp, dtau, tr); });
 }
 void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, TriM tr, const float *pi, const float *thp, CF5f R,
-                F5f x, float *Om, float *Tt, double *dbuf, float *X0, float *Y0, TrSum ms, double dtau,
+                F5f x, float *Tt, double *dbuf, float *X0, float *Y0, TrSum ms, int fuse_columns, double dtau,
                 cudaStream_t s) {
     const dim3 blk(128), grd((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)g.nz);
     const float dtf = (float)dtau, Gg = (float)(dtau * 0.5 * ph.g);
     mx_launch("mx_sub_horiz", s, [&] {
         k_mx_sub_horiz<<<grd, blk, 0, s>>>(g, mb, pi, Tt, R.u, R.v, x.u, x.v, dtf);
     });
-    mx_launch("mx_sub_expl", s, [&] {
-        k_mx_sub_expl<<<grd, blk, 0, s>>>(g, mb, ph, thp, R.r, R.t, x, Om, Tt, X0, Y0, dtf, ms);
-    });
-    mx_launch("mx_sub_col", s, [&] {
-        // deeper unrolling keeps more loads in flight once there are enough columns to fill the
-        // GPU (measured: 12% faster at 1024^2 columns, 30% slower at 256^2)
-        if (g.nxy >= (1LL << 20))
-            k_mx_sub_col<8><<<nb(g.nxy, 128), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q, X0, Y0, R.w, x.w,
-                                                           Om, dbuf, dtf, Gg);
-        else
-            k_mx_sub_col<4><<<nb(g.nxy, 128), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q, X0, Y0, R.w, x.w,
-                                                           Om, dbuf, dtf, Gg);
-    });
+    // deeper unrolling keeps more loads in flight once there are enough columns to fill the GPU
+    // (measured: 12% faster at 1024^2 columns, 30% slower at 256^2)
+    const bool deep = g.nxy >= (1LL << 20);
+    if (fuse_columns) {
+        mx_launch("mx_sub_vert", s, [&] {
+            k_mx_sub_vert<4><<<nb(g.nxy, 128), 128, 0, s>>>(g, mb, thp, R.r, R.t, R.w, x, Tt, tr.a, tr.cp, tr.im, tr.P,
+                                                            tr.Q, dbuf, dtf, Gg, ms);
+        });
+    } else {
+        mx_launch("mx_sub_expl", s, [&] {
+            k_mx_sub_expl<<<grd, blk, 0, s>>>(g, mb, ph, thp, R.r, R.t, x, Tt, X0, Y0, dtf, ms);
+        });
+        mx_launch("mx_sub_col", s, [&] {
+            if (deep)
+                k_mx_sub_col<8><<<nb(g.nxy, 128), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q, X0, Y0, R.w,
+                                                               x.w, dbuf, dtf, Gg);
+            else
+                k_mx_sub_col<4><<<nb(g.nxy, 128), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q, X0, Y0, R.w,
+                                                               x.w, dbuf, dtf, Gg);
+        });
+    }
     if (g.nx % 4 == 0) {
         const dim3 grd4((unsigned)((g.nx / 4 + 127) / 128), (unsigned)g.ny, (unsigned)g.nz);
-        mx_launch("mx_sub_fin", s, [&] { k_mx_sub_fin4<<<grd4, blk, 0, s>>>(g, mb, ph, thp, Om, x, Tt, dtf, ms.z); });
+        mx_launch("mx_sub_fin", s, [&] { k_mx_sub_fin4<<<grd4, blk, 0, s>>>(g, mb, ph, thp, x, Tt, dtf, ms.z); });
     } else {
-        mx_launch("mx_sub_fin", s, [&] { k_mx_sub_fin<<<grd, blk, 0, s>>>(g, mb, ph, thp, Om, x, Tt, dtf, ms.z); });
+        mx_launch("mx_sub_fin", s, [&] { k_mx_sub_fin<<<grd, blk, 0, s>>>(g, mb, ph, thp, x, Tt, dtf, ms.z); });
     }
 }
 void mx_stage_end(const Geo &g, F5f st, CF5f x, cudaStream_t s) {

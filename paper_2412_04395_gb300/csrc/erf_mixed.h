@@ -89,7 +89,7 @@ void mx_from_full(const Geo &g, const double *src, float *dst, int field, long l
 void mx_to_full(const Geo &g, const float *src, double *dst, int field, long long n, cudaStream_t s);
 void mx_wall_bc(const Geo &g, float *rw, cudaStream_t s);
 void mx_stage_begin(const Geo &g, const MxBase &mb, CF5f sn, CF5f st, F5f x, float *pp, float *pi, float *thp,
-                    float *Tp, float *Om, cudaStream_t s);
+                    float *Tp, cudaStream_t s);
 // TMA tile maps of the stencil fields (use = 0: the plain-load kernels) and the device word a
 // kernel sets when a bounded wait gives up
 struct MxTma {
@@ -111,8 +111,10 @@ void mx_tri_build(const Geo &g, const MxBase &mb, const Phys &ph, const float *d
 struct TrSum {
     float *x, *y, *z;
 };
+// one acoustic substep; fuse_columns = 1 runs the explicit vertical part inside the column
+// sweep (k_mx_sub_vert), 0 as its own per-cell kernel before the sweep
 void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, TriM tr, const float *pi, const float *thp, CF5f R,
-                F5f x, float *Om, float *Tt, double *dbuf, float *X0, float *Y0, TrSum ms, double dtau,
+                F5f x, float *Tt, double *dbuf, float *X0, float *Y0, TrSum ms, int fuse_columns, double dtau,
                 cudaStream_t s);
 void mx_stage_end(const Geo &g, F5f st, CF5f x, cudaStream_t s);
 // rho phi^(s) from S^n's rho phi and the stage's averaged mass fluxes (phi and flux are scratch)
