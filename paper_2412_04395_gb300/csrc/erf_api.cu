@@ -256,6 +256,9 @@ static void fill_geo(erf_handle *h) {
     P.g = c.gravity; P.f_cor = c.f_cor; P.u_g = c.u_g; P.v_g = c.v_g; P.Cs = c.Cs; P.Pr_t = c.Pr_t; P.nu = c.nu;
     P.z0 = c.z0; P.Qs = c.sfc_theta_flux; P.beta_s = c.beta_s; P.beta_d = c.beta_d;
     P.rPr_t = 1.0 / c.Pr_t;
+    P.b1 = 0.5 * (1.0 - c.beta_s);
+    P.b2 = 0.5 * (1.0 + c.beta_s);
+    P.b1h = 0.5 * P.b1;
     P.closure = c.closure; P.surface = c.surface; P.scal_adv = c.scal_adv;
 }
 

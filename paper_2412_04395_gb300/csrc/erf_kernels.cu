@@ -643,7 +643,7 @@ __global__ void k_tri_build(Geo g, Phys ph, const double *rho, const double *rt,
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= g.nxy) return;
     int i = (int)(n % g.nx), j = (int)(n / g.nx);
-    double b2 = 0.5 * (1.0 + ph.beta_s);
+    double b2 = ph.b2;
     double E = dtau * b2 * b2, Gg = dtau * 0.5 * ph.g;
     double gRd = GAMMA * RD;
     double cp_prev = 0.0;
@@ -704,12 +704,12 @@ __global__ void k_sub_horiz(Geo g, Phys ph, const double *pi, const double *Tt, 
         gx -= 0.5 * hxi_x(g, i, j, k) * (dc + dxm);
         gy -= 0.5 * heta_y(g, i, j, k) * (dc + dym);
     }
-    double gRd = GAMMA * RD;
+    // -gamma R_d pi^x: the face average's 1/2 is folded into the constant (exact, so the result
+    // is unchanged)
+    constexpr double cgr = -0.5 * (GAMMA * RD);
     double pic = pi[c];
-    double pix = 0.5 * (cval(g, pi, i - 1, j, k) + pic);
-    double piy = 0.5 * (cval(g, pi, i, j - 1, k) + pic);
-    Xu[c] += dtau * (-gRd * pix * gx + Ru[c]);
-    Xv[c] += dtau * (-gRd * piy * gy + Rv[c]);
+    Xu[c] += dtau * (cgr * (cval(g, pi, i - 1, j, k) + pic) * gx + Ru[c]);
+    Xv[c] += dtau * (cgr * (cval(g, pi, i, j - 1, k) + pic) * gy + Rv[c]);
 }
 
 // Vertical acoustic update (App. C rows 3-5) in three kernels.  Part 1, one thread per cell:
@@ -727,11 +727,13 @@ __global__ void k_sub_expl(Geo g, Phys ph, const double *th, const double *TX, c
     const long long c = ((long long)k * g.ny + j) * g.nx + i;
     const long long oxp = i + 1 < g.nx ? 1 : 1 - g.nx;
     const long long oyp = j + 1 < g.ny ? (long long)g.nx : (long long)g.nx - nxy;
-    const double b1 = 0.5 * (1.0 - ph.beta_s), b2 = 0.5 * (1.0 + ph.beta_s);
+    const double b1 = ph.b1, b2 = ph.b2;
     double om_k = k >= 1 ? Om[c] : 0.0;
     double om_p = k + 1 < nz ? Om[c + nxy] : 0.0;
     double th_c = th[c];
-    double thw_k = 0.5 * (cval(g, th, i, j, k - 1) + th_c), thw_p = 0.5 * (th_c + cval(g, th, i, j, k + 1));
+    // theta at the lower and upper w-faces, kept as twice the face average: the 1/2 is folded
+    // into b1 (exact scalings, so the result is unchanged)
+    double sw_k = cval(g, th, i, j, k - 1) + th_c, sw_p = th_c + cval(g, th, i, j, k + 1);
     double Uc = x.u[c], Up = x.u[c + oxp], Vc = x.v[c], Vp = x.v[c + oyp];
     double divM = (Hx(g, i + 1, j, k) * Up - Hx(g, i, j, k) * Uc) * g.rdx
                 + (Hy(g, i, j + 1, k) * Vp - Hy(g, i, j, k) * Vc) * g.rdy;
@@ -739,7 +741,7 @@ __global__ void k_sub_expl(Geo g, Phys ph, const double *th, const double *TX, c
                 + (__ldg(TY + c + oyp) * Vp - __ldg(TY + c) * Vc) * g.rdy;
     double rH = rHc(g, i, j, k);
     double xt = x.t[c], xr = x.r[c];
-    double Ts = xt + dtau * ((-divT - b1 * (om_p * thw_p - om_k * thw_k)) * rH + Rt[c]);
+    double Ts = xt + dtau * ((-divT - ph.b1h * (om_p * sw_p - om_k * sw_k)) * rH + Rt[c]);
     double Rs = xr + dtau * ((-divM - b1 * (om_p - om_k)) * rH + Rr[c]);
     Tt[c] = xt;
     x.t[c] = Ts;
@@ -799,16 +801,16 @@ __global__ void __launch_bounds__(128) k_sub_col(int nz, long long nxy, const do
 // Part 3, one thread per cell: Theta'', rho'' from the new Omega'' (beta_2 part), Theta~ of the
 // next substep, and W'' = Omega'' + metric shift at the cell's bottom w-face.
 __global__ void k_sub_fin(Geo g, Phys ph, const double *th, const double *Om, const double *Ash, F5 x, double *Tt,
-                          double *msz, double dtau) {
+                          double *msz, double dtb2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
     const long long c = ((long long)k * g.ny + j) * g.nx + i;
-    const double b2 = 0.5 * (1.0 + ph.beta_s), bd = ph.beta_d;
+    const double b2 = ph.b2, bd = ph.beta_d;
     double om = Om[c], om_up = Om[c + g.nxy];
     double th_c = th[c];
     double thw_k = 0.5 * (cval(g, th, i, j, k - 1) + th_c), thw_p = 0.5 * (th_c + cval(g, th, i, j, k + 1));
-    double db = dtau * b2 * rHc(g, i, j, k);
+    double db = dtb2 * rHc(g, i, j, k);   // dtb2 = dtau b2
     double xt = x.t[c] - db * (om_up * thw_p - om * thw_k);
     x.t[c] = xt;
     x.r[c] = x.r[c] - db * (om_up - om);
@@ -1066,7 +1068,7 @@ void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *pi, cons
                                                          msx, msy, msz, dtau));
     LAUNCH("sub_col", s, k_sub_col<<<nblk(g.nxy, 128), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q, X0, Y0,
                                                                     x.w, Om, dtau * 0.5 * ph.g));
-    LAUNCH("sub_fin", s, k_sub_fin<<<g3c, 128, 0, s>>>(g, ph, th, Om, Ash, x, Tp, msz, dtau));
+    LAUNCH("sub_fin", s, k_sub_fin<<<g3c, 128, 0, s>>>(g, ph, th, Om, Ash, x, Tp, msz, dtau * ph.b2));
 }
 void launch_tracer_stage(const Geo &g, const Phys &ph, CF5 st, const double *rom, const double *snphi,
                          const double *msx, const double *msy, const double *msz, int nsub, double adt,
