@@ -424,12 +424,10 @@ __global__ void k_sgs_div(Geo g, Phys ph, const double *mu, const double *t11, c
 
 // ------------------------------------------------------------------ slow tendencies
 
-// WENO5-JS / WENO5-Z face value in FP64 (same candidates, indicators and weights as weno5<T>),
-// arranged for GB300's FP64 rate: the three candidate values and the six indicator terms are
-// formed from the four first differences of the stencil, and the normalisation uses the
-// Newton-Raphson iteration for the reciprocal, r <- r + r (1 - D r) (quadratic convergence), from
-// an FP32 estimate: two steps take its 6e-8 relative error to the FP64 rounding level.  A sum
-// outside the FP32 range falls back to the division.
+// WENO5-JS / WENO5-Z face value in FP64 (same candidates and weights as weno5<T>), arranged for
+// GB300's FP64 rate: the three candidate values and the six indicator terms are formed from the
+// four first differences of the stencil, the indicators carry a common factor 12/13, and the
+// normalisation takes one reciprocal (rcp_d) instead of a division.
 __device__ __forceinline__ double weno5_d(const double *q, double s, int zflag) {
     double a, b, c, d, e;   // v_{-2}, v_{-1}, v_0, v_1, v_2 on the upwind side
     if (s >= 0.0) { a = q[0]; b = q[1]; c = q[2]; d = q[3]; e = q[4]; }
@@ -441,10 +439,14 @@ __device__ __forceinline__ double weno5_d(const double *q, double s, int zflag) 
     const double t0 = d1 - d2, u0 = fma(-3.0, d2, d1);               // a - 2b + c, a - 4b + 3c
     const double t1 = d2 - d3, u1 = d2 + d3;                         // b - 2c + d, b - d
     const double t2 = d3 - d4, u2 = fma(3.0, d3, -d4);               // c - 2d + e, 3c - 4d + e
-    const double b0 = fma(13.0 / 12.0 * t0, t0, 0.25 * u0 * u0);
-    const double b1 = fma(13.0 / 12.0 * t1, t1, 0.25 * u1 * u1);
-    const double b2 = fma(13.0 / 12.0 * t2, t2, 0.25 * u2 * u2);
-    const double eps = 1.0e-6;
+    // smoothness indicators 13/12 t^2 + 1/4 u^2 and eps = 1e-6, both scaled by 12/13: the weights
+    // are homogeneous in (eps + beta), so the scheme is unchanged and each indicator takes three
+    // FP64 operations instead of four
+    constexpr double k3 = 3.0 / 13.0;
+    const double b0 = fma(t0, t0, (k3 * u0) * u0);
+    const double b1 = fma(t1, t1, (k3 * u1) * u1);
+    const double b2 = fma(t2, t2, (k3 * u2) * u2);
+    constexpr double eps = 1.0e-6 * (12.0 / 13.0);
     double w0, w1, w2;
     if (zflag) {
         double tau = fabs(b0 - b2);
@@ -461,12 +463,7 @@ __device__ __forceinline__ double weno5_d(const double *q, double s, int zflag) 
     }
     const double N = fma(w0, p0, fma(w1, p1, w2 * p2));
     const double D = w0 + w1 + w2;
-    const float Df = (float)D;
-    if (!(fabsf(Df) > 1.0e-30f && fabsf(Df) < 1.0e30f)) return N / D;
-    double r = (double)(1.0f / Df);
-    r = fma(r, fma(-D, r, 1.0), r);
-    r = fma(r, fma(-D, r, 1.0), r);
-    return N * r;
+    return N * rcp_d(D);
 }
 
 // theta fluxes through the left x-face, front y-face and bottom w-face of each cell (each face
