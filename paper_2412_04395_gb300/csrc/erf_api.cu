@@ -51,10 +51,11 @@ struct erf_handle {
     long long steps_done = 0;
     std::string err;
     // workspace arrays
-    double *hn, *hc, *hxf, *hyf, *gxc, *gyc, *g4x, *g4y;
+    double *hn, *hc, *hxf, *hyf, *gxh, *gyh, *g4xq, *g4yq;
     double *dzeta, *zetac, *s, *sc, *ds, *dzc, *delta2, *rdzeta, *rdzc, *knz, *knt;
     double *rho0, *th0, *p0;
     double *rH3 = nullptr, *rHx3 = nullptr, *rHy3 = nullptr, *rdzw3 = nullptr, *rdz2 = nullptr;
+    double *Hx3 = nullptr, *Hy3 = nullptr;
     // passive scalar (FP64 path): rho phi (stage state), its S^n copy, substep flux sums
     double *tphi = nullptr, *snphi = nullptr, *msx = nullptr, *msy = nullptr, *msz = nullptr;
     F5 st, sn, x, R;
@@ -153,8 +154,8 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
     erf_handle tmp;
     erf_handle *H = h ? h : &tmp;
     H->hn = cv.take<double>(nxy); H->hc = cv.take<double>(nxy); H->hxf = cv.take<double>(nxy);
-    H->hyf = cv.take<double>(nxy); H->gxc = cv.take<double>(nxy); H->gyc = cv.take<double>(nxy);
-    H->g4x = cv.take<double>(nxy); H->g4y = cv.take<double>(nxy);
+    H->hyf = cv.take<double>(nxy); H->gxh = cv.take<double>(nxy); H->gyh = cv.take<double>(nxy);
+    H->g4xq = cv.take<double>(nxy); H->g4yq = cv.take<double>(nxy);
     H->dzeta = cv.take<double>(nz); H->zetac = cv.take<double>(nz); H->s = cv.take<double>(nz + 1);
     H->sc = cv.take<double>(nz); H->ds = cv.take<double>(nz); H->dzc = cv.take<double>(nz + 1);
     H->delta2 = cv.take<double>(nz);
@@ -216,6 +217,7 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
     H->flux = cv.take<double>(3 * nw);   // theta, then each momentum component's fluxes (3 planes of nw)
     if (terr) {
         H->rH3 = cv.take<double>(nc); H->rHx3 = cv.take<double>(nc); H->rHy3 = cv.take<double>(nc);
+        H->Hx3 = cv.take<double>(nc); H->Hy3 = cv.take<double>(nc);
         H->rdzw3 = cv.take<double>(nc); H->rdz2 = cv.take<double>(nc);
     }
     if (c->tracer) {
@@ -248,9 +250,10 @@ static void fill_geo(erf_handle *h) {
     G.delta2 = h->delta2;
     G.rdzeta = h->rdzeta;
     G.rdzc = h->rdzc;
-    G.hc = h->hc; G.hxf = h->hxf; G.hyf = h->hyf; G.gxc = h->gxc; G.gyc = h->gyc; G.g4x = h->g4x; G.g4y = h->g4y;
+    G.hc = h->hc; G.hxf = h->hxf; G.hyf = h->hyf; G.gxh = h->gxh; G.gyh = h->gyh; G.g4xq = h->g4xq; G.g4yq = h->g4yq;
     G.rho0 = h->rho0; G.th0 = h->th0; G.p0 = h->p0;
     G.rH3 = h->rH3; G.rHx3 = h->rHx3; G.rHy3 = h->rHy3; G.rdzw3 = h->rdzw3; G.rdz2 = h->rdz2;
+    G.Hx3 = h->Hx3; G.Hy3 = h->Hy3;
     const erf_config &c = h->cfg;
     Phys &P = h->ph;
     P.g = c.gravity; P.f_cor = c.f_cor; P.u_g = c.u_g; P.v_g = c.v_g; P.Cs = c.Cs; P.Pr_t = c.Pr_t; P.nu = c.nu;
@@ -336,9 +339,9 @@ extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config 
         CK(cudaMemsetAsync(h->hn, 0, nxy * sizeof(double), st), "zero terrain");
     }
     CK(cudaMemsetAsync(h->kerr, 0, 4 * sizeof(unsigned), st), "zero error word");
-    launch_terrain(h->geo, h->hn, h->hc, h->hxf, h->hyf, h->gxc, h->gyc, h->g4x, h->g4y, st);
+    launch_terrain(h->geo, h->hn, h->hc, h->hxf, h->hyf, h->gxh, h->gyh, h->g4xq, h->g4yq, st);
     if (h->geo.terrain && h->rH3)
-        launch_terrain_recip(h->geo, h->rH3, h->rHx3, h->rHy3, h->rdzw3, h->rdz2, st);
+        launch_terrain_recip(h->geo, h->Hx3, h->Hy3, h->rH3, h->rHx3, h->rHy3, h->rdzw3, h->rdz2, st);
     launch_base_state(h->geo, cfg->n_knots, h->knz, h->knt, cfg->theta_s, cfg->brunt_N, cfg->p_s, cfg->gravity,
                       h->rho0, h->th0, h->p0, st);
     if (h->mixed) {

@@ -36,10 +36,10 @@ struct Geo {
     const double *hc;      // 4-node average of h (cell centre / w-face centre)
     const double *hxf;     // 2-node average of h along y (x-face)
     const double *hyf;     // 2-node average of h along x (y-face)
-    const double *gxc;     // (hc_i - hc_{i-1})/dx at x-faces
-    const double *gyc;     // (hc_j - hc_{j-1})/dy at y-faces
-    const double *g4x;     // 4th-order d hc/dx at cell centres
-    const double *g4y;
+    const double *gxh;     // half the slope (hc_i - hc_{i-1})/dx at x-faces
+    const double *gyh;     // half the slope (hc_j - hc_{j-1})/dy at y-faces
+    const double *g4xq;    // a quarter of the 4th-order d hc/dx at cell centres
+    const double *g4yq;
     // hydrostatic base state: [nz][ny][nx] with terrain, [nz] when flat
     const double *rho0, *th0, *p0;
     // reciprocal 3D metrics, terrain only ([nz][ny][nx]; null on flat grids): 1/H at cells,
@@ -47,6 +47,7 @@ struct Geo {
     // of the centred vertical difference at cells (kl = max(k-1, 0), ku = min(k+1, nz-1)).
     // An FP64 division costs ~10 FP64-pipe instructions, so each is taken once at init.
     const double *rH3, *rHx3, *rHy3, *rdzw3, *rdz2;
+    const double *Hx3, *Hy3;   // terrain only: the heights H at x- and y-faces themselves
 };
 
 struct Phys {
@@ -138,11 +139,12 @@ __device__ __forceinline__ int ij2(const Geo &g, int i, int j) { return wrapi(j,
 __device__ __forceinline__ double Hc(const Geo &g, int i, int j, int k) {
     return g.terrain ? g.dzeta[k] + g.ds[k] * g.hc[ij2(g, i, j)] : g.dzeta[k];
 }
+// face heights: 1D on flat grids, tabulated over terrain (a load instead of an FP64 FMA)
 __device__ __forceinline__ double Hx(const Geo &g, int i, int j, int k) {
-    return g.terrain ? g.dzeta[k] + g.ds[k] * g.hxf[ij2(g, i, j)] : g.dzeta[k];
+    return g.terrain ? __ldg(g.Hx3 + cixw(g, i, j, k)) : g.dzeta[k];
 }
 __device__ __forceinline__ double Hy(const Geo &g, int i, int j, int k) {
-    return g.terrain ? g.dzeta[k] + g.ds[k] * g.hyf[ij2(g, i, j)] : g.dzeta[k];
+    return g.terrain ? __ldg(g.Hy3 + cixw(g, i, j, k)) : g.dzeta[k];
 }
 // reciprocal heights: 1D tables on flat grids, 3D tables over terrain
 __device__ __forceinline__ double rHc(const Geo &g, int i, int j, int k) {
@@ -168,10 +170,12 @@ __device__ __forceinline__ double zc(const Geo &g, int i, int j, int k) {
 __device__ __forceinline__ double dzcw(const Geo &g, int i, int j, int k) {
     return g.terrain ? g.dzc[k] + (g.sc[k] - g.sc[k - 1]) * g.hc[ij2(g, i, j)] : g.dzc[k];
 }
-__device__ __forceinline__ double hxi_x(const Geo &g, int i, int j, int k) { return g.sc[k] * g.gxc[ij2(g, i, j)]; }
-__device__ __forceinline__ double heta_y(const Geo &g, int i, int j, int k) { return g.sc[k] * g.gyc[ij2(g, i, j)]; }
-__device__ __forceinline__ double hxi_w(const Geo &g, int i, int j, int k) { return g.s[k] * g.g4x[ij2(g, i, j)]; }
-__device__ __forceinline__ double heta_w(const Geo &g, int i, int j, int k) { return g.s[k] * g.g4y[ij2(g, i, j)]; }
+// h_xi / 2 and h_eta / 2 at x- and y-faces (the 1/2 of the two-point average they multiply), and
+// h_xi / 4, h_eta / 4 at w-faces (the 1/4 of the four-point averages of the metric shift)
+__device__ __forceinline__ double hxi_x2(const Geo &g, int i, int j, int k) { return g.sc[k] * g.gxh[ij2(g, i, j)]; }
+__device__ __forceinline__ double heta_y2(const Geo &g, int i, int j, int k) { return g.sc[k] * g.gyh[ij2(g, i, j)]; }
+__device__ __forceinline__ double hxi_w4(const Geo &g, int i, int j, int k) { return g.s[k] * g.g4xq[ij2(g, i, j)]; }
+__device__ __forceinline__ double heta_w4(const Geo &g, int i, int j, int k) { return g.s[k] * g.g4yq[ij2(g, i, j)]; }
 __device__ __forceinline__ long long bix(const Geo &g, int i, int j, int k) {
     return g.terrain ? cixw(g, i, j, k) : (long long)k;
 }

@@ -55,25 +55,32 @@ __global__ void k_terrain_avg(Geo g, const double *hn, double *hc, double *hxf, 
     hyf[n] = 0.5 * (h00 + h10);
 }
 
-__global__ void k_terrain_grad(Geo g, const double *hc, double *gxc, double *gyc, double *g4x, double *g4y) {
+__global__ void k_terrain_grad(Geo g, const double *hc, double *gxh, double *gyh, double *g4xq, double *g4yq) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.nxy) return;
     int i = n % g.nx, j = n / g.nx;
-    gxc[n] = (hc[n] - hc[ij2(g, i - 1, j)]) * g.rdx;
-    gyc[n] = (hc[n] - hc[ij2(g, i, j - 1)]) * g.rdy;
-    g4x[n] = (hc[ij2(g, i - 2, j)] - hc[ij2(g, i + 2, j)] + 8.0 * (hc[ij2(g, i + 1, j)] - hc[ij2(g, i - 1, j)])) / (12.0 * g.dx);
-    g4y[n] = (hc[ij2(g, i, j - 2)] - hc[ij2(g, i, j + 2)] + 8.0 * (hc[ij2(g, i, j + 1)] - hc[ij2(g, i, j - 1)])) / (12.0 * g.dy);
+    // stored as half the slope (and the 4th-order slope as a quarter): the pressure-gradient
+    // correction multiplies h_xi by the 1/2 of a two-point average, the metric shift by the 1/4 of
+    // a four-point average; both scalings are exact
+    gxh[n] = 0.5 * ((hc[n] - hc[ij2(g, i - 1, j)]) * g.rdx);
+    gyh[n] = 0.5 * ((hc[n] - hc[ij2(g, i, j - 1)]) * g.rdy);
+    g4xq[n] = 0.25 * ((hc[ij2(g, i - 2, j)] - hc[ij2(g, i + 2, j)] + 8.0 * (hc[ij2(g, i + 1, j)] - hc[ij2(g, i - 1, j)])) / (12.0 * g.dx));
+    g4yq[n] = 0.25 * ((hc[ij2(g, i, j - 2)] - hc[ij2(g, i, j + 2)] + 8.0 * (hc[ij2(g, i, j + 1)] - hc[ij2(g, i, j - 1)])) / (12.0 * g.dy));
 }
 
 // reciprocal 3D metrics over terrain (built once; the step kernels multiply by them)
-__global__ void k_terrain_recip(Geo g, double *rH3, double *rHx3, double *rHy3, double *rdzw3, double *rdz2) {
+__global__ void k_terrain_recip(Geo g, double *Hx3, double *Hy3, double *rH3, double *rHx3, double *rHy3,
+                                double *rdzw3, double *rdz2) {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= g.nc) return;
     int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
     double hc = g.hc[ij2(g, i, j)];
     rH3[c] = 1.0 / (g.dzeta[k] + g.ds[k] * hc);
-    rHx3[c] = 1.0 / (g.dzeta[k] + g.ds[k] * g.hxf[ij2(g, i, j)]);
-    rHy3[c] = 1.0 / (g.dzeta[k] + g.ds[k] * g.hyf[ij2(g, i, j)]);
+    const double hx = g.dzeta[k] + g.ds[k] * g.hxf[ij2(g, i, j)], hy = g.dzeta[k] + g.ds[k] * g.hyf[ij2(g, i, j)];
+    Hx3[c] = hx;
+    Hy3[c] = hy;
+    rHx3[c] = 1.0 / hx;
+    rHy3[c] = 1.0 / hy;
     rdzw3[c] = k >= 1 ? 1.0 / (g.dzc[k] + (g.sc[k] - g.sc[k - 1]) * hc) : 0.0;
     int kl = k == 0 ? 0 : k - 1, ku = k == g.nz - 1 ? g.nz - 1 : k + 1;
     rdz2[c] = ku > kl ? 1.0 / ((g.zetac[ku] + g.sc[ku] * hc) - (g.zetac[kl] + g.sc[kl] * hc)) : 0.0;
@@ -159,9 +166,10 @@ __global__ void k_init_faces(Geo g, const double *u, const double *v, const doub
 // h_xi <U> + h_eta <V> at w-face (i,j,k) with the 4-point averages of App. B (levels outside
 // the domain reflected)
 __device__ __forceinline__ double metric_shift(const Geo &g, const double *U, const double *V, int i, int j, int k) {
-    double au = 0.25 * (cval(g, U, i, j, k - 1) + cval(g, U, i + 1, j, k - 1) + cval(g, U, i, j, k) + cval(g, U, i + 1, j, k));
-    double av = 0.25 * (cval(g, V, i, j, k - 1) + cval(g, V, i, j + 1, k - 1) + cval(g, V, i, j, k) + cval(g, V, i, j + 1, k));
-    return hxi_w(g, i, j, k) * au + heta_w(g, i, j, k) * av;
+    // four-point sums; the 1/4 of the averages is in hxi_w4, heta_w4
+    double au = cval(g, U, i, j, k - 1) + cval(g, U, i + 1, j, k - 1) + cval(g, U, i, j, k) + cval(g, U, i + 1, j, k);
+    double av = cval(g, V, i, j, k - 1) + cval(g, V, i, j + 1, k - 1) + cval(g, V, i, j, k) + cval(g, V, i, j + 1, k);
+    return hxi_w4(g, i, j, k) * au + heta_w4(g, i, j, k) * av;
 }
 
 // walls: Omega = 0 at k = 0 (rho w = metric shift of the horizontal momenta) and rho w = 0 at the top
@@ -211,7 +219,7 @@ __global__ void k_stage_begin(Geo g, CF5 sn, CF5 st, F5 x, double *pp, double *p
                 av += sn.v[a] - st.v[a];
             }
         }
-        om -= hxi_w(g, i, j, k) * 0.25 * au + heta_w(g, i, j, k) * 0.25 * av;
+        om -= hxi_w4(g, i, j, k) * au + heta_w4(g, i, j, k) * av;
     }
     Om[n] = om;
 }
@@ -578,7 +586,7 @@ __global__ void k_rhs_u(Geo g, Phys ph, CF5 st, const double *pp, const double *
         int kl = k == 0 ? 0 : k - 1, ku = k == g.nz - 1 ? g.nz - 1 : k + 1;
         double d0 = (cval(g, pp, i, j, ku) - cval(g, pp, i, j, kl)) * rdz2c(g, i, j, k);
         double d1 = (cval(g, pp, i - 1, j, ku) - cval(g, pp, i - 1, j, kl)) * rdz2c(g, i - 1, j, k);
-        px -= 0.5 * hxi_x(g, i, j, k) * (d0 + d1);
+        px -= hxi_x2(g, i, j, k) * (d0 + d1);
     }
     r -= px;
     if (ph.f_cor != 0.0) {
@@ -602,7 +610,7 @@ __global__ void k_rhs_v(Geo g, Phys ph, CF5 st, const double *pp, const double *
         int kl = k == 0 ? 0 : k - 1, ku = k == g.nz - 1 ? g.nz - 1 : k + 1;
         double d0 = (cval(g, pp, i, j, ku) - cval(g, pp, i, j, kl)) * rdz2c(g, i, j, k);
         double d1 = (cval(g, pp, i, j - 1, ku) - cval(g, pp, i, j - 1, kl)) * rdz2c(g, i, j - 1, k);
-        py -= 0.5 * heta_y(g, i, j, k) * (d0 + d1);
+        py -= heta_y2(g, i, j, k) * (d0 + d1);
     }
     r -= py;
     if (ph.f_cor != 0.0) {
@@ -698,8 +706,8 @@ __global__ void k_sub_horiz(Geo g, Phys ph, const double *pi, const double *Tt, 
         double dc = (cval(g, Tt, i, j, ku) - cval(g, Tt, i, j, kl)) * rdz2c(g, i, j, k);
         double dxm = (cval(g, Tt, i - 1, j, ku) - cval(g, Tt, i - 1, j, kl)) * rdz2c(g, i - 1, j, k);
         double dym = (cval(g, Tt, i, j - 1, ku) - cval(g, Tt, i, j - 1, kl)) * rdz2c(g, i, j - 1, k);
-        gx -= 0.5 * hxi_x(g, i, j, k) * (dc + dxm);
-        gy -= 0.5 * heta_y(g, i, j, k) * (dc + dym);
+        gx -= hxi_x2(g, i, j, k) * (dc + dxm);
+        gy -= heta_y2(g, i, j, k) * (dc + dym);
     }
     // -gamma R_d pi^x: the face average's 1/2 is folded into the constant (exact, so the result
     // is unchanged)
@@ -990,14 +998,15 @@ struct ProfScope {
         __VA_ARGS__;                      \
     } while (0)
 
-void launch_terrain(const Geo &g, const double *hn, double *hc, double *hxf, double *hyf, double *gxc,
-                    double *gyc, double *g4x, double *g4y, cudaStream_t s) {
+void launch_terrain(const Geo &g, const double *hn, double *hc, double *hxf, double *hyf, double *gxh,
+                    double *gyh, double *g4xq, double *g4yq, cudaStream_t s) {
     LAUNCH("terrain_avg", s, k_terrain_avg<<<nblk(g.nxy, BS), BS, 0, s>>>(g, hn, hc, hxf, hyf));
-    LAUNCH("terrain_grad", s, k_terrain_grad<<<nblk(g.nxy, BS), BS, 0, s>>>(g, hc, gxc, gyc, g4x, g4y));
+    LAUNCH("terrain_grad", s, k_terrain_grad<<<nblk(g.nxy, BS), BS, 0, s>>>(g, hc, gxh, gyh, g4xq, g4yq));
 }
-void launch_terrain_recip(const Geo &g, double *rH3, double *rHx3, double *rHy3, double *rdzw3, double *rdz2,
+void launch_terrain_recip(const Geo &g, double *Hx3, double *Hy3, double *rH3, double *rHx3, double *rHy3,
+                          double *rdzw3, double *rdz2,
                           cudaStream_t s) {
-    LAUNCH("terrain_recip", s, k_terrain_recip<<<nblk(g.nc, BS), BS, 0, s>>>(g, rH3, rHx3, rHy3, rdzw3, rdz2));
+    LAUNCH("terrain_recip", s, k_terrain_recip<<<nblk(g.nc, BS), BS, 0, s>>>(g, Hx3, Hy3, rH3, rHx3, rHy3, rdzw3, rdz2));
 }
 void launch_base_state(const Geo &g, int n_knots, const double *kz, const double *kt, double theta_s, double N,
                        double p_s, double grav, double *rho0, double *th0, double *p0, cudaStream_t s) {

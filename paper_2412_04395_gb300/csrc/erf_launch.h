@@ -6,10 +6,10 @@
 
 namespace erfk {
 
-void launch_terrain(const Geo &g, const double *hn, double *hc, double *hxf, double *hyf, double *gxc,
-                    double *gyc, double *g4x, double *g4y, cudaStream_t s);
-void launch_terrain_recip(const Geo &g, double *rH3, double *rHx3, double *rHy3, double *rdzw3, double *rdz2,
-                          cudaStream_t s);
+void launch_terrain(const Geo &g, const double *hn, double *hc, double *hxf, double *hyf, double *gxh,
+                    double *gyh, double *g4xq, double *g4yq, cudaStream_t s);
+void launch_terrain_recip(const Geo &g, double *Hx3, double *Hy3, double *rH3, double *rHx3, double *rHy3,
+                          double *rdzw3, double *rdz2, cudaStream_t s);
 void launch_base_state(const Geo &g, int n_knots, const double *kz, const double *kt, double theta_s, double N,
                        double p_s, double grav, double *rho0, double *th0, double *p0, cudaStream_t s);
 void launch_set_initial(const Geo &g, const double *dth, const double *u, const double *v, const double *w,
