@@ -35,11 +35,11 @@ UNIT = "cell-updates/s"
 # if every input is read once and every output written once, and the floating-point operations
 # of the formulas (FMA = 2).  unit: "cell" (nx*ny*nz) or "wface" (nx*ny*(nz+1)).
 KERNEL_MODEL = {
-    "flux_theta":  {"unit": "wface", "words": 7, "flops": 225},
-    "sub_expl":    {"unit": "cell", "words": 18, "flops": 67},
+    "flux_theta":  {"unit": "wface", "words": 7, "flops": 210},
+    "sub_expl":    {"unit": "cell", "words": 20, "flops": 56},
     "sub_col":     {"unit": "cell", "words": 11, "flops": 12},
     "sub_fin":     {"unit": "cell", "words": 10, "flops": 18},
-    "sub_horiz":   {"unit": "cell", "words": 9, "flops": 26},
+    "sub_horiz":   {"unit": "cell", "words": 9, "flops": 30},
     "flux_u":      {"unit": "wface", "words": 7, "flops": 63},
     "flux_v":      {"unit": "wface", "words": 7, "flops": 63},
     "flux_w":      {"unit": "wface", "words": 7, "flops": 63},
@@ -56,21 +56,32 @@ KERNEL_MODEL = {
 # DRAM bytes per unit from an ncu capture of the kernel as it stands (dram__bytes_read.sum +
 # dram__bytes_write.sum of a 128^3 hill-bubble launch / its units; profiles/ has the summary),
 # scaled to the benchmark's units.  A kernel missing here reports traffic null.
-KERNEL_TRAFFIC_PER_UNIT = {"flux_theta": 39.7}
+KERNEL_TRAFFIC_PER_UNIT = {"flux_theta": 39.7, "sub_expl": 161.6}
 # mixed path: algorithmic bytes per cell per launch (FP32 fields, FP64 LU factors and d');
 # these kernels are bound by HBM or latency, so their roofline is in GB/s
 KERNEL_MODEL_MIXED = {
-    "mx_sub_col":     {"unit": "cell", "bytes": 80},
+    "mx_sub_vert":    {"unit": "cell", "bytes": 96},
+    "mx_sub_col":     {"unit": "cell", "bytes": 72},
     "mx_sub_expl":    {"unit": "cell", "bytes": 52},
     "mx_sub_fin":     {"unit": "cell", "bytes": 32},
     "mx_sub_horiz":   {"unit": "cell", "bytes": 32},
-    "mx_closure_mlp": {"unit": "cell", "bytes": 60},
-    "mx_rhs_cells":   {"unit": "cell", "bytes": 56},
-    "mx_rhs_u":       {"unit": "cell", "bytes": 44},
-    "mx_rhs_v":       {"unit": "cell", "bytes": 44},
-    "mx_rhs_w":       {"unit": "wface", "bytes": 40},
-    "mx_tri_build":   {"unit": "cell", "bytes": 60},
-    "mx_stage_begin": {"unit": "wface", "bytes": 60},
+    "mx_closure_mlp": {"unit": "cell", "bytes": 56},
+    "mx_cl_edges":    {"unit": "wface", "bytes": 24},
+    "mx_cl_div":      {"unit": "wface", "bytes": 68},
+    "mx_sgs_edges":   {"unit": "wface", "bytes": 24},
+    "mx_sgs_mu":      {"unit": "cell", "bytes": 44},
+    "mx_sgs_tau":     {"unit": "wface", "bytes": 28},
+    "mx_sgs_div":     {"unit": "wface", "bytes": 64},
+    "mx_flux_theta":  {"unit": "wface", "bytes": 28},
+    "mx_flux_u":      {"unit": "wface", "bytes": 28},
+    "mx_flux_v":      {"unit": "wface", "bytes": 28},
+    "mx_flux_w":      {"unit": "wface", "bytes": 28},
+    "mx_rhs_cells":   {"unit": "cell", "bytes": 32},
+    "mx_rhs_u":       {"unit": "cell", "bytes": 28},
+    "mx_rhs_v":       {"unit": "cell", "bytes": 28},
+    "mx_rhs_w":       {"unit": "wface", "bytes": 24},
+    "mx_tri_build":   {"unit": "cell", "bytes": 48},
+    "mx_stage_begin": {"unit": "wface", "bytes": 76},
     "mx_prep":        {"unit": "wface", "bytes": 36},
     "mx_stage_end":   {"unit": "wface", "bytes": 60},
 }
