@@ -350,6 +350,9 @@ def run_ours(args):
     wl = workload(args)
     d = Dycore(wl, device=f"cuda:{local}")
     d.erf_set_initial(wl.dtheta, wl.u, wl.v, wl.w)
+    if args.column_fusion != -1:
+        from paper_2412_04395_gb300.erf import ERF_OPT_COLUMN_FUSION
+        d.erf_set_option(ERF_OPT_COLUMN_FUSION, args.column_fusion)
     if args.closure == "learned":
         blob, _ = closure_blob(wl, d)
         d.erf_set_closure_weights(blob)
@@ -487,6 +490,8 @@ def main():
                     help="learned: the MLP closure (convective_abl with --precision mixed)")
     ap.add_argument("--grid", type=int, nargs=3, default=None,
                     help="nx ny nz of a smaller window of the workload (profiling runs only)")
+    ap.add_argument("--column-fusion", type=int, default=-1, choices=[-1, 0, 1],
+                    help="explicit vertical substep part inside the column sweep: -1 by column count")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

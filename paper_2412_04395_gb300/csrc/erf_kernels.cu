@@ -4,10 +4,13 @@
 // index wrap, walls by reflected ghost levels.  The kernel sequence of one stage is
 //   stage_begin (EOS: p', pi, theta; perturbations X'' = S^n - S^t; Omega'')
 //   prep        (face velocities, mass fluxes, rho*Omega)
-//   sgs_mu      (eddy viscosity, only with a closure / MOST)
-//   rhs_cells, rhs_u, rhs_v, rhs_w   (slow tendencies R^t)
-//   tri_build   (per-column LU of the vertical acoustic system, fixed for the stage)
-//   n_s x { sub_horiz, sub_vert }   (App. C substeps)
+//   flux_theta + rhs_cells, flux_u + rhs_u, flux_v + rhs_v, flux_w + rhs_w   (slow tendencies
+//               R^t: each advective face flux once, then its divergence with the pressure
+//               gradient, buoyancy and Coriolis)
+//   sgs_edges, sgs_mu, sgs_tau, sgs_div   (subgrid terms, with a closure or MOST)
+//   tri_build   (per column: coefficients of the vertical acoustic system and their LU
+//               factors, fixed for the stage)
+//   n_s x { sub_horiz, sub_expl, sub_col, sub_fin }   (App. C substeps)
 //   stage_end   (S^t <- S^t + X'')
 #include "erf_dev.cuh"
 #include "erf_launch.h"

@@ -803,7 +803,7 @@ __global__ void k_mx_tri_build(Geo g, MxBase mb, Phys ph, const float *dr, const
         float b = 1.f - P * E * thw_k * rHk + Q * E * thw_k * rHm + Gg * E * (rHk - rHm);
         float cc = E * (P * thw_p - Gg) * rHk;
         double m = (double)b - (double)a * cp_prev;
-        double im = 1.0 / m;
+        double im = rcp_d(m);
         double cpk = (double)cc * im;
         tr.a[c] = (double)a; tr.cp[c] = cpk; tr.im[c] = im; tr.P[c] = P; tr.Q[c] = Q;
         cp_prev = cpk;
