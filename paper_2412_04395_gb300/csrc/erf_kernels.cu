@@ -436,20 +436,22 @@ __global__ void k_sgs_div(Geo g, Phys ph, const double *mu, const double *t11, c
 // ------------------------------------------------------------------ slow tendencies
 
 // WENO5-JS / WENO5-Z face value in FP64 (same candidates and weights as weno5<T>), arranged for
-// GB300's FP64 rate: the three candidate values and the six indicator terms are formed from the
-// four first differences of the stencil, the indicators carry a common factor 12/13, and the
-// normalisation takes one reciprocal (rcp_d) instead of a division.
+// GB300's FP64 rate: the middle candidate and the six indicator terms are formed from the four
+// first differences of the stencil, the other candidates enter as differences from the middle
+// one, the indicators carry a common factor 12/13, and the normalisation takes one reciprocal
+// (rcp_d) instead of a division.
 __device__ __forceinline__ double weno5_d(const double *q, double s, int zflag) {
     double a, b, c, d, e;   // v_{-2}, v_{-1}, v_0, v_1, v_2 on the upwind side
     if (s >= 0.0) { a = q[0]; b = q[1]; c = q[2]; d = q[3]; e = q[4]; }
     else { a = q[5]; b = q[4]; c = q[3]; d = q[2]; e = q[1]; }
     const double d1 = a - b, d2 = b - c, d3 = c - d, d4 = d - e;
-    const double p0 = fma(1.0 / 3.0, d1, fma(-5.0 / 6.0, d2, c));   // (2a - 7b + 11c)/6
     const double p1 = fma(-1.0 / 6.0, d2, fma(-1.0 / 3.0, d3, c));  // (-b + 5c + 2d)/6
-    const double p2 = fma(-2.0 / 3.0, d3, fma(1.0 / 6.0, d4, c));   // (2c + 5d - e)/6
     const double t0 = d1 - d2, u0 = fma(-3.0, d2, d1);               // a - 2b + c, a - 4b + 3c
     const double t1 = d2 - d3, u1 = d2 + d3;                         // b - 2c + d, b - d
     const double t2 = d3 - d4, u2 = fma(3.0, d3, -d4);               // c - 2d + e, 3c - 4d + e
+    // the other two candidates through their differences from p1: p0 - p1 = (t0 - t1)/3 and
+    // p2 - p1 = (t1 - t2)/6, so that the value is p1 + (w0 (p0 - p1) + w2 (p2 - p1)) / sum w
+    const double q0 = t0 - t1, q2 = t1 - t2;
     // smoothness indicators 13/12 t^2 + 1/4 u^2 and eps = 1e-6, both scaled by 12/13: the weights
     // are homogeneous in (eps + beta), so the scheme is unchanged and each indicator takes three
     // FP64 operations instead of four
@@ -458,23 +460,24 @@ __device__ __forceinline__ double weno5_d(const double *q, double s, int zflag) 
     const double b1 = fma(t1, t1, (k3 * u1) * u1);
     const double b2 = fma(t2, t2, (k3 * u2) * u2);
     constexpr double eps = 1.0e-6 * (12.0 / 13.0);
-    double w0, w1, w2;
     if (zflag) {
         double tau = fabs(b0 - b2);
         double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
-        w0 = 0.1 * (e0 + tau) * e1 * e2;
-        w1 = 0.6 * (e1 + tau) * e0 * e2;
-        w2 = 0.3 * (e2 + tau) * e0 * e1;
-    } else {
-        double e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
-        double f01 = e0 * e1, f02 = e0 * e2, f12 = e1 * e2;
-        w0 = 0.1 * f12 * f12;
-        w1 = 0.6 * f02 * f02;
-        w2 = 0.3 * f01 * f01;
+        double w0 = 0.1 * (e0 + tau) * e1 * e2;
+        double w1 = 0.6 * (e1 + tau) * e0 * e2;
+        double w2 = 0.3 * (e2 + tau) * e0 * e1;
+        double N = fma(w0, (1.0 / 3.0) * q0, w2 * ((1.0 / 6.0) * q2));
+        return fma(N, rcp_d(w0 + w1 + w2), p1);
     }
-    const double N = fma(w0, p0, fma(w1, p1, w2 * p2));
-    const double D = w0 + w1 + w2;
-    return N * rcp_d(D);
+    // JS: w_r = d_r / (eps + b_r)^2 scaled by the product of all (eps + b)^2, i.e. d_r g_r with
+    // g0 = (e1 e2)^2, g1 = (e0 e2)^2, g2 = (e0 e1)^2; the linear weights 1/10, 6/10, 3/10 and the
+    // 1/3, 1/6 of the differences fold into the constants
+    const double e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
+    const double f01 = e0 * e1, f02 = e0 * e2, f12 = e1 * e2;
+    const double g0 = f12 * f12, g1 = f02 * f02, g2 = f01 * f01;
+    const double D = fma(0.1, g0, fma(0.6, g1, 0.3 * g2));
+    const double N = fma(g0 * (0.1 / 3.0), q0, (g2 * (0.3 / 6.0)) * q2);
+    return fma(N, rcp_d(D), p1);
 }
 
 // theta fluxes through the left x-face, front y-face and bottom w-face of each cell (each face
