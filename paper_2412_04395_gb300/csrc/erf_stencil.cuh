@@ -20,41 +20,51 @@ __device__ __forceinline__ T upwind5(const T *q, T s) {
 }
 template <class T>
 __device__ __forceinline__ T sgnT(T x) { return x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0)); }
+// correctly rounded reciprocal (FP32: one MUFU operation and its refinement instead of a division)
+__device__ __forceinline__ float rcp_t(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
 
-// WENO5-JS (Jiang & Shu 1996) or WENO5-Z (Borges et al. 2008) face value; upwind side s >= 0
-// is the left.  The nonlinear weights are normalised with one division.
+// WENO5-JS (Jiang & Shu 1996) or WENO5-Z (Borges et al. 2008) face value in FP32 (the
+// mixed-precision kernels); upwind side s >= 0 is the left.  The three candidates
+// p0 = (2a - 7b + 11c)/6, p1 = (-b + 5c + 2d)/6, p2 = (2c + 5d - e)/6 enter as
+// p1 + (w0 (p0 - p1) + w2 (p2 - p1)) / sum w, with p0 - p1 = (t0 - t1)/3 and
+// p2 - p1 = (t1 - t2)/6 from the indicator terms; the indicators 13/12 t^2 + 1/4 u^2 and
+// eps = 1e-6 carry a common factor 12/13 (the weights are homogeneous in eps + beta); the
+// normalisation takes one correctly rounded reciprocal.
 template <class T>
 __device__ __forceinline__ T weno5(const T *q, T s, int zflag) {
     T a, b, c, d, e;   // v_{-2}, v_{-1}, v_0, v_1, v_2 on the upwind side
     if (s >= T(0)) { a = q[0]; b = q[1]; c = q[2]; d = q[3]; e = q[4]; }
     else { a = q[5]; b = q[4]; c = q[3]; d = q[2]; e = q[1]; }
-    const T eps = T(1.0e-6);
-    T p0 = (T(2) * a - T(7) * b + T(11) * c) * T(1.0 / 6.0);
-    T p1 = (-b + T(5) * c + T(2) * d) * T(1.0 / 6.0);
-    T p2 = (T(2) * c + T(5) * d - e) * T(1.0 / 6.0);
-    T t0 = a - T(2) * b + c, u0 = a - T(4) * b + T(3) * c;
-    T t1 = b - T(2) * c + d, u1 = b - d;
-    T t2 = c - T(2) * d + e, u2 = T(3) * c - T(4) * d + e;
-    T b0 = T(13.0 / 12.0) * t0 * t0 + T(0.25) * u0 * u0;
-    T b1 = T(13.0 / 12.0) * t1 * t1 + T(0.25) * u1 * u1;
-    T b2 = T(13.0 / 12.0) * t2 * t2 + T(0.25) * u2 * u2;
-    T w0, w1, w2;
+    const T d1 = a - b, d2 = b - c, d3 = c - d, d4 = d - e;
+    const T p1 = fma(T(-1.0 / 6.0), d2, fma(T(-1.0 / 3.0), d3, c));
+    const T t0 = d1 - d2, u0 = fma(T(-3), d2, d1);
+    const T t1 = d2 - d3, u1 = d2 + d3;
+    const T t2 = d3 - d4, u2 = fma(T(3), d3, -d4);
+    const T q0 = t0 - t1, q2 = t1 - t2;
+    const T k3 = T(3.0 / 13.0), eps = T(1.0e-6 * (12.0 / 13.0));
+    const T b0 = fma(t0, t0, (k3 * u0) * u0);
+    const T b1 = fma(t1, t1, (k3 * u1) * u1);
+    const T b2 = fma(t2, t2, (k3 * u2) * u2);
+    T N, D;
     if (zflag) {
         // alpha_k = d_k (1 + tau/(b_k + eps)) scaled by prod (b_j + eps)
-        T tau = fabs(b0 - b2);
-        T e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
-        w0 = T(0.1) * (e0 + tau) * e1 * e2;
-        w1 = T(0.6) * (e1 + tau) * e0 * e2;
-        w2 = T(0.3) * (e2 + tau) * e0 * e1;
+        const T tau = fabs(b0 - b2);
+        const T e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+        const T w0 = T(0.1) * (e0 + tau) * e1 * e2;
+        const T w1 = T(0.6) * (e1 + tau) * e0 * e2;
+        const T w2 = T(0.3) * (e2 + tau) * e0 * e1;
+        N = fma(w0, T(1.0 / 3.0) * q0, w2 * (T(1.0 / 6.0) * q2));
+        D = w0 + w1 + w2;
     } else {
         // alpha_k = d_k / (eps + b_k)^2 scaled by prod (eps + b_j)^2
-        T e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
-        T f01 = e0 * e1, f02 = e0 * e2, f12 = e1 * e2;
-        w0 = T(0.1) * f12 * f12;
-        w1 = T(0.6) * f02 * f02;
-        w2 = T(0.3) * f01 * f01;
+        const T e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
+        const T f01 = e0 * e1, f02 = e0 * e2, f12 = e1 * e2;
+        const T g0 = f12 * f12, g1 = f02 * f02, g2 = f01 * f01;
+        D = fma(T(0.1), g0, fma(T(0.6), g1, T(0.3) * g2));
+        N = fma(g0 * T(0.1 / 3.0), q0, (g2 * T(0.3 / 6.0)) * q2);
     }
-    return (w0 * p0 + w1 * p1 + w2 * p2) / (w0 + w1 + w2);
+    return fma(N, rcp_t(D), p1);
 }
 
 }  // namespace erfk
