@@ -318,8 +318,9 @@ def _time_form(wl, steps, out, name):
 def precision_comparison(args):
     """FP64 Smagorinsky vs FP32 perturbations (Smagorinsky) vs FP32 + learned closure (BF16
     tensor-core inference), each timed alone on the same GB300: the coarse convective ABL
-    (default 2048 x 2048 x 160 at 40 m, 671 M cells) and the neutral ABL 1024 x 1024 x 128 at
-    10 m (FP64 vs FP32)."""
+    (default 2048 x 2048 x 160 at 40 m, 671 M cells), the neutral ABL 1024 x 1024 x 128 at 10 m
+    and, as context, the paper's scaling workload 512 x 512 x 256 at 4 m with upwind-3 (FP64 vs
+    FP32)."""
     from paper_2412_04395_gb300 import workloads as W
     nx, ny, nz = args.cmp_grid
     base = W.convective_abl(nx=nx, ny=ny, nz=nz, dx=40.0)
@@ -339,6 +340,15 @@ def precision_comparison(args):
         _time_form(nb.with_(precision=W.PREC_MIXED32), args.cmp_steps, neu, "fp32")
         neu["fp32_over_fp64"] = neu["fp32"]["value"] / neu["fp64"]["value"]
         out["neutral_abl"] = neu
+    if args.paper_grid[0] > 0:
+        # context: the paper's scaling workload (Sec. 5.2), upwind-3 + Smagorinsky at 4 m
+        px, py, pz = args.paper_grid
+        pw = W.paper_scaling(nx=px, ny=py, nz=pz)
+        pap = {"workload": f"paper_scaling {px}x{py}x{pz} at 4 m, upwind-3, ns=10, Smagorinsky, MOST"}
+        _time_form(pw.with_(precision=W.PREC_FP64), fp64_steps, pap, "fp64")
+        _time_form(pw.with_(precision=W.PREC_MIXED32), args.cmp_steps, pap, "fp32")
+        pap["fp32_over_fp64"] = pap["fp32"]["value"] / pap["fp64"]["value"]
+        out["paper_scaling"] = pap
     return out
 
 
@@ -484,6 +494,8 @@ def main():
                     help="grid of the precision comparison (convective ABL at 40 m)")
     ap.add_argument("--neutral-grid", type=int, nargs=3, default=[1024, 1024, 128],
                     help="grid of the neutral-ABL FP64/FP32 line (0 0 0 skips it)")
+    ap.add_argument("--paper-grid", type=int, nargs=3, default=[512, 512, 256],
+                    help="grid of the paper's scaling workload (upwind-3) FP64/FP32 line (0 0 0 skips it)")
     ap.add_argument("--cmp-steps", type=int, default=8, help="timed steps per FP32 form (FP64: a quarter); 0 skips")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--closure", default="default", choices=["default", "learned"],

@@ -60,7 +60,7 @@ typedef enum { ERF_F64 = 0, ERF_F32 = 1 } erf_dtype;
 typedef enum { ERF_PREC_FP64 = 0, ERF_PREC_MIXED32 = 1 } erf_precision;
 typedef enum { ERF_CLOSURE_NONE = 0, ERF_CLOSURE_CONST_NU = 1, ERF_CLOSURE_SMAGORINSKY = 2,
                ERF_CLOSURE_LEARNED = 3 /* mixed precision only */ } erf_closure;
-typedef enum { ERF_SCAL_WENO5_JS = 0, ERF_SCAL_WENO5_Z = 1 } erf_scalar_scheme;
+typedef enum { ERF_SCAL_WENO5_JS = 0, ERF_SCAL_WENO5_Z = 1, ERF_SCAL_UPWIND3 = 3 } erf_scalar_scheme;
 typedef enum { ERF_SURFACE_SLIP = 0, ERF_SURFACE_MOST = 1 } erf_surface;
 
 /* Grid (Sec. 3.4, App. A/B).  Host pointers, read during erf_init_grid only. */
@@ -83,7 +83,8 @@ typedef struct {
     int32_t substep_mode;           /* 0 = semi-implicit substeps (App. C), 1 = none (plain RK3, Sec. 3.1) */
     double beta_s;                  /* off-centering, beta_1 = (1-beta_s)/2, beta_2 = (1+beta_s)/2 (App. C) */
     double beta_d;                  /* divergence damping of the forward-predicted pressure (Sec. 3.1) */
-    int32_t scal_adv;               /* erf_scalar_scheme (Sec. 3.6); momenta always upwind-5 */
+    int32_t scal_adv;               /* erf_scalar_scheme (Sec. 3.6): WENO5-JS, WENO5-Z or the linear
+                                       third-order upwind interpolant */
     int32_t closure;                /* erf_closure (Sec. 2.3) */
     double Cs, Pr_t, nu;            /* Smagorinsky constant, turbulent Prandtl number, constant nu [m^2/s] */
     int32_t precision;              /* erf_precision */
@@ -98,6 +99,8 @@ typedef struct {
                                        substeps of each stage, with the stage-averaged momenta that
                                        advanced rho; FP64, or whole FP32 values on the mixed path);
                                        0 = none */
+    int32_t mom_adv;                /* momentum interpolant order (Sec. 3.6): 5 (or 0) upwind-5,
+                                       3 upwind-3 (the paper's scaling workload, Sec. 5.2) */
 } erf_config;
 
 /* Diagnostics (Sec. 4.1.2: mass conserved to machine precision). */

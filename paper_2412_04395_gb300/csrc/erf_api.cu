@@ -123,7 +123,8 @@ static erf_status validate(const erf_grid_desc *g, const erf_config *c, std::str
         msg = "the learned closure runs on the mixed-precision path";
         return ERF_EUNSUPPORTED;
     }
-    if (c->scal_adv < 0 || c->scal_adv > 1) { msg = "scal_adv out of range"; return ERF_EINVAL; }
+    if (c->scal_adv != 0 && c->scal_adv != 1 && c->scal_adv != 3) { msg = "scal_adv must be 0, 1 or 3"; return ERF_EINVAL; }
+    if (c->mom_adv != 0 && c->mom_adv != 3 && c->mom_adv != 5) { msg = "mom_adv must be 0, 3 or 5"; return ERF_EINVAL; }
     if (c->surface < 0 || c->surface > 1) { msg = "surface out of range"; return ERF_EINVAL; }
     if (c->precision != ERF_PREC_FP64 && c->precision != ERF_PREC_MIXED32) { msg = "precision out of range"; return ERF_EINVAL; }
     if (c->n_knots < 0 || (c->n_knots > 0 && (!c->knot_z || !c->knot_theta))) { msg = "bad sounding knots"; return ERF_EINVAL; }
@@ -263,6 +264,7 @@ static void fill_geo(erf_handle *h) {
     P.b2 = 0.5 * (1.0 + c.beta_s);
     P.b1h = 0.5 * P.b1;
     P.closure = c.closure; P.surface = c.surface; P.scal_adv = c.scal_adv;
+    P.mom3 = c.mom_adv == 3 ? 1 : 0;
 }
 
 extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config *cfg, void *d_workspace,

@@ -480,25 +480,29 @@ __device__ __forceinline__ double weno5_d(const double *q, double s, int zflag) 
     return fma(N, rcp_d(D), p1);
 }
 
+// face value of an advected scalar: WENO5-JS, WENO5-Z or the linear upwind-3 interpolant
+__device__ __forceinline__ double scal_face_d(const double *q, double s, int scheme) {
+    return scheme == 3 ? upwind3(q, s) : weno5_d(q, s, scheme == 1);
+}
+
 // theta fluxes through the left x-face, front y-face and bottom w-face of each cell (each face
 // once): normal mass flux x WENO5(theta); walls carry none
 __global__ void k_flux_theta(Geo g, Phys ph, Prep pr, const double *th, double *fx, double *fy, double *fz) {
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= g.nw) return;
     int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / g.nxy);
-    int zf = ph.scal_adv == 1;
     double q[6];
     if (k < g.nz) {
         double mx = pr.mfx[n], my = pr.mfy[n];
         for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i - 3 + m, j, k);
-        fx[n] = mx * weno5_d(q, sgnd(mx), zf);
+        fx[n] = mx * scal_face_d(q, sgnd(mx), ph.scal_adv);
         for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i, j - 3 + m, k);
-        fy[n] = my * weno5_d(q, sgnd(my), zf);
+        fy[n] = my * scal_face_d(q, sgnd(my), ph.scal_adv);
     }
     if (k == 0 || k == g.nz) { fz[n] = 0.0; return; }
     double om = pr.rom[n];
     for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i, j, k - 3 + m);
-    fz[n] = om * weno5_d(q, sgnd(om), zf);
+    fz[n] = om * scal_face_d(q, sgnd(om), ph.scal_adv);
 }
 
 // continuity and potential temperature (Eq. con, Eq. theta): flux divergence / cell height
@@ -524,56 +528,56 @@ __global__ void k_rhs_cells(Geo g, Prep pr, const double *fx, const double *fy, 
     const long long n = ((long long)k * g.ny + j) * g.nx + i;
 // u: x-flux at the cell centre (i,j,k), y-flux at the xy-edge (x-face i, y-face j), z-flux at the
 // xz-edge (x-face i, w-face k; zero on the walls)
-__global__ void k_flux_u(Geo g, Prep pr, double *fx, double *fy, double *fz) {
+__global__ void k_flux_u(Geo g, Prep pr, int mom3, double *fx, double *fy, double *fz) {
     CELL3D_W();
     double q[6];
     if (k < g.nz) {
         double adv = 0.5 * (__ldg(pr.mfx + n) + cval(g, pr.mfx, i + 1, j, k));
         for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.ux, i - 2 + m, j, k);
-        fx[n] = adv * upwind5(q, sgnd(adv));
+        fx[n] = adv * upwind_mom(q, sgnd(adv), mom3);
         adv = 0.5 * (cval(g, pr.mfy, i - 1, j, k) + __ldg(pr.mfy + n));
         for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.ux, i, j - 3 + m, k);
-        fy[n] = adv * upwind5(q, sgnd(adv));
+        fy[n] = adv * upwind_mom(q, sgnd(adv), mom3);
     }
     if (k == 0 || k == g.nz) { fz[n] = 0.0; return; }
     double adv = 0.5 * (__ldg(pr.rom + cixw(g, i - 1, j, k)) + __ldg(pr.rom + n));
     for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.ux, i, j, k - 3 + m);
-    fz[n] = adv * upwind5(q, sgnd(adv));
+    fz[n] = adv * upwind_mom(q, sgnd(adv), mom3);
 }
 // v: x-flux at the xy-edge (x-face i, y-face j), y-flux at the cell centre, z-flux at the yz-edge
-__global__ void k_flux_v(Geo g, Prep pr, double *fx, double *fy, double *fz) {
+__global__ void k_flux_v(Geo g, Prep pr, int mom3, double *fx, double *fy, double *fz) {
     CELL3D_W();
     double q[6];
     if (k < g.nz) {
         double adv = 0.5 * (cval(g, pr.mfx, i, j - 1, k) + __ldg(pr.mfx + n));
         for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.vy, i - 3 + m, j, k);
-        fx[n] = adv * upwind5(q, sgnd(adv));
+        fx[n] = adv * upwind_mom(q, sgnd(adv), mom3);
         adv = 0.5 * (__ldg(pr.mfy + n) + cval(g, pr.mfy, i, j + 1, k));
         for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.vy, i, j - 2 + m, k);
-        fy[n] = adv * upwind5(q, sgnd(adv));
+        fy[n] = adv * upwind_mom(q, sgnd(adv), mom3);
     }
     if (k == 0 || k == g.nz) { fz[n] = 0.0; return; }
     double adv = 0.5 * (__ldg(pr.rom + cixw(g, i, j - 1, k)) + __ldg(pr.rom + n));
     for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.vy, i, j, k - 3 + m);
-    fz[n] = adv * upwind5(q, sgnd(adv));
+    fz[n] = adv * upwind_mom(q, sgnd(adv), mom3);
 }
 // w: x-flux at the xz-edge (x-face i, w-face k), y-flux at the yz-edge (both [nz+1] planes, zero on
 // the walls), z-flux at the cell centre (i,j,k) ([nz] planes)
-__global__ void k_flux_w(Geo g, Prep pr, double *fx, double *fy, double *fz) {
+__global__ void k_flux_w(Geo g, Prep pr, int mom3, double *fx, double *fy, double *fz) {
     CELL3D_W();
     double q[6];
     if (k < g.nz) {
         double adv = 0.5 * (__ldg(pr.rom + n) + __ldg(pr.rom + n + g.nxy));
         for (int m = 0; m < 6; ++m) q[m] = wval(g, pr.wz, i, j, k - 2 + m);
-        fz[n] = adv * upwind5(q, sgnd(adv));
+        fz[n] = adv * upwind_mom(q, sgnd(adv), mom3);
     }
     if (k == 0 || k == g.nz) { fx[n] = 0.0; fy[n] = 0.0; return; }
     double adv = 0.5 * (cval(g, pr.mfx, i, j, k - 1) + __ldg(pr.mfx + n));
     for (int m = 0; m < 6; ++m) q[m] = __ldg(pr.wz + cixw(g, i - 3 + m, j, k));
-    fx[n] = adv * upwind5(q, sgnd(adv));
+    fx[n] = adv * upwind_mom(q, sgnd(adv), mom3);
     adv = 0.5 * (cval(g, pr.mfy, i, j, k - 1) + __ldg(pr.mfy + n));
     for (int m = 0; m < 6; ++m) q[m] = __ldg(pr.wz + cixw(g, i, j - 3 + m, k));
-    fy[n] = adv * upwind5(q, sgnd(adv));
+    fy[n] = adv * upwind_mom(q, sgnd(adv), mom3);
 }
 
 // x-momentum at x-face (i,j,k): upwind-5 advection (reading R5), terrain pressure gradient
@@ -847,20 +851,19 @@ __global__ void k_tracer_flux(Geo g, Phys ph, const double *ru, const double *rv
                               const double *phi, const double *msx, const double *msy, const double *msz,
                               double rns, double *fx, double *fy, double *fz) {
     CELL3D_W();
-    const int zf = ph.scal_adv == 1;
     double q[6];
     if (k < g.nz) {
         double mx = Hx(g, i, j, k) * ru[n] + msx[n] * rns;
         for (int m = 0; m < 6; ++m) q[m] = cval(g, phi, i - 3 + m, j, k);
-        fx[n] = mx * weno5_d(q, sgnd(mx), zf);
+        fx[n] = mx * scal_face_d(q, sgnd(mx), ph.scal_adv);
         double my = Hy(g, i, j, k) * rv[n] + msy[n] * rns;
         for (int m = 0; m < 6; ++m) q[m] = cval(g, phi, i, j - 3 + m, k);
-        fy[n] = my * weno5_d(q, sgnd(my), zf);
+        fy[n] = my * scal_face_d(q, sgnd(my), ph.scal_adv);
     }
     if (k == 0 || k == g.nz) { fz[n] = 0.0; return; }
     double mz = rom[n] + msz[n] * rns;
     for (int m = 0; m < 6; ++m) q[m] = cval(g, phi, i, j, k - 3 + m);
-    fz[n] = mz * weno5_d(q, sgnd(mz), zf);
+    fz[n] = mz * scal_face_d(q, sgnd(mz), ph.scal_adv);
 }
 __global__ void k_tracer_update(Geo g, const double *snphi, const double *fx, const double *fy, const double *fz,
                                 double adt, double *rphi) {
@@ -1046,11 +1049,11 @@ void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, double *pp, const dou
     // momentum: fluxes of each component into the shared buffer, then its divergence
     const dim3 g3w((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)(g.nz + 1));
     double *ax = flux, *ay = flux + g.nw, *az = flux + 2 * g.nw;
-    LAUNCH("flux_u", s, k_flux_u<<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
+    LAUNCH("flux_u", s, k_flux_u<<<g3w, 128, 0, s>>>(g, pr, ph.mom3, ax, ay, az));
     LAUNCH("rhs_u", s, k_rhs_u<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, st, pp, ax, ay, az, R.u));
-    LAUNCH("flux_v", s, k_flux_v<<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
+    LAUNCH("flux_v", s, k_flux_v<<<g3w, 128, 0, s>>>(g, pr, ph.mom3, ax, ay, az));
     LAUNCH("rhs_v", s, k_rhs_v<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, st, pp, ax, ay, az, R.v));
-    LAUNCH("flux_w", s, k_flux_w<<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
+    LAUNCH("flux_w", s, k_flux_w<<<g3w, 128, 0, s>>>(g, pr, ph.mom3, ax, ay, az));
     LAUNCH("rhs_w", s, k_rhs_w<<<nblk(g.nw, BS), BS, 0, s>>>(g, ph, st, pp, ax, ay, az, R.w));
     if (sgs) {
         // subgrid stresses and heat fluxes, each edge and face once (the flux buffer is free again)

@@ -422,17 +422,17 @@ __global__ void k_mx_cl_div(Geo g, MxBase mb, Phys ph, const float *dr, const fl
 __global__ void k_mx_flux_theta(Geo g, MxBase mb, Phys ph, const float *mfx, const float *mfy, const float *rw,
                                 const float *thp, float *fx, float *fy, float *fz) {
     MX_CELL3D_W();
-    const int zf = ph.scal_adv == 1;
+    const int scheme = ph.scal_adv;
     float q[6];
     if (k < g.nz) {
         float mf = __ldg(mfx + n), sg = sgnT<float>(mf);
         float tu = fval(g, thp, sg >= 0.f ? i - 1 : i, j, k);
         for (int m = 0; m < 6; ++m) q[m] = fval(g, thp, i - 3 + m, j, k) - tu;
-        fx[n] = mf * (tu + weno5<float>(q, sg, zf));
+        fx[n] = mf * (tu + scal_face<float>(q, sg, scheme));
         mf = __ldg(mfy + n); sg = sgnT<float>(mf);
         tu = fval(g, thp, i, sg >= 0.f ? j - 1 : j, k);
         for (int m = 0; m < 6; ++m) q[m] = fval(g, thp, i, j - 3 + m, k) - tu;
-        fy[n] = mf * (tu + weno5<float>(q, sg, zf));
+        fy[n] = mf * (tu + scal_face<float>(q, sg, scheme));
     }
     if (k == 0 || k == g.nz) { fz[n] = 0.f; return; }
     float W = __ldg(rw + n), sg = sgnT<float>(W);
@@ -442,7 +442,7 @@ __global__ void k_mx_flux_theta(Geo g, MxBase mb, Phys ph, const float *mfx, con
         int km = k - 3 + m;
         q[m] = dth0(mb, km, ku) + (fval(g, thp, i, j, km) - tu);
     }
-    fz[n] = W * (dth0(mb, ku, k - 1) + tu + weno5<float>(q, sg, zf));
+    fz[n] = W * (dth0(mb, ku, k - 1) + tu + scal_face<float>(q, sg, scheme));
 }
 // The same theta fluxes with the stencil staged in shared memory.  A block of 32 x 4 columns and 4
 // levels loads one (32+8) x (4+6) x (4+6) tile of theta' by TMA, starting 4 cells left of the
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(FT_TX * FT_TY) k_mx_flux_theta_tma(const __gri
     if (!ft_load_tile(tile, &bar, &tmap, g, thp, g.nz, x0 - 4, y0 - 3, bz0, err)) return;
     const int i = x0 + tx, j = y0 + ty;
     if (i >= g.nx || j >= g.ny) return;
-    const int zf = ph.scal_adv == 1;
+    const int scheme = ph.scal_adv;
     const int lx = tx + 4, ly = ty + 3;
     auto T = [&](int k, int dy, int dx) { return tile[kref(k, g.nz) - bz0][ly + dy][lx + dx]; };
     float q[6];
@@ -513,11 +513,11 @@ __global__ void __launch_bounds__(FT_TX * FT_TY) k_mx_flux_theta_tma(const __gri
         float mf = __ldg(mfx + n), sg = sgnT<float>(mf);
         float tu = T(k, 0, sg >= 0.f ? -1 : 0);
         for (int m = 0; m < 6; ++m) q[m] = T(k, 0, m - 3) - tu;
-        fx[n] = mf * (tu + weno5<float>(q, sg, zf));
+        fx[n] = mf * (tu + scal_face<float>(q, sg, scheme));
         mf = __ldg(mfy + n); sg = sgnT<float>(mf);
         tu = T(k, sg >= 0.f ? -1 : 0, 0);
         for (int m = 0; m < 6; ++m) q[m] = T(k, m - 3, 0) - tu;
-        fy[n] = mf * (tu + weno5<float>(q, sg, zf));
+        fy[n] = mf * (tu + scal_face<float>(q, sg, scheme));
         if (k == 0) continue;   // wall: the bottom face carries no flux (never read)
         float W = __ldg(rw + n);
         sg = sgnT<float>(W);
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(FT_TX * FT_TY) k_mx_flux_theta_tma(const __gri
             int km = k - 3 + m;
             q[m] = dth0(mb, km, ku) + (T(km, 0, 0) - tu);
         }
-        fz[n] = W * (dth0(mb, ku, k - 1) + tu + weno5<float>(q, sg, zf));
+        fz[n] = W * (dth0(mb, ku, k - 1) + tu + scal_face<float>(q, sg, scheme));
     }
 }
 
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(FT_TX * FT_TY) k_mx_flux_theta_tma(const __gri
 // the walls).  Blocks cover levels 0..nz so that the wall fluxes (zero) are written as well.
 template <int COMP>
 __global__ void __launch_bounds__(FT_TX * FT_TY) k_mx_flux_mom_tma(const __grid_constant__ CUtensorMap tmap, Geo g,
-                                                                    const float *vel, const float *mfx,
+                                                                    int mom3, const float *vel, const float *mfx,
                                                                     const float *mfy, const float *rw, float *fx,
                                                                     float *fy, float *fz, unsigned *err) {
     __shared__ __align__(128) FtTile tile;
@@ -568,42 +568,42 @@ __global__ void __launch_bounds__(FT_TX * FT_TY) k_mx_flux_mom_tma(const __grid_
             if (k < nz) {
                 float adv = 0.5f * (__ldg(mfx + n) + __ldg(mfx + n + oxp));
                 for (int m = 0; m < 6; ++m) q[m] = C(k, 0, m - 2);
-                fx[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+                fx[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
                 adv = 0.5f * (__ldg(mfy + n + oxm) + __ldg(mfy + n));
                 for (int m = 0; m < 6; ++m) q[m] = C(k, m - 3, 0);
-                fy[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+                fy[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
             }
             if (k == 0 || k == nz) { fz[n] = 0.f; continue; }
             float adv = 0.5f * (__ldg(rw + n + oxm) + __ldg(rw + n));
             for (int m = 0; m < 6; ++m) q[m] = C(k - 3 + m, 0, 0);
-            fz[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+            fz[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
         } else if (COMP == 1) {
             if (k < nz) {
                 float adv = 0.5f * (__ldg(mfx + n + oym) + __ldg(mfx + n));
                 for (int m = 0; m < 6; ++m) q[m] = C(k, 0, m - 3);
-                fx[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+                fx[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
                 adv = 0.5f * (__ldg(mfy + n) + __ldg(mfy + n + oyp));
                 for (int m = 0; m < 6; ++m) q[m] = C(k, m - 2, 0);
-                fy[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+                fy[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
             }
             if (k == 0 || k == nz) { fz[n] = 0.f; continue; }
             float adv = 0.5f * (__ldg(rw + n + oym) + __ldg(rw + n));
             for (int m = 0; m < 6; ++m) q[m] = C(k - 3 + m, 0, 0);
-            fz[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+            fz[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
         } else {
             if (k < nz) {
                 float wa = k == 0 ? 0.f : __ldg(rw + n), wb = k + 1 == nz ? 0.f : __ldg(rw + n + nxy);
                 float adv = 0.5f * (wa + wb);
                 for (int m = 0; m < 6; ++m) q[m] = Wv(k - 2 + m);
-                fz[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+                fz[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
             }
             if (k == 0 || k == nz) { fx[n] = 0.f; fy[n] = 0.f; continue; }
             float adv = 0.5f * (__ldg(mfx + n - nxy) + __ldg(mfx + n));
             for (int m = 0; m < 6; ++m) q[m] = tile[k - bz0][ly][lx + m - 3];
-            fx[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+            fx[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
             adv = 0.5f * (__ldg(mfy + n - nxy) + __ldg(mfy + n));
             for (int m = 0; m < 6; ++m) q[m] = tile[k - bz0][ly + m - 3][lx];
-            fy[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+            fy[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
         }
     }
 }
@@ -635,41 +635,41 @@ bool mx_encode_cell_tile_map(CUtensorMap *map, const float *base, const Geo &g, 
 }
 
 // momenta (upwind-5, reading R5): the same face and edge placement as the FP64 path
-__global__ void k_mx_flux_u(Geo g, const float *ux, const float *mfx, const float *mfy, const float *rw, float *fx,
+__global__ void k_mx_flux_u(Geo g, int mom3, const float *ux, const float *mfx, const float *mfy, const float *rw, float *fx,
                             float *fy, float *fz) {
     MX_CELL3D_W();
     float q[6];
     if (k < g.nz) {
         float adv = 0.5f * (__ldg(mfx + n) + fval(g, mfx, i + 1, j, k));
         for (int m = 0; m < 6; ++m) q[m] = fval(g, ux, i - 2 + m, j, k);
-        fx[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+        fx[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
         adv = 0.5f * (fval(g, mfy, i - 1, j, k) + __ldg(mfy + n));
         for (int m = 0; m < 6; ++m) q[m] = fval(g, ux, i, j - 3 + m, k);
-        fy[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+        fy[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
     }
     if (k == 0 || k == g.nz) { fz[n] = 0.f; return; }
     float adv = 0.5f * (__ldg(rw + cixw(g, i - 1, j, k)) + __ldg(rw + n));
     for (int m = 0; m < 6; ++m) q[m] = fval(g, ux, i, j, k - 3 + m);
-    fz[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+    fz[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
 }
-__global__ void k_mx_flux_v(Geo g, const float *vy, const float *mfx, const float *mfy, const float *rw, float *fx,
+__global__ void k_mx_flux_v(Geo g, int mom3, const float *vy, const float *mfx, const float *mfy, const float *rw, float *fx,
                             float *fy, float *fz) {
     MX_CELL3D_W();
     float q[6];
     if (k < g.nz) {
         float adv = 0.5f * (fval(g, mfx, i, j - 1, k) + __ldg(mfx + n));
         for (int m = 0; m < 6; ++m) q[m] = fval(g, vy, i - 3 + m, j, k);
-        fx[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+        fx[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
         adv = 0.5f * (__ldg(mfy + n) + fval(g, mfy, i, j + 1, k));
         for (int m = 0; m < 6; ++m) q[m] = fval(g, vy, i, j - 2 + m, k);
-        fy[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+        fy[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
     }
     if (k == 0 || k == g.nz) { fz[n] = 0.f; return; }
     float adv = 0.5f * (__ldg(rw + cixw(g, i, j - 1, k)) + __ldg(rw + n));
     for (int m = 0; m < 6; ++m) q[m] = fval(g, vy, i, j, k - 3 + m);
-    fz[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+    fz[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
 }
-__global__ void k_mx_flux_w(Geo g, const float *wz, const float *mfx, const float *mfy, const float *rw, float *fx,
+__global__ void k_mx_flux_w(Geo g, int mom3, const float *wz, const float *mfx, const float *mfy, const float *rw, float *fx,
                             float *fy, float *fz) {
     MX_CELL3D_W();
     float q[6];
@@ -677,15 +677,15 @@ __global__ void k_mx_flux_w(Geo g, const float *wz, const float *mfx, const floa
         float wa = k == 0 ? 0.f : __ldg(rw + n), wb = k + 1 == g.nz ? 0.f : __ldg(rw + n + g.nxy);
         float adv = 0.5f * (wa + wb);
         for (int m = 0; m < 6; ++m) q[m] = wvalf(g, wz, i, j, k - 2 + m);
-        fz[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+        fz[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
     }
     if (k == 0 || k == g.nz) { fx[n] = 0.f; fy[n] = 0.f; return; }
     float adv = 0.5f * (fval(g, mfx, i, j, k - 1) + __ldg(mfx + n));
     for (int m = 0; m < 6; ++m) q[m] = __ldg(wz + cixw(g, i - 3 + m, j, k));
-    fx[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+    fx[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
     adv = 0.5f * (fval(g, mfy, i, j, k - 1) + __ldg(mfy + n));
     for (int m = 0; m < 6; ++m) q[m] = __ldg(wz + cixw(g, i, j - 3 + m, k));
-    fy[n] = adv * upwind5<float>(q, sgnT<float>(adv));
+    fy[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
 }
 
 // continuity and rho*theta.  Face fluxes of theta are split as F theta0_k + F (theta_face -
@@ -1106,24 +1106,24 @@ __global__ void k_mx_tracer_phi(Geo g, MxBase mb, const float *rphi, const float
 __global__ void k_mx_tracer_flux(Geo g, MxBase mb, Phys ph, const float *mfx, const float *mfy, const float *rw,
                                  const float *phi, TrSum ms, float rns, float *fx, float *fy, float *fz) {
     MX_CELL3D_W();
-    const int zf = ph.scal_adv == 1;
+    const int scheme = ph.scal_adv;
     float q[6];
     if (k < g.nz) {
         const float dz = mb.dzf[k];
         float mf = __ldg(mfx + n) + dz * (ms.x[n] * rns), sg = sgnT<float>(mf);
         float tu = fval(g, phi, sg >= 0.f ? i - 1 : i, j, k);
         for (int m = 0; m < 6; ++m) q[m] = fval(g, phi, i - 3 + m, j, k) - tu;
-        fx[n] = mf * (tu + weno5<float>(q, sg, zf));
+        fx[n] = mf * (tu + scal_face<float>(q, sg, scheme));
         mf = __ldg(mfy + n) + dz * (ms.y[n] * rns); sg = sgnT<float>(mf);
         tu = fval(g, phi, i, sg >= 0.f ? j - 1 : j, k);
         for (int m = 0; m < 6; ++m) q[m] = fval(g, phi, i, j - 3 + m, k) - tu;
-        fy[n] = mf * (tu + weno5<float>(q, sg, zf));
+        fy[n] = mf * (tu + scal_face<float>(q, sg, scheme));
     }
     if (k == 0 || k == g.nz) { fz[n] = 0.f; return; }
     float W = __ldg(rw + n) + ms.z[n] * rns, sg = sgnT<float>(W);
     float tu = fval(g, phi, i, j, sg >= 0.f ? k - 1 : k);
     for (int m = 0; m < 6; ++m) q[m] = fval(g, phi, i, j, k - 3 + m) - tu;
-    fz[n] = W * (tu + weno5<float>(q, sg, zf));
+    fz[n] = W * (tu + scal_face<float>(q, sg, scheme));
 }
 __global__ void k_mx_tracer_update(Geo g, MxBase mb, const float *snphi, const float *fx, const float *fy,
                                    const float *fz, float adt, float *rphi) {
@@ -1256,33 +1256,33 @@ void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const 
         const dim3 gt((unsigned)((g.nx + FT_TX - 1) / FT_TX), (unsigned)((g.ny + FT_TY - 1) / FT_TY),
                       (unsigned)((g.nz + 1 + FT_TZ - 1) / FT_TZ));
         mx_launch("mx_flux_u", s, [&] {
-            k_mx_flux_mom_tma<0><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->ux, g, ux, mfx, mfy, st.w, ax, ay, az,
+            k_mx_flux_mom_tma<0><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->ux, g, ph.mom3, ux, mfx, mfy, st.w, ax, ay, az,
                                                                       tma->err);
         });
     } else {
-        mx_launch("mx_flux_u", s, [&] { k_mx_flux_u<<<gw, MBX, 0, s>>>(g, ux, mfx, mfy, st.w, ax, ay, az); });
+        mx_launch("mx_flux_u", s, [&] { k_mx_flux_u<<<gw, MBX, 0, s>>>(g, ph.mom3, ux, mfx, mfy, st.w, ax, ay, az); });
     }
     mx_launch("mx_rhs_u", s, [&] { k_mx_rhs_u<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, st, pp, fl, R.u); });
     if (tma && tma->use) {
         const dim3 gt((unsigned)((g.nx + FT_TX - 1) / FT_TX), (unsigned)((g.ny + FT_TY - 1) / FT_TY),
                       (unsigned)((g.nz + 1 + FT_TZ - 1) / FT_TZ));
         mx_launch("mx_flux_v", s, [&] {
-            k_mx_flux_mom_tma<1><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->vy, g, vy, mfx, mfy, st.w, ax, ay, az,
+            k_mx_flux_mom_tma<1><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->vy, g, ph.mom3, vy, mfx, mfy, st.w, ax, ay, az,
                                                                       tma->err);
         });
     } else {
-        mx_launch("mx_flux_v", s, [&] { k_mx_flux_v<<<gw, MBX, 0, s>>>(g, vy, mfx, mfy, st.w, ax, ay, az); });
+        mx_launch("mx_flux_v", s, [&] { k_mx_flux_v<<<gw, MBX, 0, s>>>(g, ph.mom3, vy, mfx, mfy, st.w, ax, ay, az); });
     }
     mx_launch("mx_rhs_v", s, [&] { k_mx_rhs_v<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, st, pp, fl, R.v); });
     if (tma && tma->use) {
         const dim3 gt((unsigned)((g.nx + FT_TX - 1) / FT_TX), (unsigned)((g.ny + FT_TY - 1) / FT_TY),
                       (unsigned)((g.nz + 1 + FT_TZ - 1) / FT_TZ));
         mx_launch("mx_flux_w", s, [&] {
-            k_mx_flux_mom_tma<2><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->wz, g, wz, mfx, mfy, st.w, ax, ay, az,
+            k_mx_flux_mom_tma<2><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->wz, g, ph.mom3, wz, mfx, mfy, st.w, ax, ay, az,
                                                                       tma->err);
         });
     } else {
-        mx_launch("mx_flux_w", s, [&] { k_mx_flux_w<<<gw, MBX, 0, s>>>(g, wz, mfx, mfy, st.w, ax, ay, az); });
+        mx_launch("mx_flux_w", s, [&] { k_mx_flux_w<<<gw, MBX, 0, s>>>(g, ph.mom3, wz, mfx, mfy, st.w, ax, ay, az); });
     }
     mx_launch("mx_rhs_w", s, [&] { k_mx_rhs_w<<<gw, MBX, 0, s>>>(g, mb, st, pp, fl, R.w); });
     if (tau) {

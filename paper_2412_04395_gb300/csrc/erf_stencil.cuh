@@ -18,6 +18,25 @@ __device__ __forceinline__ T upwind5(const T *q, T s) {
     return fma(T(47.0 / 60.0), a2, fma(T(27.0 / 60.0), a3, fma(T(-13.0 / 60.0), a1,
                fma(T(2.0 / 60.0), a0, T(-3.0 / 60.0) * a4))));
 }
+// q[0..5] = q_{m-3}..q_{m+2}; 3rd-order upwind value at m-1/2: the centred fourth-order value
+// plus s/12 times its dissipative part (Sec. 3.6), i.e. (-1, 5, 2)/6 over the three points on the
+// upwind side (s = 0 takes the left side; every caller multiplies by that zero momentum)
+template <class T>
+__device__ __forceinline__ T upwind3(const T *q, T s) {
+    const bool l = s >= T(0);
+    const T a0 = l ? q[1] : q[4], a1 = l ? q[2] : q[3], a2 = l ? q[3] : q[2];
+    return fma(T(5.0 / 6.0), a1, fma(T(1.0 / 3.0), a2, T(-1.0 / 6.0) * a0));
+}
+// face value of an advected scalar: WENO5-JS (scheme 0), WENO5-Z (1) or upwind-3 (3); defined
+// after weno5 below
+template <class T>
+__device__ __forceinline__ T scal_face(const T *q, T s, int scheme);
+// the momentum interpolant of the configuration (upwind-3 or upwind-5)
+template <class T>
+__device__ __forceinline__ T upwind_mom(const T *q, T s, int mom3) {
+    return mom3 ? upwind3(q, s) : upwind5(q, s);
+}
+
 template <class T>
 __device__ __forceinline__ T sgnT(T x) { return x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0)); }
 // correctly rounded reciprocal (FP32: one MUFU operation and its refinement instead of a division)
@@ -65,6 +84,11 @@ __device__ __forceinline__ T weno5(const T *q, T s, int zflag) {
         N = fma(g0 * T(0.1 / 3.0), q0, (g2 * T(0.3 / 6.0)) * q2);
     }
     return fma(N, rcp_t(D), p1);
+}
+
+template <class T>
+__device__ __forceinline__ T scal_face(const T *q, T s, int scheme) {
+    return scheme == 3 ? upwind3(q, s) : weno5(q, s, scheme == 1);
 }
 
 }  // namespace erfk

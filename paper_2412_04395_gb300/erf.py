@@ -55,7 +55,7 @@ class Config(C.Structure):
                 ("surface", C.c_int32), ("z0", C.c_double), ("sfc_theta_flux", C.c_double),
                 ("theta_s", C.c_double), ("brunt_N", C.c_double), ("p_s", C.c_double),
                 ("n_knots", C.c_int32), ("knot_z", C.POINTER(C.c_double)),
-                ("knot_theta", C.POINTER(C.c_double)), ("tracer", C.c_int32)]
+                ("knot_theta", C.POINTER(C.c_double)), ("tracer", C.c_int32), ("mom_adv", C.c_int32)]
 
 
 class Diag(C.Structure):
@@ -158,7 +158,7 @@ def make_structs(wl):
                Pr_t=wl.Pr_t, nu=wl.nu, precision=wl.precision, gravity=wl.gravity, f_cor=wl.f_cor,
                u_g=wl.u_g, v_g=wl.v_g, surface=wl.surface, z0=wl.z0, sfc_theta_flux=wl.sfc_theta_flux,
                theta_s=wl.theta_s, brunt_N=wl.brunt_N, p_s=wl.p_s, n_knots=nk, knot_z=_dp(kz),
-               knot_theta=_dp(kt), tracer=getattr(wl, "tracer", 0))
+               knot_theta=_dp(kt), tracer=getattr(wl, "tracer", 0), mom_adv=wl.mom_adv)
     return g, c, keep
 
 

@@ -60,3 +60,17 @@ def test_workspace_bytes_and_validation_without_gpu(lib):
     with pytest.raises(erf.ErfError) as e:
         erf.erf_workspace_bytes(g2, c2)
     assert e.value.status == erf.ERF_EUNSUPPORTED
+
+
+def test_advection_orders_are_validated_without_gpu(lib):
+    """mom_adv takes 0/5 (upwind-5) or 3 (upwind-3); scal_adv 0, 1 (WENO5-JS/Z) or 3 (upwind-3)."""
+    from paper_2412_04395_gb300 import erf, workloads as W
+    wl = W.density_current(nx=32, ny=4, nz=16, dx=400.0)
+    for mom, scal in ((5, 0), (3, 3), (0, 1), (3, 0)):
+        g, c, keep = erf.make_structs(wl.with_(mom_adv=mom, scal_adv=scal))
+        assert erf.erf_workspace_bytes(g, c) > 0
+    for mom, scal in ((4, 0), (6, 0), (5, 2), (5, 5)):
+        g, c, keep = erf.make_structs(wl.with_(mom_adv=mom, scal_adv=scal))
+        with pytest.raises(erf.ErfError) as e:
+            erf.erf_workspace_bytes(g, c)
+        assert e.value.status == erf.ERF_EINVAL
