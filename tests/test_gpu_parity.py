@@ -267,3 +267,12 @@ def test_hill_bubble_configured_steps_on_a_window():
     d, o = _run_both(wl, 500)
     errs = _compare(d.state(), o.state(), per_field=True)
     print("hill_bubble 500 steps window:", errs)
+
+
+def test_sullivan_terrain_window():
+    """The hill-bubble window over the Sullivan coordinate (beta = 3, Sec. 3.4): every field
+    within 1e-11 after 40 steps."""
+    wl = W.hill_bubble(nx=32, ny=40, nz=64, dx=100.0).with_(terrain_beta=3)
+    d, o = _run_both(wl, 40)
+    errs = _compare(d.state(), o.state())
+    print("hill_bubble beta = 3, 40 steps:", errs)

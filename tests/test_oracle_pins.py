@@ -499,3 +499,25 @@ def test_most_surface_heat_flux_warms_the_lowest_cell():
     r = _rhs_with(o, rho, rt, 0 * rho, 0 * rho, np.zeros((nz + 1, ny, nx)))
     np.testing.assert_allclose(r["R_rhotheta"][0], rho[0] * Q / dz, rtol=1e-13)
     assert np.max(np.abs(r["R_rhotheta"][1:])) < 1e-13
+
+
+def test_sullivan_coordinate_beta3_metrics_and_rest():
+    """Sec. 3.4: z = zeta + (1 - zeta/z_t)^beta h with beta = 3 (Sullivan).  The cell heights are
+    the closed form dzeta_k + (s_{k+1} - s_k) h_c, s = (1 - zeta/z_t)^3 and h_c the 4-node
+    average of the nodal terrain; a resting hydrostatic atmosphere over the hill stays at rest."""
+    wl = W.hill_bubble(nx=16, ny=16, nz=12, dx=300.0, dz0=120.0, ratio=1.02).with_(dtheta=None, terrain_beta=3)
+    o = make_oracle(wl, init=False)
+    zeta = np.asarray(wl.zeta)
+    s = (1.0 - zeta / zeta[-1]) ** 3
+    h = np.asarray(wl.terrain)
+    hc = 0.25 * (h + np.roll(h, -1, axis=1) + np.roll(h, -1, axis=0) + np.roll(np.roll(h, -1, axis=0), -1, axis=1))
+    expect = np.diff(zeta)[:, None, None] + np.diff(s)[:, None, None] * hc[None, :, :]
+    assert np.allclose(o.geom("Hc"), expect, rtol=1e-13, atol=0)
+    # beta = 3 flattens the coordinate surfaces faster with height than beta = 1
+    s1 = 1.0 - zeta / zeta[-1]
+    assert np.all(s[1:-1] < s1[1:-1])
+    r = make_oracle(wl)
+    r.step(20)
+    st = r.state()
+    assert np.max(np.abs(st["rhow"])) <= 1e-12
+    assert np.all(st["rhou"] == 0.0) and np.all(st["rhov"] == 0.0)
