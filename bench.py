@@ -223,6 +223,12 @@ def workload(args):
         if args.closure == "learned":
             wl = wl.with_(closure=W.CLOSURE_LEARNED)
         return wl
+    if args.case == "neutral_abl":
+        nx, ny, nz = args.grid or (1024, 1024, 128)
+        return W.neutral_abl(nx=nx, ny=ny, nz=nz, dx=10.0).with_(precision=prec)
+    if args.case == "paper_scaling":
+        nx, ny, nz = args.grid or (512, 512, 256)
+        return W.paper_scaling(nx=nx, ny=ny, nz=nz).with_(precision=prec)
     raise SystemExit(f"unknown case {args.case}")
 
 

@@ -249,7 +249,7 @@ erf_status erf_reduce_state_noalloc(int32_t nx, int32_t ny, int32_t nz, double d
  *   gives up makes the next erf_diagnostics return ERF_ECUDA.
  *   ERF_OPT_COLUMN_FUSION: how the mixed-precision substep runs the explicit vertical part
  *   (App. C rows 3-4): 1 inside the column sweep of the vertical solve, one thread per column;
- *   0 as a per-cell kernel before the sweep; -1 (default) fused when nx * ny >= 2^20.  Both give
+ *   0 as a per-cell kernel before the sweep; -1 (default) fused when nx * ny >= 2^17.  Both give
  *   bit-identical results.
  * erf_set_option drops the captured step graph; erf_get_option reports whether the option is in
  * effect (1 if the TMA kernels run, 1 if the fused column sweep runs). */

@@ -366,11 +366,12 @@ static CF5f cf(const F5f &f) { return CF5f{f.r, f.t, f.u, f.v, f.w}; }
 
 // one RK3 step of the mixed-precision path (flat grids)
 // the explicit vertical part runs inside the column sweep once there are enough columns to fill
-// the GPU with one thread each (measured at 1024^2 and 2048^2 columns; below that the per-cell
-// kernel keeps more threads in flight)
+// the GPU with one thread each.  Measured per step on the convective ABL (160 levels), split vs
+// fused: 128^2 columns 7.6 vs 8.5 ms, 256^2 14.3 vs 14.3 ms, 384^2 29.5 vs 24.1 ms, 512^2 49.6 vs
+// 43.4 ms; fused also at 1024^2 and 2048^2.
 static int fuse_columns(const erf_handle *h) {
     if (h->column_fusion >= 0) return h->column_fusion;
-    return h->geo.nxy >= (1LL << 20) ? 1 : 0;
+    return h->geo.nxy >= (1LL << 17) ? 1 : 0;
 }
 
 static void enqueue_step_mixed(erf_handle *h, cudaStream_t s) {
