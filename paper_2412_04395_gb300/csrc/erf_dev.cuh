@@ -167,10 +167,6 @@ __device__ __forceinline__ double rdz2c(const Geo &g, int i, int j, int k) {
 __device__ __forceinline__ double zc(const Geo &g, int i, int j, int k) {
     return g.terrain ? g.zetac[k] + g.sc[k] * g.hc[ij2(g, i, j)] : g.zetac[k];
 }
-// distance between the cell centres k-1 and k
-__device__ __forceinline__ double dzcw(const Geo &g, int i, int j, int k) {
-    return g.terrain ? g.dzc[k] + (g.sc[k] - g.sc[k - 1]) * g.hc[ij2(g, i, j)] : g.dzc[k];
-}
 // h_xi / 2 and h_eta / 2 at x- and y-faces (the 1/2 of the two-point average they multiply), and
 // h_xi / 4, h_eta / 4 at w-faces (the 1/4 of the four-point averages of the metric shift)
 __device__ __forceinline__ double hxi_x2(const Geo &g, int i, int j, int k) { return g.sc[k] * g.gxh[ij2(g, i, j)]; }
