@@ -135,6 +135,16 @@ __device__ __forceinline__ double rcp_d(double x) {
     return fma(r, fma(-x, r, 1.0), r);
 }
 
+// 1/x to about 2^-40 relative: the hardware's approximate FP64 reciprocal and one Newton step.
+// For a quotient that only corrects a larger term (the WENO5 weighting, added to the middle
+// candidate), where that error stays far below the rounding of the sum.  x must be a normal
+// FP64 number.
+__device__ __forceinline__ double rcp1_d(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    return fma(r, fma(-x, r, 1.0), r);
+}
+
 // ---- metrics (App. B) in separable form
 __device__ __forceinline__ int ij2(const Geo &g, int i, int j) { return wrapi(j, g.ny) * g.nx + wrapi(i, g.nx); }
 __device__ __forceinline__ double Hc(const Geo &g, int i, int j, int k) {

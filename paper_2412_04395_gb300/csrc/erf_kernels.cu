@@ -438,8 +438,8 @@ __global__ void k_sgs_div(Geo g, Phys ph, const double *mu, const double *t11, c
 // WENO5-JS / WENO5-Z face value in FP64 (same candidates and weights as weno5<T>), arranged for
 // GB300's FP64 rate: the middle candidate and the six indicator terms are formed from the four
 // first differences of the stencil, the other candidates enter as differences from the middle
-// one, the indicators carry a common factor 12/13, and the normalisation takes one reciprocal
-// (rcp_d) instead of a division.
+// one, the indicators (with eps) carry a common factor 12/13, and the normalisation of that
+// correction takes one reciprocal (rcp1_d) instead of a division.
 __device__ __forceinline__ double weno5_d(const double *q, double s, int zflag) {
     double a, b, c, d, e;   // v_{-2}, v_{-1}, v_0, v_1, v_2 on the upwind side
     if (s >= 0.0) { a = q[0]; b = q[1]; c = q[2]; d = q[3]; e = q[4]; }
@@ -452,32 +452,28 @@ __device__ __forceinline__ double weno5_d(const double *q, double s, int zflag) 
     // the other two candidates through their differences from p1: p0 - p1 = (t0 - t1)/3 and
     // p2 - p1 = (t1 - t2)/6, so that the value is p1 + (w0 (p0 - p1) + w2 (p2 - p1)) / sum w
     const double q0 = t0 - t1, q2 = t1 - t2;
-    // smoothness indicators 13/12 t^2 + 1/4 u^2 and eps = 1e-6, both scaled by 12/13: the weights
-    // are homogeneous in (eps + beta), so the scheme is unchanged and each indicator takes three
-    // FP64 operations instead of four
-    constexpr double k3 = 3.0 / 13.0;
-    const double b0 = fma(t0, t0, (k3 * u0) * u0);
-    const double b1 = fma(t1, t1, (k3 * u1) * u1);
-    const double b2 = fma(t2, t2, (k3 * u2) * u2);
-    constexpr double eps = 1.0e-6 * (12.0 / 13.0);
+    // eps + beta_r with beta_r = 13/12 t^2 + 1/4 u^2 and eps = 1e-6, all scaled by 12/13 (the
+    // weights are homogeneous in eps + beta, so the scheme is unchanged): three FP64 operations
+    constexpr double k3 = 3.0 / 13.0, eps = 1.0e-6 * (12.0 / 13.0);
+    const double e0 = fma(t0, t0, fma(k3 * u0, u0, eps));
+    const double e1 = fma(t1, t1, fma(k3 * u1, u1, eps));
+    const double e2 = fma(t2, t2, fma(k3 * u2, u2, eps));
     if (zflag) {
-        double tau = fabs(b0 - b2);
-        double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+        double tau = fabs(e0 - e2);   // |beta_0 - beta_2| (scaled)
         double w0 = 0.1 * (e0 + tau) * e1 * e2;
         double w1 = 0.6 * (e1 + tau) * e0 * e2;
         double w2 = 0.3 * (e2 + tau) * e0 * e1;
         double N = fma(w0, (1.0 / 3.0) * q0, w2 * ((1.0 / 6.0) * q2));
-        return fma(N, rcp_d(w0 + w1 + w2), p1);
+        return fma(N, rcp1_d(w0 + w1 + w2), p1);
     }
-    // JS: w_r = d_r / (eps + b_r)^2 scaled by the product of all (eps + b)^2, i.e. d_r g_r with
-    // g0 = (e1 e2)^2, g1 = (e0 e2)^2, g2 = (e0 e1)^2; the linear weights 1/10, 6/10, 3/10 and the
-    // 1/3, 1/6 of the differences fold into the constants
-    const double e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
+    // JS: w_r = d_r / (eps + b_r)^2 scaled by the product of all (eps + b)^2 and by 10/3, i.e.
+    // (1/3) g0, 2 g1, g2 with g0 = (e1 e2)^2, g1 = (e0 e2)^2, g2 = (e0 e1)^2; the 1/3, 1/6 of the
+    // differences fold into the constants
     const double f01 = e0 * e1, f02 = e0 * e2, f12 = e1 * e2;
     const double g0 = f12 * f12, g1 = f02 * f02, g2 = f01 * f01;
-    const double D = fma(0.1, g0, fma(0.6, g1, 0.3 * g2));
-    const double N = fma(g0 * (0.1 / 3.0), q0, (g2 * (0.3 / 6.0)) * q2);
-    return fma(N, rcp_d(D), p1);
+    const double D = fma(1.0 / 3.0, g0, fma(2.0, g1, g2));
+    const double N = fma(g0 * (1.0 / 9.0), q0, g2 * ((1.0 / 6.0) * q2));
+    return fma(N, rcp1_d(D), p1);
 }
 
 // face value of an advected scalar: WENO5-JS, WENO5-Z or the linear upwind-3 interpolant
@@ -528,7 +524,8 @@ __global__ void k_rhs_cells(Geo g, Prep pr, const double *fx, const double *fy, 
     const long long n = ((long long)k * g.ny + j) * g.nx + i;
 // u: x-flux at the cell centre (i,j,k), y-flux at the xy-edge (x-face i, y-face j), z-flux at the
 // xz-edge (x-face i, w-face k; zero on the walls)
-__global__ void k_flux_u(Geo g, Prep pr, int mom3, double *fx, double *fy, double *fz) {
+template <int mom3>
+__global__ void k_flux_u(Geo g, Prep pr, double *fx, double *fy, double *fz) {
     CELL3D_W();
     double q[6];
     if (k < g.nz) {
@@ -545,7 +542,8 @@ __global__ void k_flux_u(Geo g, Prep pr, int mom3, double *fx, double *fy, doubl
     fz[n] = adv * upwind_mom(q, sgnd(adv), mom3);
 }
 // v: x-flux at the xy-edge (x-face i, y-face j), y-flux at the cell centre, z-flux at the yz-edge
-__global__ void k_flux_v(Geo g, Prep pr, int mom3, double *fx, double *fy, double *fz) {
+template <int mom3>
+__global__ void k_flux_v(Geo g, Prep pr, double *fx, double *fy, double *fz) {
     CELL3D_W();
     double q[6];
     if (k < g.nz) {
@@ -563,7 +561,8 @@ __global__ void k_flux_v(Geo g, Prep pr, int mom3, double *fx, double *fy, doubl
 }
 // w: x-flux at the xz-edge (x-face i, w-face k), y-flux at the yz-edge (both [nz+1] planes, zero on
 // the walls), z-flux at the cell centre (i,j,k) ([nz] planes)
-__global__ void k_flux_w(Geo g, Prep pr, int mom3, double *fx, double *fy, double *fz) {
+template <int mom3>
+__global__ void k_flux_w(Geo g, Prep pr, double *fx, double *fy, double *fz) {
     CELL3D_W();
     double q[6];
     if (k < g.nz) {
@@ -1049,11 +1048,14 @@ void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, double *pp, const dou
     // momentum: fluxes of each component into the shared buffer, then its divergence
     const dim3 g3w((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)(g.nz + 1));
     double *ax = flux, *ay = flux + g.nw, *az = flux + 2 * g.nw;
-    LAUNCH("flux_u", s, k_flux_u<<<g3w, 128, 0, s>>>(g, pr, ph.mom3, ax, ay, az));
+    if (ph.mom3) LAUNCH("flux_u", s, k_flux_u<1><<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
+    else LAUNCH("flux_u", s, k_flux_u<0><<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
     LAUNCH("rhs_u", s, k_rhs_u<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, st, pp, ax, ay, az, R.u));
-    LAUNCH("flux_v", s, k_flux_v<<<g3w, 128, 0, s>>>(g, pr, ph.mom3, ax, ay, az));
+    if (ph.mom3) LAUNCH("flux_v", s, k_flux_v<1><<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
+    else LAUNCH("flux_v", s, k_flux_v<0><<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
     LAUNCH("rhs_v", s, k_rhs_v<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, st, pp, ax, ay, az, R.v));
-    LAUNCH("flux_w", s, k_flux_w<<<g3w, 128, 0, s>>>(g, pr, ph.mom3, ax, ay, az));
+    if (ph.mom3) LAUNCH("flux_w", s, k_flux_w<1><<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
+    else LAUNCH("flux_w", s, k_flux_w<0><<<g3w, 128, 0, s>>>(g, pr, ax, ay, az));
     LAUNCH("rhs_w", s, k_rhs_w<<<nblk(g.nw, BS), BS, 0, s>>>(g, ph, st, pp, ax, ay, az, R.w));
     if (sgs) {
         // subgrid stresses and heat fluxes, each edge and face once (the flux buffer is free again)

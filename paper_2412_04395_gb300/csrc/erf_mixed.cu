@@ -534,9 +534,9 @@ __global__ void __launch_bounds__(FT_TX * FT_TY) k_mx_flux_theta_tma(const __gri
 // Momentum fluxes with the advected velocity staged in shared memory (same tiles; comp 0: u at
 // x-faces, 1: v at y-faces, both [nz] levels; 2: w at w-faces, [nz+1] levels, odd reflection about
 // the walls).  Blocks cover levels 0..nz so that the wall fluxes (zero) are written as well.
-template <int COMP>
+template <int COMP, int mom3>
 __global__ void __launch_bounds__(FT_TX * FT_TY) k_mx_flux_mom_tma(const __grid_constant__ CUtensorMap tmap, Geo g,
-                                                                    int mom3, const float *vel, const float *mfx,
+                                                                    const float *vel, const float *mfx,
                                                                     const float *mfy, const float *rw, float *fx,
                                                                     float *fy, float *fz, unsigned *err) {
     __shared__ __align__(128) FtTile tile;
@@ -635,7 +635,8 @@ bool mx_encode_cell_tile_map(CUtensorMap *map, const float *base, const Geo &g, 
 }
 
 // momenta (upwind-5, reading R5): the same face and edge placement as the FP64 path
-__global__ void k_mx_flux_u(Geo g, int mom3, const float *ux, const float *mfx, const float *mfy, const float *rw, float *fx,
+template <int mom3>
+__global__ void k_mx_flux_u(Geo g, const float *ux, const float *mfx, const float *mfy, const float *rw, float *fx,
                             float *fy, float *fz) {
     MX_CELL3D_W();
     float q[6];
@@ -652,7 +653,8 @@ __global__ void k_mx_flux_u(Geo g, int mom3, const float *ux, const float *mfx, 
     for (int m = 0; m < 6; ++m) q[m] = fval(g, ux, i, j, k - 3 + m);
     fz[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
 }
-__global__ void k_mx_flux_v(Geo g, int mom3, const float *vy, const float *mfx, const float *mfy, const float *rw, float *fx,
+template <int mom3>
+__global__ void k_mx_flux_v(Geo g, const float *vy, const float *mfx, const float *mfy, const float *rw, float *fx,
                             float *fy, float *fz) {
     MX_CELL3D_W();
     float q[6];
@@ -669,7 +671,8 @@ __global__ void k_mx_flux_v(Geo g, int mom3, const float *vy, const float *mfx, 
     for (int m = 0; m < 6; ++m) q[m] = fval(g, vy, i, j, k - 3 + m);
     fz[n] = adv * upwind_mom<float>(q, sgnT<float>(adv), mom3);
 }
-__global__ void k_mx_flux_w(Geo g, int mom3, const float *wz, const float *mfx, const float *mfy, const float *rw, float *fx,
+template <int mom3>
+__global__ void k_mx_flux_w(Geo g, const float *wz, const float *mfx, const float *mfy, const float *rw, float *fx,
                             float *fy, float *fz) {
     MX_CELL3D_W();
     float q[6];
@@ -1256,33 +1259,54 @@ void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const 
         const dim3 gt((unsigned)((g.nx + FT_TX - 1) / FT_TX), (unsigned)((g.ny + FT_TY - 1) / FT_TY),
                       (unsigned)((g.nz + 1 + FT_TZ - 1) / FT_TZ));
         mx_launch("mx_flux_u", s, [&] {
-            k_mx_flux_mom_tma<0><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->ux, g, ph.mom3, ux, mfx, mfy, st.w, ax, ay, az,
+            if (ph.mom3)
+                k_mx_flux_mom_tma<0, 1><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->ux, g, ux, mfx, mfy, st.w, ax, ay, az,
+                                                                      tma->err);
+            else
+                k_mx_flux_mom_tma<0, 0><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->ux, g, ux, mfx, mfy, st.w, ax, ay, az,
                                                                       tma->err);
         });
     } else {
-        mx_launch("mx_flux_u", s, [&] { k_mx_flux_u<<<gw, MBX, 0, s>>>(g, ph.mom3, ux, mfx, mfy, st.w, ax, ay, az); });
+        mx_launch("mx_flux_u", s, [&] {
+            if (ph.mom3) k_mx_flux_u<1><<<gw, MBX, 0, s>>>(g, ux, mfx, mfy, st.w, ax, ay, az);
+            else k_mx_flux_u<0><<<gw, MBX, 0, s>>>(g, ux, mfx, mfy, st.w, ax, ay, az);
+        });
     }
     mx_launch("mx_rhs_u", s, [&] { k_mx_rhs_u<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, st, pp, fl, R.u); });
     if (tma && tma->use) {
         const dim3 gt((unsigned)((g.nx + FT_TX - 1) / FT_TX), (unsigned)((g.ny + FT_TY - 1) / FT_TY),
                       (unsigned)((g.nz + 1 + FT_TZ - 1) / FT_TZ));
         mx_launch("mx_flux_v", s, [&] {
-            k_mx_flux_mom_tma<1><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->vy, g, ph.mom3, vy, mfx, mfy, st.w, ax, ay, az,
+            if (ph.mom3)
+                k_mx_flux_mom_tma<1, 1><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->vy, g, vy, mfx, mfy, st.w, ax, ay, az,
+                                                                      tma->err);
+            else
+                k_mx_flux_mom_tma<1, 0><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->vy, g, vy, mfx, mfy, st.w, ax, ay, az,
                                                                       tma->err);
         });
     } else {
-        mx_launch("mx_flux_v", s, [&] { k_mx_flux_v<<<gw, MBX, 0, s>>>(g, ph.mom3, vy, mfx, mfy, st.w, ax, ay, az); });
+        mx_launch("mx_flux_v", s, [&] {
+            if (ph.mom3) k_mx_flux_v<1><<<gw, MBX, 0, s>>>(g, vy, mfx, mfy, st.w, ax, ay, az);
+            else k_mx_flux_v<0><<<gw, MBX, 0, s>>>(g, vy, mfx, mfy, st.w, ax, ay, az);
+        });
     }
     mx_launch("mx_rhs_v", s, [&] { k_mx_rhs_v<<<g3(g, g.nz), MBX, 0, s>>>(g, mb, st, pp, fl, R.v); });
     if (tma && tma->use) {
         const dim3 gt((unsigned)((g.nx + FT_TX - 1) / FT_TX), (unsigned)((g.ny + FT_TY - 1) / FT_TY),
                       (unsigned)((g.nz + 1 + FT_TZ - 1) / FT_TZ));
         mx_launch("mx_flux_w", s, [&] {
-            k_mx_flux_mom_tma<2><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->wz, g, ph.mom3, wz, mfx, mfy, st.w, ax, ay, az,
+            if (ph.mom3)
+                k_mx_flux_mom_tma<2, 1><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->wz, g, wz, mfx, mfy, st.w, ax, ay, az,
+                                                                      tma->err);
+            else
+                k_mx_flux_mom_tma<2, 0><<<gt, dim3(FT_TX, FT_TY), 0, s>>>(tma->wz, g, wz, mfx, mfy, st.w, ax, ay, az,
                                                                       tma->err);
         });
     } else {
-        mx_launch("mx_flux_w", s, [&] { k_mx_flux_w<<<gw, MBX, 0, s>>>(g, ph.mom3, wz, mfx, mfy, st.w, ax, ay, az); });
+        mx_launch("mx_flux_w", s, [&] {
+            if (ph.mom3) k_mx_flux_w<1><<<gw, MBX, 0, s>>>(g, wz, mfx, mfy, st.w, ax, ay, az);
+            else k_mx_flux_w<0><<<gw, MBX, 0, s>>>(g, wz, mfx, mfy, st.w, ax, ay, az);
+        });
     }
     mx_launch("mx_rhs_w", s, [&] { k_mx_rhs_w<<<gw, MBX, 0, s>>>(g, mb, st, pp, fl, R.w); });
     if (tau) {
