@@ -61,27 +61,26 @@ __device__ __forceinline__ T weno5(const T *q, T s, int zflag) {
     const T t1 = d2 - d3, u1 = d2 + d3;
     const T t2 = d3 - d4, u2 = fma(T(3), d3, -d4);
     const T q0 = t0 - t1, q2 = t1 - t2;
+    // e_r = eps + beta_r (scaled), eps inside the indicator FMAs
     const T k3 = T(3.0 / 13.0), eps = T(1.0e-6 * (12.0 / 13.0));
-    const T b0 = fma(t0, t0, (k3 * u0) * u0);
-    const T b1 = fma(t1, t1, (k3 * u1) * u1);
-    const T b2 = fma(t2, t2, (k3 * u2) * u2);
+    const T e0 = fma(t0, t0, fma(k3 * u0, u0, eps));
+    const T e1 = fma(t1, t1, fma(k3 * u1, u1, eps));
+    const T e2 = fma(t2, t2, fma(k3 * u2, u2, eps));
     T N, D;
     if (zflag) {
         // alpha_k = d_k (1 + tau/(b_k + eps)) scaled by prod (b_j + eps)
-        const T tau = fabs(b0 - b2);
-        const T e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+        const T tau = fabs(e0 - e2);
         const T w0 = T(0.1) * (e0 + tau) * e1 * e2;
         const T w1 = T(0.6) * (e1 + tau) * e0 * e2;
         const T w2 = T(0.3) * (e2 + tau) * e0 * e1;
         N = fma(w0, T(1.0 / 3.0) * q0, w2 * (T(1.0 / 6.0) * q2));
         D = w0 + w1 + w2;
     } else {
-        // alpha_k = d_k / (eps + b_k)^2 scaled by prod (eps + b_j)^2
-        const T e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
+        // alpha_k = d_k / (eps + b_k)^2 scaled by prod (eps + b_j)^2 and by 10/3
         const T f01 = e0 * e1, f02 = e0 * e2, f12 = e1 * e2;
         const T g0 = f12 * f12, g1 = f02 * f02, g2 = f01 * f01;
-        D = fma(T(0.1), g0, fma(T(0.6), g1, T(0.3) * g2));
-        N = fma(g0 * T(0.1 / 3.0), q0, (g2 * T(0.3 / 6.0)) * q2);
+        D = fma(T(1.0 / 3.0), g0, fma(T(2), g1, g2));
+        N = fma(g0 * T(1.0 / 9.0), q0, g2 * (T(1.0 / 6.0) * q2));
     }
     return fma(N, rcp_t(D), p1);
 }
