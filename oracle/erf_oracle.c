@@ -15,7 +15,8 @@
  *   Sec. 3.4  Arakawa C-grid, terrain-following z = zeta + (1 - zeta/z_t)^beta h(x,y)
  *   App. A/B  Jacobian, contravariant Omega, discrete metric terms of Klemp (2003)
  *   Sec. 3.6  advection interpolants (upwind-5, centred-6, upwind-3, centred-4/2), WENO5
- *   Sec. 2.3  stress tensor tau = -2 mu (S - D); Smagorinsky-Lilly closure
+ *   Sec. 2.3  stress tensor tau = -2 mu (S - D); Smagorinsky-Lilly closure; a learned closure
+ *             (Sec. 6, surrogate models) as cell-centre stresses from a model callback
  *   Sec. 3.8  HSE base state by Newton-Raphson; MOST bottom boundary
  * Readings where the paper is silent (constants, Smagorinsky form, WENO5 details, the
  * tridiagonal, divergence damping, wall ghost cells, MOST formulas) are listed in the
@@ -52,7 +53,7 @@ typedef struct {
     double beta_s, beta_d;    /* off-centering (App. C) and divergence damping (Sec. 3.1) */
     int32_t mom_adv;          /* interpolant order for momenta: 2,3,4,5,6 (Sec. 3.6) */
     int32_t scal_adv;         /* scalar scheme: 0 = WENO5-JS, 1 = WENO5-Z, 2..6 = linear interpolant */
-    int32_t closure;          /* 0 none, 1 constant nu, 2 Smagorinsky */
+    int32_t closure;          /* 0 none, 1 constant nu, 2 Smagorinsky, 3 learned (model callback) */
     double Cs, Pr_t, nu;
     double gravity;
     double f_cor, u_g, v_g;   /* f-plane Coriolis + geostrophic forcing (Sec. 3.7) */
@@ -90,6 +91,14 @@ typedef struct {
     /* passive scalar: rho phi, its S^n copy, and the sums over a stage's substeps of the
      * perturbation mass fluxes that advance rho'' (x-faces, y-faces, w-faces) */
     double *rphi, *sn_phi, *msx, *msy, *msz;
+    /* learned closure (closure 3): a model evaluated on each stage state; it writes nine planes
+     * of ncell values at cell centres, density-weighted: rho t11, rho t22, rho t33, rho t12,
+     * rho t13, rho t23, rho h1, rho h2, rho h3 (kinematic stress [m^2/s^2] and SGS heat flux
+     * [K m/s], the latter along +x, +y, +z) */
+    void (*sgs_model)(void *user, const double *rho, const double *rt, const double *ru, const double *rv,
+                      const double *rw, double *planes);
+    void *sgs_user;
+    double *sgs_planes;
 } orc;
 
 enum { F_RHO = 0, F_RT = 1, F_RU = 2, F_RV = 3, F_RW = 4 };
@@ -364,7 +373,7 @@ void orc_destroy(orc *o) {
                        &o->th0, &o->p0, &o->rho, &o->rt, &o->ru, &o->rv, &o->rw, &o->pp, &o->pi,
                        &o->th, &o->Om, &o->Tprev, &o->fx, &o->fy, &o->fz, &o->mfx, &o->mfy,
                        &o->rom, &o->ux, &o->vy, &o->wz, &o->mu, &o->rphi, &o->sn_phi, &o->msx,
-                       &o->msy, &o->msz};
+                       &o->msy, &o->msz, &o->sgs_planes};
     for (size_t n = 0; n < sizeof(ptrs) / sizeof(ptrs[0]); ++n) free(*ptrs[n]);
     for (int f = 0; f < 5; ++f) { free(o->sn[f]); free(o->R[f]); free(o->X[f]); }
     free(o);
@@ -664,7 +673,7 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
 
     /* --- subgrid stress and heat flux: -div(tau), div(rho alpha grad theta) (Eq. stresstensor;
      * reading R6 for the Smagorinsky-Lilly form on a flat, possibly stretched grid) */
-    if (C->closure == 1 || C->closure == 2 || C->surface == 1) {
+    if (C->closure == 1 || C->closure == 2 || C->closure == 3 || C->surface == 1) {
         /* strain at cell centres (diagonal) and edges (off-diagonal), velocities at faces */
         double *S11 = dalloc(o->ncell), *S22 = dalloc(o->ncell), *S33 = dalloc(o->ncell);
         double *S12 = dalloc(o->ncell), *S13 = dalloc(o->nw), *S23 = dalloc(o->nw);
@@ -750,6 +759,35 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
             memset(t13, 0, sizeof(double) * o->nw); memset(t23, 0, sizeof(double) * o->nw);
             memset(hx, 0, sizeof(double) * o->ncell); memset(hy, 0, sizeof(double) * o->ncell);
             memset(hz, 0, sizeof(double) * o->nw);
+        }
+        if (C->closure == 3) {
+            /* learned closure: the model's cell-centre stresses t11, t22, t33 enter as they are;
+             * t12, t13, t23 are carried to their edges by the mean of the four cells around each
+             * edge (zero at the lid; the ground edges take MOST below, else zero); the heat flux
+             * goes to each face as the mean of its two cells, with the sign of the down-gradient
+             * flux h above (h = -rho h_model) */
+            o->sgs_model(o->sgs_user, rho, rt, ru, rv, rw, o->sgs_planes);
+            const double *P = o->sgs_planes;
+            size_t N = o->ncell;
+            #pragma omp parallel for
+            for (int k = 0; k < nz; ++k)
+                for (int j = 0; j < ny; ++j)
+                    for (int i = 0; i < nx; ++i) {
+                        size_t c = IX(o, i, j, k);
+                        t11[c] = P[c];
+                        t22[c] = P[N + c];
+                        t33[c] = P[2 * N + c];
+                        t12[c] = 0.25 * (P[3 * N + IX(o, i - 1, j - 1, k)] + P[3 * N + IX(o, i, j - 1, k)]
+                                       + P[3 * N + IX(o, i - 1, j, k)] + P[3 * N + c]);
+                        hx[c] = -0.5 * (P[6 * N + IX(o, i - 1, j, k)] + P[6 * N + c]);
+                        hy[c] = -0.5 * (P[7 * N + IX(o, i, j - 1, k)] + P[7 * N + c]);
+                        if (k == 0) continue;
+                        t13[c] = 0.25 * (P[4 * N + IX(o, i - 1, j, k - 1)] + P[4 * N + IX(o, i, j, k - 1)]
+                                       + P[4 * N + IX(o, i - 1, j, k)] + P[4 * N + c]);
+                        t23[c] = 0.25 * (P[5 * N + IX(o, i, j - 1, k - 1)] + P[5 * N + IX(o, i, j, k - 1)]
+                                       + P[5 * N + IX(o, i, j - 1, k)] + P[5 * N + c]);
+                        hz[c] = -0.5 * (P[8 * N + IX(o, i, j, k - 1)] + P[8 * N + c]);
+                    }
         }
         if (C->surface == 1) {
             /* MOST surface stress tau_i3 = -rho u*^2 u_i/|U| at the bottom edges; upward heat flux rho Q */
@@ -1104,8 +1142,17 @@ int orc_get_geom(orc *o, int which, double *dst) {
     memcpy(dst, src[which], sizeof(double) * (which < 6 ? o->ncell : o->nw));
     return 0;
 }
+/* the model of the learned closure (closure 3); it must be set before the first step */
+int orc_set_sgs_model(orc *o, void (*fn)(void *, const double *, const double *, const double *, const double *,
+                                         const double *, double *), void *user) {
+    if (!o->sgs_planes) o->sgs_planes = dalloc(9 * o->ncell);
+    o->sgs_model = fn;
+    o->sgs_user = user;
+    return 0;
+}
 int orc_step(orc *o, int nsteps) {
     if (!o->have_state) return -5;
+    if (o->c.closure == 3 && !o->sgs_model) return -5;
     for (int n = 0; n < nsteps; ++n) rk3_step(o);
     return 0;
 }
@@ -1113,6 +1160,7 @@ int orc_step(orc *o, int nsteps) {
  * the EOS fields p', pi, theta */
 int orc_slow_rhs(orc *o, double *Rr, double *Rt, double *Ru, double *Rv, double *Rw,
                  double *pp, double *pi, double *th) {
+    if (o->c.closure == 3 && !o->sgs_model) return -5;
     slow_rhs(o, o->rho, o->rt, o->ru, o->rv, o->rw);
     memcpy(Rr, o->R[F_RHO], sizeof(double) * o->ncell);
     memcpy(Rt, o->R[F_RT], sizeof(double) * o->ncell);

@@ -85,6 +85,8 @@ class OracleConfig:
 
 
 _LIB = None
+# model of the learned closure: (user, rho, rho theta, rho u, rho v, rho w, planes out)
+_SGS_FN = C.CFUNCTYPE(None, C.c_void_p, *([C.POINTER(C.c_double)] * 6))
 
 
 def _lib():
@@ -104,6 +106,7 @@ def _lib():
         L.orc_step.argtypes = [C.c_void_p, C.c_int]
         L.orc_slow_rhs.argtypes = [C.c_void_p] + [dp] * 8
         L.orc_get_mu.argtypes = [C.c_void_p, dp]
+        L.orc_set_sgs_model.argtypes = [C.c_void_p, _SGS_FN, C.c_void_p]
         L.orc_substep_once.argtypes = [C.c_void_p, C.c_double] + [dp] * 10
         L.orc_mass.restype = C.c_double
         L.orc_mass.argtypes = [C.c_void_p]
@@ -205,6 +208,23 @@ class Oracle:
         _lib().orc_get_geom(self._h, GEOM[name], _p(out))
         return out
 
+    def set_sgs_model(self, model):
+        """Model of the learned closure (configuration closure = 3): model(rho, rho theta, rho u,
+        rho v, rho w) -> array [9][nz][ny][nx] of the density-weighted cell-centre stresses
+        rho t11, t22, t33, t12, t13, t23 and heat fluxes rho h1, h2, h3, evaluated on every
+        stage state."""
+        sc, sw = self.shape_c, self.shape_w
+        n, nw = int(np.prod(sc)), int(np.prod(sw))
+
+        def call(_user, r, rt, ru, rv, rw, out):
+            a = [np.ctypeslib.as_array(q, shape=(nw if q is rw else n,)) for q in (r, rt, ru, rv, rw)]
+            planes = model(a[0].reshape(sc), a[1].reshape(sc), a[2].reshape(sc), a[3].reshape(sc),
+                           a[4].reshape(sw))
+            np.ctypeslib.as_array(out, shape=(9 * n,))[:] = np.asarray(planes, dtype=np.float64).reshape(-1)
+
+        self._sgs_cb = _SGS_FN(call)   # kept alive as long as the oracle
+        _lib().orc_set_sgs_model(self._h, self._sgs_cb, None)
+
     def step(self, n=1):
         rc = _lib().orc_step(self._h, int(n))
         assert rc == 0, rc
@@ -213,7 +233,8 @@ class Oracle:
         sc, sw = self.shape_c, self.shape_w
         out = [np.empty(sc), np.empty(sc), np.empty(sc), np.empty(sc), np.empty(sw),
                np.empty(sc), np.empty(sc), np.empty(sc)]
-        _lib().orc_slow_rhs(self._h, *[_p(x) for x in out])
+        rc = _lib().orc_slow_rhs(self._h, *[_p(x) for x in out])
+        assert rc == 0, rc
         keys = ["R_rho", "R_rhotheta", "R_rhou", "R_rhov", "R_rhow", "pp", "pi", "theta"]
         return dict(zip(keys, out))
 

@@ -275,3 +275,66 @@ def standardise_stats(A):
     sd = A.reshape(-1, A.shape[-1]).std(axis=0)
     sd = np.where(sd > 0, sd, 1.0)
     return mu, sd
+
+
+# ------------------------------------------------------------------ the closure inside a step
+def unpack_blob(blob: bytes):
+    """Inverse of pack_blob: (params, in_mean, in_std, out_mean, out_std), the FP32 values as
+    float64."""
+    head = np.frombuffer(blob[:8], dtype=np.uint32)
+    assert head[0] == 0x4D465245, "not a closure blob"
+    body = np.frombuffer(blob[8:], dtype=np.float32).astype(np.float64)
+    st, vec = body[:2 * N_IN + 2 * N_OUT], body[2 * N_IN + 2 * N_OUT:]
+    in_mu, in_sd = st[:N_IN], st[N_IN:2 * N_IN]
+    out_mu, out_sd = st[2 * N_IN:2 * N_IN + N_OUT], st[2 * N_IN + N_OUT:]
+    return unpack_params(vec), in_mu, in_sd, out_mu, out_sd
+
+
+class LearnedClosure:
+    """The learned SGS model of a stage state on a flat periodic C-grid, as the step uses it:
+    features -> standardise -> network (BF16 operands, as the tensor cores take them) ->
+    de-standardise -> backscatter limit; Smagorinsky-Lilly in any cell whose standardised input
+    leaves |z| <= 6 or whose output is not finite.  Returns the nine density-weighted
+    cell-centre planes rho t11, t22, t33, t12, t13, t23, rho h1, h2, h3.
+
+    Each call records the fallback count and the smallest distance of a cell's max |z| from the
+    threshold 6 (self.margin), so a test can tell whether a decision was close enough to the
+    threshold for FP32 and FP64 inputs to take it differently."""
+
+    def __init__(self, blob, zeta, dx, dy, theta0, Cs, Pr_t, g=9.81, bf16_operands=True):
+        self.params, self.in_mu, self.in_sd, self.out_mu, self.out_sd = unpack_blob(blob)
+        self.zeta, self.dx, self.dy = np.asarray(zeta, dtype=np.float64), dx, dy
+        self.theta0 = np.asarray(theta0, dtype=np.float64)
+        self.Pr_t, self.g, self.bf16 = Pr_t, g, bf16_operands
+        dz = np.diff(self.zeta)
+        self.delta2 = (Cs * np.cbrt(dx * dy * dz)) ** 2       # (Cs Delta)^2 per level
+        self.margin = np.inf
+        self.fallbacks = []
+
+    def __call__(self, rho, rt, ru, rv, rw):
+        F = features(rho, rt, ru, rv, rw, self.zeta, self.dx, self.dy, self.theta0, self.g)
+        shp = rho.shape
+        Fn = F.reshape(-1, N_IN)
+        d2 = np.broadcast_to(self.delta2[:, None, None], shp).reshape(-1)
+        Z = (Fn - self.in_mu) / self.in_sd
+        zmax = np.max(np.abs(Z), axis=1)
+        self.margin = min(self.margin, float(np.min(np.abs(zmax - 6.0))))
+        fb = ~(zmax <= 6.0)
+        Y, _ = forward(self.params, Z, bf16_inputs=self.bf16)
+        Y = Y * self.out_sd + self.out_mu
+        fb |= ~np.all(np.isfinite(Y), axis=1)
+        Y = clip_backscatter(np.where(np.isfinite(Y), Y, 0.0), Fn, d2)
+        # Smagorinsky-Lilly fallback: stress -2 nu dev(S), heat flux -nu/Pr_t grad(theta)
+        S = strain_from_features(Fn)
+        SS = S[:, 0] ** 2 + S[:, 1] ** 2 + S[:, 2] ** 2 + 2 * (S[:, 3] ** 2 + S[:, 4] ** 2 + S[:, 5] ** 2)
+        nu = d2 * np.sqrt(2 * SS)
+        zc = 0.5 * (self.zeta[:-1] + self.zeta[1:])
+        dthdz = _ddz_c(rt / rho, zc).reshape(-1)
+        Ys = np.empty_like(Y)
+        Ys[:, :6] = smagorinsky_stress(Fn, d2)
+        Ys[:, 6] = -nu / self.Pr_t * Fn[:, 9]
+        Ys[:, 7] = -nu / self.Pr_t * Fn[:, 10]
+        Ys[:, 8] = -nu / self.Pr_t * dthdz
+        out = np.where(fb[:, None], Ys, Y) * rho.reshape(-1)[:, None]
+        self.fallbacks.append(int(np.sum(fb)))
+        return out.T.reshape((N_OUT,) + shp)

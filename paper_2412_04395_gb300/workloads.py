@@ -107,12 +107,18 @@ def splitmix64(x: np.ndarray) -> np.ndarray:
     return z ^ (z >> np.uint64(31))
 
 
-def seeded_noise(shape, seed: int, amplitude: float) -> np.ndarray:
-    """Uniform noise in [-amplitude, amplitude] from splitmix64(seed xor global cell index)."""
-    idx = np.arange(int(np.prod(shape)), dtype=np.uint64)
-    bits = splitmix64(idx ^ np.uint64(seed))
+def seeded_noise_at(index: np.ndarray, seed: int, amplitude: float) -> np.ndarray:
+    """Uniform noise in [-amplitude, amplitude] from splitmix64(seed xor global cell index), at the
+    given global cell indices (k ny + j) nx + i."""
+    bits = splitmix64(np.asarray(index, dtype=np.uint64) ^ np.uint64(seed))
     u01 = (bits >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
-    return (amplitude * (2.0 * u01 - 1.0)).reshape(shape)
+    return amplitude * (2.0 * u01 - 1.0)
+
+
+def seeded_noise(shape, seed: int, amplitude: float) -> np.ndarray:
+    """seeded_noise_at over a whole [k][j][i] grid."""
+    idx = np.arange(int(np.prod(shape)), dtype=np.uint64)
+    return seeded_noise_at(idx, seed, amplitude).reshape(shape)
 
 
 # ---------------------------------------------------------------------------------- cases
@@ -187,6 +193,7 @@ def hill_bubble(nx=256, ny=256, nz=128, steps=500, dx=50.0, dz0=20.0, ratio=1.01
 
 
 NOISE_SEED = 20241205
+NOISE_TOP = 400.0   # seeded theta noise below this height [m]
 
 
 def _abl_common(nx, ny, nz, dx, knots, noise_top, steps, dt, name, flux, precision):
@@ -207,7 +214,7 @@ def neutral_abl(nx=1024, ny=1024, nz=128, steps=100, dx=10.0, precision=PREC_MIX
     top = nz * dx
     knots = (np.array([0.0, 500.0, 650.0, max(top, 651.0)]),
              np.array([300.0, 300.0, 301.5, 301.5 + 3.0e-3 * (max(top, 651.0) - 650.0)]))
-    return _abl_common(nx, ny, nz, dx, knots, 400.0, steps, 0.1, "neutral_abl", 0.0, precision)
+    return _abl_common(nx, ny, nz, dx, knots, NOISE_TOP, steps, 0.1, "neutral_abl", 0.0, precision)
 
 
 def convective_abl(nx=2048, ny=2048, nz=160, steps=1000, dx=40.0, precision=PREC_MIXED32) -> Workload:
@@ -216,7 +223,7 @@ def convective_abl(nx=2048, ny=2048, nz=160, steps=1000, dx=40.0, precision=PREC
     top = nz * dx
     knots = (np.array([0.0, 1000.0, 1100.0, max(top, 1101.0)]),
              np.array([300.0, 300.0, 305.0, 305.0 + 3.0e-3 * (max(top, 1101.0) - 1100.0)]))
-    return _abl_common(nx, ny, nz, dx, knots, 400.0, steps, 0.4, "convective_abl", 0.2, precision)
+    return _abl_common(nx, ny, nz, dx, knots, NOISE_TOP, steps, 0.4, "convective_abl", 0.2, precision)
 
 
 def paper_scaling(nx=512, ny=512, nz=256, steps=100, dx=4.0, precision=PREC_FP64) -> Workload:
@@ -227,8 +234,56 @@ def paper_scaling(nx=512, ny=512, nz=256, steps=100, dx=4.0, precision=PREC_FP64
     top = nz * dx
     knots = (np.array([0.0, 500.0, 650.0, max(top, 651.0)]),
              np.array([300.0, 300.0, 301.5, 301.5 + 3.0e-3 * (max(top, 651.0) - 650.0)]))
-    wl = _abl_common(nx, ny, nz, dx, knots, 400.0, steps, 0.04, "paper_scaling", 0.0, precision)
+    wl = _abl_common(nx, ny, nz, dx, knots, NOISE_TOP, steps, 0.04, "paper_scaling", 0.0, precision)
     return wl.with_(mom_adv=MOM_UPWIND3, scal_adv=SCAL_UPWIND3)
+
+
+def abl_window(case, nx_full: int, ny_full: int, i0: int, j0: int, nx: int, ny: int, **kw) -> Workload:
+    """The nx x ny columns starting at (i0, j0) (periodic wrap) of an ABL case (neutral_abl,
+    convective_abl or paper_scaling) of nx_full x ny_full columns, as a periodic workload of its
+    own: the same levels, sounding and settings, and the full case's initial noise at those
+    columns (drawn at their global cell indices, so no full-size array is built)."""
+    wl = case(nx=nx, ny=ny, **kw)
+    ii = (i0 + np.arange(nx)) % nx_full
+    jj = (j0 + np.arange(ny)) % ny_full
+    K, J, I = np.meshgrid(np.arange(wl.nz, dtype=np.uint64), jj.astype(np.uint64), ii.astype(np.uint64),
+                          indexing="ij")
+    noise = seeded_noise_at((K * np.uint64(ny_full) + J) * np.uint64(nx_full) + I, NOISE_SEED, 0.25)
+    zc = 0.5 * (wl.zeta[:-1] + wl.zeta[1:])
+    dth = np.where(zc[:, None, None] < NOISE_TOP, noise, 0.0)
+    return wl.with_(dtheta=dth, notes=wl.notes + f" (window {nx}x{ny} at ({i0}, {j0}) of {nx_full}x{ny_full})")
+
+
+def smooth_velocity(nx_full: int, ny_full: int, nz: int, seed: int, amplitude: float, i0: int = 0, j0: int = 0,
+                    nx: Optional[int] = None, ny: Optional[int] = None, modes: int = 6, kmax: int = 48):
+    """Resolved velocity perturbations (u', v', w') of a periodic domain of nx_full x ny_full columns
+    and nz levels, on the nx x ny columns from (i0, j0) (default: the whole domain): for each
+    component a sum of `modes` separable Fourier modes sin(2 pi kx x + a) cos(2 pi ky y + b) with
+    integer wavenumbers 1..kmax over the domain and seeded amplitudes and phases, times the vertical
+    envelope sin(pi z / z_top).  u' sits at x-faces, v' at y-faces, w' at w-faces (zero at both
+    walls).  Being a formula of the global position, any window of it equals the whole field
+    restricted to those columns."""
+    nx = nx_full if nx is None else nx
+    ny = ny_full if ny is None else ny
+    rng = np.random.default_rng(seed)
+    ii = (i0 + np.arange(nx)) % nx_full
+    jj = (j0 + np.arange(ny)) % ny_full
+    out = []
+    for comp in range(3):
+        xs = (ii + (0.0 if comp == 0 else 0.5)) / nx_full        # u at x-faces, v and w at centres
+        ys = (jj + (0.0 if comp == 1 else 0.5)) / ny_full
+        zs = (np.arange(nz + 1) / nz) if comp == 2 else ((np.arange(nz) + 0.5) / nz)
+        plane = np.zeros((ny, nx))
+        for _ in range(modes):
+            a = amplitude * rng.standard_normal() / np.sqrt(modes)
+            kx, ky = rng.integers(1, kmax + 1, size=2)
+            px, py = rng.uniform(0.0, 2.0 * np.pi, size=2)
+            plane += a * np.outer(np.cos(2.0 * np.pi * ky * ys + py), np.sin(2.0 * np.pi * kx * xs + px))
+        env = np.sin(np.pi * zs)
+        if comp == 2:
+            env[0] = env[-1] = 0.0
+        out.append(env[:, None, None] * plane[None])
+    return tuple(out)
 
 
 def with_tracer(wl: Workload, kind: str = "blob", radius_frac: float = 0.2) -> Workload:

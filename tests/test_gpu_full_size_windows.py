@@ -1,0 +1,208 @@
+"""Parity at the full sizes of the neutral ABL (1024 x 1024 x 128) and the convective ABL
+(2048 x 2048 x 160) on sampled windows.
+
+The GPU runs one RK3 step of the whole domain in the configuration the benchmark times (CUDA-graph
+step, default column-sweep fusion).  The oracle cannot step those domains in seconds, but one step
+only carries information a bounded number of columns sideways (the stencils of three slow passes
+and one column per acoustic substep, 16 substeps here): the oracle steps a periodic window of
+W x W columns cut from the same seeded initial state (workloads.abl_window draws the noise at the
+full grid's cell indices), and the window's central (W - 2 M) x (W - 2 M) columns, M columns away
+from the window's edges, then hold exactly the full domain's values.  That M exceeds the reach of
+one step is checked on the CPU (tests/test_oracle_windows.py: two window sizes agree bit for bit on
+a centre wider than the one compared here).
+
+Windows: one centred on the periodic corner (so the compared columns straddle both periodic seams)
+and one at a seeded interior position.  Bounds as for the other cases: FP64 within 1e-11 (rho and
+rho theta per field, momenta against the momentum-vector norm); mixed precision within 1e-8 and
+1e-6.  The learned closure on the convective ABL (the shipped trained network): its inference
+at full size against the oracle model, and the state after the step against the oracle step
+(see _check_learned)."""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+from paper_2412_04395_gb300 import workloads as W
+from conftest import make_oracle
+
+pytestmark = pytest.mark.gpu
+FIELDS = ("rho", "rhotheta", "rhou", "rhov", "rhow")
+WIN, MARGIN = 128, 48          # compared centre: 32 x 32 columns, every level
+WIN_L, MARGIN_L = 80, 32       # learned closure (the FP64 network oracle is slower): 16 x 16
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    import __graft_entry__ as ge
+    ge.build()
+
+
+def _blob():
+    import os
+    from paper_2412_04395_gb300 import erf
+    path = os.path.join(os.path.dirname(erf.__file__), "data", "closure_convective_abl.bin")
+    with open(path, "rb") as f:
+        return f.read()
+
+
+def _gpu_step(full, blob=None):
+    from paper_2412_04395_gb300.erf import Dycore
+    d = Dycore(full)
+    d.erf_set_initial(full.dtheta, full.u, full.v, full.w)
+    if blob is not None:
+        d.erf_set_closure_weights(blob)
+    d.erf_rk3_step(1)
+    assert d.erf_diagnostics()["status"] == 0
+    return d
+
+
+def _gpu_window(d, full, i0, j0, n):
+    """Fields of the GPU state on the n x n columns from (i0, j0), periodic wrap."""
+    import torch
+    ii = torch.as_tensor((i0 + np.arange(n)) % full.nx, device="cuda")
+    jj = torch.as_tensor((j0 + np.arange(n)) % full.ny, device="cuda")
+    out = {}
+    for f in FIELDS:
+        t = torch.empty(d._shape(f), dtype=torch.float64, device="cuda")
+        d.erf_get_state(f, out=t)
+        torch.cuda.synchronize()
+        out[f] = t.index_select(1, jj).index_select(2, ii).cpu().numpy()
+        del t
+    return out
+
+
+def _window_oracle(case, full, i0, j0, n, blob=None, **kw):
+    wl = W.abl_window(case, full.nx, full.ny, i0, j0, n, n, nz=full.nz, dx=full.dx, **kw)
+    if blob is None:
+        o = make_oracle(wl.with_(closure=full.closure))
+        m = None
+    else:
+        o = make_oracle(wl.with_(closure=W.CLOSURE_LEARNED))
+        th0 = o.get("base_theta")[:, 0, 0]
+        m = M.LearnedClosure(blob, wl.zeta, wl.dx, wl.dy, th0, wl.Cs, wl.Pr_t, wl.gravity)
+        o.set_sgs_model(m)
+    o.step(1)
+    return o.state(), m
+
+
+def _errors(g, r, margin):
+    c = slice(margin, -margin)
+    g = {f: a[:, c, c] for f, a in g.items()}
+    r = {f: a[:, c, c] for f, a in r.items()}
+    mom = np.sqrt(sum(np.linalg.norm(r[f]) ** 2 for f in ("rhou", "rhov", "rhow")))
+    out = {}
+    for f in FIELDS:
+        assert np.all(np.isfinite(g[f])), f
+        den = np.linalg.norm(r[f]) if f in ("rho", "rhotheta") else mom
+        out[f] = float(np.linalg.norm(g[f] - r[f]) / den)
+    return out
+
+
+def _centres(full, seed):
+    rng = np.random.default_rng(seed)
+    return [(0, 0), (int(rng.integers(full.nx)), int(rng.integers(full.ny)))]
+
+
+def _check(case, full, bounds, win=WIN, margin=MARGIN, seed=7):
+    """GPU windows of one full-size step against oracle windows."""
+    d = _gpu_step(full)
+    for ci, cj in _centres(full, seed):
+        i0, j0 = ci - win // 2, cj - win // 2
+        g = _gpu_window(d, full, i0, j0, win)
+        r, _ = _window_oracle(case, full, i0, j0, win)
+        e = _errors(g, r, margin)
+        print(full.name, full.nx, full.ny, full.nz, "precision", full.precision, "window centre", (ci, cj), e)
+        for f, b in bounds.items():
+            assert e[f] < b, (f, e[f], b)
+    d.close()
+
+
+VEL_SEED, VEL_AMP = 29, 1.0
+
+
+def _check_learned(case, full, blob, win=WIN_L, margin=MARGIN_L):
+    """The learned closure at full size, on the window across the periodic corner.
+
+    The configured initial state is a uniform wind: its resolved strain is zero up to rounding,
+    and the backscatter limit (which compares a transfer linear in the strain with a bound cubic
+    in it) is then decided by rounding noise, differently in FP32 and FP64.  The state here adds
+    resolved velocity perturbations of about 1 m/s (workloads.smooth_velocity, strain ~4e-3 1/s),
+    which make every decision well conditioned.
+
+    1. Inference: the network's nine density-weighted planes at the initial state (the same kernel
+       and launch as inside the step), against the BF16-emulating oracle model on the window.  The
+       trained network's outputs are small differences of O(1) terms, so BF16 operands move them
+       by 2e-2 .. 2e-1 (the oracle's BF16 model against its FP64 model); each output must stay
+       within 5e-3, or within 0.3 x that BF16 effect where it is larger.
+    2. The state after one step, against the oracle step with that model, within the
+       mixed-precision bounds (measured: rho 1.0e-9, momenta <= 1.2e-7; the oracle's own BF16 and
+       FP64 networks differ by 6.9e-9 and 6.3e-7 after that step)."""
+    import torch
+    c = slice(margin, -margin)
+    i0 = j0 = -(win // 2)
+    d = _gpu_step_prepared(full, blob)
+    tau, _ = d.erf_closure_fields()
+    torch.cuda.synchronize()
+    ii = torch.as_tensor((i0 + np.arange(win)) % full.nx, device="cuda")
+    jj = torch.as_tensor((j0 + np.arange(win)) % full.ny, device="cuda")
+    tg = tau.index_select(2, jj).index_select(3, ii).cpu().numpy().astype(np.float64)
+    del tau
+    d.erf_rk3_step(1)
+    assert d.erf_diagnostics()["status"] == 0
+    g = _gpu_window(d, full, i0, j0, win)
+    d.close()
+    del d
+
+    wl = W.abl_window(case, full.nx, full.ny, i0, j0, win, win, nz=full.nz, dx=full.dx)
+    up, vp, wp = W.smooth_velocity(full.nx, full.ny, full.nz, VEL_SEED, VEL_AMP, i0, j0, win, win)
+    wl = wl.with_(u=wl.u + up, v=vp, w=wp)
+    res, taus = {}, {}
+    for tag, bf in (("bf16", True), ("fp64", False)):
+        o = make_oracle(wl.with_(closure=W.CLOSURE_LEARNED))
+        th0 = o.get("base_theta")[:, 0, 0]
+        m = M.LearnedClosure(blob, wl.zeta, wl.dx, wl.dy, th0, wl.Cs, wl.Pr_t, wl.gravity, bf16_operands=bf)
+        taus[tag] = m(*[o.get(f) for f in FIELDS])
+        o.set_sgs_model(m)
+        o.step(1)
+        assert m.margin > 1e-3, m.margin   # no fallback decision near the threshold
+        res[tag] = o.state()
+    rel = lambda a, b: float(np.linalg.norm(a[:, c, c] - b[:, c, c]) / np.linalg.norm(b[:, c, c]))
+    errs = [rel(tg[q], taus["bf16"][q]) for q in range(9)]
+    bf16_gap = [rel(taus["fp64"][q], taus["bf16"][q]) for q in range(9)]
+    print(full.name, "full-size BF16 inference vs oracle, relative L2 per output:", ["%.1e" % x for x in errs])
+    print(full.name, "oracle BF16 vs FP64 network, per output:", ["%.1e" % x for x in bf16_gap])
+    for q in range(9):
+        assert errs[q] < max(5e-3, 0.3 * bf16_gap[q]), (q, errs[q], bf16_gap[q])
+    e = _errors(g, res["bf16"], margin)
+    s = _errors(res["fp64"], res["bf16"], margin)
+    print(full.name, "learned closure, GPU vs oracle:", e, "oracle BF16 vs FP64 network:", s)
+    for f in FIELDS:
+        assert e[f] < MIXED[f], (f, e[f], s[f])
+
+
+def _gpu_step_prepared(full, blob):
+    from paper_2412_04395_gb300.erf import Dycore
+    d = Dycore(full)
+    d.erf_set_initial(full.dtheta, full.u, full.v, full.w)
+    d.erf_set_closure_weights(blob)
+    return d
+
+
+FP64 = {"rho": 1e-11, "rhotheta": 1e-11, "rhou": 1e-11, "rhov": 1e-11, "rhow": 1e-11}
+MIXED = {"rho": 1e-8, "rhotheta": 1e-8, "rhou": 1e-6, "rhov": 1e-6, "rhow": 1e-6}
+
+
+def test_neutral_abl_full_size_fp64_and_mixed():
+    full = W.neutral_abl()
+    assert (full.nx, full.ny, full.nz) == (1024, 1024, 128)
+    _check(W.neutral_abl, full, MIXED)
+    _check(W.neutral_abl, full.with_(precision=W.PREC_FP64), FP64)
+
+
+def test_convective_abl_full_size_mixed_smagorinsky_and_learned():
+    full = W.convective_abl()
+    assert (full.nx, full.ny, full.nz) == (2048, 2048, 160)
+    _check(W.convective_abl, full, MIXED, seed=11)
+    up, vp, wp = W.smooth_velocity(full.nx, full.ny, full.nz, VEL_SEED, VEL_AMP)
+    full = full.with_(closure=W.CLOSURE_LEARNED, u=full.u + up, v=vp, w=wp)
+    del up
+    _check_learned(W.convective_abl, full, _blob())
