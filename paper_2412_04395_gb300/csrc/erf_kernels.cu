@@ -651,59 +651,76 @@ __global__ void k_rhs_w(Geo g, Phys ph, CF5 st, const double *pp, const double *
 // ------------------------------------------------------------------ acoustic substeps (App. C)
 
 // Per column: coefficients of the vertical system in Omega'' (reading R11) for this stage's
-// dtau, and their LU factors (Thomas forward elimination without the right-hand side).
-__global__ void k_tri_build(Geo g, Phys ph, const double *rho, const double *rt, const double *pi, const double *th,
-                            double dtau, Tri tr, double *TX, double *TY) {
+// dtau, and their LU factors (Thomas forward elimination without the right-hand side).  With
+// E = dtau b2^2, the sums S_pi = pi_{k-1} + pi_k, S_rho = rho_{k-1} + rho_k and the w-face means
+// thw of theta, the rows are
+//   P = dtau (-C_pg + C_b pi_k / Theta_k),  Q = dtau (C_pg + C_b pi_{k-1} / Theta_{k-1}),
+//   C_pg = gamma R_d (S_pi / 2) / dz_c,  C_b = g (R_d / c_v) (S_rho / 2) / S_pi,
+//   a = (E Gg - E Q thw_{k-1/2}) / H_{k-1},  c = (E P thw_{k+1/2} - E Gg) / H_k,
+//   b = 1 + thw_k (E Q / H_{k-1} - E P / H_k) + E Gg (1 / H_k - 1 / H_{k-1}),  Gg = dtau g / 2,
+// with the stage constants (dtau, E, E Gg, the halves) formed on the host (TriK).  The w-face
+// means of theta are carried up the column (each one is formed once).  Alongside: H theta^t at
+// x- and y-faces (TX, TY) and dtau (-gamma R_d) (pi_{i-1} + pi_i) / 2 at x- and y-faces (PX, PY),
+// the stage-fixed factors of the substeps' Theta'' fluxes and pressure gradients.
+struct TriK {
+    double E, EGg;    // dtau b2^2, E dtau g / 2
+    double cpg;       // dtau gamma R_d / 2
+    double kgb;       // dtau g (R_d / c_v) / 2
+    double dpx;       // -dtau gamma R_d / 2
+};
+__global__ void k_tri_build(Geo g, const double *rho, const double *rt, const double *pi, const double *th, TriK tk,
+                            Tri tr, double *TX, double *TY, double *PX, double *PY) {
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= g.nxy) return;
     int i = (int)(n % g.nx), j = (int)(n / g.nx);
-    double b2 = ph.b2;
-    double E = dtau * b2 * b2, Gg = dtau * 0.5 * ph.g;
-    double gRd = GAMMA * RD;
+    const double E = tk.E, EGg = tk.EGg;
     double cp_prev = 0.0;
     double rrt_m = rcp_d(rt[cix(g, i, j, 0)]), rHm = rHc(g, i, j, 0);
-    // H theta^t at the x- and y-faces of the column (stage-fixed factors of the Theta'' flux)
-    auto face_theta = [&](int k) {
+    auto face_factors = [&](int k) {
         long long c = cix(g, i, j, k);
-        double thc = th[c];
+        double thc = th[c], pic = pi[c];
         TX[c] = Hx(g, i, j, k) * (0.5 * (cval(g, th, i - 1, j, k) + thc));
         TY[c] = Hy(g, i, j, k) * (0.5 * (cval(g, th, i, j - 1, k) + thc));
+        PX[c] = tk.dpx * (cval(g, pi, i - 1, j, k) + pic);
+        PY[c] = tk.dpx * (cval(g, pi, i, j - 1, k) + pic);
     };
-    face_theta(0);
+    face_factors(0);
+    double th_m = th[cix(g, i, j, 0)];
+    double thw_m = th_m;                                 // the wall reflection: theta_{-1} = theta_0
+    double thw_k = 0.5 * (th_m + cval(g, th, i, j, 1));
     for (int k = 1; k < g.nz; ++k) {
-        face_theta(k);
-        long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1), w = c;
-        double rdz = rdzcw(g, i, j, k);
-        double pic = pi[c], pim = pi[cm];
-        double pib = 0.5 * (pim + pic), rpib = rcp_d(pib);
-        double rhob = 0.5 * (rho[cm] + rho[c]);
-        double rrt_c = rcp_d(rt[c]), rHk = rHc(g, i, j, k);
-        double Cpg = gRd * pib * rdz;
-        double gb = ph.g * rhob * (RD / CVD) * 0.5 * rpib;
-        double Cbp = gb * pic * rrt_c;
-        double Cbm = gb * pim * rrt_m;
-        double P = dtau * (-Cpg + Cbp), Q = dtau * (Cpg + Cbm);
-        double thw_m = 0.5 * (cval(g, th, i, j, k - 2) + th[cm]);
-        double thw_k = 0.5 * (th[cm] + th[c]);
+        face_factors(k);
+        long long c = cix(g, i, j, k), cm = c - g.nxy, w = c;
         double thw_p = 0.5 * (th[c] + cval(g, th, i, j, k + 1));
-        double a = E * (Gg - Q * thw_m) * rHm;
-        double b = 1.0 - P * E * thw_k * rHk + Q * E * thw_k * rHm + Gg * E * (rHk - rHm);
-        double cc = E * (P * thw_p - Gg) * rHk;
-        double m = b - a * cp_prev;
-        double im = rcp_d(m);
+        double pic = pi[c], pim = pi[cm];
+        double Spi = pim + pic;
+        double Cpg = tk.cpg * Spi * rdzcw(g, i, j, k);
+        double Cb = tk.kgb * (rho[cm] + rho[c]) * rcp_d(Spi);
+        double rrt_c = rcp_d(rt[c]), rHk = rHc(g, i, j, k);
+        double P = fma(Cb * pic, rrt_c, -Cpg);
+        double Q = fma(Cb * pim, rrt_m, Cpg);
+        double Pe = E * P, Qe = E * Q;
+        double a = fma(-Qe, thw_m, EGg) * rHm;
+        double cc = fma(Pe, thw_p, -EGg) * rHk;
+        double b = fma(thw_k, fma(-Pe, rHk, Qe * rHm), 1.0);
+        b = fma(EGg, rHk - rHm, b);
+        double im = rcp_d(fma(-a, cp_prev, b));
         double cpk = cc * im;
         tr.a[w] = a; tr.cp[w] = cpk; tr.im[w] = im; tr.P[w] = P; tr.Q[w] = Q;
         cp_prev = cpk;
         rrt_m = rrt_c;
         rHm = rHk;
+        thw_m = thw_k;
+        thw_k = thw_p;
     }
 }
 
 // horizontal momenta: Delta U'' = dtau (-gamma R_d pi^t (dTheta~/dxi - h_xi/h_zeta dTheta~/dzeta) + R_U),
 // Theta~ = Theta'' + beta_d (Theta'' - Theta''_prev) (reading R10), which the previous vertical
-// solve (or the stage start, where Theta~ = Theta'') left in Tt.
-__global__ void k_sub_horiz(Geo g, Phys ph, const double *pi, const double *Tt, const double *Ru, const double *Rv,
-                            double *Xu, double *Xv, double dtau) {
+// solve (or the stage start, where Theta~ = Theta'') left in Tt.  PX, PY hold the stage's
+// dtau (-gamma R_d) pi^t at x- and y-faces.
+__global__ void k_sub_horiz(Geo g, const double *PX, const double *PY, const double *Tt, const double *Ru,
+                            const double *Rv, double *Xu, double *Xv, double dtau) {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= g.nc) return;
     int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
@@ -718,12 +735,8 @@ __global__ void k_sub_horiz(Geo g, Phys ph, const double *pi, const double *Tt, 
         gx -= hxi_x2(g, i, j, k) * (dc + dxm);
         gy -= heta_y2(g, i, j, k) * (dc + dym);
     }
-    // -gamma R_d pi^x: the face average's 1/2 is folded into the constant (exact, so the result
-    // is unchanged)
-    constexpr double cgr = -0.5 * (GAMMA * RD);
-    double pic = pi[c];
-    Xu[c] += dtau * (cgr * (cval(g, pi, i - 1, j, k) + pic) * gx + Ru[c]);
-    Xv[c] += dtau * (cgr * (cval(g, pi, i, j - 1, k) + pic) * gy + Rv[c]);
+    Xu[c] = fma(dtau, Ru[c], fma(PX[c], gx, Xu[c]));
+    Xv[c] = fma(dtau, Rv[c], fma(PY[c], gy, Xv[c]));
 }
 
 // Vertical acoustic update (App. C rows 3-5) in three kernels.  Part 1, one thread per cell:
@@ -1073,14 +1086,22 @@ void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, double *pp, const dou
     }
 }
 void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const double *rt, const double *pi,
-                      const double *th, double dtau, Tri tr, double *TX, double *TY, cudaStream_t s) {
-    LAUNCH("tri_build", s, k_tri_build<<<nblk(g.nxy, 128), 128, 0, s>>>(g, ph, rho, rt, pi, th, dtau, tr, TX, TY));
+                      const double *th, double dtau, Tri tr, double *TX, double *TY, double *PX, double *PY,
+                      cudaStream_t s) {
+    TriK tk;
+    tk.E = dtau * ph.b2 * ph.b2;
+    tk.EGg = tk.E * (dtau * 0.5 * ph.g);
+    tk.cpg = dtau * (GAMMA * RD) * 0.5;
+    tk.kgb = dtau * ph.g * (RD / CVD) * 0.5;
+    tk.dpx = -tk.cpg;
+    LAUNCH("tri_build", s, k_tri_build<<<nblk(g.nxy, 128), 128, 0, s>>>(g, rho, rt, pi, th, tk, tr, TX, TY, PX, PY));
 }
-void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *pi, const double *th, const double *TX,
-                    const double *TY, CF5 R, F5 x, double *Om, double *Tp, double *X0, double *Y0, double *Ash,
+void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *PX, const double *PY, const double *th,
+                    const double *TX, const double *TY, CF5 R, F5 x, double *Om, double *Tp, double *X0, double *Y0,
+                    double *Ash,
                     double *msx, double *msy, double *msz, double dtau, cudaStream_t s) {
     const dim3 g3c((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)g.nz);
-    LAUNCH("sub_horiz", s, k_sub_horiz<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, pi, Tp, R.u, R.v, x.u, x.v, dtau));
+    LAUNCH("sub_horiz", s, k_sub_horiz<<<nblk(g.nc, BS), BS, 0, s>>>(g, PX, PY, Tp, R.u, R.v, x.u, x.v, dtau));
     LAUNCH("sub_expl", s, k_sub_expl<<<g3c, 128, 0, s>>>(g, ph, th, TX, TY, R.r, R.t, R.w, x, Om, Tp, X0, Y0, Ash,
                                                          msx, msy, msz, dtau));
     LAUNCH("sub_col", s, k_sub_col<<<nblk(g.nxy, 128), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q, X0, Y0,
