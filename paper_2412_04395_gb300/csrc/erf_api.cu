@@ -262,7 +262,6 @@ static void fill_geo(erf_handle *h) {
     P.rPr_t = 1.0 / c.Pr_t;
     P.b1 = 0.5 * (1.0 - c.beta_s);
     P.b2 = 0.5 * (1.0 + c.beta_s);
-    P.b1h = 0.5 * P.b1;
     P.closure = c.closure; P.surface = c.surface; P.scal_adv = c.scal_adv;
     P.mom3 = c.mom_adv == 3 ? 1 : 0;
 }
@@ -451,12 +450,12 @@ static void enqueue_step(erf_handle *h, cudaStream_t s) {
         int nsub = stage == 0 ? 1 : (stage == 1 ? c.n_substeps / 2 : c.n_substeps);
         double dtau = stage == 0 ? c.dt / 3.0 : c.dt / c.n_substeps;
         // the slow-tendency scratch is free once the tendencies exist: the mass-flux arrays take
-        // the stage's H theta at faces, two planes of the flux buffer its pressure-gradient
-        // factors, the face velocities the substeps' X0, Y0 and metric shift
-        double *PX = h->flux, *PY = h->flux + g.nw;
-        launch_tri_build(g, ph, h->st.r, h->st.t, h->pi, h->th, dtau, h->tri, h->mfx, h->mfy, PX, PY, s);
+        // the stage's H theta at faces, the planes of the flux buffer its pressure-gradient
+        // factors and w-face theta, the face velocities the substeps' X0, Y0 and metric shift
+        double *PX = h->flux, *PY = h->flux + g.nw, *THW = h->flux + 2 * g.nw;
+        launch_tri_build(g, ph, h->st.r, h->st.t, h->pi, h->th, dtau, h->tri, h->mfx, h->mfy, PX, PY, THW, s);
         for (int n = 0; n < nsub; ++n)
-            launch_substep(g, ph, h->tri, PX, PY, h->th, h->mfx, h->mfy, cf(h->R), h->x, h->Om, h->Tp, h->ux, h->vy,
+            launch_substep(g, ph, h->tri, PX, PY, THW, h->mfx, h->mfy, cf(h->R), h->x, h->Om, h->Tp, h->ux, h->vy,
                            h->wz, h->msx, h->msy, h->msz, dtau, s);
         // the passive scalar after the substeps, from the stage state S^t (Sec. 3.1)
         if (h->tphi)

@@ -52,7 +52,7 @@ struct Geo {
 
 struct Phys {
     double g, f_cor, u_g, v_g, Cs, Pr_t, nu, z0, Qs, beta_s, beta_d, rPr_t;
-    double b1, b2, b1h;   // substep off-centring weights (1 - beta_s)/2, (1 + beta_s)/2 and b1/2, formed on the host
+    double b1, b2;        // substep off-centring weights (1 - beta_s)/2, (1 + beta_s)/2, formed on the host
     int closure, surface, scal_adv;
     int mom3;   // 1: upwind-3 momentum interpolant instead of upwind-5
 };

@@ -28,21 +28,17 @@ __device__ __forceinline__ double sgnd(double x) { return sgnT<double>(x); }
 // subtracted exactly and an undisturbed column keeps p' = 0 bit for bit.
 __device__ __forceinline__ void eos_pi(double rt, double &p, double &pi) {
     // pi = x^(R_d/c_v) with x = R_d rho theta / P00 and R_d/c_v = 2/5, so pi = x z with
-    // z = a^(-1/5), a = x^3.  z starts from an FP32 estimate and takes two Newton steps of the
-    // reciprocal n-th root, z <- z + z (1 - a z^n)/n (no division; the relative error e
-    // becomes ~(n+1)/2 e^2 per step: 1e-6 -> 3e-12 -> rounding), so the FP64 cost is 17
-    // multiply/FMA instead of a general pow.
-    static_assert(RD / CVD == 0.4, "the Newton form of the EOS assumes R_d/c_v = 2/5");
+    // z = a^(-1/5), a = x^3.  z starts from an FP32 estimate z0 (relative error ~1e-7) and takes
+    // one step of the binomial series of the correction: with r = 1 - a z0^5, z = z0 (1 - r)^(-1/5)
+    // = z0 (1 + r/5 + 3 r^2/25 + O(r^3)), so the error becomes O(r^3) ~ 1e-21, below rounding (no
+    // division; 8 FP64 multiply/FMA for the root instead of a general pow).
+    static_assert(RD / CVD == 0.4, "this form of the EOS assumes R_d/c_v = 2/5");
     double x = RD * rt * (1.0 / P00);
     double a = x * x * x;
     double z = (double)exp2f(-0.6f * log2f((float)x));
-    #pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        double z2 = z * z;
-        double z5 = z2 * z2 * z;
-        double r = fma(-a, z5, 1.0);
-        z = fma(z * 0.2, r, z);
-    }
+    double z2 = z * z;
+    double r = fma(-a, z2 * z2 * z, 1.0);
+    z = fma(z, fma(0.12, r, 0.2) * r, z);
     pi = x * z;
     p = __dmul_rn(RD * rt, pi);
 }
@@ -659,7 +655,8 @@ __global__ void k_rhs_w(Geo g, Phys ph, CF5 st, const double *pp, const double *
 //   a = (E Gg - E Q thw_{k-1/2}) / H_{k-1},  c = (E P thw_{k+1/2} - E Gg) / H_k,
 //   b = 1 + thw_k (E Q / H_{k-1} - E P / H_k) + E Gg (1 / H_k - 1 / H_{k-1}),  Gg = dtau g / 2,
 // with the stage constants (dtau, E, E Gg, the halves) formed on the host (TriK).  The w-face
-// means of theta are carried up the column (each one is formed once).  Alongside: H theta^t at
+// means of theta are carried up the column (each one is formed once) and stored for the substeps
+// (THW, levels 0..nz, the wall faces taking the reflected cell's value).  Alongside: H theta^t at
 // x- and y-faces (TX, TY) and dtau (-gamma R_d) (pi_{i-1} + pi_i) / 2 at x- and y-faces (PX, PY),
 // the stage-fixed factors of the substeps' Theta'' fluxes and pressure gradients.
 struct TriK {
@@ -669,7 +666,7 @@ struct TriK {
     double dpx;       // -dtau gamma R_d / 2
 };
 __global__ void k_tri_build(Geo g, const double *rho, const double *rt, const double *pi, const double *th, TriK tk,
-                            Tri tr, double *TX, double *TY, double *PX, double *PY) {
+                            Tri tr, double *TX, double *TY, double *PX, double *PY, double *THW) {
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= g.nxy) return;
     int i = (int)(n % g.nx), j = (int)(n / g.nx);
@@ -688,9 +685,12 @@ __global__ void k_tri_build(Geo g, const double *rho, const double *rt, const do
     double th_m = th[cix(g, i, j, 0)];
     double thw_m = th_m;                                 // the wall reflection: theta_{-1} = theta_0
     double thw_k = 0.5 * (th_m + cval(g, th, i, j, 1));
+    THW[cix(g, i, j, 0)] = th_m;
+    THW[cix(g, i, j, g.nz)] = th[cix(g, i, j, g.nz - 1)];
     for (int k = 1; k < g.nz; ++k) {
         face_factors(k);
         long long c = cix(g, i, j, k), cm = c - g.nxy, w = c;
+        THW[w] = thw_k;
         double thw_p = 0.5 * (th[c] + cval(g, th, i, j, k + 1));
         double pic = pi[c], pim = pi[cm];
         double Spi = pim + pic;
@@ -744,7 +744,7 @@ __global__ void k_sub_horiz(Geo g, const double *PX, const double *PY, const dou
 // flux; the beta-weighted X0 = b1 Theta''^tau + b2 Theta*, Y0 = b1 rho''^tau + b2 rho* of the
 // Omega'' rows; and, at the cell's bottom w-face, W'' - (metric shift) + dtau R_W.  TX, TY hold
 // H theta^t at x- and y-faces for this stage.  Theta''^tau is kept in Tt.
-__global__ void k_sub_expl(Geo g, Phys ph, const double *th, const double *TX, const double *TY, const double *Rr,
+__global__ void k_sub_expl(Geo g, Phys ph, const double *thw, const double *TX, const double *TY, const double *Rr,
                            const double *Rt, const double *Rw, F5 x, const double *Om, double *Tt, double *X0,
                            double *Y0, double *Ash, double *msx, double *msy, double *msz, double dtau) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -757,10 +757,8 @@ __global__ void k_sub_expl(Geo g, Phys ph, const double *th, const double *TX, c
     const double b1 = ph.b1, b2 = ph.b2;
     double om_k = k >= 1 ? Om[c] : 0.0;
     double om_p = k + 1 < nz ? Om[c + nxy] : 0.0;
-    double th_c = th[c];
-    // theta at the lower and upper w-faces, kept as twice the face average: the 1/2 is folded
-    // into b1 (exact scalings, so the result is unchanged)
-    double sw_k = cval(g, th, i, j, k - 1) + th_c, sw_p = th_c + cval(g, th, i, j, k + 1);
+    // theta^t at the lower and upper w-faces
+    double tw_k = thw[c], tw_p = thw[c + nxy];
     double Uc = x.u[c], Up = x.u[c + oxp], Vc = x.v[c], Vp = x.v[c + oyp];
     double divM = (Hx(g, i + 1, j, k) * Up - Hx(g, i, j, k) * Uc) * g.rdx
                 + (Hy(g, i, j + 1, k) * Vp - Hy(g, i, j, k) * Vc) * g.rdy;
@@ -768,7 +766,7 @@ __global__ void k_sub_expl(Geo g, Phys ph, const double *th, const double *TX, c
                 + (__ldg(TY + c + oyp) * Vp - __ldg(TY + c) * Vc) * g.rdy;
     double rH = rHc(g, i, j, k);
     double xt = x.t[c], xr = x.r[c];
-    double Ts = xt + dtau * ((-divT - ph.b1h * (om_p * sw_p - om_k * sw_k)) * rH + Rt[c]);
+    double Ts = xt + dtau * ((-divT - b1 * (om_p * tw_p - om_k * tw_k)) * rH + Rt[c]);
     double Rs = xr + dtau * ((-divM - b1 * (om_p - om_k)) * rH + Rr[c]);
     Tt[c] = xt;
     x.t[c] = Ts;
@@ -791,7 +789,10 @@ __global__ void k_sub_expl(Geo g, Phys ph, const double *th, const double *TX, c
 }
 
 // Part 2, one thread per column: the Omega'' rows' right-hand side, forward substitution with the
-// stage LU factors (d' held in Om) and back substitution.  Only the recurrences are serial.
+// stage LU factors (d' held in Om) and back substitution.  Only the recurrences are serial; the
+// operands of SB levels are loaded ahead of each stretch of the recurrence, so a thread keeps
+// 7 SB loads in flight (the columns alone do not fill the GPU with warps).
+constexpr int SB = 8;
 __global__ void __launch_bounds__(128) k_sub_col(int nz, long long nxy, const double *__restrict__ ta,
                                                  const double *__restrict__ tcp, const double *__restrict__ tim,
                                                  const double *__restrict__ tP, const double *__restrict__ tQ,
@@ -801,23 +802,50 @@ __global__ void __launch_bounds__(128) k_sub_col(int nz, long long nxy, const do
     if (n >= nxy) return;
     double dpm = 0.0;
     double X0m = X0[n], Y0m = Y0[n];
-#pragma unroll 4
-    for (int k = 1; k < nz; ++k) {
-        long long c = n + k * nxy;
-        double X0c = X0[c], Y0c = Y0[c];
-        double rhs = W[c] + tP[c] * X0c + tQ[c] * X0m - Gg * (Y0c + Y0m);
-        double dp = (rhs - ta[c] * dpm) * tim[c];
+    auto fwd = [&](long long c, double X0c, double Y0c, double Wc, double Pc, double Qc, double ac, double imc) {
+        double rhs = Wc + Pc * X0c + Qc * X0m - Gg * (Y0c + Y0m);
+        double dp = (rhs - ac * dpm) * imc;
         Om[c] = dp;
         dpm = dp;
         X0m = X0c; Y0m = Y0c;
+    };
+    int k = 1;
+    for (; k + SB <= nz; k += SB) {
+        double xv[SB], yv[SB], wv[SB], pv[SB], qv[SB], av[SB], iv[SB];
+#pragma unroll
+        for (int u = 0; u < SB; ++u) {
+            long long c = n + (long long)(k + u) * nxy;
+            xv[u] = X0[c]; yv[u] = Y0[c]; wv[u] = W[c]; pv[u] = tP[c]; qv[u] = tQ[c]; av[u] = ta[c]; iv[u] = tim[c];
+        }
+#pragma unroll
+        for (int u = 0; u < SB; ++u)
+            fwd(n + (long long)(k + u) * nxy, xv[u], yv[u], wv[u], pv[u], qv[u], av[u], iv[u]);
+    }
+    for (; k < nz; ++k) {
+        long long c = n + (long long)k * nxy;
+        fwd(c, X0[c], Y0[c], W[c], tP[c], tQ[c], ta[c], tim[c]);
     }
     long long top = n + nz * nxy;
     W[top] = 0.0;
     Om[top] = 0.0;
     double om_up = 0.0;
-#pragma unroll 4
-    for (int k = nz - 1; k >= 1; --k) {
-        long long c = n + k * nxy;
+    k = nz - 1;
+    for (; k - SB >= 0; k -= SB) {   // levels k, k - 1, ..., k - SB + 1 (all >= 1)
+        double ov[SB], cv[SB];
+#pragma unroll
+        for (int u = 0; u < SB; ++u) {
+            long long c = n + (long long)(k - u) * nxy;
+            ov[u] = Om[c]; cv[u] = tcp[c];
+        }
+#pragma unroll
+        for (int u = 0; u < SB; ++u) {
+            double om = ov[u] - cv[u] * om_up;
+            Om[n + (long long)(k - u) * nxy] = om;
+            om_up = om;
+        }
+    }
+    for (; k >= 1; --k) {
+        long long c = n + (long long)k * nxy;
         double om = Om[c] - tcp[c] * om_up;
         Om[c] = om;
         om_up = om;
@@ -827,7 +855,7 @@ __global__ void __launch_bounds__(128) k_sub_col(int nz, long long nxy, const do
 
 // Part 3, one thread per cell: Theta'', rho'' from the new Omega'' (beta_2 part), Theta~ of the
 // next substep, and W'' = Omega'' + metric shift at the cell's bottom w-face.
-__global__ void k_sub_fin(Geo g, Phys ph, const double *th, const double *Om, const double *Ash, F5 x, double *Tt,
+__global__ void k_sub_fin(Geo g, Phys ph, const double *thw, const double *Om, const double *Ash, F5 x, double *Tt,
                           double *msz, double dtb2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
@@ -835,8 +863,7 @@ __global__ void k_sub_fin(Geo g, Phys ph, const double *th, const double *Om, co
     const long long c = ((long long)k * g.ny + j) * g.nx + i;
     const double b2 = ph.b2, bd = ph.beta_d;
     double om = Om[c], om_up = Om[c + g.nxy];
-    double th_c = th[c];
-    double thw_k = 0.5 * (cval(g, th, i, j, k - 1) + th_c), thw_p = 0.5 * (th_c + cval(g, th, i, j, k + 1));
+    double thw_k = thw[c], thw_p = thw[c + g.nxy];
     double db = dtb2 * rHc(g, i, j, k);   // dtb2 = dtau b2
     double xt = x.t[c] - db * (om_up * thw_p - om * thw_k);
     x.t[c] = xt;
@@ -1087,26 +1114,27 @@ void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, double *pp, const dou
 }
 void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const double *rt, const double *pi,
                       const double *th, double dtau, Tri tr, double *TX, double *TY, double *PX, double *PY,
-                      cudaStream_t s) {
+                      double *THW, cudaStream_t s) {
     TriK tk;
     tk.E = dtau * ph.b2 * ph.b2;
     tk.EGg = tk.E * (dtau * 0.5 * ph.g);
     tk.cpg = dtau * (GAMMA * RD) * 0.5;
     tk.kgb = dtau * ph.g * (RD / CVD) * 0.5;
     tk.dpx = -tk.cpg;
-    LAUNCH("tri_build", s, k_tri_build<<<nblk(g.nxy, 128), 128, 0, s>>>(g, rho, rt, pi, th, tk, tr, TX, TY, PX, PY));
+    LAUNCH("tri_build", s, k_tri_build<<<nblk(g.nxy, 128), 128, 0, s>>>(g, rho, rt, pi, th, tk, tr, TX, TY, PX, PY,
+                                                                        THW));
 }
-void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *PX, const double *PY, const double *th,
+void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *PX, const double *PY, const double *thw,
                     const double *TX, const double *TY, CF5 R, F5 x, double *Om, double *Tp, double *X0, double *Y0,
                     double *Ash,
                     double *msx, double *msy, double *msz, double dtau, cudaStream_t s) {
     const dim3 g3c((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)g.nz);
     LAUNCH("sub_horiz", s, k_sub_horiz<<<nblk(g.nc, BS), BS, 0, s>>>(g, PX, PY, Tp, R.u, R.v, x.u, x.v, dtau));
-    LAUNCH("sub_expl", s, k_sub_expl<<<g3c, 128, 0, s>>>(g, ph, th, TX, TY, R.r, R.t, R.w, x, Om, Tp, X0, Y0, Ash,
+    LAUNCH("sub_expl", s, k_sub_expl<<<g3c, 128, 0, s>>>(g, ph, thw, TX, TY, R.r, R.t, R.w, x, Om, Tp, X0, Y0, Ash,
                                                          msx, msy, msz, dtau));
     LAUNCH("sub_col", s, k_sub_col<<<nblk(g.nxy, 128), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q, X0, Y0,
                                                                     x.w, Om, dtau * 0.5 * ph.g));
-    LAUNCH("sub_fin", s, k_sub_fin<<<g3c, 128, 0, s>>>(g, ph, th, Om, Ash, x, Tp, msz, dtau * ph.b2));
+    LAUNCH("sub_fin", s, k_sub_fin<<<g3c, 128, 0, s>>>(g, ph, thw, Om, Ash, x, Tp, msz, dtau * ph.b2));
 }
 void launch_tracer_stage(const Geo &g, const Phys &ph, CF5 st, const double *rom, const double *snphi,
                          const double *msx, const double *msy, const double *msz, int nsub, double adt,

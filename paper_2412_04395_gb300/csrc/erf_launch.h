@@ -22,8 +22,8 @@ void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, double *pp, const dou
                      double *flux, F5 R, cudaStream_t s);
 void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const double *rt, const double *pi,
                       const double *th, double dtau, Tri tr, double *TX, double *TY, double *PX, double *PY,
-                      cudaStream_t s);
-void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *PX, const double *PY, const double *th,
+                      double *THW, cudaStream_t s);
+void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *PX, const double *PY, const double *thw,
                     const double *TX, const double *TY, CF5 R, F5 x, double *Om, double *Tp, double *X0, double *Y0,
                     double *Ash, double *msx, double *msy, double *msz, double dtau, cudaStream_t s);
 void launch_tracer_stage(const Geo &g, const Phys &ph, CF5 st, const double *rom, const double *snphi,
