@@ -20,7 +20,10 @@
 
 namespace erfk {
 
-__device__ __forceinline__ double sgnd(double x) { return sgnT<double>(x); }
+// the upwind side of an advecting momentum m: the left one for m >= 0, by an integer test of the
+// sign bit (an FP64 comparison would take the FP64 pipe, the bound of these kernels).  -0 takes
+// the right side; every caller multiplies the interpolated value by that zero.
+__device__ __forceinline__ bool upwind_left(double m) { return __double2hiint(m) >= 0; }
 
 // Exner function and pressure from rho*theta (Sec. 2.1 EOS, dry):
 // pi = (R_d rho theta / P00)^(R_d/c_v), p = R_d rho theta pi.  The product is rounded on its
@@ -436,9 +439,9 @@ __global__ void k_sgs_div(Geo g, Phys ph, const double *mu, const double *t11, c
 // first differences of the stencil, the other candidates enter as differences from the middle
 // one, the indicators (with eps) carry a common factor 12/13, and the normalisation of that
 // correction takes one reciprocal (rcp1_d) instead of a division.
-__device__ __forceinline__ double weno5_d(const double *q, double s, int zflag) {
+__device__ __forceinline__ double weno5_d(const double *q, bool left, int zflag) {
     double a, b, c, d, e;   // v_{-2}, v_{-1}, v_0, v_1, v_2 on the upwind side
-    if (s >= 0.0) { a = q[0]; b = q[1]; c = q[2]; d = q[3]; e = q[4]; }
+    if (left) { a = q[0]; b = q[1]; c = q[2]; d = q[3]; e = q[4]; }
     else { a = q[5]; b = q[4]; c = q[3]; d = q[2]; e = q[1]; }
     const double d1 = a - b, d2 = b - c, d3 = c - d, d4 = d - e;
     const double p1 = fma(-1.0 / 6.0, d2, fma(-1.0 / 3.0, d3, c));  // (-b + 5c + 2d)/6
@@ -473,8 +476,8 @@ __device__ __forceinline__ double weno5_d(const double *q, double s, int zflag) 
 }
 
 // face value of an advected scalar: WENO5-JS, WENO5-Z or the linear upwind-3 interpolant
-__device__ __forceinline__ double scal_face_d(const double *q, double s, int scheme) {
-    return scheme == 3 ? upwind3(q, s) : weno5_d(q, s, scheme == 1);
+__device__ __forceinline__ double scal_face_d(const double *q, bool left, int scheme) {
+    return scheme == 3 ? upwind3_side<double>(q, left) : weno5_d(q, left, scheme == 1);
 }
 
 // theta fluxes through the left x-face, front y-face and bottom w-face of each cell (each face
@@ -487,14 +490,14 @@ __global__ void k_flux_theta(Geo g, Phys ph, Prep pr, const double *th, double *
     if (k < g.nz) {
         double mx = pr.mfx[n], my = pr.mfy[n];
         for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i - 3 + m, j, k);
-        fx[n] = mx * scal_face_d(q, sgnd(mx), ph.scal_adv);
+        fx[n] = mx * scal_face_d(q, upwind_left(mx), ph.scal_adv);
         for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i, j - 3 + m, k);
-        fy[n] = my * scal_face_d(q, sgnd(my), ph.scal_adv);
+        fy[n] = my * scal_face_d(q, upwind_left(my), ph.scal_adv);
     }
     if (k == 0 || k == g.nz) { fz[n] = 0.0; return; }
     double om = pr.rom[n];
     for (int m = 0; m < 6; ++m) q[m] = cval(g, th, i, j, k - 3 + m);
-    fz[n] = om * scal_face_d(q, sgnd(om), ph.scal_adv);
+    fz[n] = om * scal_face_d(q, upwind_left(om), ph.scal_adv);
 }
 
 // continuity and potential temperature (Eq. con, Eq. theta): flux divergence / cell height
@@ -518,6 +521,12 @@ __global__ void k_rhs_cells(Geo g, Prep pr, const double *fx, const double *fy, 
     if (i >= g.nx) return;                                          \
     const int j = blockIdx.y, k = blockIdx.z;                       \
     const long long n = ((long long)k * g.ny + j) * g.nx + i;
+// The advecting mass flux is the mean of two face mass fluxes; its 1/2 is folded into the
+// interpolant's weights (exact), so adv below is their sum.
+template <int mom3>
+__device__ __forceinline__ double mom_face_h(const double *q, bool left) {
+    return mom3 ? upwind3_side<double, 2>(q, left) : upwind5_side<double, 2>(q, left);
+}
 // u: x-flux at the cell centre (i,j,k), y-flux at the xy-edge (x-face i, y-face j), z-flux at the
 // xz-edge (x-face i, w-face k; zero on the walls)
 template <int mom3>
@@ -525,17 +534,17 @@ __global__ void k_flux_u(Geo g, Prep pr, double *fx, double *fy, double *fz) {
     CELL3D_W();
     double q[6];
     if (k < g.nz) {
-        double adv = 0.5 * (__ldg(pr.mfx + n) + cval(g, pr.mfx, i + 1, j, k));
+        double adv = (__ldg(pr.mfx + n) + cval(g, pr.mfx, i + 1, j, k));
         for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.ux, i - 2 + m, j, k);
-        fx[n] = adv * upwind_mom(q, sgnd(adv), mom3);
-        adv = 0.5 * (cval(g, pr.mfy, i - 1, j, k) + __ldg(pr.mfy + n));
+        fx[n] = adv * mom_face_h<mom3>(q, upwind_left(adv));
+        adv = (cval(g, pr.mfy, i - 1, j, k) + __ldg(pr.mfy + n));
         for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.ux, i, j - 3 + m, k);
-        fy[n] = adv * upwind_mom(q, sgnd(adv), mom3);
+        fy[n] = adv * mom_face_h<mom3>(q, upwind_left(adv));
     }
     if (k == 0 || k == g.nz) { fz[n] = 0.0; return; }
-    double adv = 0.5 * (__ldg(pr.rom + cixw(g, i - 1, j, k)) + __ldg(pr.rom + n));
+    double adv = (__ldg(pr.rom + cixw(g, i - 1, j, k)) + __ldg(pr.rom + n));
     for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.ux, i, j, k - 3 + m);
-    fz[n] = adv * upwind_mom(q, sgnd(adv), mom3);
+    fz[n] = adv * mom_face_h<mom3>(q, upwind_left(adv));
 }
 // v: x-flux at the xy-edge (x-face i, y-face j), y-flux at the cell centre, z-flux at the yz-edge
 template <int mom3>
@@ -543,17 +552,17 @@ __global__ void k_flux_v(Geo g, Prep pr, double *fx, double *fy, double *fz) {
     CELL3D_W();
     double q[6];
     if (k < g.nz) {
-        double adv = 0.5 * (cval(g, pr.mfx, i, j - 1, k) + __ldg(pr.mfx + n));
+        double adv = (cval(g, pr.mfx, i, j - 1, k) + __ldg(pr.mfx + n));
         for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.vy, i - 3 + m, j, k);
-        fx[n] = adv * upwind_mom(q, sgnd(adv), mom3);
-        adv = 0.5 * (__ldg(pr.mfy + n) + cval(g, pr.mfy, i, j + 1, k));
+        fx[n] = adv * mom_face_h<mom3>(q, upwind_left(adv));
+        adv = (__ldg(pr.mfy + n) + cval(g, pr.mfy, i, j + 1, k));
         for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.vy, i, j - 2 + m, k);
-        fy[n] = adv * upwind_mom(q, sgnd(adv), mom3);
+        fy[n] = adv * mom_face_h<mom3>(q, upwind_left(adv));
     }
     if (k == 0 || k == g.nz) { fz[n] = 0.0; return; }
-    double adv = 0.5 * (__ldg(pr.rom + cixw(g, i, j - 1, k)) + __ldg(pr.rom + n));
+    double adv = (__ldg(pr.rom + cixw(g, i, j - 1, k)) + __ldg(pr.rom + n));
     for (int m = 0; m < 6; ++m) q[m] = cval(g, pr.vy, i, j, k - 3 + m);
-    fz[n] = adv * upwind_mom(q, sgnd(adv), mom3);
+    fz[n] = adv * mom_face_h<mom3>(q, upwind_left(adv));
 }
 // w: x-flux at the xz-edge (x-face i, w-face k), y-flux at the yz-edge (both [nz+1] planes, zero on
 // the walls), z-flux at the cell centre (i,j,k) ([nz] planes)
@@ -562,17 +571,17 @@ __global__ void k_flux_w(Geo g, Prep pr, double *fx, double *fy, double *fz) {
     CELL3D_W();
     double q[6];
     if (k < g.nz) {
-        double adv = 0.5 * (__ldg(pr.rom + n) + __ldg(pr.rom + n + g.nxy));
+        double adv = (__ldg(pr.rom + n) + __ldg(pr.rom + n + g.nxy));
         for (int m = 0; m < 6; ++m) q[m] = wval(g, pr.wz, i, j, k - 2 + m);
-        fz[n] = adv * upwind_mom(q, sgnd(adv), mom3);
+        fz[n] = adv * mom_face_h<mom3>(q, upwind_left(adv));
     }
     if (k == 0 || k == g.nz) { fx[n] = 0.0; fy[n] = 0.0; return; }
-    double adv = 0.5 * (cval(g, pr.mfx, i, j, k - 1) + __ldg(pr.mfx + n));
+    double adv = (cval(g, pr.mfx, i, j, k - 1) + __ldg(pr.mfx + n));
     for (int m = 0; m < 6; ++m) q[m] = __ldg(pr.wz + cixw(g, i - 3 + m, j, k));
-    fx[n] = adv * upwind_mom(q, sgnd(adv), mom3);
-    adv = 0.5 * (cval(g, pr.mfy, i, j, k - 1) + __ldg(pr.mfy + n));
+    fx[n] = adv * mom_face_h<mom3>(q, upwind_left(adv));
+    adv = (cval(g, pr.mfy, i, j, k - 1) + __ldg(pr.mfy + n));
     for (int m = 0; m < 6; ++m) q[m] = __ldg(pr.wz + cixw(g, i, j - 3 + m, k));
-    fy[n] = adv * upwind_mom(q, sgnd(adv), mom3);
+    fy[n] = adv * mom_face_h<mom3>(q, upwind_left(adv));
 }
 
 // x-momentum at x-face (i,j,k): upwind-5 advection (reading R5), terrain pressure gradient
@@ -894,15 +903,15 @@ __global__ void k_tracer_flux(Geo g, Phys ph, const double *ru, const double *rv
     if (k < g.nz) {
         double mx = Hx(g, i, j, k) * ru[n] + msx[n] * rns;
         for (int m = 0; m < 6; ++m) q[m] = cval(g, phi, i - 3 + m, j, k);
-        fx[n] = mx * scal_face_d(q, sgnd(mx), ph.scal_adv);
+        fx[n] = mx * scal_face_d(q, upwind_left(mx), ph.scal_adv);
         double my = Hy(g, i, j, k) * rv[n] + msy[n] * rns;
         for (int m = 0; m < 6; ++m) q[m] = cval(g, phi, i, j - 3 + m, k);
-        fy[n] = my * scal_face_d(q, sgnd(my), ph.scal_adv);
+        fy[n] = my * scal_face_d(q, upwind_left(my), ph.scal_adv);
     }
     if (k == 0 || k == g.nz) { fz[n] = 0.0; return; }
     double mz = rom[n] + msz[n] * rns;
     for (int m = 0; m < 6; ++m) q[m] = cval(g, phi, i, j, k - 3 + m);
-    fz[n] = mz * scal_face_d(q, sgnd(mz), ph.scal_adv);
+    fz[n] = mz * scal_face_d(q, upwind_left(mz), ph.scal_adv);
 }
 __global__ void k_tracer_update(Geo g, const double *snphi, const double *fx, const double *fy, const double *fz,
                                 double adt, double *rphi) {

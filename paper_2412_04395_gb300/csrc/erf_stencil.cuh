@@ -10,22 +10,32 @@ namespace erfk {
 // points on the upwind side: the side is selected (no FP64 work) and the stencil takes five
 // multiply-adds instead of thirteen operations.  s = 0 takes the left side; every caller
 // multiplies the value by that zero momentum.
-template <class T>
-__device__ __forceinline__ T upwind5(const T *q, T s) {
-    const bool l = s >= T(0);
+// upwind5_side takes the side itself (l: the left one) and every weight times H; H a power of two
+// scales the result exactly (the FP64 momentum fluxes fold the 1/2 of their face average into it).
+template <class T, int H = 1>
+__device__ __forceinline__ T upwind5_side(const T *q, bool l) {
+    constexpr T h = H == 1 ? T(1) : T(0.5);
     const T a0 = l ? q[0] : q[5], a1 = l ? q[1] : q[4], a2 = l ? q[2] : q[3], a3 = l ? q[3] : q[2];
     const T a4 = l ? q[4] : q[1];
-    return fma(T(47.0 / 60.0), a2, fma(T(27.0 / 60.0), a3, fma(T(-13.0 / 60.0), a1,
-               fma(T(2.0 / 60.0), a0, T(-3.0 / 60.0) * a4))));
+    return fma(T(47.0 / 60.0) * h, a2, fma(T(27.0 / 60.0) * h, a3, fma(T(-13.0 / 60.0) * h, a1,
+               fma(T(2.0 / 60.0) * h, a0, (T(-3.0 / 60.0) * h) * a4))));
+}
+template <class T>
+__device__ __forceinline__ T upwind5(const T *q, T s) {
+    return upwind5_side<T>(q, s >= T(0));
 }
 // q[0..5] = q_{m-3}..q_{m+2}; 3rd-order upwind value at m-1/2: the centred fourth-order value
 // plus s/12 times its dissipative part (Sec. 3.6), i.e. (-1, 5, 2)/6 over the three points on the
 // upwind side (s = 0 takes the left side; every caller multiplies by that zero momentum)
+template <class T, int H = 1>
+__device__ __forceinline__ T upwind3_side(const T *q, bool l) {
+    constexpr T h = H == 1 ? T(1) : T(0.5);
+    const T a0 = l ? q[1] : q[4], a1 = l ? q[2] : q[3], a2 = l ? q[3] : q[2];
+    return fma(T(5.0 / 6.0) * h, a1, fma(T(1.0 / 3.0) * h, a2, (T(-1.0 / 6.0) * h) * a0));
+}
 template <class T>
 __device__ __forceinline__ T upwind3(const T *q, T s) {
-    const bool l = s >= T(0);
-    const T a0 = l ? q[1] : q[4], a1 = l ? q[2] : q[3], a2 = l ? q[3] : q[2];
-    return fma(T(5.0 / 6.0), a1, fma(T(1.0 / 3.0), a2, T(-1.0 / 6.0) * a0));
+    return upwind3_side<T>(q, s >= T(0));
 }
 // face value of an advected scalar: WENO5-JS (scheme 0), WENO5-Z (1) or upwind-3 (3); defined
 // after weno5 below
