@@ -19,8 +19,8 @@
  *             (Sec. 6, surrogate models) as cell-centre stresses from a model callback
  *   Sec. 3.8  HSE base state by Newton-Raphson; MOST bottom boundary
  * Readings where the paper is silent (constants, Smagorinsky form, WENO5 details, the
- * tridiagonal, divergence damping, wall ghost cells, MOST formulas) are listed in the
- * design notes and restated beside the code that takes them.
+ * tridiagonal, divergence damping, wall ghost cells, MOST formulas) are stated beside the code
+ * that takes them.
  *
  * Storage: C order [k][j][i], i fastest, periodic in x and y with every face stored once:
  *   cell (i,j,k) centred at ((i+1/2)dx, (j+1/2)dy);  x-face (i,j,k) at x = i dx (left face of cell i);

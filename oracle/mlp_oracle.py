@@ -1,7 +1,7 @@
 """FP64 oracle of the learned subgrid closure (numpy; test infrastructure only).
 
 The paper names surrogate models as future work (Sec. 6) and fixes nothing about them; the
-closure follows the readings of the design notes:
+closure takes these readings:
   * features at cell centres of a flat C-grid: the 9 resolved velocity gradients du_i/dx_j,
     dtheta/dx, dtheta/dy and N^2 = g/theta0 dtheta/dz (12 inputs);
   * MLP 12 -> 64 -> 64 -> 64 -> 9, SiLU hidden activations, linear output;

@@ -1,6 +1,6 @@
 """Mixed precision (FP32 perturbations about the FP64 base state, FP64 tridiagonal and mass sums)
 against the FP64 oracle.  The error of each field is measured and bounded; the bounds are the
-FP32 storage/arithmetic error grown over the run, stated in the tests and in the design notes."""
+FP32 storage/arithmetic error grown over the run, stated beside each test."""
 import numpy as np
 import pytest
 
