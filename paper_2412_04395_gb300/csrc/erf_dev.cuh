@@ -177,12 +177,15 @@ __device__ __forceinline__ double rdz2c(const Geo &g, int i, int j, int k) {
 __device__ __forceinline__ double zc(const Geo &g, int i, int j, int k) {
     return g.terrain ? g.zetac[k] + g.sc[k] * g.hc[ij2(g, i, j)] : g.zetac[k];
 }
-// h_xi / 2 and h_eta / 2 at x- and y-faces (the 1/2 of the two-point average they multiply), and
-// h_xi / 4, h_eta / 4 at w-faces (the 1/4 of the four-point averages of the metric shift)
+// h_xi / 2 and h_eta / 2 at x- and y-faces (the 1/2 of the two-point average they multiply); the
+// w-face slopes carry the 1/4 of the four-point averages of the metric shift
 __device__ __forceinline__ double hxi_x2(const Geo &g, int i, int j, int k) { return g.sc[k] * g.gxh[ij2(g, i, j)]; }
 __device__ __forceinline__ double heta_y2(const Geo &g, int i, int j, int k) { return g.sc[k] * g.gyh[ij2(g, i, j)]; }
-__device__ __forceinline__ double hxi_w4(const Geo &g, int i, int j, int k) { return g.s[k] * g.g4xq[ij2(g, i, j)]; }
-__device__ __forceinline__ double heta_w4(const Geo &g, int i, int j, int k) { return g.s[k] * g.g4yq[ij2(g, i, j)]; }
+// the metric shift h_xi <U> + h_eta <V> at w-face (i,j,k) from the four-point sums au, av of U and V
+__device__ __forceinline__ double w4_shift(const Geo &g, int i, int j, int k, double au, double av) {
+    const int n = ij2(g, i, j);
+    return g.s[k] * fma(g.g4xq[n], au, g.g4yq[n] * av);
+}
 __device__ __forceinline__ long long bix(const Geo &g, int i, int j, int k) {
     return g.terrain ? cixw(g, i, j, k) : (long long)k;
 }

@@ -168,10 +168,11 @@ __global__ void k_init_faces(Geo g, const double *u, const double *v, const doub
 // h_xi <U> + h_eta <V> at w-face (i,j,k) with the 4-point averages of App. B (levels outside
 // the domain reflected)
 __device__ __forceinline__ double metric_shift(const Geo &g, const double *U, const double *V, int i, int j, int k) {
-    // four-point sums; the 1/4 of the averages is in hxi_w4, heta_w4
+    // four-point sums; the 1/4 of the averages is in the slope tables, the level factor s_k is
+    // applied once to both terms
     double au = cval(g, U, i, j, k - 1) + cval(g, U, i + 1, j, k - 1) + cval(g, U, i, j, k) + cval(g, U, i + 1, j, k);
     double av = cval(g, V, i, j, k - 1) + cval(g, V, i, j + 1, k - 1) + cval(g, V, i, j, k) + cval(g, V, i, j + 1, k);
-    return hxi_w4(g, i, j, k) * au + heta_w4(g, i, j, k) * av;
+    return w4_shift(g, i, j, k, au, av);
 }
 
 // walls: Omega = 0 at k = 0 (rho w = metric shift of the horizontal momenta) and rho w = 0 at the top
@@ -221,7 +222,7 @@ __global__ void k_stage_begin(Geo g, CF5 sn, CF5 st, F5 x, double *pp, double *p
                 av += sn.v[a] - st.v[a];
             }
         }
-        om -= hxi_w4(g, i, j, k) * au + heta_w4(g, i, j, k) * av;
+        om -= w4_shift(g, i, j, k, au, av);
     }
     Om[n] = om;
 }
@@ -665,14 +666,16 @@ __global__ void k_rhs_w(Geo g, Phys ph, CF5 st, const double *pp, const double *
 //   b = 1 + thw_k (E Q / H_{k-1} - E P / H_k) + E Gg (1 / H_k - 1 / H_{k-1}),  Gg = dtau g / 2,
 // with the stage constants (dtau, E, E Gg, the halves) formed on the host (TriK).  The w-face
 // means of theta are carried up the column (each one is formed once) and stored for the substeps
-// (THW, levels 0..nz, the wall faces taking the reflected cell's value).  Alongside: H theta^t at
-// x- and y-faces (TX, TY) and dtau (-gamma R_d) (pi_{i-1} + pi_i) / 2 at x- and y-faces (PX, PY),
-// the stage-fixed factors of the substeps' Theta'' fluxes and pressure gradients.
+// (THW, levels 0..nz, the wall faces taking the reflected cell's value).  Alongside: H theta^t / dx
+// at x-faces and H theta^t / dy at y-faces (TX, TY) and dtau (-gamma R_d) (pi_{i-1} + pi_i) / 2 at
+// x- and y-faces (PX, PY), the stage-fixed factors of the substeps' Theta'' fluxes and pressure
+// gradients.
 struct TriK {
     double E, EGg;    // dtau b2^2, E dtau g / 2
     double cpg;       // dtau gamma R_d / 2
     double kgb;       // dtau g (R_d / c_v) / 2
     double dpx;       // -dtau gamma R_d / 2
+    double hrdx, hrdy;  // 1 / (2 dx), 1 / (2 dy): the face mean of theta and the substeps' 1/dx, 1/dy
 };
 __global__ void k_tri_build(Geo g, const double *rho, const double *rt, const double *pi, const double *th, TriK tk,
                             Tri tr, double *TX, double *TY, double *PX, double *PY, double *THW) {
@@ -685,8 +688,8 @@ __global__ void k_tri_build(Geo g, const double *rho, const double *rt, const do
     auto face_factors = [&](int k) {
         long long c = cix(g, i, j, k);
         double thc = th[c], pic = pi[c];
-        TX[c] = Hx(g, i, j, k) * (0.5 * (cval(g, th, i - 1, j, k) + thc));
-        TY[c] = Hy(g, i, j, k) * (0.5 * (cval(g, th, i, j - 1, k) + thc));
+        TX[c] = Hx(g, i, j, k) * (tk.hrdx * (cval(g, th, i - 1, j, k) + thc));
+        TY[c] = Hy(g, i, j, k) * (tk.hrdy * (cval(g, th, i, j - 1, k) + thc));
         PX[c] = tk.dpx * (cval(g, pi, i - 1, j, k) + pic);
         PY[c] = tk.dpx * (cval(g, pi, i, j - 1, k) + pic);
     };
@@ -752,7 +755,8 @@ __global__ void k_sub_horiz(Geo g, const double *PX, const double *PY, const dou
 // explicit Theta*, rho* from the new U'', V'' divergence and the beta_1 part of the old Omega''
 // flux; the beta-weighted X0 = b1 Theta''^tau + b2 Theta*, Y0 = b1 rho''^tau + b2 rho* of the
 // Omega'' rows; and, at the cell's bottom w-face, W'' - (metric shift) + dtau R_W.  TX, TY hold
-// H theta^t at x- and y-faces for this stage.  Theta''^tau is kept in Tt.
+// H theta^t / dx at x-faces and H theta^t / dy at y-faces for this stage.  Theta''^tau is kept in
+// Tt.
 __global__ void k_sub_expl(Geo g, Phys ph, const double *thw, const double *TX, const double *TY, const double *Rr,
                            const double *Rt, const double *Rw, F5 x, const double *Om, double *Tt, double *X0,
                            double *Y0, double *Ash, double *msx, double *msy, double *msz, double dtau) {
@@ -771,8 +775,7 @@ __global__ void k_sub_expl(Geo g, Phys ph, const double *thw, const double *TX, 
     double Uc = x.u[c], Up = x.u[c + oxp], Vc = x.v[c], Vp = x.v[c + oyp];
     double divM = (Hx(g, i + 1, j, k) * Up - Hx(g, i, j, k) * Uc) * g.rdx
                 + (Hy(g, i, j + 1, k) * Vp - Hy(g, i, j, k) * Vc) * g.rdy;
-    double divT = (__ldg(TX + c + oxp) * Up - __ldg(TX + c) * Uc) * g.rdx
-                + (__ldg(TY + c + oyp) * Vp - __ldg(TY + c) * Vc) * g.rdy;
+    double divT = (__ldg(TX + c + oxp) * Up - __ldg(TX + c) * Uc) + (__ldg(TY + c + oyp) * Vp - __ldg(TY + c) * Vc);
     double rH = rHc(g, i, j, k);
     double xt = x.t[c], xr = x.r[c];
     double Ts = xt + dtau * ((-divT - b1 * (om_p * tw_p - om_k * tw_k)) * rH + Rt[c]);
@@ -1130,6 +1133,8 @@ void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const dou
     tk.cpg = dtau * (GAMMA * RD) * 0.5;
     tk.kgb = dtau * ph.g * (RD / CVD) * 0.5;
     tk.dpx = -tk.cpg;
+    tk.hrdx = 0.5 * g.rdx;
+    tk.hrdy = 0.5 * g.rdy;
     LAUNCH("tri_build", s, k_tri_build<<<nblk(g.nxy, 128), 128, 0, s>>>(g, rho, rt, pi, th, tk, tr, TX, TY, PX, PY,
                                                                         THW));
 }
