@@ -56,7 +56,7 @@ KERNEL_MODEL = {
 # DRAM bytes per unit from an ncu capture of the kernel as it stands (dram__bytes_read.sum +
 # dram__bytes_write.sum of a 128^3 hill-bubble launch / its units; profiles/ has the summary),
 # scaled to the benchmark's units.  A kernel missing here reports traffic null.
-KERNEL_TRAFFIC_PER_UNIT = {"flux_theta": 39.7, "sub_expl": 160.8}
+KERNEL_TRAFFIC_PER_UNIT = {"flux_theta": 39.9, "sub_expl": 160.8}
 # mixed path: algorithmic bytes per cell per launch (FP32 fields, FP64 LU factors and d');
 # these kernels are bound by HBM or latency, so their roofline is in GB/s
 KERNEL_MODEL_MIXED = {
