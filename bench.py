@@ -39,7 +39,7 @@ KERNEL_MODEL = {
     "sub_expl":    {"unit": "cell", "words": 20, "flops": 56},
     "sub_col":     {"unit": "cell", "words": 11, "flops": 12},
     "sub_fin":     {"unit": "cell", "words": 10, "flops": 18},
-    "sub_horiz":   {"unit": "cell", "words": 9, "flops": 30},
+    "sub_horiz":   {"unit": "cell", "words": 10, "flops": 30},
     "flux_u":      {"unit": "wface", "words": 7, "flops": 63},
     "flux_v":      {"unit": "wface", "words": 7, "flops": 63},
     "flux_w":      {"unit": "wface", "words": 7, "flops": 63},
@@ -49,7 +49,7 @@ KERNEL_MODEL = {
     "rhs_w":       {"unit": "wface", "words": 7, "flops": 25},
     "stage_begin": {"unit": "wface", "words": 20, "flops": 60},
     "prep":        {"unit": "wface", "words": 10, "flops": 40},
-    "tri_build":   {"unit": "cell", "words": 11, "flops": 90},
+    "tri_build":   {"unit": "cell", "words": 14, "flops": 90},
     "stage_end":   {"unit": "wface", "words": 15, "flops": 5},
     "wall_bc":     {"unit": "none", "words": 0, "flops": 0},
 }
