@@ -173,3 +173,19 @@ def test_learned_closure_without_a_model_is_refused():
     o, _ = _rest_oracle()
     with pytest.raises(AssertionError):
         o.step(1)
+
+
+def test_backscatter_limit_inside_the_model_closed_form():
+    """A network that returns a constant t13 = c > 0 on the linear shear u = S z (S13 = S/2): its
+    transfer -2 c S13 is backscatter below -1/2 of Smagorinsky's 4 nu S13^2 (nu = (Cs Delta)^2 S),
+    so t13 is scaled onto the bound: c (nu S13 / c) = (Cs Delta)^2 S^2 / 2, times rho."""
+    S, G, Cs = 0.02, 0.003, 0.17
+    zeta = W.uniform_zeta(NZ, DZ)
+    th0 = 300.0 + G * (np.arange(NZ) + 0.5) * DZ
+    omu = np.zeros(9)
+    omu[4] = 0.05
+    m = M.LearnedClosure(_net(6, in_sd=1e3, out_mu=omu, zero=True), zeta, DX, DY, th0, Cs, 1.0 / 3.0)
+    P = m(*_shear_state(S, G))
+    assert m.fallbacks == [0]
+    d2 = (Cs * np.cbrt(DX * DY * DZ)) ** 2
+    np.testing.assert_allclose(P[4], 1.1 * d2 * S * S / 2, rtol=1e-12)
