@@ -34,11 +34,24 @@ def dsilu(x):
 
 
 def bf16(x):
-    """Round to the nearest bfloat16 (ties to even), returned as float64."""
-    f = np.ascontiguousarray(x, dtype=np.float32)
-    u = f.view(np.uint32).astype(np.uint64)
-    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
-    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+    """Round to the nearest bfloat16 (ties to even), returned as float64.
+
+    bfloat16 has float32's exponent range and 8 significant bits: a finite value a = m 2^e
+    (1/2 <= |m| < 1) is a multiple of the quantum q = 2^(max(e, -125) - 8), so normal numbers keep
+    8 bits and everything below 2^-126 is a multiple of the subnormal quantum 2^-133.  The value
+    is rounded once, straight from float64 (no intermediate float32 rounding), to the nearest
+    multiple of its quantum with exact halves going to the even multiple; a result of magnitude
+    2^128 or more is an infinity (the largest finite bfloat16 is 255 * 2^120).  Signed zeros,
+    infinities and NaNs pass through."""
+    a = np.asarray(x, dtype=np.float64)
+    finite = np.isfinite(a)
+    af = np.where(finite, a, 0.0)
+    _, e = np.frexp(af)
+    q = np.ldexp(1.0, np.maximum(e, -125) - 8)
+    r = np.round(af / q) * q            # a / q is exact (a power-of-two scaling); round = half-even
+    r = np.where(np.abs(r) >= 2.0 ** 128, np.copysign(np.inf, af), r)
+    r = np.where(af == 0.0, af, r)      # keeps the sign of zero
+    return np.where(finite, r, a)
 
 
 def forward(params, X, bf16_inputs=False):
