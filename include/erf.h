@@ -228,7 +228,10 @@ erf_status erf_profile_steps(erf_handle *h, int32_t nsteps, erf_kernel_time *out
  * It reduces a state the caller already holds in device memory - flat grid, the same layout as
  * erf_get_state, d_dz = the nz cell heights - into d_out[0..4] = {mass, max abs(w) over interior
  * w-faces, theta min, theta max, nonfinite flag (1.0/0.0)} on cuda_stream, with the same fixed
- * reduction order on every call.  It needs no handle and no workspace and calls no allocator:
+ * reduction order on every call.  The mass weights each cell by dz[k] dx dy, the volume of a
+ * flat-grid cell: for a state over terrain (where each column's cell heights differ) the mass it
+ * returns is wrong, and erf_diagnostics, which weights by each cell's own height, is the one to
+ * use.  It needs no handle and no workspace and calls no allocator:
  * its only scratch is a file-scope device array of ERF_NOALLOC_MAX_PARTS x 5 doubles (2.5 MiB)
  * that every GPU loading the library keeps until the process exits.  Grids of more than
  * ERF_NOALLOC_MAX_PARTS x 4096 cells are rejected with ERF_ENOSPACE.  The first call on a

@@ -523,6 +523,7 @@ extern "C" erf_status erf_profile_steps(erf_handle *h, int32_t nsteps, erf_kerne
                                         int32_t *n_entries) {
     if (!h || !out || !n_entries || max_entries < 1 || nsteps < 1) return fail(h, ERF_EINVAL, "bad profile arguments");
     if (!h->have_state) return fail(h, ERF_ESTATE, "no state set");
+    if (h->cfg.closure == 3 && !h->cl_ready) return fail(h, ERF_ESTATE, "learned closure weights not set");
     EventSink sink;
     set_profiler(&sink);
     for (int n = 0; n < nsteps; ++n) enqueue_step(h, h->user);
