@@ -57,6 +57,9 @@ KERNEL_MODEL = {
 # dram__bytes_write.sum of a 128^3 hill-bubble launch / its units; profiles/ has the summary),
 # scaled to the benchmark's units.  A kernel missing here reports traffic null.
 KERNEL_TRAFFIC_PER_UNIT = {"flux_theta": 39.9, "sub_expl": 160.8}
+# the same for the FP32-perturbation kernels (DRAM bytes per unit of a 256 x 256 x 160
+# convective-ABL capture); kernels changed since their capture are left out (traffic null)
+KERNEL_TRAFFIC_PER_UNIT_MIXED = {}
 # mixed path: algorithmic bytes per cell per launch (FP32 fields, FP64 LU factors and d');
 # these kernels are bound by HBM or latency, so their roofline is in GB/s
 KERNEL_MODEL_MIXED = {
@@ -88,6 +91,48 @@ KERNEL_MODEL_MIXED = {
 # FP64 peak from the unit count ncu reports on GB300 (sm__sass_thread_inst_executed_op_dfma_
 # pred_on.sum.peak_sustained = 304 per cycle, 2 per SM) x 2 flop x 2.07 GHz maximum SM clock
 FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
+
+
+def step_bytes_per_cell_update(precision, n_substeps):
+    """Algorithmic HBM bytes of one whole RK3 step per cell (each kernel reads its inputs once
+    and writes its outputs once, stage init/finalize folded into the first/last substep):
+    3 stages x (10 words of slow tendencies + 10 of stage init/finalize) + 17 words per substep
+    pass, sum over stages of the substep counts = 1 + ns/2 + ns.  FP64: 8-byte words; the
+    FP32-perturbation form: 950 B at ns = 6 and 1400 B at ns = 10 (FP32 fields, FP64 tridiagonal
+    coefficients)."""
+    passes = 1 + n_substeps // 2 + n_substeps
+    if precision == "fp64":
+        return 8 * (60 + 17 * passes)
+    return {6: 950.0, 10: 1400.0}.get(n_substeps, 4.0 * (60 + 17 * passes) + 12.0 * passes)
+
+
+def kernel_roofline(name, tms, nl, total, wl, hbm, hsrc):
+    """Roofline object of one kernel from its profiled time: HBM-bound kernels (the FP32 path)
+    in GB/s of algorithmic bytes, FP64-ALU-bound kernels in TFLOP/s of algorithmic flops."""
+    avg_s = tms / nl * 1e-3
+    units_of = {"cell": wl.ncell, "wface": wl.nx * wl.ny * (wl.nz + 1), "none": 0}
+    if name in KERNEL_MODEL_MIXED:
+        mm = KERNEL_MODEL_MIXED[name]
+        units = units_of[mm["unit"]]
+        gbs = mm["bytes"] * units / avg_s / 1e9
+        tpu = KERNEL_TRAFFIC_PER_UNIT_MIXED.get(name)
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "traffic": None if tpu is None else tpu * units, "kernel": name,
+                "alg_bytes": mm["bytes"] * units, "kernel_avg_ms": tms / nl,
+                "kernel_share": tms / total, "peak_source": hsrc}
+    model = KERNEL_MODEL.get(name, {"unit": "cell", "words": 0, "flops": 0})
+    units = units_of[model["unit"]]
+    flops = model["flops"] * units
+    bytes_ = 8 * model["words"] * units
+    fp64_tf = flops / avg_s / 1e12
+    hbm_gbs = bytes_ / avg_s / 1e9
+    tpu = KERNEL_TRAFFIC_PER_UNIT.get(name)
+    return {"bound": "alu", "achieved": fp64_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": fp64_tf / FP64_PEAK_TFLOPS, "traffic": None if tpu is None else tpu * units,
+            "kernel": name, "alg_flops": flops, "kernel_avg_ms": tms / nl, "kernel_share": tms / total,
+            "peak_source": "derived: 304 DFMA/cycle (ncu unit count) x 2 flop x 2.07 GHz",
+            "hbm": {"achieved": hbm_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_gbs / hbm,
+                    "peak_source": hsrc}}
 
 
 def peaks():
@@ -300,9 +345,43 @@ def closure_blob(wl, d):
     return np.array([0x4D465245, 1], dtype=np.uint32).tobytes() + body.tobytes(), "random"
 
 
-def _time_form(wl, steps, out, name):
+def _e2e_rate(d, wl, steps, dtype):
+    """Cell-updates/s end to end through the C ABI with pinned host buffers: every step uploads
+    the five state fields from the host, advances one step and downloads them (dtype "f64" or
+    "f32" host buffers; the library converts on the device).  Returns the e2e object."""
+    import torch
+    from paper_2412_04395_gb300.erf import FIELDS
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    code = 0 if dtype == "f64" else 1
+    host = {k: torch.empty(d._shape(k), dtype=tdt).pin_memory() for k in
+            ("rho", "rhotheta", "rhou", "rhov", "rhow")}
+    L = d.L
+    for k, t in host.items():
+        assert L.erf_get_state(d.h, FIELDS[k], t.data_ptr(), 0, code) == 0
+    nbytes = sum(t.numel() * t.element_size() for t in host.values())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for k, t in host.items():
+            st = L.erf_set_state(d.h, FIELDS[k], t.data_ptr(), 0, code)
+            assert st == 0
+        d.erf_rk3_step(1)
+        for k, t in host.items():
+            st = L.erf_get_state(d.h, FIELDS[k], t.data_ptr(), 0, code)
+            assert st == 0
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    del host
+    return {"value": wl.ncell * steps / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "steps": steps, "host_dtype": dtype}
+
+
+def _time_form(wl, steps, out, name, prec, e2e_steps=0):
     """Cell-updates/s of one form of a workload (CUDA events around graph-launched steps after
-    3 warm-up steps) and its per-kernel device times of one further step."""
+    3 warm-up steps), its per-kernel device times over one further step, the roofline of its
+    dominant kernel, its step-level fraction of the HBM roofline (cell-updates/s x the step's
+    algorithmic bytes per cell-update / measured HBM bandwidth) and, with e2e_steps, its rate end
+    to end through the C ABI with host buffers."""
     import torch
     from paper_2412_04395_gb300 import workloads as W
     from paper_2412_04395_gb300.erf import Dycore
@@ -314,8 +393,19 @@ def _time_form(wl, steps, out, name):
         out["learned_weights"] = kind
     ms = time_steps(d, steps, 3)
     prof = d.erf_profile_steps(1)
-    out[name] = {"value": wl.ncell * steps / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps,
-                 "kernel_ms_per_step": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]}}
+    total = sum(v[0] for v in prof.values())
+    top_name, (tms, nl) = max(prof.items(), key=lambda kv: kv[1][0])
+    hbm, hsrc, _ = peaks()
+    value = wl.ncell * steps / (ms * 1e-3)
+    sb = step_bytes_per_cell_update(prec, wl.n_substeps)
+    rec = {"value": value, "ms_per_step": ms / steps, "steps": steps,
+           "roofline": kernel_roofline(top_name, tms, nl, total, wl, hbm, hsrc),
+           "hbm_frac_step": value * sb / (hbm * 1e9), "step_alg_bytes_per_cell_update": sb,
+           "kernel_ms_per_step": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:10]},
+           "kernel_share": {k: round(v[0] / total, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:10]}}
+    if e2e_steps > 0:
+        rec["e2e"] = _e2e_rate(d, wl, e2e_steps, "f32" if prec == "mixed" else "f64")
+    out[name] = rec
     d.close()
     del d
     torch.cuda.empty_cache()
@@ -332,9 +422,10 @@ def precision_comparison(args):
     base = W.convective_abl(nx=nx, ny=ny, nz=nz, dx=40.0)
     out = {"workload": f"convective_abl {nx}x{ny}x{nz} at 40 m, ns=10, Smagorinsky/learned, MOST"}
     fp64_steps = max(1, args.cmp_steps // 4)
-    _time_form(base.with_(precision=W.PREC_FP64), fp64_steps, out, "fp64_smagorinsky")
-    _time_form(base.with_(precision=W.PREC_MIXED32), args.cmp_steps, out, "fp32_smagorinsky")
-    _time_form(base.with_(precision=W.PREC_MIXED32, closure=W.CLOSURE_LEARNED), args.cmp_steps, out, "fp32_learned")
+    _time_form(base.with_(precision=W.PREC_FP64), fp64_steps, out, "fp64_smagorinsky", "fp64")
+    _time_form(base.with_(precision=W.PREC_MIXED32), args.cmp_steps, out, "fp32_smagorinsky", "mixed")
+    _time_form(base.with_(precision=W.PREC_MIXED32, closure=W.CLOSURE_LEARNED), args.cmp_steps, out,
+               "fp32_learned", "mixed", e2e_steps=args.cmp_e2e_steps)
     del base
     out["fp32_learned_over_fp64"] = out["fp32_learned"]["value"] / out["fp64_smagorinsky"]["value"]
     out["fp32_over_fp64"] = out["fp32_smagorinsky"]["value"] / out["fp64_smagorinsky"]["value"]
@@ -342,8 +433,8 @@ def precision_comparison(args):
         mx, my, mz = args.neutral_grid
         nb = W.neutral_abl(nx=mx, ny=my, nz=mz, dx=10.0)
         neu = {"workload": f"neutral_abl {mx}x{my}x{mz} at 10 m, ns=10, Smagorinsky, MOST"}
-        _time_form(nb.with_(precision=W.PREC_FP64), fp64_steps, neu, "fp64")
-        _time_form(nb.with_(precision=W.PREC_MIXED32), args.cmp_steps, neu, "fp32")
+        _time_form(nb.with_(precision=W.PREC_FP64), fp64_steps, neu, "fp64", "fp64")
+        _time_form(nb.with_(precision=W.PREC_MIXED32), args.cmp_steps, neu, "fp32", "mixed")
         neu["fp32_over_fp64"] = neu["fp32"]["value"] / neu["fp64"]["value"]
         out["neutral_abl"] = neu
     if args.paper_grid[0] > 0:
@@ -351,8 +442,8 @@ def precision_comparison(args):
         px, py, pz = args.paper_grid
         pw = W.paper_scaling(nx=px, ny=py, nz=pz)
         pap = {"workload": f"paper_scaling {px}x{py}x{pz} at 4 m, upwind-3, ns=10, Smagorinsky, MOST"}
-        _time_form(pw.with_(precision=W.PREC_FP64), fp64_steps, pap, "fp64")
-        _time_form(pw.with_(precision=W.PREC_MIXED32), args.cmp_steps, pap, "fp32")
+        _time_form(pw.with_(precision=W.PREC_FP64), fp64_steps, pap, "fp64", "fp64")
+        _time_form(pw.with_(precision=W.PREC_MIXED32), args.cmp_steps, pap, "fp32", "mixed")
         pap["fp32_over_fp64"] = pap["fp32"]["value"] / pap["fp64"]["value"]
         out["paper_scaling"] = pap
     return out
@@ -376,7 +467,8 @@ def run_ours(args):
     # warm-up (graph capture happens on the first step)
     d.erf_rk3_step(args.warmup)
     torch.cuda.synchronize()
-    kps = d.erf_diagnostics()["kernels_per_step"]
+    diag0 = d.erf_diagnostics()
+    kps = diag0["kernels_per_step"]
     # timed region: K graph launches, CUDA events on the bound stream
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as cs:
@@ -396,58 +488,20 @@ def run_ours(args):
     # per-kernel device times (event-bracketed direct launches of 2 further steps)
     prof = d.erf_profile_steps(2)
     total = sum(v[0] for v in prof.values())
-    top = max(prof.items(), key=lambda kv: kv[1][0])
-    name, (tms, nl) = top
+    name, (tms, nl) = max(prof.items(), key=lambda kv: kv[1][0])
     hbm, hsrc, pk = peaks()
-    avg_s = tms / nl * 1e-3
-    if name in KERNEL_MODEL_MIXED:
-        mm = KERNEL_MODEL_MIXED[name]
-        units = {"cell": wl.ncell, "wface": wl.nx * wl.ny * (wl.nz + 1)}[mm["unit"]]
-        gbs = mm["bytes"] * units / avg_s / 1e9
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                "traffic": None, "kernel": name, "kernel_avg_ms": tms / nl, "kernel_share": tms / total,
-                "peak_source": hsrc}
-    else:
-        model = KERNEL_MODEL.get(name, {"unit": "cell", "words": 0, "flops": 0})
-        units = {"cell": wl.ncell, "wface": wl.nx * wl.ny * (wl.nz + 1), "none": 0}[model["unit"]]
-        flops = model["flops"] * units
-        bytes_ = 8 * model["words"] * units
-        fp64_tf = flops / avg_s / 1e12
-        hbm_gbs = bytes_ / avg_s / 1e9
-        tpu = KERNEL_TRAFFIC_PER_UNIT.get(name)
-        roof = {"bound": "alu", "achieved": fp64_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": fp64_tf / FP64_PEAK_TFLOPS, "traffic": None if tpu is None else tpu * units,
-                "kernel": name,
-                "kernel_avg_ms": tms / nl, "kernel_share": tms / total,
-                "peak_source": "derived: 304 DFMA/cycle (ncu unit count) x 2 flop x 2.07 GHz",
-                "hbm": {"achieved": hbm_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_gbs / hbm,
-                        "peak_source": hsrc}}
+    roof = kernel_roofline(name, tms, nl, total, wl, hbm, hsrc)
+    sb = step_bytes_per_cell_update(args.precision, wl.n_substeps)
+    hbm_frac_step = (value / ws) * sb / (hbm * 1e9)
 
     # end to end through the C ABI: every step uploads the state from pinned host memory,
     # advances one step and downloads the state
     e2e = None
     if args.e2e_steps > 0:
-        host = {k: torch.empty(d._shape(k), dtype=torch.float64).pin_memory() for k in
-                ("rho", "rhotheta", "rhou", "rhov", "rhow")}
-        for k, t in host.items():
-            t.copy_(torch.from_numpy(d.erf_get_state(k)))
-        L = d.L
-        nbytes = sum(t.numel() * 8 for t in host.values())
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            for k, t in host.items():
-                st = L.erf_set_state(d.h, FIELDS[k], t.data_ptr(), 0, 0)
-                assert st == 0
-            d.erf_rk3_step(1)
-            for k, t in host.items():
-                st = L.erf_get_state(d.h, FIELDS[k], t.data_ptr(), 0, 0)
-                assert st == 0
-        torch.cuda.synchronize()
-        te = time.perf_counter() - t0
+        e2e = _e2e_rate(d, wl, args.e2e_steps, "f64" if args.precision == "fp64" else "f32")
+        te = wl.ncell * args.e2e_steps / e2e["value"]
         te = max_over_ranks(pg, te)
-        e2e = {"value": ws * wl.ncell * args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
+        e2e["value"] = ws * wl.ncell * args.e2e_steps / te
 
     cmp = None
     if args.cmp_steps > 0:
@@ -479,7 +533,9 @@ def run_ours(args):
                            "reasons": clocks["reasons"], "samples": clocks["samples"]},
                 "e2e": e2e, "gpu_launches": kps * args.steps, "kernels_per_step": kps,
                 "roofline": roof, "cpu_baseline": cpu, "precision_comparison": cmp,
-                "mass_rel_drift": None if diag["mass"] == 0 else None,
+                "mass_rel_drift": abs(diag["mass"] - diag0["mass"]) / abs(diag0["mass"]),
+                "mass_drift_steps": args.steps,
+                "hbm_frac_step": hbm_frac_step, "step_alg_bytes_per_cell_update": sb,
                 "kernel_times_ms": {k: round(v[0] / 2, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
         print(json.dumps(line), flush=True)
     if pg is not None:
@@ -493,7 +549,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--case", default="hill_bubble")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--cmp-grid", type=int, nargs=3, default=[2048, 2048, 160],
@@ -503,6 +559,8 @@ def main():
     ap.add_argument("--paper-grid", type=int, nargs=3, default=[512, 512, 256],
                     help="grid of the paper's scaling workload (upwind-3) FP64/FP32 line (0 0 0 skips it)")
     ap.add_argument("--cmp-steps", type=int, default=8, help="timed steps per FP32 form (FP64: a quarter); 0 skips")
+    ap.add_argument("--cmp-e2e-steps", type=int, default=2,
+                    help="steps of the FP32 + learned form timed end to end through the C ABI with host buffers")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--closure", default="default", choices=["default", "learned"],
                     help="learned: the MLP closure (convective_abl with --precision mixed)")

@@ -245,6 +245,23 @@ erf_status erf_reduce_state_noalloc(int32_t nx, int32_t ny, int32_t nz, double d
                                     const double *d_rhou, const double *d_rhov, const double *d_rhow,
                                     double *d_out, void *cuda_stream);
 
+/* ---- x-y pencil decomposition (Sec. 5.1-5.2: the domain is split over ranks, each rank's
+ * boundary columns refreshed from its neighbours).  A rank advances its pencil widened by a halo
+ * of H columns per sharded side (H at least the columns one RK3 step reaches sideways) and
+ * refreshes the halo once per step; these calls move the halo strips.  A column block is the
+ * columns [i0, i0+ni) x [j0, j0+nj) (0 <= i0, i0+ni <= nx, likewise j) at every level of every
+ * prognostic field - rho, rho theta, rho u, rho v (nz levels each), rho w (nz+1), then rho phi
+ * when the handle carries the passive scalar - packed field after field, each [k][jj][ii] with ii
+ * fastest, in the path's storage type (FP64 on the FP64 path; the FP32 perturbations from the
+ * base state on the mixed path, so a block copied between two handles of the same grid levels
+ * and base state is bit-identical).  d_buf is a device buffer owned by the caller, at least
+ * erf_column_block_bytes long.  Both copies are asynchronous on the bound stream (capturable);
+ * erf_unpack_columns takes effect for the next step.  Errors: ERF_EINVAL for a block outside the
+ * grid or NULL pointers, ERF_ESTATE for a pack before any state was set. */
+erf_status erf_column_block_bytes(const erf_handle *h, int32_t ni, int32_t nj, size_t *bytes);
+erf_status erf_pack_columns(erf_handle *h, int32_t i0, int32_t ni, int32_t j0, int32_t nj, void *d_buf);
+erf_status erf_unpack_columns(erf_handle *h, int32_t i0, int32_t ni, int32_t j0, int32_t nj, const void *d_buf);
+
 /* Runtime options (no counterpart in the paper).
  *   ERF_OPT_TMA_STENCILS: 1 (default) stages the 3D stencils of the mixed-precision flux kernels
  *   in shared memory with TMA tile loads where the grid allows it (nx % 4 == 0, nx >= 64,

@@ -556,6 +556,65 @@ extern "C" erf_status erf_profile_steps(erf_handle *h, int32_t nsteps, erf_kerne
     return ERF_OK;
 }
 
+// the prognostic fields in storage order: rho, rho theta, rho u, rho v (nz levels), rho w (nz+1),
+// then rho phi when the handle carries the passive scalar
+static int state_fields(erf_handle *h, void **ptr, int *levels) {
+    const int nz = h->geo.nz;
+    int n = 0;
+    if (h->mixed) {
+        void *f[5] = {h->mst.r, h->mst.t, h->mst.u, h->mst.v, h->mst.w};
+        for (int q = 0; q < 5; ++q) { ptr[n] = f[q]; levels[n++] = q == 4 ? nz + 1 : nz; }
+        if (h->mtphi) { ptr[n] = h->mtphi; levels[n++] = nz; }
+    } else {
+        void *f[5] = {h->st.r, h->st.t, h->st.u, h->st.v, h->st.w};
+        for (int q = 0; q < 5; ++q) { ptr[n] = f[q]; levels[n++] = q == 4 ? nz + 1 : nz; }
+        if (h->tphi) { ptr[n] = h->tphi; levels[n++] = nz; }
+    }
+    return n;
+}
+
+extern "C" erf_status erf_column_block_bytes(const erf_handle *hc, int32_t ni, int32_t nj, size_t *bytes) {
+    erf_handle *h = const_cast<erf_handle *>(hc);
+    if (!h || !bytes || ni < 0 || nj < 0) return fail(h, ERF_EINVAL, "bad column-block arguments");
+    void *p[8];
+    int lv[8];
+    int nf = state_fields(h, p, lv);
+    size_t words = 0;
+    for (int q = 0; q < nf; ++q) words += (size_t)lv[q] * ni * nj;
+    *bytes = words * (h->mixed ? sizeof(float) : sizeof(double));
+    return ERF_OK;
+}
+
+static erf_status column_block(erf_handle *h, int32_t i0, int32_t ni, int32_t j0, int32_t nj, void *buf,
+                               int unpack) {
+    if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
+    const Geo &g = h->geo;
+    if (!buf || ni < 0 || nj < 0 || i0 < 0 || j0 < 0 || (long long)i0 + ni > g.nx || (long long)j0 + nj > g.ny)
+        return fail(h, ERF_EINVAL, "column block outside the grid");
+    if (unpack == 0 && !h->have_state) return fail(h, ERF_ESTATE, "no state set");
+    void *p[8];
+    int lv[8];
+    int nf = state_fields(h, p, lv);
+    const int eb = h->mixed ? (int)sizeof(float) : (int)sizeof(double);
+    char *b = reinterpret_cast<char *>(buf);
+    for (int q = 0; q < nf; ++q) {
+        launch_column_block(p[q], b, eb, g.nx, g.ny, lv[q], i0, ni, j0, nj, unpack, h->user);
+        b += (size_t)lv[q] * ni * nj * eb;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, unpack ? "unpack columns" : "pack columns");
+    return ERF_OK;
+}
+
+extern "C" erf_status erf_pack_columns(erf_handle *h, int32_t i0, int32_t ni, int32_t j0, int32_t nj, void *d_buf) {
+    return column_block(h, i0, ni, j0, nj, d_buf, 0);
+}
+
+extern "C" erf_status erf_unpack_columns(erf_handle *h, int32_t i0, int32_t ni, int32_t j0, int32_t nj,
+                                         const void *d_buf) {
+    return column_block(h, i0, ni, j0, nj, const_cast<void *>(d_buf), 1);
+}
+
 extern "C" erf_status erf_set_initial(erf_handle *h, const double *dtheta, const double *u, const double *v,
                                       const double *w, int32_t is_device) {
     if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");

@@ -34,6 +34,10 @@ void launch_stage_end(const Geo &g, F5 st, CF5 x, cudaStream_t s);
 void launch_stage_nosub(const Geo &g, F5 st, CF5 sn, CF5 R, double adt, cudaStream_t s);
 void launch_diag(const Geo &g, CF5 st, double dt, double *part, double *out, cudaStream_t s);
 void launch_convert(const void *src, void *dst, long long n, int to_f64, cudaStream_t s);
+// copies the columns [i0, i0+ni) x [j0, j0+nj) of one field (levels x ny x nx, elem_bytes 8 or 4)
+// to (unpack = 0) or from (unpack = 1) a packed buffer [levels][nj][ni]
+void launch_column_block(void *field, void *buf, int elem_bytes, int nx, int ny, int levels, int i0, int ni,
+                         int j0, int nj, int unpack, cudaStream_t s);
 
 constexpr int DIAG_PARTS = 512;
 

@@ -29,7 +29,8 @@ EXPORTS = ["erf_workspace_bytes", "erf_init_grid", "erf_set_initial", "erf_set_s
            "erf_reduce_state_noalloc", "erf_train_scratch_bytes", "erf_train_closure", "erf_closure_grad",
            "erf_column_stats", "erf_standardise", "erf_set_closure_weights", "erf_closure_features",
            "erf_closure_fields", "erf_filter_state", "erf_set_tracer_initial", "erf_set_option",
-           "erf_get_option", "erf_selftest_wait_timeout", "erf_selftest_tensor_cores"]
+           "erf_get_option", "erf_selftest_wait_timeout", "erf_selftest_tensor_cores",
+           "erf_column_block_bytes", "erf_pack_columns", "erf_unpack_columns"]
 
 
 class ErfError(RuntimeError):
@@ -108,6 +109,9 @@ def load_library(path: str = LIB_PATH):
     L.erf_closure_features.argtypes = [vp, vp]
     L.erf_closure_fields.argtypes = [vp, vp, C.POINTER(C.c_uint32)]
     L.erf_filter_state.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp, vp]
+    L.erf_column_block_bytes.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]
+    L.erf_pack_columns.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp]
+    L.erf_unpack_columns.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp]
     L.erf_last_error.argtypes = [vp]
     L.erf_last_error.restype = C.c_char_p
     L.erf_destroy.argtypes = [vp]
@@ -115,7 +119,8 @@ def load_library(path: str = LIB_PATH):
                  "erf_get_state", "erf_diagnostics", "erf_profile_steps", "erf_train_closure", "erf_closure_grad",
                  "erf_column_stats", "erf_standardise", "erf_set_closure_weights", "erf_closure_features",
                  "erf_closure_fields", "erf_filter_state", "erf_set_tracer_initial", "erf_set_option",
-                 "erf_get_option", "erf_selftest_wait_timeout", "erf_selftest_tensor_cores"):
+                 "erf_get_option", "erf_selftest_wait_timeout", "erf_selftest_tensor_cores",
+                 "erf_column_block_bytes", "erf_pack_columns", "erf_unpack_columns"):
         getattr(L, name).restype = C.c_int
     _LIB = L
     return L
@@ -292,6 +297,29 @@ class Dycore:
 
     def state(self):
         return {k: self.erf_get_state(k) for k in ("rho", "rhotheta", "rhou", "rhov", "rhow")}
+
+    # -- x-y pencil decomposition: column blocks of the prognostic state (device buffers)
+    def erf_column_block_bytes(self, ni, nj):
+        n = C.c_size_t()
+        _check(self.L, self.h, self.L.erf_column_block_bytes(self.h, int(ni), int(nj), C.byref(n)))
+        return n.value
+
+    def empty(self, ni, nj):
+        """A device buffer for one column block (the path's storage type)."""
+        import torch
+        dt = torch.float32 if self.wl.precision == 1 else torch.float64
+        n = self.erf_column_block_bytes(ni, nj) // (4 if dt == torch.float32 else 8)
+        return torch.empty(n, dtype=dt, device=self.device)
+
+    def pack(self, i0, ni, j0, nj, out=None):
+        buf = self.empty(ni, nj) if out is None else out
+        _check(self.L, self.h, self.L.erf_pack_columns(self.h, int(i0), int(ni), int(j0), int(nj), buf.data_ptr()))
+        return buf
+
+    def unpack(self, i0, ni, j0, nj, buf):
+        assert buf.is_cuda and buf.is_contiguous()
+        assert buf.numel() * buf.element_size() >= self.erf_column_block_bytes(ni, nj)
+        _check(self.L, self.h, self.L.erf_unpack_columns(self.h, int(i0), int(ni), int(j0), int(nj), buf.data_ptr()))
 
     # -- learned closure
     def erf_set_closure_weights(self, blob: bytes):
