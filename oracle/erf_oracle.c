@@ -61,6 +61,11 @@ typedef struct {
     double z0, sfc_theta_flux;
     double theta_s, brunt_N, p_s;  /* base state: theta0 = theta_s exp(N^2 z/g) unless knots given */
     int32_t tracer;           /* 1: advance a passive scalar rho phi after the substeps (Sec. 3.1) */
+    /* Rayleigh damping (Sec. 3.7, App. D): inverse timescale tau_max [1/s] at the domain top,
+     * ramped by sin^2 from 0 at the bottom z_d of the damping layer; fields bitmask 1 = u, 2 = v,
+     * 4 = w, 8 = theta (0 = off) */
+    double ray_tau, ray_zd;
+    int32_t ray_fields;
 } orc_cfg;
 
 typedef struct {
@@ -91,6 +96,10 @@ typedef struct {
     /* passive scalar: rho phi, its S^n copy, and the sums over a stage's substeps of the
      * perturbation mass fluxes that advance rho'' (x-faces, y-faces, w-faces) */
     double *rphi, *sn_phi, *msx, *msy, *msz;
+    /* Deardorff 1.5-order closure (closure 4): rho e (SGS kinetic energy per unit mass e), its S^n
+     * copy, the stage's source rho (P + B - eps) + div(2 mu grad e) at cells, and the heat
+     * diffusivity rho K_h at cells */
+    double *rtke, *sn_tke, *tke_src, *muh;
     /* learned closure (closure 3): a model evaluated on each stage state; it writes nine planes
      * of ncell values at cell centres, density-weighted: rho t11, rho t22, rho t33, rho t12,
      * rho t13, rho t23, rho h1, rho h2, rho h3 (kinematic stress [m^2/s^2] and SGS heat flux
@@ -298,6 +307,7 @@ orc *orc_create(const orc_cfg *cfg, const double *zeta, const double *hnode,
     o->mfx = dalloc(NC); o->mfy = dalloc(NC); o->rom = dalloc(NW);
     o->ux = dalloc(NC); o->vy = dalloc(NC); o->wz = dalloc(NW); o->mu = dalloc(NC);
     o->rphi = dalloc(NC); o->sn_phi = dalloc(NC); o->msx = dalloc(NC); o->msy = dalloc(NC); o->msz = dalloc(NW);
+    o->rtke = dalloc(NC); o->sn_tke = dalloc(NC); o->tke_src = dalloc(NC); o->muh = dalloc(NC);
 
     /* node heights, App. B + canonical smoothing z = zeta + (1 - zeta/z_t)^beta h (Sec. 3.4) */
     #pragma omp parallel for
@@ -373,7 +383,7 @@ void orc_destroy(orc *o) {
                        &o->th0, &o->p0, &o->rho, &o->rt, &o->ru, &o->rv, &o->rw, &o->pp, &o->pi,
                        &o->th, &o->Om, &o->Tprev, &o->fx, &o->fy, &o->fz, &o->mfx, &o->mfy,
                        &o->rom, &o->ux, &o->vy, &o->wz, &o->mu, &o->rphi, &o->sn_phi, &o->msx,
-                       &o->msy, &o->msz, &o->sgs_planes};
+                       &o->msy, &o->msz, &o->sgs_planes, &o->rtke, &o->sn_tke, &o->tke_src, &o->muh};
     for (size_t n = 0; n < sizeof(ptrs) / sizeof(ptrs[0]); ++n) free(*ptrs[n]);
     for (int f = 0; f < 5; ++f) { free(o->sn[f]); free(o->R[f]); free(o->X[f]); }
     free(o);
@@ -673,14 +683,14 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
 
     /* --- subgrid stress and heat flux: -div(tau), div(rho alpha grad theta) (Eq. stresstensor;
      * reading R6 for the Smagorinsky-Lilly form on a flat, possibly stretched grid) */
-    if (C->closure == 1 || C->closure == 2 || C->closure == 3 || C->surface == 1) {
+    if (C->closure >= 1 || C->surface == 1) {
         /* strain at cell centres (diagonal) and edges (off-diagonal), velocities at faces */
         double *S11 = dalloc(o->ncell), *S22 = dalloc(o->ncell), *S33 = dalloc(o->ncell);
         double *S12 = dalloc(o->ncell), *S13 = dalloc(o->nw), *S23 = dalloc(o->nw);
         double *t11 = dalloc(o->ncell), *t22 = dalloc(o->ncell), *t33 = dalloc(o->ncell);
         double *t12 = dalloc(o->ncell), *t13 = dalloc(o->nw), *t23 = dalloc(o->nw);
         double *hx = dalloc(o->ncell), *hy = dalloc(o->ncell), *hz = dalloc(o->nw);
-        int visc = (C->closure == 1 || C->closure == 2);
+        int visc = (C->closure == 1 || C->closure == 2 || C->closure == 4);
         #pragma omp parallel for
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
@@ -721,8 +731,39 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                     } else if (C->closure == 1) {
                         mu = rho[c] * C->nu;
                     }
-                    o->mu[c] = mu;
                     double dv = S11[c] + S22[c] + S33[c];
+                    if (C->closure == 4) {
+                        /* Deardorff (1980) 1.5-order closure with the coefficients of Moeng (1984):
+                         * mixing length l = Delta, or 0.76 sqrt(e)/N in stable stratification when
+                         * shorter; K_m = 0.1 l sqrt(e); K_h = (1 + 2 l/Delta) K_m; dissipation
+                         * C_eps e^(3/2)/l with C_eps = 0.19 + 0.51 l/Delta.  N^2 = (g/theta) dtheta/dz
+                         * from the cells above and below (one-sided at the walls).  The shear
+                         * production is the energy the resolved flow loses to the stress
+                         * tau = -2 mu (S - D): -tau_ij S_ij / rho = 2 K_m (S_ij S_ij - (S_kk)^2/3). */
+                        double e = o->rtke[c] / rho[c];
+                        if (e < 0.0) e = 0.0;
+                        double Delta = cbrt(dx * dy * o->Hc[c]);
+                        int kl = (k == 0) ? 0 : k - 1, ku = (k == nz - 1) ? nz - 1 : k + 1;
+                        double N2 = 0.0;
+                        if (ku > kl) {
+                            size_t cl = IX(o, i, j, kl), cu = IX(o, i, j, ku);
+                            N2 = g / o->th[c] * (o->th[cu] - o->th[cl]) / (o->zc[cu] - o->zc[cl]);
+                        }
+                        double l = Delta;
+                        if (N2 > 0.0 && e > 0.0) {
+                            double ls = 0.76 * sqrt(e) / sqrt(N2);
+                            if (ls < l) l = ls;
+                        }
+                        double Km = 0.1 * l * sqrt(e);
+                        double Kh = (1.0 + 2.0 * l / Delta) * Km;
+                        mu = rho[c] * Km;
+                        o->muh[c] = rho[c] * Kh;
+                        double P = 2.0 * Km * (SS - dv * dv / 3.0);
+                        double B = -Kh * N2;
+                        double eps = (0.19 + 0.51 * l / Delta) * e * sqrt(e) / l;
+                        o->tke_src[c] = rho[c] * (P + B - eps);
+                    }
+                    o->mu[c] = mu;
                     t11[c] = -2.0 * mu * (S11[c] - dv / 3.0);
                     t22[c] = -2.0 * mu * (S22[c] - dv / 3.0);
                     t33[c] = -2.0 * mu * (S33[c] - dv / 3.0);
@@ -737,10 +778,13 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                         double me = 0.25 * (o->mu[IX(o, i - 1, j - 1, k)] + o->mu[IX(o, i, j - 1, k)]
                                           + o->mu[IX(o, i - 1, j, k)] + o->mu[c]);
                         t12[c] = -2.0 * me * S12[c];
-                        hx[c] = 0.5 * (o->mu[IX(o, i - 1, j, k)] + o->mu[c]) / C->Pr_t
-                              * (o->th[c] - o->th[IX(o, i - 1, j, k)]) / dx;
-                        hy[c] = 0.5 * (o->mu[IX(o, i, j - 1, k)] + o->mu[c]) / C->Pr_t
-                              * (o->th[c] - o->th[IX(o, i, j - 1, k)]) / dy;
+                        /* heat diffusivity rho alpha_theta: mu / Pr_t, or rho K_h (Deardorff) */
+                        double ax = (C->closure == 4) ? 0.5 * (o->muh[IX(o, i - 1, j, k)] + o->muh[c])
+                                                      : 0.5 * (o->mu[IX(o, i - 1, j, k)] + o->mu[c]) / C->Pr_t;
+                        double ay = (C->closure == 4) ? 0.5 * (o->muh[IX(o, i, j - 1, k)] + o->muh[c])
+                                                      : 0.5 * (o->mu[IX(o, i, j - 1, k)] + o->mu[c]) / C->Pr_t;
+                        hx[c] = ax * (o->th[c] - o->th[IX(o, i - 1, j, k)]) / dx;
+                        hy[c] = ay * (o->th[c] - o->th[IX(o, i, j - 1, k)]) / dy;
                     }
                     if (k == 0 || k == nz) { t13[w] = 0.0; t23[w] = 0.0; hz[w] = 0.0; continue; }
                     double mxz = 0.25 * (o->mu[IX(o, i - 1, j, k - 1)] + o->mu[IX(o, i, j, k - 1)]
@@ -750,8 +794,9 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                     t13[w] = -2.0 * mxz * S13[w];
                     t23[w] = -2.0 * myz * S23[w];
                     double dzc = o->zc[IX(o, i, j, k)] - o->zc[IX(o, i, j, k - 1)];
-                    hz[w] = 0.5 * (o->mu[IX(o, i, j, k - 1)] + o->mu[IX(o, i, j, k)]) / C->Pr_t
-                          * (o->th[IX(o, i, j, k)] - o->th[IX(o, i, j, k - 1)]) / dzc;
+                    double az = (C->closure == 4) ? 0.5 * (o->muh[IX(o, i, j, k - 1)] + o->muh[IX(o, i, j, k)])
+                                                  : 0.5 * (o->mu[IX(o, i, j, k - 1)] + o->mu[IX(o, i, j, k)]) / C->Pr_t;
+                    hz[w] = az * (o->th[IX(o, i, j, k)] - o->th[IX(o, i, j, k - 1)]) / dzc;
                 }
         if (!visc) {   /* MOST without a closure: only the surface fluxes below */
             memset(t11, 0, sizeof(double) * o->ncell); memset(t22, 0, sizeof(double) * o->ncell);
@@ -839,9 +884,75 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                     Rw[w] -= (t13[IX(o, i + 1, j, k)] - t13[w]) / dx + (t23[IX(o, i, j + 1, k)] - t23[w]) / dy
                            + (t33[IX(o, i, j, k)] - t33[IX(o, i, j, k - 1)]) / dzc;
                 }
+        if (C->closure == 4) {
+            /* transport of e by the SGS eddies: div(rho 2 K_m grad e), face coefficient the mean
+             * of the two cells' 2 mu; no flux through the walls */
+            double *e = dalloc(o->ncell);
+            for (size_t c = 0; c < o->ncell; ++c) { double v = o->rtke[c] / rho[c]; e[c] = v > 0.0 ? v : 0.0; }
+            #pragma omp parallel for
+            for (int k = 0; k < nz; ++k)
+                for (int j = 0; j < ny; ++j)
+                    for (int i = 0; i < nx; ++i) {
+                        size_t c = IX(o, i, j, k);
+                        size_t cxm = IX(o, i - 1, j, k), cxp = IX(o, i + 1, j, k);
+                        size_t cym = IX(o, i, j - 1, k), cyp = IX(o, i, j + 1, k);
+                        double fxm = (o->mu[cxm] + o->mu[c]) * (e[c] - e[cxm]) / dx;
+                        double fxp = (o->mu[c] + o->mu[cxp]) * (e[cxp] - e[c]) / dx;
+                        double fym = (o->mu[cym] + o->mu[c]) * (e[c] - e[cym]) / dy;
+                        double fyp = (o->mu[c] + o->mu[cyp]) * (e[cyp] - e[c]) / dy;
+                        double fzm = 0.0, fzp = 0.0;
+                        if (k > 0) {
+                            size_t cm = IX(o, i, j, k - 1);
+                            fzm = (o->mu[cm] + o->mu[c]) * (e[c] - e[cm]) / (o->zc[c] - o->zc[cm]);
+                        }
+                        if (k < nz - 1) {
+                            size_t cp = IX(o, i, j, k + 1);
+                            fzp = (o->mu[c] + o->mu[cp]) * (e[cp] - e[c]) / (o->zc[cp] - o->zc[c]);
+                        }
+                        o->tke_src[c] += (fxp - fxm) / dx + (fyp - fym) / dy + (fzp - fzm) / o->Hc[c];
+                    }
+            free(e);
+        }
         free(S11); free(S22); free(S33); free(S12); free(S13); free(S23);
         free(t11); free(t22); free(t33); free(t12); free(t13); free(t23);
         free(hx); free(hy); free(hz);
+    }
+
+    /* --- Rayleigh damping (Sec. 3.7; App. D: strength an inverse timescale, sin^2 ramp from 0 at
+     * the bottom z_d of the layer to tau_max at the top z_t).  Reading: each damped quantity relaxes
+     * toward its reference at its own physical height - u, v toward the geostrophic wind (u_g,
+     * v_g), w toward 0, theta toward the base state theta0 - as -tau(z) rho (phi - phi_ref) in the
+     * tendency of rho phi (the face density the mean of the two cells). */
+    if (C->ray_tau > 0.0 && C->ray_fields != 0) {
+        const double zd = C->ray_zd, zt = o->zt;
+        #pragma omp parallel for
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    size_t c = IX(o, i, j, k), cxm = IX(o, i - 1, j, k), cym = IX(o, i, j - 1, k);
+                    double z, t;
+                    if (C->ray_fields & 8) {
+                        z = o->zc[c];
+                        t = (z > zd) ? C->ray_tau * pow(sin(0.5 * M_PI * (z - zd) / (zt - zd)), 2.0) : 0.0;
+                        Rt[c] -= t * (rt[c] - rho[c] * o->th0[c]);
+                    }
+                    if (C->ray_fields & 1) {
+                        z = 0.5 * (o->zc[cxm] + o->zc[c]);
+                        t = (z > zd) ? C->ray_tau * pow(sin(0.5 * M_PI * (z - zd) / (zt - zd)), 2.0) : 0.0;
+                        Ru[c] -= t * (ru[c] - 0.5 * (rho[cxm] + rho[c]) * C->u_g);
+                    }
+                    if (C->ray_fields & 2) {
+                        z = 0.5 * (o->zc[cym] + o->zc[c]);
+                        t = (z > zd) ? C->ray_tau * pow(sin(0.5 * M_PI * (z - zd) / (zt - zd)), 2.0) : 0.0;
+                        Rv[c] -= t * (rv[c] - 0.5 * (rho[cym] + rho[c]) * C->v_g);
+                    }
+                    if ((C->ray_fields & 4) && k >= 1) {
+                        size_t w = IX(o, i, j, k);
+                        z = o->zw[w];
+                        t = (z > zd) ? C->ray_tau * pow(sin(0.5 * M_PI * (z - zd) / (zt - zd)), 2.0) : 0.0;
+                        Rw[w] -= t * rw[w];
+                    }
+                }
     }
 }
 
@@ -977,13 +1088,17 @@ static void substep(orc *o, const double *rho_t, const double *rt_t, double dtau
  * advanced rho (stage momentum + perturbation flux of each substep).  With that average,
  * rho phi / rho stays 1 for phi = 1 (rho^(s) = rho^n - alpha_s dt div <M>).  phi^t is
  * interpolated like theta (WENO5 or the linear interpolant of scal_adv). */
-static void tracer_stage(orc *o, const double *rho_t, double adt, int nsub) {
+/* The same stage update serves every transported scalar q (rho phi, and rho e of the Deardorff
+ * closure): rho q^(s) = rho q^n + alpha_s dt (-div F(q^t) / H + src), src the scalar's own source
+ * at the stage state (NULL: none); clip = 1 keeps rho q >= 0 (the SGS energy). */
+static void scalar_stage(orc *o, double *rq, const double *sn_q, const double *src, int clip,
+                         const double *rho_t, double adt, int nsub) {
     const orc_cfg *C = &o->c;
     int nx = o->nx, ny = o->ny, nz = o->nz;
     double dx = C->dx, dy = C->dy;
     int zf = (C->scal_adv == 1);
     double *phi = dalloc(o->ncell), *F[3] = {dalloc(o->ncell), dalloc(o->ncell), dalloc(o->nw)};
-    for (size_t c = 0; c < o->ncell; ++c) phi[c] = o->rphi[c] / rho_t[c];
+    for (size_t c = 0; c < o->ncell; ++c) phi[c] = rq[c] / rho_t[c];
     #pragma omp parallel for
     for (int k = 0; k <= nz; ++k)
         for (int j = 0; j < ny; ++j)
@@ -1010,9 +1125,16 @@ static void tracer_stage(orc *o, const double *rho_t, double adt, int nsub) {
                 double div = (F[0][IX(o, i + 1, j, k)] - F[0][c]) / dx
                            + (F[1][IX(o, i, j + 1, k)] - F[1][c]) / dy
                            + (F[2][IX(o, i, j, k + 1)] - F[2][c]);
-                o->rphi[c] = o->sn_phi[c] + adt * (-div / o->Hc[c]);
+                double v = sn_q[c] + adt * (-div / o->Hc[c] + (src ? src[c] : 0.0));
+                rq[c] = (clip && v < 0.0) ? 0.0 : v;
             }
     free(phi); free(F[0]); free(F[1]); free(F[2]);
+}
+static void tracer_stage(orc *o, const double *rho_t, double adt, int nsub) {
+    scalar_stage(o, o->rphi, o->sn_phi, NULL, 0, rho_t, adt, nsub);
+}
+static void tke_stage(orc *o, const double *rho_t, double adt, int nsub) {
+    scalar_stage(o, o->rtke, o->sn_tke, o->tke_src, 1, rho_t, adt, nsub);
 }
 
 /* ------------------------------------------------------------------ RK3 step (Sec. 3.1) */
@@ -1035,17 +1157,20 @@ static void rk3_step(orc *o) {
     apply_wall_bc(o, o->rw, o->ru, o->rv);
     for (int f = 0; f < 5; ++f) memcpy(o->sn[f], field_ptr(o, f), sizeof(double) * field_len(o, f));
     if (C->tracer) memcpy(o->sn_phi, o->rphi, sizeof(double) * o->ncell);
+    int tke = (C->closure == 4);
+    if (tke) memcpy(o->sn_tke, o->rtke, sizeof(double) * o->ncell);
     const double alpha[3] = {1.0 / 3.0, 0.5, 1.0};
     /* S^t is held in o->rho.. (the state arrays), updated in place at the end of each stage */
     for (int s = 0; s < 3; ++s) {
         slow_rhs(o, o->rho, o->rt, o->ru, o->rv, o->rw);
-        if (C->tracer) {
+        if (C->tracer || tke) {
             memset(o->msx, 0, sizeof(double) * o->ncell);
             memset(o->msy, 0, sizeof(double) * o->ncell);
             memset(o->msz, 0, sizeof(double) * o->nw);
         }
         if (C->substep_mode == 1) {
             if (C->tracer) tracer_stage(o, o->rho, alpha[s] * dt, 1);
+            if (tke) tke_stage(o, o->rho, alpha[s] * dt, 1);
             /* no substepping: S^(s) = S^n + alpha_s dt f(S^t) */
             for (int f = 0; f < 5; ++f) {
                 double *S = field_ptr(o, f);
@@ -1076,6 +1201,7 @@ static void rk3_step(orc *o) {
         memcpy(rt_t, o->rt, sizeof(double) * o->ncell);
         for (int n = 0; n < nsub; ++n) substep(o, rho_t, rt_t, dtau);
         if (C->tracer) tracer_stage(o, rho_t, alpha[s] * dt, nsub);
+        if (tke) tke_stage(o, rho_t, alpha[s] * dt, nsub);
         free(rho_t); free(rt_t);
         /* S^(s) = S^t + X'' */
         for (int f = 0; f < 5; ++f) {
@@ -1126,10 +1252,12 @@ int orc_get_field(orc *o, int f, double *dst) {
     if (f == 6) { memcpy(dst, o->p0, sizeof(double) * o->ncell); return 0; }
     if (f == 7) { memcpy(dst, o->th0, sizeof(double) * o->ncell); return 0; }
     if (f == 8) { memcpy(dst, o->rphi, sizeof(double) * o->ncell); return 0; }
+    if (f == 9) { memcpy(dst, o->rtke, sizeof(double) * o->ncell); return 0; }
     return -1;
 }
 int orc_set_field(orc *o, int f, const double *src) {
     if (f == 8) { memcpy(o->rphi, src, sizeof(double) * o->ncell); return 0; }
+    if (f == 9) { memcpy(o->rtke, src, sizeof(double) * o->ncell); return 0; }
     if (f < 0 || f >= 5) return -1;
     memcpy(field_ptr(o, f), src, sizeof(double) * field_len(o, f));
     o->have_state = 1;
@@ -1201,6 +1329,14 @@ int orc_substep_once(orc *o, double dtau, double *Xr, double *Xt, double *Xu, do
 
 /* eddy viscosity of the last slow-RHS evaluation */
 int orc_get_mu(orc *o, double *dst) { memcpy(dst, o->mu, sizeof(double) * o->ncell); return 0; }
+/* cell arrays of the last slow-RHS evaluation: 0 mu (= rho K_m), 1 rho K_h (Deardorff),
+ * 2 the SGS-energy source rho (P + B - eps) + div(2 mu grad e) (Deardorff) */
+int orc_get_aux(orc *o, int which, double *dst) {
+    const double *src[] = {o->mu, o->muh, o->tke_src};
+    if (which < 0 || which > 2) return -1;
+    memcpy(dst, src[which], sizeof(double) * o->ncell);
+    return 0;
+}
 /* domain-integrated mass: sum of rho times the physical cell volume, in fixed (k,j,i) order */
 double orc_mass(orc *o) {
     double m = 0.0;

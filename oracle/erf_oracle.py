@@ -48,6 +48,7 @@ class _Cfg(C.Structure):
         ("surface", C.c_int32), ("z0", C.c_double), ("sfc_theta_flux", C.c_double),
         ("theta_s", C.c_double), ("brunt_N", C.c_double), ("p_s", C.c_double),
         ("tracer", C.c_int32),
+        ("ray_tau", C.c_double), ("ray_zd", C.c_double), ("ray_fields", C.c_int32),
     ]
 
 
@@ -82,6 +83,9 @@ class OracleConfig:
     brunt_N: float = 0.0
     p_s: float = 1.0e5
     tracer: int = 0
+    ray_tau: float = 0.0
+    ray_zd: float = 0.0
+    ray_fields: int = 0
 
 
 _LIB = None
@@ -106,6 +110,7 @@ def _lib():
         L.orc_step.argtypes = [C.c_void_p, C.c_int]
         L.orc_slow_rhs.argtypes = [C.c_void_p] + [dp] * 8
         L.orc_get_mu.argtypes = [C.c_void_p, dp]
+        L.orc_get_aux.argtypes = [C.c_void_p, C.c_int, dp]
         L.orc_set_sgs_model.argtypes = [C.c_void_p, _SGS_FN, C.c_void_p]
         L.orc_substep_once.argtypes = [C.c_void_p, C.c_double] + [dp] * 10
         L.orc_mass.restype = C.c_double
@@ -140,7 +145,7 @@ def _f64(a):
 
 
 FIELDS = {"rho": 0, "rhotheta": 1, "rhou": 2, "rhov": 3, "rhow": 4,
-          "base_rho": 5, "base_p": 6, "base_theta": 7, "rhophi": 8}
+          "base_rho": 5, "base_p": 6, "base_theta": 7, "rhophi": 8, "rhotke": 9}
 GEOM = {"zc": 0, "Hc": 1, "Hx": 2, "Hy": 3, "hxi_x": 4, "heta_y": 5,
         "zw": 6, "hxi_w": 7, "heta_w": 8, "zn": 9}
 
@@ -250,6 +255,14 @@ class Oracle:
     def mu(self):
         out = np.empty(self.shape_c)
         _lib().orc_get_mu(self._h, _p(out))
+        return out
+
+    def aux(self, name):
+        """Cell arrays of the last slow-RHS evaluation: "mu" (rho K_m), "muh" (rho K_h) and
+        "tke_src" (the SGS-energy source) of the Deardorff closure."""
+        out = np.empty(self.shape_c)
+        rc = _lib().orc_get_aux(self._h, {"mu": 0, "muh": 1, "tke_src": 2}[name], _p(out))
+        assert rc == 0
         return out
 
     def mass(self):

@@ -23,7 +23,8 @@ import numpy as np
 # configuration enums shared by both implementations' wrappers (pure names, no arithmetic)
 MOM_UPWIND3, MOM_UPWIND5 = 3, 5
 SCAL_WENO5_JS, SCAL_WENO5_Z, SCAL_UPWIND3 = 0, 1, 3
-CLOSURE_NONE, CLOSURE_CONST_NU, CLOSURE_SMAGORINSKY, CLOSURE_LEARNED = 0, 1, 2, 3
+CLOSURE_NONE, CLOSURE_CONST_NU, CLOSURE_SMAGORINSKY, CLOSURE_LEARNED, CLOSURE_DEARDORFF = 0, 1, 2, 3, 4
+RAY_U, RAY_V, RAY_W, RAY_THETA = 1, 2, 4, 8
 SURFACE_SLIP, SURFACE_MOST = 0, 1
 PREC_FP64, PREC_MIXED32 = 0, 1
 
@@ -69,6 +70,10 @@ class Workload:
     w: Optional[np.ndarray] = None
     tracer: int = 0                        # 1: passive scalar rho phi (advanced after the substeps)
     phi: Optional[np.ndarray] = None       # initial phi at cells (tracer = 1)
+    tke: Optional[np.ndarray] = None       # initial SGS kinetic energy e [m^2/s^2] at cells (closure 4)
+    ray_tau: float = 0.0                   # Rayleigh damping strength at the top [1/s] (0 = off)
+    ray_zd: float = 0.0                    # bottom of the damping layer [m]
+    ray_fields: int = 0                    # RAY_U | RAY_V | RAY_W | RAY_THETA
     notes: str = ""
 
     @property

@@ -22,7 +22,8 @@ def oracle_config_from(wl, **over):
                        scal_adv=wl.scal_adv, closure=wl.closure, Cs=wl.Cs, Pr_t=wl.Pr_t,
                        nu=wl.nu, gravity=wl.gravity, f_cor=wl.f_cor, u_g=wl.u_g, v_g=wl.v_g,
                        surface=wl.surface, z0=wl.z0, sfc_theta_flux=wl.sfc_theta_flux,
-                       theta_s=wl.theta_s, brunt_N=wl.brunt_N, p_s=wl.p_s, tracer=wl.tracer)
+                       theta_s=wl.theta_s, brunt_N=wl.brunt_N, p_s=wl.p_s, tracer=wl.tracer,
+                       ray_tau=wl.ray_tau, ray_zd=wl.ray_zd, ray_fields=wl.ray_fields)
     for k, v in over.items():
         setattr(cfg, k, v)
     return cfg
@@ -36,6 +37,8 @@ def make_oracle(wl, init=True, **over):
         o.set_initial(wl.dtheta, wl.u, wl.v, wl.w)
         if wl.tracer and wl.phi is not None:
             o.set_tracer_initial(wl.phi)
+        if wl.closure == 4 and wl.tke is not None:
+            o.set("rhotke", o.get("rho") * wl.tke)
     return o
 
 
