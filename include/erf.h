@@ -53,13 +53,15 @@ typedef enum {
 typedef enum {
     ERF_RHO = 0, ERF_RHOTHETA = 1, ERF_RHOU = 2, ERF_RHOV = 3, ERF_RHOW = 4,
     ERF_BASE_RHO = 5, ERF_BASE_P = 6, ERF_BASE_THETA = 7,    /* base state: get only */
-    ERF_RHOPHI = 8                  /* passive scalar rho phi at cells (config tracer = 1) */
+    ERF_RHOPHI = 8,                 /* passive scalar rho phi at cells (config tracer = 1) */
+    ERF_RHOTKE = 9                  /* rho e, the SGS kinetic energy of the Deardorff closure */
 } erf_field;
 
 typedef enum { ERF_F64 = 0, ERF_F32 = 1 } erf_dtype;
 typedef enum { ERF_PREC_FP64 = 0, ERF_PREC_MIXED32 = 1 } erf_precision;
 typedef enum { ERF_CLOSURE_NONE = 0, ERF_CLOSURE_CONST_NU = 1, ERF_CLOSURE_SMAGORINSKY = 2,
-               ERF_CLOSURE_LEARNED = 3 /* mixed precision only */ } erf_closure;
+               ERF_CLOSURE_LEARNED = 3 /* mixed precision only */,
+               ERF_CLOSURE_DEARDORFF = 4 /* FP64 path, flat grids */ } erf_closure;
 typedef enum { ERF_SCAL_WENO5_JS = 0, ERF_SCAL_WENO5_Z = 1, ERF_SCAL_UPWIND3 = 3 } erf_scalar_scheme;
 typedef enum { ERF_SURFACE_SLIP = 0, ERF_SURFACE_MOST = 1 } erf_surface;
 
@@ -85,7 +87,16 @@ typedef struct {
     double beta_d;                  /* divergence damping of the forward-predicted pressure (Sec. 3.1) */
     int32_t scal_adv;               /* erf_scalar_scheme (Sec. 3.6): WENO5-JS, WENO5-Z or the linear
                                        third-order upwind interpolant */
-    int32_t closure;                /* erf_closure (Sec. 2.3) */
+    int32_t closure;                /* erf_closure (Sec. 2.3).  ERF_CLOSURE_DEARDORFF: the 1.5-order
+                                       TKE model of Deardorff (1980) with the coefficients of Moeng
+                                       (1984): l = Delta = (dx dy dz)^(1/3), or 0.76 sqrt(e)/N when
+                                       shorter in stable air; mu = rho 0.1 l sqrt(e) in the stress,
+                                       rho K_h = (1 + 2 l/Delta) mu for the heat flux; rho e is a
+                                       transported scalar (the stage-averaged fluxes of Sec. 3.1) with
+                                       the source rho (P - K_h N^2 - C_eps e^(3/2)/l) + div(2 mu grad e),
+                                       P the energy the stress takes from the resolved flow, C_eps =
+                                       0.19 + 0.51 l/Delta, clipped at rho e >= 0.  Initial rho e is set
+                                       with erf_set_state(ERF_RHOTKE) (zero otherwise). */
     double Cs, Pr_t, nu;            /* Smagorinsky constant, turbulent Prandtl number, constant nu [m^2/s] */
     int32_t precision;              /* erf_precision */
     double gravity;                 /* g [m/s^2] (0 allowed) */
@@ -101,6 +112,12 @@ typedef struct {
                                        0 = none */
     int32_t mom_adv;                /* momentum interpolant order (Sec. 3.6): 5 (or 0) upwind-5,
                                        3 upwind-3 (the paper's scaling workload, Sec. 5.2) */
+    double ray_tau, ray_zd;         /* Rayleigh damping (Sec. 3.7, App. D; FP64 path): rate [1/s] at
+                                       the domain top, ramped by sin^2 from 0 at height ray_zd [m];
+                                       each damped quantity relaxes at its own physical height,
+                                       -tau(z) rho (phi - phi_ref), toward u_g, v_g, 0 and the base
+                                       theta0.  ray_tau = 0 or ray_fields = 0: off */
+    int32_t ray_fields;             /* bitmask: 1 u, 2 v, 4 w, 8 theta */
 } erf_config;
 
 /* Diagnostics (Sec. 4.1.2: mass conserved to machine precision). */

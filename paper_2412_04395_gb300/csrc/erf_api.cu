@@ -52,12 +52,15 @@ struct erf_handle {
     std::string err;
     // workspace arrays
     double *hn, *hc, *hxf, *hyf, *gxh, *gyh, *g4xq, *g4yq;
-    double *dzeta, *zetac, *s, *sc, *ds, *dzc, *delta2, *rdzeta, *rdzc, *knz, *knt;
+    double *dzeta, *zetac, *s, *sc, *ds, *dzc, *delta2, *rdzeta, *rdzc, *knz, *knt, *delta;
     double *rho0, *th0, *p0;
     double *rH3 = nullptr, *rHx3 = nullptr, *rHy3 = nullptr, *rdzw3 = nullptr, *rdz2 = nullptr;
     double *Hx3 = nullptr, *Hy3 = nullptr;
     // passive scalar (FP64 path): rho phi (stage state), its S^n copy, substep flux sums
     double *tphi = nullptr, *snphi = nullptr, *msx = nullptr, *msy = nullptr, *msz = nullptr;
+    // Deardorff closure (FP64 path): rho e (stage state), its S^n copy, the stage's energy source
+    // and the heat diffusivity rho K_h
+    double *tke = nullptr, *sntke = nullptr, *tke_src = nullptr, *muh = nullptr;
     F5 st, sn, x, R;
     double *pp, *pi, *th, *Tp, *Om;
     Tri tri;
@@ -118,7 +121,20 @@ static erf_status validate(const erf_grid_desc *g, const erf_config *c, std::str
     if (!(c->dt > 0.0)) { msg = "dt must be positive"; return ERF_EINVAL; }
     if (c->substep_mode != 0 && c->substep_mode != 1) { msg = "substep_mode must be 0 or 1"; return ERF_EINVAL; }
     if (c->substep_mode == 0 && (c->n_substeps < 2 || c->n_substeps % 2)) { msg = "n_substeps must be even and >= 2"; return ERF_EINVAL; }
-    if (c->closure < 0 || c->closure > 3) { msg = "closure out of range"; return ERF_EINVAL; }
+    if (c->closure < 0 || c->closure > 4) { msg = "closure out of range"; return ERF_EINVAL; }
+    if (c->closure == 4 && c->precision != ERF_PREC_FP64) {
+        msg = "the Deardorff closure runs on the FP64 path";
+        return ERF_EUNSUPPORTED;
+    }
+    if (c->ray_fields < 0 || c->ray_fields > 15 || !(c->ray_tau >= 0.0) || !(c->ray_zd >= 0.0) ||
+        (c->ray_fields != 0 && !(c->ray_zd < g->z_faces[g->nz]))) {
+        msg = "Rayleigh damping: fields 0..15, tau >= 0, 0 <= z_d < domain top";
+        return ERF_EINVAL;
+    }
+    if (c->ray_fields != 0 && c->ray_tau > 0.0 && c->precision != ERF_PREC_FP64) {
+        msg = "Rayleigh damping runs on the FP64 path";
+        return ERF_EUNSUPPORTED;
+    }
     if (c->closure == 3 && c->precision != ERF_PREC_MIXED32) {
         msg = "the learned closure runs on the mixed-precision path";
         return ERF_EUNSUPPORTED;
@@ -162,6 +178,7 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
     H->delta2 = cv.take<double>(nz);
     H->rdzeta = cv.take<double>(nz);
     H->rdzc = cv.take<double>(nz + 1);
+    H->delta = cv.take<double>(nz);
     H->knz = cv.take<double>(c->n_knots > 0 ? c->n_knots : 1);
     H->knt = cv.take<double>(c->n_knots > 0 ? c->n_knots : 1);
     bool terr = false;
@@ -223,7 +240,13 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
     }
     if (c->tracer) {
         H->tphi = cv.take<double>(nc); H->snphi = cv.take<double>(nc);
+    }
+    if (c->tracer || c->closure == 4) {
         H->msx = cv.take<double>(nc); H->msy = cv.take<double>(nc); H->msz = cv.take<double>(nw);
+    }
+    if (c->closure == 4) {
+        H->tke = cv.take<double>(nc); H->sntke = cv.take<double>(nc);
+        H->tke_src = cv.take<double>(nc); H->muh = cv.take<double>(nc);
     }
     }
     H->kerr = cv.take<unsigned>(4);
@@ -251,6 +274,7 @@ static void fill_geo(erf_handle *h) {
     G.delta2 = h->delta2;
     G.rdzeta = h->rdzeta;
     G.rdzc = h->rdzc;
+    G.delta = h->delta;
     G.hc = h->hc; G.hxf = h->hxf; G.hyf = h->hyf; G.gxh = h->gxh; G.gyh = h->gyh; G.g4xq = h->g4xq; G.g4yq = h->g4yq;
     G.rho0 = h->rho0; G.th0 = h->th0; G.p0 = h->p0;
     G.rH3 = h->rH3; G.rHx3 = h->rHx3; G.rHy3 = h->rHy3; G.rdzw3 = h->rdzw3; G.rdz2 = h->rdz2;
@@ -264,6 +288,10 @@ static void fill_geo(erf_handle *h) {
     P.b2 = 0.5 * (1.0 + c.beta_s);
     P.closure = c.closure; P.surface = c.surface; P.scal_adv = c.scal_adv;
     P.mom3 = c.mom_adv == 3 ? 1 : 0;
+    P.ray_tau = c.ray_tau;
+    P.ray_zd = c.ray_zd;
+    P.ray_fields = c.ray_tau > 0.0 ? c.ray_fields : 0;
+    P.ray_zt = 0.0;   // set in erf_init_grid from the face heights
 }
 
 extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config *cfg, void *d_workspace,
@@ -306,8 +334,10 @@ extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config 
         d2[k] = (cfg->Cs * Delta) * (cfg->Cs * Delta);
     }
     for (int k = 1; k < nz; ++k) dzc[k] = zetac[k] - zetac[k - 1];
-    std::vector<double> rdzeta(nz), rdzc(nz + 1, 0.0);
+    std::vector<double> rdzeta(nz), rdzc(nz + 1, 0.0), delta(nz);
     for (int k = 0; k < nz; ++k) rdzeta[k] = 1.0 / dzeta[k];
+    for (int k = 0; k < nz; ++k) delta[k] = std::cbrt(grid->dx * grid->dy * dzeta[k]);
+    h->ph.ray_zt = zt;
     for (int k = 1; k < nz; ++k) rdzc[k] = 1.0 / dzc[k];
     cudaStream_t st = h->user;
     cudaError_t e;
@@ -329,6 +359,7 @@ extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config 
     CK(cudaMemcpyAsync(h->delta2, d2.data(), nz * sizeof(double), cudaMemcpyHostToDevice, st), "copy delta2");
     CK(cudaMemcpyAsync(h->rdzeta, rdzeta.data(), nz * sizeof(double), cudaMemcpyHostToDevice, st), "copy rdzeta");
     CK(cudaMemcpyAsync(h->rdzc, rdzc.data(), (nz + 1) * sizeof(double), cudaMemcpyHostToDevice, st), "copy rdzc");
+    CK(cudaMemcpyAsync(h->delta, delta.data(), nz * sizeof(double), cudaMemcpyHostToDevice, st), "copy delta");
     if (cfg->n_knots > 0) {
         CK(cudaMemcpyAsync(h->knz, cfg->knot_z, cfg->n_knots * sizeof(double), cudaMemcpyHostToDevice, st), "copy knots");
         CK(cudaMemcpyAsync(h->knt, cfg->knot_theta, cfg->n_knots * sizeof(double), cudaMemcpyHostToDevice, st), "copy knots");
@@ -428,13 +459,14 @@ static void enqueue_step(erf_handle *h, cudaStream_t s) {
     cudaMemcpyAsync(h->sn.v, h->st.v, bc, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(h->sn.w, h->st.w, bw, cudaMemcpyDeviceToDevice, s);
     if (h->tphi) cudaMemcpyAsync(h->snphi, h->tphi, bc, cudaMemcpyDeviceToDevice, s);
+    if (h->tke) cudaMemcpyAsync(h->sntke, h->tke, bc, cudaMemcpyDeviceToDevice, s);
     const double alpha[3] = {1.0 / 3.0, 0.5, 1.0};
     Prep pr{h->ux, h->vy, h->wz, h->mfx, h->mfy, h->rom};
     for (int stage = 0; stage < 3; ++stage) {
         launch_stage_begin(g, cf(h->sn), cf(h->st), h->x, h->pp, h->pi, h->th, h->Tp, h->Om, s);
         launch_slow_rhs(g, ph, cf(h->st), h->pp, h->th, pr, h->ux, h->vy, h->wz, h->mfx, h->mfy, h->rom, h->mu,
-                        h->flux, h->R, s);
-        if (h->tphi) {
+                        h->flux, h->R, s, h->tke, h->muh, h->tke_src);
+        if (h->msx) {
             cudaMemsetAsync(h->msx, 0, bc, s);
             cudaMemsetAsync(h->msy, 0, bc, s);
             cudaMemsetAsync(h->msz, 0, bw, s);
@@ -443,6 +475,9 @@ static void enqueue_step(erf_handle *h, cudaStream_t s) {
             if (h->tphi)
                 launch_tracer_stage(g, ph, cf(h->st), h->rom, h->snphi, h->msx, h->msy, h->msz, 1,
                                     alpha[stage] * c.dt, h->pp, h->flux, h->tphi, s);
+            if (h->tke)
+                launch_tracer_stage(g, ph, cf(h->st), h->rom, h->sntke, h->msx, h->msy, h->msz, 1,
+                                    alpha[stage] * c.dt, h->pp, h->flux, h->tke, s, h->tke_src, 1);
             launch_stage_nosub(g, h->st, cf(h->sn), cf(h->R), alpha[stage] * c.dt, s);
             launch_wall_bc(g, h->st.u, h->st.v, h->st.w, s);
             continue;
@@ -461,6 +496,9 @@ static void enqueue_step(erf_handle *h, cudaStream_t s) {
         if (h->tphi)
             launch_tracer_stage(g, ph, cf(h->st), h->rom, h->snphi, h->msx, h->msy, h->msz, nsub,
                                 alpha[stage] * c.dt, h->pp, h->flux, h->tphi, s);
+        if (h->tke)
+            launch_tracer_stage(g, ph, cf(h->st), h->rom, h->sntke, h->msx, h->msy, h->msz, nsub,
+                                alpha[stage] * c.dt, h->pp, h->flux, h->tke, s, h->tke_src, 1);
         launch_stage_end(g, h->st, cf(h->x), s);
     }
 }
@@ -569,6 +607,7 @@ static int state_fields(erf_handle *h, void **ptr, int *levels) {
         void *f[5] = {h->st.r, h->st.t, h->st.u, h->st.v, h->st.w};
         for (int q = 0; q < 5; ++q) { ptr[n] = f[q]; levels[n++] = q == 4 ? nz + 1 : nz; }
         if (h->tphi) { ptr[n] = h->tphi; levels[n++] = nz; }
+        if (h->tke) { ptr[n] = h->tke; levels[n++] = nz; }
     }
     return n;
 }
@@ -677,6 +716,7 @@ static double *field_dev(erf_handle *h, int f, long long &n) {
     case ERF_BASE_P: n = g.terrain ? g.nc : g.nz; return h->p0;
     case ERF_BASE_THETA: n = g.terrain ? g.nc : g.nz; return h->th0;
     case ERF_RHOPHI: return h->tphi;
+    case ERF_RHOTKE: return h->tke;
     }
     return nullptr;
 }
@@ -684,7 +724,8 @@ static double *field_dev(erf_handle *h, int f, long long &n) {
 extern "C" erf_status erf_set_state(erf_handle *h, int32_t field, const void *src, int32_t src_is_device,
                                     int32_t src_dtype) {
     if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
-    if ((field < ERF_RHO || field > ERF_RHOW) && !(field == ERF_RHOPHI && has_tracer(h)))
+    if ((field < ERF_RHO || field > ERF_RHOW) && !(field == ERF_RHOPHI && has_tracer(h)) &&
+        !(field == ERF_RHOTKE && h->tke))
         return fail(h, ERF_EINVAL, "field not settable");
     if (!src) return fail(h, ERF_EINVAL, "src is NULL");
     if (src_dtype != ERF_F64 && src_dtype != ERF_F32) return fail(h, ERF_EINVAL, "bad dtype");
@@ -788,7 +829,8 @@ extern "C" erf_status erf_set_tracer_initial(erf_handle *h, const double *phi0, 
 extern "C" erf_status erf_get_state(erf_handle *h, int32_t field, void *dst, int32_t dst_is_device,
                                     int32_t dst_dtype) {
     if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
-    if ((field < ERF_RHO || field > ERF_BASE_THETA) && !(field == ERF_RHOPHI && has_tracer(h)))
+    if ((field < ERF_RHO || field > ERF_BASE_THETA) && !(field == ERF_RHOPHI && has_tracer(h)) &&
+        !(field == ERF_RHOTKE && h->tke))
         return fail(h, ERF_EINVAL, "bad field");
     if (!dst) return fail(h, ERF_EINVAL, "dst is NULL");
     if (dst_dtype != ERF_F64 && dst_dtype != ERF_F32) return fail(h, ERF_EINVAL, "bad dtype");

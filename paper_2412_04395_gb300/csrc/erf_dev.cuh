@@ -32,6 +32,7 @@ struct Geo {
     const double *delta2;  // [nz]   (Cs * (dx dy dzeta)^(1/3))^2 for Smagorinsky
     const double *rdzeta;  // [nz]   1 / dzeta
     const double *rdzc;    // [nz+1] 1 / dzc (k = 1..nz-1)
+    const double *delta;   // [nz]   (dx dy dzeta)^(1/3), the filter width of the Deardorff closure
     // horizontal 2D terrain arrays [ny][nx]
     const double *hc;      // 4-node average of h (cell centre / w-face centre)
     const double *hxf;     // 2-node average of h along y (x-face)
@@ -55,7 +56,18 @@ struct Phys {
     double b1, b2;        // substep off-centring weights (1 - beta_s)/2, (1 + beta_s)/2, formed on the host
     int closure, surface, scal_adv;
     int mom3;   // 1: upwind-3 momentum interpolant instead of upwind-5
+    // Rayleigh damping (Sec. 3.7, App. D): rate ray_tau sin^2(pi/2 (z - ray_zd)/(ray_zt - ray_zd))
+    // above ray_zd; ray_fields bitmask 1 u, 2 v, 4 w, 8 theta (0 = off)
+    double ray_tau, ray_zd, ray_zt;
+    int ray_fields;
 };
+
+// Rayleigh damping rate at physical height z (0 below the damping layer)
+__device__ __forceinline__ double ray_rate(const Phys &ph, double z) {
+    if (!(z > ph.ray_zd)) return 0.0;
+    const double s = sin(0.5 * 3.141592653589793 * (z - ph.ray_zd) / (ph.ray_zt - ph.ray_zd));
+    return ph.ray_tau * (s * s);
+}
 
 // FP64 prognostic fields (cell, cell, x-face, y-face, w-face)
 struct F5 {

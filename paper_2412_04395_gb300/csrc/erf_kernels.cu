@@ -277,22 +277,54 @@ __device__ __forceinline__ void diag_strain(const Geo &g, const Vel &v, int i, i
 // mu = rho (Cs Delta)^2 sqrt(2 S_ij S_ij) (Smagorinsky-Lilly) or rho nu (constant); the
 // off-diagonal strains come from the edge arrays of k_sgs_edges (4-point averages to the centre)
 // eddy viscosity at cells and the deviatoric diagonal stresses -2 mu (S_ii - div/3) (t11, t22, t33)
+// Deardorff (closure 4, Sec. 2.3; Deardorff 1980 with the coefficients of Moeng 1984): from the
+// SGS energy e = max(rho e / rho, 0) and N^2 = (g/theta) dtheta/dz (centred, one-sided at the
+// walls), l = Delta or 0.76 sqrt(e)/N when shorter in stable air, K_m = 0.1 l sqrt(e),
+// K_h = (1 + 2 l/Delta) K_m; mu = rho K_m, muh = rho K_h and the local part of the energy source
+// rho (P + B - eps) with P = 2 K_m (S_ij S_ij - (S_kk)^2/3) (what the stress -2 mu (S - D) takes
+// from the resolved flow), B = -K_h N^2, eps = (0.19 + 0.51 l/Delta) e^(3/2)/l.  Flat grids.
+struct Tke {
+    const double *rtke, *th;
+    double *muh, *src;
+};
 __global__ void k_sgs_mu(Geo g, Phys ph, Vel v, const double *rho, const double *e12, const double *e13,
-                         const double *e23, double *mu, double *t11, double *t22, double *t33) {
+                         const double *e23, double *mu, double *t11, double *t22, double *t33, Tke tk) {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= g.nc) return;
     int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
     double m = 0.0;
     double s11, s22, s33;
     diag_strain(g, v, i, j, k, s11, s22, s33);
-    if (ph.closure == 2) {
+    if (ph.closure == 2 || ph.closure == 4) {
         double s12 = 0.25 * (cval(g, e12, i, j, k) + cval(g, e12, i + 1, j, k) + cval(g, e12, i, j + 1, k) + cval(g, e12, i + 1, j + 1, k));
         double s13 = 0.25 * (__ldg(e13 + cixw(g, i, j, k)) + __ldg(e13 + cixw(g, i + 1, j, k)) + __ldg(e13 + cixw(g, i, j, k + 1))
                            + __ldg(e13 + cixw(g, i + 1, j, k + 1)));
         double s23 = 0.25 * (__ldg(e23 + cixw(g, i, j, k)) + __ldg(e23 + cixw(g, i, j + 1, k)) + __ldg(e23 + cixw(g, i, j, k + 1))
                            + __ldg(e23 + cixw(g, i, j + 1, k + 1)));
         double SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.0 * (s12 * s12 + s13 * s13 + s23 * s23);
-        m = rho[c] * g.delta2[k] * sqrt(2.0 * SS);
+        if (ph.closure == 2) {
+            m = rho[c] * g.delta2[k] * sqrt(2.0 * SS);
+        } else {
+            const double r = rho[c];
+            const double e = fmax(__ldg(tk.rtke + c) / r, 0.0);
+            const double se = sqrt(e);
+            const double D = g.delta[k];
+            const int kl = k == 0 ? 0 : k - 1, ku = k == g.nz - 1 ? g.nz - 1 : k + 1;
+            double N2 = 0.0;
+            if (ku > kl)
+                N2 = ph.g / __ldg(tk.th + c) * (cval(g, tk.th, i, j, ku) - cval(g, tk.th, i, j, kl))
+                   / (g.zetac[ku] - g.zetac[kl]);
+            double l = D;
+            if (N2 > 0.0 && e > 0.0) l = fmin(D, 0.76 * se / sqrt(N2));
+            const double Km = 0.1 * l * se;
+            const double Kh = (1.0 + 2.0 * l / D) * Km;
+            const double dv3 = s11 + s22 + s33;
+            m = r * Km;
+            tk.muh[c] = r * Kh;
+            const double P = 2.0 * Km * (SS - dv3 * dv3 / 3.0);
+            const double eps = (0.19 + 0.51 * l / D) * e * se / l;
+            tk.src[c] = r * (P - Kh * N2 - eps);
+        }
     } else if (ph.closure == 1) {
         m = rho[c] * ph.nu;
     }
@@ -354,17 +386,19 @@ __device__ double most23(const Geo &g, const Phys &ph, const Vel &v, const doubl
 }
 // rho alpha dtheta/dn at the three face types (minus the diffusive flux); bottom face: the
 // upward MOST flux rho Q enters as -rho Q
-__device__ __forceinline__ double heat_x(const Geo &g, const Phys &ph, const double *mu, const double *th, int i, int j, int k) {
-    return 0.5 * (cval(g, mu, i - 1, j, k) + cval(g, mu, i, j, k)) * ph.rPr_t * (cval(g, th, i, j, k) - cval(g, th, i - 1, j, k)) * g.rdx;
+// The heat diffusivity rho alpha_theta is hs * hk at cells: mu / Pr_t (hk = mu, hs = 1/Pr_t), or
+// rho K_h of the Deardorff closure (hk = muh, hs = 1).
+__device__ __forceinline__ double heat_x(const Geo &g, double hs, const double *hk, const double *th, int i, int j, int k) {
+    return 0.5 * (cval(g, hk, i - 1, j, k) + cval(g, hk, i, j, k)) * hs * (cval(g, th, i, j, k) - cval(g, th, i - 1, j, k)) * g.rdx;
 }
-__device__ __forceinline__ double heat_y(const Geo &g, const Phys &ph, const double *mu, const double *th, int i, int j, int k) {
-    return 0.5 * (cval(g, mu, i, j - 1, k) + cval(g, mu, i, j, k)) * ph.rPr_t * (cval(g, th, i, j, k) - cval(g, th, i, j - 1, k)) * g.rdy;
+__device__ __forceinline__ double heat_y(const Geo &g, double hs, const double *hk, const double *th, int i, int j, int k) {
+    return 0.5 * (cval(g, hk, i, j - 1, k) + cval(g, hk, i, j, k)) * hs * (cval(g, th, i, j, k) - cval(g, th, i, j - 1, k)) * g.rdy;
 }
-__device__ __forceinline__ double heat_z(const Geo &g, const Phys &ph, const double *mu, const double *th, const double *rho,
-                                         int i, int j, int k, int visc) {
+__device__ __forceinline__ double heat_z(const Geo &g, const Phys &ph, double hs, const double *hk, const double *th,
+                                         const double *rho, int i, int j, int k, int visc) {
     if (k == 0) return ph.surface == 1 ? -cval(g, rho, i, j, 0) * ph.Qs : 0.0;   // upward flux rho Q
     if (k >= g.nz || !visc) return 0.0;
-    return 0.5 * (cval(g, mu, i, j, k - 1) + cval(g, mu, i, j, k)) * ph.rPr_t
+    return 0.5 * (cval(g, hk, i, j, k - 1) + cval(g, hk, i, j, k)) * hs
          * (cval(g, th, i, j, k) - cval(g, th, i, j, k - 1)) * g.rdzc[k];
 }
 
@@ -403,9 +437,9 @@ __global__ void k_sgs_tau(Geo g, Phys ph, Vel v, const double *mu, const double 
         t23[n] = -2.0 * my * t23[n];
     }
 }
-__global__ void k_sgs_div(Geo g, Phys ph, const double *mu, const double *t11, const double *t22, const double *t33,
-                          const double *rho, const double *th, int visc, const double *t12, const double *t13,
-                          const double *t23, F5 R) {
+__global__ void k_sgs_div(Geo g, Phys ph, const double *hk, double hs, const double *t11, const double *t22,
+                          const double *t33, const double *rho, const double *th, int visc, const double *t12,
+                          const double *t13, const double *t23, F5 R) {
     SGS_CELL3D_W();
     const long long nxy = g.nxy;
     if (k < g.nz) {
@@ -415,12 +449,12 @@ __global__ void k_sgs_div(Geo g, Phys ph, const double *mu, const double *t11, c
                + (__ldg(t12 + cixw(g, i, j + 1, k)) - __ldg(t12 + n)) * g.rdy;
             dv = (__ldg(t12 + cixw(g, i + 1, j, k)) - __ldg(t12 + n)) * g.rdx
                + (__ldg(t22 + n) - __ldg(t22 + cixw(g, i, j - 1, k))) * g.rdy;
-            hd = (heat_x(g, ph, mu, th, i + 1, j, k) - heat_x(g, ph, mu, th, i, j, k)) * g.rdx
-               + (heat_y(g, ph, mu, th, i, j + 1, k) - heat_y(g, ph, mu, th, i, j, k)) * g.rdy;
+            hd = (heat_x(g, hs, hk, th, i + 1, j, k) - heat_x(g, hs, hk, th, i, j, k)) * g.rdx
+               + (heat_y(g, hs, hk, th, i, j + 1, k) - heat_y(g, hs, hk, th, i, j, k)) * g.rdy;
         }
         du += (__ldg(t13 + n + nxy) - __ldg(t13 + n)) * g.rdzeta[k];
         dv += (__ldg(t23 + n + nxy) - __ldg(t23 + n)) * g.rdzeta[k];
-        hd += (heat_z(g, ph, mu, th, rho, i, j, k + 1, visc) - heat_z(g, ph, mu, th, rho, i, j, k, visc)) * rHc(g, i, j, k);
+        hd += (heat_z(g, ph, hs, hk, th, rho, i, j, k + 1, visc) - heat_z(g, ph, hs, hk, th, rho, i, j, k, visc)) * rHc(g, i, j, k);
         R.u[n] -= du;
         R.v[n] -= dv;
         R.t[n] += hd;
@@ -431,6 +465,28 @@ __global__ void k_sgs_div(Geo g, Phys ph, const double *mu, const double *t11, c
                   + (__ldg(t33 + n) - __ldg(t33 + n - nxy)) * rdzcw(g, i, j, k);
         R.w[n] -= dw;
     }
+}
+
+// transport of the SGS energy by the SGS eddies (Deardorff): div(2 mu grad e) added to the
+// source, face coefficient the mean of the two cells' 2 mu (mu = rho K_m), e = max(rho e / rho, 0),
+// no flux through the walls.  Flat grids.
+__global__ void k_tke_diff(Geo g, const double *mu, const double *rtke, const double *rho, double *src) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    auto ev = [&](int ii, int jj, int kk) {
+        const long long q = cixw(g, ii, jj, kk);
+        return fmax(__ldg(rtke + q) / __ldg(rho + q), 0.0);
+    };
+    const double m0 = __ldg(mu + c), e0 = ev(i, j, k);
+    const double fxm = (cval(g, mu, i - 1, j, k) + m0) * (e0 - ev(i - 1, j, k)) * g.rdx;
+    const double fxp = (m0 + cval(g, mu, i + 1, j, k)) * (ev(i + 1, j, k) - e0) * g.rdx;
+    const double fym = (cval(g, mu, i, j - 1, k) + m0) * (e0 - ev(i, j - 1, k)) * g.rdy;
+    const double fyp = (m0 + cval(g, mu, i, j + 1, k)) * (ev(i, j + 1, k) - e0) * g.rdy;
+    double fzm = 0.0, fzp = 0.0;
+    if (k > 0) fzm = (__ldg(mu + c - g.nxy) + m0) * (e0 - ev(i, j, k - 1)) * g.rdzc[k];
+    if (k < g.nz - 1) fzp = (m0 + __ldg(mu + c + g.nxy)) * (ev(i, j, k + 1) - e0) * g.rdzc[k + 1];
+    src[c] += (fxp - fxm) * g.rdx + (fyp - fym) * g.rdy + (fzp - fzm) * g.rdzeta[k];
 }
 
 // ------------------------------------------------------------------ slow tendencies
@@ -502,8 +558,8 @@ __global__ void k_flux_theta(Geo g, Phys ph, Prep pr, const double *th, double *
 }
 
 // continuity and potential temperature (Eq. con, Eq. theta): flux divergence / cell height
-__global__ void k_rhs_cells(Geo g, Prep pr, const double *fx, const double *fy, const double *fz, double *Rr,
-                            double *Rt) {
+__global__ void k_rhs_cells(Geo g, Phys ph, CF5 st, Prep pr, const double *fx, const double *fy, const double *fz,
+                            double *Rr, double *Rt) {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= g.nc) return;
     int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
@@ -511,6 +567,8 @@ __global__ void k_rhs_cells(Geo g, Prep pr, const double *fx, const double *fy, 
     double rH = rHc(g, i, j, k);
     Rr[c] = -((pr.mfx[cxp] - pr.mfx[c]) * g.rdx + (pr.mfy[cyp] - pr.mfy[c]) * g.rdy + (pr.rom[ckp] - pr.rom[c])) * rH;
     double r = -((fx[cxp] - fx[c]) * g.rdx + (fy[cyp] - fy[c]) * g.rdy + (fz[ckp] - fz[c])) * rH;
+    // Rayleigh damping of theta toward the base state theta0 (Sec. 3.7)
+    if (ph.ray_fields & 8) r -= ray_rate(ph, zc(g, i, j, k)) * (st.t[c] - st.r[c] * g.th0[bix(g, i, j, k)]);
     Rt[c] = r;
 }
 
@@ -609,6 +667,10 @@ __global__ void k_rhs_u(Geo g, Phys ph, CF5 st, const double *pp, const double *
         double rhx = 0.5 * (cval(g, st.r, i - 1, j, k) + cval(g, st.r, i, j, k));
         r += ph.f_cor * (rvx - rhx * ph.v_g);
     }
+    if (ph.ray_fields & 1) {   // Rayleigh damping toward u_g (Sec. 3.7)
+        const double z = 0.5 * (zc(g, i - 1, j, k) + zc(g, i, j, k));
+        r -= ray_rate(ph, z) * (st.u[c] - 0.5 * (cval(g, st.r, i - 1, j, k) + st.r[c]) * ph.u_g);
+    }
     Ru[c] = r;
 }
 
@@ -633,6 +695,10 @@ __global__ void k_rhs_v(Geo g, Phys ph, CF5 st, const double *pp, const double *
         double rhy = 0.5 * (cval(g, st.r, i, j - 1, k) + cval(g, st.r, i, j, k));
         r -= ph.f_cor * (rux - rhy * ph.u_g);
     }
+    if (ph.ray_fields & 2) {   // Rayleigh damping toward v_g (Sec. 3.7)
+        const double z = 0.5 * (zc(g, i, j - 1, k) + zc(g, i, j, k));
+        r -= ray_rate(ph, z) * (st.v[c] - 0.5 * (cval(g, st.r, i, j - 1, k) + st.r[c]) * ph.v_g);
+    }
     Rv[c] = r;
 }
 
@@ -651,6 +717,10 @@ __global__ void k_rhs_w(Geo g, Phys ph, CF5 st, const double *pp, const double *
     r -= (pp[c] - pp[cm]) * rdz;
     double b0 = g.rho0[bix(g, i, j, k - 1)], b1 = g.rho0[bix(g, i, j, k)];
     r += 0.5 * (-ph.g * (st.r[cm] - b0) - ph.g * (st.r[c] - b1));
+    if (ph.ray_fields & 4) {   // Rayleigh damping toward w = 0 at the w-face height (Sec. 3.7)
+        const double zw = g.zetac[k - 1] + 0.5 * g.dzeta[k - 1] + (g.terrain ? g.s[k] * g.hc[ij2(g, i, j)] : 0.0);
+        r -= ray_rate(ph, zw) * st.w[n];
+    }
     Rw[n] = r;
 }
 
@@ -916,15 +986,20 @@ __global__ void k_tracer_flux(Geo g, Phys ph, const double *ru, const double *rv
     for (int m = 0; m < 6; ++m) q[m] = cval(g, phi, i, j, k - 3 + m);
     fz[n] = mz * scal_face_d(q, upwind_left(mz), ph.scal_adv);
 }
+// rho q^(s) = rho q^n + alpha dt (-div F / H + src) for a transported scalar; src (may be null)
+// is the scalar's own source at the stage state; clip = 1 keeps rho q >= 0 (the SGS energy)
 __global__ void k_tracer_update(Geo g, const double *snphi, const double *fx, const double *fy, const double *fz,
-                                double adt, double *rphi) {
+                                const double *src, int clip, double adt, double *rphi) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
     const long long c = ((long long)k * g.ny + j) * g.nx + i;
     double div = (fx[cixw(g, i + 1, j, k)] - fx[c]) * g.rdx + (fy[cixw(g, i, j + 1, k)] - fy[c]) * g.rdy
                + (fz[c + g.nxy] - fz[c]);
-    rphi[c] = snphi[c] + adt * (-div * rHc(g, i, j, k));
+    double t = -div * rHc(g, i, j, k);
+    if (src) t += src[c];
+    const double v = snphi[c] + adt * t;
+    rphi[c] = (clip && v < 0.0) ? 0.0 : v;
 }
 __global__ void k_tracer_init(Geo g, const double *rho, const double *phi0, double *rphi) {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1089,14 +1164,14 @@ void launch_stage_begin(const Geo &g, CF5 sn, CF5 st, F5 x, double *pp, double *
 }
 void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, double *pp, const double *th, Prep pr,
                      double *ux, double *vy, double *wz, double *mfx, double *mfy, double *rom, double *mu,
-                     double *flux, F5 R, cudaStream_t s) {
+                     double *flux, F5 R, cudaStream_t s, const double *rtke, double *muh, double *tke_src) {
     LAUNCH("prep", s, k_prep<<<nblk(g.nw, BS), BS, 0, s>>>(g, st, ux, vy, wz, mfx, mfy, rom));
-    const int visc = (ph.closure == 1 || ph.closure == 2) ? 1 : 0;
+    const int visc = (ph.closure == 1 || ph.closure == 2 || ph.closure == 4) ? 1 : 0;
     const int sgs = (visc || ph.surface == 1) ? 1 : 0;
     // advection, pressure gradient, buoyancy and Coriolis (the subgrid terms follow below)
     double *fx = flux, *fy = flux + g.nc, *fz = flux + 2 * g.nc;
     LAUNCH("flux_theta", s, k_flux_theta<<<nblk(g.nw, BS), BS, 0, s>>>(g, ph, pr, th, fx, fy, fz));
-    LAUNCH("rhs_cells", s, k_rhs_cells<<<nblk(g.nc, BS), BS, 0, s>>>(g, pr, fx, fy, fz, R.r, R.t));
+    LAUNCH("rhs_cells", s, k_rhs_cells<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, st, pr, fx, fy, fz, R.r, R.t));
     // momentum: fluxes of each component into the shared buffer, then its divergence
     const dim3 g3w((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)(g.nz + 1));
     double *ax = flux, *ay = flux + g.nw, *az = flux + 2 * g.nw;
@@ -1116,12 +1191,19 @@ void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, double *pp, const dou
         // the pressure and the mass fluxes are no longer needed in this stage's slow pass: they
         // take the diagonal stresses
         double *t11 = pp, *t22 = mfx, *t33 = mfy;
+        Tke tk{rtke, th, muh, tke_src};
         if (visc) {
             LAUNCH("sgs_edges", s, k_sgs_edges<<<g3w, 128, 0, s>>>(g, v, e12, e13, e23));
-            LAUNCH("sgs_mu", s, k_sgs_mu<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, v, st.r, e12, e13, e23, mu, t11, t22, t33));
+            LAUNCH("sgs_mu", s, k_sgs_mu<<<nblk(g.nc, BS), BS, 0, s>>>(g, ph, v, st.r, e12, e13, e23, mu, t11, t22, t33,
+                                                                       tk));
+            if (ph.closure == 4)
+                LAUNCH("tke_diff", s, k_tke_diff<<<nblk(g.nc, BS), BS, 0, s>>>(g, mu, rtke, st.r, tke_src));
         }
         LAUNCH("sgs_tau", s, k_sgs_tau<<<g3w, 128, 0, s>>>(g, ph, v, mu, st.r, th, visc, e12, e13, e23));
-        LAUNCH("sgs_div", s, k_sgs_div<<<g3w, 128, 0, s>>>(g, ph, mu, t11, t22, t33, st.r, th, visc, e12, e13, e23, R));
+        const double *hk = ph.closure == 4 ? muh : mu;
+        const double hs = ph.closure == 4 ? 1.0 : ph.rPr_t;
+        LAUNCH("sgs_div", s, k_sgs_div<<<g3w, 128, 0, s>>>(g, ph, hk, hs, t11, t22, t33, st.r, th, visc, e12, e13, e23,
+                                                           R));
     }
 }
 void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const double *rt, const double *pi,
@@ -1152,14 +1234,15 @@ void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *PX, cons
 }
 void launch_tracer_stage(const Geo &g, const Phys &ph, CF5 st, const double *rom, const double *snphi,
                          const double *msx, const double *msy, const double *msz, int nsub, double adt,
-                         double *phi, double *flux, double *rphi, cudaStream_t s) {
+                         double *phi, double *flux, double *rphi, cudaStream_t s, const double *src, int clip) {
     const dim3 g3w((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)(g.nz + 1));
     const dim3 g3c((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)g.nz);
     double *fx = flux, *fy = flux + g.nw, *fz = flux + 2 * g.nw;
     LAUNCH("tracer_phi", s, k_tracer_phi<<<nblk(g.nc, BS), BS, 0, s>>>(g, rphi, st.r, phi));
     LAUNCH("tracer_flux", s, k_tracer_flux<<<g3w, 128, 0, s>>>(g, ph, st.u, st.v, rom, phi, msx, msy, msz,
                                                                 1.0 / nsub, fx, fy, fz));
-    LAUNCH("tracer_update", s, k_tracer_update<<<g3c, 128, 0, s>>>(g, snphi, fx, fy, fz, adt, rphi));
+    LAUNCH(src ? "tke_update" : "tracer_update", s,
+           k_tracer_update<<<g3c, 128, 0, s>>>(g, snphi, fx, fy, fz, src, clip, adt, rphi));
 }
 void launch_tracer_init(const Geo &g, const double *rho, const double *phi0, double *rphi, cudaStream_t s) {
     LAUNCH("tracer_init", s, k_tracer_init<<<nblk(g.nc, BS), BS, 0, s>>>(g, rho, phi0, rphi));

@@ -19,7 +19,8 @@ void launch_stage_begin(const Geo &g, CF5 sn, CF5 st, F5 x, double *pp, double *
                         double *Om, cudaStream_t s);
 void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, double *pp, const double *th, Prep pr,
                      double *ux, double *vy, double *wz, double *mfx, double *mfy, double *rom, double *mu,
-                     double *flux, F5 R, cudaStream_t s);
+                     double *flux, F5 R, cudaStream_t s, const double *rtke = nullptr, double *muh = nullptr,
+                     double *tke_src = nullptr);
 void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const double *rt, const double *pi,
                       const double *th, double dtau, Tri tr, double *TX, double *TY, double *PX, double *PY,
                       double *THW, cudaStream_t s);
@@ -28,7 +29,8 @@ void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *PX, cons
                     double *Ash, double *msx, double *msy, double *msz, double dtau, cudaStream_t s);
 void launch_tracer_stage(const Geo &g, const Phys &ph, CF5 st, const double *rom, const double *snphi,
                          const double *msx, const double *msy, const double *msz, int nsub, double adt,
-                         double *phi, double *flux, double *rphi, cudaStream_t s);
+                         double *phi, double *flux, double *rphi, cudaStream_t s, const double *src = nullptr,
+                         int clip = 0);
 void launch_tracer_init(const Geo &g, const double *rho, const double *phi0, double *rphi, cudaStream_t s);
 void launch_stage_end(const Geo &g, F5 st, CF5 x, cudaStream_t s);
 void launch_stage_nosub(const Geo &g, F5 st, CF5 sn, CF5 R, double adt, cudaStream_t s);

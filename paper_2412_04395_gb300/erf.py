@@ -18,7 +18,7 @@ ERF_OK, ERF_EINVAL, ERF_ENOSPACE, ERF_ECUDA, ERF_ENONFINITE, ERF_ESTATE, ERF_EUN
 STATUS_NAMES = {0: "ERF_OK", -1: "ERF_EINVAL", -2: "ERF_ENOSPACE", -3: "ERF_ECUDA", -4: "ERF_ENONFINITE",
                 -5: "ERF_ESTATE", -6: "ERF_EUNSUPPORTED"}
 FIELDS = {"rho": 0, "rhotheta": 1, "rhou": 2, "rhov": 3, "rhow": 4,
-          "base_rho": 5, "base_p": 6, "base_theta": 7, "rhophi": 8}
+          "base_rho": 5, "base_p": 6, "base_theta": 7, "rhophi": 8, "rhotke": 9}
 ERF_F64, ERF_F32 = 0, 1
 ERF_OPT_TMA_STENCILS = 1
 ERF_OPT_COLUMN_FUSION = 2
@@ -56,7 +56,8 @@ class Config(C.Structure):
                 ("surface", C.c_int32), ("z0", C.c_double), ("sfc_theta_flux", C.c_double),
                 ("theta_s", C.c_double), ("brunt_N", C.c_double), ("p_s", C.c_double),
                 ("n_knots", C.c_int32), ("knot_z", C.POINTER(C.c_double)),
-                ("knot_theta", C.POINTER(C.c_double)), ("tracer", C.c_int32), ("mom_adv", C.c_int32)]
+                ("knot_theta", C.POINTER(C.c_double)), ("tracer", C.c_int32), ("mom_adv", C.c_int32),
+                ("ray_tau", C.c_double), ("ray_zd", C.c_double), ("ray_fields", C.c_int32)]
 
 
 class Diag(C.Structure):
@@ -163,7 +164,8 @@ def make_structs(wl):
                Pr_t=wl.Pr_t, nu=wl.nu, precision=wl.precision, gravity=wl.gravity, f_cor=wl.f_cor,
                u_g=wl.u_g, v_g=wl.v_g, surface=wl.surface, z0=wl.z0, sfc_theta_flux=wl.sfc_theta_flux,
                theta_s=wl.theta_s, brunt_N=wl.brunt_N, p_s=wl.p_s, n_knots=nk, knot_z=_dp(kz),
-               knot_theta=_dp(kt), tracer=getattr(wl, "tracer", 0), mom_adv=wl.mom_adv)
+               knot_theta=_dp(kt), tracer=getattr(wl, "tracer", 0), mom_adv=wl.mom_adv,
+               ray_tau=wl.ray_tau, ray_zd=wl.ray_zd, ray_fields=wl.ray_fields)
     return g, c, keep
 
 
