@@ -5,7 +5,8 @@ Test infrastructure only: the tests, ``__graft_entry__.smoke()`` and the CPU-bas
 library in ``paper_2412_04395_gb300``.
 """
 from .erf_oracle import (Oracle, OracleConfig, build_oracle, lib_path, interp, weno5,
-                         thomas, eos, hse_column, ustar, psi_m, set_threads)
+                         thomas, eos, hse_column, ustar, psi_m, set_threads, qvs, rain_speed,
+                         rain_evap)
 
 __all__ = ["Oracle", "OracleConfig", "build_oracle", "lib_path", "interp", "weno5", "thomas",
-           "eos", "hse_column", "ustar", "psi_m", "set_threads"]
+           "eos", "hse_column", "ustar", "psi_m", "set_threads", "qvs", "rain_speed", "rain_evap"]

@@ -41,6 +41,11 @@
 #define ORC_CV (ORC_CP - ORC_RD)
 #define ORC_GAMMA (ORC_CP / ORC_CV)
 #define ORC_KAPPA 0.4
+/* moist air (Sec. 2.1, 2.4; not printed, readings): water-vapour gas constant, latent heat of
+ * vaporisation, liquid-water density */
+#define ORC_RV 461.5
+#define ORC_LV 2.5e6
+#define ORC_RHOW 1000.0
 
 typedef struct {
     int32_t nx, ny, nz;
@@ -66,6 +71,13 @@ typedef struct {
      * 4 = w, 8 = theta (0 = off) */
     double ray_tau, ray_zd;
     int32_t ray_fields;
+    /* moisture (Sec. 2.1 Eqs. nonprecip/precip, Sec. 2.4): 1 carries rho q_v, rho q_c, rho q_r with
+     * the moist EOS and momentum terms, and applies Kessler microphysics after every RK3 step */
+    int32_t moist;
+    /* lateral relaxation zones (open x boundaries, Sec. 3.8 / Table D): every prognostic field
+     * relaxes toward its initial value at rate relax_tau sin^2(pi/2 (1 - d/relax_width)) within
+     * relax_width of an x-edge (d the distance to it); relax_tau = 0: off */
+    double relax_tau, relax_width;
 } orc_cfg;
 
 typedef struct {
@@ -100,6 +112,12 @@ typedef struct {
      * copy, the stage's source rho (P + B - eps) + div(2 mu grad e) at cells, and the heat
      * diffusivity rho K_h at cells */
     double *rtke, *sn_tke, *tke_src, *muh;
+    /* moisture: rho q_v, rho q_c, rho q_r (per unit dry mass), their S^n copies, the scalar
+     * diffusion sources, the base-state vapour q_v0 at cells, and the accumulated surface
+     * precipitation (metres of liquid water) per column */
+    double *rq[3], *sn_q[3], *q_src[3], *qv0, *precip;
+    /* relaxation zones: the reference (initial) state of every prognostic field */
+    double *ref[5], *ref_q[3];
     /* learned closure (closure 3): a model evaluated on each stage state; it writes nine planes
      * of ncell values at cell centres, density-weighted: rho t11, rho t22, rho t33, rho t12,
      * rho t13, rho t23, rho h1, rho h2, rho h3 (kinematic stress [m^2/s^2] and SGS heat flux
@@ -202,6 +220,16 @@ void orc_eos(double rt, double *p, double *pi) {
 static double rho_of(double p, double theta) {
     return (ORC_P00 / (ORC_RD * theta)) * pow(p / ORC_P00, 1.0 / ORC_GAMMA);
 }
+/* the moist EOS of Sec. 2.1: p = P00 (R_d rho_d theta_d (1 + (R_v/R_d) q_v) / P00)^gamma
+ * (rt = rho_d theta_d; q_v = 0 gives the dry EOS exactly) */
+static void eos_q(double rt, double qv, double *p, double *pi) {
+    orc_eos(rt * (1.0 + (ORC_RV / ORC_RD) * qv), p, pi);
+}
+/* total (moist) density rho_d (1 + q_v) of saturated-or-not air at pressure p, dry potential
+ * temperature theta and vapour q_v (no condensate), from the moist EOS */
+static double rho_m_of(double p, double theta, double qv) {
+    return rho_of(p, theta * (1.0 + (ORC_RV / ORC_RD) * qv)) * (1.0 + qv);
+}
 
 /* ------------------------------------------------------------------ tridiagonal (Thomas) */
 /* rows r = 0..n-1: a[r] x[r-1] + b[r] x[r] + c[r] x[r+1] = d[r]  (a[0], c[n-1] ignored) */
@@ -239,29 +267,48 @@ static double theta0_at(const orc *o, double z) {
     return o->c.theta_s * exp(o->c.brunt_N * o->c.brunt_N * z / g);
 }
 
+/* base-state water vapour q_v0(z): piecewise-linear sounding, constant beyond the ends (0 without one) */
+static double qv0_at(int n, const double *kz, const double *kq, double z) {
+    if (n <= 0) return 0.0;
+    if (z <= kz[0]) return kq[0];
+    for (int m = 1; m < n; ++m)
+        if (z <= kz[m]) {
+            double t = (z - kz[m - 1]) / (kz[m] - kz[m - 1]);
+            return kq[m - 1] + t * (kq[m] - kq[m - 1]);
+        }
+    return kq[n - 1];
+}
+
 /* HSE column by Newton-Raphson (Sec. 3.8): from p_s at z = 0, trapezoidal hydrostatic steps
  *   p_k = p_{k-1} - g (z_k - z_{k-1}) (rho_{k-1} + rho_k)/2,  rho_k = EOS^-1(p_k, theta0(z_k)),
  * solved for p_k; z are the column's cell-centre heights.  p0 is then re-evaluated from the
  * EOS of rho0 theta0 so that an undisturbed state has p' = 0 exactly. */
-void orc_hse_column(int nz, const double *zcol, const double *thcol, double p_s, double th_surf,
-                    double g, double *rho0, double *p0out) {
-    double p_prev = p_s, rho_prev = rho_of(p_s, th_surf), z_prev = 0.0;
+/* The same column with moisture (Sec. 3.8: the moist background state matches the input
+ * profiles of theta and q_v at every height): the hydrostatic density is the total density
+ * rho_d (1 + q_v0) from the moist EOS; qcol = NULL is the dry column. */
+static void hse_column_q(int nz, const double *zcol, const double *thcol, const double *qcol, double p_s,
+                         double th_surf, double q_surf, double g, double *rho0, double *p0out) {
+    double p_prev = p_s, rho_prev = rho_m_of(p_s, th_surf, q_surf), z_prev = 0.0;
     for (int k = 0; k < nz; ++k) {
-        double dz = zcol[k] - z_prev, th = thcol[k];
+        double dz = zcol[k] - z_prev, th = thcol[k], q = qcol ? qcol[k] : 0.0;
         double p = p_prev - g * dz * rho_prev;
         for (int it = 0; it < 50; ++it) {
-            double r = rho_of(p, th);
+            double r = rho_m_of(p, th, q);
             double f = p - p_prev + 0.5 * g * dz * (rho_prev + r);
             double df = 1.0 + 0.5 * g * dz * r / (ORC_GAMMA * p);
             double dp = -f / df;
             p += dp;
             if (fabs(dp) <= 1.0e-14 * fabs(p)) break;
         }
-        double r = rho_of(p, th);
+        double r = rho_m_of(p, th, q);
         rho0[k] = r;
         p0out[k] = p;
         p_prev = p; rho_prev = r; z_prev = zcol[k];
     }
+}
+void orc_hse_column(int nz, const double *zcol, const double *thcol, double p_s, double th_surf,
+                    double g, double *rho0, double *p0out) {
+    hse_column_q(nz, zcol, thcol, NULL, p_s, th_surf, 0.0, g, rho0, p0out);
 }
 
 /* ------------------------------------------------------------------ setup */
@@ -269,8 +316,15 @@ static double *dalloc(size_t n) { return (double *)calloc(n ? n : 1, sizeof(doub
 
 void orc_destroy(orc *o);
 
+orc *orc_create2(const orc_cfg *cfg, const double *zeta, const double *hnode, int n_knots, const double *knot_z,
+                 const double *knot_th, int n_qknots, const double *qknot_z, const double *qknot_v);
 orc *orc_create(const orc_cfg *cfg, const double *zeta, const double *hnode,
                 int n_knots, const double *knot_z, const double *knot_th) {
+    return orc_create2(cfg, zeta, hnode, n_knots, knot_z, knot_th, 0, NULL, NULL);
+}
+/* with a base-state water-vapour sounding (moist configurations) */
+orc *orc_create2(const orc_cfg *cfg, const double *zeta, const double *hnode, int n_knots, const double *knot_z,
+                 const double *knot_th, int n_qknots, const double *qknot_z, const double *qknot_v) {
     orc *o = (orc *)calloc(1, sizeof(orc));
     o->c = *cfg;
     int nx = o->nx = cfg->nx, ny = o->ny = cfg->ny, nz = o->nz = cfg->nz;
@@ -308,6 +362,11 @@ orc *orc_create(const orc_cfg *cfg, const double *zeta, const double *hnode,
     o->ux = dalloc(NC); o->vy = dalloc(NC); o->wz = dalloc(NW); o->mu = dalloc(NC);
     o->rphi = dalloc(NC); o->sn_phi = dalloc(NC); o->msx = dalloc(NC); o->msy = dalloc(NC); o->msz = dalloc(NW);
     o->rtke = dalloc(NC); o->sn_tke = dalloc(NC); o->tke_src = dalloc(NC); o->muh = dalloc(NC);
+    for (int q = 0; q < 3; ++q) {
+        o->rq[q] = dalloc(NC); o->sn_q[q] = dalloc(NC); o->q_src[q] = dalloc(NC); o->ref_q[q] = dalloc(NC);
+    }
+    for (int f = 0; f < 5; ++f) o->ref[f] = dalloc(f == F_RW ? NW : NC);
+    o->qv0 = dalloc(NC); o->precip = dalloc((size_t)nx * ny);
 
     /* node heights, App. B + canonical smoothing z = zeta + (1 - zeta/z_t)^beta h (Sec. 3.4) */
     #pragma omp parallel for
@@ -355,24 +414,32 @@ orc *orc_create(const orc_cfg *cfg, const double *zeta, const double *hnode,
                     + 8.0 * (o->zw[IX(o, i, j + 1, k)] - o->zw[IX(o, i, j - 1, k)])) / (12.0 * cfg->dy);
             }
     /* base state per column (HSE in physical height, Sec. 2 and Sec. 3.8) */
-    double *zcol = dalloc(nz), *thcol = dalloc(nz), *rcol = dalloc(nz), *pcol = dalloc(nz);
+    double *zcol = dalloc(nz), *thcol = dalloc(nz), *rcol = dalloc(nz), *pcol = dalloc(nz), *qcol = dalloc(nz);
+    int moist = cfg->moist && n_qknots > 0;
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             for (int k = 0; k < nz; ++k) {
                 zcol[k] = o->zc[IX(o, i, j, k)];
                 thcol[k] = theta0_at(o, zcol[k]);
+                qcol[k] = moist ? qv0_at(n_qknots, qknot_z, qknot_v, zcol[k]) : 0.0;
             }
-            orc_hse_column(nz, zcol, thcol, cfg->p_s, theta0_at(o, 0.0), cfg->gravity, rcol, pcol);
+            if (moist)
+                hse_column_q(nz, zcol, thcol, qcol, cfg->p_s, theta0_at(o, 0.0),
+                             qv0_at(n_qknots, qknot_z, qknot_v, 0.0), cfg->gravity, rcol, pcol);
+            else
+                orc_hse_column(nz, zcol, thcol, cfg->p_s, theta0_at(o, 0.0), cfg->gravity, rcol, pcol);
             for (int k = 0; k < nz; ++k) {
                 size_t c = IX(o, i, j, k);
                 double pr, pie;
-                o->rho0[c] = rcol[k];
+                o->rho0[c] = rcol[k];                     /* total density (moist base states) */
                 o->th0[c] = thcol[k];
-                orc_eos(rcol[k] * thcol[k], &pr, &pie);
+                o->qv0[c] = qcol[k];
+                /* p0 from the EOS of the base dry density rho0 / (1 + q_v0), so that p' = 0 exactly */
+                eos_q(rcol[k] / (1.0 + qcol[k]) * thcol[k], qcol[k], &pr, &pie);
                 o->p0[c] = pr;
             }
         }
-    free(zcol); free(thcol); free(rcol); free(pcol);
+    free(zcol); free(thcol); free(rcol); free(pcol); free(qcol);
     return o;
 }
 
@@ -385,7 +452,9 @@ void orc_destroy(orc *o) {
                        &o->rom, &o->ux, &o->vy, &o->wz, &o->mu, &o->rphi, &o->sn_phi, &o->msx,
                        &o->msy, &o->msz, &o->sgs_planes, &o->rtke, &o->sn_tke, &o->tke_src, &o->muh};
     for (size_t n = 0; n < sizeof(ptrs) / sizeof(ptrs[0]); ++n) free(*ptrs[n]);
-    for (int f = 0; f < 5; ++f) { free(o->sn[f]); free(o->R[f]); free(o->X[f]); }
+    for (int f = 0; f < 5; ++f) { free(o->sn[f]); free(o->R[f]); free(o->X[f]); free(o->ref[f]); }
+    for (int q = 0; q < 3; ++q) { free(o->rq[q]); free(o->sn_q[q]); free(o->q_src[q]); free(o->ref_q[q]); }
+    free(o->qv0); free(o->precip);
     free(o);
 }
 
@@ -414,10 +483,12 @@ static void apply_wall_bc(orc *o, double *rw, const double *ru, const double *rv
 
 /* ------------------------------------------------------------------ stage EOS pass */
 static void eos_pass(orc *o, const double *rho, const double *rt) {
+    const int moist = o->c.moist;
 #pragma omp parallel for
     for (long c = 0; c < (long)o->ncell; ++c) {
         double p, pie;
-        orc_eos(rt[c], &p, &pie);
+        if (moist) eos_q(rt[c], o->rq[0][c] / rho[c], &p, &pie);   /* q_v of the stage state */
+        else orc_eos(rt[c], &p, &pie);
         o->pp[c] = p - o->p0[c];
         o->pi[c] = pie;
         o->th[c] = rt[c] / rho[c];
@@ -469,6 +540,18 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
     memset(Rw, 0, sizeof(double) * o->nw);
 
     eos_pass(o, rho, rt);
+    if (C->moist)
+        for (int q = 0; q < 3; ++q) memset(o->q_src[q], 0, sizeof(double) * o->ncell);
+    /* moisture (Eq. mom): pressure gradient and buoyancy scaled by 1 / (1 + q_v + q_c), buoyancy of the
+     * total density rho_m = rho_d (1 + q_v + q_c + q_r); qvc = q_v + q_c, qt = rho_m - rho_d at cells */
+    double *qvc = NULL, *qtm = NULL;
+    if (C->moist) {
+        qvc = dalloc(o->ncell); qtm = dalloc(o->ncell);
+        for (size_t c = 0; c < o->ncell; ++c) {
+            qvc[c] = (o->rq[0][c] + o->rq[1][c]) / rho[c];
+            qtm[c] = o->rq[0][c] + o->rq[1][c] + o->rq[2][c];
+        }
+    }
     /* mass fluxes per unit length (Sec. 3.6: normal momentum at the face) and rho*Omega */
     #pragma omp parallel for
     for (int k = 0; k < nz; ++k)
@@ -654,6 +737,10 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                     px -= 0.5 * o->hxi_x[c] * (d[0] + d[1]);
                     py -= 0.5 * o->heta_y[c] * (d[2] + d[3]);
                 }
+                if (qvc) {
+                    px /= 1.0 + 0.5 * (qvc[IX(o, i - 1, j, k)] + qvc[c]);
+                    py /= 1.0 + 0.5 * (qvc[IX(o, i, j - 1, k)] + qvc[c]);
+                }
                 Ru[c] -= px;
                 Rv[c] -= py;
             }
@@ -663,8 +750,13 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
             for (int i = 0; i < nx; ++i) {
                 size_t w = IX(o, i, j, k), c = IX(o, i, j, k), cm = IX(o, i, j, k - 1);
                 double pz = (o->pp[c] - o->pp[cm]) / (o->zc[c] - o->zc[cm]);
-                double B = 0.5 * (-g * (rho[cm] - o->rho0[cm]) - g * (rho[c] - o->rho0[c]));
-                Rw[w] += -pz + B;
+                if (qtm) {
+                    double B = 0.5 * (-g * (rho[cm] + qtm[cm] - o->rho0[cm]) - g * (rho[c] + qtm[c] - o->rho0[c]));
+                    Rw[w] += (-pz + B) / (1.0 + 0.5 * (qvc[cm] + qvc[c]));
+                } else {
+                    double B = 0.5 * (-g * (rho[cm] - o->rho0[cm]) - g * (rho[c] - o->rho0[c]));
+                    Rw[w] += -pz + B;
+                }
             }
 
     /* --- Coriolis and geostrophic forcing on an f-plane (Sec. 3.7) */
@@ -884,6 +976,40 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                     Rw[w] -= (t13[IX(o, i + 1, j, k)] - t13[w]) / dx + (t23[IX(o, i, j + 1, k)] - t23[w]) / dy
                            + (t33[IX(o, i, j, k)] - t33[IX(o, i, j, k - 1)]) / dzc;
                 }
+        if (C->moist) {
+            /* moisture diffusion (Eq. nonprecip, precip): div(rho alpha_q grad q) with alpha_q the
+             * heat diffusivity of the closure (mu / Pr_t, or rho K_h), no flux through the walls */
+            for (int q = 0; q < 3; ++q) {
+                double *qq = dalloc(o->ncell);
+                for (size_t c = 0; c < o->ncell; ++c) qq[c] = o->rq[q][c] / rho[c];
+                #pragma omp parallel for
+                for (int k = 0; k < nz; ++k)
+                    for (int j = 0; j < ny; ++j)
+                        for (int i = 0; i < nx; ++i) {
+                            size_t c = IX(o, i, j, k);
+                            if (!visc) { o->q_src[q][c] = 0.0; continue; }
+                            const double *hk = (C->closure == 4) ? o->muh : o->mu;
+                            double hs = (C->closure == 4) ? 1.0 : 1.0 / C->Pr_t;
+                            size_t cxm = IX(o, i - 1, j, k), cxp = IX(o, i + 1, j, k);
+                            size_t cym = IX(o, i, j - 1, k), cyp = IX(o, i, j + 1, k);
+                            double fxm = 0.5 * (hk[cxm] + hk[c]) * hs * (qq[c] - qq[cxm]) / dx;
+                            double fxp = 0.5 * (hk[c] + hk[cxp]) * hs * (qq[cxp] - qq[c]) / dx;
+                            double fym = 0.5 * (hk[cym] + hk[c]) * hs * (qq[c] - qq[cym]) / dy;
+                            double fyp = 0.5 * (hk[c] + hk[cyp]) * hs * (qq[cyp] - qq[c]) / dy;
+                            double fzm = 0.0, fzp = 0.0;
+                            if (k > 0) {
+                                size_t cm = IX(o, i, j, k - 1);
+                                fzm = 0.5 * (hk[cm] + hk[c]) * hs * (qq[c] - qq[cm]) / (o->zc[c] - o->zc[cm]);
+                            }
+                            if (k < nz - 1) {
+                                size_t cp = IX(o, i, j, k + 1);
+                                fzp = 0.5 * (hk[c] + hk[cp]) * hs * (qq[cp] - qq[c]) / (o->zc[cp] - o->zc[c]);
+                            }
+                            o->q_src[q][c] = (fxp - fxm) / dx + (fyp - fym) / dy + (fzp - fzm) / o->Hc[c];
+                        }
+                free(qq);
+            }
+        }
         if (C->closure == 4) {
             /* transport of e by the SGS eddies: div(rho 2 K_m grad e), face coefficient the mean
              * of the two cells' 2 mu; no flux through the walls */
@@ -954,6 +1080,41 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
                     }
                 }
     }
+
+    /* --- lateral relaxation zones (open x boundaries; Sec. 3.8 nudging toward boundary data, here
+     * the initial state): -tau_r(d) (S - S_ref), tau_r = relax_tau sin^2(pi/2 (1 - d/W)) for d < W,
+     * d the distance of the point from the nearer x-edge (cells at x_c, x-faces at x = i dx) */
+    if (C->relax_tau > 0.0 && C->relax_width > 0.0) {
+        const double Lx = nx * dx, W = C->relax_width;
+        #pragma omp parallel for
+        for (int k = 0; k <= nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    double xc = (i + 0.5) * dx, xf = i * dx;
+                    double dc = xc < Lx - xc ? xc : Lx - xc, df = xf < Lx - xf ? xf : Lx - xf;
+                    double tc = dc < W ? C->relax_tau * pow(sin(0.5 * M_PI * (1.0 - dc / W)), 2.0) : 0.0;
+                    double tf = df < W ? C->relax_tau * pow(sin(0.5 * M_PI * (1.0 - df / W)), 2.0) : 0.0;
+                    size_t c = IX(o, i, j, k);
+                    if (k < nz) {
+                        Rr[c] -= tc * (rho[c] - o->ref[F_RHO][c]);
+                        Rt[c] -= tc * (rt[c] - o->ref[F_RT][c]);
+                        Ru[c] -= tf * (ru[c] - o->ref[F_RU][c]);
+                        Rv[c] -= tc * (rv[c] - o->ref[F_RV][c]);
+                        if (C->moist)
+                            for (int q = 0; q < 3; ++q) o->q_src[q][c] -= tc * (o->rq[q][c] - o->ref_q[q][c]);
+                    }
+                    if (k >= 1 && k < nz) Rw[c] -= tc * (rw[c] - o->ref[F_RW][c]);
+                }
+    }
+    free(qvc); free(qtm);
+}
+
+/* stage-t mixing ratios q_v + q_c and q_v + q_c + q_r at a cell */
+static inline double qvc_at(const orc *o, const double *rho_t, size_t c) {
+    return (o->rq[0][c] + o->rq[1][c]) / rho_t[c];
+}
+static inline double qt_at(const orc *o, const double *rho_t, size_t c) {
+    return (o->rq[0][c] + o->rq[1][c] + o->rq[2][c]) / rho_t[c];
 }
 
 /* ------------------------------------------------------------------ acoustic substep (App. C) */
@@ -997,6 +1158,10 @@ static void substep(orc *o, const double *rho_t, const double *rt_t, double dtau
                 }
                 double pix = 0.5 * (o->pi[IX(o, i - 1, j, k)] + o->pi[c]);
                 double piy = 0.5 * (o->pi[IX(o, i, j - 1, k)] + o->pi[c]);
+                if (C->moist) {   /* App. C: gamma R_d pi^t / (1 + q_v^t + q_c^t) at the face */
+                    pix /= 1.0 + 0.5 * (qvc_at(o, rho_t, IX(o, i - 1, j, k)) + qvc_at(o, rho_t, c));
+                    piy /= 1.0 + 0.5 * (qvc_at(o, rho_t, IX(o, i, j - 1, k)) + qvc_at(o, rho_t, c));
+                }
                 Un[c] = Xu[c] + dtau * (-lin * gRd * pix * gx + Ru[c]);
                 Vn[c] = Xv[c] + dtau * (-lin * gRd * piy * gy + Rv[c]);
             }
@@ -1050,6 +1215,14 @@ static void substep(orc *o, const double *rho_t, const double *rt_t, double dtau
                 double Cpg = gRd * pib / dzc;                                  /* gamma R_d pi / (h_zeta dzeta) */
                 double Cbp = g * rhob * (ORC_RD / ORC_CV) * 0.5 * o->pi[c] / (rt_t[c] * pib);   /* reading R13 */
                 double Cbm = g * rhob * (ORC_RD / ORC_CV) * 0.5 * o->pi[cm] / (rt_t[cm] * pib);
+                if (C->moist) {
+                    /* App. C: the pressure term over 1 + q_v + q_c, the Theta'' buoyancy times
+                     * rho_d / rho_m = 1 / (1 + q_v + q_c + q_r), all face means of stage-t cells */
+                    Cpg /= 1.0 + 0.5 * (qvc_at(o, rho_t, cm) + qvc_at(o, rho_t, c));
+                    double rm = 1.0 + 0.5 * (qt_at(o, rho_t, cm) + qt_at(o, rho_t, c));
+                    Cbp /= rm;
+                    Cbm /= rm;
+                }
                 double P = lin * dtau * (-Cpg + Cbp), Q = lin * dtau * (Cpg + Cbm);
                 double Hk = o->Hc[c], Hm = o->Hc[cm];
                 double X0k = b1 * Xt[c] + b2 * Ts[k], X0m = b1 * Xt[cm] + b2 * Ts[k - 1];
@@ -1137,6 +1310,98 @@ static void tke_stage(orc *o, const double *rho_t, double adt, int nsub) {
     scalar_stage(o, o->rtke, o->sn_tke, o->tke_src, 1, rho_t, adt, nsub);
 }
 
+/* ------------------------------------------------------------------ Kessler microphysics (Sec. 2.4) */
+/* Saturation mixing ratio over liquid water, q_vs = (R_d/R_v) e_s / (p - e_s), with the Tetens
+ * (1930) vapour pressure e_s = 610.78 exp(17.27 (T - 273.16) / (T - 35.86)) Pa (reading: the paper's
+ * Flatau et al. polynomial is cited, not printed; WRF's Kessler scheme uses this Tetens form). */
+double orc_qvs(double T, double p) {
+    double es = 610.78 * exp(17.27 * (T - 273.16) / (T - 35.86));
+    return (ORC_RD / ORC_RV) * es / (p - es);
+}
+/* Rain terminal velocity of Klemp & Wilhelmson (1978), V = 3634 (rho q_r)^0.1346 (rho_0/rho)^(1/2)
+ * cm/s with rho q_r in g/cm^3, rho_0 the base-state density at the ground: in SI units
+ * V = 36.34 (1e-3 rho q_r)^0.1346 sqrt(rho_0 / rho) m/s. */
+double orc_rain_speed(double rho, double qr, double rho_sfc) {
+    if (!(qr > 0.0)) return 0.0;
+    return 36.34 * pow(1.0e-3 * rho * qr, 0.1346) * sqrt(rho_sfc / rho);
+}
+/* Rain evaporation rate of Klemp & Wilhelmson (1978) [1/s]:
+ *   E_r = (1/rho) (1 - q_v/q_vs) C (rho q_r)^0.525 / (5.4e5 + 2.55e6 / (p q_vs)),
+ *   C = 1.6 + 124.9 (rho q_r)^0.2046, rho in g/cm^3, p in mb; 0 in saturated air or without rain. */
+double orc_rain_evap(double rho, double qv, double qr, double qvs, double p) {
+    if (!(qr > 0.0) || !(qv < qvs)) return 0.0;
+    double rg = 1.0e-3 * rho, X = rg * qr;
+    double C = 1.6 + 124.9 * pow(X, 0.2046);
+    return (1.0 / rg) * (1.0 - qv / qvs) * C * pow(X, 0.525) / (5.4e5 + 2.55e6 / ((1.0e-2 * p) * qvs));
+}
+/* One time-split Kessler step (Kessler 1969; Klemp & Wilhelmson 1978) after the RK3 step, per
+ * column, with the dry density unchanged:
+ *   1. rain falls one explicit upwind step, F = rho q_r V through each cell's bottom face; what
+ *      leaves the lowest cell adds F dt / rho_water to the surface accumulation;
+ *   2. autoconversion k1 (q_c - a)^+ (k1 = 1e-3 1/s, a = 1e-3) and accretion k2 q_c q_r^0.875
+ *      (k2 = 2.2 1/s) move cloud water to rain, at most all of it;
+ *   3. saturation adjustment in one linearised step (Soong & Ogura 1973):
+ *      s = (q_v - q_vs) / (1 + q_vs L_v 4098.17 / (c_p (T - 35.86)^2)), the Tetens slope at T = theta pi;
+ *      condensation s (> 0) or evaporation of cloud water (at most q_c); rain evaporates
+ *      min(dt E_r, (-s - q_c)^+, q_r), only what cloud water cannot cover;
+ *      theta += L_v / (c_p pi) (condensation - evaporation), pi from the moist EOS before the step. */
+static void kessler(orc *o) {
+    const double dt = o->c.dt;
+    int nx = o->nx, ny = o->ny, nz = o->nz;
+#pragma omp parallel
+    {
+    double *F = dalloc(nz + 1);
+#pragma omp for
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t c0 = IX(o, i, j, 0);
+            double rho_sfc = o->rho0[c0] / (1.0 + o->qv0[c0]);
+            for (int k = 0; k < nz; ++k) {
+                size_t c = IX(o, i, j, k);
+                F[k] = o->rq[2][c] * orc_rain_speed(o->rho[c], o->rq[2][c] / o->rho[c], rho_sfc);
+            }
+            F[nz] = 0.0;
+            for (int k = 0; k < nz; ++k) {
+                size_t c = IX(o, i, j, k);
+                o->rq[2][c] += dt * (F[k + 1] - F[k]) / o->Hc[c];
+            }
+            o->precip[(size_t)j * nx + i] += dt * F[0] / ORC_RHOW;
+            for (int k = 0; k < nz; ++k) {
+                size_t c = IX(o, i, j, k);
+                double r = o->rho[c], th = o->rt[c] / r;
+                double qv = o->rq[0][c] / r, qc = o->rq[1][c] / r, qr = o->rq[2][c] / r;
+                double p, pie;
+                eos_q(o->rt[c], qv, &p, &pie);
+                double ar = 1.0e-3 * (qc - 1.0e-3);
+                if (ar < 0.0) ar = 0.0;
+                double cr = (qr > 0.0) ? 2.2 * qc * pow(qr, 0.875) : 0.0;
+                double prod = dt * (ar + cr);
+                if (prod > qc) prod = qc;
+                qc -= prod;                 /* the cloud and rain the adjustment below sees */
+                qr += prod;
+                double T = th * pie;
+                double qvs = orc_qvs(T, p);
+                double sadj = (qv - qvs) / (1.0 + qvs * ORC_LV * 4098.17 / (ORC_CP * (T - 35.86) * (T - 35.86)));
+                double ern = dt * orc_rain_evap(r, qv, qr, qvs, p);
+                double lim = -sadj - qc;
+                if (lim < 0.0) lim = 0.0;
+                if (ern > lim) ern = lim;
+                if (ern > qr) ern = qr;
+                double cond = sadj > -qc ? sadj : -qc;
+                /* increments of the conserved variables (nothing changes where nothing happens) */
+                o->rt[c] += r * (ORC_LV / (ORC_CP * pie) * (cond - ern));
+                o->rq[0][c] += r * (ern - cond);
+                o->rq[1][c] += r * (cond - prod);
+                o->rq[2][c] += r * (prod - ern);
+                (void)th;
+            }
+        }
+    free(F);
+    }
+}
+/* test hook: one Kessler step on the current state */
+int orc_kessler(orc *o) { kessler(o); return 0; }
+
 /* ------------------------------------------------------------------ RK3 step (Sec. 3.1) */
 static double *field_ptr(orc *o, int f) {
     switch (f) {
@@ -1159,11 +1424,13 @@ static void rk3_step(orc *o) {
     if (C->tracer) memcpy(o->sn_phi, o->rphi, sizeof(double) * o->ncell);
     int tke = (C->closure == 4);
     if (tke) memcpy(o->sn_tke, o->rtke, sizeof(double) * o->ncell);
+    if (C->moist)
+        for (int q = 0; q < 3; ++q) memcpy(o->sn_q[q], o->rq[q], sizeof(double) * o->ncell);
     const double alpha[3] = {1.0 / 3.0, 0.5, 1.0};
     /* S^t is held in o->rho.. (the state arrays), updated in place at the end of each stage */
     for (int s = 0; s < 3; ++s) {
         slow_rhs(o, o->rho, o->rt, o->ru, o->rv, o->rw);
-        if (C->tracer || tke) {
+        if (C->tracer || tke || C->moist) {
             memset(o->msx, 0, sizeof(double) * o->ncell);
             memset(o->msy, 0, sizeof(double) * o->ncell);
             memset(o->msz, 0, sizeof(double) * o->nw);
@@ -1171,6 +1438,8 @@ static void rk3_step(orc *o) {
         if (C->substep_mode == 1) {
             if (C->tracer) tracer_stage(o, o->rho, alpha[s] * dt, 1);
             if (tke) tke_stage(o, o->rho, alpha[s] * dt, 1);
+            if (C->moist)
+                for (int q = 0; q < 3; ++q) scalar_stage(o, o->rq[q], o->sn_q[q], o->q_src[q], 1, o->rho, alpha[s] * dt, 1);
             /* no substepping: S^(s) = S^n + alpha_s dt f(S^t) */
             for (int f = 0; f < 5; ++f) {
                 double *S = field_ptr(o, f);
@@ -1202,6 +1471,8 @@ static void rk3_step(orc *o) {
         for (int n = 0; n < nsub; ++n) substep(o, rho_t, rt_t, dtau);
         if (C->tracer) tracer_stage(o, rho_t, alpha[s] * dt, nsub);
         if (tke) tke_stage(o, rho_t, alpha[s] * dt, nsub);
+        if (C->moist)
+            for (int q = 0; q < 3; ++q) scalar_stage(o, o->rq[q], o->sn_q[q], o->q_src[q], 1, rho_t, alpha[s] * dt, nsub);
         free(rho_t); free(rt_t);
         /* S^(s) = S^t + X'' */
         for (int f = 0; f < 5; ++f) {
@@ -1209,6 +1480,7 @@ static void rk3_step(orc *o) {
             for (size_t n = 0; n < field_len(o, f); ++n) S[n] += o->X[f][n];
         }
     }
+    if (C->moist) kessler(o);   /* microphysics after the dycore step (time split) */
 }
 
 /* ------------------------------------------------------------------ public API (ctypes) */
@@ -1216,14 +1488,35 @@ static void rk3_step(orc *o) {
  * warm perturbations at constant pressure give negative density perturbations):
  *   theta = theta0 + dtheta, rho theta = rho0 theta0, rho = rho theta / theta;
  * velocities given at faces are multiplied by the face-averaged density; walls get Omega = 0. */
+void orc_set_initial_q(orc *o, const double *dtheta, const double *qv, const double *u, const double *v,
+                       const double *w);
 void orc_set_initial(orc *o, const double *dtheta, const double *u, const double *v, const double *w) {
+    orc_set_initial_q(o, dtheta, NULL, u, v, w);
+}
+/* Moist configurations take the water vapour q_v at cells (NULL: the base state's q_v0) and keep
+ * the pressure too: rho_d theta_d (1 + (R_v/R_d) q_v) = rho_d0 theta0 (1 + (R_v/R_d) q_v0), with
+ * rho_d0 = rho0 / (1 + q_v0) the base dry density; rho q_c = rho q_r = 0.  Every field's initial
+ * value becomes the reference of the lateral relaxation zones. */
+void orc_set_initial_q(orc *o, const double *dtheta, const double *qv, const double *u, const double *v,
+                       const double *w) {
+    const double ev = ORC_RV / ORC_RD;
     for (int k = 0; k < o->nz; ++k)
         for (int j = 0; j < o->ny; ++j)
             for (int i = 0; i < o->nx; ++i) {
                 size_t c = IX(o, i, j, k);
                 double th = o->th0[c] + (dtheta ? dtheta[c] : 0.0);
-                o->rt[c] = o->rho0[c] * o->th0[c];
-                o->rho[c] = o->rho0[c] * (o->th0[c] / th);   /* = rho0 theta0 / theta; exact at rest */
+                if (o->c.moist) {
+                    double q0 = o->qv0[c], q = qv ? qv[c] : q0;
+                    double rd0 = o->rho0[c] / (1.0 + q0), f = (1.0 + ev * q0) / (1.0 + ev * q);
+                    o->rt[c] = rd0 * o->th0[c] * f;
+                    o->rho[c] = rd0 * (o->th0[c] / th) * f;   /* the dry form times f (1 without vapour) */
+                    o->rq[0][c] = o->rho[c] * q;
+                    o->rq[1][c] = 0.0;
+                    o->rq[2][c] = 0.0;
+                } else {
+                    o->rt[c] = o->rho0[c] * o->th0[c];
+                    o->rho[c] = o->rho0[c] * (o->th0[c] / th);   /* = rho0 theta0 / theta; exact at rest */
+                }
             }
     for (int k = 0; k <= o->nz; ++k)
         for (int j = 0; j < o->ny; ++j)
@@ -1237,10 +1530,24 @@ void orc_set_initial(orc *o, const double *dtheta, const double *u, const double
             }
     apply_wall_bc(o, o->rw, o->ru, o->rv);
     o->have_state = 1;
+    for (int f = 0; f < 5; ++f) memcpy(o->ref[f], field_ptr(o, f), sizeof(double) * field_len(o, f));
+    for (int q = 0; q < 3; ++q) memcpy(o->ref_q[q], o->rq[q], sizeof(double) * o->ncell);
+}
+/* the current state becomes the reference of the lateral relaxation zones */
+int orc_capture_reference(orc *o) {
+    for (int f = 0; f < 5; ++f) memcpy(o->ref[f], field_ptr(o, f), sizeof(double) * field_len(o, f));
+    for (int q = 0; q < 3; ++q) memcpy(o->ref_q[q], o->rq[q], sizeof(double) * o->ncell);
+    return 0;
+}
+/* accumulated surface precipitation [m of liquid water] per column (ny*nx) */
+int orc_get_precip(orc *o, double *dst) {
+    memcpy(dst, o->precip, sizeof(double) * (size_t)o->nx * o->ny);
+    return 0;
 }
 
 /* fields 0..4 = rho, rho theta, rho u, rho v, rho w; 5..7 = base rho0, p0, theta0 (get only);
- * 8 = rho phi (passive scalar) */
+ * 8 = rho phi (passive scalar); 9 = rho e (Deardorff); 10..12 = rho q_v, rho q_c, rho q_r;
+ * 13 = base q_v0 (get only) */
 /* passive-scalar initial state: rho phi = rho phi0 at cells, with the current rho */
 int orc_set_tracer_initial(orc *o, const double *phi) {
     for (size_t c = 0; c < o->ncell; ++c) o->rphi[c] = o->rho[c] * phi[c];
@@ -1253,11 +1560,14 @@ int orc_get_field(orc *o, int f, double *dst) {
     if (f == 7) { memcpy(dst, o->th0, sizeof(double) * o->ncell); return 0; }
     if (f == 8) { memcpy(dst, o->rphi, sizeof(double) * o->ncell); return 0; }
     if (f == 9) { memcpy(dst, o->rtke, sizeof(double) * o->ncell); return 0; }
+    if (f >= 10 && f <= 12) { memcpy(dst, o->rq[f - 10], sizeof(double) * o->ncell); return 0; }
+    if (f == 13) { memcpy(dst, o->qv0, sizeof(double) * o->ncell); return 0; }
     return -1;
 }
 int orc_set_field(orc *o, int f, const double *src) {
     if (f == 8) { memcpy(o->rphi, src, sizeof(double) * o->ncell); return 0; }
     if (f == 9) { memcpy(o->rtke, src, sizeof(double) * o->ncell); return 0; }
+    if (f >= 10 && f <= 12) { memcpy(o->rq[f - 10], src, sizeof(double) * o->ncell); return 0; }
     if (f < 0 || f >= 5) return -1;
     memcpy(field_ptr(o, f), src, sizeof(double) * field_len(o, f));
     o->have_state = 1;

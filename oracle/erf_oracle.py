@@ -49,6 +49,7 @@ class _Cfg(C.Structure):
         ("theta_s", C.c_double), ("brunt_N", C.c_double), ("p_s", C.c_double),
         ("tracer", C.c_int32),
         ("ray_tau", C.c_double), ("ray_zd", C.c_double), ("ray_fields", C.c_int32),
+        ("moist", C.c_int32), ("relax_tau", C.c_double), ("relax_width", C.c_double),
     ]
 
 
@@ -86,6 +87,9 @@ class OracleConfig:
     ray_tau: float = 0.0
     ray_zd: float = 0.0
     ray_fields: int = 0
+    moist: int = 0
+    relax_tau: float = 0.0
+    relax_width: float = 0.0
 
 
 _LIB = None
@@ -101,6 +105,18 @@ def _lib():
         dp = C.POINTER(C.c_double)
         L.orc_create.restype = C.c_void_p
         L.orc_create.argtypes = [C.POINTER(_Cfg), dp, dp, C.c_int, dp, dp]
+        L.orc_create2.restype = C.c_void_p
+        L.orc_create2.argtypes = [C.POINTER(_Cfg), dp, dp, C.c_int, dp, dp, C.c_int, dp, dp]
+        L.orc_set_initial_q.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
+        L.orc_capture_reference.argtypes = [C.c_void_p]
+        L.orc_get_precip.argtypes = [C.c_void_p, dp]
+        L.orc_kessler.argtypes = [C.c_void_p]
+        L.orc_qvs.restype = C.c_double
+        L.orc_qvs.argtypes = [C.c_double, C.c_double]
+        L.orc_rain_speed.restype = C.c_double
+        L.orc_rain_speed.argtypes = [C.c_double] * 3
+        L.orc_rain_evap.restype = C.c_double
+        L.orc_rain_evap.argtypes = [C.c_double] * 5
         L.orc_destroy.argtypes = [C.c_void_p]
         L.orc_set_initial.argtypes = [C.c_void_p, dp, dp, dp, dp]
         L.orc_get_field.argtypes = [C.c_void_p, C.c_int, dp]
@@ -145,7 +161,8 @@ def _f64(a):
 
 
 FIELDS = {"rho": 0, "rhotheta": 1, "rhou": 2, "rhov": 3, "rhow": 4,
-          "base_rho": 5, "base_p": 6, "base_theta": 7, "rhophi": 8, "rhotke": 9}
+          "base_rho": 5, "base_p": 6, "base_theta": 7, "rhophi": 8, "rhotke": 9,
+          "rhoqv": 10, "rhoqc": 11, "rhoqr": 12, "base_qv": 13}
 GEOM = {"zc": 0, "Hc": 1, "Hx": 2, "Hy": 3, "hxi_x": 4, "heta_y": 5,
         "zw": 6, "hxi_w": 7, "heta_w": 8, "zn": 9}
 
@@ -153,7 +170,7 @@ GEOM = {"zc": 0, "Hc": 1, "Hx": 2, "Hy": 3, "hxi_x": 4, "heta_y": 5,
 class Oracle:
     """One grid + configuration of the oracle; fields are numpy arrays [k][j][i]."""
 
-    def __init__(self, cfg: OracleConfig, zeta, terrain=None, knots=None):
+    def __init__(self, cfg: OracleConfig, zeta, terrain=None, knots=None, qv_knots=None):
         L = _lib()
         self.cfg = cfg
         c = _Cfg(**{f.name: getattr(cfg, f.name) for f in fields(cfg)})
@@ -167,7 +184,12 @@ class Oracle:
         if knots is not None:
             kz = _f64(knots[0]); kt = _f64(knots[1]); nk = len(kz)
         self._kz, self._kt = kz, kt
-        self._h = L.orc_create(C.byref(c), _p(self._zeta), _p(self._ter), nk, _p(kz), _p(kt))
+        qz = qv = None
+        nq = 0
+        if qv_knots is not None:
+            qz = _f64(qv_knots[0]); qv = _f64(qv_knots[1]); nq = len(qz)
+        self._qz, self._qv = qz, qv
+        self._h = L.orc_create2(C.byref(c), _p(self._zeta), _p(self._ter), nk, _p(kz), _p(kt), nq, _p(qz), _p(qv))
         self.shape_c = (cfg.nz, cfg.ny, cfg.nx)
         self.shape_w = (cfg.nz + 1, cfg.ny, cfg.nx)
 
@@ -185,9 +207,24 @@ class Oracle:
     def _shape(self, f):
         return self.shape_w if f == "rhow" else self.shape_c
 
-    def set_initial(self, dtheta=None, u=None, v=None, w=None):
-        a = [_f64(x) for x in (dtheta, u, v, w)]
-        _lib().orc_set_initial(self._h, *[_p(x) for x in a])
+    def set_initial(self, dtheta=None, u=None, v=None, w=None, qv=None):
+        """Initial state at unchanged pressure; moist configurations take the water vapour q_v
+        at cells (None: the base state's)."""
+        a = [_f64(x) for x in (dtheta, qv, u, v, w)]
+        _lib().orc_set_initial_q(self._h, *[_p(x) for x in a])
+
+    def capture_reference(self):
+        """The current state becomes the reference of the lateral relaxation zones."""
+        _lib().orc_capture_reference(self._h)
+
+    def precip(self):
+        out = np.empty((self.cfg.ny, self.cfg.nx))
+        _lib().orc_get_precip(self._h, _p(out))
+        return out
+
+    def kessler(self):
+        """One Kessler microphysics step on the current state (test hook)."""
+        _lib().orc_kessler(self._h)
 
     def set_tracer_initial(self, phi):
         """rho phi = rho phi0 with the current rho (configuration with tracer = 1)."""
@@ -269,7 +306,10 @@ class Oracle:
         return _lib().orc_mass(self._h)
 
     def state(self):
-        return {k: self.get(k) for k in ("rho", "rhotheta", "rhou", "rhov", "rhow")}
+        out = {k: self.get(k) for k in ("rho", "rhotheta", "rhou", "rhov", "rhow")}
+        if self.cfg.moist:
+            out.update({k: self.get(k) for k in ("rhoqv", "rhoqc", "rhoqr")})
+        return out
 
 
 def set_threads(n: int) -> int:
@@ -318,3 +358,18 @@ def psi_m(zeta):
 
 def ustar(U, z1, z0, Q=0.0, theta=300.0, g=9.81):
     return _lib().orc_ustar(float(U), float(z1), float(z0), float(Q), float(theta), float(g))
+
+
+def qvs(T, p):
+    """Saturation mixing ratio (Tetens) of the oracle's Kessler scheme."""
+    return _lib().orc_qvs(float(T), float(p))
+
+
+def rain_speed(rho, qr, rho_sfc):
+    """Rain terminal velocity [m/s] of the oracle's Kessler scheme."""
+    return _lib().orc_rain_speed(float(rho), float(qr), float(rho_sfc))
+
+
+def rain_evap(rho, qv, qr, qvs_, p):
+    """Rain evaporation rate [1/s] of the oracle's Kessler scheme."""
+    return _lib().orc_rain_evap(float(rho), float(qv), float(qr), float(qvs_), float(p))

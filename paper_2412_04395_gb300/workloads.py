@@ -74,6 +74,13 @@ class Workload:
     ray_tau: float = 0.0                   # Rayleigh damping strength at the top [1/s] (0 = off)
     ray_zd: float = 0.0                    # bottom of the damping layer [m]
     ray_fields: int = 0                    # RAY_U | RAY_V | RAY_W | RAY_THETA
+    moist: int = 0                         # 1: rho q_v, rho q_c, rho q_r with Kessler microphysics
+    qv_knots: Optional[tuple] = None       # (z[], q_v[]) base-state water-vapour sounding [kg/kg]
+    qv: Optional[np.ndarray] = None        # initial q_v at cells (None: the base state's)
+    qc: Optional[np.ndarray] = None        # initial cloud water / rain mixing ratios at cells
+    qr: Optional[np.ndarray] = None
+    relax_tau: float = 0.0                 # lateral relaxation zones (open x boundaries) [1/s]
+    relax_width: float = 0.0               # their width [m]
     notes: str = ""
 
     @property
@@ -197,6 +204,36 @@ def hill_bubble(nx=256, ny=256, nz=128, steps=500, dx=50.0, dz0=20.0, ratio=1.01
                     dtheta=dth, notes="3D warm bubble over a Gaussian hill, FP64, inviscid")
 
 
+def squall_line(nx=1500, ny=4, nz=240, dx=100.0, dt=0.25, steps=36000, relax_width=10000.0,
+                relax_tau=0.01) -> Workload:
+    """Idealised two-dimensional squall line (Sec. 4.1.3): 150 km x 24 km at 100 m, dt 0.25 s,
+    constant diffusivities nu = alpha = 200 m^2/s for every variable, Kessler microphysics, open
+    lateral boundaries (here relaxation zones of relax_width toward the initial state at rate
+    relax_tau), slip walls at the ground and the lid.  Warm bubble dtheta = 3 cos^2(pi r / 2),
+    r < 1, centre (75 km, 2 km), radii 10 km x 1.5 km; wind u = -12 + 0.0048 z below 2.5 km, 0 above.
+    Sounding (the paper names a moist, subsaturated hydrostatic background without printing it):
+    theta after Weisman & Klemp (1982), 300 K at the ground rising as (z/12 km)^(5/4) to 343 K at
+    the 12 km tropopause and isothermal (213 K) above; water vapour by piecewise-linear knots from
+    14 g/kg at the ground, decreasing with height (subsaturated everywhere)."""
+    zeta = uniform_zeta(nz, dx)
+    X, Y, Z = cell_coords(nx, ny, zeta, dx, dx)
+    xc = 0.5 * nx * dx
+    r = np.sqrt(((X - xc) / 10000.0) ** 2 + ((Z - 2000.0) / 1500.0) ** 2)
+    dth = np.where(r < 1.0, 3.0 * np.cos(0.5 * np.pi * r) ** 2, 0.0)
+    zf = Z  # u sits at x-faces, at the cell-centre height
+    u = np.where(zf <= 2500.0, -12.0 + 0.0048 * zf, 0.0)
+    top = max(nz * dx, 12001.0)
+    zk = np.concatenate([np.linspace(0.0, 12000.0, 25), [top + 1.0]])
+    thk = np.where(zk <= 12000.0, 300.0 + 43.0 * (np.minimum(zk, 12000.0) / 12000.0) ** 1.25,
+                   343.0 * np.exp(9.81 * (zk - 12000.0) / (1004.5 * 213.0)))
+    qz = np.array([0.0, 1000.0, 2000.0, 4000.0, 6000.0, 8000.0, 10000.0, 12000.0, top + 1.0])
+    qk = np.array([14.0, 11.0, 8.0, 4.0, 1.6, 0.5, 0.12, 0.02, 0.01]) * 1.0e-3
+    return Workload("squall_line", nx, ny, nz, dx, dx, zeta, dt=dt, n_substeps=6, closure=CLOSURE_CONST_NU,
+                    nu=200.0, Pr_t=1.0, knots=(zk, thk), steps=steps, dtheta=dth, u=u, moist=1,
+                    qv_knots=(qz, qk), relax_tau=relax_tau, relax_width=relax_width,
+                    notes="2D squall line, Kessler microphysics, FP64")
+
+
 NOISE_SEED = 20241205
 NOISE_TOP = 400.0   # seeded theta noise below this height [m]
 
@@ -305,6 +342,7 @@ def with_tracer(wl: Workload, kind: str = "blob", radius_frac: float = 0.2) -> W
 
 
 CASES = {
+    "squall_line": squall_line,
     "density_current": density_current,
     "hill_bubble": hill_bubble,
     "neutral_abl": neutral_abl,

@@ -23,7 +23,8 @@ def oracle_config_from(wl, **over):
                        nu=wl.nu, gravity=wl.gravity, f_cor=wl.f_cor, u_g=wl.u_g, v_g=wl.v_g,
                        surface=wl.surface, z0=wl.z0, sfc_theta_flux=wl.sfc_theta_flux,
                        theta_s=wl.theta_s, brunt_N=wl.brunt_N, p_s=wl.p_s, tracer=wl.tracer,
-                       ray_tau=wl.ray_tau, ray_zd=wl.ray_zd, ray_fields=wl.ray_fields)
+                       ray_tau=wl.ray_tau, ray_zd=wl.ray_zd, ray_fields=wl.ray_fields,
+                       moist=wl.moist, relax_tau=wl.relax_tau, relax_width=wl.relax_width)
     for k, v in over.items():
         setattr(cfg, k, v)
     return cfg
@@ -32,9 +33,16 @@ def oracle_config_from(wl, **over):
 def make_oracle(wl, init=True, **over):
     """Oracle for a workload (optionally overriding configuration fields), initial state set."""
     from oracle import Oracle
-    o = Oracle(oracle_config_from(wl, **over), wl.zeta, wl.terrain, wl.knots)
+    o = Oracle(oracle_config_from(wl, **over), wl.zeta, wl.terrain, wl.knots, wl.qv_knots)
     if init:
-        o.set_initial(wl.dtheta, wl.u, wl.v, wl.w)
+        o.set_initial(wl.dtheta, wl.u, wl.v, wl.w, qv=wl.qv)
+        if wl.moist and (wl.qc is not None or wl.qr is not None):
+            rho = o.get("rho")
+            if wl.qc is not None:
+                o.set("rhoqc", rho * wl.qc)
+            if wl.qr is not None:
+                o.set("rhoqr", rho * wl.qr)
+            o.capture_reference()
         if wl.tracer and wl.phi is not None:
             o.set_tracer_initial(wl.phi)
         if wl.closure == 4 and wl.tke is not None:
