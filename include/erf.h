@@ -54,7 +54,11 @@ typedef enum {
     ERF_RHO = 0, ERF_RHOTHETA = 1, ERF_RHOU = 2, ERF_RHOV = 3, ERF_RHOW = 4,
     ERF_BASE_RHO = 5, ERF_BASE_P = 6, ERF_BASE_THETA = 7,    /* base state: get only */
     ERF_RHOPHI = 8,                 /* passive scalar rho phi at cells (config tracer = 1) */
-    ERF_RHOTKE = 9                  /* rho e, the SGS kinetic energy of the Deardorff closure */
+    ERF_RHOTKE = 9,                 /* rho e, the SGS kinetic energy of the Deardorff closure */
+    ERF_RHOQV = 10, ERF_RHOQC = 11, ERF_RHOQR = 12,   /* rho q_v, rho q_c, rho q_r (moist handles) */
+    ERF_PRECIP = 13,                /* accumulated surface precipitation [m of water], ny*nx, get only */
+    ERF_BASE_QV = 14,               /* base-state water vapour q_v0, get only (layout of the base state) */
+    ERF_P_ANELASTIC = 15            /* the anelastic pressure perturbation p' at cells (anelastic handles) */
 } erf_field;
 
 typedef enum { ERF_F64 = 0, ERF_F32 = 1 } erf_dtype;
@@ -118,6 +122,34 @@ typedef struct {
                                        -tau(z) rho (phi - phi_ref), toward u_g, v_g, 0 and the base
                                        theta0.  ray_tau = 0 or ray_fields = 0: off */
     int32_t ray_fields;             /* bitmask: 1 u, 2 v, 4 w, 8 theta */
+    int32_t moist;                  /* 1 = moist air (FP64 path, flat or terrain): rho q_v, rho q_c,
+                                       rho q_r per unit dry mass, transported like scalars (Sec. 3.1)
+                                       and diffused with the heat diffusivity of the closure; the
+                                       moist EOS p = P00 (R_d rho theta (1 + (R_v/R_d) q_v)/P00)^gamma
+                                       (Sec. 2.1, R_v = 461.5); pressure gradient and buoyancy over
+                                       1 + q_v + q_c with the buoyancy of the total density
+                                       rho (1 + q_v + q_c + q_r) (Eq. mom); App. C's moisture factors
+                                       in the substep coefficients; the base state hydrostatic in
+                                       the total density with the vapour sounding below; and Kessler
+                                       microphysics (Sec. 2.4, Klemp & Wilhelmson 1978 with a Tetens
+                                       saturation) after every RK3 step.  0 = dry */
+    int32_t n_qknots;               /* moist: piecewise-linear base-state vapour sounding q_v0(z) */
+    const double *qknot_z, *qknot_v;   /* host, n_qknots each [m, kg/kg], read during erf_init_grid only */
+    double relax_tau, relax_width;  /* open x boundaries as relaxation zones (Sec. 3.8, FP64 path):
+                                       within relax_width [m] of an x-edge every prognostic field
+                                       (moisture included) relaxes toward the reference state at rate
+                                       relax_tau sin^2(pi/2 (1 - d/relax_width)) [1/s], d the distance
+                                       to the edge; the reference is the state after
+                                       erf_set_initial(_moist) or erf_capture_reference.  0 = off */
+    int32_t anelastic;              /* 1 = the anelastic equation set (Sec. 2.2; FP64 path, flat grids,
+                                       nx and ny powers of two up to 4096): rho held at the base
+                                       density, buoyancy rho0 g (theta - theta0) / theta0, SSP-RK2 steps
+                                       (Sec. 3.2) on the slow tendencies with the lagged pressure, each
+                                       stage projected by an exact FFT (x, y) + tridiagonal (z) Poisson
+                                       solve of dt div(grad psi) = div(rho0 u): rho0 u -= dt grad psi;
+                                       p' = p'^n + psi after stage 1 and (p'^n + p'*)/2 + psi after
+                                       stage 2 (the field ERF_P_ANELASTIC); erf_set_initial projects
+                                       the initial momentum.  No acoustic substeps.  0 = compressible */
 } erf_config;
 
 /* Diagnostics (Sec. 4.1.2: mass conserved to machine precision). */
@@ -149,6 +181,17 @@ erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config *cfg, void 
  * host (is_device = 0) or the device (is_device = 1). */
 erf_status erf_set_initial(erf_handle *h, const double *dtheta, const double *u, const double *v,
                            const double *w, int32_t is_device);
+
+/* Moist initial state (config moist = 1): theta = theta0 + dtheta and water vapour q_v (nz*ny*nx,
+ * NULL = the base state's q_v0) at unchanged pressure (rho theta (1 + (R_v/R_d) q_v) held at its
+ * base-state value), no cloud or rain; velocities as erf_set_initial.  The result is also the
+ * reference of the relaxation zones.  ERF_EUNSUPPORTED on a dry handle. */
+erf_status erf_set_initial_moist(erf_handle *h, const double *dtheta, const double *qv, const double *u,
+                                 const double *v, const double *w, int32_t is_device);
+
+/* The current state becomes the reference of the lateral relaxation zones (after fields were set
+ * with erf_set_state).  ERF_EUNSUPPORTED without relaxation zones, ERF_ESTATE before any state. */
+erf_status erf_capture_reference(erf_handle *h);
 
 /* Passive-scalar initial state: rho phi = rho phi0 at cells with the current rho (Sec. 3.1,
  * scalar equation).  phi0 is nz*ny*nx FP64 on the host (is_device = 0) or the device.

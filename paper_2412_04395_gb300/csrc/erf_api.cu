@@ -61,6 +61,17 @@ struct erf_handle {
     // Deardorff closure (FP64 path): rho e (stage state), its S^n copy, the stage's energy source
     // and the heat diffusivity rho K_h
     double *tke = nullptr, *sntke = nullptr, *tke_src = nullptr, *muh = nullptr;
+    // moisture (FP64 path): rho q_v, rho q_c, rho q_r (stage state), their S^n copies, their
+    // slow-pass sources, the base-state q_v0, the sounding knots and the surface precipitation
+    double *rq[3] = {nullptr, nullptr, nullptr}, *snq[3] = {nullptr, nullptr, nullptr};
+    double *qsrc[3] = {nullptr, nullptr, nullptr}, *qv0 = nullptr, *qkz = nullptr, *qkv = nullptr;
+    double *precip = nullptr;
+    // lateral relaxation zones: the reference state (rho, rho theta, rho u, rho v, rho w, rho q's)
+    double *ref[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // anelastic equation set: projection pressure p' (now, at the step start, after stage 1), FFT
+    // twiddles and second-difference eigenvalues
+    double *pa = nullptr, *pan = nullptr, *pa1 = nullptr, *lamx = nullptr, *lamy = nullptr;
+    double2 *twx = nullptr, *twy = nullptr;
     F5 st, sn, x, R;
     double *pp, *pi, *th, *Tp, *Om;
     Tri tri;
@@ -130,6 +141,38 @@ static erf_status validate(const erf_grid_desc *g, const erf_config *c, std::str
         (c->ray_fields != 0 && !(c->ray_zd < g->z_faces[g->nz]))) {
         msg = "Rayleigh damping: fields 0..15, tau >= 0, 0 <= z_d < domain top";
         return ERF_EINVAL;
+    }
+    if (c->anelastic != 0 && c->anelastic != 1) { msg = "anelastic must be 0 or 1"; return ERF_EINVAL; }
+    if (c->anelastic) {
+        auto pow2 = [](int n) { return n >= 1 && n <= 4096 && (n & (n - 1)) == 0; };
+        if (c->precision != ERF_PREC_FP64 || c->moist || c->tracer || c->closure == 4 || c->relax_tau > 0.0) {
+            msg = "the anelastic equation set runs on the FP64 path without moisture, scalars or relaxation zones";
+            return ERF_EUNSUPPORTED;
+        }
+        if (!pow2(g->nx) || !pow2(g->ny)) {
+            msg = "the anelastic projection's FFT needs nx and ny powers of two up to 4096";
+            return ERF_EUNSUPPORTED;
+        }
+        if (g->terrain_nodes)
+            for (long long n = 0; n < (long long)g->nx * g->ny; ++n)
+                if (g->terrain_nodes[n] != 0.0) { msg = "the anelastic projection is built for flat grids"; return ERF_EUNSUPPORTED; }
+    }
+    if (c->moist != 0 && c->moist != 1) { msg = "moist must be 0 or 1"; return ERF_EINVAL; }
+    if (c->moist && c->precision != ERF_PREC_FP64) {
+        msg = "moisture and microphysics run on the FP64 path";
+        return ERF_EUNSUPPORTED;
+    }
+    if (c->moist && (c->n_qknots < 1 || !c->qknot_z || !c->qknot_v)) {
+        msg = "a moist configuration needs its water-vapour sounding (n_qknots >= 1)";
+        return ERF_EINVAL;
+    }
+    if (!(c->relax_tau >= 0.0) || (c->relax_tau > 0.0 && !(c->relax_width > 0.0))) {
+        msg = "relaxation zones: relax_tau >= 0 and relax_width > 0";
+        return ERF_EINVAL;
+    }
+    if (c->relax_tau > 0.0 && c->precision != ERF_PREC_FP64) {
+        msg = "relaxation zones run on the FP64 path";
+        return ERF_EUNSUPPORTED;
     }
     if (c->ray_fields != 0 && c->ray_tau > 0.0 && c->precision != ERF_PREC_FP64) {
         msg = "Rayleigh damping runs on the FP64 path";
@@ -241,8 +284,26 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
     if (c->tracer) {
         H->tphi = cv.take<double>(nc); H->snphi = cv.take<double>(nc);
     }
-    if (c->tracer || c->closure == 4) {
+    if (c->tracer || c->closure == 4 || c->moist) {
         H->msx = cv.take<double>(nc); H->msy = cv.take<double>(nc); H->msz = cv.take<double>(nw);
+    }
+    if (c->moist) {
+        for (int q = 0; q < 3; ++q) {
+            H->rq[q] = cv.take<double>(nc); H->snq[q] = cv.take<double>(nc); H->qsrc[q] = cv.take<double>(nc);
+        }
+        H->qv0 = cv.take<double>(nb);
+        H->qkz = cv.take<double>(c->n_qknots); H->qkv = cv.take<double>(c->n_qknots);
+        H->precip = cv.take<double>(nxy);
+    }
+    if (c->anelastic) {
+        H->pa = cv.take<double>(nc); H->pan = cv.take<double>(nc); H->pa1 = cv.take<double>(nc);
+        H->lamx = cv.take<double>(nx); H->lamy = cv.take<double>(ny);
+        H->twx = cv.take<double2>(nx / 2 > 0 ? nx / 2 : 1); H->twy = cv.take<double2>(ny / 2 > 0 ? ny / 2 : 1);
+    }
+    if (c->relax_tau > 0.0) {
+        for (int f = 0; f < 5; ++f) H->ref[f] = cv.take<double>(f == 4 ? nw : nc);
+        if (c->moist)
+            for (int q = 0; q < 3; ++q) H->ref[5 + q] = cv.take<double>(nc);
     }
     if (c->closure == 4) {
         H->tke = cv.take<double>(nc); H->sntke = cv.take<double>(nc);
@@ -292,6 +353,13 @@ static void fill_geo(erf_handle *h) {
     P.ray_zd = c.ray_zd;
     P.ray_fields = c.ray_tau > 0.0 ? c.ray_fields : 0;
     P.ray_zt = 0.0;   // set in erf_init_grid from the face heights
+    P.moist = c.moist ? 1 : 0;
+    P.rqv = h->rq[0]; P.rqc = h->rq[1]; P.rqr = h->rq[2];
+    P.relax_tau = c.relax_tau;
+    P.relax_w = c.relax_width;
+    P.Lx = g.nx * g.dx;
+    P.anelastic = c.anelastic ? 1 : 0;
+    G.qv0 = h->qv0;
 }
 
 extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config *cfg, void *d_workspace,
@@ -312,6 +380,7 @@ extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config 
     h->grid.terrain_nodes = nullptr;
     h->cfg = *cfg;
     h->cfg.knot_z = h->cfg.knot_theta = nullptr;
+    h->cfg.qknot_z = h->cfg.qknot_v = nullptr;
     h->user = reinterpret_cast<cudaStream_t>(cuda_stream);
     carve(h, grid, cfg, d_workspace, false);
     const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
@@ -374,8 +443,29 @@ extern "C" erf_status erf_init_grid(const erf_grid_desc *grid, const erf_config 
     launch_terrain(h->geo, h->hn, h->hc, h->hxf, h->hyf, h->gxh, h->gyh, h->g4xq, h->g4yq, st);
     if (h->geo.terrain && h->rH3)
         launch_terrain_recip(h->geo, h->Hx3, h->Hy3, h->rH3, h->rHx3, h->rHy3, h->rdzw3, h->rdz2, st);
+    if (cfg->moist) {
+        CK(cudaMemcpyAsync(h->qkz, cfg->qknot_z, cfg->n_qknots * sizeof(double), cudaMemcpyHostToDevice, st), "copy q knots");
+        CK(cudaMemcpyAsync(h->qkv, cfg->qknot_v, cfg->n_qknots * sizeof(double), cudaMemcpyHostToDevice, st), "copy q knots");
+        CK(cudaMemsetAsync(h->precip, 0, nxy * sizeof(double), st), "zero precipitation");
+        for (int q = 0; q < 3; ++q) CK(cudaMemsetAsync(h->rq[q], 0, h->geo.nc * sizeof(double), st), "zero moisture");
+    }
     launch_base_state(h->geo, cfg->n_knots, h->knz, h->knt, cfg->theta_s, cfg->brunt_N, cfg->p_s, cfg->gravity,
-                      h->rho0, h->th0, h->p0, st);
+                      h->rho0, h->th0, h->p0, st, cfg->moist ? cfg->n_qknots : 0, h->qkz, h->qkv, h->qv0);
+    std::vector<double> lamx(nx), lamy(ny), twx(nx > 1 ? nx : 2), twy(ny > 1 ? ny : 2);
+    if (cfg->anelastic) {
+        // eigenvalues of the periodic second differences and the FFT twiddles exp(-2 pi i m / n)
+        const double pi_ = 3.141592653589793;
+        for (int i = 0; i < nx; ++i) { double sn = std::sin(pi_ * i / nx); lamx[i] = -4.0 / (grid->dx * grid->dx) * sn * sn; }
+        for (int j = 0; j < ny; ++j) { double sn = std::sin(pi_ * j / ny); lamy[j] = -4.0 / (grid->dy * grid->dy) * sn * sn; }
+        for (int m = 0; m < nx / 2; ++m) { twx[2 * m] = std::cos(2.0 * pi_ * m / nx); twx[2 * m + 1] = -std::sin(2.0 * pi_ * m / nx); }
+        for (int m = 0; m < ny / 2; ++m) { twy[2 * m] = std::cos(2.0 * pi_ * m / ny); twy[2 * m + 1] = -std::sin(2.0 * pi_ * m / ny); }
+        CK(cudaMemcpyAsync(h->lamx, lamx.data(), nx * sizeof(double), cudaMemcpyHostToDevice, st), "copy eigenvalues");
+        CK(cudaMemcpyAsync(h->lamy, lamy.data(), ny * sizeof(double), cudaMemcpyHostToDevice, st), "copy eigenvalues");
+        if (nx > 1) CK(cudaMemcpyAsync(h->twx, twx.data(), nx / 2 * sizeof(double2), cudaMemcpyHostToDevice, st), "copy twiddles");
+        if (ny > 1) CK(cudaMemcpyAsync(h->twy, twy.data(), ny / 2 * sizeof(double2), cudaMemcpyHostToDevice, st), "copy twiddles");
+        CK(cudaMemsetAsync(h->pa, 0, h->geo.nc * sizeof(double), st), "zero pressure");
+        if (!anel_fft_setup()) CK(cudaGetLastError(), "FFT shared-memory attribute");
+    }
     if (h->mixed) {
         mx_build_base(h->geo, cfg->Cs, grid->dx, grid->dy, cfg->gravity, h->mbase, h->mrt0, st);
         h->mb = mx_base_view(h->mbase, h->mrt0, nz);
@@ -442,10 +532,53 @@ static void enqueue_step_mixed(erf_handle *h, cudaStream_t s) {
     }
 }
 
+static AnelWork anel_work(erf_handle *h) {
+    // the flux buffer (3 nw doubles) holds the complex field and the mass-density tendency (unused
+    // by the anelastic set) the z-solve scratch: both are free during the projection
+    return AnelWork{reinterpret_cast<double2 *>(h->flux), h->twx, h->twy, h->lamx, h->lamy, h->R.r, h->pa, h->pan,
+                    h->pa1};
+}
+
+// one SSP-RK2 step of the anelastic equations (Sec. 3.2), enqueued on stream s:
+//   S* = S^n + dt f(S^n), project;  S^{n+1} = S^n + dt/2 (f(S^n) + f(S*)), project
+static void enqueue_step_anelastic(erf_handle *h, cudaStream_t s) {
+    const Geo &g = h->geo;
+    const Phys &ph = h->ph;
+    const double dt = h->cfg.dt;
+    launch_wall_bc(g, h->st.u, h->st.v, h->st.w, s);
+    size_t bc = g.nc * sizeof(double), bw = g.nw * sizeof(double);
+    cudaMemcpyAsync(h->sn.t, h->st.t, bc, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->sn.u, h->st.u, bc, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->sn.v, h->st.v, bc, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->sn.w, h->st.w, bw, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->pan, h->pa, bc, cudaMemcpyDeviceToDevice, s);
+    Prep pr{h->ux, h->vy, h->wz, h->mfx, h->mfy, h->rom};
+    const AnelWork w = anel_work(h);
+    for (int stage = 1; stage <= 2; ++stage) {
+        launch_anel_begin(g, h->st.t, h->st.r, h->pa, h->pp, h->th, s);
+        launch_slow_rhs(g, ph, cf(h->st), h->pp, h->th, pr, h->ux, h->vy, h->wz, h->mfx, h->mfy, h->rom, h->mu,
+                        h->flux, h->R, s);
+        if (stage == 1) {   // the first stage's tendencies (rho theta, momenta) are kept in x
+            cudaMemcpyAsync(h->x.t, h->R.t, bc, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(h->x.u, h->R.u, bc, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(h->x.v, h->R.v, bc, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(h->x.w, h->R.w, bw, cudaMemcpyDeviceToDevice, s);
+            launch_anel_stage(g, h->st, cf(h->sn), cf(h->x), cf(h->R), dt, 0.0, s);
+        } else {
+            launch_anel_stage(g, h->st, cf(h->sn), cf(h->x), cf(h->R), 0.5 * dt, 0.5 * dt, s);
+        }
+        launch_anel_project(g, w, dt, h->st.u, h->st.v, h->st.w, stage, s);
+    }
+}
+
 // one RK3 step (Sec. 3.1) with the App. C substeps, enqueued on stream s
 static void enqueue_step(erf_handle *h, cudaStream_t s) {
     if (h->mixed) {
         enqueue_step_mixed(h, s);
+        return;
+    }
+    if (h->pa) {
+        enqueue_step_anelastic(h, s);
         return;
     }
     const Geo &g = h->geo;
@@ -460,12 +593,25 @@ static void enqueue_step(erf_handle *h, cudaStream_t s) {
     cudaMemcpyAsync(h->sn.w, h->st.w, bw, cudaMemcpyDeviceToDevice, s);
     if (h->tphi) cudaMemcpyAsync(h->snphi, h->tphi, bc, cudaMemcpyDeviceToDevice, s);
     if (h->tke) cudaMemcpyAsync(h->sntke, h->tke, bc, cudaMemcpyDeviceToDevice, s);
+    if (h->rq[0])
+        for (int q = 0; q < 3; ++q) cudaMemcpyAsync(h->snq[q], h->rq[q], bc, cudaMemcpyDeviceToDevice, s);
     const double alpha[3] = {1.0 / 3.0, 0.5, 1.0};
     Prep pr{h->ux, h->vy, h->wz, h->mfx, h->mfy, h->rom};
+    MoistIO mio{{h->qsrc[0], h->qsrc[1], h->qsrc[2]},
+                {h->ref[0], h->ref[1], h->ref[2], h->ref[3], h->ref[4], h->ref[5], h->ref[6], h->ref[7]}};
+    const MoistIO *miop = (h->rq[0] || h->ref[0]) ? &mio : nullptr;
+    // the moisture scalars after the substeps of a stage: the stage-averaged fluxes, their sources,
+    // clipped at zero
+    auto moist_stage = [&](int nsub, double adt) {
+        if (!h->rq[0]) return;
+        for (int q = 0; q < 3; ++q)
+            launch_tracer_stage(g, ph, cf(h->st), h->rom, h->snq[q], h->msx, h->msy, h->msz, nsub, adt, h->pp,
+                                h->flux, h->rq[q], s, h->qsrc[q], 1);
+    };
     for (int stage = 0; stage < 3; ++stage) {
-        launch_stage_begin(g, cf(h->sn), cf(h->st), h->x, h->pp, h->pi, h->th, h->Tp, h->Om, s);
+        launch_stage_begin(g, cf(h->sn), cf(h->st), h->x, h->pp, h->pi, h->th, h->Tp, h->Om, s, h->rq[0]);
         launch_slow_rhs(g, ph, cf(h->st), h->pp, h->th, pr, h->ux, h->vy, h->wz, h->mfx, h->mfy, h->rom, h->mu,
-                        h->flux, h->R, s, h->tke, h->muh, h->tke_src);
+                        h->flux, h->R, s, h->tke, h->muh, h->tke_src, miop);
         if (h->msx) {
             cudaMemsetAsync(h->msx, 0, bc, s);
             cudaMemsetAsync(h->msy, 0, bc, s);
@@ -478,6 +624,7 @@ static void enqueue_step(erf_handle *h, cudaStream_t s) {
             if (h->tke)
                 launch_tracer_stage(g, ph, cf(h->st), h->rom, h->sntke, h->msx, h->msy, h->msz, 1,
                                     alpha[stage] * c.dt, h->pp, h->flux, h->tke, s, h->tke_src, 1);
+            moist_stage(1, alpha[stage] * c.dt);
             launch_stage_nosub(g, h->st, cf(h->sn), cf(h->R), alpha[stage] * c.dt, s);
             launch_wall_bc(g, h->st.u, h->st.v, h->st.w, s);
             continue;
@@ -499,8 +646,11 @@ static void enqueue_step(erf_handle *h, cudaStream_t s) {
         if (h->tke)
             launch_tracer_stage(g, ph, cf(h->st), h->rom, h->sntke, h->msx, h->msy, h->msz, nsub,
                                 alpha[stage] * c.dt, h->pp, h->flux, h->tke, s, h->tke_src, 1);
+        moist_stage(nsub, alpha[stage] * c.dt);
         launch_stage_end(g, h->st, cf(h->x), s);
     }
+    // microphysics after the dycore step (time split, Sec. 2.4)
+    if (h->rq[0]) launch_kessler(g, c.dt, h->st.t, h->st.r, h->rq[0], h->rq[1], h->rq[2], h->precip, s);
 }
 
 static erf_status build_graph(erf_handle *h) {
@@ -608,6 +758,8 @@ static int state_fields(erf_handle *h, void **ptr, int *levels) {
         for (int q = 0; q < 5; ++q) { ptr[n] = f[q]; levels[n++] = q == 4 ? nz + 1 : nz; }
         if (h->tphi) { ptr[n] = h->tphi; levels[n++] = nz; }
         if (h->tke) { ptr[n] = h->tke; levels[n++] = nz; }
+        for (int q = 0; q < 3; ++q)
+            if (h->rq[q]) { ptr[n] = h->rq[q]; levels[n++] = nz; }
     }
     return n;
 }
@@ -615,8 +767,8 @@ static int state_fields(erf_handle *h, void **ptr, int *levels) {
 extern "C" erf_status erf_column_block_bytes(const erf_handle *hc, int32_t ni, int32_t nj, size_t *bytes) {
     erf_handle *h = const_cast<erf_handle *>(hc);
     if (!h || !bytes || ni < 0 || nj < 0) return fail(h, ERF_EINVAL, "bad column-block arguments");
-    void *p[8];
-    int lv[8];
+    void *p[12];
+    int lv[12];
     int nf = state_fields(h, p, lv);
     size_t words = 0;
     for (int q = 0; q < nf; ++q) words += (size_t)lv[q] * ni * nj;
@@ -631,8 +783,8 @@ static erf_status column_block(erf_handle *h, int32_t i0, int32_t ni, int32_t j0
     if (!buf || ni < 0 || nj < 0 || i0 < 0 || j0 < 0 || (long long)i0 + ni > g.nx || (long long)j0 + nj > g.ny)
         return fail(h, ERF_EINVAL, "column block outside the grid");
     if (unpack == 0 && !h->have_state) return fail(h, ERF_ESTATE, "no state set");
-    void *p[8];
-    int lv[8];
+    void *p[12];
+    int lv[12];
     int nf = state_fields(h, p, lv);
     const int eb = h->mixed ? (int)sizeof(float) : (int)sizeof(double);
     char *b = reinterpret_cast<char *>(buf);
@@ -654,9 +806,86 @@ extern "C" erf_status erf_unpack_columns(erf_handle *h, int32_t i0, int32_t ni, 
     return column_block(h, i0, ni, j0, nj, const_cast<void *>(d_buf), 1);
 }
 
+static erf_status capture_reference(erf_handle *h) {
+    if (!h->ref[0]) return ERF_OK;
+    const Geo &g = h->geo;
+    const double *src[8] = {h->st.r, h->st.t, h->st.u, h->st.v, h->st.w, h->rq[0], h->rq[1], h->rq[2]};
+    for (int f = 0; f < 8; ++f) {
+        if (!h->ref[f]) continue;
+        cudaError_t e = cudaMemcpyAsync(h->ref[f], src[f], (f == 4 ? g.nw : g.nc) * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, h->user);
+        if (e != cudaSuccess) return cuda_fail(h, e, "capture relaxation reference");
+    }
+    return ERF_OK;
+}
+
+extern "C" erf_status erf_capture_reference(erf_handle *h) {
+    if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
+    if (!h->have_state) return fail(h, ERF_ESTATE, "no state set");
+    if (!h->ref[0]) return fail(h, ERF_EUNSUPPORTED, "handle configured without relaxation zones");
+    return capture_reference(h);
+}
+
+extern "C" erf_status erf_set_initial_moist(erf_handle *h, const double *dtheta, const double *qv, const double *u,
+                                            const double *v, const double *w, int32_t is_device) {
+    if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
+    if (!h->rq[0]) return fail(h, ERF_EUNSUPPORTED, "handle configured without moisture");
+    const Geo &g = h->geo;
+    cudaStream_t s = h->user;
+    const double *src[5] = {dtheta, qv, u, v, w};
+    double *stage[5] = {h->x.r, h->x.t, h->x.u, h->x.v, h->x.w};   // perturbation arrays as staging
+    long long len[5] = {g.nc, g.nc, g.nc, g.nc, g.nw};
+    const double *dev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    for (int n = 0; n < 5; ++n) {
+        if (!src[n]) continue;
+        if (is_device) { dev[n] = src[n]; continue; }
+        cudaError_t e = cudaMemcpyAsync(stage[n], src[n], len[n] * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy initial field");
+        dev[n] = stage[n];
+    }
+    launch_set_initial_moist(g, dev[0], dev[1], dev[2], dev[3], dev[4], h->st.r, h->st.t, h->st.u, h->st.v, h->st.w,
+                             h->rq[0], h->rq[1], h->rq[2], s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_initial_moist kernels");
+    h->have_state = true;
+    erf_status st = capture_reference(h);
+    if (st != ERF_OK) return st;
+    if (!is_device) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "set_initial sync");
+    }
+    return ERF_OK;
+}
+
 extern "C" erf_status erf_set_initial(erf_handle *h, const double *dtheta, const double *u, const double *v,
                                       const double *w, int32_t is_device) {
     if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
+    if (h->rq[0]) return erf_set_initial_moist(h, dtheta, nullptr, u, v, w, is_device);
+    if (h->pa) {
+        // anelastic: rho = rho0, rho theta = rho0 theta; the momentum projected once, p' = 0
+        const Geo &g = h->geo;
+        cudaStream_t s = h->user;
+        const double *src[4] = {dtheta, u, v, w};
+        double *stage[4] = {h->x.r, h->x.u, h->x.v, h->x.w};
+        long long len[4] = {g.nc, g.nc, g.nc, g.nw};
+        const double *dev[4] = {nullptr, nullptr, nullptr, nullptr};
+        for (int n = 0; n < 4; ++n) {
+            if (!src[n]) continue;
+            if (is_device) { dev[n] = src[n]; continue; }
+            cudaError_t e = cudaMemcpyAsync(stage[n], src[n], len[n] * sizeof(double), cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "copy initial field");
+            dev[n] = stage[n];
+        }
+        launch_anel_init(g, dev[0], h->st.r, h->st.t, s);
+        launch_init_faces(g, dev[1], dev[2], dev[3], h->st.r, h->st.u, h->st.v, h->st.w, s);
+        cudaMemsetAsync(h->pa, 0, g.nc * sizeof(double), s);
+        launch_anel_project(g, anel_work(h), 1.0, h->st.u, h->st.v, h->st.w, 0, s);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && !is_device) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "anelastic initial state");
+        h->have_state = true;
+        return ERF_OK;
+    }
     const Geo &g = h->geo;
     cudaStream_t s = h->user;
     if (h->mixed) {
@@ -693,6 +922,8 @@ extern "C" erf_status erf_set_initial(erf_handle *h, const double *dtheta, const
     launch_set_initial(g, dev[0], dev[1], dev[2], dev[3], h->st.r, h->st.t, h->st.u, h->st.v, h->st.w, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "set_initial kernels");
+    h->have_state = true;
+    if (capture_reference(h) != ERF_OK) return ERF_ECUDA;
     if (!is_device) {
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(h, e, "set_initial sync");
@@ -717,6 +948,12 @@ static double *field_dev(erf_handle *h, int f, long long &n) {
     case ERF_BASE_THETA: n = g.terrain ? g.nc : g.nz; return h->th0;
     case ERF_RHOPHI: return h->tphi;
     case ERF_RHOTKE: return h->tke;
+    case ERF_RHOQV: return h->rq[0];
+    case ERF_RHOQC: return h->rq[1];
+    case ERF_RHOQR: return h->rq[2];
+    case ERF_PRECIP: n = g.nxy; return h->precip;
+    case ERF_BASE_QV: n = g.terrain ? g.nc : g.nz; return h->qv0;
+    case ERF_P_ANELASTIC: return h->pa;
     }
     return nullptr;
 }
@@ -725,7 +962,8 @@ extern "C" erf_status erf_set_state(erf_handle *h, int32_t field, const void *sr
                                     int32_t src_dtype) {
     if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
     if ((field < ERF_RHO || field > ERF_RHOW) && !(field == ERF_RHOPHI && has_tracer(h)) &&
-        !(field == ERF_RHOTKE && h->tke))
+        !(field == ERF_RHOTKE && h->tke) && !(field >= ERF_RHOQV && field <= ERF_RHOQR && h->rq[0]) &&
+        !(field == ERF_P_ANELASTIC && h->pa))
         return fail(h, ERF_EINVAL, "field not settable");
     if (!src) return fail(h, ERF_EINVAL, "src is NULL");
     if (src_dtype != ERF_F64 && src_dtype != ERF_F32) return fail(h, ERF_EINVAL, "bad dtype");
@@ -830,7 +1068,8 @@ extern "C" erf_status erf_get_state(erf_handle *h, int32_t field, void *dst, int
                                     int32_t dst_dtype) {
     if (!h) return fail(nullptr, ERF_EINVAL, "NULL handle");
     if ((field < ERF_RHO || field > ERF_BASE_THETA) && !(field == ERF_RHOPHI && has_tracer(h)) &&
-        !(field == ERF_RHOTKE && h->tke))
+        !(field == ERF_RHOTKE && h->tke) && !(field >= ERF_RHOQV && field <= ERF_BASE_QV && h->rq[0]) &&
+        !(field == ERF_P_ANELASTIC && h->pa))
         return fail(h, ERF_EINVAL, "bad field");
     if (!dst) return fail(h, ERF_EINVAL, "dst is NULL");
     if (dst_dtype != ERF_F64 && dst_dtype != ERF_F32) return fail(h, ERF_EINVAL, "bad dtype");

@@ -16,6 +16,9 @@ constexpr double CPD = 1004.5;         // specific heat at constant pressure
 constexpr double CVD = CPD - RD;
 constexpr double GAMMA = CPD / CVD;
 constexpr double KAPPA = 0.4;          // von Karman constant (MOST)
+constexpr double RV = 461.5;           // water-vapour gas constant (moist air, Sec. 2.1)
+constexpr double LV = 2.5e6;           // latent heat of vaporisation (Kessler microphysics, Sec. 2.4)
+constexpr double RHOW = 1000.0;        // liquid-water density (surface precipitation depth)
 
 struct Geo {
     int nx, ny, nz;
@@ -43,6 +46,7 @@ struct Geo {
     const double *g4yq;
     // hydrostatic base state: [nz][ny][nx] with terrain, [nz] when flat
     const double *rho0, *th0, *p0;
+    const double *qv0;     // base-state water vapour (moist handles; same layout as rho0), else null
     // reciprocal 3D metrics, terrain only ([nz][ny][nx]; null on flat grids): 1/H at cells,
     // x-faces and y-faces, 1/(z_c(k) - z_c(k-1)) at w-faces (k >= 1), and 1/(z_c(ku) - z_c(kl))
     // of the centred vertical difference at cells (kl = max(k-1, 0), ku = min(k+1, nz-1)).
@@ -60,7 +64,29 @@ struct Phys {
     // above ray_zd; ray_fields bitmask 1 u, 2 v, 4 w, 8 theta (0 = off)
     double ray_tau, ray_zd, ray_zt;
     int ray_fields;
+    // moisture (Sec. 2.1, App. C): rho q_v, rho q_c, rho q_r of the stage state (null when dry)
+    const double *rqv, *rqc, *rqr;
+    int moist;
+    // lateral relaxation zones (open x boundaries): rate relax_tau sin^2(pi/2 (1 - d/relax_w))
+    // within relax_w of an x-edge of the domain of length Lx (relax_tau = 0: off)
+    double relax_tau, relax_w, Lx;
+    int anelastic;    // 1: anelastic equation set (Sec. 2.2): buoyancy rho0 g (theta - theta0) / theta0
 };
+
+// mixing ratios of the stage state at a cell: q_v + q_c (the 1/(1 + q_v + q_c) of Eq. mom) and
+// (rho_m - rho_d) / rho_d = q_v + q_c + q_r; 0 on dry handles
+__device__ __forceinline__ double q_vc(const Phys &ph, long long c, double rho) {
+    return ph.moist ? (__ldg(ph.rqv + c) + __ldg(ph.rqc + c)) / rho : 0.0;
+}
+__device__ __forceinline__ double q_t(const Phys &ph, long long c, double rho) {
+    return ph.moist ? (__ldg(ph.rqv + c) + __ldg(ph.rqc + c) + __ldg(ph.rqr + c)) / rho : 0.0;
+}
+__device__ __forceinline__ double relax_rate(const Phys &ph, double x) {
+    const double d = fmin(x, ph.Lx - x);
+    if (!(ph.relax_tau > 0.0) || !(d < ph.relax_w)) return 0.0;
+    const double s = sin(0.5 * 3.141592653589793 * (1.0 - d / ph.relax_w));
+    return ph.relax_tau * (s * s);
+}
 
 // Rayleigh damping rate at physical height z (0 below the damping layer)
 __device__ __forceinline__ double ray_rate(const Phys &ph, double z) {

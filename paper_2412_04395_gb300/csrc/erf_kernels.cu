@@ -114,29 +114,58 @@ __device__ __forceinline__ double rho_from(double p, double th) {
 // Hydrostatic base state per column (Sec. 3.8): trapezoidal dp/dz = -rho g between cell
 // centres, starting from p_s at z = 0, each level solved by Newton-Raphson for p; then
 // p0 is re-evaluated by the EOS of rho0 theta0 so the undisturbed state has p' = 0.
-__global__ void k_base_state(Geo g, ThetaProfile tp, double p_s, double grav, double *rho0, double *th0, double *p0) {
+// base-state water vapour q_v0(z): piecewise-linear sounding, constant beyond its ends
+struct QvProfile {
+    int n;
+    const double *kz, *kq;
+};
+__device__ double qv0_of(const QvProfile &qp, double z) {
+    if (qp.n <= 0) return 0.0;
+    if (z <= qp.kz[0]) return qp.kq[0];
+    for (int m = 1; m < qp.n; ++m)
+        if (z <= qp.kz[m]) {
+            double t = (z - qp.kz[m - 1]) / (qp.kz[m] - qp.kz[m - 1]);
+            return qp.kq[m - 1] + t * (qp.kq[m] - qp.kq[m - 1]);
+        }
+    return qp.kq[qp.n - 1];
+}
+// total density rho_d (1 + q_v) from p, theta_d and q_v by the moist EOS of Sec. 2.1
+__device__ __forceinline__ double rho_m_from(double p, double th, double q) {
+    return rho_from(p, th * (1.0 + (RV / RD) * q)) * (1.0 + q);
+}
+
+__global__ void k_base_state(Geo g, ThetaProfile tp, QvProfile qp, double p_s, double grav, double *rho0,
+                             double *th0, double *p0, double *qv0) {
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     long long ncol = g.terrain ? g.nxy : 1;
     if (n >= ncol) return;
     int i = (int)(n % g.nx), j = (int)(n / g.nx);
-    double p_prev = p_s, r_prev = rho_from(p_s, theta0_of(tp, 0.0)), z_prev = 0.0;
+    const bool moist = qv0 != nullptr;
+    double p_prev = p_s, z_prev = 0.0;
+    double r_prev = moist ? rho_m_from(p_s, theta0_of(tp, 0.0), qv0_of(qp, 0.0)) : rho_from(p_s, theta0_of(tp, 0.0));
     for (int k = 0; k < g.nz; ++k) {
         double z = zc(g, i, j, k), th = theta0_of(tp, z), dz = z - z_prev;
+        double q = moist ? qv0_of(qp, z) : 0.0;
         double p = p_prev - grav * dz * r_prev;
         for (int it = 0; it < 50; ++it) {
-            double r = rho_from(p, th);
+            double r = moist ? rho_m_from(p, th, q) : rho_from(p, th);
             double f = p - p_prev + 0.5 * grav * dz * (r_prev + r);
             double df = 1.0 + 0.5 * grav * dz * r / (GAMMA * p);
             double dp = -f / df;
             p += dp;
             if (fabs(dp) <= 1.0e-14 * fabs(p)) break;
         }
-        double r = rho_from(p, th);
+        double r = moist ? rho_m_from(p, th, q) : rho_from(p, th);
         long long b = g.terrain ? cix(g, i, j, k) : k;
-        rho0[b] = r;
+        rho0[b] = r;          // total density on moist handles
         th0[b] = th;
         double pp, pie;
-        eos_pi(r * th, pp, pie);
+        if (moist) {
+            qv0[b] = q;
+            eos_pi(r / (1.0 + q) * th * (1.0 + (RV / RD) * q), pp, pie);
+        } else {
+            eos_pi(r * th, pp, pie);
+        }
         p0[b] = pp;
         p_prev = p; r_prev = r; z_prev = z;
     }
@@ -152,6 +181,25 @@ __global__ void k_init_cells(Geo g, const double *dth, double *rho, double *rt) 
     double t = g.rho0[b] * g.th0[b];
     rt[c] = t;
     rho[c] = g.rho0[b] * (g.th0[b] / th);   // rho0 theta0 / theta, exactly rho0 when dtheta = 0
+}
+// moist handles: water vapour q_v at cells (null: the base state's q_v0), pressure unchanged,
+// rho_d theta_d (1 + (R_v/R_d) q_v) = rho_d0 theta0 (1 + (R_v/R_d) q_v0), rho_d0 = rho0 / (1 + q_v0);
+// no cloud or rain
+__global__ void k_init_cells_moist(Geo g, const double *dth, const double *qv, double *rho, double *rt,
+                                   double *rqv, double *rqc, double *rqr) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    long long b = bix(g, i, j, k);
+    double th = g.th0[b] + (dth ? dth[c] : 0.0);
+    double q0 = g.qv0[b], q = qv ? qv[c] : q0;
+    double rd0 = g.rho0[b] / (1.0 + q0), f = (1.0 + (RV / RD) * q0) / (1.0 + (RV / RD) * q);
+    rt[c] = rd0 * g.th0[b] * f;
+    double r = rd0 * (g.th0[b] / th) * f;
+    rho[c] = r;
+    rqv[c] = r * q;
+    rqc[c] = 0.0;
+    rqr[c] = 0.0;
 }
 __global__ void k_init_faces(Geo g, const double *u, const double *v, const double *w, const double *rho,
                              double *ru, double *rv, double *rw) {
@@ -187,14 +235,16 @@ __global__ void k_wall_bc(Geo g, const double *ru, const double *rv, double *rw)
 // ------------------------------------------------------------------ stage begin
 // EOS at the stage state; X'' = S^n - S^t; Theta''_prev = Theta''; Omega'' = W'' - metric shift
 __global__ void k_stage_begin(Geo g, CF5 sn, CF5 st, F5 x, double *pp, double *pi, double *th,
-                              double *Tprev, double *Om) {
+                              double *Tprev, double *Om, const double *rqv) {
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= g.nw) return;
     int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / g.nxy);
     if (k < g.nz) {
         double rt = st.t[n], rho = st.r[n];
         double p, pie;
-        eos_pi(rt, p, pie);
+        // the moist EOS (Sec. 2.1) with the stage's q_v, else the dry one
+        if (rqv) eos_pi(rt * (1.0 + (RV / RD) * (rqv[n] / rho)), p, pie);
+        else eos_pi(rt, p, pie);
         long long b = bix(g, i, j, k);
         pp[n] = p - g.p0[b];
         pi[n] = pie;
@@ -489,6 +539,126 @@ __global__ void k_tke_diff(Geo g, const double *mu, const double *rtke, const do
     src[c] += (fxp - fxm) * g.rdx + (fyp - fym) * g.rdy + (fzp - fzm) * g.rdzeta[k];
 }
 
+// moisture diffusion (Eqs. nonprecip, precip): src_q = div(rho alpha_q grad q) for q_v, q_c, q_r,
+// rho alpha_q = hs * hk (the heat diffusivity of the closure), face coefficient the mean of the
+// two cells, no flux through the walls.  Flat grids.
+struct Q3 {
+    const double *q[3];
+};
+struct Q3w {
+    double *q[3];
+};
+__global__ void k_moist_diff(Geo g, const double *hk, double hs, Q3 rq, const double *rho, Q3w src) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    const double h0 = __ldg(hk + c);
+    const double hxm = cval(g, hk, i - 1, j, k), hxp = cval(g, hk, i + 1, j, k);
+    const double hym = cval(g, hk, i, j - 1, k), hyp = cval(g, hk, i, j + 1, k);
+    for (int q = 0; q < 3; ++q) {
+        auto qv = [&](int ii, int jj, int kk) {
+            const long long a = cixw(g, ii, jj, kk);
+            return __ldg(rq.q[q] + a) / __ldg(rho + a);
+        };
+        const double q0 = qv(i, j, k);
+        const double fxm = 0.5 * (hxm + h0) * hs * (q0 - qv(i - 1, j, k)) * g.rdx;
+        const double fxp = 0.5 * (h0 + hxp) * hs * (qv(i + 1, j, k) - q0) * g.rdx;
+        const double fym = 0.5 * (hym + h0) * hs * (q0 - qv(i, j - 1, k)) * g.rdy;
+        const double fyp = 0.5 * (h0 + hyp) * hs * (qv(i, j + 1, k) - q0) * g.rdy;
+        double fzm = 0.0, fzp = 0.0;
+        if (k > 0) fzm = 0.5 * (__ldg(hk + c - g.nxy) + h0) * hs * (q0 - qv(i, j, k - 1)) * g.rdzc[k];
+        if (k < g.nz - 1) fzp = 0.5 * (h0 + __ldg(hk + c + g.nxy)) * hs * (qv(i, j, k + 1) - q0) * g.rdzc[k + 1];
+        src.q[q][c] = (fxp - fxm) * g.rdx + (fyp - fym) * g.rdy + (fzp - fzm) * g.rdzeta[k];
+    }
+}
+
+// lateral relaxation zones (open x boundaries; Sec. 3.8 nudging toward boundary data, here the
+// initial state): -tau_r(d) (S - S_ref) in every slow tendency and moisture source, d the distance
+// of the point from the nearer x-edge (cells at their centres, x-faces at x = i dx)
+__global__ void k_relax(Geo g, Phys ph, CF5 st, CF5 ref, F5 R, Q3 rq, Q3 rqref, Q3w qsrc) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.nw) return;
+    int i = (int)(n % g.nx), k = (int)(n / g.nxy);
+    const double tc = relax_rate(ph, (i + 0.5) * g.dx), tf = relax_rate(ph, i * g.dx);
+    if (k < g.nz) {
+        R.r[n] -= tc * (st.r[n] - ref.r[n]);
+        R.t[n] -= tc * (st.t[n] - ref.t[n]);
+        R.u[n] -= tf * (st.u[n] - ref.u[n]);
+        R.v[n] -= tc * (st.v[n] - ref.v[n]);
+        if (ph.moist)
+            for (int q = 0; q < 3; ++q) qsrc.q[q][n] -= tc * (rq.q[q][n] - rqref.q[q][n]);
+    }
+    if (k >= 1 && k < g.nz) R.w[n] -= tc * (st.w[n] - ref.w[n]);
+}
+
+// One time-split Kessler step after the RK3 step (Kessler 1969; Klemp & Wilhelmson 1978), one
+// thread per column, the dry density unchanged:
+//   1. rain falls one explicit upwind step: F = rho q_r V through each cell's bottom face,
+//      V = 36.34 (1e-3 rho q_r)^0.1346 (rho_0 / rho)^(1/2) m/s (the cgs form V = 3634 (rho q_r)^0.1346
+//      (rho_0/rho)^(1/2) cm/s, rho q_r in g/cm^3, rho_0 the base dry density at the ground); what
+//      leaves the lowest cell adds F dt / rho_water to the surface accumulation;
+//   2. autoconversion 1e-3 (q_c - 1e-3)^+ and accretion 2.2 q_c q_r^0.875 (1/s) move cloud to rain;
+//   3. saturation adjustment in one linearised step (Soong & Ogura 1973) with the Tetens q_vs and
+//      its slope q_vs 4098.17 / (T - 35.86)^2 at T = theta pi (pi from the moist EOS before the step);
+//      rain evaporates min(dt E_r, (-s - q_c)^+, q_r), E_r = (1/rho) (1 - q_v/q_vs) C (rho q_r)^0.525
+//      / (5.4e5 + 2.55e6 / (p q_vs)), C = 1.6 + 124.9 (rho q_r)^0.2046 (rho in g/cm^3, p in mb);
+//      theta gains L_v / (c_p pi) (condensation - evaporation).
+// Every quantity is applied as an increment of the conserved variables.
+__global__ void k_kessler(Geo g, double dt, double *rt, const double *rho, double *rqv, double *rqc, double *rqr,
+                          double *precip) {
+    long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (col >= g.nxy) return;
+    const int i = (int)(col % g.nx), j = (int)(col / g.nx);
+    const long long b0 = bix(g, i, j, 0);
+    const double rho_sfc = g.rho0[b0] / (1.0 + g.qv0[b0]);
+    auto flux = [&](int k) {   // rho q_r V at the bottom face of cell k
+        if (k >= g.nz) return 0.0;
+        const long long c = cix(g, i, j, k);
+        const double r = rho[c], rr = rqr[c], qr = rr / r;
+        if (!(qr > 0.0)) return 0.0;
+        return rr * (36.34 * pow(1.0e-3 * r * qr, 0.1346) * sqrt(rho_sfc / r));
+    };
+    // 1. sedimentation: every face flux from the rain before the fall
+    double f_below = flux(0);
+    precip[col] += dt * f_below / RHOW;
+    for (int k = 0; k < g.nz; ++k) {
+        const double f_above = flux(k + 1);
+        rqr[cix(g, i, j, k)] += dt * (f_above - f_below) * (g.terrain ? rHc(g, i, j, k) : g.rdzeta[k]);
+        f_below = f_above;
+    }
+    for (int k = 0; k < g.nz; ++k) {
+        const long long c = cix(g, i, j, k);
+        const double r = rho[c], th = rt[c] / r;
+        const double qv = rqv[c] / r;
+        double qc = rqc[c] / r, qr = rqr[c] / r;
+        double p, pie;
+        eos_pi(rt[c] * (1.0 + (RV / RD) * qv), p, pie);
+        // 2. autoconversion and accretion
+        double ar = fmax(1.0e-3 * (qc - 1.0e-3), 0.0);
+        double cr = qr > 0.0 ? 2.2 * qc * pow(qr, 0.875) : 0.0;
+        double prod = fmin(dt * (ar + cr), qc);
+        qc -= prod;
+        qr += prod;
+        // 3. saturation adjustment and rain evaporation
+        const double T = th * pie;
+        const double es = 610.78 * exp(17.27 * (T - 273.16) / (T - 35.86));
+        const double qvs = (RD / RV) * es / (p - es);
+        const double sadj = (qv - qvs) / (1.0 + qvs * LV * 4098.17 / (CPD * (T - 35.86) * (T - 35.86)));
+        double ern = 0.0;
+        if (qr > 0.0 && qv < qvs) {
+            const double rg = 1.0e-3 * r, X = rg * qr;
+            const double C = 1.6 + 124.9 * pow(X, 0.2046);
+            ern = dt * ((1.0 / rg) * (1.0 - qv / qvs) * C * pow(X, 0.525) / (5.4e5 + 2.55e6 / ((1.0e-2 * p) * qvs)));
+        }
+        ern = fmin(fmin(ern, fmax(-sadj - qc, 0.0)), qr);
+        const double cond = sadj > -qc ? sadj : -qc;
+        rt[c] += r * (LV / (CPD * pie) * (cond - ern));
+        rqv[c] += r * (ern - cond);
+        rqc[c] += r * (cond - prod);
+        rqr[c] += r * (prod - ern);
+    }
+}
+
 // ------------------------------------------------------------------ slow tendencies
 
 // WENO5-JS / WENO5-Z face value in FP64 (same candidates and weights as weno5<T>), arranged for
@@ -661,6 +831,7 @@ __global__ void k_rhs_u(Geo g, Phys ph, CF5 st, const double *pp, const double *
         double d1 = (cval(g, pp, i - 1, j, ku) - cval(g, pp, i - 1, j, kl)) * rdz2c(g, i - 1, j, k);
         px -= hxi_x2(g, i, j, k) * (d0 + d1);
     }
+    if (ph.moist) px /= 1.0 + 0.5 * (q_vc(ph, cixw(g, i - 1, j, k), cval(g, st.r, i - 1, j, k)) + q_vc(ph, c, st.r[c]));
     r -= px;
     if (ph.f_cor != 0.0) {
         double rvx = 0.25 * (cval(g, st.v, i - 1, j, k) + cval(g, st.v, i, j, k) + cval(g, st.v, i - 1, j + 1, k) + cval(g, st.v, i, j + 1, k));
@@ -689,6 +860,7 @@ __global__ void k_rhs_v(Geo g, Phys ph, CF5 st, const double *pp, const double *
         double d1 = (cval(g, pp, i, j - 1, ku) - cval(g, pp, i, j - 1, kl)) * rdz2c(g, i, j - 1, k);
         py -= heta_y2(g, i, j, k) * (d0 + d1);
     }
+    if (ph.moist) py /= 1.0 + 0.5 * (q_vc(ph, cixw(g, i, j - 1, k), cval(g, st.r, i, j - 1, k)) + q_vc(ph, c, st.r[c]));
     r -= py;
     if (ph.f_cor != 0.0) {
         double rux = 0.25 * (cval(g, st.u, i, j - 1, k) + cval(g, st.u, i + 1, j - 1, k) + cval(g, st.u, i, j, k) + cval(g, st.u, i + 1, j, k));
@@ -714,9 +886,27 @@ __global__ void k_rhs_w(Geo g, Phys ph, CF5 st, const double *pp, const double *
     double rdz = rdzcw(g, i, j, k);
     double r = -div * rdz;
     long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1);
-    r -= (pp[c] - pp[cm]) * rdz;
     double b0 = g.rho0[bix(g, i, j, k - 1)], b1 = g.rho0[bix(g, i, j, k)];
-    r += 0.5 * (-ph.g * (st.r[cm] - b0) - ph.g * (st.r[c] - b1));
+    if (ph.anelastic) {
+        // Sec. 2.2: B = rho0 g (theta - theta0) / theta0, the face mean of the two cells
+        const double t0m = g.th0[bix(g, i, j, k - 1)], t0c = g.th0[bix(g, i, j, k)];
+        const double Bm = b0 * ph.g * (st.t[cm] / st.r[cm] - t0m) / t0m;
+        const double Bc = b1 * ph.g * (st.t[c] / st.r[c] - t0c) / t0c;
+        r -= (pp[c] - pp[cm]) * rdz;
+        r += 0.5 * (Bm + Bc);
+    } else if (ph.moist) {
+        // Eq. mom: (-dp'/dz + B) / (1 + q_v + q_c), B of the total density rho_d (1 + q_v + q_c + q_r)
+        const double rm = st.r[cm] + (__ldg(ph.rqv + cm) + __ldg(ph.rqc + cm) + __ldg(ph.rqr + cm));
+        const double rc = st.r[c] + (__ldg(ph.rqv + c) + __ldg(ph.rqc + c) + __ldg(ph.rqr + c));
+        const double B = 0.5 * (-ph.g * (rm - b0) - ph.g * (rc - b1));
+        const double f = 1.0 + 0.5 * (q_vc(ph, cm, st.r[cm]) + q_vc(ph, c, st.r[c]));
+        // the dry path's order of operations (exact for f = 1: no water, the dry result)
+        r -= (pp[c] - pp[cm]) * rdz / f;
+        r += B / f;
+    } else {
+        r -= (pp[c] - pp[cm]) * rdz;
+        r += 0.5 * (-ph.g * (st.r[cm] - b0) - ph.g * (st.r[c] - b1));
+    }
     if (ph.ray_fields & 4) {   // Rayleigh damping toward w = 0 at the w-face height (Sec. 3.7)
         const double zw = g.zetac[k - 1] + 0.5 * g.dzeta[k - 1] + (g.terrain ? g.s[k] * g.hc[ij2(g, i, j)] : 0.0);
         r -= ray_rate(ph, zw) * st.w[n];
@@ -748,7 +938,7 @@ struct TriK {
     double hrdx, hrdy;  // 1 / (2 dx), 1 / (2 dy): the face mean of theta and the substeps' 1/dx, 1/dy
 };
 __global__ void k_tri_build(Geo g, const double *rho, const double *rt, const double *pi, const double *th, TriK tk,
-                            Tri tr, double *TX, double *TY, double *PX, double *PY, double *THW) {
+                            Tri tr, double *TX, double *TY, double *PX, double *PY, double *THW, Phys ph) {
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= g.nxy) return;
     int i = (int)(n % g.nx), j = (int)(n / g.nx);
@@ -762,6 +952,11 @@ __global__ void k_tri_build(Geo g, const double *rho, const double *rt, const do
         TY[c] = Hy(g, i, j, k) * (tk.hrdy * (cval(g, th, i, j - 1, k) + thc));
         PX[c] = tk.dpx * (cval(g, pi, i - 1, j, k) + pic);
         PY[c] = tk.dpx * (cval(g, pi, i, j - 1, k) + pic);
+        if (ph.moist) {   // App. C: gamma R_d pi^t / (1 + q_v^t + q_c^t) at the face
+            const double qc0 = q_vc(ph, c, rho[c]);
+            PX[c] /= 1.0 + 0.5 * (q_vc(ph, cixw(g, i - 1, j, k), cval(g, rho, i - 1, j, k)) + qc0);
+            PY[c] /= 1.0 + 0.5 * (q_vc(ph, cixw(g, i, j - 1, k), cval(g, rho, i, j - 1, k)) + qc0);
+        }
     };
     face_factors(0);
     double th_m = th[cix(g, i, j, 0)];
@@ -778,6 +973,11 @@ __global__ void k_tri_build(Geo g, const double *rho, const double *rt, const do
         double Spi = pim + pic;
         double Cpg = tk.cpg * Spi * rdzcw(g, i, j, k);
         double Cb = tk.kgb * (rho[cm] + rho[c]) * rcp_d(Spi);
+        if (ph.moist) {
+            // App. C: the pressure term over 1 + q_v + q_c, the Theta'' buoyancy times rho_d / rho_m
+            Cpg /= 1.0 + 0.5 * (q_vc(ph, cm, rho[cm]) + q_vc(ph, c, rho[c]));
+            Cb /= 1.0 + 0.5 * (q_t(ph, cm, rho[cm]) + q_t(ph, c, rho[c]));
+        }
         double rrt_c = rcp_d(rt[c]), rHk = rHc(g, i, j, k);
         double P = fma(Cb * pic, rrt_c, -Cpg);
         double Q = fma(Cb * pim, rrt_m, Cpg);
@@ -1144,10 +1344,23 @@ void launch_terrain_recip(const Geo &g, double *Hx3, double *Hy3, double *rH3, d
     LAUNCH("terrain_recip", s, k_terrain_recip<<<nblk(g.nc, BS), BS, 0, s>>>(g, Hx3, Hy3, rH3, rHx3, rHy3, rdzw3, rdz2));
 }
 void launch_base_state(const Geo &g, int n_knots, const double *kz, const double *kt, double theta_s, double N,
-                       double p_s, double grav, double *rho0, double *th0, double *p0, cudaStream_t s) {
+                       double p_s, double grav, double *rho0, double *th0, double *p0, cudaStream_t s,
+                       int n_qknots, const double *qz, const double *qk, double *qv0) {
     ThetaProfile tp{n_knots, kz, kt, theta_s, N, grav};
+    QvProfile qp{n_qknots, qz, qk};
     long long ncol = g.terrain ? g.nxy : 1;
-    LAUNCH("base_state", s, k_base_state<<<nblk(ncol, 128), 128, 0, s>>>(g, tp, p_s, grav, rho0, th0, p0));
+    LAUNCH("base_state", s, k_base_state<<<nblk(ncol, 128), 128, 0, s>>>(g, tp, qp, p_s, grav, rho0, th0, p0, qv0));
+}
+void launch_set_initial_moist(const Geo &g, const double *dth, const double *qv, const double *u, const double *v,
+                              const double *w, double *rho, double *rt, double *ru, double *rv, double *rw,
+                              double *rqv, double *rqc, double *rqr, cudaStream_t s) {
+    LAUNCH("init_cells", s, k_init_cells_moist<<<nblk(g.nc, BS), BS, 0, s>>>(g, dth, qv, rho, rt, rqv, rqc, rqr));
+    LAUNCH("init_faces", s, k_init_faces<<<nblk(g.nw, BS), BS, 0, s>>>(g, u, v, w, rho, ru, rv, rw));
+    LAUNCH("wall_bc", s, k_wall_bc<<<nblk(g.nxy, BS), BS, 0, s>>>(g, ru, rv, rw));
+}
+void launch_kessler(const Geo &g, double dt, double *rt, const double *rho, double *rqv, double *rqc, double *rqr,
+                    double *precip, cudaStream_t s) {
+    LAUNCH("kessler", s, k_kessler<<<nblk(g.nxy, 128), 128, 0, s>>>(g, dt, rt, rho, rqv, rqc, rqr, precip));
 }
 void launch_set_initial(const Geo &g, const double *dth, const double *u, const double *v, const double *w,
                         double *rho, double *rt, double *ru, double *rv, double *rw, cudaStream_t s) {
@@ -1155,16 +1368,22 @@ void launch_set_initial(const Geo &g, const double *dth, const double *u, const 
     LAUNCH("init_faces", s, k_init_faces<<<nblk(g.nw, BS), BS, 0, s>>>(g, u, v, w, rho, ru, rv, rw));
     LAUNCH("wall_bc", s, k_wall_bc<<<nblk(g.nxy, BS), BS, 0, s>>>(g, ru, rv, rw));
 }
+void launch_init_faces(const Geo &g, const double *u, const double *v, const double *w, const double *rho,
+                       double *ru, double *rv, double *rw, cudaStream_t s) {
+    LAUNCH("init_faces", s, k_init_faces<<<nblk(g.nw, BS), BS, 0, s>>>(g, u, v, w, rho, ru, rv, rw));
+    LAUNCH("wall_bc", s, k_wall_bc<<<nblk(g.nxy, BS), BS, 0, s>>>(g, ru, rv, rw));
+}
 void launch_wall_bc(const Geo &g, const double *ru, const double *rv, double *rw, cudaStream_t s) {
     LAUNCH("wall_bc", s, k_wall_bc<<<nblk(g.nxy, BS), BS, 0, s>>>(g, ru, rv, rw));
 }
 void launch_stage_begin(const Geo &g, CF5 sn, CF5 st, F5 x, double *pp, double *pi, double *th, double *Tp,
-                        double *Om, cudaStream_t s) {
-    LAUNCH("stage_begin", s, k_stage_begin<<<nblk(g.nw, BS), BS, 0, s>>>(g, sn, st, x, pp, pi, th, Tp, Om));
+                        double *Om, cudaStream_t s, const double *rqv) {
+    LAUNCH("stage_begin", s, k_stage_begin<<<nblk(g.nw, BS), BS, 0, s>>>(g, sn, st, x, pp, pi, th, Tp, Om, rqv));
 }
 void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, double *pp, const double *th, Prep pr,
                      double *ux, double *vy, double *wz, double *mfx, double *mfy, double *rom, double *mu,
-                     double *flux, F5 R, cudaStream_t s, const double *rtke, double *muh, double *tke_src) {
+                     double *flux, F5 R, cudaStream_t s, const double *rtke, double *muh, double *tke_src,
+                     const MoistIO *mio) {
     LAUNCH("prep", s, k_prep<<<nblk(g.nw, BS), BS, 0, s>>>(g, st, ux, vy, wz, mfx, mfy, rom));
     const int visc = (ph.closure == 1 || ph.closure == 2 || ph.closure == 4) ? 1 : 0;
     const int sgs = (visc || ph.surface == 1) ? 1 : 0;
@@ -1204,6 +1423,17 @@ void launch_slow_rhs(const Geo &g, const Phys &ph, CF5 st, double *pp, const dou
         const double hs = ph.closure == 4 ? 1.0 : ph.rPr_t;
         LAUNCH("sgs_div", s, k_sgs_div<<<g3w, 128, 0, s>>>(g, ph, hk, hs, t11, t22, t33, st.r, th, visc, e12, e13, e23,
                                                            R));
+        if (mio && ph.moist && visc)
+            LAUNCH("moist_diff", s, k_moist_diff<<<nblk(g.nc, BS), BS, 0, s>>>(g, hk, hs, Q3{{ph.rqv, ph.rqc, ph.rqr}}, st.r,
+                                                                           Q3w{{mio->src[0], mio->src[1], mio->src[2]}}));
+    }
+    if (mio && ph.moist && !(sgs && visc))
+        for (int q = 0; q < 3; ++q) cudaMemsetAsync(mio->src[q], 0, g.nc * sizeof(double), s);
+    if (mio && mio->ref[0]) {
+        CF5 ref{mio->ref[0], mio->ref[1], mio->ref[2], mio->ref[3], mio->ref[4]};
+        Q3 rq{{ph.rqv, ph.rqc, ph.rqr}}, rr{{mio->ref[5], mio->ref[6], mio->ref[7]}};
+        Q3w qs{{mio->src[0], mio->src[1], mio->src[2]}};
+        LAUNCH("relax", s, k_relax<<<nblk(g.nw, BS), BS, 0, s>>>(g, ph, st, ref, R, rq, rr, qs));
     }
 }
 void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const double *rt, const double *pi,
@@ -1218,7 +1448,7 @@ void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const dou
     tk.hrdx = 0.5 * g.rdx;
     tk.hrdy = 0.5 * g.rdy;
     LAUNCH("tri_build", s, k_tri_build<<<nblk(g.nxy, 128), 128, 0, s>>>(g, rho, rt, pi, th, tk, tr, TX, TY, PX, PY,
-                                                                        THW));
+                                                                        THW, ph));
 }
 void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *PX, const double *PY, const double *thw,
                     const double *TX, const double *TY, CF5 R, F5 x, double *Om, double *Tp, double *X0, double *Y0,

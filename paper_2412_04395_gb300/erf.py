@@ -18,7 +18,8 @@ ERF_OK, ERF_EINVAL, ERF_ENOSPACE, ERF_ECUDA, ERF_ENONFINITE, ERF_ESTATE, ERF_EUN
 STATUS_NAMES = {0: "ERF_OK", -1: "ERF_EINVAL", -2: "ERF_ENOSPACE", -3: "ERF_ECUDA", -4: "ERF_ENONFINITE",
                 -5: "ERF_ESTATE", -6: "ERF_EUNSUPPORTED"}
 FIELDS = {"rho": 0, "rhotheta": 1, "rhou": 2, "rhov": 3, "rhow": 4,
-          "base_rho": 5, "base_p": 6, "base_theta": 7, "rhophi": 8, "rhotke": 9}
+          "base_rho": 5, "base_p": 6, "base_theta": 7, "rhophi": 8, "rhotke": 9,
+          "rhoqv": 10, "rhoqc": 11, "rhoqr": 12, "precip": 13, "base_qv": 14, "p_anelastic": 15}
 ERF_F64, ERF_F32 = 0, 1
 ERF_OPT_TMA_STENCILS = 1
 ERF_OPT_COLUMN_FUSION = 2
@@ -30,7 +31,8 @@ EXPORTS = ["erf_workspace_bytes", "erf_init_grid", "erf_set_initial", "erf_set_s
            "erf_column_stats", "erf_standardise", "erf_set_closure_weights", "erf_closure_features",
            "erf_closure_fields", "erf_filter_state", "erf_set_tracer_initial", "erf_set_option",
            "erf_get_option", "erf_selftest_wait_timeout", "erf_selftest_tensor_cores",
-           "erf_column_block_bytes", "erf_pack_columns", "erf_unpack_columns"]
+           "erf_column_block_bytes", "erf_pack_columns", "erf_unpack_columns", "erf_set_initial_moist",
+           "erf_capture_reference"]
 
 
 class ErfError(RuntimeError):
@@ -57,7 +59,10 @@ class Config(C.Structure):
                 ("theta_s", C.c_double), ("brunt_N", C.c_double), ("p_s", C.c_double),
                 ("n_knots", C.c_int32), ("knot_z", C.POINTER(C.c_double)),
                 ("knot_theta", C.POINTER(C.c_double)), ("tracer", C.c_int32), ("mom_adv", C.c_int32),
-                ("ray_tau", C.c_double), ("ray_zd", C.c_double), ("ray_fields", C.c_int32)]
+                ("ray_tau", C.c_double), ("ray_zd", C.c_double), ("ray_fields", C.c_int32),
+                ("moist", C.c_int32), ("n_qknots", C.c_int32), ("qknot_z", C.POINTER(C.c_double)),
+                ("qknot_v", C.POINTER(C.c_double)), ("relax_tau", C.c_double), ("relax_width", C.c_double),
+                ("anelastic", C.c_int32)]
 
 
 class Diag(C.Structure):
@@ -110,6 +115,8 @@ def load_library(path: str = LIB_PATH):
     L.erf_closure_features.argtypes = [vp, vp]
     L.erf_closure_fields.argtypes = [vp, vp, C.POINTER(C.c_uint32)]
     L.erf_filter_state.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp, vp]
+    L.erf_set_initial_moist.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int32]
+    L.erf_capture_reference.argtypes = [vp]
     L.erf_column_block_bytes.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]
     L.erf_pack_columns.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp]
     L.erf_unpack_columns.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp]
@@ -121,7 +128,8 @@ def load_library(path: str = LIB_PATH):
                  "erf_column_stats", "erf_standardise", "erf_set_closure_weights", "erf_closure_features",
                  "erf_closure_fields", "erf_filter_state", "erf_set_tracer_initial", "erf_set_option",
                  "erf_get_option", "erf_selftest_wait_timeout", "erf_selftest_tensor_cores",
-                 "erf_column_block_bytes", "erf_pack_columns", "erf_unpack_columns"):
+                 "erf_column_block_bytes", "erf_pack_columns", "erf_unpack_columns", "erf_set_initial_moist",
+                 "erf_capture_reference"):
         getattr(L, name).restype = C.c_int
     _LIB = L
     return L
@@ -159,13 +167,20 @@ def make_structs(wl):
     if wl.knots is not None:
         kz, kt = keep(wl.knots[0]), keep(wl.knots[1])
         nk = len(kz)
+    qz = qk = None
+    nq = 0
+    if getattr(wl, "qv_knots", None) is not None:
+        qz, qk = keep(wl.qv_knots[0]), keep(wl.qv_knots[1])
+        nq = len(qz)
     c = Config(dt=wl.dt, n_substeps=wl.n_substeps, substep_mode=getattr(wl, "substep_mode", 0),
                beta_s=wl.beta_s, beta_d=wl.beta_d, scal_adv=wl.scal_adv, closure=wl.closure, Cs=wl.Cs,
                Pr_t=wl.Pr_t, nu=wl.nu, precision=wl.precision, gravity=wl.gravity, f_cor=wl.f_cor,
                u_g=wl.u_g, v_g=wl.v_g, surface=wl.surface, z0=wl.z0, sfc_theta_flux=wl.sfc_theta_flux,
                theta_s=wl.theta_s, brunt_N=wl.brunt_N, p_s=wl.p_s, n_knots=nk, knot_z=_dp(kz),
                knot_theta=_dp(kt), tracer=getattr(wl, "tracer", 0), mom_adv=wl.mom_adv,
-               ray_tau=wl.ray_tau, ray_zd=wl.ray_zd, ray_fields=wl.ray_fields)
+               ray_tau=wl.ray_tau, ray_zd=wl.ray_zd, ray_fields=wl.ray_fields, moist=wl.moist, n_qknots=nq,
+               qknot_z=_dp(qz), qknot_v=_dp(qk), relax_tau=wl.relax_tau, relax_width=wl.relax_width,
+               anelastic=getattr(wl, "anelastic", 0))
     return g, c, keep
 
 
@@ -228,6 +243,8 @@ class Dycore:
     def _shape(self, name):
         if name == "rhow":
             return self.shape_w
+        if name == "precip":
+            return (self.wl.ny, self.wl.nx)
         if name.startswith("base_") and not self.terrain:
             return (self.wl.nz,)
         return self.shape_c
@@ -237,6 +254,14 @@ class Dycore:
         arrs = [_f64(a) for a in (dtheta, u, v, w)]
         ptrs = [None if a is None else a.ctypes.data for a in arrs]
         _check(self.L, self.h, self.L.erf_set_initial(self.h, *ptrs, 0))
+
+    def erf_set_initial_moist(self, dtheta=None, qv=None, u=None, v=None, w=None):
+        arrs = [_f64(a) for a in (dtheta, qv, u, v, w)]
+        ptrs = [None if a is None else a.ctypes.data for a in arrs]
+        _check(self.L, self.h, self.L.erf_set_initial_moist(self.h, *ptrs, 0))
+
+    def erf_capture_reference(self):
+        _check(self.L, self.h, self.L.erf_capture_reference(self.h))
 
     def erf_set_initial_device(self, dtheta=None, u=None, v=None, w=None):
         ptrs = [None if t is None else t.data_ptr() for t in (dtheta, u, v, w)]
@@ -298,7 +323,10 @@ class Dycore:
         return {buf[i].name.decode(): (buf[i].total_ms, buf[i].launches) for i in range(n.value)}
 
     def state(self):
-        return {k: self.erf_get_state(k) for k in ("rho", "rhotheta", "rhou", "rhov", "rhow")}
+        out = {k: self.erf_get_state(k) for k in ("rho", "rhotheta", "rhou", "rhov", "rhow")}
+        if getattr(self.wl, "moist", 0):
+            out.update({k: self.erf_get_state(k) for k in ("rhoqv", "rhoqc", "rhoqr")})
+        return out
 
     # -- x-y pencil decomposition: column blocks of the prognostic state (device buffers)
     def erf_column_block_bytes(self, ni, nj):
