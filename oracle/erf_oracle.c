@@ -78,6 +78,11 @@ typedef struct {
      * relaxes toward its initial value at rate relax_tau sin^2(pi/2 (1 - d/relax_width)) within
      * relax_width of an x-edge (d the distance to it); relax_tau = 0: off */
     double relax_tau, relax_width;
+    /* anelastic equation set (Sec. 2.2): rho stays the base density rho0, the pressure
+     * perturbation is the projection's (stored, not from the EOS) and the buoyancy is
+     * rho0 g (theta - theta0) / theta0; the SSP-RK2 steps and the projection of Sec. 3.2 are
+     * driven from oracle/anelastic.py */
+    int32_t anelastic;
 } orc_cfg;
 
 typedef struct {
@@ -118,6 +123,8 @@ typedef struct {
     double *rq[3], *sn_q[3], *q_src[3], *qv0, *precip;
     /* relaxation zones: the reference (initial) state of every prognostic field */
     double *ref[5], *ref_q[3];
+    /* anelastic pressure perturbation p' at cells */
+    double *pa;
     /* learned closure (closure 3): a model evaluated on each stage state; it writes nine planes
      * of ncell values at cell centres, density-weighted: rho t11, rho t22, rho t33, rho t12,
      * rho t13, rho t23, rho h1, rho h2, rho h3 (kinematic stress [m^2/s^2] and SGS heat flux
@@ -367,6 +374,7 @@ orc *orc_create2(const orc_cfg *cfg, const double *zeta, const double *hnode, in
     }
     for (int f = 0; f < 5; ++f) o->ref[f] = dalloc(f == F_RW ? NW : NC);
     o->qv0 = dalloc(NC); o->precip = dalloc((size_t)nx * ny);
+    o->pa = dalloc(NC);
 
     /* node heights, App. B + canonical smoothing z = zeta + (1 - zeta/z_t)^beta h (Sec. 3.4) */
     #pragma omp parallel for
@@ -454,7 +462,7 @@ void orc_destroy(orc *o) {
     for (size_t n = 0; n < sizeof(ptrs) / sizeof(ptrs[0]); ++n) free(*ptrs[n]);
     for (int f = 0; f < 5; ++f) { free(o->sn[f]); free(o->R[f]); free(o->X[f]); free(o->ref[f]); }
     for (int q = 0; q < 3; ++q) { free(o->rq[q]); free(o->sn_q[q]); free(o->q_src[q]); free(o->ref_q[q]); }
-    free(o->qv0); free(o->precip);
+    free(o->qv0); free(o->precip); free(o->pa);
     free(o);
 }
 
@@ -484,6 +492,14 @@ static void apply_wall_bc(orc *o, double *rw, const double *ru, const double *rv
 /* ------------------------------------------------------------------ stage EOS pass */
 static void eos_pass(orc *o, const double *rho, const double *rt) {
     const int moist = o->c.moist;
+    if (o->c.anelastic) {   /* Sec. 2.2: p' from the projection, no EOS; pi is not used */
+        for (size_t c = 0; c < o->ncell; ++c) {
+            o->pp[c] = o->pa[c];
+            o->pi[c] = 1.0;
+            o->th[c] = rt[c] / rho[c];
+        }
+        return;
+    }
 #pragma omp parallel for
     for (long c = 0; c < (long)o->ncell; ++c) {
         double p, pie;
@@ -750,7 +766,12 @@ static void slow_rhs(orc *o, const double *rho, const double *rt, const double *
             for (int i = 0; i < nx; ++i) {
                 size_t w = IX(o, i, j, k), c = IX(o, i, j, k), cm = IX(o, i, j, k - 1);
                 double pz = (o->pp[c] - o->pp[cm]) / (o->zc[c] - o->zc[cm]);
-                if (qtm) {
+                if (C->anelastic) {
+                    /* Sec. 2.2: B = rho0 g (theta - theta0) / theta0, the face mean of the two cells */
+                    double Bm = o->rho0[cm] * g * (o->th[cm] - o->th0[cm]) / o->th0[cm];
+                    double Bc = o->rho0[c] * g * (o->th[c] - o->th0[c]) / o->th0[c];
+                    Rw[w] += -pz + 0.5 * (Bm + Bc);
+                } else if (qtm) {
                     double B = 0.5 * (-g * (rho[cm] + qtm[cm] - o->rho0[cm]) - g * (rho[c] + qtm[c] - o->rho0[c]));
                     Rw[w] += (-pz + B) / (1.0 + 0.5 * (qvc[cm] + qvc[c]));
                 } else {
@@ -1505,7 +1526,10 @@ void orc_set_initial_q(orc *o, const double *dtheta, const double *qv, const dou
             for (int i = 0; i < o->nx; ++i) {
                 size_t c = IX(o, i, j, k);
                 double th = o->th0[c] + (dtheta ? dtheta[c] : 0.0);
-                if (o->c.moist) {
+                if (o->c.anelastic) {          /* Sec. 2.2: the density is the base density */
+                    o->rho[c] = o->rho0[c];
+                    o->rt[c] = o->rho0[c] * th;
+                } else if (o->c.moist) {
                     double q0 = o->qv0[c], q = qv ? qv[c] : q0;
                     double rd0 = o->rho0[c] / (1.0 + q0), f = (1.0 + ev * q0) / (1.0 + ev * q);
                     o->rt[c] = rd0 * o->th0[c] * f;
@@ -1562,12 +1586,14 @@ int orc_get_field(orc *o, int f, double *dst) {
     if (f == 9) { memcpy(dst, o->rtke, sizeof(double) * o->ncell); return 0; }
     if (f >= 10 && f <= 12) { memcpy(dst, o->rq[f - 10], sizeof(double) * o->ncell); return 0; }
     if (f == 13) { memcpy(dst, o->qv0, sizeof(double) * o->ncell); return 0; }
+    if (f == 14) { memcpy(dst, o->pa, sizeof(double) * o->ncell); return 0; }
     return -1;
 }
 int orc_set_field(orc *o, int f, const double *src) {
     if (f == 8) { memcpy(o->rphi, src, sizeof(double) * o->ncell); return 0; }
     if (f == 9) { memcpy(o->rtke, src, sizeof(double) * o->ncell); return 0; }
     if (f >= 10 && f <= 12) { memcpy(o->rq[f - 10], src, sizeof(double) * o->ncell); return 0; }
+    if (f == 14) { memcpy(o->pa, src, sizeof(double) * o->ncell); return 0; }
     if (f < 0 || f >= 5) return -1;
     memcpy(field_ptr(o, f), src, sizeof(double) * field_len(o, f));
     o->have_state = 1;
@@ -1590,6 +1616,7 @@ int orc_set_sgs_model(orc *o, void (*fn)(void *, const double *, const double *,
 }
 int orc_step(orc *o, int nsteps) {
     if (!o->have_state) return -5;
+    if (o->c.anelastic) return -6;     /* the anelastic steps are driven from oracle/anelastic.py */
     if (o->c.closure == 3 && !o->sgs_model) return -5;
     for (int n = 0; n < nsteps; ++n) rk3_step(o);
     return 0;

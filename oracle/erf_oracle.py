@@ -50,6 +50,7 @@ class _Cfg(C.Structure):
         ("tracer", C.c_int32),
         ("ray_tau", C.c_double), ("ray_zd", C.c_double), ("ray_fields", C.c_int32),
         ("moist", C.c_int32), ("relax_tau", C.c_double), ("relax_width", C.c_double),
+        ("anelastic", C.c_int32),
     ]
 
 
@@ -90,6 +91,7 @@ class OracleConfig:
     moist: int = 0
     relax_tau: float = 0.0
     relax_width: float = 0.0
+    anelastic: int = 0
 
 
 _LIB = None
@@ -162,7 +164,7 @@ def _f64(a):
 
 FIELDS = {"rho": 0, "rhotheta": 1, "rhou": 2, "rhov": 3, "rhow": 4,
           "base_rho": 5, "base_p": 6, "base_theta": 7, "rhophi": 8, "rhotke": 9,
-          "rhoqv": 10, "rhoqc": 11, "rhoqr": 12, "base_qv": 13}
+          "rhoqv": 10, "rhoqc": 11, "rhoqr": 12, "base_qv": 13, "p_anelastic": 14}
 GEOM = {"zc": 0, "Hc": 1, "Hx": 2, "Hy": 3, "hxi_x": 4, "heta_y": 5,
         "zw": 6, "hxi_w": 7, "heta_w": 8, "zn": 9}
 

@@ -81,6 +81,7 @@ class Workload:
     qr: Optional[np.ndarray] = None
     relax_tau: float = 0.0                 # lateral relaxation zones (open x boundaries) [1/s]
     relax_width: float = 0.0               # their width [m]
+    anelastic: int = 0                     # 1: the anelastic equation set (SSP-RK2 + projection)
     notes: str = ""
 
     @property

@@ -24,7 +24,8 @@ def oracle_config_from(wl, **over):
                        surface=wl.surface, z0=wl.z0, sfc_theta_flux=wl.sfc_theta_flux,
                        theta_s=wl.theta_s, brunt_N=wl.brunt_N, p_s=wl.p_s, tracer=wl.tracer,
                        ray_tau=wl.ray_tau, ray_zd=wl.ray_zd, ray_fields=wl.ray_fields,
-                       moist=wl.moist, relax_tau=wl.relax_tau, relax_width=wl.relax_width)
+                       moist=wl.moist, relax_tau=wl.relax_tau, relax_width=wl.relax_width,
+                       anelastic=wl.anelastic)
     for k, v in over.items():
         setattr(cfg, k, v)
     return cfg
