@@ -52,6 +52,22 @@ KERNEL_MODEL = {
     "tri_build":   {"unit": "cell", "words": 14, "flops": 90},
     "stage_end":   {"unit": "wface", "words": 15, "flops": 5},
     "wall_bc":     {"unit": "none", "words": 0, "flops": 0},
+    # moist path: Kessler reads rho, rho theta, 3 water species, writes 4 (pow/exp/sqrt each ~20 flop)
+    "kessler":     {"unit": "cell", "words": 9, "flops": 220},
+    "moist_diff":  {"unit": "cell", "words": 8, "flops": 90},
+    "relax":       {"unit": "wface", "words": 18, "flops": 30},
+    "tke_diff":    {"unit": "cell", "words": 4, "flops": 40},
+    "tke_update":  {"unit": "cell", "words": 5, "flops": 12},
+    "tracer_update": {"unit": "cell", "words": 5, "flops": 10},
+    "tracer_flux": {"unit": "wface", "words": 10, "flops": 210},
+    # anelastic projection: complex FP64 field in and out per pass; an FFT of length n costs
+    # 5 log2 n flops per point (forward x + y, or inverse y + x, in one scope)
+    "anel_fft":    {"unit": "cell", "words": 8, "flops": 80},
+    "anel_tri":    {"unit": "cell", "words": 6, "flops": 14},
+    "anel_div":    {"unit": "cell", "words": 5, "flops": 8},
+    "anel_correct": {"unit": "wface", "words": 9, "flops": 10},
+    "anel_stage":  {"unit": "wface", "words": 12, "flops": 16},
+    "anel_begin":  {"unit": "cell", "words": 4, "flops": 2},
 }
 # DRAM bytes per unit from an ncu capture of the kernel as it stands (dram__bytes_read.sum +
 # dram__bytes_write.sum of a 128^3 hill-bubble launch / its units; profiles/ has the summary),
@@ -386,7 +402,12 @@ def _time_form(wl, steps, out, name, prec, e2e_steps=0):
     from paper_2412_04395_gb300 import workloads as W
     from paper_2412_04395_gb300.erf import Dycore
     d = Dycore(wl)
-    d.erf_set_initial(wl.dtheta, wl.u, wl.v, wl.w)
+    if wl.moist:
+        d.erf_set_initial_moist(wl.dtheta, wl.qv, wl.u, wl.v, wl.w)
+    else:
+        d.erf_set_initial(wl.dtheta, wl.u, wl.v, wl.w)
+    if wl.closure == W.CLOSURE_DEARDORFF and wl.tke is not None:
+        d.erf_set_state("rhotke", d.erf_get_state("rho") * wl.tke)
     if wl.closure == W.CLOSURE_LEARNED:
         blob, kind = closure_blob(wl, d)
         d.erf_set_closure_weights(blob)
@@ -446,6 +467,35 @@ def precision_comparison(args):
         _time_form(pw.with_(precision=W.PREC_MIXED32), args.cmp_steps, pap, "fp32", "mixed")
         pap["fp32_over_fp64"] = pap["fp32"]["value"] / pap["fp64"]["value"]
         out["paper_scaling"] = pap
+    return out
+
+
+def extension_lines(args):
+    """Cell-updates/s of the paths beyond the RK3 dycore (CUDA events around graph-launched steps
+    after 3 warm-up steps, per-kernel times of one further step), each on one GB300:
+      * the moist squall line (Sec. 4.1.3) at its full size, 1500 x 4 x 240 at 100 m, FP64, Kessler
+        microphysics, constant nu = alpha = 200 m^2/s, relaxation-zone open boundaries;
+      * the Deardorff 1.5-order closure (FP64) on the convective ABL at 512 x 512 x 160 (40 m);
+      * the anelastic equation set (SSP-RK2 + FFT projection, FP64) on a 3D warm bubble,
+        256 x 256 x 128 at 50 m."""
+    from paper_2412_04395_gb300 import workloads as W
+    out = {}
+    sq = W.squall_line()
+    _time_form(sq, args.ext_steps, out, "squall_line_fp64_kessler", "fp64")
+    out["squall_line_fp64_kessler"]["workload"] = "squall_line 1500x4x240 at 100 m, dt 0.25 s, ns 6"
+    cb = W.convective_abl(nx=512, ny=512, nz=160, dx=40.0).with_(precision=W.PREC_FP64,
+                                                                closure=W.CLOSURE_DEARDORFF, Pr_t=1.0 / 3.0)
+    zc = 0.5 * (cb.zeta[:-1] + cb.zeta[1:])
+    cb = cb.with_(tke=np.broadcast_to((0.5 * np.exp(-zc / 400.0) + 0.01)[:, None, None], (cb.nz, cb.ny, cb.nx)).copy())
+    _time_form(cb, max(1, args.ext_steps // 2), out, "convective_abl_fp64_deardorff", "fp64")
+    out["convective_abl_fp64_deardorff"]["workload"] = "convective_abl 512x512x160 at 40 m, Deardorff, ns 10"
+    zeta = W.uniform_zeta(128, 50.0)
+    X, Y, Z = W.cell_coords(256, 256, zeta, 50.0, 50.0)
+    r = np.sqrt((X - 6400.0) ** 2 + (Y - 6400.0) ** 2 + (Z - 1500.0) ** 2) / 1000.0
+    an = W.Workload("anelastic_bubble", 256, 256, 128, 50.0, 50.0, zeta, dt=1.0, closure=W.CLOSURE_NONE,
+                    dtheta=np.where(r < 1.0, 2.0 * np.cos(0.5 * np.pi * r) ** 2, 0.0), anelastic=1)
+    _time_form(an, args.ext_steps, out, "anelastic_bubble_fp64", "fp64")
+    out["anelastic_bubble_fp64"]["workload"] = "anelastic warm bubble 256x256x128 at 50 m, SSP-RK2 + FFT projection"
     return out
 
 
@@ -509,6 +559,7 @@ def run_ours(args):
         del d
         torch.cuda.empty_cache()
         cmp = precision_comparison(args)
+    ext = extension_lines(args) if args.ext_steps > 0 else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -532,7 +583,7 @@ def run_ours(args):
                 "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                            "reasons": clocks["reasons"], "samples": clocks["samples"]},
                 "e2e": e2e, "gpu_launches": kps * args.steps, "kernels_per_step": kps,
-                "roofline": roof, "cpu_baseline": cpu, "precision_comparison": cmp,
+                "roofline": roof, "cpu_baseline": cpu, "precision_comparison": cmp, "extensions": ext,
                 "mass_rel_drift": abs(diag["mass"] - diag0["mass"]) / abs(diag0["mass"]),
                 "mass_drift_steps": args.steps,
                 "hbm_frac_step": hbm_frac_step, "step_alg_bytes_per_cell_update": sb,
@@ -561,6 +612,8 @@ def main():
     ap.add_argument("--cmp-steps", type=int, default=8, help="timed steps per FP32 form (FP64: a quarter); 0 skips")
     ap.add_argument("--cmp-e2e-steps", type=int, default=2,
                     help="steps of the FP32 + learned form timed end to end through the C ABI with host buffers")
+    ap.add_argument("--ext-steps", type=int, default=6,
+                    help="timed steps of the moist, Deardorff and anelastic lines (0 skips them)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--closure", default="default", choices=["default", "learned"],
                     help="learned: the MLP closure (convective_abl with --precision mixed)")

@@ -6,7 +6,8 @@ library in ``paper_2412_04395_gb300``.
 """
 from .erf_oracle import (Oracle, OracleConfig, build_oracle, lib_path, interp, weno5,
                          thomas, eos, hse_column, ustar, psi_m, set_threads, qvs, rain_speed,
-                         rain_evap)
+                         rain_evap, config_from, from_workload)
 
 __all__ = ["Oracle", "OracleConfig", "build_oracle", "lib_path", "interp", "weno5", "thomas",
-           "eos", "hse_column", "ustar", "psi_m", "set_threads", "qvs", "rain_speed", "rain_evap"]
+           "eos", "hse_column", "ustar", "psi_m", "set_threads", "qvs", "rain_speed", "rain_evap",
+           "config_from", "from_workload"]

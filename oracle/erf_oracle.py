@@ -375,3 +375,41 @@ def rain_speed(rho, qr, rho_sfc):
 def rain_evap(rho, qv, qr, qvs_, p):
     """Rain evaporation rate [1/s] of the oracle's Kessler scheme."""
     return _lib().orc_rain_evap(float(rho), float(qv), float(qr), float(qvs_), float(p))
+
+
+def config_from(wl, **over) -> OracleConfig:
+    """The oracle configuration of a workload (paper_2412_04395_gb300.workloads.Workload, the seeded
+    input description both implementations read), optionally with fields overridden."""
+    cfg = OracleConfig(nx=wl.nx, ny=wl.ny, nz=wl.nz, dx=wl.dx, dy=wl.dy,
+                       terrain_beta=wl.terrain_beta, dt=wl.dt, n_substeps=wl.n_substeps,
+                       beta_s=wl.beta_s, beta_d=wl.beta_d, mom_adv=wl.mom_adv,
+                       scal_adv=wl.scal_adv, closure=wl.closure, Cs=wl.Cs, Pr_t=wl.Pr_t,
+                       nu=wl.nu, gravity=wl.gravity, f_cor=wl.f_cor, u_g=wl.u_g, v_g=wl.v_g,
+                       surface=wl.surface, z0=wl.z0, sfc_theta_flux=wl.sfc_theta_flux,
+                       theta_s=wl.theta_s, brunt_N=wl.brunt_N, p_s=wl.p_s, tracer=wl.tracer,
+                       ray_tau=wl.ray_tau, ray_zd=wl.ray_zd, ray_fields=wl.ray_fields,
+                       moist=wl.moist, relax_tau=wl.relax_tau, relax_width=wl.relax_width,
+                       anelastic=wl.anelastic)
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def from_workload(wl, init=True, **over) -> Oracle:
+    """An oracle of a workload with its initial state set (passive scalar, SGS energy and water
+    species included)."""
+    o = Oracle(config_from(wl, **over), wl.zeta, wl.terrain, wl.knots, wl.qv_knots)
+    if init:
+        o.set_initial(wl.dtheta, wl.u, wl.v, wl.w, qv=wl.qv)
+        if wl.tracer and wl.phi is not None:
+            o.set_tracer_initial(wl.phi)
+        if wl.closure == 4 and wl.tke is not None:
+            o.set("rhotke", o.get("rho") * wl.tke)
+        if wl.moist and (wl.qc is not None or wl.qr is not None):
+            rho = o.get("rho")
+            if wl.qc is not None:
+                o.set("rhoqc", rho * wl.qc)
+            if wl.qr is not None:
+                o.set("rhoqr", rho * wl.qr)
+            o.capture_reference()
+    return o
