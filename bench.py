@@ -53,7 +53,8 @@ KERNEL_MODEL = {
     "stage_end":   {"unit": "wface", "words": 15, "flops": 5},
     "wall_bc":     {"unit": "none", "words": 0, "flops": 0},
     # moist path: Kessler reads rho, rho theta, 3 water species, writes 4 (pow/exp/sqrt each ~20 flop)
-    "kessler":     {"unit": "cell", "words": 9, "flops": 220},
+    "kessler_fall": {"unit": "cell", "words": 3, "flops": 40},
+    "kessler":     {"unit": "cell", "words": 11, "flops": 200},
     "moist_diff":  {"unit": "cell", "words": 8, "flops": 90},
     "relax":       {"unit": "wface", "words": 18, "flops": 30},
     "tke_diff":    {"unit": "cell", "words": 4, "flops": 40},
@@ -510,6 +511,9 @@ def run_ours(args):
     if args.column_fusion != -1:
         from paper_2412_04395_gb300.erf import ERF_OPT_COLUMN_FUSION
         d.erf_set_option(ERF_OPT_COLUMN_FUSION, args.column_fusion)
+    if args.warp_columns != -1:
+        from paper_2412_04395_gb300.erf import ERF_OPT_WARP_COLUMNS
+        d.erf_set_option(ERF_OPT_WARP_COLUMNS, args.warp_columns)
     if args.closure == "learned":
         blob, _ = closure_blob(wl, d)
         d.erf_set_closure_weights(blob)
@@ -578,7 +582,7 @@ def run_ours(args):
                 "data": "synthetic",
                 "config": {"workload": wl.name, "grid": [wl.nx, wl.ny, wl.nz], "dx": wl.dx,
                            "substeps": wl.n_substeps, "precision": args.precision, "closure": args.closure,
-                           "parallelism": f"replicas{ws}",
+                           "parallelism": f"replicas{ws}", "warp_columns": args.warp_columns,
                            "l2": "working set >> L2 (no flush needed)"},
                 "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                            "reasons": clocks["reasons"], "samples": clocks["samples"]},
@@ -621,6 +625,8 @@ def main():
                     help="nx ny nz of a smaller window of the workload (profiling runs only)")
     ap.add_argument("--column-fusion", type=int, default=-1, choices=[-1, 0, 1],
                     help="explicit vertical substep part inside the column sweep: -1 by column count")
+    ap.add_argument("--warp-columns", type=int, default=-1, choices=[-1, 0, 1],
+                    help="FP64 column kernels one warp per column (1), one thread (0), by column count (-1)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

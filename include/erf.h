@@ -331,9 +331,13 @@ erf_status erf_unpack_columns(erf_handle *h, int32_t i0, int32_t ni, int32_t j0,
  *   (App. C rows 3-4): 1 inside the column sweep of the vertical solve, one thread per column;
  *   0 as a per-cell kernel before the sweep; -1 (default) fused when nx * ny >= 2^17.  Both give
  *   bit-identical results.
+ *   ERF_OPT_WARP_COLUMNS: how the FP64 path builds the stage's vertical acoustic system (App. C):
+ *   1 one warp per column (the lanes form the levels' coefficients at once, one lane runs the LU
+ *   recurrence; for grids with few columns such as 2D slabs, nz <= 256), 0 one thread per column,
+ *   -1 (default) one warp per column below 2^15 columns.  Both give bit-identical results.
  * erf_set_option drops the captured step graph; erf_get_option reports whether the option is in
- * effect (1 if the TMA kernels run, 1 if the fused column sweep runs). */
-typedef enum { ERF_OPT_TMA_STENCILS = 1, ERF_OPT_COLUMN_FUSION = 2 } erf_option;
+ * effect (1 if the TMA kernels run, 1 if the fused column sweep runs, 1 if warps build the columns). */
+typedef enum { ERF_OPT_TMA_STENCILS = 1, ERF_OPT_COLUMN_FUSION = 2, ERF_OPT_WARP_COLUMNS = 3 } erf_option;
 erf_status erf_set_option(erf_handle *h, int32_t option, int64_t value);
 erf_status erf_get_option(erf_handle *h, int32_t option, int64_t *value);
 

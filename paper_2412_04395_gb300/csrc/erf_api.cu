@@ -87,6 +87,7 @@ struct erf_handle {
     MxTma tma{};                            // TMA tile maps of the stencil fields
     bool tma_enabled = true;
     int column_fusion = -1;                 // ERF_OPT_COLUMN_FUSION: -1 by column count, 0 off, 1 on
+    int warp_columns = -1;                  // ERF_OPT_WARP_COLUMNS: -1 by column count, 0 off, 1 on
     unsigned *kerr = nullptr;               // set by a kernel whose bounded wait gave up
     float *mX0 = nullptr, *mY0 = nullptr;   // beta-weighted Theta'', rho'' of the vertical substep (in mflux)
     // passive scalar (mixed path, FP32): rho phi, its S^n copy, substep momentum sums
@@ -573,6 +574,7 @@ static void enqueue_step_anelastic(erf_handle *h, cudaStream_t s) {
 
 // one RK3 step (Sec. 3.1) with the App. C substeps, enqueued on stream s
 static void enqueue_step(erf_handle *h, cudaStream_t s) {
+    set_warp_columns(h->warp_columns);
     if (h->mixed) {
         enqueue_step_mixed(h, s);
         return;
@@ -650,7 +652,8 @@ static void enqueue_step(erf_handle *h, cudaStream_t s) {
         launch_stage_end(g, h->st, cf(h->x), s);
     }
     // microphysics after the dycore step (time split, Sec. 2.4)
-    if (h->rq[0]) launch_kessler(g, c.dt, h->st.t, h->st.r, h->rq[0], h->rq[1], h->rq[2], h->precip, s);
+    // (the flux buffer is free once the last stage has ended)
+    if (h->rq[0]) launch_kessler(g, c.dt, h->st.t, h->st.r, h->rq[0], h->rq[1], h->rq[2], h->precip, h->flux, s);
 }
 
 static erf_status build_graph(erf_handle *h) {
@@ -1161,6 +1164,9 @@ extern "C" erf_status erf_set_option(erf_handle *h, int32_t option, int64_t valu
     } else if (option == ERF_OPT_COLUMN_FUSION) {
         if (value < -1 || value > 1) return fail(h, ERF_EINVAL, "column fusion must be -1, 0 or 1");
         h->column_fusion = (int)value;
+    } else if (option == ERF_OPT_WARP_COLUMNS) {
+        if (value < -1 || value > 1) return fail(h, ERF_EINVAL, "warp columns must be -1, 0 or 1");
+        h->warp_columns = (int)value;
     } else {
         return fail(h, ERF_EINVAL, "unknown option");
     }
@@ -1206,6 +1212,9 @@ extern "C" erf_status erf_get_option(erf_handle *h, int32_t option, int64_t *val
     if (!h || !value) return fail(h, ERF_EINVAL, "NULL argument");
     if (option == ERF_OPT_TMA_STENCILS) *value = (h->mixed && h->tma.use) ? 1 : 0;
     else if (option == ERF_OPT_COLUMN_FUSION) *value = (h->mixed && fuse_columns(h)) ? 1 : 0;
+    else if (option == ERF_OPT_WARP_COLUMNS)
+        *value = (!h->mixed && h->geo.nz <= 256 &&
+                  (h->warp_columns >= 0 ? h->warp_columns == 1 : h->geo.nxy < (1LL << 15))) ? 1 : 0;
     else return fail(h, ERF_EINVAL, "unknown option");
     return ERF_OK;
 }

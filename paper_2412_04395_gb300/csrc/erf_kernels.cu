@@ -524,9 +524,11 @@ __global__ void k_tke_diff(Geo g, const double *mu, const double *rtke, const do
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= g.nc) return;
     int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    // e at a stencil point from the Newton reciprocal of rho (four FMAs; a division takes ~ten
+    // FP64-pipe operations)
     auto ev = [&](int ii, int jj, int kk) {
         const long long q = cixw(g, ii, jj, kk);
-        return fmax(__ldg(rtke + q) / __ldg(rho + q), 0.0);
+        return fmax(__ldg(rtke + q) * rcp_d(__ldg(rho + q)), 0.0);
     };
     const double m0 = __ldg(mu + c), e0 = ev(i, j, k);
     const double fxm = (cval(g, mu, i - 1, j, k) + m0) * (e0 - ev(i - 1, j, k)) * g.rdx;
@@ -555,20 +557,26 @@ __global__ void k_moist_diff(Geo g, const double *hk, double hs, Q3 rq, const do
     const double h0 = __ldg(hk + c);
     const double hxm = cval(g, hk, i - 1, j, k), hxp = cval(g, hk, i + 1, j, k);
     const double hym = cval(g, hk, i, j - 1, k), hyp = cval(g, hk, i, j + 1, k);
+    // the seven stencil points and their reciprocal densities, shared by the three species (an
+    // FP64 division costs about ten FP64-pipe operations, the Newton reciprocal four)
+    const bool km = k > 0, kp = k < g.nz - 1;
+    const long long a[7] = {c, cixw(g, i - 1, j, k), cixw(g, i + 1, j, k), cixw(g, i, j - 1, k), cixw(g, i, j + 1, k),
+                            km ? c - g.nxy : c, kp ? c + g.nxy : c};
+    double rr[7];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) rr[m] = rcp_d(__ldg(rho + a[m]));
+    const double cxm = 0.5 * (hxm + h0) * hs * g.rdx, cxp = 0.5 * (h0 + hxp) * hs * g.rdx;
+    const double cym = 0.5 * (hym + h0) * hs * g.rdy, cyp = 0.5 * (h0 + hyp) * hs * g.rdy;
+    const double czm = km ? 0.5 * (__ldg(hk + c - g.nxy) + h0) * hs * g.rdzc[k] : 0.0;
+    const double czp = kp ? 0.5 * (h0 + __ldg(hk + c + g.nxy)) * hs * g.rdzc[k + 1] : 0.0;
+#pragma unroll
     for (int q = 0; q < 3; ++q) {
-        auto qv = [&](int ii, int jj, int kk) {
-            const long long a = cixw(g, ii, jj, kk);
-            return __ldg(rq.q[q] + a) / __ldg(rho + a);
-        };
-        const double q0 = qv(i, j, k);
-        const double fxm = 0.5 * (hxm + h0) * hs * (q0 - qv(i - 1, j, k)) * g.rdx;
-        const double fxp = 0.5 * (h0 + hxp) * hs * (qv(i + 1, j, k) - q0) * g.rdx;
-        const double fym = 0.5 * (hym + h0) * hs * (q0 - qv(i, j - 1, k)) * g.rdy;
-        const double fyp = 0.5 * (h0 + hyp) * hs * (qv(i, j + 1, k) - q0) * g.rdy;
-        double fzm = 0.0, fzp = 0.0;
-        if (k > 0) fzm = 0.5 * (__ldg(hk + c - g.nxy) + h0) * hs * (q0 - qv(i, j, k - 1)) * g.rdzc[k];
-        if (k < g.nz - 1) fzp = 0.5 * (h0 + __ldg(hk + c + g.nxy)) * hs * (qv(i, j, k + 1) - q0) * g.rdzc[k + 1];
-        src.q[q][c] = (fxp - fxm) * g.rdx + (fyp - fym) * g.rdy + (fzp - fzm) * g.rdzeta[k];
+        double v[7];
+#pragma unroll
+        for (int m = 0; m < 7; ++m) v[m] = __ldg(rq.q[q] + a[m]) * rr[m];
+        const double q0 = v[0];
+        src.q[q][c] = (cxp * (v[2] - q0) - cxm * (q0 - v[1])) * g.rdx + (cyp * (v[4] - q0) - cym * (q0 - v[3])) * g.rdy
+                    + (czp * (v[6] - q0) - czm * (q0 - v[5])) * g.rdzeta[k];
     }
 }
 
@@ -591,12 +599,14 @@ __global__ void k_relax(Geo g, Phys ph, CF5 st, CF5 ref, F5 R, Q3 rq, Q3 rqref, 
     if (k >= 1 && k < g.nz) R.w[n] -= tc * (st.w[n] - ref.w[n]);
 }
 
-// One time-split Kessler step after the RK3 step (Kessler 1969; Klemp & Wilhelmson 1978), one
-// thread per column, the dry density unchanged:
-//   1. rain falls one explicit upwind step: F = rho q_r V through each cell's bottom face,
-//      V = 36.34 (1e-3 rho q_r)^0.1346 (rho_0 / rho)^(1/2) m/s (the cgs form V = 3634 (rho q_r)^0.1346
-//      (rho_0/rho)^(1/2) cm/s, rho q_r in g/cm^3, rho_0 the base dry density at the ground); what
-//      leaves the lowest cell adds F dt / rho_water to the surface accumulation;
+// One time-split Kessler step after the RK3 step (Kessler 1969; Klemp & Wilhelmson 1978), the dry
+// density unchanged, in two per-cell kernels (the rain fall needs only the rain before the fall, so
+// no column recurrence is left):
+//   k_kessler_fall: F = rho q_r V through each cell's bottom face, V = 36.34 (1e-3 rho q_r)^0.1346
+//      (rho_0 / rho)^(1/2) m/s (the cgs form V = 3634 (rho q_r)^0.1346 (rho_0/rho)^(1/2) cm/s,
+//      rho q_r in g/cm^3, rho_0 the base dry density at the ground);
+//   k_kessler: the upwind fall step (what leaves the lowest cell adds F dt / rho_water to the
+//      surface accumulation), then
 //   2. autoconversion 1e-3 (q_c - 1e-3)^+ and accretion 2.2 q_c q_r^0.875 (1/s) move cloud to rain;
 //   3. saturation adjustment in one linearised step (Soong & Ogura 1973) with the Tetens q_vs and
 //      its slope q_vs 4098.17 / (T - 35.86)^2 at T = theta pi (pi from the moist EOS before the step);
@@ -604,59 +614,52 @@ __global__ void k_relax(Geo g, Phys ph, CF5 st, CF5 ref, F5 R, Q3 rq, Q3 rqref, 
 //      / (5.4e5 + 2.55e6 / (p q_vs)), C = 1.6 + 124.9 (rho q_r)^0.2046 (rho in g/cm^3, p in mb);
 //      theta gains L_v / (c_p pi) (condensation - evaporation).
 // Every quantity is applied as an increment of the conserved variables.
-__global__ void k_kessler(Geo g, double dt, double *rt, const double *rho, double *rqv, double *rqc, double *rqr,
-                          double *precip) {
-    long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (col >= g.nxy) return;
-    const int i = (int)(col % g.nx), j = (int)(col / g.nx);
+__global__ void k_kessler_fall(Geo g, const double *rho, const double *rqr, double *F) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny);
     const long long b0 = bix(g, i, j, 0);
     const double rho_sfc = g.rho0[b0] / (1.0 + g.qv0[b0]);
-    auto flux = [&](int k) {   // rho q_r V at the bottom face of cell k
-        if (k >= g.nz) return 0.0;
-        const long long c = cix(g, i, j, k);
-        const double r = rho[c], rr = rqr[c], qr = rr / r;
-        if (!(qr > 0.0)) return 0.0;
-        return rr * (36.34 * pow(1.0e-3 * r * qr, 0.1346) * sqrt(rho_sfc / r));
-    };
-    // 1. sedimentation: every face flux from the rain before the fall
-    double f_below = flux(0);
-    precip[col] += dt * f_below / RHOW;
-    for (int k = 0; k < g.nz; ++k) {
-        const double f_above = flux(k + 1);
-        rqr[cix(g, i, j, k)] += dt * (f_above - f_below) * (g.terrain ? rHc(g, i, j, k) : g.rdzeta[k]);
-        f_below = f_above;
+    const double r = rho[c], rr = rqr[c], qr = rr / r;
+    F[c] = qr > 0.0 ? rr * (36.34 * pow(1.0e-3 * r * qr, 0.1346) * sqrt(rho_sfc / r)) : 0.0;
+}
+__global__ void k_kessler(Geo g, double dt, const double *F, double *rt, const double *rho, double *rqv,
+                          double *rqc, double *rqr, double *precip) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.nc) return;
+    const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.nxy);
+    // 1. rain fall
+    const double f_below = F[c], f_above = k + 1 < g.nz ? F[c + g.nxy] : 0.0;
+    if (k == 0) precip[(long long)j * g.nx + i] += dt * f_below / RHOW;
+    rqr[c] += dt * (f_above - f_below) * (g.terrain ? rHc(g, i, j, k) : g.rdzeta[k]);
+    const double r = rho[c], th = rt[c] / r;
+    const double qv = rqv[c] / r;
+    double qc = rqc[c] / r, qr = rqr[c] / r;
+    double p, pie;
+    eos_pi(rt[c] * (1.0 + (RV / RD) * qv), p, pie);
+    // 2. autoconversion and accretion
+    double ar = fmax(1.0e-3 * (qc - 1.0e-3), 0.0);
+    double cr = qr > 0.0 ? 2.2 * qc * pow(qr, 0.875) : 0.0;
+    double prod = fmin(dt * (ar + cr), qc);
+    qc -= prod;
+    qr += prod;
+    // 3. saturation adjustment and rain evaporation
+    const double T = th * pie;
+    const double es = 610.78 * exp(17.27 * (T - 273.16) / (T - 35.86));
+    const double qvs = (RD / RV) * es / (p - es);
+    const double sadj = (qv - qvs) / (1.0 + qvs * LV * 4098.17 / (CPD * (T - 35.86) * (T - 35.86)));
+    double ern = 0.0;
+    if (qr > 0.0 && qv < qvs) {
+        const double rg = 1.0e-3 * r, X = rg * qr;
+        const double C = 1.6 + 124.9 * pow(X, 0.2046);
+        ern = dt * ((1.0 / rg) * (1.0 - qv / qvs) * C * pow(X, 0.525) / (5.4e5 + 2.55e6 / ((1.0e-2 * p) * qvs)));
     }
-    for (int k = 0; k < g.nz; ++k) {
-        const long long c = cix(g, i, j, k);
-        const double r = rho[c], th = rt[c] / r;
-        const double qv = rqv[c] / r;
-        double qc = rqc[c] / r, qr = rqr[c] / r;
-        double p, pie;
-        eos_pi(rt[c] * (1.0 + (RV / RD) * qv), p, pie);
-        // 2. autoconversion and accretion
-        double ar = fmax(1.0e-3 * (qc - 1.0e-3), 0.0);
-        double cr = qr > 0.0 ? 2.2 * qc * pow(qr, 0.875) : 0.0;
-        double prod = fmin(dt * (ar + cr), qc);
-        qc -= prod;
-        qr += prod;
-        // 3. saturation adjustment and rain evaporation
-        const double T = th * pie;
-        const double es = 610.78 * exp(17.27 * (T - 273.16) / (T - 35.86));
-        const double qvs = (RD / RV) * es / (p - es);
-        const double sadj = (qv - qvs) / (1.0 + qvs * LV * 4098.17 / (CPD * (T - 35.86) * (T - 35.86)));
-        double ern = 0.0;
-        if (qr > 0.0 && qv < qvs) {
-            const double rg = 1.0e-3 * r, X = rg * qr;
-            const double C = 1.6 + 124.9 * pow(X, 0.2046);
-            ern = dt * ((1.0 / rg) * (1.0 - qv / qvs) * C * pow(X, 0.525) / (5.4e5 + 2.55e6 / ((1.0e-2 * p) * qvs)));
-        }
-        ern = fmin(fmin(ern, fmax(-sadj - qc, 0.0)), qr);
-        const double cond = sadj > -qc ? sadj : -qc;
-        rt[c] += r * (LV / (CPD * pie) * (cond - ern));
-        rqv[c] += r * (ern - cond);
-        rqc[c] += r * (cond - prod);
-        rqr[c] += r * (prod - ern);
-    }
+    ern = fmin(fmin(ern, fmax(-sadj - qc, 0.0)), qr);
+    const double cond = sadj > -qc ? sadj : -qc;
+    rt[c] += r * (LV / (CPD * pie) * (cond - ern));
+    rqv[c] += r * (ern - cond);
+    rqc[c] += r * (cond - prod);
+    rqr[c] += r * (prod - ern);
 }
 
 // ------------------------------------------------------------------ slow tendencies
@@ -997,6 +1000,75 @@ __global__ void k_tri_build(Geo g, const double *rho, const double *rt, const do
     }
 }
 
+// The same system for grids with few columns (a 2D slab has a few thousand): one warp per column.
+// The lanes form every level's face factors, w-face theta and row coefficients at once (the same
+// operands and operations as k_tri_build), then lane 0 runs only the LU recurrence
+// im_k = 1 / (b_k - a_k cp_{k-1}), cp_k = c_k im_k over shared memory.  Bit-identical to
+// k_tri_build.  nz <= TRIW_NZ.
+constexpr int TRIW_WARPS = 4, TRIW_NZ = 256;
+__global__ void __launch_bounds__(32 * TRIW_WARPS) k_tri_build_warp(Geo g, const double *rho, const double *rt,
+                                                                     const double *pi, const double *th, TriK tk,
+                                                                     Tri tr, double *TX, double *TY, double *PX,
+                                                                     double *PY, double *THW, Phys ph) {
+    __shared__ double sb[TRIW_WARPS][TRIW_NZ], sc[TRIW_WARPS][TRIW_NZ], sa[TRIW_WARPS][TRIW_NZ];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long n = (long long)blockIdx.x * TRIW_WARPS + warp;
+    if (n >= g.nxy) return;
+    const int i = (int)(n % g.nx), j = (int)(n / g.nx), nz = g.nz;
+    const double E = tk.E, EGg = tk.EGg;
+    for (int k = lane; k < nz; k += 32) {
+        long long c = cix(g, i, j, k);
+        double thc = th[c], pic = pi[c];
+        TX[c] = Hx(g, i, j, k) * (tk.hrdx * (cval(g, th, i - 1, j, k) + thc));
+        TY[c] = Hy(g, i, j, k) * (tk.hrdy * (cval(g, th, i, j - 1, k) + thc));
+        PX[c] = tk.dpx * (cval(g, pi, i - 1, j, k) + pic);
+        PY[c] = tk.dpx * (cval(g, pi, i, j - 1, k) + pic);
+        if (ph.moist) {
+            const double qc0 = q_vc(ph, c, rho[c]);
+            PX[c] /= 1.0 + 0.5 * (q_vc(ph, cixw(g, i - 1, j, k), cval(g, rho, i - 1, j, k)) + qc0);
+            PY[c] /= 1.0 + 0.5 * (q_vc(ph, cixw(g, i, j - 1, k), cval(g, rho, i, j - 1, k)) + qc0);
+        }
+        // w-face theta below cell k (the wall reflection at k = 0) and, for the top cell, at the lid
+        THW[c] = k == 0 ? thc : 0.5 * (th[c - g.nxy] + thc);
+        if (k == nz - 1) THW[cix(g, i, j, nz)] = thc;
+    }
+    for (int k = 1 + lane; k < nz; k += 32) {
+        long long c = cix(g, i, j, k), cm = c - g.nxy, w = c;
+        const double thw_m = k == 1 ? th[cm] : 0.5 * (th[cm - g.nxy] + th[cm]);
+        const double thw_k = 0.5 * (th[cm] + th[c]);
+        const double thw_p = 0.5 * (th[c] + cval(g, th, i, j, k + 1));
+        double pic = pi[c], pim = pi[cm];
+        double Spi = pim + pic;
+        double Cpg = tk.cpg * Spi * rdzcw(g, i, j, k);
+        double Cb = tk.kgb * (rho[cm] + rho[c]) * rcp_d(Spi);
+        if (ph.moist) {
+            Cpg /= 1.0 + 0.5 * (q_vc(ph, cm, rho[cm]) + q_vc(ph, c, rho[c]));
+            Cb /= 1.0 + 0.5 * (q_t(ph, cm, rho[cm]) + q_t(ph, c, rho[c]));
+        }
+        double rrt_c = rcp_d(rt[c]), rrt_m = rcp_d(rt[cm]), rHk = rHc(g, i, j, k), rHm = rHc(g, i, j, k - 1);
+        double P = fma(Cb * pic, rrt_c, -Cpg);
+        double Q = fma(Cb * pim, rrt_m, Cpg);
+        double Pe = E * P, Qe = E * Q;
+        double a = fma(-Qe, thw_m, EGg) * rHm;
+        double cc = fma(Pe, thw_p, -EGg) * rHk;
+        double b = fma(thw_k, fma(-Pe, rHk, Qe * rHm), 1.0);
+        b = fma(EGg, rHk - rHm, b);
+        tr.a[w] = a; tr.P[w] = P; tr.Q[w] = Q;
+        sa[warp][k] = a; sb[warp][k] = b; sc[warp][k] = cc;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        double cp_prev = 0.0;
+        for (int k = 1; k < nz; ++k) {
+            const long long w = cix(g, i, j, k);
+            double im = rcp_d(fma(-sa[warp][k], cp_prev, sb[warp][k]));
+            double cpk = sc[warp][k] * im;
+            tr.cp[w] = cpk; tr.im[w] = im;
+            cp_prev = cpk;
+        }
+    }
+}
+
 // horizontal momenta: Delta U'' = dtau (-gamma R_d pi^t (dTheta~/dxi - h_xi/h_zeta dTheta~/dzeta) + R_U),
 // Theta~ = Theta'' + beta_d (Theta'' - Theta''_prev) (reading R10), which the previous vertical
 // solve (or the stage start, where Theta~ = Theta'') left in Tt.  PX, PY hold the stage's
@@ -1133,6 +1205,88 @@ __global__ void __launch_bounds__(128) k_sub_col(int nz, long long nxy, const do
         om_up = om;
     }
     Om[n] = 0.0;
+}
+
+// Part 2 for grids with few columns: one warp per column.  The forward substitution
+// d'_k = (r_k - a_k d'_{k-1}) / m_k and the back substitution Omega_k = d'_k - c'_k Omega_{k+1} are
+// affine in their incoming value, so each lane takes a segment of at most SCW rows, composes its
+// segment's map x -> A x + B, a warp scan (shuffles) of the composed maps gives every lane its
+// incoming value, and the lane recomputes its rows with the same formulas as k_sub_col (the rows'
+// operands stay in registers).  The values differ from k_sub_col's at rounding level only (the
+// incoming values come through the composed maps).  nz <= 32 SCW + 1.
+constexpr int SCW = 8;
+__device__ __forceinline__ void affine_compose(double &A, double &B, double A2, double B2) {
+    // (A2, B2) after (A, B): x -> A2 (A x + B) + B2
+    B = fma(A2, B, B2);
+    A = A2 * A;
+}
+__global__ void __launch_bounds__(128) k_sub_col_warp(int nz, long long nxy, const double *__restrict__ ta,
+                                                      const double *__restrict__ tcp, const double *__restrict__ tim,
+                                                      const double *__restrict__ tP, const double *__restrict__ tQ,
+                                                      const double *__restrict__ X0, const double *__restrict__ Y0,
+                                                      double *__restrict__ W, double *__restrict__ Om, double Gg) {
+    const int lane = threadIdx.x & 31;
+    const long long n = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (n >= nxy) return;
+    const int rows = nz - 1, chunk = (rows + 31) / 32;
+    const int k0 = 1 + lane * chunk, k1 = min(k0 + chunk, nz);
+    double rv[SCW], av[SCW], iv[SCW], cv[SCW], dv[SCW];
+    // the rows' right-hand sides and factors; the segment's forward map
+    double A = 1.0, B = 0.0;
+    for (int u = 0; u < SCW; ++u) {
+        const int k = k0 + u;
+        if (k >= k1) break;
+        const long long c = n + (long long)k * nxy, cm = c - nxy;
+        rv[u] = W[c] + tP[c] * X0[c] + tQ[c] * X0[cm] - Gg * (Y0[c] + Y0[cm]);
+        av[u] = ta[c];
+        iv[u] = tim[c];
+        cv[u] = tcp[c];
+        affine_compose(A, B, -av[u] * iv[u], rv[u] * iv[u]);
+    }
+    // exclusive scan over the lanes (lane 0 starts from d'_0 = 0)
+    double sA = A, sB = B;
+    for (int o = 1; o < 32; o <<= 1) {
+        const double pA = __shfl_up_sync(0xffffffffu, sA, o), pB = __shfl_up_sync(0xffffffffu, sB, o);
+        if (lane >= o) { double a2 = sA, b2 = sB; sA = pA; sB = pB; affine_compose(sA, sB, a2, b2); }
+    }
+    double din = __shfl_up_sync(0xffffffffu, sB, 1);   // the composed maps applied to 0
+    if (lane == 0) din = 0.0;
+    double dpm = din;
+    for (int u = 0; u < SCW; ++u) {
+        const int k = k0 + u;
+        if (k >= k1) break;
+        const double dp = (rv[u] - av[u] * dpm) * iv[u];
+        dv[u] = dp;
+        dpm = dp;
+    }
+    // back substitution from the lid (Omega_nz = 0): the segment's map from above, a reverse scan
+    A = 1.0; B = 0.0;
+    for (int u = SCW - 1; u >= 0; --u) {
+        const int k = k0 + u;
+        if (k >= k1) continue;
+        affine_compose(A, B, -cv[u], dv[u]);
+    }
+    sA = A; sB = B;
+    for (int o = 1; o < 32; o <<= 1) {
+        const double pA = __shfl_down_sync(0xffffffffu, sA, o), pB = __shfl_down_sync(0xffffffffu, sB, o);
+        if (lane + o < 32) { double a2 = sA, b2 = sB; sA = pA; sB = pB; affine_compose(sA, sB, a2, b2); }
+    }
+    double oin = __shfl_down_sync(0xffffffffu, sB, 1);
+    if (lane == 31) oin = 0.0;
+    double om_up = oin;
+    for (int u = SCW - 1; u >= 0; --u) {
+        const int k = k0 + u;
+        if (k >= k1) continue;
+        const double om = dv[u] - cv[u] * om_up;
+        Om[n + (long long)k * nxy] = om;
+        om_up = om;
+    }
+    if (lane == 0) {
+        const long long top = n + (long long)nz * nxy;
+        W[top] = 0.0;
+        Om[top] = 0.0;
+        Om[n] = 0.0;
+    }
 }
 
 // Part 3, one thread per cell: Theta'', rho'' from the new Omega'' (beta_2 part), Theta~ of the
@@ -1305,6 +1459,16 @@ __global__ void k_f64_to_f32(const double *src, float *dst, long long n) {
 static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 constexpr int BS = 256;
 
+// the column kernels with one warp per column: -1 (default) below 2^15 columns, 0 never, 1 always
+// (nz <= 256); set per step enqueue by the handle (erf_set_option ERF_OPT_WARP_COLUMNS)
+static thread_local int g_warp_columns = -1;
+void set_warp_columns(int mode) { g_warp_columns = mode; }
+static bool warp_columns(const Geo &g) {
+    if (g.nz > TRIW_NZ) return false;
+    if (g_warp_columns >= 0) return g_warp_columns == 1;
+    return g.nxy < (1LL << 15);
+}
+
 // Optional per-launch event timing (profiling mode, never inside a graph capture).
 static thread_local ProfSink *g_prof = nullptr;
 void set_profiler(ProfSink *p) { g_prof = p; }
@@ -1359,8 +1523,9 @@ void launch_set_initial_moist(const Geo &g, const double *dth, const double *qv,
     LAUNCH("wall_bc", s, k_wall_bc<<<nblk(g.nxy, BS), BS, 0, s>>>(g, ru, rv, rw));
 }
 void launch_kessler(const Geo &g, double dt, double *rt, const double *rho, double *rqv, double *rqc, double *rqr,
-                    double *precip, cudaStream_t s) {
-    LAUNCH("kessler", s, k_kessler<<<nblk(g.nxy, 128), 128, 0, s>>>(g, dt, rt, rho, rqv, rqc, rqr, precip));
+                    double *precip, double *fscratch, cudaStream_t s) {
+    LAUNCH("kessler_fall", s, k_kessler_fall<<<nblk(g.nc, BS), BS, 0, s>>>(g, rho, rqr, fscratch));
+    LAUNCH("kessler", s, k_kessler<<<nblk(g.nc, BS), BS, 0, s>>>(g, dt, fscratch, rt, rho, rqv, rqc, rqr, precip));
 }
 void launch_set_initial(const Geo &g, const double *dth, const double *u, const double *v, const double *w,
                         double *rho, double *rt, double *ru, double *rv, double *rw, cudaStream_t s) {
@@ -1447,8 +1612,12 @@ void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const dou
     tk.dpx = -tk.cpg;
     tk.hrdx = 0.5 * g.rdx;
     tk.hrdy = 0.5 * g.rdy;
-    LAUNCH("tri_build", s, k_tri_build<<<nblk(g.nxy, 128), 128, 0, s>>>(g, rho, rt, pi, th, tk, tr, TX, TY, PX, PY,
-                                                                        THW, ph));
+    if (warp_columns(g))
+        LAUNCH("tri_build", s, k_tri_build_warp<<<nblk(g.nxy, TRIW_WARPS), 32 * TRIW_WARPS, 0, s>>>(
+                                   g, rho, rt, pi, th, tk, tr, TX, TY, PX, PY, THW, ph));
+    else
+        LAUNCH("tri_build", s, k_tri_build<<<nblk(g.nxy, 128), 128, 0, s>>>(g, rho, rt, pi, th, tk, tr, TX, TY, PX, PY,
+                                                                            THW, ph));
 }
 void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *PX, const double *PY, const double *thw,
                     const double *TX, const double *TY, CF5 R, F5 x, double *Om, double *Tp, double *X0, double *Y0,
@@ -1458,6 +1627,10 @@ void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *PX, cons
     LAUNCH("sub_horiz", s, k_sub_horiz<<<nblk(g.nc, BS), BS, 0, s>>>(g, PX, PY, Tp, R.u, R.v, x.u, x.v, dtau));
     LAUNCH("sub_expl", s, k_sub_expl<<<g3c, 128, 0, s>>>(g, ph, thw, TX, TY, R.r, R.t, R.w, x, Om, Tp, X0, Y0, Ash,
                                                          msx, msy, msz, dtau));
+    if (warp_columns(g))
+        LAUNCH("sub_col", s, k_sub_col_warp<<<nblk(g.nxy, 4), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q,
+                                                                           X0, Y0, x.w, Om, dtau * 0.5 * ph.g));
+    else
     LAUNCH("sub_col", s, k_sub_col<<<nblk(g.nxy, 128), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q, X0, Y0,
                                                                     x.w, Om, dtau * 0.5 * ph.g));
     LAUNCH("sub_fin", s, k_sub_fin<<<g3c, 128, 0, s>>>(g, ph, thw, Om, Ash, x, Tp, msz, dtau * ph.b2));

@@ -16,8 +16,9 @@ void launch_base_state(const Geo &g, int n_knots, const double *kz, const double
 void launch_set_initial_moist(const Geo &g, const double *dth, const double *qv, const double *u, const double *v,
                               const double *w, double *rho, double *rt, double *ru, double *rv, double *rw,
                               double *rqv, double *rqc, double *rqr, cudaStream_t s);
+// fscratch: nc doubles for the rain-fall fluxes
 void launch_kessler(const Geo &g, double dt, double *rt, const double *rho, double *rqv, double *rqc, double *rqr,
-                    double *precip, cudaStream_t s);
+                    double *precip, double *fscratch, cudaStream_t s);
 // moisture sources of the slow pass (diffusion, relaxation) and the relaxation reference state:
 // ref[0..4] = rho, rho theta, rho u, rho v, rho w; ref[5..7] = rho q_v, q_c, q_r (ref[0] null: no
 // relaxation zones); src[0..2] receive the moisture sources
@@ -58,6 +59,8 @@ void launch_column_block(void *field, void *buf, int elem_bytes, int nx, int ny,
                          int j0, int nj, int unpack, cudaStream_t s);
 
 constexpr int DIAG_PARTS = 512;
+// mode of the one-warp-per-column kernels for the launches that follow (-1 by column count)
+void set_warp_columns(int mode);
 
 // receives (kernel name, start event, stop event) for every launch while profiling is on
 struct ProfSink {

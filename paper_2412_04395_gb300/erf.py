@@ -23,6 +23,7 @@ FIELDS = {"rho": 0, "rhotheta": 1, "rhou": 2, "rhov": 3, "rhow": 4,
 ERF_F64, ERF_F32 = 0, 1
 ERF_OPT_TMA_STENCILS = 1
 ERF_OPT_COLUMN_FUSION = 2
+ERF_OPT_WARP_COLUMNS = 3
 
 # symbols the library must export (checked by the CPU tests)
 EXPORTS = ["erf_workspace_bytes", "erf_init_grid", "erf_set_initial", "erf_set_state", "erf_rk3_step",
