@@ -211,16 +211,21 @@ def aposteriori(fine_d, fine: W.Workload, cw: W.Workload, blob: bytes, r: int, h
 
 
 def run(grid=(256, 256, 128), dx=10.0, dt=0.1, spinup=6000, snapshots=10, every=300, test_every=5,
-        epochs=20, batch=8192, lr=1e-3, seed=7, horizons=(), log=print):
+        epochs=20, batch=8192, lr=1e-3, seed=7, horizons=(), log=print, holdout_last=0):
     """Every test_every-th snapshot is held out (interleaved, so train and test see the same
-    stage of the boundary layer's development).  With horizons (fine steps), the fine run goes
-    on after the last snapshot for the a-posteriori comparison."""
+    stage of the boundary layer's development), or, with holdout_last > 0, the last holdout_last
+    snapshots (the test set then lies later in time than anything trained on).  With horizons
+    (fine steps), the fine run goes on after the last snapshot for the a-posteriori comparison."""
     nx, ny, nz = grid
     r = 4
     fine = W.convective_abl(nx=nx, ny=ny, nz=nz, dx=dx).with_(dt=dt)
     res = collect(fine, r, spinup, snapshots, every, log, keep_fine=bool(horizons))
     Xs, Ts, states, cw = res[:4]
-    test_idx = [i for i in range(snapshots) if i % test_every == test_every - 1]
+    if holdout_last > 0:
+        assert holdout_last < snapshots
+        test_idx = list(range(snapshots - holdout_last, snapshots))
+    else:
+        test_idx = [i for i in range(snapshots) if i % test_every == test_every - 1]
     train_idx = [i for i in range(snapshots) if i not in test_idx]
     params, stats, losses = train(Xs, Ts, train_idx, epochs, batch, lr, seed, log)
     blob = blob_from(params, stats)
@@ -249,11 +254,13 @@ def main():
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--horizons", type=int, nargs="*", default=[],
                     help="a-posteriori comparison after these numbers of fine steps (multiples of 4)")
+    ap.add_argument("--holdout-last", type=int, default=0,
+                    help="hold out the last N snapshots instead of every test-every-th")
     ap.add_argument("--report", default=None)
     args = ap.parse_args()
     blob, ap, losses, cw, post = run(tuple(args.grid), args.dx, args.dt, args.spinup, args.snapshots, args.every,
                                      args.test_every, args.epochs, args.batch, args.lr, args.seed,
-                                     tuple(args.horizons))
+                                     tuple(args.horizons), holdout_last=args.holdout_last)
     open(args.out, "wb").write(blob)
     print(f"wrote {args.out} ({len(blob)} bytes)")
     if args.report:
