@@ -80,8 +80,8 @@ KERNEL_TRAFFIC_PER_UNIT_MIXED = {}
 # mixed path: algorithmic bytes per cell per launch (FP32 fields, FP64 LU factors and d');
 # these kernels are bound by HBM or latency, so their roofline is in GB/s
 KERNEL_MODEL_MIXED = {
-    "mx_sub_vert":    {"unit": "cell", "bytes": 96},
-    "mx_sub_col":     {"unit": "cell", "bytes": 72},
+    "mx_sub_vert":    {"unit": "cell", "bytes": 92},
+    "mx_sub_col":     {"unit": "cell", "bytes": 68},
     "mx_sub_expl":    {"unit": "cell", "bytes": 52},
     "mx_sub_fin":     {"unit": "cell", "bytes": 32},
     "mx_sub_horiz":   {"unit": "cell", "bytes": 32},
@@ -100,7 +100,7 @@ KERNEL_MODEL_MIXED = {
     "mx_rhs_u":       {"unit": "cell", "bytes": 28},
     "mx_rhs_v":       {"unit": "cell", "bytes": 28},
     "mx_rhs_w":       {"unit": "wface", "bytes": 24},
-    "mx_tri_build":   {"unit": "cell", "bytes": 48},
+    "mx_tri_build":   {"unit": "cell", "bytes": 44},
     "mx_stage_begin": {"unit": "wface", "bytes": 76},
     "mx_prep":        {"unit": "wface", "bytes": 36},
     "mx_stage_end":   {"unit": "wface", "bytes": 60},

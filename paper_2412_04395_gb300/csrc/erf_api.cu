@@ -76,6 +76,7 @@ struct erf_handle {
     double *pp, *pi, *th, *Tp, *Om;
     Tri tri;
     TriM mtri;
+    double *mstage = nullptr;
     double *ux, *vy, *wz, *mfx, *mfy, *rom, *mu, *flux;
     double *diag_part, *diag_out;
     // mixed-precision path (flat grids): FP32 perturbation fields + FP64 solve scratch
@@ -249,7 +250,8 @@ static size_t carve(erf_handle *h, const erf_grid_desc *g, const erf_config *c, 
         // the flux planes are free during the substeps, which keep X0 and Y0 there
         H->mflux = cv.take<float>(3 * nw);
         H->mX0 = H->mflux; H->mY0 = H->mflux + nw;
-        H->mtri.a = cv.take<double>(nw); H->mtri.cp = cv.take<double>(nw); H->mtri.im = cv.take<double>(nw);
+        H->mstage = cv.take<double>(nw);   // FP64 staging outside the step; the stage's sub-diagonal during it
+        H->mtri.a = reinterpret_cast<float *>(H->mstage); H->mtri.cp = cv.take<double>(nw); H->mtri.im = cv.take<double>(nw);
         H->mtri.P = cv.take<float>(nw); H->mtri.Q = cv.take<float>(nw);
         if (c->tracer) {
             H->mtphi = cv.take<float>(nc); H->msnphi = cv.take<float>(nc);
@@ -894,7 +896,7 @@ extern "C" erf_status erf_set_initial(erf_handle *h, const double *dtheta, const
     if (h->mixed) {
         // FP64 staging in the (not yet used) LU arrays and solve scratch
         const double *src[4] = {dtheta, u, v, w};
-        double *stage[4] = {h->mtri.a, h->mtri.cp, h->mtri.im, h->mdbuf};
+        double *stage[4] = {h->mstage, h->mtri.cp, h->mtri.im, h->mdbuf};
         long long len[4] = {g.nc, g.nc, g.nc, g.nw};
         const double *dev[4] = {nullptr, nullptr, nullptr, nullptr};
         for (int n = 0; n < 4; ++n) {
@@ -1000,7 +1002,7 @@ extern "C" erf_status erf_set_state(erf_handle *h, int32_t field, const void *sr
         const double *d64 = nullptr;
         if (src_dtype == ERF_F64 && src_is_device) d64 = (const double *)src;
         else {
-            double *stg = h->mtri.a;
+            double *stg = h->mstage;
             if (src_dtype == ERF_F64) {
                 e = cudaMemcpyAsync(stg, src, n * sizeof(double), cudaMemcpyHostToDevice, s);
             } else {

@@ -107,25 +107,129 @@ __device__ __forceinline__ float silu_half(float acc, float hb) {
 
 // Learned SGS stress/heat flux at every cell (mixed path), with Smagorinsky as the per-cell
 // fallback and backscatter limited to half the Smagorinsky transfer.  Persistent CTAs of 128
-// threads load the weights once into the canonical K-major operand layout, allocate 64 TMEM
-// columns and loop over 128-cell tiles.  Every wait on the MMA barrier is bounded: a CTA whose
-// wait gives up sets bit 2 of *err, waits once more (bounded) for its MMAs, frees its TMEM and
-// stops.
+// threads load the weights once into the canonical K-major operand layout and loop over 128-cell
+// tiles.  Every wait on an MMA barrier is bounded: a CTA whose wait gives up sets bit 2 of *err,
+// waits once more (bounded) for its MMAs, frees its TMEM and stops.
 // out: 9 planes of nc floats: rho t11, rho t22, rho t33, rho t12, rho t13, rho t23, rho h1..h3.
 constexpr int CLT = 128;            // threads per CTA = cells per tile = MMA rows
-constexpr uint32_t CL_TCOLS = 64;   // TMEM columns per CTA (FP32 accumulators)
+constexpr int CL_NM = 18;           // per-cell values the output step needs (fallback, strain, bound)
+
+// Step 1 of a tile: cell c's standardised features (BF16) into its row of the activation
+// operand; the Smagorinsky fallback stresses m[0..8], the density m[9], the strain m[11..16] and
+// the backscatter bound m[17]; fb = 1 if a feature lies outside the training range (|z| > 6).
+__device__ __forceinline__ void cl_cell_inputs(const Geo &g, const MxBase &mb, const VelIn &v, const float *dr,
+                                               const float *in_mu, const float *in_rsd, float rPr, long long c,
+                                               bool valid, unsigned char *row, float *m, int &fb) {
+    float z[12];
+    for (int q = 0; q < 12; ++q) z[q] = 0.f;
+    for (int q = 0; q < CL_NM; ++q) m[q] = 0.f;
+    fb = 0;
+    if (valid) {
+        unsigned rw = (unsigned)(c / g.nx);
+        int i = (int)(c - (long long)rw * g.nx);
+        int j = (int)(rw % (unsigned)g.ny), k = (int)(rw / (unsigned)g.ny);
+        float f[12], dthdz;
+        cl_features(g, mb, v, i, j, k, f, dthdz);
+        for (int q = 0; q < 12; ++q) {
+            z[q] = (f[q] - in_mu[q]) * in_rsd[q];
+            if (!(fabsf(z[q]) <= 6.f)) fb = 1;
+        }
+        float s11 = f[0], s22 = f[4], s33 = f[8];
+        float s12 = 0.5f * (f[1] + f[3]), s13 = 0.5f * (f[2] + f[6]), s23 = 0.5f * (f[5] + f[7]);
+        float rho = mb.rho0f[k] + dr[c];
+        float SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.f * (s12 * s12 + s13 * s13 + s23 * s23);
+        float mu = rho * mb.delta2f[k] * sqrtf(2.f * SS);
+        float tr = (s11 + s22 + s33) * (1.f / 3.f);
+        m[0] = -2.f * mu * (s11 - tr); m[1] = -2.f * mu * (s22 - tr); m[2] = -2.f * mu * (s33 - tr);
+        m[3] = -2.f * mu * s12; m[4] = -2.f * mu * s13; m[5] = -2.f * mu * s23;
+        m[6] = -mu * rPr * f[9]; m[7] = -mu * rPr * f[10]; m[8] = -mu * rPr * dthdz;
+        m[9] = rho;
+        m[11] = s11; m[12] = s22; m[13] = s33; m[14] = s12; m[15] = s13; m[16] = s23;
+        // backscatter bound: the learned transfer -t_ij S_ij may not fall below -1/2 of the
+        // Smagorinsky transfer (both density-weighted)
+        float ps = -(m[0] * s11 + m[1] * s22 + m[2] * s33 + 2.f * (m[3] * s12 + m[4] * s13 + m[5] * s23));
+        m[17] = -0.5f * ps;
+    }
+    *reinterpret_cast<uint4 *>(row) =
+        make_uint4(pack_bf16(z[0], z[1]), pack_bf16(z[2], z[3]), pack_bf16(z[4], z[5]), pack_bf16(z[6], z[7]));
+    *reinterpret_cast<uint4 *>(row + 128) = make_uint4(pack_bf16(z[8], z[9]), pack_bf16(z[10], z[11]), 0u, 0u);
+}
+
+// Step 2: this thread's accumulator row of a hidden layer (64 FP32 columns of TMEM) + bias,
+// SiLU, back into its operand row as BF16 (hb: the layer's half biases)
+__device__ __forceinline__ void cl_row_silu(uint32_t tlane, const float *hb, unsigned char *row) {
+    for (int h = 0; h < 2; ++h) {
+        uint32_t r[32];
+        tc_ld32(tlane + 32u * h, r);
+        uint32_t pk[16];
+        for (int q = 0; q < 16; ++q)
+            pk[q] = pack_bf16(silu_half(__uint_as_float(r[2 * q]), hb[32 * h + 2 * q]),
+                              silu_half(__uint_as_float(r[2 * q + 1]), hb[32 * h + 2 * q + 1]));
+        for (int u = 0; u < 4; ++u)
+            *reinterpret_cast<uint4 *>(row + (4 * h + u) * 128) =
+                make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+    }
+}
+
+// Step 3: the output row (9 of 16 columns), de-standardised, density-weighted, bounded, or the
+// fallback; stored to the 9 planes
+__device__ __forceinline__ void cl_cell_output(uint32_t tlane, const float *sb4, const float *out_mu,
+                                               const float *out_sd, const float *m, int fb, bool valid,
+                                               long long c, long long nc, float *out, unsigned *nfallback) {
+    uint32_t r[16];
+    tc_ld16(tlane, r);
+    if (!valid) return;
+    int use_fb = fb;
+    float o[9];
+    for (int q = 0; q < 9; ++q) {
+        o[q] = (__uint_as_float(r[q]) + sb4[q]) * out_sd[q] + out_mu[q];
+        if (!isfinite(o[q])) use_fb = 1;
+    }
+    float rho = m[9];
+    for (int q = 0; q < 9; ++q) o[q] *= rho;
+    float pl = -(o[0] * m[11] + o[1] * m[12] + o[2] * m[13] + 2.f * (o[3] * m[14] + o[4] * m[15] + o[5] * m[16]));
+    if (pl < m[17]) {
+        float a = m[17] / pl;
+        for (int q = 0; q < 6; ++q) o[q] *= a;
+    }
+    for (int q = 0; q < 9; ++q) out[(long long)q * nc + c] = use_fb ? m[q] : o[q];
+    if (use_fb && nfallback) atomicAdd(nfallback, 1u);
+}
+
+// the MMAs of layer L (0: K = 16 -> N = 64; 1, 2: K = 64 -> N = 64; 3: K = 64 -> N = 16) of the
+// tile whose operand is dA into the accumulator at TMEM address tm; issued by one thread
+struct ClDesc {
+    uint64_t W1, W2, W3, W4;
+};
+__device__ __forceinline__ void cl_issue_layer(int layer, uint32_t tm, uint64_t dA, const ClDesc &dw) {
+    constexpr uint32_t I64 = tc_idesc_bf16(128, 64), I16 = tc_idesc_bf16(128, 16);
+    if (layer == 0) {
+        tc_mma_bf16(tm, dA, dw.W1, I64, 0u);
+    } else {
+        const uint64_t dW = layer == 1 ? dw.W2 : (layer == 2 ? dw.W3 : dw.W4);
+        const uint32_t id = layer == 3 ? I16 : I64;
+        for (int s = 0; s < 4; ++s) tc_mma_bf16(tm, dA + 16u * s, dW + 16u * s, id, s > 0 ? 1u : 0u);
+    }
+}
+
+// One tile per pass: 128 threads, 64 TMEM columns and 38 KB of static shared memory per CTA,
+// five CTAs per SM.  Measured and not kept: two tiles in flight per CTA (while the tensor cores run
+// one tile's layer the threads run the other's SiLU; three CTAs per SM for its 73 KB of shared
+// memory) took 200 ms per step at 2048^2 x 160 against 141 ms; the kernel is bound by its SIMT
+// work's issue and latency at the warps an SM holds, not by the MMA round trips.
+constexpr uint32_t CL_TCOLS = 64;
 constexpr int CL_CTAS_PER_SM = 5;
 __global__ void __launch_bounds__(CLT, CL_CTAS_PER_SM) k_cl_infer(Geo g, MxBase mb, Phys ph, ClDev cl, VelIn v,
-                                                                  const float *dr, float *out, unsigned *nfallback,
-                                                                  unsigned *err) {
-    __shared__ __align__(1024) unsigned char sA[128 * 64 * 2];   // activations [128 cells][64], K-major
-    __shared__ __align__(1024) unsigned char sW1[64 * 16 * 2];   // [64 out][16 in] (12 used)
+                                                                    const float *dr, float *out, unsigned *nfallback,
+                                                                    unsigned *err) {
+    __shared__ __align__(1024) unsigned char sA[128 * 64 * 2];
+    __shared__ __align__(1024) unsigned char sW1[64 * 16 * 2];
     __shared__ __align__(1024) unsigned char sW2[64 * 64 * 2];
     __shared__ __align__(1024) unsigned char sW3[64 * 64 * 2];
-    __shared__ __align__(1024) unsigned char sW4[16 * 64 * 2];   // [16 out (9 used)][64 in]
-    __shared__ float shb[3 * 64];                               // half biases of the hidden layers
+    __shared__ __align__(1024) unsigned char sW4[16 * 64 * 2];
+    __shared__ float shb[3 * 64];
     __shared__ float sb4[16];
-    __shared__ float sst[2 * CL_NIN + 2 * CL_NOUT];             // in_mean, 1/in_std, out_mean, out_std
+    __shared__ float sst[2 * CL_NIN + 2 * CL_NOUT];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t s_taddr;
     const int t = threadIdx.x, warp = t >> 5;
@@ -148,17 +252,14 @@ __global__ void __launch_bounds__(CLT, CL_CTAS_PER_SM) k_cl_infer(Geo g, MxBase 
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tm = s_taddr, tlane = tm + ((uint32_t)(32 * warp) << 16);   // this warp's 32 TMEM lanes
+    const uint32_t tm = s_taddr, tlane = tm + ((uint32_t)(32 * warp) << 16);
     const uint64_t dA = tc_smem_desc(smem_u32(sA), 128, 1024);
-    const uint64_t dW1 = tc_smem_desc(smem_u32(sW1), 128, 256), dW2 = tc_smem_desc(smem_u32(sW2), 128, 1024);
-    const uint64_t dW3 = tc_smem_desc(smem_u32(sW3), 128, 1024), dW4 = tc_smem_desc(smem_u32(sW4), 128, 1024);
-    constexpr uint32_t I64 = tc_idesc_bf16(128, 64), I16 = tc_idesc_bf16(128, 16);
+    const ClDesc dw{tc_smem_desc(smem_u32(sW1), 128, 256), tc_smem_desc(smem_u32(sW2), 128, 1024),
+                    tc_smem_desc(smem_u32(sW3), 128, 1024), tc_smem_desc(smem_u32(sW4), 128, 1024)};
     const float *in_mu = sst, *in_rsd = sst + 12, *out_mu = sst + 24, *out_sd = sst + 33;
-    const float rPr = mb.rPr;
-    unsigned char *row = sA + (t >> 3) * 1024 + (t & 7) * 16;   // row t, core-matrix column 0
+    unsigned char *row = sA + (t >> 3) * 1024 + (t & 7) * 16;
     unsigned phase = 0, pend = 0;
-    int timeout = 0;
-    // all threads: this layer's operand is written and the previous TMEM reads are done
+    int timeout = 0, aborted = 0;
     auto sync_layer = [&]() -> int {
         fence_async_smem();
         tc_fence_before();
@@ -166,109 +267,32 @@ __global__ void __launch_bounds__(CLT, CL_CTAS_PER_SM) k_cl_infer(Geo g, MxBase 
         tc_fence_after();
         return ab;
     };
-    auto wait_mma = [&]() {
+    auto run_layer = [&](int layer) {
+        if (t == 0) {
+            cl_issue_layer(layer, tm, dA, dw);
+            tc_commit(&bar);
+        }
         pend = phase;
         if (!mbar_wait_bounded(&bar, phase, TMA_MAX_POLLS)) timeout = 1;
         phase ^= 1u;
         tc_fence_after();
     };
     const long long ntiles = (g.nc + CLT - 1) / CLT;
-    int aborted = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long long c = tile * CLT + t;
         const bool valid = c < g.nc;
-        // 1. features (standardised, BF16) into row t; fallback stresses and S_ij in registers
-        float m[18];
-        int fb = 0;
-        {
-            float z[12];
-            for (int q = 0; q < 12; ++q) z[q] = 0.f;
-            m[9] = 0.f;
-            if (valid) {
-                unsigned rw = (unsigned)(c / g.nx);
-                int i = (int)(c - (long long)rw * g.nx);
-                int j = (int)(rw % (unsigned)g.ny), k = (int)(rw / (unsigned)g.ny);
-                float f[12], dthdz;
-                cl_features(g, mb, v, i, j, k, f, dthdz);
-                for (int q = 0; q < 12; ++q) {
-                    z[q] = (f[q] - in_mu[q]) * in_rsd[q];
-                    if (!(fabsf(z[q]) <= 6.f)) fb = 1;
-                }
-                float s11 = f[0], s22 = f[4], s33 = f[8];
-                float s12 = 0.5f * (f[1] + f[3]), s13 = 0.5f * (f[2] + f[6]), s23 = 0.5f * (f[5] + f[7]);
-                float rho = mb.rho0f[k] + dr[c];
-                float SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.f * (s12 * s12 + s13 * s13 + s23 * s23);
-                float mu = rho * mb.delta2f[k] * sqrtf(2.f * SS);
-                float tr = (s11 + s22 + s33) * (1.f / 3.f);
-                m[0] = -2.f * mu * (s11 - tr); m[1] = -2.f * mu * (s22 - tr); m[2] = -2.f * mu * (s33 - tr);
-                m[3] = -2.f * mu * s12; m[4] = -2.f * mu * s13; m[5] = -2.f * mu * s23;
-                m[6] = -mu * rPr * f[9]; m[7] = -mu * rPr * f[10]; m[8] = -mu * rPr * dthdz;
-                m[9] = rho;
-                m[11] = s11; m[12] = s22; m[13] = s33; m[14] = s12; m[15] = s13; m[16] = s23;
-                // backscatter bound: the learned transfer -t_ij S_ij may not fall below -1/2 of
-                // the Smagorinsky transfer (both density-weighted)
-                float ps = -(m[0] * s11 + m[1] * s22 + m[2] * s33 + 2.f * (m[3] * s12 + m[4] * s13 + m[5] * s23));
-                m[17] = -0.5f * ps;
-            }
-            *reinterpret_cast<uint4 *>(row) =
-                make_uint4(pack_bf16(z[0], z[1]), pack_bf16(z[2], z[3]), pack_bf16(z[4], z[5]), pack_bf16(z[6], z[7]));
-            *reinterpret_cast<uint4 *>(row + 128) = make_uint4(pack_bf16(z[8], z[9]), pack_bf16(z[10], z[11]), 0u, 0u);
-        }
-        // 2. three hidden layers: MMA into TMEM, then bias + SiLU back into the operand
+        float m[CL_NM];
+        int fb;
+        cl_cell_inputs(g, mb, v, dr, in_mu, in_rsd, mb.rPr, c, valid, row, m, fb);
         for (int layer = 0; layer < 3 && !aborted; ++layer) {
             if (sync_layer()) { aborted = 1; break; }
-            if (t == 0) {
-                if (layer == 0) {
-                    tc_mma_bf16(tm, dA, dW1, I64, 0u);
-                } else {
-                    const uint64_t dW = layer == 1 ? dW2 : dW3;
-                    for (int s = 0; s < 4; ++s) tc_mma_bf16(tm, dA + 16u * s, dW + 16u * s, I64, s > 0 ? 1u : 0u);
-                }
-                tc_commit(&bar);
-            }
-            wait_mma();
-            const float *hb = shb + 64 * layer;
-            for (int h = 0; h < 2; ++h) {
-                uint32_t r[32];
-                tc_ld32(tlane + 32u * h, r);
-                uint32_t pk[16];
-                for (int q = 0; q < 16; ++q)
-                    pk[q] = pack_bf16(silu_half(__uint_as_float(r[2 * q]), hb[32 * h + 2 * q]),
-                                      silu_half(__uint_as_float(r[2 * q + 1]), hb[32 * h + 2 * q + 1]));
-                for (int u = 0; u < 4; ++u)
-                    *reinterpret_cast<uint4 *>(row + (4 * h + u) * 128) =
-                        make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
-            }
+            run_layer(layer);
+            cl_row_silu(tlane, shb + 64 * layer, row);
         }
         if (aborted || sync_layer()) { aborted = 1; break; }
-        // 3. output layer (N = 16, 9 used), de-standardise, fallback, density weighting, store
-        if (t == 0) {
-            for (int s = 0; s < 4; ++s) tc_mma_bf16(tm, dA + 16u * s, dW4 + 16u * s, I16, s > 0 ? 1u : 0u);
-            tc_commit(&bar);
-        }
-        wait_mma();
-        uint32_t r[16];
-        tc_ld16(tlane, r);
-        if (valid) {
-            int use_fb = fb;
-            float o[9];
-            for (int q = 0; q < 9; ++q) {
-                o[q] = (__uint_as_float(r[q]) + sb4[q]) * out_sd[q] + out_mu[q];
-                if (!isfinite(o[q])) use_fb = 1;
-            }
-            float rho = m[9];
-            for (int q = 0; q < 9; ++q) o[q] *= rho;
-            float pl = -(o[0] * m[11] + o[1] * m[12] + o[2] * m[13] + 2.f * (o[3] * m[14] + o[4] * m[15] + o[5] * m[16]));
-            if (pl < m[17]) {
-                float a = m[17] / pl;
-                for (int q = 0; q < 6; ++q) o[q] *= a;
-            }
-            for (int q = 0; q < 9; ++q) out[(long long)q * g.nc + c] = use_fb ? m[q] : o[q];
-            if (use_fb && nfallback) atomicAdd(nfallback, 1u);
-        }
+        run_layer(3);
+        cl_cell_output(tlane, sb4, out_mu, out_sd, m, fb, valid, c, g.nc, out, nfallback);
     }
-    // the last output layer's wait, then release: on a timeout report it and give the MMAs one
-    // more bounded wait before the TMEM is freed
     tc_fence_before();
     if (__syncthreads_or(timeout) || aborted) {
         if (t == 0 && err) atomicOr(err, 2u);
@@ -279,6 +303,7 @@ __global__ void __launch_bounds__(CLT, CL_CTAS_PER_SM) k_cl_infer(Geo g, MxBase 
     tc_fence_after();
     if (warp == 0) tc_dealloc(tm, CL_TCOLS);
 }
+
 
 // Self-test of the tensor-core path on exact integer data: the operand shapes of the network
 // (K = 64 with N = 64 and with N = 16; K = 16 with N = 64) through the same descriptors and

@@ -808,7 +808,7 @@ __global__ void k_mx_tri_build(Geo g, MxBase mb, Phys ph, const float *dr, const
         double m = (double)b - (double)a * cp_prev;
         double im = rcp_d(m);
         double cpk = (double)cc * im;
-        tr.a[c] = (double)a; tr.cp[c] = cpk; tr.im[c] = im; tr.P[c] = P; tr.Q[c] = Q;
+        tr.a[c] = a; tr.cp[c] = cpk; tr.im[c] = im; tr.P[c] = P; tr.Q[c] = Q;
         cp_prev = cpk;
         rrt_m = rrt_c;
         thw_m = thw_k; thw_k = thw_p;
@@ -912,7 +912,7 @@ __device__ __forceinline__ void mx_back_substitute(int nz, long long nxy, long l
 // Only the two recurrences are serial; every load is independent of them, so the unrolled loop
 // keeps several levels of loads in flight.
 template <int UNROLL>
-__global__ void __launch_bounds__(128) k_mx_sub_col(int nz, long long nxy, const double *__restrict__ ta,
+__global__ void __launch_bounds__(128) k_mx_sub_col(int nz, long long nxy, const float *__restrict__ ta,
                                                     const double *__restrict__ tcp, const double *__restrict__ tim,
                                                     const float *__restrict__ tP, const float *__restrict__ tQ,
                                                     const float *__restrict__ X0, const float *__restrict__ Y0,
@@ -927,7 +927,7 @@ __global__ void __launch_bounds__(128) k_mx_sub_col(int nz, long long nxy, const
         long long c = n + k * nxy;
         float X0c = X0[c], Y0c = Y0[c];
         float rhs = W[c] + dtf * Rw[c] + tP[c] * X0c + tQ[c] * X0m - Gg * (Y0c + Y0m);
-        double dp = ((double)rhs - ta[c] * dpm) * tim[c];
+        double dp = ((double)rhs - (double)ta[c] * dpm) * tim[c];
         dbuf[c] = dp;
         dpm = dp;
         X0m = X0c; Y0m = Y0c;
@@ -944,7 +944,7 @@ template <int UNROLL>
 __global__ void __launch_bounds__(128, 8) k_mx_sub_vert(Geo g, MxBase mb, const float *__restrict__ thp,
                                                         const float *__restrict__ Rr, const float *__restrict__ Rt,
                                                         const float *__restrict__ Rw, F5f x, float *__restrict__ Tt,
-                                                        const double *__restrict__ ta, const double *__restrict__ tcp,
+                                                        const float *__restrict__ ta, const double *__restrict__ tcp,
                                                         const double *__restrict__ tim, const float *__restrict__ tP,
                                                         const float *__restrict__ tQ, double *__restrict__ dbuf,
                                                         float dtf, float Gg, TrSum ms) {
@@ -1001,7 +1001,7 @@ __global__ void __launch_bounds__(128, 8) k_mx_sub_vert(Geo g, MxBase mb, const 
         float X0c, Y0c;
         cell(k, om_k, om_p, X0c, Y0c);
         float rhs = om_k + dtf * Rw[c] + tP[c] * X0c + tQ[c] * X0m - Gg * (Y0c + Y0m);
-        double dp = ((double)rhs - ta[c] * dpm) * tim[c];
+        double dp = ((double)rhs - (double)ta[c] * dpm) * tim[c];
         dbuf[c] = dp;
         dpm = dp;
         X0m = X0c; Y0m = Y0c;

@@ -41,8 +41,11 @@ inline void mx_base_scalars(MxBase &mb, const Geo &g, const Phys &ph) {
 __device__ __forceinline__ float mx_dth0(const MxBase &mb, int ka, int kb) { return mb.dth0t[kb * 7 + (ka - kb) + 3]; }
 
 // stage LU factors of the vertical system in FP64 and its right-hand-side coefficients in FP32
+// a (the sub-diagonal) is formed in FP32 from the FP32 stage fields, so it is stored in FP32 with
+// no loss; the elimination reads it as the exact FP64 value
 struct TriM {
-    double *a, *cp, *im;
+    float *a;
+    double *cp, *im;
     float *P, *Q;
 };
 

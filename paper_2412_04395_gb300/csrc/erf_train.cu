@@ -56,13 +56,31 @@ __global__ void k_act_back(float *G, const float *Z, long long n) {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t < n) G[t] *= dsilu_f(Z[t]);
 }
-// out[c] = sum over rows of G[r][c] in row order (one thread per column)
-__global__ void k_colsum(const float *G, long long rows, int cols, float *out) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
+// Column reductions, one CTA of CS_T threads per column: thread q sums rows q, q + CS_T, ... in
+// order, then a fixed binary tree over the threads; the order is fixed, so the result is
+// reproducible bit for bit.
+constexpr int CS_T = 256;
+template <class T>
+__device__ __forceinline__ T cta_tree_sum(T v, T *sh) {
+    const int q = threadIdx.x;
+    sh[q] = v;
+    __syncthreads();
+    for (int w = CS_T / 2; w > 0; w >>= 1) {
+        if (q < w) sh[q] += sh[q + w];
+        __syncthreads();
+    }
+    const T r = sh[0];
+    __syncthreads();   // sh may be reused at once
+    return r;
+}
+// out[c] = sum over rows of G[r][c]
+__global__ void __launch_bounds__(CS_T) k_colsum(const float *G, long long rows, int cols, float *out) {
+    __shared__ float sh[CS_T];
+    const int c = blockIdx.x;
     float s = 0.f;
-    for (long long r = 0; r < rows; ++r) s += G[r * cols + c];
-    out[c] = s;
+    for (long long r = threadIdx.x; r < rows; r += CS_T) s += G[r * cols + c];
+    s = cta_tree_sum(s, sh);
+    if (threadIdx.x == 0) out[c] = s;
 }
 // dY = 2 (Y - T) / (rows cols); per-block partial sums of (Y - T)^2
 __global__ void k_mse(const float *Y, const float *T, float *dY, long long n, float scale, float *part) {
@@ -99,16 +117,19 @@ __global__ void k_adam(float *p, const float *g, float *m, float *v, int n, floa
     v[t] = vt;
     p[t] -= lr * (mt / c1) / (sqrtf(vt / c2) + eps);
 }
-// column mean / standard deviation over rows (FP64 accumulation, one thread per column)
-__global__ void k_col_stats(const float *A, long long rows, int cols, float *mean, float *sd) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
+// column mean / standard deviation over rows (FP64 accumulation, one CTA per column)
+__global__ void __launch_bounds__(CS_T) k_col_stats(const float *A, long long rows, int cols, float *mean, float *sd) {
+    __shared__ double sh[CS_T];
+    const int c = blockIdx.x;
     double s = 0.0, s2 = 0.0;
-    for (long long r = 0; r < rows; ++r) {
+    for (long long r = threadIdx.x; r < rows; r += CS_T) {
         double x = A[r * cols + c];
         s += x;
         s2 += x * x;
     }
+    s = cta_tree_sum(s, sh);
+    s2 = cta_tree_sum(s2, sh);
+    if (threadIdx.x != 0) return;
     double mu = s / (double)rows;
     double var = s2 / (double)rows - mu * mu;
     double d = var > 0.0 ? sqrt(var) : 0.0;
@@ -182,7 +203,7 @@ static void fwd_bwd(const float *X, const float *T, int B, float *p, float *g, f
     k_loss_final<<<1, 32, 0, s>>>(part, (int)np, 1.f / (float)ny, d_loss);
     // backward: layer 4
     gemm(O, H, B, dY, O, 1, A[2], H, 0, Gv.W[3], H, 0, s);
-    k_colsum<<<nb(O, 64), 64, 0, s>>>(dY, B, O, Gv.b[3]);
+    k_colsum<<<O, CS_T, 0, s>>>(dY, B, O, Gv.b[3]);
     gemm(B, H, O, dY, O, 0, P.W[3], H, 0, G0, H, 0, s);
     float *gcur = G0, *gnext = G1;
     for (int l = 2; l >= 0; --l) {
@@ -190,7 +211,7 @@ static void fwd_bwd(const float *X, const float *T, int B, float *p, float *g, f
         const float *a_in = l == 0 ? X : A[l - 1];
         int nin_l = l == 0 ? I : H;
         gemm(H, nin_l, B, gcur, H, 1, a_in, nin_l, 0, Gv.W[l], nin_l, 0, s);
-        k_colsum<<<nb(H, 64), 64, 0, s>>>(gcur, B, H, Gv.b[l]);
+        k_colsum<<<H, CS_T, 0, s>>>(gcur, B, H, Gv.b[l]);
         if (l > 0) {
             gemm(B, H, H, gcur, H, 0, P.W[l], H, 0, gnext, H, 0, s);
             float *t = gcur; gcur = gnext; gnext = t;
@@ -244,7 +265,7 @@ extern "C" erf_status erf_train_closure(const erf_train_cfg *cfg, const float *d
 extern "C" erf_status erf_column_stats(const float *d_A, int64_t rows, int32_t cols, float *d_mean, float *d_std,
                                        void *cuda_stream) {
     if (!d_A || !d_mean || !d_std || rows < 1 || cols < 1) return ERF_EINVAL;
-    k_col_stats<<<nb(cols, 64), 64, 0, reinterpret_cast<cudaStream_t>(cuda_stream)>>>(d_A, rows, cols, d_mean, d_std);
+    k_col_stats<<<cols, CS_T, 0, reinterpret_cast<cudaStream_t>(cuda_stream)>>>(d_A, rows, cols, d_mean, d_std);
     return cudaGetLastError() == cudaSuccess ? ERF_OK : ERF_ECUDA;
 }
 
