@@ -10,6 +10,11 @@ values is index (m * STRIDE) mod n, with STRIDE a prime that divides no field si
 SAMPLES indices are distinct and spread over the whole field.  Run (about an hour on 8 cores):
 
     python tests/golden/make_hill_bubble_500.py [--threads N]
+
+With --ulp-floor it instead measures the run's round-off floor: the oracle from the same initial
+state with rho theta perturbed by a seeded random relative 1.1e-16 (about one ulp), 500 steps, and
+the relative L2 of its difference from the stored values on the same samples, written (five
+numbers, one per field) to hill_bubble_256x256x128_500steps_ulp.json.
 """
 import argparse
 import os
@@ -39,6 +44,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
     ap.add_argument("--out", default=OUT)
+    ap.add_argument("--ulp-floor", action="store_true")
     args = ap.parse_args()
     import oracle
     from oracle import Oracle, OracleConfig
@@ -53,12 +59,27 @@ def main():
                        brunt_N=wl.brunt_N, p_s=wl.p_s)
     o = Oracle(cfg, wl.zeta, wl.terrain, wl.knots)
     o.set_initial(wl.dtheta, wl.u, wl.v, wl.w)
+    if args.ulp_floor:
+        r = o.get("rhotheta")
+        o.set("rhotheta", r * (1 + 1.1e-16 * np.random.default_rng(1).standard_normal(r.shape)))
     mass0 = o.mass()
     t0 = time.time()
     for s in range(STEPS):
         o.step(1)
         if (s + 1) % 25 == 0:
             print(f"step {s + 1}/{STEPS}  {time.time() - t0:.0f} s", flush=True)
+    if args.ulp_floor:
+        import json
+        g = np.load(args.out)
+        floor = {}
+        for f in FIELDS:
+            a = o.get(f).ravel()[sample_indices(o.get(f).size)]
+            floor[f] = float(np.linalg.norm(a - g[f]) / np.linalg.norm(g[f]))
+        path = os.path.join(HERE, "hill_bubble_256x256x128_500steps_ulp.json")
+        json.dump({"steps": STEPS, "perturbation": "rho theta x (1 + 1.1e-16 N(0,1)), seed 1",
+                   "rel_l2_on_samples": floor}, open(path, "w"), indent=1)
+        print(f"wrote {path}: {floor}")
+        return
     out = {"steps": np.int64(STEPS), "samples": np.int64(SAMPLES), "stride": np.int64(STRIDE),
            "mass0": np.float64(mass0), "mass": np.float64(o.mass()), "threads": np.int64(used)}
     for f in FIELDS:
