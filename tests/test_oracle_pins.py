@@ -209,6 +209,24 @@ def test_mass_conserved_to_roundoff():
     assert abs(o.mass() - m0) / m0 < 4e-14
 
 
+def test_mass_sum_is_the_exactly_rounded_sum():
+    """The domain mass is the sum of rho times the cell volumes; the oracle's compensated sum
+    equals math.fsum (exactly rounded) of the same products to within an ulp, on a field whose
+    plain running sum already loses more than that."""
+    import math
+    wl = W.hill_bubble(nx=64, ny=64, nz=48, dx=250.0, dz0=60.0, ratio=1.03, h0=300.0)
+    o = make_oracle(wl)
+    rng = np.random.default_rng(5)
+    o.set("rho", o.get("rho") * (1.0 + 0.3 * rng.standard_normal(o.shape_c)))
+    terms = (o.get("rho") * o.geom("Hc") * wl.dx * wl.dy).ravel()
+    exact = math.fsum(terms)
+    assert abs(o.mass() - exact) <= 2.3e-16 * exact
+    plain = 0.0
+    for x in terms:
+        plain += x
+    assert abs(plain - exact) > 2.3e-16 * exact     # the case is one a plain sum gets wrong
+
+
 def test_rest_over_terrain_stays_at_rest():
     """A resting hydrostatic atmosphere over a hill stays exactly at rest (p' = 0, B = 0)."""
     wl = W.hill_bubble(nx=16, ny=16, nz=12, dx=300.0, dz0=120.0, ratio=1.02).with_(dtheta=None)
