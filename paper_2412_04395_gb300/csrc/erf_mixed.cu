@@ -144,10 +144,11 @@ __global__ void k_mx_prep(Geo g, MxBase mb, CF5f st, float *ux, float *vy, float
     const int j = blockIdx.y, k = blockIdx.z;
     const long long n = ((long long)k * g.ny + j) * g.nx + i;
     if (k < g.nz) {
+        const long long oxm = i > 0 ? -1 : g.nx - 1, oym = j > 0 ? -(long long)g.nx : g.nxy - g.nx;
         float dr = st.r[n], r0 = mb.rho0f[k], dz = mb.dzf[k];
         float ru = st.u[n], rv = st.v[n];
-        ux[n] = ru / (r0 + 0.5f * (fval(g, st.r, i - 1, j, k) + dr));
-        vy[n] = rv / (r0 + 0.5f * (fval(g, st.r, i, j - 1, k) + dr));
+        ux[n] = ru / (r0 + 0.5f * (__ldg(st.r + n + oxm) + dr));
+        vy[n] = rv / (r0 + 0.5f * (__ldg(st.r + n + oym) + dr));
         mfx[n] = dz * ru;
         mfy[n] = dz * rv;
     }
@@ -702,17 +703,18 @@ __global__ void k_mx_rhs_cells(Geo g, MxBase mb, const float *mfx, const float *
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
     const long long c = ((long long)k * g.ny + j) * g.nx + i;
+    const NbrOff o = nbr_off(g, i, j);
     float rdx = mb.rdx, rdy = mb.rdy, rH = mb.rdzf[k];
-    float mxm = mfx[c], mxp = __ldg(mfx + cixw(g, i + 1, j, k));
-    float mym = mfy[c], myp = __ldg(mfy + cixw(g, i, j + 1, k));
-    float omm = (k == 0) ? 0.f : __ldg(rw + cix(g, i, j, k));
-    float omp = (k == g.nz - 1) ? 0.f : __ldg(rw + cix(g, i, j, k + 1));
+    float mxm = mfx[c], mxp = __ldg(mfx + c + o.xp);
+    float mym = mfy[c], myp = __ldg(mfy + c + o.yp);
+    float omm = (k == 0) ? 0.f : __ldg(rw + c);
+    float omp = (k == g.nz - 1) ? 0.f : __ldg(rw + c + g.nxy);
     // face mass fluxes carry the face height, so the whole divergence is divided by the cell height
     float Rrho = -((mxp - mxm) * rdx + (myp - mym) * rdy + (omp - omm)) * rH;
     Rr[c] = Rrho;
     // theta fluxes (k_mx_flux_theta); the bottom face's is moved to the theta0_k reference
-    float fxm = __ldg(fth.x + c), fxp = __ldg(fth.x + cixw(g, i + 1, j, k));
-    float fym = __ldg(fth.y + c), fyp = __ldg(fth.y + cixw(g, i, j + 1, k));
+    float fxm = __ldg(fth.x + c), fxp = __ldg(fth.x + c + o.xp);
+    float fym = __ldg(fth.y + c), fyp = __ldg(fth.y + c + o.yp);
     float fzm = k > 0 ? __ldg(fth.z + c) + omm * dth0(mb, k - 1, k) : 0.f;
     float fzp = k < g.nz - 1 ? __ldg(fth.z + c + g.nxy) : 0.f;
     float r = mb.th0f[k] * Rrho - ((fxp - fxm) * rdx + (fyp - fym) * rdy + (fzp - fzm)) * rH;
@@ -724,14 +726,15 @@ __global__ void k_mx_rhs_u(Geo g, MxBase mb, CF5f st, const float *pp, FluxF fm,
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
     const long long c = ((long long)k * g.ny + j) * g.nx + i;
+    const NbrOff o = nbr_off(g, i, j);
     float rdx = mb.rdx, rdy = mb.rdy, rH = mb.rdzf[k];
-    float div = (__ldg(fm.x + c) - __ldg(fm.x + cixw(g, i - 1, j, k))) * rdx
-              + (__ldg(fm.y + cixw(g, i, j + 1, k)) - __ldg(fm.y + c)) * rdy + (__ldg(fm.z + c + g.nxy) - __ldg(fm.z + c));
+    float div = (__ldg(fm.x + c) - __ldg(fm.x + c + o.xm)) * rdx
+              + (__ldg(fm.y + c + o.yp) - __ldg(fm.y + c)) * rdy + (__ldg(fm.z + c + g.nxy) - __ldg(fm.z + c));
     float r = -div * rH;
-    r -= (pp[c] - fval(g, pp, i - 1, j, k)) * rdx;
+    r -= (pp[c] - __ldg(pp + c + o.xm)) * rdx;
     if (mb.f_cor != 0.f) {
-        float rvx = 0.25f * (fval(g, st.v, i - 1, j, k) + fval(g, st.v, i, j, k) + fval(g, st.v, i - 1, j + 1, k) + fval(g, st.v, i, j + 1, k));
-        float rhx = mb.rho0f[k] + 0.5f * (fval(g, st.r, i - 1, j, k) + st.r[c]);
+        float rvx = 0.25f * (__ldg(st.v + c + o.xm) + __ldg(st.v + c) + __ldg(st.v + c + o.xm + o.yp) + __ldg(st.v + c + o.yp));
+        float rhx = mb.rho0f[k] + 0.5f * (__ldg(st.r + c + o.xm) + st.r[c]);
         r += mb.f_cor * (rvx - rhx * mb.v_g);
     }
     Ru[c] = r;
@@ -742,14 +745,15 @@ __global__ void k_mx_rhs_v(Geo g, MxBase mb, CF5f st, const float *pp, FluxF fm,
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z;
     const long long c = ((long long)k * g.ny + j) * g.nx + i;
+    const NbrOff o = nbr_off(g, i, j);
     float rdx = mb.rdx, rdy = mb.rdy, rH = mb.rdzf[k];
-    float div = (__ldg(fm.x + cixw(g, i + 1, j, k)) - __ldg(fm.x + c)) * rdx
-              + (__ldg(fm.y + c) - __ldg(fm.y + cixw(g, i, j - 1, k))) * rdy + (__ldg(fm.z + c + g.nxy) - __ldg(fm.z + c));
+    float div = (__ldg(fm.x + c + o.xp) - __ldg(fm.x + c)) * rdx
+              + (__ldg(fm.y + c) - __ldg(fm.y + c + o.ym)) * rdy + (__ldg(fm.z + c + g.nxy) - __ldg(fm.z + c));
     float r = -div * rH;
-    r -= (pp[c] - fval(g, pp, i, j - 1, k)) * rdy;
+    r -= (pp[c] - __ldg(pp + c + o.ym)) * rdy;
     if (mb.f_cor != 0.f) {
-        float rux = 0.25f * (fval(g, st.u, i, j - 1, k) + fval(g, st.u, i + 1, j - 1, k) + fval(g, st.u, i, j, k) + fval(g, st.u, i + 1, j, k));
-        float rhy = mb.rho0f[k] + 0.5f * (fval(g, st.r, i, j - 1, k) + st.r[c]);
+        float rux = 0.25f * (__ldg(st.u + c + o.ym) + __ldg(st.u + c + o.xp + o.ym) + __ldg(st.u + c) + __ldg(st.u + c + o.xp));
+        float rhy = mb.rho0f[k] + 0.5f * (__ldg(st.r + c + o.ym) + st.r[c]);
         r -= mb.f_cor * (rux - rhy * mb.u_g);
     }
     Rv[c] = r;
@@ -761,11 +765,12 @@ __global__ void k_mx_rhs_w(Geo g, MxBase mb, CF5f st, const float *pp, FluxF fm,
     const int j = blockIdx.y, k = blockIdx.z;
     const long long n = ((long long)k * g.ny + j) * g.nx + i;
     if (k == 0 || k == g.nz) { Rw[n] = 0.f; return; }
+    const NbrOff o = nbr_off(g, i, j);
     float rdx = mb.rdx, rdy = mb.rdy, rdzc = mb.rdzcf[k];
-    float div = (__ldg(fm.x + cixw(g, i + 1, j, k)) - __ldg(fm.x + n)) * rdx
-              + (__ldg(fm.y + cixw(g, i, j + 1, k)) - __ldg(fm.y + n)) * rdy + (__ldg(fm.z + n) - __ldg(fm.z + n - g.nxy));
+    float div = (__ldg(fm.x + n + o.xp) - __ldg(fm.x + n)) * rdx
+              + (__ldg(fm.y + n + o.yp) - __ldg(fm.y + n)) * rdy + (__ldg(fm.z + n) - __ldg(fm.z + n - g.nxy));
     float r = -div * rdzc;
-    long long c = cix(g, i, j, k), cm = cix(g, i, j, k - 1);
+    long long c = n, cm = n - g.nxy;
     r -= (pp[c] - pp[cm]) * rdzc;
     r += -0.5f * mb.grav * (st.r[cm] + st.r[c]);
     Rw[n] = r;
