@@ -9,7 +9,9 @@ resident in HBM; the working set (~2.7 GB) is far larger than L2, so no flush is
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 N > 1 (under torchrun): independent replicas, one per GPU (the dycore runs one domain per GPU),
-value = total cell-updates over all ranks / max-over-ranks time.
+value = total cell-updates over all ranks / max-over-ranks time.  --shard runs the x-y pencil
+decomposition instead (weak-scaled: one benchmark-sized interior per rank, halo exchange per step;
+on one GPU, --shard-ranks P pencils share it).
 --impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the same
 workload (the method's reference implementation here is that oracle).
 """
@@ -74,9 +76,10 @@ KERNEL_MODEL = {
 # dram__bytes_write.sum of a 128^3 hill-bubble launch / its units; profiles/ has the summary),
 # scaled to the benchmark's units.  A kernel missing here reports traffic null.
 KERNEL_TRAFFIC_PER_UNIT = {"flux_theta": 39.9, "sub_expl": 160.8}
-# the same for the FP32-perturbation kernels (DRAM bytes per unit of a 256 x 256 x 160
-# convective-ABL capture); kernels changed since their capture are left out (traffic null)
-KERNEL_TRAFFIC_PER_UNIT_MIXED = {}
+# the same for the FP32-perturbation kernels: DRAM bytes per cell of one launch of the column sweep
+# in a 384 x 384 x 160 convective-ABL capture (2.232 GB over 23.6 M cells; traffic grows with the
+# cells); kernels changed since their capture are left out (traffic null)
+KERNEL_TRAFFIC_PER_UNIT_MIXED = {"mx_sub_vert": 94.6}
 # mixed path: algorithmic bytes per cell per launch (FP32 fields, FP64 LU factors and d');
 # these kernels are bound by HBM or latency, so their roofline is in GB/s
 KERNEL_MODEL_MIXED = {
@@ -597,6 +600,89 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+def run_sharded(args):
+    """The x-y pencil decomposition (decomp.py), weak-scaled: every rank owns an interior of the
+    benchmark's horizontal size (the global domain is px x py of them), advances its window (the
+    interior plus a halo of one step's reach) and refreshes the halo once per step.  Under
+    torchrun (N > 1) one rank per GPU with the halo strips sent point to point (NCCL); on one GPU
+    (--shard-ranks P) the P windows are handles on the same GPU and the strips are device copies
+    (decomp.LocalRouter), which measures what the decomposition itself costs.  value = interior
+    cell-updates of all ranks / the slowest rank's time."""
+    import torch
+    from paper_2412_04395_gb300 import decomp as D
+    from paper_2412_04395_gb300.erf import Dycore
+    ws, rank, local, pg = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    P = ws if ws > 1 else max(1, args.shard_ranks)
+    px, py = D.shard_grid(P)
+    base = workload(args)
+    g_args = argparse.Namespace(**vars(args))
+    g_args.grid = [base.nx * px, base.ny * py, base.nz]
+    wl = workload(g_args)
+    dec = D.PencilDecomp(wl.nx, wl.ny, px, py, D.step_reach(wl.n_substeps, wl.terrain is not None))
+    mine = [rank] if ws > 1 else list(range(P))
+    eng = {}
+    for r in mine:
+        w = D.window_workload(wl, dec, r)
+        eng[r] = Dycore(w, device=f"cuda:{local}")
+        eng[r].erf_set_initial(w.dtheta, w.u, w.v, w.w)
+    router = D.LocalRouter(dec, [eng[r] for r in range(P)]) if ws == 1 else None
+
+    def step():
+        for r in mine:
+            eng[r].erf_rk3_step(1)
+        if ws > 1:
+            D.exchange(dec, rank, eng[rank], pg)
+        elif P > 1:
+            router.exchange()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    kps = eng[mine[0]].erf_diagnostics()["kernels_per_step"]
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as cs:
+        barrier(pg)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(pg)
+    clocks = cs.summary()
+    sec = max_over_ranks(pg, ev0.elapsed_time(ev1) * 1e-3)
+    interior = base.nx * base.ny * base.nz
+    value = P * interior * args.steps / sec
+    p0 = dec.pencil(mine[0])
+    sends, _ = dec.messages(mine[0])
+    strip_cols = sum(b[1] * b[3] for _, _, _, b in sends)
+    col_bytes = eng[mine[0]].erf_column_block_bytes(1, 1)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+                "data": "synthetic",
+                "config": {"workload": f"{wl.name} sharded", "grid": [wl.nx, wl.ny, wl.nz],
+                           "interior_per_rank": [base.nx, base.ny, base.nz],
+                           "window_per_rank": [p0.nxw, p0.nyw, wl.nz], "halo": dec.halo,
+                           "parallelism": f"pencil{px}x{py}" + ("" if ws > 1 else f"-on-1-gpu"),
+                           "transport": "nccl point-to-point" if ws > 1 else "device copies (one process)",
+                           "l2": "working set >> L2 (no flush needed)"},
+                "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                           "reasons": clocks["reasons"], "samples": clocks["samples"]},
+                "e2e": None, "gpu_launches": kps * args.steps * len(mine),
+                "halo_bytes_per_step_per_rank": strip_cols * col_bytes,
+                "redundant_fraction": p0.nxw * p0.nyw / (base.nx * base.ny) - 1.0,
+                "roofline": None, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+    for d in eng.values():
+        d.close()
+    if pg is not None:
+        pg.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -625,6 +711,10 @@ def main():
                     help="nx ny nz of a smaller window of the workload (profiling runs only)")
     ap.add_argument("--column-fusion", type=int, default=-1, choices=[-1, 0, 1],
                     help="explicit vertical substep part inside the column sweep: -1 by column count")
+    ap.add_argument("--shard", action="store_true",
+                    help="run the x-y pencil decomposition (one pencil per rank, halo exchange per step)")
+    ap.add_argument("--shard-ranks", type=int, default=4,
+                    help="with --shard on one GPU: number of pencils emulated there")
     ap.add_argument("--warp-columns", type=int, default=-1, choices=[-1, 0, 1],
                     help="FP64 column kernels one warp per column (1), one thread (0), by column count (-1)")
     args = ap.parse_args()
@@ -632,6 +722,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.shard:
+        run_sharded(args)
     else:
         run_ours(args)
 

@@ -155,6 +155,26 @@ class PencilDecomp:
         return sends, recvs
 
 
+def shard_grid(n: int):
+    """(px, py) for n ranks: the factorisation n = px * py closest to square, px >= py."""
+    py = int(np.floor(np.sqrt(n)))
+    while n % py:
+        py -= 1
+    return n // py, py
+
+
+def window_workload(wl, decomp: PencilDecomp, rank: int):
+    """The workload of rank `rank`: its window of every initial field and of the nodal terrain,
+    on the window's grid (the spacing, levels and physics of `wl`)."""
+    p = decomp.pencil(rank)
+    kw = dict(nx=p.nxw, ny=p.nyw)
+    for name in ("dtheta", "u", "v", "w", "phi"):
+        a = getattr(wl, name)
+        kw[name] = None if a is None else decomp.window_slices(rank, a)
+    kw["terrain"] = None if wl.terrain is None else decomp.window_nodes(rank, wl.terrain)
+    return wl.with_(**kw)
+
+
 def exchange(decomp: PencilDecomp, rank: int, engine, dist) -> None:
     """Refreshes one rank's halo from its neighbours (collective over all ranks).  `dist` is
     torch.distributed (initialised); the engine's buffers must live where the backend expects

@@ -20,14 +20,9 @@ from conftest import make_oracle
 FIELDS = ("rho", "rhotheta", "rhou", "rhov", "rhow")
 
 
-def window_workload(wl, dec, rank):
-    p = dec.pencil(rank)
-    kw = dict(nx=p.nxw, ny=p.nyw)
-    for name in ("dtheta", "u", "v", "w", "phi"):
-        a = getattr(wl, name)
-        kw[name] = None if a is None else dec.window_slices(rank, a)
-    kw["terrain"] = None if wl.terrain is None else dec.window_nodes(rank, wl.terrain)
-    return wl.with_(**kw)
+def test_shard_grid_is_the_squarest_factorisation():
+    assert [D.shard_grid(n) for n in (1, 2, 3, 4, 6, 8, 12, 16)] == \
+        [(1, 1), (2, 1), (3, 1), (2, 2), (3, 2), (4, 2), (4, 3), (4, 4)]
 
 
 class OracleEngine:
@@ -119,7 +114,7 @@ def test_local_router_matches_the_undivided_run(name, px, py):
     steps = 3
     ref, mass_ref = undivided(wl, steps)
     dec = D.PencilDecomp(wl.nx, wl.ny, px, py, halo_of(wl))
-    orcs = [make_oracle(window_workload(wl, dec, r)) for r in range(dec.size)]
+    orcs = [make_oracle(D.window_workload(wl, dec, r)) for r in range(dec.size)]
     router = D.LocalRouter(dec, [OracleEngine(o) for o in orcs])
     for _ in range(steps):
         for o in orcs:
@@ -147,7 +142,7 @@ def _gloo_rank(rank, world, px, py, name, steps, port, outdir):
     oracle.set_threads(1)
     wl = cases()[name]
     dec = D.PencilDecomp(wl.nx, wl.ny, px, py, halo_of(wl))
-    o = make_oracle(window_workload(wl, dec, rank))
+    o = make_oracle(D.window_workload(wl, dec, rank))
     eng = OracleEngine(o)
     for _ in range(steps):
         o.step(1)

@@ -20,15 +20,6 @@ def _build():
     ge.build()
 
 
-def window_workload(wl, dec, rank):
-    kw = dict(nx=dec.pencil(rank).nxw, ny=dec.pencil(rank).nyw)
-    for name in ("dtheta", "u", "v", "w", "phi"):
-        a = getattr(wl, name)
-        kw[name] = None if a is None else dec.window_slices(rank, a)
-    kw["terrain"] = None if wl.terrain is None else dec.window_nodes(rank, wl.terrain)
-    return wl.with_(**kw)
-
-
 def run_split(wl, px, py, steps):
     from paper_2412_04395_gb300.erf import Dycore
     whole = Dycore(wl)
@@ -39,7 +30,7 @@ def run_split(wl, px, py, steps):
     dec = D.PencilDecomp(wl.nx, wl.ny, px, py, D.step_reach(wl.n_substeps, wl.terrain is not None))
     ranks = []
     for r in range(dec.size):
-        w = window_workload(wl, dec, r)
+        w = D.window_workload(wl, dec, r)
         d = Dycore(w)
         d.erf_set_initial(w.dtheta, w.u, w.v, w.w)
         ranks.append(d)
