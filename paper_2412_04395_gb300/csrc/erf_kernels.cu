@@ -1461,6 +1461,10 @@ constexpr int BS = 256;
 
 // the column kernels with one warp per column: -1 (default) below 2^15 columns, 0 never, 1 always
 // (nz <= 256); set per step enqueue by the handle (erf_set_option ERF_OPT_WARP_COLUMNS)
+// threads per block of the one-thread-per-column kernels: each thread runs a whole column, so an
+// SM's time is its number of columns; with few columns (a few blocks per SM) small blocks spread
+// them evenly over the SMs (128-thread blocks leave some SMs a whole block more than others)
+static int col_block(const Geo &g) { return g.nxy <= (1LL << 18) ? 32 : 128; }
 static thread_local int g_warp_columns = -1;
 void set_warp_columns(int mode) { g_warp_columns = mode; }
 static bool warp_columns(const Geo &g) {
@@ -1616,8 +1620,8 @@ void launch_tri_build(const Geo &g, const Phys &ph, const double *rho, const dou
         LAUNCH("tri_build", s, k_tri_build_warp<<<nblk(g.nxy, TRIW_WARPS), 32 * TRIW_WARPS, 0, s>>>(
                                    g, rho, rt, pi, th, tk, tr, TX, TY, PX, PY, THW, ph));
     else
-        LAUNCH("tri_build", s, k_tri_build<<<nblk(g.nxy, 128), 128, 0, s>>>(g, rho, rt, pi, th, tk, tr, TX, TY, PX, PY,
-                                                                            THW, ph));
+        LAUNCH("tri_build", s, k_tri_build<<<nblk(g.nxy, col_block(g)), col_block(g), 0, s>>>(g, rho, rt, pi, th, tk, tr,
+                                                                                          TX, TY, PX, PY, THW, ph));
 }
 void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *PX, const double *PY, const double *thw,
                     const double *TX, const double *TY, CF5 R, F5 x, double *Om, double *Tp, double *X0, double *Y0,
@@ -1631,8 +1635,9 @@ void launch_substep(const Geo &g, const Phys &ph, Tri tr, const double *PX, cons
         LAUNCH("sub_col", s, k_sub_col_warp<<<nblk(g.nxy, 4), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q,
                                                                            X0, Y0, x.w, Om, dtau * 0.5 * ph.g));
     else
-    LAUNCH("sub_col", s, k_sub_col<<<nblk(g.nxy, 128), 128, 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im, tr.P, tr.Q, X0, Y0,
-                                                                    x.w, Om, dtau * 0.5 * ph.g));
+    LAUNCH("sub_col", s, k_sub_col<<<nblk(g.nxy, col_block(g)), col_block(g), 0, s>>>(g.nz, g.nxy, tr.a, tr.cp, tr.im,
+                                                                                      tr.P, tr.Q, X0, Y0, x.w, Om,
+                                                                                      dtau * 0.5 * ph.g));
     LAUNCH("sub_fin", s, k_sub_fin<<<g3c, 128, 0, s>>>(g, ph, thw, Om, Ash, x, Tp, msz, dtau * ph.b2));
 }
 void launch_tracer_stage(const Geo &g, const Phys &ph, CF5 st, const double *rom, const double *snphi,
