@@ -104,7 +104,7 @@ KERNEL_MODEL_MIXED = {
     "mx_rhs_v":       {"unit": "cell", "bytes": 28},
     "mx_rhs_w":       {"unit": "wface", "bytes": 24},
     "mx_tri_build":   {"unit": "cell", "bytes": 44},
-    "mx_stage_begin": {"unit": "wface", "bytes": 76},
+    "mx_stage_begin": {"unit": "wface", "bytes": 96},   # with the face velocities and mass fluxes
     "mx_prep":        {"unit": "wface", "bytes": 36},
     "mx_stage_end":   {"unit": "wface", "bytes": 60},
 }

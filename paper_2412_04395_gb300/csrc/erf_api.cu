@@ -503,18 +503,15 @@ static void enqueue_step_mixed(erf_handle *h, cudaStream_t s) {
     const erf_config &c = h->cfg;
     mx_wall_bc(g, h->mst.w, s);
     size_t bc = g.nc * sizeof(float), bw = g.nw * sizeof(float);
-    cudaMemcpyAsync(h->msn.r, h->mst.r, bc, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(h->msn.t, h->mst.t, bc, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(h->msn.u, h->mst.u, bc, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(h->msn.v, h->mst.v, bc, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(h->msn.w, h->mst.w, bw, cudaMemcpyDeviceToDevice, s);
+    // S^n = S^t is written by the first stage's opening pass
     if (h->mtphi) cudaMemcpyAsync(h->msnphi, h->mtphi, bc, cudaMemcpyDeviceToDevice, s);
     const double alpha[3] = {1.0 / 3.0, 0.5, 1.0};
     for (int stage = 0; stage < 3; ++stage) {
-        mx_stage_begin(g, h->mb, cf(h->msn), cf(h->mst), h->mx, h->mpp, h->mpi, h->mthp, h->mTp, s);
+        mx_stage_open(g, h->mb, h->msn, cf(h->mst), h->mx, h->mpp, h->mpi, h->mthp, h->mTp, h->mux, h->mvy, h->mwz,
+                      h->mmfx, h->mmfy, stage == 0, s);
         ClIn clin{h->cl_w, h->cl_b, h->cl_stats, h->cl_out, h->cl_nfb};
         mx_slow_rhs(g, h->mb, ph, cf(h->mst), h->mpp, h->mthp, h->mux, h->mvy, h->mwz, h->mmfx, h->mmfy, h->mmu,
-                    h->mflux, h->mR, s, h->cl_ready ? &clin : nullptr, &h->tma);
+                    h->mflux, h->mR, s, h->cl_ready ? &clin : nullptr, &h->tma, false);
         int nsub = stage == 0 ? 1 : (stage == 1 ? c.n_substeps / 2 : c.n_substeps);
         double dtau = stage == 0 ? c.dt / 3.0 : c.dt / c.n_substeps;
         mx_tri_build(g, h->mb, ph, h->mst.r, h->mst.t, h->mpi, h->mthp, dtau, h->mtri, s);

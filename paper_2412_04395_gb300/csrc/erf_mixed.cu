@@ -138,6 +138,56 @@ __global__ void k_mx_stage_begin(Geo g, MxBase mb, CF5f sn, CF5f st, F5f x, floa
     x.w[n] = sn.w[n] - st.w[n];   // on flat grids W'' is Omega'' (the walls are set by the solve)
 }
 
+// The stage's opening pass in one kernel: the EOS quantities and X'' of k_mx_stage_begin and the
+// face velocities and mass fluxes of k_mx_prep, with the same arithmetic, reading the stage state
+// once.  In the first stage of a step S^n is S^t: the pass writes the S^n copy and X'' = 0 (what
+// S^n - S^t gives) instead of reading S^n back.
+template <bool FIRST>
+__global__ void k_mx_stage_open(Geo g, MxBase mb, F5f sn, CF5f st, F5f x, float *pp, float *pi, float *thp,
+                                float *Tp, float *ux, float *vy, float *wz, float *mfx, float *mfy) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long n = ((long long)k * g.ny + j) * g.nx + i;
+    if (k < g.nz) {
+        const float dr = st.r[n], dT = st.t[n], ru = st.u[n], rv = st.v[n];
+        const float xr = dT * mb.rrt0f[k];           // dTh / (rho0 theta0)
+        const float l1 = log1pf(xr);
+        pp[n] = mb.p0f[k] * expm1f(GAMMAf * l1);
+        pi[n] = mb.pi0f[k] * expf(RDCVf * l1);
+        thp[n] = (dT - mb.th0f[k] * dr) / (mb.rho0f[k] + dr);
+        if (FIRST) {
+            sn.r[n] = dr; sn.t[n] = dT; sn.u[n] = ru; sn.v[n] = rv;
+            x.r[n] = 0.f; x.t[n] = 0.f; Tp[n] = 0.f; x.u[n] = 0.f; x.v[n] = 0.f;
+        } else {
+            x.r[n] = sn.r[n] - dr;
+            const float xt = sn.t[n] - dT;
+            x.t[n] = xt;
+            Tp[n] = xt;
+            x.u[n] = sn.u[n] - ru;
+            x.v[n] = sn.v[n] - rv;
+        }
+        const long long oxm = i > 0 ? -1 : g.nx - 1, oym = j > 0 ? -(long long)g.nx : g.nxy - g.nx;
+        const float r0 = mb.rho0f[k], dz = mb.dzf[k];
+        ux[n] = ru / (r0 + 0.5f * (__ldg(st.r + n + oxm) + dr));
+        vy[n] = rv / (r0 + 0.5f * (__ldg(st.r + n + oym) + dr));
+        mfx[n] = dz * ru;
+        mfy[n] = dz * rv;
+    }
+    const float rw = st.w[n];
+    if (FIRST) {
+        sn.w[n] = rw;
+        x.w[n] = 0.f;
+    } else {
+        x.w[n] = sn.w[n] - rw;   // on flat grids W'' is Omega'' (the walls are set by the solve)
+    }
+    float rb;
+    if (k == 0) rb = mb.rho0f[0] + st.r[n];
+    else if (k == g.nz) rb = mb.rho0f[g.nz - 1] + st.r[n - g.nxy];
+    else rb = mb.rhowf[k] + 0.5f * (st.r[n - g.nxy] + st.r[n]);
+    wz[n] = rw / rb;
+}
+
 __global__ void k_mx_prep(Geo g, MxBase mb, CF5f st, float *ux, float *vy, float *wz, float *mfx, float *mfy) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
@@ -1230,10 +1280,22 @@ void mx_stage_begin(const Geo &g, const MxBase &mb, CF5f sn, CF5f st, F5f x, flo
         k_mx_stage_begin<<<g3(g, g.nz + 1), MBX, 0, s>>>(g, mb, sn, st, x, pp, pi, thp, Tp);
     });
 }
+void mx_stage_open(const Geo &g, const MxBase &mb, F5f sn, CF5f st, F5f x, float *pp, float *pi, float *thp,
+                   float *Tp, float *ux, float *vy, float *wz, float *mfx, float *mfy, bool first, cudaStream_t s) {
+    mx_launch("mx_stage_begin", s, [&] {
+        if (first)
+            k_mx_stage_open<true><<<g3(g, g.nz + 1), MBX, 0, s>>>(g, mb, sn, st, x, pp, pi, thp, Tp, ux, vy, wz, mfx,
+                                                                  mfy);
+        else
+            k_mx_stage_open<false><<<g3(g, g.nz + 1), MBX, 0, s>>>(g, mb, sn, st, x, pp, pi, thp, Tp, ux, vy, wz, mfx,
+                                                                   mfy);
+    });
+}
 void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const float *pp, const float *thp,
                  float *ux, float *vy, float *wz, float *mfx, float *mfy, float *mu, float *flux, F5f R, cudaStream_t s,
-                 const ClIn *cl, const MxTma *tma) {
-    mx_launch("mx_prep", s, [&] { k_mx_prep<<<g3(g, g.nz + 1), MBX, 0, s>>>(g, mb, st, ux, vy, wz, mfx, mfy); });
+                 const ClIn *cl, const MxTma *tma, bool prep) {
+    if (prep)
+        mx_launch("mx_prep", s, [&] { k_mx_prep<<<g3(g, g.nz + 1), MBX, 0, s>>>(g, mb, st, ux, vy, wz, mfx, mfy); });
     int learned = ph.closure == 3 && cl;
     const int visc = (ph.closure == 1 || ph.closure == 2) ? 1 : 0;
     const int sgs = (visc || (ph.surface == 1 && !learned)) ? 1 : 0;

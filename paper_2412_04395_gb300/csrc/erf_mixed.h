@@ -104,7 +104,11 @@ bool mx_encode_cell_tile_map(CUtensorMap *map, const float *base, const Geo &g, 
 void selftest_wait_timeout(int max_polls, unsigned *flag, cudaStream_t s);
 void mx_slow_rhs(const Geo &g, const MxBase &mb, const Phys &ph, CF5f st, const float *pp, const float *thp,
                  float *ux, float *vy, float *wz, float *mfx, float *mfy, float *mu, float *flux, F5f R, cudaStream_t s,
-                 const ClIn *cl, const MxTma *tma);
+                 const ClIn *cl, const MxTma *tma, bool prep = true);
+// the stage's opening pass: EOS quantities, X'' and the face velocities / mass fluxes in one
+// kernel (first: the step's first stage, which also writes the S^n copy)
+void mx_stage_open(const Geo &g, const MxBase &mb, F5f sn, CF5f st, F5f x, float *pp, float *pi, float *thp,
+                   float *Tp, float *ux, float *vy, float *wz, float *mfx, float *mfy, bool first, cudaStream_t s);
 void mx_slow_prep_only(const Geo &g, const MxBase &mb, CF5f st, float *ux, float *vy, float *wz, float *mfx,
                        float *mfy, cudaStream_t s);
 void mx_tri_build(const Geo &g, const MxBase &mb, const Phys &ph, const float *dr, const float *dT, const float *pi,
