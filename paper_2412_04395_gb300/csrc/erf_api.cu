@@ -520,15 +520,18 @@ static void enqueue_step_mixed(erf_handle *h, cudaStream_t s) {
             cudaMemsetAsync(h->mms.y, 0, bc, s);
             cudaMemsetAsync(h->mms.z, 0, bw, s);
         }
+        // without a passive scalar (which needs S^t after the substeps) the stage end is folded into
+        // the last substep's finishing pass (its float4 form, nx % 4 == 0)
+        const bool fold_end = !h->mtphi && g.nx % 4 == 0;
         for (int n = 0; n < nsub; ++n)
             mx_substep(g, h->mb, ph, h->mtri, h->mpi, h->mthp, cf(h->mR), h->mx, h->mTp, h->mdbuf, h->mX0, h->mY0,
-                       h->mms, fuse_columns(h), dtau, s);
+                       h->mms, fuse_columns(h), dtau, s, fold_end && n == nsub - 1 ? &h->mst : nullptr);
         // the passive scalar after the substeps, from the stage state S^t (the pressure and flux
         // scratch are free until the next stage begins)
         if (h->mtphi)
             mx_tracer_stage(g, h->mb, ph, h->mst.r, h->mmfx, h->mmfy, h->mst.w, h->msnphi, h->mms, nsub,
                             alpha[stage] * c.dt, h->mpp, h->mflux, h->mtphi, s);
-        mx_stage_end(g, h->mst, cf(h->mx), s);
+        if (!fold_end) mx_stage_end(g, h->mst, cf(h->mx), s);
     }
 }
 

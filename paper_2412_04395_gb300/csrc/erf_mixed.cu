@@ -1103,7 +1103,13 @@ __device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret
 __device__ __forceinline__ float4 ldw4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 __device__ __forceinline__ float &el(float4 &v, int e) { return (&v.x)[e]; }
-__global__ void k_mx_sub_fin4(Geo g, MxBase mb, Phys ph, const float *thp, F5f x, float *Tt, float dtf, float *msz) {
+// LAST: the stage's last substep on a handle without a passive scalar.  The stage end
+// S^t += X'' is folded in: the finished Theta'', rho'' and the substep's U'', V'', W'' are added to
+// S^t here (the same single additions the stage-end pass makes), and X'' and Theta~, which the next
+// stage's opening pass overwrites, are not stored.
+template <bool LAST>
+__global__ void k_mx_sub_fin4(Geo g, MxBase mb, Phys ph, const float *thp, F5f x, float *Tt, float dtf, float *msz,
+                              F5f st) {
     const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (i >= g.nx) return;
     const int j = blockIdx.y, k = blockIdx.z, nz = g.nz;
@@ -1136,6 +1142,24 @@ __global__ void k_mx_sub_fin4(Geo g, MxBase mb, Phys ph, const float *thp, F5f x
         el(xt, e) = v;
         el(xr, e) -= db * (omf_up - omf);
         el(tt, e) = v + bd * (v - el(told, e));
+    }
+    if (LAST) {
+        auto add4 = [&](float *f, float4 v) {
+            float4 a = ldw4(f + c);
+            for (int e = 0; e < 4; ++e) el(a, e) += el(v, e);
+            st4(f + c, a);
+        };
+        add4(st.r, xr);
+        add4(st.t, xt);
+        add4(st.u, ldw4(x.u + c));
+        add4(st.v, ldw4(x.v + c));
+        add4(st.w, om);                               // W'' at the cell's bottom face
+        if (k == nz - 1) {                            // and the lid
+            float4 a = ldw4(st.w + c + nxy), b = omu;
+            for (int e = 0; e < 4; ++e) el(a, e) += el(b, e);
+            st4(st.w + c + nxy, a);
+        }
+        return;
     }
     st4(x.t + c, xt);
     st4(x.r + c, xr);
@@ -1406,7 +1430,7 @@ void mx_tri_build(const Geo &g, const MxBase &mb, const Phys &ph, const float *d
 }
 void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, TriM tr, const float *pi, const float *thp, CF5f R,
                 F5f x, float *Tt, double *dbuf, float *X0, float *Y0, TrSum ms, int fuse_columns, double dtau,
-                cudaStream_t s) {
+                cudaStream_t s, const F5f *stage_end) {
     const dim3 blk(128), grd((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)g.nz);
     const float dtf = (float)dtau, Gg = (float)(dtau * 0.5 * ph.g);
     mx_launch("mx_sub_horiz", s, [&] {
@@ -1435,7 +1459,14 @@ void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, TriM tr, const f
     }
     if (g.nx % 4 == 0) {
         const dim3 grd4((unsigned)((g.nx / 4 + 127) / 128), (unsigned)g.ny, (unsigned)g.nz);
-        mx_launch("mx_sub_fin", s, [&] { k_mx_sub_fin4<<<grd4, blk, 0, s>>>(g, mb, ph, thp, x, Tt, dtf, ms.z); });
+        if (stage_end)
+            mx_launch("mx_sub_fin", s, [&] {
+                k_mx_sub_fin4<true><<<grd4, blk, 0, s>>>(g, mb, ph, thp, x, Tt, dtf, ms.z, *stage_end);
+            });
+        else
+            mx_launch("mx_sub_fin", s, [&] {
+                k_mx_sub_fin4<false><<<grd4, blk, 0, s>>>(g, mb, ph, thp, x, Tt, dtf, ms.z, F5f{});
+            });
     } else {
         mx_launch("mx_sub_fin", s, [&] { k_mx_sub_fin<<<grd, blk, 0, s>>>(g, mb, ph, thp, x, Tt, dtf, ms.z); });
     }

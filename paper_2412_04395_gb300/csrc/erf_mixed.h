@@ -122,7 +122,7 @@ struct TrSum {
 // sweep (k_mx_sub_vert), 0 as its own per-cell kernel before the sweep
 void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, TriM tr, const float *pi, const float *thp, CF5f R,
                 F5f x, float *Tt, double *dbuf, float *X0, float *Y0, TrSum ms, int fuse_columns, double dtau,
-                cudaStream_t s);
+                cudaStream_t s, const F5f *stage_end = nullptr);
 void mx_stage_end(const Geo &g, F5f st, CF5f x, cudaStream_t s);
 // rho phi^(s) from S^n's rho phi and the stage's averaged mass fluxes (phi and flux are scratch)
 void mx_tracer_stage(const Geo &g, const MxBase &mb, const Phys &ph, const float *dr, const float *mfx,
