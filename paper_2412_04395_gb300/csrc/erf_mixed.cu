@@ -996,15 +996,17 @@ __global__ void __launch_bounds__(128) k_mx_sub_col(int nz, long long nxy, const
 // never leave registers and W'' is read once; then the back substitution.  The horizontal
 // neighbours are the adjacent columns of the same level (coalesced across the warp).
 template <int UNROLL>
-__global__ void __launch_bounds__(128, 8) k_mx_sub_vert(Geo g, MxBase mb, const float *__restrict__ thp,
+__global__ void __launch_bounds__(128, 16) k_mx_sub_vert(Geo g, MxBase mb, const float *__restrict__ thp,
                                                         const float *__restrict__ Rr, const float *__restrict__ Rt,
                                                         const float *__restrict__ Rw, F5f x, float *__restrict__ Tt,
                                                         const float *__restrict__ ta, const double *__restrict__ tcp,
                                                         const double *__restrict__ tim, const float *__restrict__ tP,
                                                         const float *__restrict__ tQ, double *__restrict__ dbuf,
                                                         float dtf, float Gg, TrSum ms) {
-    // 32-bit indices throughout (grids hold fewer than 2^31 w-points), which keeps the kernel
-    // inside the 64 registers that 8 resident blocks per SM allow
+    // 32-bit indices throughout (grids hold fewer than 2^31 w-points).  The sweep waits on its
+    // loads, so it runs at the SM's full 64 warps (16 blocks, 32 registers a thread): measured at
+    // 2048^2 x 160 against 8 blocks (64 registers) and a 4-level unroll, 177 against 208 ms per
+    // step; deeper unrolling with fewer blocks was slower still
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const int nxy = (int)g.nxy;
     if (n >= nxy) return;
@@ -1441,7 +1443,7 @@ void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, TriM tr, const f
     const bool deep = g.nxy >= (1LL << 20);
     if (fuse_columns) {
         mx_launch("mx_sub_vert", s, [&] {
-            k_mx_sub_vert<4><<<nb(g.nxy, 128), 128, 0, s>>>(g, mb, thp, R.r, R.t, R.w, x, Tt, tr.a, tr.cp, tr.im, tr.P,
+            k_mx_sub_vert<1><<<nb(g.nxy, 128), 128, 0, s>>>(g, mb, thp, R.r, R.t, R.w, x, Tt, tr.a, tr.cp, tr.im, tr.P,
                                                             tr.Q, dbuf, dtf, Gg, ms);
         });
     } else {
