@@ -995,8 +995,8 @@ __global__ void __launch_bounds__(128) k_mx_sub_col(int nz, long long nxy, const
 // k_mx_sub_expl, in the same order) feed the row of the face below it at once, so X0 and Y0
 // never leave registers and W'' is read once; then the back substitution.  The horizontal
 // neighbours are the adjacent columns of the same level (coalesced across the warp).
-template <int UNROLL>
-__global__ void __launch_bounds__(128, 16) k_mx_sub_vert(Geo g, MxBase mb, const float *__restrict__ thp,
+template <int UNROLL, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_mx_sub_vert(Geo g, MxBase mb, const float *__restrict__ thp,
                                                         const float *__restrict__ Rr, const float *__restrict__ Rt,
                                                         const float *__restrict__ Rw, F5f x, float *__restrict__ Tt,
                                                         const float *__restrict__ ta, const double *__restrict__ tcp,
@@ -1004,9 +1004,11 @@ __global__ void __launch_bounds__(128, 16) k_mx_sub_vert(Geo g, MxBase mb, const
                                                         const float *__restrict__ tQ, double *__restrict__ dbuf,
                                                         float dtf, float Gg, TrSum ms) {
     // 32-bit indices throughout (grids hold fewer than 2^31 w-points).  The sweep waits on its
-    // loads, so it runs at the SM's full 64 warps (16 blocks, 32 registers a thread): measured at
-    // 2048^2 x 160 against 8 blocks (64 registers) and a 4-level unroll, 177 against 208 ms per
-    // step; deeper unrolling with fewer blocks was slower still
+    // loads: when the grid has more than 8 blocks per SM it runs at up to the SM's full 64 warps
+    // (MINB 16, 32 registers, no unrolling; at 2048^2 x 160 174 against 208 ms per step for 8
+    // blocks with a 4-level unroll, at 512^2 x 256 the step 58 against 63 ms), with fewer columns
+    // at 8 blocks with the unroll (at 384^2 columns, 7.6 blocks per SM, 473 against 514 us per
+    // launch).  The arithmetic is the same in both forms.
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const int nxy = (int)g.nxy;
     if (n >= nxy) return;
@@ -1441,10 +1443,22 @@ void mx_substep(const Geo &g, const MxBase &mb, const Phys &ph, TriM tr, const f
     // deeper unrolling keeps more loads in flight once there are enough columns to fill the GPU
     // (measured: 12% faster at 1024^2 columns, 30% slower at 256^2)
     const bool deep = g.nxy >= (1LL << 20);
+    // the column sweep's grid supplies more blocks than the 8 per SM the unrolled form can hold
+    static int sm_count = 0;
+    if (sm_count == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const bool full_sms = (long long)nb(g.nxy, 128) > 8LL * sm_count;
     if (fuse_columns) {
         mx_launch("mx_sub_vert", s, [&] {
-            k_mx_sub_vert<1><<<nb(g.nxy, 128), 128, 0, s>>>(g, mb, thp, R.r, R.t, R.w, x, Tt, tr.a, tr.cp, tr.im, tr.P,
-                                                            tr.Q, dbuf, dtf, Gg, ms);
+            if (full_sms)
+                k_mx_sub_vert<1, 16><<<nb(g.nxy, 128), 128, 0, s>>>(g, mb, thp, R.r, R.t, R.w, x, Tt, tr.a, tr.cp, tr.im,
+                                                                    tr.P, tr.Q, dbuf, dtf, Gg, ms);
+            else
+                k_mx_sub_vert<4, 8><<<nb(g.nxy, 128), 128, 0, s>>>(g, mb, thp, R.r, R.t, R.w, x, Tt, tr.a, tr.cp, tr.im,
+                                                                   tr.P, tr.Q, dbuf, dtf, Gg, ms);
         });
     } else {
         mx_launch("mx_sub_expl", s, [&] {
